@@ -1,0 +1,177 @@
+/* feti.h -- C ABI of the GB300 FETI dual-operator library.
+ *
+ * The library assembles and applies the FETI dual operator
+ *     F = sum_i B_i K_i^+ B_i^T                       (arXiv 2502.08382, Sec. II, eqs. 6-9)
+ * explicitly on one GPU: for every subdomain i it regularises K_i with fixing
+ * DOFs (K^+ = K_reg^{-1}, Sec. III), factorises K_reg = L L^T (Sec. III), forms
+ * X_i = L^{-1} P B_i^T with a pruned triangular solve and F_i = X_i^T X_i
+ * (the SYRK path of Sec. IV, Table I), and applies F p every PCPG iteration
+ * (Algorithm 1) as a batched packed-tile SYMV with the scatter/gather of
+ * Algorithm 2 fused in.
+ *
+ * Conventions for every entry point:
+ *  - Host pointers are borrowed for the duration of the call and deep-copied;
+ *    the caller keeps ownership.
+ *  - Device pointers (suffix _dev) are caller-owned, hold FP64 values, and are
+ *    used on the context's stream (feti_options.stream); calls are ordered on
+ *    that stream and return before the GPU work completes unless stated.
+ *  - Every call returns a feti_status; nothing is thrown across the ABI.
+ *    The first error is sticky: later calls on the same context return
+ *    FETI_ERR_STATE until feti_destroy.  FETI_ERR_NOT_CONVERGED is
+ *    informative and not sticky.  feti_last_error gives the message.
+ *  - Dual vectors have n_lambda entries in the global multiplier order.
+ */
+#ifndef FETI_GB300_H
+#define FETI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FETI_OK = 0,
+  FETI_ERR_ARG = 1,           /* invalid argument (shape, index, missing pointer) */
+  FETI_ERR_ALLOC = 2,         /* device allocation failed */
+  FETI_ERR_NOT_SPD = 3,       /* a Cholesky pivot of some K_reg,i was not positive */
+  FETI_ERR_NOT_CONVERGED = 4, /* PCPG stopped at maxit or broke down (informative) */
+  FETI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  FETI_ERR_STATE = 6,         /* call out of order, or an earlier error is sticky */
+  FETI_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+} feti_status;
+
+typedef enum {
+  FETI_PREC_FP64 = 0,       /* FP64 everywhere; F_i stored as FP64 tiles */
+  FETI_PREC_TF32 = 1,       /* TRSM updates / SYRK on tensor cores in TF32, F_i as FP32 tiles */
+  FETI_PREC_SPLIT_BF16 = 2  /* as TF32 but each FP32 operand split into two bf16 halves */
+} feti_precision;
+
+/* One subdomain (Sec. II, eq. 2 block i).  All arrays are host memory. */
+typedef struct {
+  int32_t n;                  /* DOFs of the subdomain */
+  int64_t nnz;                /* entries of K_i */
+  const int64_t* K_rowptr;    /* [n+1] CSR row pointers of the FULL symmetric K_i */
+  const int32_t* K_col;       /* [nnz] column indices, sorted within each row */
+  const double* K_val;        /* [nnz] values */
+  int32_t m;                  /* rows of B_i (multipliers touching this subdomain) */
+  const int64_t* B_rowptr;    /* [m+1] CSR of B_i (m x n); exactly one entry per row */
+  const int32_t* B_col;       /* [m] local DOF of each row */
+  const double* B_val;        /* [m] +1 or -1 */
+  const int32_t* B_lambda;    /* [m] global multiplier id of each row (strictly increasing) */
+  int32_t d;                  /* dimension of ker K_i (0: not floating, no regularisation) */
+  const double* R;            /* [n*d] column-major basis of ker K_i (eq. 4) */
+  const double* f;            /* [n] load vector */
+  int32_t nfix;               /* fixing DOFs; must equal d (a generalised inverse needs it) */
+  const int32_t* fix_dofs;    /* [nfix] DOFs penalised by rho = max diag K_i */
+  const double* coords;       /* [n*3] node coordinates of each DOF, or NULL (ordering hint) */
+  int32_t nelem, edofs;       /* optional element data for feti_adjoint (0 if unused) */
+  const int32_t* elem_dofs;   /* [nelem*edofs] local DOFs of each element */
+  const double* dKe_ref;      /* [edofs*edofs] shared reference element derivative */
+  const double* dKe_scale;    /* [nelem] d K_e / d theta_e = dKe_scale[e] * dKe_ref */
+} feti_subdomain;
+
+typedef struct {
+  int32_t nsub;
+  const feti_subdomain* sub;  /* [nsub] */
+  int32_t n_lambda;           /* length of the dual vectors */
+  const double* c;            /* [n_lambda] right-hand side of the gluing/Dirichlet rows (eq. 2) */
+} feti_problem;
+
+typedef struct {
+  feti_precision prec;
+  int32_t refine_every;       /* PCPG: recompute the FP64 residual every k iterations (0 = never) */
+  double tol;                 /* PCPG: stop when ||P r|| <= tol * ||P r_0|| */
+  int32_t maxit;
+  int32_t recompute_X;        /* reserved: 1 = do not keep X_i after assembly */
+  void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator (NULL: cudaMalloc) */
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  void* stream;               /* cudaStream_t; NULL = legacy default stream */
+  int32_t leaf_dofs;          /* nested-dissection leaf size (0 = 64) */
+  int32_t use_coords;         /* 1 = coordinate bisection when coords are given */
+} feti_options;
+
+typedef struct {
+  int32_t iterations;
+  int32_t refinements;
+  double rel_residual;        /* ||P r|| / ||P r_0|| in FP64 at exit */
+  int32_t converged;
+} feti_solve_info;
+
+typedef struct {
+  /* sizes */
+  int32_t nsub, n_lambda, npatterns, nbplans;
+  int64_t sum_n, sum_m, L_doubles, X_elems, F_elems, workspace_bytes, device_bytes;
+  /* algorithmic work (counted by the symbolic phase) */
+  double chol_flops, trsm_flops, syrk_flops, syrk_exec_flops;
+  double apply_bytes;         /* algorithmic bytes of one explicit apply */
+  double implicit_bytes;      /* factor bytes read by one implicit apply */
+  /* last feti_assemble, CUDA-event times on the context's stream (ms) */
+  double t_chol_ms, t_trsm_ms, t_syrk_ms, t_coarse_ms, t_assemble_ms;
+  double t_symbolic_ms;       /* host analysis time in feti_create */
+} feti_stats;
+
+typedef struct feti_ctx feti_ctx;
+
+/* Analyse, copy inputs to the device and plan memory (Algorithm 2,
+ * "preparation").  Symbolic analysis runs on host threads once per distinct
+ * sparsity pattern.  Errors: FETI_ERR_ARG (malformed CSR, B row without a
+ * single +-1, nfix != d, non-increasing B_lambda), FETI_ERR_ALLOC, FETI_ERR_CUDA. */
+feti_status feti_create(const feti_problem* prob, const feti_options* opt, feti_ctx** out);
+
+/* Replace the values of K_i (same pattern) for the next feti_assemble
+ * (Algorithm 2: numeric values change between steps).  K_val is host memory. */
+feti_status feti_update_values(feti_ctx* ctx, int32_t sub, const double* K_val);
+
+/* Numeric phase (Algorithm 2, "preprocessing"): regularise, factorise,
+ * pruned TRSM, SYRK into packed F_i tiles, and set up the coarse problem
+ * G^T G (eqs. 6-8).  Synchronises the stream.  Errors: FETI_ERR_NOT_SPD. */
+feti_status feti_assemble(feti_ctx* ctx);
+
+/* Explicit application q = F p (eq. 12 summed over subdomains; scatter,
+ * per-subdomain SYMV and gather of Algorithm 2) with the stored F_i.
+ * p_dev, q_dev: [n_lambda] device FP64. */
+feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev);
+
+/* Implicit application q = sum_i B_i L_i^{-T} L_i^{-1} B_i^T p (eq. 11) in FP64. */
+feti_status feti_apply_implicit(feti_ctx* ctx, const double* p_dev, double* q_dev);
+
+/* Projected PCPG (Algorithm 1, M = I) for the dual problem (eq. 7), then
+ * alpha (eq. 8) and u (eq. 5).  lambda_dev [n_lambda], alpha_dev [sum d_i],
+ * u_dev [sum n_i] (subdomains concatenated in order); any may be NULL except
+ * lambda_dev.  Synchronises.  Returns FETI_ERR_NOT_CONVERGED (informative)
+ * when maxit is reached. */
+feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev,
+                       feti_solve_info* info);
+
+/* Adjoint of L = sum_i <W_i, F_i>: dtheta[e] = -<Z_i^T dK_e Z_i, W_i> with
+ * Z_i = K_reg,i^{-1} B_i^T (derivative of the inverse, rho held fixed).
+ * W_dev: per subdomain m_i x m_i row-major FP64 in B-row order, concatenated;
+ * dtheta_dev: [sum nelem_i] device FP64.  Needs element data at create. */
+feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev);
+
+/* Copy F_i (m_i x m_i, row-major, B-row order, FP64) to host memory. */
+feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host);
+
+feti_status feti_get_stats(feti_ctx* ctx, feti_stats* out);
+const char* feti_last_error(feti_ctx* ctx);
+void feti_destroy(feti_ctx* ctx);
+
+/* Host-only symbolic analysis of one subdomain (no GPU needed): fills
+ * info[0..15] = {n, nsn, max_front, max_width, nnzL, chol_flops, Lsize,
+ * m, Xsize, trsm_flops, syrk_flops, ntile_contrib, chol_stack, rhs_stack,
+ * nroots, 0} and, if perm_out is not NULL, the fill-reducing permutation
+ * (perm_out[new] = old DOF).  sn_out, if not NULL, receives
+ * [nsn first columns..., nsn widths..., nsn parents...]. */
+feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, double* info,
+                         int32_t* perm_out, int32_t* sn_out);
+
+/* Library version string. */
+const char* feti_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

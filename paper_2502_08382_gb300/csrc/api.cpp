@@ -1,0 +1,721 @@
+// C ABI of the FETI dual-operator library: create / assemble / apply / query.
+// The solver entry points (implicit apply, PCPG, recovery, adjoint) live in
+// api_solve.cpp.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <stdexcept>
+#include <thread>
+#include <unordered_map>
+
+#include "context.h"
+#include "kernels.h"
+
+using namespace feti;
+
+namespace feti {
+
+feti_status set_error(feti_ctx* c, feti_status s, const std::string& msg) {
+  if (c) {
+    if (c->sticky == FETI_OK && s != FETI_ERR_NOT_CONVERGED) c->sticky = s;
+    c->err = msg;
+  }
+  return s;
+}
+
+void* dalloc(feti_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->opt.dev_alloc) {
+    p = c->opt.dev_alloc(bytes, c->opt.alloc_ctx);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  }
+  if (!p) throw std::bad_alloc();
+  c->bufs.push_back({p, bytes});
+  c->device_bytes += bytes;
+  return p;
+}
+
+}  // namespace feti
+
+namespace {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct ArgError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) throw CudaError(std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+T* upload(feti_ctx* c, const std::vector<T>& v) {
+  T* p = (T*)dalloc(c, v.size() * sizeof(T));
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
+  return p;
+}
+
+feti_status guard(feti_ctx* c) {
+  if (!c) return FETI_ERR_ARG;
+  if (c->sticky != FETI_OK) return FETI_ERR_STATE;
+  return FETI_OK;
+}
+
+void copy_sub(const feti_subdomain& s, SubHost& h, int idx) {
+  auto need = [&](bool ok, const char* what) {
+    if (!ok) throw ArgError("subdomain " + std::to_string(idx) + ": " + what);
+  };
+  need(s.n > 0 && s.m >= 0 && s.d >= 0, "sizes must be n > 0, m >= 0, d >= 0");
+  need(s.K_rowptr && s.K_col && s.K_val, "K arrays missing");
+  need(s.m == 0 || (s.B_rowptr && s.B_col && s.B_val && s.B_lambda), "B arrays missing");
+  need(s.nfix == s.d, "nfix must equal d (one fixing DOF per kernel vector)");
+  need(s.d == 0 || (s.R && s.fix_dofs), "R / fix_dofs missing");
+  need(s.f != nullptr, "f missing");
+  h.n = s.n;
+  h.m = s.m;
+  h.d = s.d;
+  h.nfix = s.nfix;
+  h.rowptr.assign(s.K_rowptr, s.K_rowptr + s.n + 1);
+  need(h.rowptr[0] == 0 && h.rowptr[s.n] == s.nnz, "K_rowptr must start at 0 and end at nnz");
+  for (int i = 0; i < s.n; ++i) need(h.rowptr[i + 1] >= h.rowptr[i], "K_rowptr must be non-decreasing");
+  h.col.assign(s.K_col, s.K_col + s.nnz);
+  h.val.assign(s.K_val, s.K_val + s.nnz);
+  for (int i = 0; i < s.n; ++i)
+    for (int64_t k = h.rowptr[i]; k < h.rowptr[i + 1]; ++k) {
+      need(h.col[k] >= 0 && h.col[k] < s.n, "K column index out of range");
+      need(k == h.rowptr[i] || h.col[k] > h.col[k - 1], "K columns must be sorted and unique per row");
+    }
+  h.bdof.resize(s.m);
+  h.bsign.resize(s.m);
+  h.blam.assign(s.B_lambda, s.B_lambda + s.m);
+  for (int r = 0; r < s.m; ++r) {
+    need(s.B_rowptr[r + 1] - s.B_rowptr[r] == 1, "each B row must hold exactly one entry");
+    int64_t k = s.B_rowptr[r];
+    need(s.B_col[k] >= 0 && s.B_col[k] < s.n, "B column out of range");
+    need(std::fabs(s.B_val[k]) == 1.0, "B entries must be +1 or -1");
+    h.bdof[r] = s.B_col[k];
+    h.bsign[r] = s.B_val[k];
+    need(r == 0 || h.blam[r] > h.blam[r - 1], "B_lambda must be strictly increasing");
+  }
+  h.R.assign(s.R ? s.R : nullptr, s.R ? s.R + (size_t)s.n * s.d : nullptr);
+  h.f.assign(s.f, s.f + s.n);
+  h.fix.assign(s.fix_dofs ? s.fix_dofs : nullptr, s.fix_dofs ? s.fix_dofs + s.nfix : nullptr);
+  for (int k = 0; k < s.nfix; ++k) need(h.fix[k] >= 0 && h.fix[k] < s.n, "fix DOF out of range");
+  if (s.coords) h.coords.assign(s.coords, s.coords + (size_t)s.n * 3);
+  h.nelem = s.nelem;
+  h.edofs = s.edofs;
+  if (s.nelem > 0) {
+    need(s.elem_dofs && s.dKe_ref && s.dKe_scale && s.edofs > 0, "element data incomplete");
+    h.elem_dofs.assign(s.elem_dofs, s.elem_dofs + (size_t)s.nelem * s.edofs);
+    h.dKe_ref.assign(s.dKe_ref, s.dKe_ref + (size_t)s.edofs * s.edofs);
+    h.dKe_scale.assign(s.dKe_scale, s.dKe_scale + s.nelem);
+    for (auto v : h.elem_dofs) need(v >= 0 && v < s.n, "element DOF out of range");
+  }
+}
+
+template <typename F>
+void parallel_for(int n, F fn) {
+  int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  nt = std::min(nt, n);
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::vector<std::string> errs(nt);
+  std::atomic<int> next{0};
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      try {
+        for (int i = next++; i < n; i = next++) fn(i);
+      } catch (std::exception& e) {
+        errs[t] = e.what();
+      }
+    });
+  for (auto& x : th) x.join();
+  for (auto& e : errs)
+    if (!e.empty()) throw ArgError(e);
+}
+
+void build(feti_ctx* c) {
+  using clk = std::chrono::steady_clock;
+  auto t0 = clk::now();
+  const int ns = c->nsub;
+  // ---- distinct patterns
+  std::unordered_map<uint64_t, int> pat_of;
+  std::vector<int> pat_rep;
+  for (int i = 0; i < ns; ++i) {
+    auto& s = c->subs[i];
+    uint64_t h = hash_pattern(s.n, s.rowptr.data(), s.col.data());
+    auto it = pat_of.find(h);
+    if (it == pat_of.end()) {
+      pat_of[h] = (int)pat_rep.size();
+      s.pat = (int)pat_rep.size();
+      pat_rep.push_back(i);
+    } else {
+      s.pat = it->second;
+      auto& r = c->subs[pat_rep[s.pat]];
+      if (r.n != s.n || r.col.size() != s.col.size()) throw ArgError("pattern hash collision");
+    }
+  }
+  SymbolicOptions so;
+  so.leaf_dofs = c->opt.leaf_dofs > 0 ? c->opt.leaf_dofs : 64;
+  so.use_coords = c->opt.use_coords != 0;
+  c->pats.resize(pat_rep.size());
+  parallel_for((int)pat_rep.size(), [&](int p) {
+    auto& s = c->subs[pat_rep[p]];
+    analyse_pattern(s.n, s.rowptr.data(), s.col.data(), s.coords.empty() ? nullptr : s.coords.data(), so,
+                    c->pats[p]);
+  });
+  // ---- distinct RHS plans (pattern, B DOFs)
+  std::map<std::pair<int, uint64_t>, int> bp_of;
+  std::vector<int> bp_rep;
+  for (int i = 0; i < ns; ++i) {
+    auto& s = c->subs[i];
+    uint64_t h = hash_ints(s.bdof.data(), s.m, (uint64_t)s.m * 1315423911ull);
+    auto key = std::make_pair(s.pat, h);
+    auto it = bp_of.find(key);
+    if (it == bp_of.end()) {
+      bp_of[key] = (int)bp_rep.size();
+      s.bp = (int)bp_rep.size();
+      bp_rep.push_back(i);
+    } else {
+      s.bp = it->second;
+      auto& r = c->subs[bp_rep[s.bp]];
+      if (r.m != s.m || !std::equal(r.bdof.begin(), r.bdof.end(), s.bdof.begin()))
+        throw ArgError("B pattern hash collision");
+    }
+  }
+  c->bps.resize(bp_rep.size());
+  c->bp_pat.resize(bp_rep.size());
+  parallel_for((int)bp_rep.size(), [&](int b) {
+    auto& s = c->subs[bp_rep[b]];
+    c->bp_pat[b] = s.pat;
+    plan_rhs(c->pats[s.pat], s.m, s.bdof.data(), c->bps[b]);
+  });
+  c->stats.t_symbolic_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  c->stats.npatterns = (int)c->pats.size();
+  c->stats.nbplans = (int)c->bps.size();
+
+  // ---- concatenate pattern tables
+  std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src;
+  std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs;
+  std::vector<int> pat_sn0(c->pats.size());
+  std::vector<int64_t> pat_diag0(c->pats.size());
+  for (size_t p = 0; p < c->pats.size(); ++p) {
+    auto& P = c->pats[p];
+    pat_sn0[p] = (int)sn_c0.size();
+    int64_t rows0 = rows.size(), ch0 = ch_list.size(), rel0 = rel.size(), km0 = kmap_src.size();
+    for (int s = 0; s < P.nsn; ++s) {
+      sn_c0.push_back(P.sn_c0[s]);
+      sn_w.push_back(P.sn_w[s]);
+      sn_r.push_back(P.sn_r[s]);
+      sn_parent.push_back(P.sn_parent[s]);
+      sn_rows.push_back(rows0 + P.sn_rows_off[s]);
+      ch_off.push_back((int)(ch0 + P.ch_off[s]));
+      rel_off.push_back(rel0 + P.rel_off[s]);
+      Lofs.push_back(P.Lofs[s]);
+      kmap_off.push_back(km0 + P.kmap_off[s]);
+      upd_ofs.push_back(P.upd_stack_ofs[s]);
+    }
+    rows.insert(rows.end(), P.rows.begin(), P.rows.end());
+    ch_list.insert(ch_list.end(), P.ch_list.begin(), P.ch_list.end());
+    rel.insert(rel.end(), P.rel.begin(), P.rel.end());
+    kmap_src.insert(kmap_src.end(), P.kmap_src.begin(), P.kmap_src.end());
+    kmap_dst.insert(kmap_dst.end(), P.kmap_dst.begin(), P.kmap_dst.end());
+    pat_diag0[p] = diag_src.size();
+    diag_src.insert(diag_src.end(), P.diag_src.begin(), P.diag_src.end());
+  }
+  sn_rows.push_back(rows.size());
+  ch_off.push_back((int)ch_list.size());
+  rel_off.push_back(rel.size());
+  kmap_off.push_back(kmap_src.size());
+  // ---- concatenate RHS plans
+  std::vector<int> jb, je, jo, act, spos, tile_off, tile_sn;
+  std::vector<int64_t> Xofs, rhs_ofs;
+  std::vector<int> bp_sn0(c->bps.size()), bp_act0(c->bps.size()), bp_col0(c->bps.size()), bp_tile0(c->bps.size());
+  for (size_t b = 0; b < c->bps.size(); ++b) {
+    auto& B = c->bps[b];
+    bp_sn0[b] = (int)jb.size();
+    bp_act0[b] = (int)act.size();
+    bp_col0[b] = (int)spos.size();
+    bp_tile0[b] = (int)tile_off.size();
+    jb.insert(jb.end(), B.jb.begin(), B.jb.end());
+    je.insert(je.end(), B.je.begin(), B.je.end());
+    jo.insert(jo.end(), B.jo.begin(), B.jo.end());
+    Xofs.insert(Xofs.end(), B.Xofs.begin(), B.Xofs.end());
+    rhs_ofs.insert(rhs_ofs.end(), B.rhs_stack_ofs.begin(), B.rhs_stack_ofs.end());
+    act.insert(act.end(), B.act.begin(), B.act.end());
+    spos.insert(spos.end(), B.spos.begin(), B.spos.end());
+    int base = (int)tile_sn.size();
+    int ntile = B.nb * (B.nb + 1) / 2;
+    for (int t = 0; t < ntile; ++t) tile_off.push_back(base + B.tile_off[t]);
+    tile_sn.insert(tile_sn.end(), B.tile_sn.begin(), B.tile_sn.end());
+  }
+  tile_off.push_back((int)tile_sn.size());
+
+  // ---- per-subdomain layout
+  c->info.resize(ns);
+  std::vector<int> qmap, fix_sn, colsub, colperm;
+  std::vector<double> qsign;
+  std::vector<int64_t> fix_pos;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0;
+  int fixo = 0, alo = 0;
+  double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
+  int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0;
+  size_t esz = c->fp32 ? 4 : 8;
+  double apply_bytes = 0;
+  c->colperm_ofs.resize(ns);
+  for (int i = 0; i < ns; ++i) {
+    auto& s = c->subs[i];
+    auto& P = c->pats[s.pat];
+    auto& B = c->bps[s.bp];
+    SubInfo& I = c->info[i];
+    I.n = s.n;
+    I.m = s.m;
+    I.m_pad = B.m_pad;
+    I.nb = B.nb;
+    I.nsn = P.nsn;
+    I.nact = (int)B.act.size();
+    I.d = s.d;
+    I.nfix = s.nfix;
+    I.sn0 = pat_sn0[s.pat];
+    I.bsn0 = bp_sn0[s.bp];
+    I.act0 = bp_act0[s.bp];
+    I.col0 = bp_col0[s.bp];
+    I.tile0 = bp_tile0[s.bp];
+    I.fix0 = fixo;
+    I.alpha0 = alo;
+    I.kmapb = 0;
+    I.diag0 = pat_diag0[s.pat];
+    I.Kval = Kofs;
+    I.L = Lo;
+    I.X = Xo;
+    I.F = Fo;
+    I.qcol = qo;
+    I.trow = qo;
+    I.dof = dofo;
+    I.R = Ro;
+    I.tpart = tpo;
+    int ntile = B.nb * (B.nb + 1) / 2;
+    Kofs += (int64_t)s.col.size();
+    Lo += P.Lsize;
+    Xo += B.Xsize;
+    Fo += (int64_t)ntile * kT * kT;
+    qo += B.m_pad;
+    dofo += s.n;
+    Ro += (int64_t)s.n * s.d;
+    tpo += (int64_t)ntile * kT;
+    alo += s.d;
+    for (int j = 0; j < B.m_pad; ++j) {
+      if (j < s.m) {
+        int r = B.colperm[j];
+        qmap.push_back(s.blam[r]);
+        qsign.push_back(s.bsign[r]);
+        colperm.push_back(r);
+      } else {
+        qmap.push_back(-1);
+        qsign.push_back(0.0);
+      }
+      colsub.push_back(i);
+    }
+    c->colperm_ofs[i] = (int64_t)colperm.size() - s.m;
+    for (int k = 0; k < s.nfix; ++k) {
+      int nd = P.iperm[s.fix[k]];
+      int sn = P.col2sn[nd];
+      int loc = nd - P.sn_c0[sn];
+      int f = P.sn_w[sn] + P.sn_r[sn];
+      fix_sn.push_back(sn);
+      fix_pos.push_back(P.Lofs[sn] + (int64_t)loc * f + loc);
+    }
+    fixo += s.nfix;
+    chol += P.chol_flops;
+    trsm += B.trsm_flops;
+    syrk += B.syrk_flops;
+    syrke += B.syrk_exec_flops;
+    implb += 2.0 * 8.0 * P.nnzL;
+    max_chol = std::max(max_chol, P.chol_stack);
+    max_cf = std::max(max_cf, P.chol_front);
+    max_rhs = std::max(max_rhs, B.rhs_stack);
+    max_rf = std::max(max_rf, B.rhs_front);
+    apply_bytes += (double)esz * s.m * (s.m + 1) / 2.0 + (double)s.m * (4 + 8 + 8);
+  }
+  apply_bytes += (double)c->nlam * 16.0;
+  c->ncols = qo;
+  c->dtot = alo;
+  c->stats.nsub = ns;
+  c->stats.n_lambda = c->nlam;
+  c->stats.sum_n = dofo;
+  c->stats.sum_m = 0;
+  for (auto& s : c->subs) c->stats.sum_m += s.m;
+  c->stats.L_doubles = Lo;
+  c->stats.X_elems = Xo;
+  c->stats.F_elems = Fo;
+  c->stats.chol_flops = chol;
+  c->stats.trsm_flops = trsm;
+  c->stats.syrk_flops = syrk;
+  c->stats.syrk_exec_flops = syrke;
+  c->stats.apply_bytes = apply_bytes;
+  c->stats.implicit_bytes = implb;
+
+  // ---- lambda -> contributions (deterministic: subdomain order)
+  std::vector<int> c0(c->nlam, -1), c1(c->nlam, -1);
+  for (int i = 0; i < ns; ++i) {
+    auto& I = c->info[i];
+    for (int j = 0; j < I.m; ++j) {
+      int lam = qmap[I.qcol + j];
+      if (lam < 0 || lam >= c->nlam) throw ArgError("B_lambda out of range");
+      if (c0[lam] < 0) c0[lam] = (int)(I.qcol + j);
+      else if (c1[lam] < 0) c1[lam] = (int)(I.qcol + j);
+      else throw ArgError("a multiplier touches more than two subdomains");
+    }
+  }
+
+  // ---- work orders
+  std::vector<int> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return c->pats[c->subs[a].pat].chol_flops > c->pats[c->subs[b].pat].chol_flops;
+  });
+  std::vector<int> order_t(order);
+  std::stable_sort(order_t.begin(), order_t.end(), [&](int a, int b) {
+    return c->bps[c->subs[a].bp].trsm_flops > c->bps[c->subs[b].bp].trsm_flops;
+  });
+  std::vector<int> order_i(order);
+  std::stable_sort(order_i.begin(), order_i.end(), [&](int a, int b) {
+    return c->pats[c->subs[a].pat].nnzL > c->pats[c->subs[b].pat].nnzL;
+  });
+  std::vector<std::pair<double, int2>> sy, ap;
+  for (int i = 0; i < ns; ++i) {
+    auto& B = c->bps[c->subs[i].bp];
+    auto& P = c->pats[c->subs[i].pat];
+    int ntile = B.nb * (B.nb + 1) / 2;
+    for (int t = 0; t < ntile; ++t) {
+      double cost = 1.0;
+      for (int k = B.tile_off[t]; k < B.tile_off[t + 1]; ++k) cost += P.sn_w[B.tile_sn[k]];
+      sy.push_back({cost, make_int2(i, t)});
+    }
+    for (int b = 0; b < B.nb; ++b) ap.push_back({(double)(b + 1), make_int2(i, b)});
+  }
+  std::stable_sort(sy.begin(), sy.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  std::stable_sort(ap.begin(), ap.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  std::vector<int2> syi, api;
+  for (auto& x : sy) syi.push_back(x.second);
+  for (auto& x : ap) api.push_back(x.second);
+  c->nsyrk = (int)syi.size();
+  c->napply = (int)api.size();
+
+  // ---- persistent grids and workspace
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  c->nsm = prop.multiProcessorCount;
+  c->grid_chol = std::min(ns, c->nsm * 2);
+  c->grid_trsm = std::min(ns, c->nsm * 2);
+  c->chol_front = max_cf;
+  c->rhs_front = max_rf;
+  c->ws_stride = std::max(max_cf + max_chol, max_rf + max_rhs);
+  c->ws_stride = (c->ws_stride + 31) / 32 * 32;
+  int gw = std::max(c->grid_chol, c->grid_trsm);
+
+  // ---- device uploads
+  DevPlan& D = c->P;
+  D.sn_c0 = upload(c, sn_c0);
+  D.sn_w = upload(c, sn_w);
+  D.sn_r = upload(c, sn_r);
+  D.sn_parent = upload(c, sn_parent);
+  D.sn_rows = upload(c, sn_rows);
+  D.rows = upload(c, rows);
+  D.ch_off = upload(c, ch_off);
+  D.ch_list = upload(c, ch_list);
+  D.rel_off = upload(c, rel_off);
+  D.rel = upload(c, rel);
+  D.Lofs = upload(c, Lofs);
+  D.kmap_off = upload(c, kmap_off);
+  D.kmap_src = upload(c, kmap_src);
+  D.kmap_dst = upload(c, kmap_dst);
+  D.diag_src = upload(c, diag_src);
+  D.upd_ofs = upload(c, upd_ofs);
+  D.jb = upload(c, jb);
+  D.je = upload(c, je);
+  D.jo = upload(c, jo);
+  D.Xofs = upload(c, Xofs);
+  D.rhs_ofs = upload(c, rhs_ofs);
+  D.act = upload(c, act);
+  D.spos = upload(c, spos);
+  D.tile_off = upload(c, tile_off);
+  D.tile_sn = upload(c, tile_sn);
+  D.qmap = upload(c, qmap);
+  D.qsign = upload(c, qsign);
+  D.fix_sn = upload(c, fix_sn);
+  D.fix_pos = upload(c, fix_pos);
+  D.sub = upload(c, c->info);
+  std::vector<double> kv;
+  kv.reserve(Kofs);
+  std::vector<double> Rall, fall;
+  for (auto& s : c->subs) {
+    kv.insert(kv.end(), s.val.begin(), s.val.end());
+    Rall.insert(Rall.end(), s.R.begin(), s.R.end());
+    fall.insert(fall.end(), s.f.begin(), s.f.end());
+  }
+  c->d_Kval = upload(c, kv);
+  D.Kval = c->d_Kval;
+  c->d_L = (double*)dalloc(c, (size_t)Lo * 8);
+  D.L = c->d_L;
+  D.rho = (double*)dalloc(c, (size_t)ns * 8);
+  c->d_X = dalloc(c, (size_t)Xo * 8);
+  c->d_F = dalloc(c, (size_t)Fo * esz);
+  c->d_ws = (double*)dalloc(c, (size_t)gw * c->ws_stride * 8);
+  c->d_trow = (double*)dalloc(c, (size_t)qo * 8);
+  c->d_tpart = (double*)dalloc(c, (size_t)std::max<int64_t>(tpo, 1) * 8);
+  c->d_qi = (double*)dalloc(c, (size_t)qo * 8);
+  c->d_colsub = upload(c, colsub);
+  c->d_c0 = upload(c, c0);
+  c->d_c1 = upload(c, c1);
+  c->d_queue = (int*)dalloc(c, 64 * sizeof(int));
+  c->d_status = (int*)dalloc(c, sizeof(int));
+  c->d_chol_order = upload(c, order);
+  c->d_trsm_order = upload(c, order_t);
+  c->d_impl_order = upload(c, order_i);
+  c->d_syrk_items = upload(c, syi);
+  c->d_apply_items = upload(c, api);
+  c->d_colperm = upload(c, colperm);
+  c->d_R = upload(c, Rall);
+  c->d_f = upload(c, fall);
+  c->d_c = upload(c, c->c_host);
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+  CK(cudaMemsetAsync(c->d_tpart, 0, (size_t)std::max<int64_t>(tpo, 1) * 8, c->st));
+  c->stats.workspace_bytes = (int64_t)gw * c->ws_stride * 8;
+  for (auto& e : c->ev) CK(cudaEventCreate(&e));
+  CK(cudaStreamSynchronize(c->st));
+  c->stats.device_bytes = (int64_t)c->device_bytes;
+}
+
+}  // namespace
+
+#define API_BEGIN try {
+#define API_END                                                           \
+  }                                                                       \
+  catch (ArgError & e) {                                                  \
+    return set_error(ctx, FETI_ERR_ARG, e.what());                        \
+  }                                                                       \
+  catch (CudaError & e) {                                                 \
+    return set_error(ctx, FETI_ERR_CUDA, e.what());                       \
+  }                                                                       \
+  catch (std::bad_alloc&) {                                               \
+    return set_error(ctx, FETI_ERR_ALLOC, "device or host allocation failed"); \
+  }                                                                       \
+  catch (std::exception & e) {                                            \
+    return set_error(ctx, FETI_ERR_ARG, e.what());                        \
+  }
+
+extern "C" {
+
+const char* feti_version(void) { return "feti-gb300 0.1 (sm_103a)"; }
+
+feti_status feti_create(const feti_problem* prob, const feti_options* opt, feti_ctx** out) {
+  if (!prob || !out || prob->nsub <= 0 || !prob->sub || prob->n_lambda < 0) return FETI_ERR_ARG;
+  *out = nullptr;
+  feti_ctx* ctx = new feti_ctx();
+  API_BEGIN
+  if (opt) ctx->opt = *opt;
+  else {
+    ctx->opt.prec = FETI_PREC_FP64;
+    ctx->opt.tol = 1e-10;
+    ctx->opt.maxit = 1000;
+    ctx->opt.use_coords = 1;
+  }
+  if (ctx->opt.prec < FETI_PREC_FP64 || ctx->opt.prec > FETI_PREC_SPLIT_BF16) throw ArgError("bad precision");
+  ctx->st = (cudaStream_t)ctx->opt.stream;
+  ctx->fp32 = ctx->opt.prec != FETI_PREC_FP64;
+  ctx->nsub = prob->nsub;
+  ctx->nlam = prob->n_lambda;
+  if (prob->n_lambda > 0 && !prob->c) throw ArgError("c missing");
+  ctx->c_host.assign(prob->c ? prob->c : nullptr, prob->c ? prob->c + prob->n_lambda : nullptr);
+  ctx->subs.resize(prob->nsub);
+  for (int i = 0; i < prob->nsub; ++i) copy_sub(prob->sub[i], ctx->subs[i], i);
+  build(ctx);
+  *out = ctx;
+  return FETI_OK;
+  }
+  catch (ArgError& e) {
+    set_error(ctx, FETI_ERR_ARG, e.what());
+  }
+  catch (CudaError& e) {
+    set_error(ctx, FETI_ERR_CUDA, e.what());
+  }
+  catch (std::bad_alloc&) {
+    set_error(ctx, FETI_ERR_ALLOC, "device or host allocation failed");
+  }
+  catch (std::exception& e) {
+    set_error(ctx, FETI_ERR_ARG, e.what());
+  }
+  *out = ctx;  // keep the context so feti_last_error can report; caller destroys it
+  return ctx->sticky;
+}
+
+feti_status feti_update_values(feti_ctx* ctx, int32_t sub, const double* K_val) {
+  feti_status g = guard(ctx);
+  if (g != FETI_OK) return g;
+  API_BEGIN
+  if (sub < 0 || sub >= ctx->nsub || !K_val) throw ArgError("feti_update_values: bad subdomain or values");
+  auto& s = ctx->subs[sub];
+  std::copy(K_val, K_val + s.col.size(), s.val.begin());
+  CK(cudaMemcpyAsync(ctx->d_Kval + ctx->info[sub].Kval, s.val.data(), s.col.size() * 8, cudaMemcpyHostToDevice,
+                     ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->assembled = false;
+  return FETI_OK;
+  API_END
+}
+
+feti_status feti_assemble(feti_ctx* ctx) {
+  feti_status g = guard(ctx);
+  if (g != FETI_OK) return g;
+  API_BEGIN
+  cudaStream_t st = ctx->st;
+  CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  CK(cudaEventRecord(ctx->ev[0], st));
+  launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
+              ctx->grid_chol, ctx->d_status, st);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[1], st));
+  if (ctx->fp32) throw ArgError("mixed-precision assembly is not available in this build");
+  launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, (double*)ctx->d_X, ctx->d_ws,
+              ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, st);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[2], st));
+  launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
+                  std::min(ctx->nsyrk, ctx->nsm * 8), st);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[3], st));
+  CK(cudaEventRecord(ctx->ev[4], st));
+  CK(cudaStreamSynchronize(st));
+  float a, b, cc, d;
+  CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+  CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+  CK(cudaEventElapsedTime(&cc, ctx->ev[2], ctx->ev[3]));
+  CK(cudaEventElapsedTime(&d, ctx->ev[0], ctx->ev[4]));
+  ctx->stats.t_chol_ms = a;
+  ctx->stats.t_trsm_ms = b;
+  ctx->stats.t_syrk_ms = cc;
+  ctx->stats.t_coarse_ms = 0;
+  ctx->stats.t_assemble_ms = d;
+  int status = 0;
+  CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status & kStatNotSPD) return set_error(ctx, FETI_ERR_NOT_SPD, "a Cholesky pivot was not positive");
+  ctx->assembled = true;
+  return FETI_OK;
+  API_END
+}
+
+feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
+  feti_status g = guard(ctx);
+  if (g != FETI_OK) return g;
+  if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_apply before feti_assemble");
+  API_BEGIN
+  cudaStream_t st = ctx->st;
+  int grid = std::min(ctx->napply, ctx->nsm * 4);
+  if (ctx->fp32)
+    launch_apply_rows_f32(ctx->P, ctx->d_apply_items, ctx->napply, (const float*)ctx->d_F, p_dev, ctx->d_trow,
+                          ctx->d_tpart, grid, st);
+  else
+    launch_apply_rows_f64(ctx->P, ctx->d_apply_items, ctx->napply, (const double*)ctx->d_F, p_dev, ctx->d_trow,
+                          ctx->d_tpart, grid, st);
+  launch_apply_cols(ctx->P, ctx->d_colsub, ctx->ncols, ctx->d_trow, ctx->d_tpart, ctx->d_qi, st);
+  launch_gather_lambda(ctx->d_c0, ctx->d_c1, ctx->nlam, ctx->d_qi, q_dev, st);
+  CK(cudaGetLastError());
+  return FETI_OK;
+  API_END
+}
+
+feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host) {
+  feti_status g = guard(ctx);
+  if (g != FETI_OK) return g;
+  if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_get_F before feti_assemble");
+  API_BEGIN
+  if (sub < 0 || sub >= ctx->nsub || !out_host) throw ArgError("feti_get_F: bad arguments");
+  const SubInfo& I = ctx->info[sub];
+  size_t bytes = (size_t)I.m * I.m * 8;
+  double* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, std::max<size_t>(bytes, 8), ctx->st));
+  size_t esz = ctx->fp32 ? 4 : 8;
+  const char* Fsub = (const char*)ctx->d_F + I.F * esz;
+  launch_unpack_F(Fsub, ctx->fp32, I.m, I.nb, ctx->d_colperm + ctx->colperm_ofs[sub], tmp, ctx->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out_host, tmp, bytes, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaFreeAsync(tmp, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return FETI_OK;
+  API_END
+}
+
+feti_status feti_get_stats(feti_ctx* ctx, feti_stats* out) {
+  if (!ctx || !out) return FETI_ERR_ARG;
+  *out = ctx->stats;
+  return FETI_OK;
+}
+
+const char* feti_last_error(feti_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void feti_destroy(feti_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st || true) cudaStreamSynchronize(ctx->st);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& b : ctx->bufs) {
+    if (ctx->opt.dev_free) ctx->opt.dev_free(b.p, ctx->opt.alloc_ctx);
+    else if (!ctx->opt.dev_alloc) cudaFree(b.p);
+  }
+  delete ctx;
+}
+
+feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, double* info, int32_t* perm_out,
+                         int32_t* sn_out) {
+  feti_ctx* ctx = nullptr;
+  if (!sub || !info) return FETI_ERR_ARG;
+  try {
+    SubHost h;
+    copy_sub(*sub, h, 0);
+    SymbolicOptions so;
+    if (opt) {
+      so.leaf_dofs = opt->leaf_dofs > 0 ? opt->leaf_dofs : 64;
+      so.use_coords = opt->use_coords != 0;
+    }
+    PatternPlan P;
+    analyse_pattern(h.n, h.rowptr.data(), h.col.data(), h.coords.empty() ? nullptr : h.coords.data(), so, P);
+    BPlan B;
+    plan_rhs(P, h.m, h.bdof.data(), B);
+    int roots = 0;
+    for (int s = 0; s < P.nsn; ++s) roots += P.sn_parent[s] < 0;
+    double v[16] = {(double)P.n, (double)P.nsn, (double)P.max_f, (double)P.max_w, P.nnzL, P.chol_flops,
+                    (double)P.Lsize, (double)B.m, (double)B.Xsize, B.trsm_flops, B.syrk_flops,
+                    (double)B.tile_sn.size(), (double)P.chol_stack, (double)B.rhs_stack, (double)roots, 0.0};
+    std::memcpy(info, v, sizeof(v));
+    if (perm_out) std::copy(P.perm.begin(), P.perm.end(), perm_out);
+    if (sn_out) {
+      std::copy(P.sn_c0.begin(), P.sn_c0.end(), sn_out);
+      std::copy(P.sn_w.begin(), P.sn_w.end(), sn_out + P.nsn);
+      std::copy(P.sn_parent.begin(), P.sn_parent.end(), sn_out + 2 * P.nsn);
+    }
+    return FETI_OK;
+  } catch (std::exception& e) {
+    (void)ctx;
+    return FETI_ERR_ARG;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Device-side plan layout shared by the FETI kernels.
+//
+// The host symbolic phase (symbolic.cpp) produces one plan per distinct K
+// pattern and one pruned-RHS plan per distinct set of B-touched DOFs; they
+// are concatenated into flat device arrays.  Offsets stored in the tables
+// below are absolute within those flat arrays unless marked "relative".
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace feti {
+
+constexpr int kT = 64;          // F tile edge
+constexpr int kThreads = 256;   // CTA size of the dense kernels
+constexpr int kNB = 32;         // panel block of the dense factorisation / solve
+
+struct SubInfo {
+  int n, m, m_pad, nb, nsn, nact, d, nfix;
+  int sn0;           // pattern supernode base (sn_* arrays)
+  int bsn0;          // bplan supernode base (jb/je/jo/Xofs/rhs_stack_ofs)
+  int act0;          // bplan active-list base
+  int col0;          // bplan sorted-column base (spos)
+  int tile0;         // bplan tile_off base
+  int fix0;          // fix arrays base
+  int alpha0;        // offset of this subdomain's alpha block
+  int pad_;
+  int64_t kmapb;     // base of this pattern's kmap entries (kmap_off values are absolute)
+  int64_t diag0;     // diag_src base
+  int64_t Kval;      // subdomain K values base
+  int64_t L;         // subdomain L base (doubles)
+  int64_t X;         // subdomain X base (elements)
+  int64_t F;         // subdomain F tiles base (elements)
+  int64_t qcol;      // subdomain sorted-column arrays base (m_pad entries)
+  int64_t dof;       // subdomain DOF-vector base (n entries)
+  int64_t R;         // subdomain R base (n*d, column-major)
+  int64_t trow;      // base of this subdomain's tile-row partials (nb*kT entries) == qcol
+  int64_t tpart;     // base of this subdomain's per-tile column partials (ntile*kT entries)
+};
+
+struct DevPlan {
+  const SubInfo* sub;
+  // pattern tables
+  const int* sn_c0;
+  const int* sn_w;
+  const int* sn_r;
+  const int* sn_parent;
+  const int64_t* sn_rows;    // [sn] absolute offset of struct-below rows (size nsn+1 per pattern)
+  const int* rows;
+  const int* ch_off;         // [sn] absolute offsets into ch_list (size nsn+1 per pattern)
+  const int* ch_list;        // local supernode ids
+  const int64_t* rel_off;    // [sn] absolute offsets into rel (size nsn+1 per pattern)
+  const int* rel;
+  const int64_t* Lofs;       // [sn] relative to the subdomain's L base
+  const int64_t* kmap_off;   // [sn] absolute (size nsn+1 per pattern)
+  const int* kmap_src;       // relative to the subdomain's K values
+  const int* kmap_dst;       // relative to the subdomain's L base
+  const int* diag_src;       // relative to the subdomain's K values
+  const int64_t* upd_ofs;    // [sn] relative to the CTA stack
+  // bplan tables
+  const int* jb;
+  const int* je;
+  const int* jo;
+  const int64_t* Xofs;       // [bsn] relative to the subdomain's X base
+  const int64_t* rhs_ofs;    // [bsn] relative to the CTA stack
+  const int* act;            // local supernode ids
+  const int* spos;           // [col0 + j] new-numbered DOF of sorted column j
+  const int* tile_off;       // [tile0 + t] absolute offsets into tile_sn
+  const int* tile_sn;        // local supernode ids
+  // per subdomain
+  const int* qmap;           // [qcol + j] global multiplier of sorted column j, -1 for padding
+  const double* qsign;       // [qcol + j] sign of B in sorted column j (0 for padding)
+  const int* fix_sn;         // [fix0 + k] supernode holding fixing DOF k
+  const int64_t* fix_pos;    // [fix0 + k] diagonal position in L (relative)
+  // values
+  const double* Kval;
+  double* L;
+  double* rho;               // [nsub]
+};
+
+// status word bits written by kernels
+enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };
+
+}  // namespace feti

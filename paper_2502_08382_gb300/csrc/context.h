@@ -1,0 +1,93 @@
+// Internal definition of feti_ctx (host runtime state).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/feti.h"
+#include "common.cuh"
+#include "symbolic.h"
+
+namespace feti {
+
+struct SubHost {
+  int n = 0, m = 0, d = 0, nfix = 0, nelem = 0, edofs = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  std::vector<int32_t> bdof, blam;
+  std::vector<double> bsign;
+  std::vector<double> R, f, coords;
+  std::vector<int32_t> fix;
+  std::vector<int32_t> elem_dofs;
+  std::vector<double> dKe_ref, dKe_scale;
+  int pat = -1, bp = -1;
+};
+
+// a device buffer owned by the context
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace feti
+
+struct feti_ctx {
+  feti_options opt{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  feti_status sticky = FETI_OK;
+  int nsub = 0, nlam = 0, nsm = 0;
+  bool fp32 = false;
+  bool assembled = false;
+  std::vector<double> c_host;
+  std::vector<feti::SubHost> subs;
+  std::vector<feti::PatternPlan> pats;
+  std::vector<feti::BPlan> bps;
+  std::vector<int> bp_pat;
+  std::vector<feti::SubInfo> info;
+  feti::DevPlan P{};
+  std::vector<feti::DBuf> bufs;
+  size_t device_bytes = 0;
+  // device arrays not in DevPlan
+  double* d_Kval = nullptr;
+  double* d_L = nullptr;
+  void* d_X = nullptr;
+  void* d_F = nullptr;
+  double* d_ws = nullptr;
+  int64_t ws_stride = 0, chol_front = 0, rhs_front = 0;
+  double* d_trow = nullptr;
+  double* d_tpart = nullptr;
+  double* d_qi = nullptr;
+  int* d_colsub = nullptr;
+  int* d_c0 = nullptr;
+  int* d_c1 = nullptr;
+  int* d_queue = nullptr;     // [8] work-queue counters
+  int* d_status = nullptr;    // [1]
+  int* d_chol_order = nullptr;
+  int* d_trsm_order = nullptr;
+  int* d_impl_order = nullptr;
+  int2* d_syrk_items = nullptr;
+  int2* d_apply_items = nullptr;
+  int* d_colperm = nullptr;   // per subdomain sorted column -> B row (for get_F)
+  std::vector<int64_t> colperm_ofs;
+  int nsyrk = 0, napply = 0;
+  int64_t ncols = 0;
+  int grid_chol = 0, grid_trsm = 0, grid_impl = 0;
+  size_t impl_smem = 0;
+  // solve-side data
+  double* d_R = nullptr;       // concatenated R_i (column-major n x d)
+  double* d_f = nullptr;       // concatenated f_i
+  double* d_c = nullptr;       // c
+  int dtot = 0;
+  // stats
+  feti_stats stats{};
+  cudaEvent_t ev[8]{};
+};
+
+namespace feti {
+feti_status set_error(feti_ctx* c, feti_status s, const std::string& msg);
+void* dalloc(feti_ctx* c, size_t bytes);
+}  // namespace feti

@@ -1,0 +1,29 @@
+// Host-side launchers of the FETI device kernels (internal to the library).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace feti {
+
+void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
+                 int64_t front_sz, int grid, int* status, cudaStream_t st);
+void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, double* X, double* ws,
+                 int64_t ws_stride, int64_t front_sz, int grid, cudaStream_t st);
+void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
+                     cudaStream_t st);
+void launch_apply_rows_f64(const DevPlan& P, const int2* items, int nitems, const double* F, const double* p,
+                           double* trow, double* tpart, int grid, cudaStream_t st);
+void launch_apply_rows_f32(const DevPlan& P, const int2* items, int nitems, const float* F, const double* p,
+                           double* trow, double* tpart, int grid, cudaStream_t st);
+void launch_apply_cols(const DevPlan& P, const int* colsub, int64_t ncols, const double* trow,
+                       const double* tpart, double* qi, cudaStream_t st);
+void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* qi, double* q, cudaStream_t st);
+void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, const int* colperm, double* out, cudaStream_t st);
+
+// implicit FP64 operator (eq. 11) and the vector kernels of PCPG / eqs. 5-8
+void launch_implicit(const DevPlan& P, const int* order, int nsub, int* queue, const double* p, double* qi,
+                     double* ws, int64_t ws_stride, int grid, size_t smem, cudaStream_t st);
+
+}  // namespace feti

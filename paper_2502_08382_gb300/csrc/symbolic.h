@@ -1,0 +1,71 @@
+// Host-side symbolic analysis for the FETI dual-operator path.
+//
+// Runs once per sparsity pattern (paper Sec. III, symbolic/numeric split and
+// Algorithm 2's preparation step): a fill-reducing nested-dissection
+// ordering, the elimination tree, supernodes, the multifrontal plan used by
+// the numeric Cholesky, and -- per distinct set of B-touched DOFs -- the
+// pruned right-hand-side plan (X_i = L_i^{-1} P_i B_i^T column j is zero
+// above row s_j) and the SYRK tile lists for F_i = X_i^T X_i.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace feti {
+
+constexpr int kTile = 64;  // F_i tile edge (apply and SYRK)
+
+struct PatternPlan {
+  int n = 0;
+  std::vector<int> perm;   // new -> old DOF
+  std::vector<int> iperm;  // old -> new DOF
+  int nsn = 0;             // supernodes, in postorder (children before parents)
+  std::vector<int> sn_c0, sn_w, sn_r, sn_parent, sn_first_desc;
+  std::vector<int64_t> sn_rows_off;  // struct_below rows (new numbering), size nsn+1
+  std::vector<int> rows;
+  std::vector<int> col2sn;
+  std::vector<int> ch_off, ch_list;  // children of each supernode (CSR)
+  std::vector<int64_t> rel_off;      // extend-add map of s into its parent, size nsn+1
+  std::vector<int> rel;
+  std::vector<int64_t> Lofs;         // column-major (w+r) x w panel of each supernode
+  int64_t Lsize = 0;
+  std::vector<int64_t> kmap_off;     // per supernode, size nsn+1
+  std::vector<int> kmap_src;         // CSR index of K entry
+  std::vector<int> kmap_dst;         // offset in the subdomain's L storage
+  std::vector<int> diag_src;         // CSR index of each diagonal entry (old numbering)
+  std::vector<int64_t> upd_stack_ofs;  // where the r x r update block of s lives
+  int64_t chol_stack = 0;            // peak stack (doubles)
+  int64_t chol_front = 0;            // max r*r (doubles)
+  int max_f = 0, max_w = 0;
+  double chol_flops = 0, nnzL = 0;
+};
+
+struct BPlan {
+  int m = 0, m_pad = 0, nb = 0;
+  std::vector<int> colperm;  // sorted column j -> original B row
+  std::vector<int> spos;     // sorted column j -> new-numbered DOF
+  std::vector<int> jb, je, jo;  // per supernode: J_s = [jb, je), own columns [jo, je)
+  std::vector<int> act;      // supernodes with a non-empty J (postorder)
+  std::vector<int64_t> Xofs; // per supernode, w x |J| row-major block
+  int64_t Xsize = 0;
+  std::vector<int64_t> rhs_stack_ofs;
+  int64_t rhs_stack = 0, rhs_front = 0;
+  std::vector<int> tile_off, tile_sn;  // SYRK contributions per lower tile (bi,bj)
+  double trsm_flops = 0, syrk_flops = 0, syrk_exec_flops = 0;
+};
+
+struct SymbolicOptions {
+  int leaf_dofs = 64;
+  bool use_coords = true;
+};
+
+// K pattern: full symmetric CSR (rowptr int64, col int32).  coords: n x 3 or null.
+void analyse_pattern(int n, const int64_t* rowptr, const int32_t* col, const double* coords,
+                     const SymbolicOptions& opt, PatternPlan& out);
+// B: m rows, B_dof[r] = local DOF of row r.
+void plan_rhs(const PatternPlan& pp, int m, const int32_t* B_dof, BPlan& out);
+
+uint64_t hash_pattern(int n, const int64_t* rowptr, const int32_t* col);
+uint64_t hash_ints(const int32_t* a, int64_t n, uint64_t seed);
+
+}  // namespace feti

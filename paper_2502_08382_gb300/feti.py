@@ -1,0 +1,322 @@
+"""Thin Python binding of the C ABI in include/feti.h (argument marshalling only).
+
+Every numeric step runs in the CUDA library libfeti_gb300.so; this module only
+converts NumPy inputs to the C structs, passes torch device pointers and the
+current CUDA stream, and routes device allocations through torch's caching
+allocator.  There is no CPU fallback: if the library is missing, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libfeti_gb300.so")
+
+FETI_OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_NOT_SPD", 4: "ERR_NOT_CONVERGED",
+          5: "ERR_CUDA", 6: "ERR_STATE", 7: "ERR_TIMEOUT"}
+PREC = {"fp64": 0, "tf32": 1, "split_bf16": 2}
+
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_f64p = C.POINTER(C.c_double)
+
+
+class FetiSubdomain(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("K_rowptr", _i64p), ("K_col", _i32p),
+                ("K_val", _f64p), ("m", C.c_int32), ("B_rowptr", _i64p), ("B_col", _i32p),
+                ("B_val", _f64p), ("B_lambda", _i32p), ("d", C.c_int32), ("R", _f64p), ("f", _f64p),
+                ("nfix", C.c_int32), ("fix_dofs", _i32p), ("coords", _f64p), ("nelem", C.c_int32),
+                ("edofs", C.c_int32), ("elem_dofs", _i32p), ("dKe_ref", _f64p), ("dKe_scale", _f64p)]
+
+
+class FetiProblem(C.Structure):
+    _fields_ = [("nsub", C.c_int32), ("sub", C.POINTER(FetiSubdomain)), ("n_lambda", C.c_int32),
+                ("c", _f64p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class FetiOptions(C.Structure):
+    _fields_ = [("prec", C.c_int), ("refine_every", C.c_int32), ("tol", C.c_double), ("maxit", C.c_int32),
+                ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
+                ("use_coords", C.c_int32)]
+
+
+class FetiSolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32), ("rel_residual", C.c_double),
+                ("converged", C.c_int32)]
+
+
+class FetiStats(C.Structure):
+    _fields_ = [("nsub", C.c_int32), ("n_lambda", C.c_int32), ("npatterns", C.c_int32), ("nbplans", C.c_int32),
+                ("sum_n", C.c_int64), ("sum_m", C.c_int64), ("L_doubles", C.c_int64), ("X_elems", C.c_int64),
+                ("F_elems", C.c_int64), ("workspace_bytes", C.c_int64), ("device_bytes", C.c_int64),
+                ("chol_flops", C.c_double), ("trsm_flops", C.c_double), ("syrk_flops", C.c_double),
+                ("syrk_exec_flops", C.c_double), ("apply_bytes", C.c_double), ("implicit_bytes", C.c_double),
+                ("t_chol_ms", C.c_double), ("t_trsm_ms", C.c_double), ("t_syrk_ms", C.c_double),
+                ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
+           "feti_solve", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
+           "feti_analyse", "feti_version"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libfeti_gb300.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.feti_create.argtypes = [C.POINTER(FetiProblem), C.POINTER(FetiOptions), C.POINTER(vp)]
+    lib.feti_update_values.argtypes = [vp, C.c_int32, _f64p]
+    lib.feti_assemble.argtypes = [vp]
+    lib.feti_apply.argtypes = [vp, vp, vp]
+    lib.feti_apply_implicit.argtypes = [vp, vp, vp]
+    lib.feti_solve.argtypes = [vp, vp, vp, vp, C.POINTER(FetiSolveInfo)]
+    lib.feti_adjoint.argtypes = [vp, vp, vp]
+    lib.feti_get_F.argtypes = [vp, C.c_int32, _f64p]
+    lib.feti_get_stats.argtypes = [vp, C.POINTER(FetiStats)]
+    lib.feti_last_error.argtypes = [vp]
+    lib.feti_last_error.restype = C.c_char_p
+    lib.feti_destroy.argtypes = [vp]
+    lib.feti_destroy.restype = None
+    lib.feti_analyse.argtypes = [C.POINTER(FetiSubdomain), C.POINTER(FetiOptions), _f64p, _i32p, _i32p]
+    lib.feti_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("feti_last_error", "feti_destroy", "feti_version"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class FetiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+class _Marshal:
+    """Keeps the NumPy arrays behind a FetiProblem alive during feti_create."""
+
+    def __init__(self, problem, with_elements=False):
+        self.keep = []
+        subs = (FetiSubdomain * problem.nsub)()
+        for i, s in enumerate(problem.subs):
+            sub = subs[i]
+            a = lambda x, dt: self._k(np.ascontiguousarray(x, dtype=dt))
+            sub.n = s.n
+            sub.nnz = s.K_col.shape[0]
+            sub.K_rowptr = _ptr(a(s.K_rowptr, np.int64), C.c_int64)
+            sub.K_col = _ptr(a(s.K_col, np.int32), C.c_int32)
+            sub.K_val = _ptr(a(s.K_val, np.float64), C.c_double)
+            sub.m = s.m
+            sub.B_rowptr = _ptr(a(np.arange(s.m + 1), np.int64), C.c_int64)
+            sub.B_col = _ptr(a(s.B_dof, np.int32), C.c_int32)
+            sub.B_val = _ptr(a(s.B_sign, np.float64), C.c_double)
+            sub.B_lambda = _ptr(a(s.B_lambda, np.int32), C.c_int32)
+            sub.d = s.R.shape[1]
+            sub.R = _ptr(a(np.asfortranarray(s.R).ravel(order="F"), np.float64), C.c_double)
+            sub.f = _ptr(a(s.f, np.float64), C.c_double)
+            sub.nfix = len(s.fix_dofs)
+            sub.fix_dofs = _ptr(a(s.fix_dofs, np.int32), C.c_int32)
+            sub.coords = _ptr(a(s.coords, np.float64), C.c_double) if s.coords is not None else None
+            if with_elements:
+                sub.nelem = s.elem_dofs.shape[0]
+                sub.edofs = s.elem_dofs.shape[1]
+                sub.elem_dofs = _ptr(a(s.elem_dofs, np.int32), C.c_int32)
+                sub.dKe_ref = _ptr(a(problem.K_ref, np.float64), C.c_double)
+                sub.dKe_scale = _ptr(a(s.elem_dcoef, np.float64), C.c_double)
+        self.subs = subs
+        self.c = self._k(np.ascontiguousarray(problem.c, dtype=np.float64))
+        self.prob = FetiProblem(problem.nsub, subs, problem.n_lambda, _ptr(self.c, C.c_double))
+
+    def _k(self, x):
+        self.keep.append(x)
+        return x
+
+
+def subdomain_struct(s, keep):
+    """FetiSubdomain for one problems.Subdomain (used by feti_analyse)."""
+    class _P:
+        pass
+    p = _P()
+    p.subs = [s]
+    p.nsub = 1
+    p.c = np.zeros(0)
+    p.n_lambda = 0
+    m = _Marshal(p)
+    keep.append(m)
+    return m.subs[0]
+
+
+def analyse(sub, leaf_dofs=64, use_coords=True):
+    """Host-only symbolic analysis of one subdomain (no GPU): returns a dict
+    of the plan's statistics, the permutation and the supernode partition."""
+    lib = load_library()
+    keep = []
+    st = subdomain_struct(sub, keep)
+    opt = FetiOptions()
+    opt.leaf_dofs = leaf_dofs
+    opt.use_coords = 1 if use_coords else 0
+    info = np.zeros(16)
+    perm = np.zeros(sub.n, dtype=np.int32)
+    snb = np.zeros(3 * sub.n, dtype=np.int32)
+    rc = lib.feti_analyse(C.byref(st), C.byref(opt), _ptr(info, C.c_double), _ptr(perm, C.c_int32),
+                          _ptr(snb, C.c_int32))
+    if rc != FETI_OK:
+        raise FetiError(rc, "feti_analyse failed")
+    keys = ["n", "nsn", "max_front", "max_width", "nnzL", "chol_flops", "Lsize", "m", "Xsize", "trsm_flops",
+            "syrk_flops", "ntile_contrib", "chol_stack", "rhs_stack", "nroots"]
+    out = {k: info[i] for i, k in enumerate(keys)}
+    ns = int(out["nsn"])
+    out["perm"] = perm
+    out["sn_c0"] = snb[:ns].copy()
+    out["sn_w"] = snb[ns:2 * ns].copy()
+    out["sn_parent"] = snb[2 * ns:3 * ns].copy()
+    return out
+
+
+class FetiOperator:
+    """Explicit FETI dual operator on one GPU (wraps feti_create / feti_assemble /
+    feti_apply / feti_apply_implicit / feti_solve / feti_adjoint)."""
+
+    def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
+                 refine_every: int = 0, leaf_dofs: int = 64, use_coords: bool = True,
+                 with_elements: bool = False, torch_alloc: bool = True):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("FetiOperator needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream(self.device)
+        self.problem = problem
+        self.n_lambda = problem.n_lambda
+        self.dtot = sum(s.R.shape[1] for s in problem.subs)
+        self.sum_n = sum(s.n for s in problem.subs)
+        opt = FetiOptions()
+        opt.prec = PREC[prec]
+        opt.refine_every = refine_every
+        opt.tol = tol
+        opt.maxit = maxit
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        opt.leaf_dofs = leaf_dofs
+        opt.use_coords = 1 if use_coords else 0
+        self._cb = None
+        if torch_alloc:
+            dev = self.device.index
+            st = self.stream.cuda_stream
+
+            def _alloc(nbytes, _ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:
+                    return None
+
+            def _free(ptr, _ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            opt.dev_alloc, opt.dev_free = self._cb
+        self.opt = opt
+        m = _Marshal(problem, with_elements=with_elements)
+        h = C.c_void_p()
+        rc = self.lib.feti_create(C.byref(m.prob), C.byref(opt), C.byref(h))
+        self.h = h
+        if rc != FETI_OK:
+            msg = self.lib.feti_last_error(h).decode() if h else ""
+            if h:
+                self.lib.feti_destroy(h)
+                self.h = None
+            raise FetiError(rc, msg)
+
+    # -- helpers
+    def _check(self, rc):
+        if rc != FETI_OK:
+            raise FetiError(rc, self.lib.feti_last_error(self.h).decode())
+
+    def _dvec(self, n):
+        return self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+
+    # -- API
+    def assemble(self):
+        self._check(self.lib.feti_assemble(self.h))
+
+    def update_values(self, sub, K_val):
+        K_val = np.ascontiguousarray(K_val, dtype=np.float64)
+        self._check(self.lib.feti_update_values(self.h, sub, _ptr(K_val, C.c_double)))
+
+    def apply(self, p, out=None):
+        assert p.dtype == self.torch.float64 and p.is_cuda and p.numel() == self.n_lambda
+        p = p.contiguous()
+        q = out if out is not None else self._dvec(self.n_lambda)
+        self._check(self.lib.feti_apply(self.h, C.c_void_p(p.data_ptr()), C.c_void_p(q.data_ptr())))
+        return q
+
+    def apply_implicit(self, p, out=None):
+        p = p.contiguous()
+        q = out if out is not None else self._dvec(self.n_lambda)
+        self._check(self.lib.feti_apply_implicit(self.h, C.c_void_p(p.data_ptr()), C.c_void_p(q.data_ptr())))
+        return q
+
+    def solve(self):
+        lam = self._dvec(self.n_lambda)
+        alpha = self._dvec(max(self.dtot, 1))
+        u = self._dvec(self.sum_n)
+        info = FetiSolveInfo()
+        rc = self.lib.feti_solve(self.h, C.c_void_p(lam.data_ptr()), C.c_void_p(alpha.data_ptr()),
+                                 C.c_void_p(u.data_ptr()), C.byref(info))
+        if rc not in (FETI_OK, 4):
+            self._check(rc)
+        return lam, alpha[:self.dtot], u, dict(iterations=info.iterations, refinements=info.refinements,
+                                                 rel_residual=info.rel_residual, converged=bool(info.converged))
+
+    def adjoint(self, W_dev, nelem_total):
+        out = self._dvec(nelem_total)
+        self._check(self.lib.feti_adjoint(self.h, C.c_void_p(W_dev.data_ptr()), C.c_void_p(out.data_ptr())))
+        return out
+
+    def get_F(self, sub):
+        m = self.problem.subs[sub].m
+        out = np.zeros((m, m))
+        self._check(self.lib.feti_get_F(self.h, sub, _ptr(out, C.c_double)))
+        return out
+
+    def stats(self):
+        st = FetiStats()
+        self._check(self.lib.feti_get_stats(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.torch.cuda.synchronize(self.device)
+            self.lib.feti_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
