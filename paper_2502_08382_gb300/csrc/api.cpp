@@ -242,7 +242,8 @@ void build(feti_ctx* c) {
   rel_off.push_back(rel.size());
   kmap_off.push_back(kmap_src.size());
   // ---- concatenate RHS plans
-  std::vector<int> jb, je, jo, act, spos, tile_off, tile_sn;
+  std::vector<int> jb, je, jo, act, spos, tile_off, tile_sn, t2_off, t2_sn;
+  std::vector<int> bp_t20(c->bps.size());
   std::vector<int64_t> Xofs, rhs_ofs;
   std::vector<int> bp_sn0(c->bps.size()), bp_act0(c->bps.size()), bp_col0(c->bps.size()), bp_tile0(c->bps.size());
   for (size_t b = 0; b < c->bps.size(); ++b) {
@@ -262,8 +263,14 @@ void build(feti_ctx* c) {
     int ntile = B.nb * (B.nb + 1) / 2;
     for (int t = 0; t < ntile; ++t) tile_off.push_back(base + B.tile_off[t]);
     tile_sn.insert(tile_sn.end(), B.tile_sn.begin(), B.tile_sn.end());
+    bp_t20[b] = (int)t2_off.size();
+    int base2 = (int)t2_sn.size();
+    int nt2 = B.nb2 * (B.nb2 + 1) / 2;
+    for (int t = 0; t < nt2; ++t) t2_off.push_back(base2 + B.t2_off[t]);
+    t2_sn.insert(t2_sn.end(), B.t2_sn.begin(), B.t2_sn.end());
   }
   tile_off.push_back((int)tile_sn.size());
+  t2_off.push_back((int)t2_sn.size());
 
   // ---- per-subdomain layout
   c->info.resize(ns);
@@ -295,6 +302,8 @@ void build(feti_ctx* c) {
     I.act0 = bp_act0[s.bp];
     I.col0 = bp_col0[s.bp];
     I.tile0 = bp_tile0[s.bp];
+    I.t20 = bp_t20[s.bp];
+    I.nb2 = B.nb2;
     I.fix0 = fixo;
     I.alpha0 = alo;
     I.kmapb = 0;
@@ -408,6 +417,21 @@ void build(feti_ctx* c) {
     }
     for (int b = 0; b < B.nb; ++b) ap.push_back({(double)(b + 1), make_int2(i, b)});
   }
+  std::vector<std::pair<double, int2>> sy2;
+  for (int i = 0; i < ns; ++i) {
+    auto& B = c->bps[c->subs[i].bp];
+    auto& P = c->pats[c->subs[i].pat];
+    int nt2 = B.nb2 * (B.nb2 + 1) / 2;
+    for (int t = 0; t < nt2; ++t) {
+      double cost = 1.0;
+      for (int k = B.t2_off[t]; k < B.t2_off[t + 1]; ++k) cost += P.sn_w[B.t2_sn[k]];
+      sy2.push_back({cost, make_int2(i, t)});
+    }
+  }
+  std::stable_sort(sy2.begin(), sy2.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  std::vector<int2> sy2i;
+  for (auto& x : sy2) sy2i.push_back(x.second);
+  c->nsyrk2 = (int)sy2i.size();
   std::stable_sort(sy.begin(), sy.end(), [](auto& a, auto& b) { return a.first > b.first; });
   std::stable_sort(ap.begin(), ap.end(), [](auto& a, auto& b) { return a.first > b.first; });
   std::vector<int2> syi, api;
@@ -457,6 +481,8 @@ void build(feti_ctx* c) {
   D.spos = upload(c, spos);
   D.tile_off = upload(c, tile_off);
   D.tile_sn = upload(c, tile_sn);
+  D.t2_off = upload(c, t2_off);
+  D.t2_sn = upload(c, t2_sn);
   D.qmap = upload(c, qmap);
   D.qsign = upload(c, qsign);
   D.fix_sn = upload(c, fix_sn);
@@ -475,7 +501,7 @@ void build(feti_ctx* c) {
   c->d_L = (double*)dalloc(c, (size_t)Lo * 8);
   D.L = c->d_L;
   D.rho = (double*)dalloc(c, (size_t)ns * 8);
-  c->d_X = dalloc(c, (size_t)Xo * 8);
+  c->d_X = dalloc(c, (size_t)Xo * esz);
   c->d_F = dalloc(c, (size_t)Fo * esz);
   c->d_ws = (double*)dalloc(c, (size_t)gw * c->ws_stride * 8);
   c->d_trow = (double*)dalloc(c, (size_t)qo * 8);
@@ -491,6 +517,7 @@ void build(feti_ctx* c) {
   c->d_impl_order = upload(c, order_i);
   c->d_syrk_items = upload(c, syi);
   c->d_apply_items = upload(c, api);
+  c->d_syrk2_items = upload(c, sy2i);
   c->d_colperm = upload(c, colperm);
   c->d_R = upload(c, Rall);
   c->d_f = upload(c, fall);
@@ -593,13 +620,18 @@ feti_status feti_assemble(feti_ctx* ctx) {
               ctx->grid_chol, ctx->d_status, st);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
-  if (ctx->fp32) throw ArgError("mixed-precision assembly is not available in this build");
-  launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, (double*)ctx->d_X, ctx->d_ws,
+  launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
               ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, st);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
-  launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
-                  std::min(ctx->nsyrk, ctx->nsm * 8), st);
+  if (ctx->fp32) {
+    int split = ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 1 : 0;
+    launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, (float*)ctx->d_F,
+                   std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split, ctx->d_status, st);
+  } else {
+    launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
+                    std::min(ctx->nsyrk, ctx->nsm * 8), st);
+  }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[3], st));
   CK(cudaEventRecord(ctx->ev[4], st));
@@ -617,6 +649,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
   int status = 0;
   CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status & kStatNotSPD) return set_error(ctx, FETI_ERR_NOT_SPD, "a Cholesky pivot was not positive");
+  if (status & kStatTimeout) return set_error(ctx, FETI_ERR_TIMEOUT, "a bounded device wait gave up");
   ctx->assembled = true;
   return FETI_OK;
   API_END

@@ -23,6 +23,8 @@ struct SubInfo {
   int tile0;         // bplan tile_off base
   int fix0;          // fix arrays base
   int alpha0;        // offset of this subdomain's alpha block
+  int t20;           // bplan t2_off base (128 x 128 tiles)
+  int nb2;           // 128-wide blocks
   int pad_;
   int64_t kmapb;     // base of this pattern's kmap entries (kmap_off values are absolute)
   int64_t diag0;     // diag_src base
@@ -66,6 +68,8 @@ struct DevPlan {
   const int* spos;           // [col0 + j] new-numbered DOF of sorted column j
   const int* tile_off;       // [tile0 + t] absolute offsets into tile_sn
   const int* tile_sn;        // local supernode ids
+  const int* t2_off;         // [t20 + t] absolute offsets into t2_sn (128 x 128 tiles)
+  const int* t2_sn;
   // per subdomain
   const int* qmap;           // [qcol + j] global multiplier of sorted column j, -1 for padding
   const double* qsign;       // [qcol + j] sign of B in sorted column j (0 for padding)

@@ -71,6 +71,8 @@ struct feti_ctx {
   int* d_impl_order = nullptr;
   int2* d_syrk_items = nullptr;
   int2* d_apply_items = nullptr;
+  int2* d_syrk2_items = nullptr;
+  int nsyrk2 = 0;
   int* d_colperm = nullptr;   // per subdomain sorted column -> B row (for get_F)
   std::vector<int64_t> colperm_ofs;
   int nsyrk = 0, napply = 0;

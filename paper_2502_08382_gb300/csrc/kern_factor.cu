@@ -214,25 +214,37 @@ __global__ void __launch_bounds__(kThreads) chol_kernel(DevPlan P, const int* or
   }
 }
 
-// Forward solve X_s = L_ss^{-1} X_s and update C -= L_rs X_s (C = remaining
-// rows of the RHS front), X_s row-major w x J, W2 row-major r x J.
-__device__ void solve_front(Smem& sm, const double* Ls, int f, int w, double* Xs, double* W2, int J) {
+// Smem of the solve (element type T of X).
+template <typename T>
+struct SolveSmem {
+  T D[kNB][kNB + 1];
+  T A[kNB][kT];
+  T B[kNB][kT];
+};
+
+// Forward solve of one RHS front: X_s = L_ss^{-1} X_s, then C -= L_rs X_s
+// (C = the r bottom rows).  Column-major fronts: column j of X_s is
+// Xs[j * wp + 0 .. w), column j of the bottom block is W2[j * r + 0 .. r).
+template <typename T>
+__device__ void solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T* Xs, int wp, T* W2, int J) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int r = f - w;
   for (int kb = 0; kb < w; kb += kNB) {
     const int nbk = min(kNB, w - kb);
     for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
       int i = idx % kNB, j = idx / kNB;
-      sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : 0.0;
+      sm.D[i][j] = (i < nbk && j <= i) ? (T)Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
     }
     __syncthreads();
     for (int col = tid; col < J; col += kThreads) {
-      double x[kNB];
+      T* xc = Xs + (int64_t)col * wp + kb;
+      T x[kNB];
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) x[k] = (k < nbk) ? Xs[(int64_t)(kb + k) * J + col] : 0.0;
+      for (int k = 0; k < kNB; ++k) x[k] = (k < nbk) ? xc[k] : (T)0;
 #pragma unroll
       for (int k = 0; k < kNB; ++k) {
         if (k < nbk) {
-          double s = x[k];
+          T s = x[k];
 #pragma unroll
           for (int l = 0; l < k; ++l) s = fma(-sm.D[k][l], x[l], s);
           x[k] = s / sm.D[k][k];
@@ -240,7 +252,7 @@ __device__ void solve_front(Smem& sm, const double* Ls, int f, int w, double* Xs
       }
 #pragma unroll
       for (int k = 0; k < kNB; ++k)
-        if (k < nbk) Xs[(int64_t)(kb + k) * J + col] = x[k];
+        if (k < nbk) xc[k] = x[k];
     }
     __syncthreads();
     const int i0 = kb + nbk;
@@ -250,21 +262,36 @@ __device__ void solve_front(Smem& sm, const double* Ls, int f, int w, double* Xs
         const int ri = i0 + ti * kT, cj = tc * kT;
         for (int idx = tid; idx < nbk * kT; idx += kThreads) {
           int x = idx % kT, k = idx / kT;
-          sm.A[k][x] = (ri + x < f) ? Ls[(int64_t)(kb + k) * f + ri + x] : 0.0;
-          sm.B[k][x] = (cj + x < J) ? Xs[(int64_t)(kb + k) * J + cj + x] : 0.0;
+          sm.A[k][x] = (ri + x < f) ? (T)Ls[(int64_t)(kb + k) * f + ri + x] : (T)0;
+        }
+        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
+          int k = idx % kNB, y = idx / kNB;
+          sm.B[k][y] = (k < nbk && cj + y < J) ? Xs[(int64_t)(cj + y) * wp + kb + k] : (T)0;
         }
         __syncthreads();
-        double acc[4][4] = {};
-        tile_mma(sm.A, sm.B, nbk, acc, tx, ty);
+        T acc[4][4] = {};
+        for (int k = 0; k < nbk; ++k) {
+          T a[4], b[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int i = ri + ty + 16 * u;
-          if (i >= f) continue;
-          double* row = (i < w) ? Xs + (int64_t)i * J : W2 + (int64_t)(i - w) * J;
+          for (int u = 0; u < 4; ++u) {
+            a[u] = sm.A[k][tx + 16 * u];
+            b[u] = sm.B[k][ty + 16 * u];
+          }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            int j = cj + tx + 16 * v;
-            if (j < J) row[j] -= acc[u][v];
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          int col = cj + ty + 16 * v;
+          if (col >= J) continue;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            int i = ri + tx + 16 * u;
+            if (i >= f) continue;
+            if (i < w) Xs[(int64_t)col * wp + i] -= acc[u][v];
+            else W2[(int64_t)col * r + (i - w)] -= acc[u][v];
           }
         }
         __syncthreads();
@@ -273,33 +300,34 @@ __device__ void solve_front(Smem& sm, const double* Ls, int f, int w, double* Xs
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
-                                                         double* X, double* ws, int64_t ws_stride,
-                                                         int64_t front_sz) {
-  __shared__ Smem sm;
+                                                         T* X, T* ws, int64_t ws_stride, int64_t front_sz) {
+  __shared__ SolveSmem<T> sm;
   const int tid = threadIdx.x;
-  double* W2 = ws + (int64_t)blockIdx.x * ws_stride;
-  double* stack = W2 + front_sz;
+  T* W2 = ws + (int64_t)blockIdx.x * ws_stride;
+  T* stack = W2 + front_sz;
   for (;;) {
     int it = pop_item(queue);
     if (it >= nsub) return;
     const int si = order[it];
     const SubInfo S = P.sub[si];
     const double* L = P.L + S.L;
-    double* Xsub = X + S.X;
+    T* Xsub = X + S.X;
     for (int a = 0; a < S.nact; ++a) {
       const int s = P.act[S.act0 + a];
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
       const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
+      const int wp = (w + 3) & ~3;
       const int jb = P.jb[bs], je = P.je[bs], jo = P.jo[bs];
       const int J = je - jb;
-      double* Xs = Xsub + P.Xofs[bs];
-      for (int64_t idx = tid; idx < (int64_t)w * J; idx += kThreads) Xs[idx] = 0.0;
-      for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) W2[idx] = 0.0;
+      T* Xs = Xsub + P.Xofs[bs];
+      for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) Xs[idx] = (T)0;
+      for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) W2[idx] = (T)0;
       __syncthreads();
       for (int j = jo + tid; j < je; j += kThreads) {
         int row = P.spos[S.col0 + j] - c0;
-        Xs[(int64_t)row * J + (j - jb)] = P.qsign[S.qcol + j];
+        Xs[(int64_t)(j - jb) * wp + row] = (T)P.qsign[S.qcol + j];
       }
       for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
         const int lc = P.ch_list[c];
@@ -307,22 +335,22 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(DevPlan P, const int* or
         const int Jc = P.je[bc] - P.jb[bc];
         if (Jc <= 0) continue;
         const int rc = P.sn_r[gc], coff = P.jb[bc] - jb;
-        const double* U = stack + P.rhs_ofs[bc];
+        const T* U = stack + P.rhs_ofs[bc];
         const int* rl = P.rel + P.rel_off[gc];
         // children own disjoint column ranges: no conflicts between them
         for (int64_t idx = tid; idx < (int64_t)rc * Jc; idx += kThreads) {
-          int a2 = (int)(idx / Jc), col = (int)(idx % Jc);
+          int col = (int)(idx / rc), a2 = (int)(idx % rc);
           int ra = rl[a2];
-          double v = U[idx];
-          if (ra < w) Xs[(int64_t)ra * J + coff + col] += v;
-          else W2[(int64_t)(ra - w) * J + coff + col] += v;
+          T v = U[idx];
+          if (ra < w) Xs[(int64_t)(coff + col) * wp + ra] += v;
+          else W2[(int64_t)(coff + col) * r + (ra - w)] += v;
         }
       }
       __syncthreads();
-      solve_front(sm, L + P.Lofs[gs], f, w, Xs, W2, J);
+      solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J);
       __syncthreads();
       if (P.sn_parent[gs] >= 0) {
-        double* dst = stack + P.rhs_ofs[bs];
+        T* dst = stack + P.rhs_ofs[bs];
         for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) dst[idx] = W2[idx];
       }
       __syncthreads();
@@ -337,9 +365,13 @@ void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, doubl
   chol_kernel<<<grid, kThreads, 0, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, status);
 }
 
-void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, double* X, double* ws,
+void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
                  int64_t ws_stride, int64_t front_sz, int grid, cudaStream_t st) {
-  trsm_kernel<<<grid, kThreads, 0, st>>>(P, order, nsub, queue, X, ws, ws_stride, front_sz);
+  if (fp32)
+    trsm_kernel<float><<<grid, kThreads, 0, st>>>(P, order, nsub, queue, (float*)X, (float*)ws, 2 * ws_stride,
+                                                  front_sz);
+  else
+    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, order, nsub, queue, (double*)X, ws, ws_stride, front_sz);
 }
 
 }  // namespace feti

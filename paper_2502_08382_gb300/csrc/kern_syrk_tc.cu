@@ -1,0 +1,340 @@
+// Tensor-core SYRK F_i = X_i^T X_i (paper Sec. IV, SYRK path) on sm_103a.
+//
+// One CTA computes one 128 x 128 tile (BI, BJ), BJ <= BI, of F_i in sorted
+// column order:  F[a][b] = sum_s sum_k X_s[a][k] X_s[b][k]  over the supernodes
+// s whose column range J_s meets both 128-blocks (pruning: other supernodes
+// hold zeros there).  X_s is stored column-major per supernode (column j of
+// X holds the w_s values of rows in s, padded to wp), which is the K-major
+// operand layout of tcgen05.mma: A = rows a of the tile, B = rows b, K = the
+// supernode rows.
+//
+// Staging: 16-byte cp.async (zero-filled outside J_s and beyond w_s) writes
+// each 128 x 32 FP32 chunk into the canonical 128-byte-swizzled K-major
+// layout (8-row atoms of 1024 B).  One thread issues tcgen05.mma kind::tf32
+// (M = N = 128, K = 8) into a 128-column TMEM accumulator and commits to a
+// per-stage mbarrier, which releases the stage for the next cp.async.  The
+// epilogue reads TMEM with tcgen05.ld 32x32b and writes the 64 x 64 storage
+// tiles of the lower triangle.  SPLIT = 1 stages bf16 hi/lo halves of each
+// FP32 value and accumulates hi*hi + hi*lo + lo*hi (kind::f16 with bf16).
+// All waits are bounded; on timeout the kernel flags kStatTimeout, drains its
+// copies, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace feti {
+namespace {
+
+constexpr int kM = 128;
+constexpr int kStages = 3;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: canonical K-major, 128-byte swizzle,
+// stride between 8-row atoms 1024 B (sm_100 descriptor version 1)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: D = F32, A/B format fmt (2 = TF32, 1 = BF16), both K-major, M = N = 128
+__device__ __forceinline__ constexpr uint32_t idesc_mn128(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait (about a second); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int i = 0; i < (1 << 25); ++i) {
+    if (mbar_test(mbar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile2_of(int t, int& bi, int& bj) {
+  int b = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((b + 1) * (b + 2) / 2 <= t) ++b;
+  while (b * (b + 1) / 2 > t) --b;
+  bi = b;
+  bj = t - b * (b + 1) / 2;
+}
+
+// Loader cursor over the (supernode, k-chunk) sequence of one tile.
+struct Cursor {
+  int c, k0;
+};
+
+// bytes of one operand buffer (128 rows x 128 B)
+constexpr int kOpBytes = kM * 128;
+
+template <int SPLIT>
+struct Cfg {
+  static constexpr int kKC = SPLIT ? 64 : 32;            // K values per chunk (one swizzled row)
+  static constexpr int kOps = SPLIT ? 4 : 2;             // A(hi,lo), B(hi,lo) or A, B
+  static constexpr int kStageBytes = kOps * kOpBytes;
+};
+
+// Stage the chunk (supernode s, rows k0..k0+KC) of the A rows (tile block BI)
+// and B rows (tile block BJ).
+template <int SPLIT>
+__device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, int wp, int w, int J, int ca, int cb,
+                                           int k0, const float* safe) {
+  const int tid = threadIdx.x;
+  if constexpr (!SPLIT) {
+    const uint32_t sA = smem_u32(stage), sB = sA + kOpBytes;
+    // 2 operands x 128 rows x 8 chunks of 16 B
+    for (int idx = tid; idx < 2 * kM * 8; idx += kTcThreads) {
+      const int op = idx / (kM * 8), rem = idx % (kM * 8);
+      const int m = rem / 8, c = rem % 8;
+      const int x = (op ? cb : ca) + m;
+      const int k = k0 + 4 * c;
+      const bool ok = x >= 0 && x < J && k < w;
+      const float* src = ok ? Xs + (int64_t)x * wp + k : safe;
+      const uint32_t dst = (op ? sB : sA) + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+      cp_async16(dst, src, ok);
+    }
+  } else {
+    // bf16 hi/lo split: 64 K values per 128-byte row; each thread converts 8 floats -> one 16 B chunk
+    uint8_t* base = stage;
+    for (int idx = tid; idx < 2 * kM * 8; idx += kTcThreads) {
+      const int op = idx / (kM * 8), rem = idx % (kM * 8);
+      const int m = rem / 8, c = rem % 8;
+      const int x = (op ? cb : ca) + m;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; e += 4) {
+        const int k = k0 + 8 * c + e;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x >= 0 && x < J && k < w) q = __ldg(reinterpret_cast<const float4*>(Xs + (int64_t)x * wp + k));
+        v[e] = q.x;
+        v[e + 1] = q.y;
+        v[e + 2] = q.z;
+        v[e + 3] = q.w;
+      }
+      __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
+        hi[e] = __halves2bfloat162(h0, h1);
+        lo[e] = __halves2bfloat162(__float2bfloat16_rn(v[2 * e] - __bfloat162float(h0)),
+                                   __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1)));
+      }
+      const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+      uint8_t* ph = base + (op ? 2 : 0) * kOpBytes + off;
+      uint8_t* pl = base + (op ? 3 : 1) * kOpBytes + off;
+      *reinterpret_cast<uint4*>(ph) = *reinterpret_cast<uint4*>(hi);
+      *reinterpret_cast<uint4*>(pl) = *reinterpret_cast<uint4*>(lo);
+    }
+  }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const int2* items, int nitems,
+                                                                const float* X, float* F, int* status) {
+  using C = Cfg<SPLIT>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t mbar[kStages];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_mn128(SPLIT ? 1u : 2u);
+  uint32_t g0 = 0;  // chunks issued by this CTA so far (stage = g % kStages)
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int si = items[it].x, t2 = items[it].y;
+    const SubInfo S = P.sub[si];
+    int BI, BJ;
+    tile2_of(t2, BI, BJ);
+    const int* tl = P.t2_off + S.t20;
+    const int cbeg = tl[t2], cend = tl[t2 + 1];
+    int nch = 0;
+    for (int c = cbeg; c < cend; ++c) {
+      int w = P.sn_w[S.sn0 + P.t2_sn[c]];
+      nch += (w + C::kKC - 1) / C::kKC;
+    }
+    const float* Xsub = X + S.X;
+    Cursor cur{cbeg, 0};
+    auto issue = [&](int i) {
+      // load local chunk i (the cursor walks the chunks in order)
+      const int s = P.t2_sn[cur.c];
+      const int gs = S.sn0 + s, bs = S.bsn0 + s;
+      const int w = P.sn_w[gs], wp = (w + 3) & ~3, jb = P.jb[bs], J = P.je[bs] - jb;
+      uint8_t* stage = smem + ((g0 + i) % kStages) * C::kStageBytes;
+      load_chunk<SPLIT>(stage, Xsub + P.Xofs[bs], wp, w, J, BI * kM - jb, BJ * kM - jb, cur.k0, X);
+      cur.k0 += C::kKC;
+      if (cur.k0 >= w) {
+        cur.c++;
+        cur.k0 = 0;
+      }
+    };
+    for (int i = 0; i < nch + kStages - 1; ++i) {
+      if (i < nch) {
+        if (i >= kStages) {
+          const uint32_t gp = g0 + i - kStages;
+          if (tid == 0 && !mbar_wait(smem_u32(&mbar[gp % kStages]), (gp / kStages) & 1)) s_abort = 1;
+          __syncthreads();
+          if (s_abort) break;
+        }
+        issue(i);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      const int j = i - (kStages - 1);
+      if (j >= 0 && j < nch) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sbase = smem_u32(smem + ((g0 + j) % kStages) * C::kStageBytes);
+          if constexpr (!SPLIT) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = sw128_desc(sbase + kk * 32), bd = sw128_desc(sbase + kOpBytes + kk * 32);
+              mma_tf32(tmem, ad, bd, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = kk * 32;
+              const uint64_t ah = sw128_desc(sbase + o), al = sw128_desc(sbase + kOpBytes + o);
+              const uint64_t bh = sw128_desc(sbase + 2 * kOpBytes + o), bl = sw128_desc(sbase + 3 * kOpBytes + o);
+              mma_f16(tmem, ah, bh, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+              mma_f16(tmem, ah, bl, idesc, 1u);
+              mma_f16(tmem, al, bh, idesc, 1u);
+            }
+          }
+          mma_commit(smem_u32(&mbar[(g0 + j) % kStages]));
+        }
+      }
+    }
+    if (s_abort) break;
+    if (nch > 0) {
+      const uint32_t gl = g0 + nch - 1;
+      if (tid == 0 && !mbar_wait(smem_u32(&mbar[gl % kStages]), (gl / kStages) & 1)) s_abort = 1;
+      __syncthreads();
+      if (s_abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    g0 += nch;
+    // epilogue: warp w owns tile rows 32w .. 32w+31 (TMEM lanes)
+    const int row = BI * kM + warp * 32 + lane;
+    const int bi = row / kT;
+#pragma unroll 1
+    for (int cc = 0; cc < 4; ++cc) {
+      uint32_t v[32];
+      if (nch > 0) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = 0u;
+      }
+      const int col = BJ * kM + cc * 32;
+      const int bj = col / kT;
+      if (bi < S.nb && bj < S.nb && bj <= bi) {
+        float* dst = F + S.F + (int64_t)(bi * (bi + 1) / 2 + bj) * kT * kT + (row % kT) * kT + (col % kT);
+#pragma unroll
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4*>(dst + e) = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                                            __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  // drain copies, release TMEM
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (s_abort && tid == 0) atomicOr(status, kStatTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+}  // namespace
+
+size_t syrk_tc_smem(int split) {
+  return (size_t)kStages * (split ? Cfg<1>::kStageBytes : Cfg<0>::kStageBytes) + 1024;
+}
+
+void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid, int split,
+                    int* status, cudaStream_t st) {
+  size_t smem = syrk_tc_smem(split);
+  if (split) {
+    cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    syrk_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, F, status);
+  } else {
+    cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    syrk_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, F, status);
+  }
+}
+
+}  // namespace feti

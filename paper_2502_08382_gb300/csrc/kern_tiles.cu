@@ -37,17 +37,17 @@ __global__ void __launch_bounds__(kThreads) syrk_f64_kernel(DevPlan P, const int
     for (int c = tl[t]; c < tl[t + 1]; ++c) {
       const int s = P.tile_sn[c];
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
-      const int w = P.sn_w[gs], jb = P.jb[bs], J = P.je[bs] - jb;
+      const int w = P.sn_w[gs], wp = (w + 3) & ~3, jb = P.jb[bs], J = P.je[bs] - jb;
       const double* Xs = X + S.X + P.Xofs[bs];
       const int ca = bi * kT - jb, cb = bj * kT - jb;
       for (int k0 = 0; k0 < w; k0 += 32) {
         const int kc = min(32, w - k0);
         for (int idx = tid; idx < 32 * kT; idx += kThreads) {
-          int x = idx % kT, k = idx / kT;
+          int k = idx % 32, x = idx / 32;
           bool kin = k < kc;
           int xa = ca + x, xb = cb + x;
-          A[k][x] = (kin && xa >= 0 && xa < J) ? Xs[(int64_t)(k0 + k) * J + xa] : 0.0;
-          B[k][x] = (kin && xb >= 0 && xb < J) ? Xs[(int64_t)(k0 + k) * J + xb] : 0.0;
+          A[k][x] = (kin && xa >= 0 && xa < J) ? Xs[(int64_t)xa * wp + k0 + k] : 0.0;
+          B[k][x] = (kin && xb >= 0 && xb < J) ? Xs[(int64_t)xb * wp + k0 + k] : 0.0;
         }
         __syncthreads();
         for (int k = 0; k < kc; ++k) {

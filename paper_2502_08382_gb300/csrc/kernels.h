@@ -9,8 +9,11 @@ namespace feti {
 
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
                  int64_t front_sz, int grid, int* status, cudaStream_t st);
-void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, double* X, double* ws,
+void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
                  int64_t ws_stride, int64_t front_sz, int grid, cudaStream_t st);
+void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
+                    int split, int* status, cudaStream_t st);
+size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);
 void launch_apply_rows_f64(const DevPlan& P, const int2* items, int nitems, const double* F, const double* p,

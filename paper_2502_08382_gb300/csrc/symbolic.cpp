@@ -581,7 +581,7 @@ void plan_rhs(const PatternPlan& P, int m, const int32_t* B_dof, BPlan& Bp) {
     Bp.act.push_back(s);
     Bp.Xofs[s] = X;
     int w = P.sn_w[s], r = P.sn_r[s];
-    X += (int64_t)w * J;
+    X += (int64_t)xpad(w) * J;
     tf += (double)J * ((double)w * w + 2.0 * w * r);
     sf += (double)J * (J + 1) * w;
   }
@@ -621,6 +621,18 @@ void plan_rhs(const PatternPlan& P, int m, const int32_t* B_dof, BPlan& Bp) {
   for (int t = 0; t < ntile; ++t) Bp.tile_off[t + 1] = Bp.tile_off[t] + (int)per[t].size();
   Bp.tile_sn.reserve(Bp.tile_off[ntile]);
   for (int t = 0; t < ntile; ++t) Bp.tile_sn.insert(Bp.tile_sn.end(), per[t].begin(), per[t].end());
+  // the same lists for 128 x 128 tiles
+  Bp.nb2 = (Bp.m_pad + 127) / 128;
+  int nt2 = Bp.nb2 * (Bp.nb2 + 1) / 2;
+  std::vector<std::vector<int>> per2(nt2);
+  for (int s : Bp.act) {
+    int t0 = Bp.jb[s] / 128, t1 = (Bp.je[s] - 1) / 128;
+    for (int bi = t0; bi <= t1; ++bi)
+      for (int bj = t0; bj <= bi; ++bj) per2[bi * (bi + 1) / 2 + bj].push_back(s);
+  }
+  Bp.t2_off.assign(nt2 + 1, 0);
+  for (int t = 0; t < nt2; ++t) Bp.t2_off[t + 1] = Bp.t2_off[t] + (int)per2[t].size();
+  for (int t = 0; t < nt2; ++t) Bp.t2_sn.insert(Bp.t2_sn.end(), per2[t].begin(), per2[t].end());
   Bp.trsm_flops = tf;
   Bp.syrk_flops = sf;
   Bp.syrk_exec_flops = sfe;

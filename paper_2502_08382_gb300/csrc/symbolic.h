@@ -13,7 +13,10 @@
 
 namespace feti {
 
-constexpr int kTile = 64;  // F_i tile edge (apply and SYRK)
+constexpr int kTile = 64;  // F tile edge (apply and SYRK)
+
+// padded row length of a supernode X block (16-byte aligned rows)
+inline int xpad(int w) { return (w + 3) & ~3; }
 
 struct PatternPlan {
   int n = 0;
@@ -46,11 +49,13 @@ struct BPlan {
   std::vector<int> spos;     // sorted column j -> new-numbered DOF
   std::vector<int> jb, je, jo;  // per supernode: J_s = [jb, je), own columns [jo, je)
   std::vector<int> act;      // supernodes with a non-empty J (postorder)
-  std::vector<int64_t> Xofs; // per supernode, w x |J| row-major block
+  std::vector<int64_t> Xofs; // per supernode, |J| x wp block (column j holds w values, padded to wp)
   int64_t Xsize = 0;
   std::vector<int64_t> rhs_stack_ofs;
   int64_t rhs_stack = 0, rhs_front = 0;
-  std::vector<int> tile_off, tile_sn;  // SYRK contributions per lower tile (bi,bj)
+  std::vector<int> tile_off, tile_sn;  // SYRK contributions per lower kTile tile (bi,bj)
+  int nb2 = 0;                         // 128-wide blocks (tensor-core SYRK)
+  std::vector<int> t2_off, t2_sn;      // contributions per lower 128 x 128 tile
   double trsm_flops = 0, syrk_flops = 0, syrk_exec_flops = 0;
 };
 

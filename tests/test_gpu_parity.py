@@ -69,3 +69,39 @@ def test_apply_fp64_matches_oracle(torch_cuda, name):
     b = op.apply(p).cpu().numpy()
     assert np.array_equal(a, b)
     op.close()
+
+
+# Mixed precision: FP32 pruned TRSM + tensor-core SYRK, F_i stored as FP32 tiles.
+# Tolerances follow the operand precision of the SYRK: TF32 keeps 10 mantissa
+# bits (the tensor core drops the low 13 bits of each FP32 operand), split
+# bf16 keeps about 16 (hi*hi + hi*lo + lo*hi, the lo*lo term ~2^-16 dropped).
+MIXED_TOL = {"tf32": 4e-3, "split_bf16": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "split_bf16"])
+@pytest.mark.parametrize("name", ["cfg1", "heat3d_ragged", "elast3d_2x2x2", "cfg3_2x2x2"])
+def test_F_mixed_matches_oracle(torch_cuda, name, prec):
+    P = CASES[name]()
+    op = _op(P, prec=prec)
+    idx = range(P.nsub) if P.nsub <= 27 else range(8)
+    worst = 0.0
+    for i in idx:
+        Fo = O.local_F(P.subs[i])
+        Fg = op.get_F(int(i))
+        worst = max(worst, np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo))
+    op.close()
+    print(f"{name} {prec}: max relative Frobenius error of F_i = {worst:.3e}")
+    assert worst <= MIXED_TOL[prec], worst
+
+
+@pytest.mark.parametrize("prec", ["tf32", "split_bf16"])
+def test_apply_mixed_matches_oracle(torch_cuda, prec):
+    torch = torch_cuda
+    P = CASES["heat3d_ragged"]()
+    op = _op(P, prec=prec)
+    Fs = [O.local_F(s) for s in P.subs]
+    p = seeded_vector(P.n_lambda, 4)
+    q = op.apply(torch.from_numpy(p).cuda()).cpu().numpy()
+    qo = O.apply_F(P, Fs, p)
+    op.close()
+    assert np.linalg.norm(q - qo) <= MIXED_TOL[prec] * np.linalg.norm(qo)
