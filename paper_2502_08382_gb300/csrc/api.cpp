@@ -277,7 +277,7 @@ void build(feti_ctx* c) {
   std::vector<int> qmap, fix_sn, colsub, colperm;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
-  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, rpo = 0;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
   int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0;
@@ -317,6 +317,8 @@ void build(feti_ctx* c) {
     I.dof = dofo;
     I.R = Ro;
     I.tpart = tpo;
+    I.rpart = rpo;
+    rpo += (int64_t)B.nb * ((B.nb + kApplyChunk - 1) / kApplyChunk) * kT;
     int ntile = B.nb * (B.nb + 1) / 2;
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
@@ -405,7 +407,8 @@ void build(feti_ctx* c) {
   std::stable_sort(order_i.begin(), order_i.end(), [&](int a, int b) {
     return c->pats[c->subs[a].pat].nnzL > c->pats[c->subs[b].pat].nnzL;
   });
-  std::vector<std::pair<double, int2>> sy, ap;
+  std::vector<std::pair<double, int2>> sy;
+  std::vector<int4> api;
   for (int i = 0; i < ns; ++i) {
     auto& B = c->bps[c->subs[i].bp];
     auto& P = c->pats[c->subs[i].pat];
@@ -415,7 +418,8 @@ void build(feti_ctx* c) {
       for (int k = B.tile_off[t]; k < B.tile_off[t + 1]; ++k) cost += P.sn_w[B.tile_sn[k]];
       sy.push_back({cost, make_int2(i, t)});
     }
-    for (int b = 0; b < B.nb; ++b) ap.push_back({(double)(b + 1), make_int2(i, b)});
+    for (int b = 0; b < B.nb; ++b)
+      for (int c = 0; c <= b; c += kApplyChunk) api.push_back(make_int4(i, b, c, std::min(c + kApplyChunk, b + 1)));
   }
   std::vector<std::pair<double, int2>> sy2;
   for (int i = 0; i < ns; ++i) {
@@ -433,10 +437,8 @@ void build(feti_ctx* c) {
   for (auto& x : sy2) sy2i.push_back(x.second);
   c->nsyrk2 = (int)sy2i.size();
   std::stable_sort(sy.begin(), sy.end(), [](auto& a, auto& b) { return a.first > b.first; });
-  std::stable_sort(ap.begin(), ap.end(), [](auto& a, auto& b) { return a.first > b.first; });
-  std::vector<int2> syi, api;
+  std::vector<int2> syi;
   for (auto& x : sy) syi.push_back(x.second);
-  for (auto& x : ap) api.push_back(x.second);
   c->nsyrk = (int)syi.size();
   c->napply = (int)api.size();
 
@@ -446,8 +448,8 @@ void build(feti_ctx* c) {
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev));
   c->nsm = prop.multiProcessorCount;
-  c->grid_chol = std::min(ns, c->nsm * 2);
-  c->grid_trsm = std::min(ns, c->nsm * 2);
+  c->grid_chol = std::min(ns, c->nsm * 3);
+  c->grid_trsm = std::min(ns, c->nsm * 3);
   c->chol_front = max_cf;
   c->rhs_front = max_rf;
   c->ws_stride = std::max(max_cf + max_chol, max_rf + max_rhs);
@@ -506,6 +508,8 @@ void build(feti_ctx* c) {
   c->d_ws = (double*)dalloc(c, (size_t)gw * c->ws_stride * 8);
   c->d_trow = (double*)dalloc(c, (size_t)qo * 8);
   c->d_tpart = (double*)dalloc(c, (size_t)std::max<int64_t>(tpo, 1) * 8);
+  c->d_rowpart = dalloc(c, (size_t)std::max<int64_t>(rpo, 1) * 8);
+  c->d_pg = dalloc(c, (size_t)qo * 8);
   c->d_qi = (double*)dalloc(c, (size_t)qo * 8);
   c->d_colsub = upload(c, colsub);
   c->d_c0 = upload(c, c0);
@@ -661,15 +665,10 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_apply before feti_assemble");
   API_BEGIN
   cudaStream_t st = ctx->st;
-  int grid = std::min(ctx->napply, ctx->nsm * 4);
-  if (ctx->fp32)
-    launch_apply_rows_f32(ctx->P, ctx->d_apply_items, ctx->napply, (const float*)ctx->d_F, p_dev, ctx->d_trow,
-                          ctx->d_tpart, grid, st);
-  else
-    launch_apply_rows_f64(ctx->P, ctx->d_apply_items, ctx->napply, (const double*)ctx->d_F, p_dev, ctx->d_trow,
-                          ctx->d_tpart, grid, st);
-  launch_apply_cols(ctx->P, ctx->d_colsub, ctx->ncols, ctx->d_trow, ctx->d_tpart, ctx->d_qi, st);
-  launch_gather_lambda(ctx->d_c0, ctx->d_c1, ctx->nlam, ctx->d_qi, q_dev, st);
+  int grid = std::max(1, std::min(ctx->napply, ctx->nsm * 2));
+  launch_apply(ctx->P, ctx->fp32, ctx->d_apply_items, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
+               ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_colsub, ctx->d_c0, ctx->d_c1, ctx->nlam, q_dev, grid,
+               ctx->d_status, st);
   CK(cudaGetLastError());
   return FETI_OK;
   API_END

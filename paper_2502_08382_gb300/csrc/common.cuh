@@ -13,6 +13,7 @@ namespace feti {
 constexpr int kT = 64;          // F tile edge
 constexpr int kThreads = 256;   // CTA size of the dense kernels
 constexpr int kNB = 32;         // panel block of the dense factorisation / solve
+constexpr int kApplyChunk = 8;  // tiles per apply work item (one tile row is cut into chunks)
 
 struct SubInfo {
   int n, m, m_pad, nb, nsn, nact, d, nfix;
@@ -37,6 +38,7 @@ struct SubInfo {
   int64_t R;         // subdomain R base (n*d, column-major)
   int64_t trow;      // base of this subdomain's tile-row partials (nb*kT entries) == qcol
   int64_t tpart;     // base of this subdomain's per-tile column partials (ntile*kT entries)
+  int64_t rpart;     // base of this subdomain's row partials (nb * ceil(nb / kApplyChunk) * kT entries)
 };
 
 struct DevPlan {

@@ -70,7 +70,9 @@ struct feti_ctx {
   int* d_trsm_order = nullptr;
   int* d_impl_order = nullptr;
   int2* d_syrk_items = nullptr;
-  int2* d_apply_items = nullptr;
+  int4* d_apply_items = nullptr;
+  void* d_pg = nullptr;
+  void* d_rowpart = nullptr;
   int2* d_syrk2_items = nullptr;
   int nsyrk2 = 0;
   int* d_colperm = nullptr;   // per subdomain sorted column -> B row (for get_F)

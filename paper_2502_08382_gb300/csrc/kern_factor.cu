@@ -26,60 +26,102 @@ __device__ __forceinline__ int pop_item(int* queue) {
   return item;
 }
 
-// acc[a][b] += sum_k A[k][ty + 16a] * B[k][tx + 16b]
-__device__ __forceinline__ void tile_mma(const double (*A)[kT], const double (*B)[kT], int kc,
-                                         double acc[4][4], int tx, int ty) {
+// acc[u][v] += sum_k A[k][r0 + 16u] * B[k][c0 + 16v] for u < NU, v < NV
+// (skipping v > u on diagonal tiles).  NU / NV are warp-uniform counts of
+// micro-rows / micro-columns that hold real data, so padded parts of small
+// fronts issue no FP64 work.
+template <typename T, int NU, int NV, bool DIAG>
+__device__ __forceinline__ void tile_mma_g(const T (*A)[kT], const T (*B)[kT], int kc, T acc[4][4], int r0,
+                                           int c0) {
   for (int k = 0; k < kc; ++k) {
-    double a[4], b[4];
+    T a[NU], b[NV];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u] = A[k][ty + 16 * u];
-      b[u] = B[k][tx + 16 * u];
-    }
+    for (int u = 0; u < NU; ++u) a[u] = A[k][r0 + 16 * u];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < NV; ++v) b[v] = B[k][c0 + 16 * v];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (!DIAG || v <= u) acc[u][v] = fma(a[u], b[v], acc[u][v]);
   }
 }
 
+template <typename T, bool DIAG>
+__device__ __forceinline__ void tile_mma_dispatch(const T (*A)[kT], const T (*B)[kT], int kc, T acc[4][4], int r0,
+                                                  int c0, int nu, int nv) {
+#define FETI_TM(U, V) \
+  case (U) * 8 + (V): tile_mma_g<T, U, V, DIAG>(A, B, kc, acc, r0, c0); break;
+  switch (nu * 8 + nv) {
+    FETI_TM(1, 1) FETI_TM(1, 2) FETI_TM(1, 3) FETI_TM(1, 4)
+    FETI_TM(2, 1) FETI_TM(2, 2) FETI_TM(2, 3) FETI_TM(2, 4)
+    FETI_TM(3, 1) FETI_TM(3, 2) FETI_TM(3, 3) FETI_TM(3, 4)
+    FETI_TM(4, 1) FETI_TM(4, 2) FETI_TM(4, 3) FETI_TM(4, 4)
+    default: break;
+  }
+#undef FETI_TM
+}
+
+__device__ __forceinline__ int groups16(int valid) { return valid <= 0 ? 0 : min(4, (valid + 15) / 16); }
+
 struct Smem {
-  double D[kNB][kNB + 1];
+  double D[kNB][kNB + 1];  // diagonal block, becomes L_bb
   double A[kNB][kT];
-  double B[kNB][kT];
+  double B[kNB][kT];       // also holds L_bb^{-1} (as [kNB][kNB + 1]) in the solve kernel
+  double dinv[kNB];
   double red[kThreads / 32];
 };
 
-// Unblocked Cholesky of the nbk x nbk block in sm.D (lower).  Sets *bad on a
-// non-positive pivot (the pivot is then replaced by 1 so the sweep finishes).
-__device__ void chol_diag(Smem& sm, int nbk, int* bad) {
-  const int tid = threadIdx.x;
+// Warp-level Cholesky of the nbk x nbk block D (lower, in place) with
+// reciprocal pivots kept in dinv.  A non-positive pivot sets *bad and is
+// replaced by 1 so the sweep finishes with finite values.
+template <typename T>
+__device__ void warp_chol(T (*D)[kNB + 1], T* dinv, int nbk, int* bad) {
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < nbk; ++k) {
-    if (tid == 0) {
-      double d = sm.D[k][k];
-      if (!(d > 0.0)) {
-        *bad = 1;
-        d = 1.0;
+    if (lane == k) {
+      T d = D[k][k];
+      if (!(d > (T)0)) {
+        if (bad) *bad = 1;
+        d = (T)1;
       }
-      sm.D[k][k] = sqrt(d);
+      d = sqrt(d);
+      D[k][k] = d;
+      dinv[k] = (T)1 / d;
     }
-    __syncthreads();
-    if (tid > k && tid < nbk) sm.D[tid][k] = sm.D[tid][k] / sm.D[k][k];
-    __syncthreads();
-    int rem = nbk - k - 1;
-    for (int idx = tid; idx < rem * rem; idx += kThreads) {
-      int i = k + 1 + idx % rem, j = k + 1 + idx / rem;
-      if (i >= j) sm.D[i][j] -= sm.D[i][k] * sm.D[j][k];
+    __syncwarp();
+    if (lane > k && lane < nbk) D[lane][k] *= dinv[k];
+    __syncwarp();
+    if (lane > k && lane < nbk) {
+      const T lik = D[lane][k];
+      for (int j = k + 1; j <= lane; ++j) D[lane][j] -= lik * D[j][k];
     }
-    __syncthreads();
+    __syncwarp();
   }
+}
+
+// Warp-level inverse of the lower-triangular nbk x nbk factor in D (with
+// reciprocal pivots dinv): lane j computes column j of L^{-1} into Di.
+template <typename T>
+__device__ void warp_tri_inverse(const T (*D)[kNB + 1], const T* dinv, T (*Di)[kNB + 1], int nbk) {
+  const int j = threadIdx.x & 31;
+  for (int i = 0; i < kNB; ++i) Di[i][j] = (T)0;
+  if (j < nbk) {
+    Di[j][j] = dinv[j];
+    for (int i = j + 1; i < nbk; ++i) {
+      T s = (T)0;
+      for (int k = j; k < i; ++k) s = fma(D[i][k], Di[k][j], s);
+      Di[i][j] = -s * dinv[i];
+    }
+  }
+  __syncwarp();
 }
 
 // Partial dense factorisation of one front: eliminate the first w columns of
 // the (w+r) x (w+r) symmetric front held as Ls (column-major f x w) and W
 // (column-major r x r, lower part used).
 __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int r, int* bad) {
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
   for (int kb = 0; kb < w; kb += kNB) {
     const int nbk = min(kNB, w - kb);
     for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
@@ -87,31 +129,31 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
       sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : 0.0;
     }
     __syncthreads();
-    chol_diag(sm, nbk, bad);
+    if (warp == 0) warp_chol<double>(sm.D, sm.dinv, nbk, bad);
+    __syncthreads();
     for (int idx = tid; idx < nbk * nbk; idx += kThreads) {
       int i = idx % nbk, j = idx / nbk;
       if (i >= j) Ls[(int64_t)(kb + j) * f + kb + i] = sm.D[i][j];
     }
-    // panel: rows below the block, L_ib = A_ib L_bb^{-T}
+    // panel: rows below the block solve x L_bb^T = a, one thread per row, 64 rows at a time
     const int i0 = kb + nbk;
-    for (int i = i0 + tid; i < f; i += kThreads) {
-      double x[kNB];
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) x[k] = (k < nbk) ? Ls[(int64_t)(kb + k) * f + i] : 0.0;
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) {
-        if (k < nbk) {
-          double s = x[k];
-#pragma unroll
-          for (int l = 0; l < k; ++l) s = fma(-sm.D[k][l], x[l], s);
-          x[k] = s / sm.D[k][k];
+    for (int ri = i0; ri < f; ri += kT) {
+      for (int idx = tid; idx < nbk * kT; idx += kThreads) {
+        int xx = idx % kT, k = idx / kT;
+        sm.A[k][xx] = (ri + xx < f) ? Ls[(int64_t)(kb + k) * f + ri + xx] : 0.0;
+      }
+      __syncthreads();
+      if (tid < kT && ri + tid < f) {
+        for (int k = 0; k < nbk; ++k) {
+          double s = sm.A[k][tid];
+          for (int l = 0; l < k; ++l) s = fma(-sm.D[k][l], sm.A[l][tid], s);
+          s *= sm.dinv[k];
+          sm.A[k][tid] = s;
+          Ls[(int64_t)(kb + k) * f + ri + tid] = s;
         }
       }
-#pragma unroll
-      for (int k = 0; k < kNB; ++k)
-        if (k < nbk) Ls[(int64_t)(kb + k) * f + i] = x[k];
+      __syncthreads();
     }
-    __syncthreads();
     // trailing update C -= L_ib L_jb^T on the lower triangle of rows/cols [i0, f)
     const int nr = f - i0;
     const int T = (nr + kT - 1) / kT;
@@ -126,14 +168,16 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
         }
         __syncthreads();
         double acc[4][4] = {};
-        tile_mma(sm.A, sm.B, nbk, acc, tx, ty);
+        const int nu = groups16(f - ri - 2 * warp), nv = groups16(f - cj);
+        if (ti == tj) tile_mma_dispatch<double, true>(sm.A, sm.B, nbk, acc, ty, tx, nu, nv);
+        else tile_mma_dispatch<double, false>(sm.A, sm.B, nbk, acc, ty, tx, nu, nv);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           int i = ri + ty + 16 * u;
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             int j = cj + tx + 16 * v;
-            if (i < f && j <= i) {
+            if (u < nu && v < nv && i < f && j <= i) {
               double* p = (j < w) ? Ls + (int64_t)j * f + i : W + (int64_t)(j - w) * r + (i - w);
               *p -= acc[u][v];
             }
@@ -145,7 +189,7 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
+__global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          double* ws, int64_t ws_stride, int64_t front_sz,
                                                          int* status) {
   __shared__ Smem sm;
@@ -219,42 +263,57 @@ template <typename T>
 struct SolveSmem {
   T D[kNB][kNB + 1];
   T A[kNB][kT];
-  T B[kNB][kT];
+  T B[kNB][kT];  // also holds L_bb^{-1} (as [kNB][kNB + 1]) during the block solve
+  T dinv[kNB];
 };
 
 // Forward solve of one RHS front: X_s = L_ss^{-1} X_s, then C -= L_rs X_s
 // (C = the r bottom rows).  Column-major fronts: column j of X_s is
 // Xs[j * wp + 0 .. w), column j of the bottom block is W2[j * r + 0 .. r).
+// Each 32-row diagonal block is applied as its explicit inverse (computed in
+// the solve's precision T from L_bb), so the block solve is a small GEMM.
 template <typename T>
 __device__ void solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T* Xs, int wp, T* W2, int J) {
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
   const int r = f - w;
+  auto Di = reinterpret_cast<T (*)[kNB + 1]>(&sm.B[0][0]);
   for (int kb = 0; kb < w; kb += kNB) {
     const int nbk = min(kNB, w - kb);
     for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
       int i = idx % kNB, j = idx / kNB;
       sm.D[i][j] = (i < nbk && j <= i) ? (T)Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
     }
+    if (tid < kNB) sm.dinv[tid] = tid < nbk ? (T)(1.0 / Ls[(int64_t)(kb + tid) * f + kb + tid]) : (T)0;
     __syncthreads();
-    for (int col = tid; col < J; col += kThreads) {
-      T* xc = Xs + (int64_t)col * wp + kb;
-      T x[kNB];
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) x[k] = (k < nbk) ? xc[k] : (T)0;
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) {
-        if (k < nbk) {
-          T s = x[k];
-#pragma unroll
-          for (int l = 0; l < k; ++l) s = fma(-sm.D[k][l], x[l], s);
-          x[k] = s / sm.D[k][k];
+    if (warp == 0) warp_tri_inverse<T>(sm.D, sm.dinv, Di, nbk);
+    __syncthreads();
+    {
+      // X_b <- Di X_b for 64 columns at a time: column y = tid % 64, rows jg*8 .. jg*8+7
+      const int y = tid % kT, jg = tid / kT;
+      for (int cj = 0; cj < J; cj += kT) {
+        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
+          int k = idx % kNB, yy = idx / kNB;
+          sm.A[k][yy] = (k < nbk && cj + yy < J) ? Xs[(int64_t)(cj + yy) * wp + kb + k] : (T)0;
         }
-      }
+        __syncthreads();
+        if (jg * 8 < nbk && cj + (y & ~31) < J) {
+          T acc[8] = {};
+          for (int k = 0; k <= min(nbk - 1, jg * 8 + 7); ++k) {
+            const T a = sm.A[k][y];
 #pragma unroll
-      for (int k = 0; k < kNB; ++k)
-        if (k < nbk) xc[k] = x[k];
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = fma(Di[jg * 8 + jj][k], a, acc[jj]);
+          }
+          if (cj + y < J) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int j = jg * 8 + jj;
+              if (j < nbk) Xs[(int64_t)(cj + y) * wp + kb + j] = acc[jj];
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
     const int i0 = kb + nbk;
     const int TR = (f - i0 + kT - 1) / kT, TC = (J + kT - 1) / kT;
     for (int ti = 0; ti < TR; ++ti) {
@@ -270,26 +329,17 @@ __device__ void solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
         }
         __syncthreads();
         T acc[4][4] = {};
-        for (int k = 0; k < nbk; ++k) {
-          T a[4], b[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            a[u] = sm.A[k][tx + 16 * u];
-            b[u] = sm.B[k][ty + 16 * u];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-        }
+        // rows tx + 16u (all 16 tx per warp), columns ty + 16v (ty = 2 warp, 2 warp + 1)
+        const int nu = groups16(f - ri), nv = groups16(J - cj - 2 * warp);
+        tile_mma_dispatch<T, false>(sm.A, sm.B, nbk, acc, tx, ty, nu, nv);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           int col = cj + ty + 16 * v;
-          if (col >= J) continue;
+          if (v >= nv || col >= J) continue;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             int i = ri + tx + 16 * u;
-            if (i >= f) continue;
+            if (u >= nu || i >= f) continue;
             if (i < w) Xs[(int64_t)col * wp + i] -= acc[u][v];
             else W2[(int64_t)col * r + (i - w)] -= acc[u][v];
           }
@@ -301,7 +351,7 @@ __device__ void solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
+__global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          T* X, T* ws, int64_t ws_stride, int64_t front_sz) {
   __shared__ SolveSmem<T> sm;
   const int tid = threadIdx.x;

@@ -16,13 +16,10 @@ void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float
 size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);
-void launch_apply_rows_f64(const DevPlan& P, const int2* items, int nitems, const double* F, const double* p,
-                           double* trow, double* tpart, int grid, cudaStream_t st);
-void launch_apply_rows_f32(const DevPlan& P, const int2* items, int nitems, const float* F, const double* p,
-                           double* trow, double* tpart, int grid, cudaStream_t st);
-void launch_apply_cols(const DevPlan& P, const int* colsub, int64_t ncols, const double* trow,
-                       const double* tpart, double* qi, cudaStream_t st);
-void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* qi, double* q, cudaStream_t st);
+size_t apply_tiles_smem(bool fp32);
+void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
+                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int* colsub,
+                  const int* c0, const int* c1, int nlam, double* q, int grid, int* status, cudaStream_t st);
 void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, const int* colperm, double* out, cudaStream_t st);
 
 // implicit FP64 operator (eq. 11) and the vector kernels of PCPG / eqs. 5-8
