@@ -18,6 +18,7 @@
 using namespace feti;
 
 namespace feti {
+void coarse_setup_entry(feti_ctx* c);
 
 feti_status set_error(feti_ctx* c, feti_status s, const std::string& msg) {
   if (c) {
@@ -209,7 +210,7 @@ void build(feti_ctx* c) {
   c->stats.nbplans = (int)c->bps.size();
 
   // ---- concatenate pattern tables
-  std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src;
+  std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
   std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs;
   std::vector<int> pat_sn0(c->pats.size());
   std::vector<int64_t> pat_diag0(c->pats.size());
@@ -236,6 +237,7 @@ void build(feti_ctx* c) {
     kmap_dst.insert(kmap_dst.end(), P.kmap_dst.begin(), P.kmap_dst.end());
     pat_diag0[p] = diag_src.size();
     diag_src.insert(diag_src.end(), P.diag_src.begin(), P.diag_src.end());
+    iperm.insert(iperm.end(), P.iperm.begin(), P.iperm.end());
   }
   sn_rows.push_back(rows.size());
   ch_off.push_back((int)ch_list.size());
@@ -274,7 +276,7 @@ void build(feti_ctx* c) {
 
   // ---- per-subdomain layout
   c->info.resize(ns);
-  std::vector<int> qmap, fix_sn, colsub, colperm;
+  std::vector<int> qmap, fix_sn, colsub, colperm, qdof, dofsub;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
   int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, rpo = 0;
@@ -282,7 +284,7 @@ void build(feti_ctx* c) {
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
   int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0;
   size_t esz = c->fp32 ? 4 : 8;
-  double apply_bytes = 0;
+  double apply_bytes = 0, stored_bytes = 0;
   c->colperm_ofs.resize(ns);
   for (int i = 0; i < ns; ++i) {
     auto& s = c->subs[i];
@@ -304,6 +306,7 @@ void build(feti_ctx* c) {
     I.tile0 = bp_tile0[s.bp];
     I.t20 = bp_t20[s.bp];
     I.nb2 = B.nb2;
+    I.vr = B.nb > 0 ? s.m - kT * (B.nb - 1) : 0;
     I.fix0 = fixo;
     I.alpha0 = alo;
     I.kmapb = 0;
@@ -323,7 +326,7 @@ void build(feti_ctx* c) {
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
     Xo += B.Xsize;
-    Fo += (int64_t)ntile * kT * kT;
+    Fo += F_size(B.nb, I.vr);
     qo += B.m_pad;
     dofo += s.n;
     Ro += (int64_t)s.n * s.d;
@@ -335,9 +338,11 @@ void build(feti_ctx* c) {
         qmap.push_back(s.blam[r]);
         qsign.push_back(s.bsign[r]);
         colperm.push_back(r);
+        qdof.push_back(s.bdof[r]);
       } else {
         qmap.push_back(-1);
         qsign.push_back(0.0);
+        qdof.push_back(0);
       }
       colsub.push_back(i);
     }
@@ -351,6 +356,8 @@ void build(feti_ctx* c) {
       fix_pos.push_back(P.Lofs[sn] + (int64_t)loc * f + loc);
     }
     fixo += s.nfix;
+    for (int k = 0; k < s.n; ++k) dofsub.push_back(i);
+    c->nmax = std::max(c->nmax, s.n);
     chol += P.chol_flops;
     trsm += B.trsm_flops;
     syrk += B.syrk_flops;
@@ -361,6 +368,7 @@ void build(feti_ctx* c) {
     max_rhs = std::max(max_rhs, B.rhs_stack);
     max_rf = std::max(max_rf, B.rhs_front);
     apply_bytes += (double)esz * s.m * (s.m + 1) / 2.0 + (double)s.m * (4 + 8 + 8);
+    stored_bytes += (double)esz * F_size(B.nb, I.vr);
   }
   apply_bytes += (double)c->nlam * 16.0;
   c->ncols = qo;
@@ -392,6 +400,38 @@ void build(feti_ctx* c) {
       else throw ArgError("a multiplier touches more than two subdomains");
     }
   }
+
+  // ---- coarse problem pairs: (i, k) blocks of G^T G and the sorted columns they pair
+  {
+    std::map<std::pair<int, int>, std::vector<int2>> pm;
+    for (int i = 0; i < ns; ++i) {
+      auto& I = c->info[i];
+      if (I.d == 0) continue;
+      auto& v = pm[{i, i}];
+      for (int j = 0; j < I.m; ++j) v.push_back(make_int2((int)(I.qcol + j), (int)(I.qcol + j)));
+    }
+    for (int l = 0; l < c->nlam; ++l) {
+      if (c0[l] < 0 || c1[l] < 0) continue;
+      int i = colsub[c0[l]], k = colsub[c1[l]];
+      if (c->info[i].d == 0 || c->info[k].d == 0) continue;
+      if (i < k) pm[{i, k}].push_back(make_int2(c0[l], c1[l]));
+      else pm[{k, i}].push_back(make_int2(c1[l], c0[l]));
+    }
+    std::vector<int4> pairs;
+    std::vector<int2> plist;
+    for (auto& kv : pm) {
+      auto& Ii = c->info[kv.first.first];
+      auto& Ik = c->info[kv.first.second];
+      int b = (int)plist.size();
+      plist.insert(plist.end(), kv.second.begin(), kv.second.end());
+      pairs.push_back(make_int4(Ii.alpha0 | (Ii.d << 24), Ik.alpha0 | (Ik.d << 24), b, (int)plist.size()));
+    }
+    c->npairs = (int)pairs.size();
+    c->d_pairs = upload(c, pairs);
+    c->d_plist = upload(c, plist);
+  }
+  for (auto& I : c->info)
+    if (I.d > 6) throw ArgError("kernel dimension d > 6 is not supported");
 
   // ---- work orders
   std::vector<int> order(ns);
@@ -439,6 +479,10 @@ void build(feti_ctx* c) {
   std::stable_sort(sy.begin(), sy.end(), [](auto& a, auto& b) { return a.first > b.first; });
   std::vector<int2> syi;
   for (auto& x : sy) syi.push_back(x.second);
+  std::vector<int2> blocks;
+  for (int i = 0; i < ns; ++i)
+    for (int b = 0; b < c->bps[c->subs[i].bp].nb; ++b) blocks.push_back(make_int2(i, b));
+  c->nblocks = (int)blocks.size();
   c->nsyrk = (int)syi.size();
   c->napply = (int)api.size();
 
@@ -488,6 +532,10 @@ void build(feti_ctx* c) {
   D.qmap = upload(c, qmap);
   D.qsign = upload(c, qsign);
   D.fix_sn = upload(c, fix_sn);
+  D.iperm = upload(c, iperm);
+  D.qdof = upload(c, qdof);
+  c->d_dofsub = upload(c, dofsub);
+  c->ndof = (int64_t)dofsub.size();
   D.fix_pos = upload(c, fix_pos);
   D.sub = upload(c, c->info);
   std::vector<double> kv;
@@ -522,10 +570,33 @@ void build(feti_ctx* c) {
   c->d_syrk_items = upload(c, syi);
   c->d_apply_items = upload(c, api);
   c->d_syrk2_items = upload(c, sy2i);
+  c->d_blocks = upload(c, blocks);
   c->d_colperm = upload(c, colperm);
   c->d_R = upload(c, Rall);
   c->d_f = upload(c, fall);
   c->d_c = upload(c, c->c_host);
+  {
+    const int D2 = std::max(c->dtot, 1);
+    const int nblk = (D2 + kT - 1) / kT;
+    c->d_G6 = (double*)dalloc(c, (size_t)qo * 6 * 8);
+    c->d_A = (double*)dalloc(c, (size_t)D2 * D2 * 8);
+    c->d_Ainv = (double*)dalloc(c, (size_t)D2 * D2 * 8);
+    c->d_Linv = (double*)dalloc(c, (size_t)D2 * D2 * 8);
+    c->d_Dinv = (double*)dalloc(c, (size_t)nblk * kT * kT * 8);
+    c->d_Tp = (double*)dalloc(c, (size_t)D2 * kT * 8);
+    c->d_Tb = (double*)dalloc(c, (size_t)D2 * kT * 8);
+    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 8 * 8);
+    c->d_cv = (double*)dalloc(c, (size_t)D2 * 4 * 8);
+    c->d_sc = (double*)dalloc(c, 16 * 8);
+    c->d_part = (double*)dalloc(c, 1024 * 8);
+    CK(cudaMallocHost((void**)&c->h_sc, 16 * 8));
+    launch_build_G(D, c->d_colsub, qo, c->d_R, c->d_G6, c->st);
+    CK(cudaGetLastError());
+    size_t sm = implicit_smem(c->nmax);
+    if (sm > 227 * 1024) throw ArgError("subdomain too large for the shared-memory implicit solve");
+    c->impl_smem = sm;
+    c->grid_impl = std::min(ns, c->nsm * implicit_occupancy(sm));
+  }
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
   CK(cudaMemsetAsync(c->d_tpart, 0, (size_t)std::max<int64_t>(tpo, 1) * 8, c->st));
   c->stats.workspace_bytes = (int64_t)gw * c->ws_stride * 8;
@@ -638,6 +709,11 @@ feti_status feti_assemble(feti_ctx* ctx) {
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[3], st));
+  if (!ctx->coarse_ready) {
+    // G = B R does not depend on the values of K: the coarse problem is set up once
+    coarse_setup_entry(ctx);
+    CK(cudaGetLastError());
+  }
   CK(cudaEventRecord(ctx->ev[4], st));
   CK(cudaStreamSynchronize(st));
   float a, b, cc, d;
@@ -648,7 +724,10 @@ feti_status feti_assemble(feti_ctx* ctx) {
   ctx->stats.t_chol_ms = a;
   ctx->stats.t_trsm_ms = b;
   ctx->stats.t_syrk_ms = cc;
-  ctx->stats.t_coarse_ms = 0;
+  float e34;
+  CK(cudaEventElapsedTime(&e34, ctx->ev[3], ctx->ev[4]));
+  if (!ctx->coarse_ready) ctx->stats.t_coarse_ms = e34;
+  ctx->coarse_ready = true;
   ctx->stats.t_assemble_ms = d;
   int status = 0;
   CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -667,8 +746,8 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   cudaStream_t st = ctx->st;
   int grid = std::max(1, std::min(ctx->napply, ctx->nsm * 2));
   launch_apply(ctx->P, ctx->fp32, ctx->d_apply_items, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
-               ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_colsub, ctx->d_c0, ctx->d_c1, ctx->nlam, q_dev, grid,
-               ctx->d_status, st);
+               ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
+               ctx->nlam, q_dev, grid, ctx->d_status, st);
   CK(cudaGetLastError());
   return FETI_OK;
   API_END
@@ -686,7 +765,7 @@ feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host) {
   CK(cudaMallocAsync((void**)&tmp, std::max<size_t>(bytes, 8), ctx->st));
   size_t esz = ctx->fp32 ? 4 : 8;
   const char* Fsub = (const char*)ctx->d_F + I.F * esz;
-  launch_unpack_F(Fsub, ctx->fp32, I.m, I.nb, ctx->d_colperm + ctx->colperm_ofs[sub], tmp, ctx->st);
+  launch_unpack_F(Fsub, ctx->fp32, I.m, I.nb, I.vr, ctx->d_colperm + ctx->colperm_ofs[sub], tmp, ctx->st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out_host, tmp, bytes, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaFreeAsync(tmp, ctx->st));
@@ -708,6 +787,7 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->st || true) cudaStreamSynchronize(ctx->st);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   for (auto& b : ctx->bufs) {
     if (ctx->opt.dev_free) ctx->opt.dev_free(b.p, ctx->opt.alloc_ctx);
     else if (!ctx->opt.dev_alloc) cudaFree(b.p);

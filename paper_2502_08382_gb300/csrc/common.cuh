@@ -26,7 +26,7 @@ struct SubInfo {
   int alpha0;        // offset of this subdomain's alpha block
   int t20;           // bplan t2_off base (128 x 128 tiles)
   int nb2;           // 128-wide blocks
-  int pad_;
+  int vr;            // rows of the last block row (m - kT (nb - 1)); that row stores only these
   int64_t kmapb;     // base of this pattern's kmap entries (kmap_off values are absolute)
   int64_t diag0;     // diag_src base
   int64_t Kval;      // subdomain K values base
@@ -75,6 +75,8 @@ struct DevPlan {
   // per subdomain
   const int* qmap;           // [qcol + j] global multiplier of sorted column j, -1 for padding
   const double* qsign;       // [qcol + j] sign of B in sorted column j (0 for padding)
+  const int* iperm;          // [diag0 + old DOF] new-numbered DOF (pattern)
+  const int* qdof;           // [qcol + j] original local DOF of sorted column j
   const int* fix_sn;         // [fix0 + k] supernode holding fixing DOF k
   const int64_t* fix_pos;    // [fix0 + k] diagonal position in L (relative)
   // values
@@ -82,6 +84,17 @@ struct DevPlan {
   double* L;
   double* rho;               // [nsub]
 };
+
+// F_i storage: lower tiles (bi, bj), bj <= bi, tile rows kT wide; block row
+// bi < nb - 1 holds kT rows per tile, the last block row only S.vr rows.
+__host__ __device__ inline int64_t tile_offset(int nb, int vr, int bi, int bj) {
+  if (bi < nb - 1) return ((int64_t)bi * (bi + 1) / 2 + bj) * kT * kT;
+  return ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)bj * vr * kT;
+}
+__host__ __device__ inline int tile_rows(int nb, int vr, int bi) { return bi < nb - 1 ? kT : vr; }
+__host__ __device__ inline int64_t F_size(int nb, int vr) {
+  return nb == 0 ? 0 : ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)nb * vr * kT;
+}
 
 // status word bits written by kernels
 enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };

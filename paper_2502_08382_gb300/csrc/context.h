@@ -74,6 +74,8 @@ struct feti_ctx {
   void* d_pg = nullptr;
   void* d_rowpart = nullptr;
   int2* d_syrk2_items = nullptr;
+  int2* d_blocks = nullptr;
+  int nblocks = 0;
   int nsyrk2 = 0;
   int* d_colperm = nullptr;   // per subdomain sorted column -> B row (for get_F)
   std::vector<int64_t> colperm_ofs;
@@ -82,6 +84,25 @@ struct feti_ctx {
   int grid_chol = 0, grid_trsm = 0, grid_impl = 0;
   size_t impl_smem = 0;
   // solve-side data
+  bool coarse_ready = false;
+  int npairs = 0;
+  int4* d_pairs = nullptr;
+  int2* d_plist = nullptr;
+  double* d_G6 = nullptr;      // [ncols * 6] G = B R per sorted column
+  double* d_A = nullptr;       // D x D coarse matrix, then its factor
+  double* d_Ainv = nullptr;    // (G^T G)^{-1}
+  double* d_Linv = nullptr;
+  double* d_Dinv = nullptr;    // inverses of the 64 x 64 diagonal factor blocks
+  double* d_Tp = nullptr;      // D x 64 panel scratch
+  double* d_Tb = nullptr;      // 64 x D row-block scratch
+  double* d_vec = nullptr;     // PCPG vectors (7 x n_lambda)
+  double* d_cv = nullptr;      // coarse vectors (4 x D)
+  double* d_sc = nullptr;      // scalars
+  double* d_part = nullptr;    // dot partials
+  double* h_sc = nullptr;      // pinned host scalars
+  int* d_dofsub = nullptr;
+  int64_t ndof = 0;
+  int nmax = 0;
   double* d_R = nullptr;       // concatenated R_i (column-major n x d)
   double* d_f = nullptr;       // concatenated f_i
   double* d_c = nullptr;       // c

@@ -1,31 +1,38 @@
 // Explicit application q = F p (paper eq. 12 summed over subdomains, with
 // Algorithm 2's scatter / per-subdomain apply / gather), three launches:
 //
-//  1. scatter:  pg[j] = p[map_i(j)] for every sorted column j of every
-//               subdomain (FP32 for FP32 tiles, FP64 for FP64 tiles);
-//  2. tiles:    a persistent kernel streams the lower tiles of all F_i from
-//               HBM with 1D bulk copies (cp.async.bulk + mbarrier
-//               complete_tx) through a ring of shared-memory stages.  A work
-//               item is up to kChunk consecutive tiles (b, bj0..bj1) of one
-//               tile row, which are contiguous in memory.  For each tile the
-//               CTA forms the row partial F_t p_bj (accumulated over the
-//               item) and, off the diagonal, the column partial F_t^T p_b;
-//               both go to small per-item / per-tile scratch slots;
-//  3. gather:   q[lambda] = sum over the (at most two) subdomain columns of
-//               lambda of their row and column partials, in a fixed order
-//               (deterministic, no atomics).
+//  0. scatter: pg[j] = p[map_i(j)] for every sorted column j of every
+//             subdomain (Algorithm 2's scatter), in the tile precision;
+//  1. tiles:  a persistent, warp-specialised kernel streams the lower tiles
+//             of all F_i from HBM.  Lane 0 of warp 8 is the producer: for each
+//             tile it issues 1D bulk copies (cp.async.bulk + mbarrier
+//             complete_tx) of the contiguous 16 KB (FP32) / 32 KB (FP64) tile
+//             and of the two 64-entry segments of pg it needs into a ring of
+//             shared-memory stages.  Warps 0-7 consume: per tile the row partial F_t p_bj
+//             (accumulated over the work item) and, off the diagonal, the
+//             column partial F_t^T p_b.  A work item is up to kApplyChunk
+//             consecutive tiles (b, bj0..bj1) of one tile row (contiguous in
+//             memory).  Stages are released through per-stage `empty`
+//             mbarriers; the last consumer warp to finish a tile sums the 8
+//             per-warp column partials (no CTA-wide barrier in the loop).
+//  2. gather: q[lambda] = sum over the (at most two) subdomain columns of
+//             lambda of their row and column partials, in a fixed order
+//             (deterministic, no atomics on values).
 // Tile arithmetic runs in the tile's precision (FP32 tiles: FP32 FMAs over
-// 64 terms); the cross-tile sums in phase 3 are FP64.
+// 64 terms); the cross-tile sums in phase 2 are FP64.  All waits are bounded.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace feti {
 namespace {
 
-constexpr int kApplyThreads = 256;
+constexpr int kConsumerWarps = 8;
+constexpr int kApplyThreads = (kConsumerWarps + 1) * 32;
 template <typename TF>
 struct ApplyCfg {
-  static constexpr int kStages = sizeof(TF) == 4 ? 6 : 3;
+  static constexpr int kStages = sizeof(TF) == 4 ? 5 : 2;
+  static constexpr int kTileBytes = kT * kT * (int)sizeof(TF);
+  static constexpr int kStageBytes = kTileBytes + 2 * kT * (int)sizeof(TF);
 };
 
 __device__ __forceinline__ uint32_t smem_u32a(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -41,8 +48,38 @@ __device__ __forceinline__ bool mbar_test_a(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+__device__ __forceinline__ bool mbar_try_a(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// lane 0 waits (try_wait, bounded by about 2e9 clock cycles), result broadcast to the warp
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) {
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_a(mbar, parity))) {
+      if (clock64() - t0 > 2000000000LL) break;
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(mbar)
@@ -57,116 +94,145 @@ __global__ void scatter_kernel(const int* qmap, int64_t ncols, const double* p, 
   }
 }
 
-// Cursor over this CTA's flattened tile sequence (items blockIdx.x + k * gridDim.x).
-struct TileCursor {
-  int item, tile;  // item index into the list, tile offset inside the item
-};
-
 template <typename TF>
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_tiles_kernel(DevPlan P, const int4* items, int nitems,
                                                                       const TF* F, const TF* pg, TF* rowpart,
                                                                       TF* colpart, int* status) {
-  constexpr int kTileBytes = kT * kT * (int)sizeof(TF);
-  constexpr int kStagesA = ApplyCfg<TF>::kStages;
+  using C = ApplyCfg<TF>;
+  constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  __shared__ uint64_t full[kStagesA];
-  __shared__ TF prow[kT], pcol[kT];
-  __shared__ TF cred[16][kT + 1];
-  __shared__ int s_abort;
-  const int tid = threadIdx.x;
-  const int rg = tid / 16, cg = tid % 16;  // 4 x 4 block: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
+  __shared__ uint64_t full[S], empty[S];
+  __shared__ TF cred[S][kConsumerWarps][kT];
+  __shared__ int cnt[S];
+  __shared__ volatile int s_abort;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   if (tid == 0) {
-    for (int s = 0; s < kStagesA; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(&full[s])));
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32a(&empty[s])), "r"(kConsumerWarps));
+      cnt[s] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
   __syncthreads();
-  // producer state (thread 0 only)
-  TileCursor pc{(int)blockIdx.x, 0};
-  uint32_t issued = 0;
-  auto produce = [&]() {
-    // issue the next tile of this CTA's sequence, if any
-    while (pc.item < nitems && pc.tile >= items[pc.item].w - items[pc.item].z) {
-      pc.item += gridDim.x;
-      pc.tile = 0;
-    }
-    if (pc.item >= nitems) return;
-    const int4 it = items[pc.item];
-    const SubInfo& S = P.sub[it.x];
-    const int b = it.y, bj = it.z + pc.tile;
-    const TF* src = F + S.F + (int64_t)(b * (b + 1) / 2 + bj) * kT * kT;
-    const int st = issued % kStagesA;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    bulk_load(smem_u32a(smem + st * kTileBytes), src, kTileBytes, smem_u32a(&full[st]));
-    ++issued;
-    ++pc.tile;
-  };
-  if (tid == 0)
-    for (int s = 0; s < kStagesA; ++s) produce();
 
-  uint32_t consumed = 0;
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    uint32_t t = 0;
+    for (int ii = blockIdx.x; ii < nitems && !s_abort; ii += gridDim.x) {
+      const int4 it = items[ii];
+      const SubInfo& Sb = P.sub[it.x];
+      const int b = it.y;
+      for (int bj = it.z; bj < it.w; ++bj, ++t) {
+        const int st = t % S;
+        if (t >= S && !warp_wait(smem_u32a(&empty[st]), ((t / S) + 1) & 1)) {
+          s_abort = 1;
+          break;
+        }
+        if (lane == 0) {
+          const uint32_t stage = smem_u32a(smem + st * C::kStageBytes);
+          const uint32_t fb = smem_u32a(&full[st]);
+          const TF* src = F + Sb.F + tile_offset(Sb.nb, Sb.vr, b, bj);
+          const uint32_t tb = (uint32_t)tile_rows(Sb.nb, Sb.vr, b) * kT * (uint32_t)sizeof(TF);
+          expect_tx(fb, tb + 2 * kT * (uint32_t)sizeof(TF));
+          bulk_copy(stage, src, tb, fb);
+          bulk_copy(stage + C::kTileBytes, pg + Sb.qcol + b * kT, kT * sizeof(TF), fb);
+          bulk_copy(stage + C::kTileBytes + kT * sizeof(TF), pg + Sb.qcol + bj * kT, kT * sizeof(TF), fb);
+        }
+        __syncwarp();
+      }
+    }
+    // drain: every issued copy must land before the CTA exits
+    if (s_abort) {
+      for (uint32_t u = (t > S ? t - S : 0); u < t; ++u) warp_wait(smem_u32a(&full[u % S]), (u / S) & 1);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int rg = tid / 16, cg = tid % 16;  // 4 x 4 block: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
+  uint32_t t = 0;
   for (int ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
     const int4 it = items[ii];
-    const SubInfo S = P.sub[it.x];
+    const SubInfo& Sb = P.sub[it.x];
     const int b = it.y;
-    __syncthreads();
-    if (tid < kT) prow[tid] = pg[S.qcol + b * kT + tid];
     TF racc[4] = {(TF)0, (TF)0, (TF)0, (TF)0};
-    for (int bj = it.z; bj < it.w; ++bj) {
-      const int st = consumed % kStagesA;
-      if (tid < kT) pcol[tid] = pg[S.qcol + bj * kT + tid];
-      if (tid == 0) {
-        bool ok = false;
-        for (int spin = 0; spin < (1 << 25); ++spin) {
-          if (mbar_test_a(smem_u32a(&full[st]), (consumed / kStagesA) & 1)) {
-            ok = true;
-            break;
-          }
-          __nanosleep(20);
-        }
-        if (!ok) s_abort = 1;
+    bool ok = true;
+    for (int bj = it.z; bj < it.w; ++bj, ++t) {
+      const int st = t % S;
+      if (!warp_wait(smem_u32a(&full[st]), (t / S) & 1)) {
+        ok = false;
+        break;
       }
-      __syncthreads();
-      if (s_abort) break;
-      const TF* Ft = reinterpret_cast<const TF*>(smem + st * kTileBytes);
+      const uint8_t* stage = smem + st * C::kStageBytes;
+      const TF* Ft = reinterpret_cast<const TF*>(stage);
+      const TF* pr = reinterpret_cast<const TF*>(stage + C::kTileBytes);
+      const TF* pc = pr + kT;
+      // rows at or beyond the tile's stored rows hold stale data: read as zero
+      const int nrow = tile_rows(Sb.nb, Sb.vr, b);
       TF v[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const TF* rowp = Ft + (4 * rg + a) * kT + 4 * cg;
+        const bool in = 4 * rg + a < nrow;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[a][c] = rowp[c];
+        for (int c = 0; c < 4; ++c) v[a][c] = in ? rowp[c] : (TF)0;
       }
-      // row partial: rows 4rg+a over columns 4cg..4cg+3 (reduced over cg after the item)
+      TF pcv[4], prv[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        pcv[c] = pc[4 * cg + c];
+        prv[c] = pr[4 * rg + c];
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         TF s = (TF)0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) s = fma(v[a][c], pcol[4 * cg + c], s);
+        for (int c = 0; c < 4; ++c) s = fma(v[a][c], pcv[c], s);
         racc[a] += s;
       }
       if (bj < b) {
-        // column partial: columns 4cg+c over rows 4rg..4rg+3, reduced over rg through shared memory
+        TF cs[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           TF s = (TF)0;
 #pragma unroll
-          for (int a = 0; a < 4; ++a) s = fma(v[a][c], prow[4 * rg + a], s);
-          cred[rg][4 * cg + c] = s;
+          for (int a = 0; a < 4; ++a) s = fma(v[a][c], prv[a], s);
+          cs[c] = s + __shfl_xor_sync(0xffffffffu, s, 16);  // the warp's two row groups
+        }
+        if (lane < 16) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cred[st][warp][4 * cg + c] = cs[c];
+        }
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          __threadfence_block();
+          last = atomicAdd(&cnt[st], 1) == kConsumerWarps - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+          __threadfence_block();
+          for (int c = lane; c < kT; c += 32) {
+            TF s = (TF)0;
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) s += cred[st][w][c];
+            colpart[Sb.tpart + (int64_t)(b * (b + 1) / 2 + bj) * kT + c] = s;  // per-tile slots (unragged)
+          }
+          if (lane == 0) cnt[st] = 0;
+          __syncwarp();
         }
       }
-      __syncthreads();  // stage fully read; column partials staged
-      ++consumed;
-      if (tid == 0) produce();
-      if (bj < b && tid < kT) {
-        TF s = (TF)0;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) s += cred[r][tid];
-        colpart[S.tpart + (int64_t)(b * (b + 1) / 2 + bj) * kT + tid] = s;
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32a(&empty[st]));
     }
-    if (s_abort) break;
-    // reduce the row partial over the 16 column groups (lanes cg within a half warp)
+    if (!ok) {
+      s_abort = 1;
+      break;
+    }
+    // row partial: reduce over the 16 column groups (lanes of a half warp)
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       TF s = racc[a];
@@ -175,85 +241,87 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_tiles_kernel(DevPlan P
       racc[a] = s;
     }
     if (cg == 0) {
-      const int nch = (S.nb + kApplyChunk - 1) / kApplyChunk;
+      const int nch = (Sb.nb + kApplyChunk - 1) / kApplyChunk;
       const int chunk = it.z / kApplyChunk;
-      TF* dst = rowpart + S.rpart + ((int64_t)b * nch + chunk) * kT + 4 * rg;
+      TF* dst = rowpart + Sb.rpart + ((int64_t)b * nch + chunk) * kT + 4 * rg;
 #pragma unroll
       for (int a = 0; a < 4; ++a) dst[a] = racc[a];
     }
   }
   if (s_abort && tid == 0) atomicOr(status, kStatTimeout);
-  // drain: wait (bounded) for copies this CTA issued but did not consume
-  if (tid == 0) {
-    while (consumed < issued) {
-      const int st = consumed % kStagesA;
-      bool ok = false;
-      for (int spin = 0; spin < (1 << 25); ++spin) {
-        if (mbar_test_a(smem_u32a(&full[st]), (consumed / kStagesA) & 1)) {
-          ok = true;
-          break;
-        }
-        __nanosleep(20);
-      }
-      if (!ok) break;
-      ++consumed;
-    }
-  }
-  __syncthreads();
 }
 
-// q[lambda] = sum over its subdomain columns g of (row partials of g's block
-// over the item chunks) + (column partials of the tiles below g's block).
+// q_i[j] = (row partials of block b(j) over the item chunks) + (column
+// partials of the tiles below block b(j)); one warp per (subdomain, block),
+// lanes over the 64 columns of the block.  FP64 sums in a fixed order.
 template <typename TF>
-__global__ void gather_kernel(DevPlan P, const int* colsub, const int* c0, const int* c1, int nlam,
-                              const TF* rowpart, const TF* colpart, double* q) {
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
-    double tot = 0.0;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int g = e == 0 ? c0[l] : c1[l];
-      if (g < 0) continue;
-      const SubInfo& S = P.sub[colsub[g]];
-      const int j = (int)(g - S.qcol), b = j / kT, x = j % kT;
-      const int nch = (S.nb + kApplyChunk - 1) / kApplyChunk;
+__global__ void reduce_cols_kernel(DevPlan P, const int2* blocks, int nblocks, const TF* rowpart,
+                                   const TF* colpart, double* qi) {
+  const int lane = threadIdx.x & 31;
+  for (int wb = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wb < nblocks; wb += gridDim.x * blockDim.x / 32) {
+    const int2 sb = blocks[wb];
+    const SubInfo& S = P.sub[sb.x];
+    const int b = sb.y, nb = S.nb;
+    const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
+    const int64_t rp = S.rpart, tp = S.tpart, qc = S.qcol;
+    for (int x = lane; x < kT; x += 32) {
       double s = 0.0;
-      for (int c = 0; c * kApplyChunk <= b; ++c) s += (double)rowpart[S.rpart + ((int64_t)b * nch + c) * kT + x];
-      for (int bi = b + 1; bi < S.nb; ++bi) s += (double)colpart[S.tpart + (int64_t)(bi * (bi + 1) / 2 + b) * kT + x];
-      tot += s;
+      for (int c = 0; c * kApplyChunk <= b; ++c) s += (double)rowpart[rp + ((int64_t)b * nch + c) * kT + x];
+      for (int bi = b + 1; bi < nb; ++bi) s += (double)colpart[tp + (int64_t)(bi * (bi + 1) / 2 + b) * kT + x];
+      qi[qc + b * kT + x] = s;
     }
-    q[l] = tot;
+  }
+}
+
+// q[lambda] = its (at most two) subdomain contributions, in subdomain order
+__global__ void gather_lambda_kernel(const int* c0, const int* c1, int nlam, const double* qi, double* q) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int a = c0[l], b = c1[l];
+    double s = a >= 0 ? qi[a] : 0.0;
+    if (b >= 0) s += qi[b];
+    q[l] = s;
   }
 }
 
 }  // namespace
 
 size_t apply_tiles_smem(bool fp32) {
-  return fp32 ? (size_t)ApplyCfg<float>::kStages * kT * kT * 4 + 128 : (size_t)ApplyCfg<double>::kStages * kT * kT * 8 + 128;
+  return fp32 ? (size_t)ApplyCfg<float>::kStages * ApplyCfg<float>::kStageBytes + 128
+              : (size_t)ApplyCfg<double>::kStages * ApplyCfg<double>::kStageBytes + 128;
 }
 
 template <typename TF>
 static void launch_apply_t(const DevPlan& P, const int4* items, int nitems, const void* F, const int* qmap,
-                           int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int* colsub,
-                           const int* c0, const int* c1, int nlam, double* q, int grid, int* status, cudaStream_t st) {
-  const int sg = (int)std::min<int64_t>((ncols + 255) / 256, 152 * 8);
+                           int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                           int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid,
+                           int* status, cudaStream_t st) {
+  const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 152 * 8));
+  scatter_kernel<TF><<<sg, 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
   const size_t smem = apply_tiles_smem(sizeof(TF) == 4);
-  scatter_kernel<TF><<<std::max(sg, 1), 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
   cudaFuncSetAttribute(apply_tiles_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   apply_tiles_kernel<TF><<<grid, kApplyThreads, smem, st>>>(P, items, nitems, (const TF*)F, (const TF*)pg,
                                                            (TF*)rowpart, (TF*)colpart, status);
+  const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
+  reduce_cols_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
-  gather_kernel<TF><<<gg, 256, 0, st>>>(P, colsub, c0, c1, nlam, (const TF*)rowpart, (const TF*)colpart, q);
+  gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
+}
+
+void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* qi, double* q, cudaStream_t st) {
+  const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
+  gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
 }
 
 void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
-                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int* colsub,
-                  const int* c0, const int* c1, int nlam, double* q, int grid, int* status, cudaStream_t st) {
+                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                  int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int* status,
+                  cudaStream_t st) {
   if (fp32)
-    launch_apply_t<float>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, colsub, c0, c1, nlam, q, grid,
-                          status, st);
+    launch_apply_t<float>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                          nlam, q, grid, status, st);
   else
-    launch_apply_t<double>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, colsub, c0, c1, nlam, q, grid,
-                           status, st);
+    launch_apply_t<double>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                           nlam, q, grid, status, st);
 }
 
 }  // namespace feti

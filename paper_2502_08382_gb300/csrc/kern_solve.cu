@@ -1,0 +1,507 @@
+// FP64 solve-side kernels:
+//  * implicit operator (paper eq. 11) and the solves with K_reg used by d
+//    (eq. 7) and the primal recovery (eq. 5): supernodal forward / backward
+//    substitution with L_i, one subdomain per CTA, the subdomain vector held
+//    in shared memory;
+//  * the coarse problem G^T G (G = B R, eqs. 6-8): deterministic assembly,
+//    blocked Cholesky and explicit inverse built from 64 x 64 FP64 tile GEMMs;
+//  * the projector P = I - G (G^T G)^{-1} G^T and the PCPG vector updates of
+//    Algorithm 1 (M = I), with dot products reduced in a fixed order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace feti {
+namespace {
+
+constexpr int kW = 32;
+
+__device__ __forceinline__ int pop_item_s(int* queue) {
+  __shared__ int item;
+  __syncthreads();
+  if (threadIdx.x == 0) item = atomicAdd(queue, 1);
+  __syncthreads();
+  return item;
+}
+
+// MODE 0: qi = B L^-T L^-1 P B^T p        (implicit apply, eq. 11)
+// MODE 1: qi = B K_reg^{-1} f             (d = B K^+ f - c, eq. 7)
+// MODE 2: u  = K_reg^{-1} (f - B^T lambda) (eq. 5 without R alpha)
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
+                                                             const double* p, const double* f, double* qi,
+                                                             double* u) {
+  extern __shared__ double y[];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  for (;;) {
+    const int itx = pop_item_s(queue);
+    if (itx >= nsub) return;
+    const int si = order[itx];
+    const SubInfo& S = P.sub[si];
+    const int n = S.n;
+    const double* L = P.L + S.L;
+    for (int k = tid; k < n; k += kThreads) y[k] = 0.0;
+    __syncthreads();
+    if (MODE >= 1)
+      for (int k = tid; k < n; k += kThreads) y[P.iperm[S.diag0 + k]] = f[S.dof + k];
+    __syncthreads();
+    if (MODE != 1) {
+      // B^T p: columns sharing a DOF are adjacent in sorted order; the first of a run sums it
+      const int* sp = P.spos + S.col0;
+      for (int j = tid; j < S.m; j += kThreads) {
+        if (j > 0 && sp[j - 1] == sp[j]) continue;
+        double s = 0.0;
+        for (int jj = j; jj < S.m && sp[jj] == sp[j]; ++jj) s += P.qsign[S.qcol + jj] * p[P.qmap[S.qcol + jj]];
+        y[sp[j]] += (MODE == 0) ? s : -s;
+      }
+    }
+    __syncthreads();
+    // forward substitution L z = y, supernodes in postorder
+    for (int s = 0; s < S.nsn; ++s) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+      const double* Ls = L + P.Lofs[gs];
+      const int* rows = P.rows + P.sn_rows[gs];
+      for (int kb = 0; kb < w; kb += kW) {
+        const int nbk = min(kW, w - kb);
+        if (warp == 0) {
+          double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
+          for (int k = 0; k < nbk; ++k) {
+            const double yk = __shfl_sync(0xffffffffu, yi, k) / Ls[(int64_t)(kb + k) * f_ + kb + k];
+            if (lane == k) yi = yk;
+            else if (lane > k && lane < nbk) yi -= Ls[(int64_t)(kb + k) * f_ + kb + lane] * yk;
+          }
+          if (lane < nbk) y[c0 + kb + lane] = yi;
+        }
+        __syncthreads();
+        for (int i = kb + nbk + tid; i < f_; i += kThreads) {
+          double acc = 0.0;
+          for (int k = 0; k < nbk; ++k) acc += Ls[(int64_t)(kb + k) * f_ + i] * y[c0 + kb + k];
+          const int tgt = i < w ? c0 + i : rows[i - w];
+          y[tgt] -= acc;
+        }
+        __syncthreads();
+      }
+    }
+    // backward substitution L^T x = z, supernodes in reverse postorder
+    for (int s = S.nsn - 1; s >= 0; --s) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
+      const double* Ls = L + P.Lofs[gs];
+      const int* rows = P.rows + P.sn_rows[gs];
+      for (int l = warp; l < w; l += kThreads / 32) {
+        double acc = 0.0;
+        for (int k = lane; k < r; k += 32) acc += Ls[(int64_t)l * f_ + w + k] * y[rows[k]];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[c0 + l] -= acc;
+      }
+      __syncthreads();
+      for (int kb = ((w - 1) / kW) * kW; kb >= 0; kb -= kW) {
+        const int nbk = min(kW, w - kb);
+        for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
+          double acc = 0.0;
+          for (int i = kb + nbk + lane; i < w; i += 32) acc += Ls[(int64_t)l * f_ + i] * y[c0 + i];
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) y[c0 + l] -= acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
+          for (int k = nbk - 1; k >= 0; --k) {
+            const double yk = __shfl_sync(0xffffffffu, yi, k) / Ls[(int64_t)(kb + k) * f_ + kb + k];
+            if (lane == k) yi = yk;
+            else if (lane < k) yi -= Ls[(int64_t)(kb + lane) * f_ + kb + k] * yk;
+          }
+          if (lane < nbk) y[c0 + kb + lane] = yi;
+        }
+        __syncthreads();
+      }
+    }
+    if (MODE != 2) {
+      for (int j = tid; j < S.m_pad; j += kThreads)
+        qi[S.qcol + j] = j < S.m ? P.qsign[S.qcol + j] * y[P.spos[S.col0 + j]] : 0.0;
+    } else {
+      for (int k = tid; k < n; k += kThreads) u[S.dof + k] = y[P.iperm[S.diag0 + k]];
+    }
+    __syncthreads();
+  }
+}
+
+// q[l] = qi[c0] + qi[c1] - c[l]
+__global__ void gather_minus_c_kernel(const int* c0, const int* c1, int nlam, const double* qi, const double* c,
+                                      double* q) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int a = c0[l], b = c1[l];
+    double s = a >= 0 ? qi[a] : 0.0;
+    if (b >= 0) s += qi[b];
+    q[l] = s - (c ? c[l] : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------- G = B R
+
+// G6[g * 6 + k] = sign_j R_i[dof_j, k] for sorted column g of subdomain i
+__global__ void build_G_kernel(DevPlan P, const int* colsub, int64_t ncols, const double* R, double* G6) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ncols; g += (int64_t)gridDim.x * blockDim.x) {
+    const SubInfo& S = P.sub[colsub[g]];
+    const int j = (int)(g - S.qcol);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double v = 0.0;
+      if (j < S.m && k < S.d) v = P.qsign[g] * R[S.R + (int64_t)k * S.n + P.qdof[g]];
+      G6[g * 6 + k] = v;
+    }
+  }
+}
+
+// e[alpha0 + k] = R_i[:, k]^T f_i ; one warp per (subdomain, k)
+__global__ void rtf_kernel(DevPlan P, int nsub, const double* R, const double* f, double* e) {
+  const int lane = threadIdx.x & 31;
+  for (int wk = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wk < nsub * 6; wk += gridDim.x * blockDim.x / 32) {
+    const int si = wk / 6, k = wk % 6;
+    const SubInfo& S = P.sub[si];
+    if (k >= S.d) continue;
+    double acc = 0.0;
+    for (int i = lane; i < S.n; i += 32) acc += R[S.R + (int64_t)k * S.n + i] * f[S.dof + i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) e[S.alpha0 + k] = acc;
+  }
+}
+
+// c[alpha0 + k] = sum_j G6[(qcol + j) * 6 + k] x[map_j]  (G^T x), warp per (subdomain, k)
+__global__ void gt_kernel(DevPlan P, int nsub, const double* G6, const double* x, double* c) {
+  const int lane = threadIdx.x & 31;
+  for (int wk = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wk < nsub * 6; wk += gridDim.x * blockDim.x / 32) {
+    const int si = wk / 6, k = wk % 6;
+    const SubInfo& S = P.sub[si];
+    if (k >= S.d) continue;
+    double acc = 0.0;
+    for (int j = lane; j < S.m; j += 32) acc += G6[(S.qcol + j) * 6 + k] * x[P.qmap[S.qcol + j]];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c[S.alpha0 + k] = acc;
+  }
+}
+
+// out[l] = (x ? x[l] : 0) - sgn * (G z)[l]
+__global__ void gz_kernel(DevPlan P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+                          const double* x, const double* z, double sgn, double* out) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int g = e == 0 ? c0[l] : c1[l];
+      if (g < 0) continue;
+      const SubInfo& S = P.sub[colsub[g]];
+      for (int k = 0; k < S.d; ++k) s += G6[(int64_t)g * 6 + k] * z[S.alpha0 + k];
+    }
+    out[l] = (x ? x[l] : 0.0) - sgn * s;
+  }
+}
+
+// G^T G block (i, k) from the multiplier pairs shared by subdomains i and k
+__global__ void gtg_kernel(const int4* pairs, int npairs, const int2* plist, const double* G6, double* A, int D) {
+  for (int pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+    const int4 pr = pairs[pi];  // x = offset_i, y = offset_k, z = list begin, w = list end
+    const int a = threadIdx.x / 6, b = threadIdx.x % 6;
+    if (threadIdx.x >= 36) continue;
+    const int di = (pr.x >> 24) & 0xff, dk = (pr.y >> 24) & 0xff;
+    const int oi = pr.x & 0xffffff, ok = pr.y & 0xffffff;
+    if (a >= di || b >= dk) continue;
+    double s = 0.0;
+    for (int t = pr.z; t < pr.w; ++t) s += G6[(int64_t)plist[t].x * 6 + a] * G6[(int64_t)plist[t].y * 6 + b];
+    A[(int64_t)(oi + a) * D + ok + b] = s;
+    if (oi != ok) A[(int64_t)(ok + b) * D + oi + a] = s;
+  }
+}
+
+// ---------------------------------------------------------------- dense FP64 tiles
+
+// C = beta C + alpha op(A) op(B), row-major, 64 x 64 tile per CTA.
+// lower: only tiles/entries with col <= row.  ktri: the K sum starts at
+// max(row tile, col tile) (op(A) = W^T, op(B) = W with W lower triangular).
+__global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, double alpha, const double* A, int lda,
+                                                     int ta, const double* B, int ldb, int tb, double beta,
+                                                     double* C, int ldc, int lower, int ktri) {
+  __shared__ double As[16][kT + 1];
+  __shared__ double Bs[16][kT + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int r0 = blockIdx.y * kT, c0 = blockIdx.x * kT;
+  if (lower && c0 > r0 + kT - 1) return;
+  double acc[4][4] = {};
+  int kstart = ktri ? (max(r0, c0) / 16) * 16 : 0;
+  for (int k0 = kstart; k0 < K; k0 += 16) {
+    for (int idx = tid; idx < 16 * kT; idx += 256) {
+      const int k = idx / kT, x = idx % kT;
+      const int gi = r0 + x, gk = k0 + k, gj = c0 + x;
+      As[k][x] = (gi < M && gk < K) ? (ta ? A[(int64_t)gk * lda + gi] : A[(int64_t)gi * lda + gk]) : 0.0;
+      Bs[k][x] = (gj < N && gk < K) ? (tb ? B[(int64_t)gj * ldb + gk] : B[(int64_t)gk * ldb + gj]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[k][ty + 16 * u];
+        b[u] = Bs[k][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = r0 + ty + 16 * u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = c0 + tx + 16 * v;
+      if (i < M && j < N && (!lower || j <= i)) {
+        double* pc = C + (int64_t)i * ldc + j;
+        *pc = (beta == 0.0 ? 0.0 : beta * *pc) + alpha * acc[u][v];
+      }
+    }
+  }
+}
+
+// Cholesky of the n x n (n <= 64) diagonal block at A (row-major, ld lda),
+// in place (lower, upper part zeroed), and the inverse of the factor into
+// Dinv (64 x 64, row-major, ld 64).
+__global__ void __launch_bounds__(256) potrf64_kernel(double* A, int lda, int n, double* Dinv, int* status) {
+  __shared__ double a[kT][kT + 1];
+  __shared__ double b[kT][kT + 1];
+  __shared__ double rinv[kT];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kT * kT; idx += 256) {
+    const int i = idx / kT, j = idx % kT;
+    a[i][j] = (i < n && j < n && j <= i) ? A[(int64_t)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      double d = a[k][k];
+      if (!(d > 0.0)) {
+        atomicOr(status, kStatNotSPD);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      a[k][k] = d;
+      rinv[k] = 1.0 / d;
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += 256) a[i][k] *= rinv[k];
+    __syncthreads();
+    const int rem = n - k - 1;
+    for (int idx = tid; idx < rem * rem; idx += 256) {
+      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+      if (j <= i) a[i][j] -= a[i][k] * a[j][k];
+    }
+    __syncthreads();
+  }
+  // inverse of the factor, column j by thread j
+  if (tid < kT) {
+    const int j = tid;
+    for (int i = 0; i < kT; ++i) b[i][j] = 0.0;
+    if (j < n) {
+      b[j][j] = rinv[j];
+      for (int i = j + 1; i < n; ++i) {
+        double s = 0.0;
+        for (int k = j; k < i; ++k) s += a[i][k] * b[k][j];
+        b[i][j] = -s * rinv[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kT * kT; idx += 256) {
+    const int i = idx / kT, j = idx % kT;
+    if (i < n && j < n) A[(int64_t)i * lda + j] = j <= i ? a[i][j] : 0.0;
+    Dinv[i * kT + j] = b[i][j];
+  }
+}
+
+__global__ void copy2d_kernel(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < (int64_t)rows * cols; g += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(g / cols), j = (int)(g % cols);
+    dst[(int64_t)i * ldd + j] = scale * src[(int64_t)i * lds + j];
+  }
+}
+
+// ---------------------------------------------------------------- vectors
+
+__global__ void dot_partial_kernel(const double* x, const double* y, int n, double* part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void dot_final_kernel(const double* part, int np, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[k];
+    *out = t;
+  }
+}
+
+// sc[0] = w.y (current), sc[1] = p.q, sc[2] = w.y (new)
+__global__ void pcg_upd1_kernel(double* lam, double* r, const double* p, const double* q, const double* sc, int n) {
+  const double delta = sc[0] / sc[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    lam[i] += delta * p[i];
+    r[i] -= delta * q[i];
+  }
+}
+
+__global__ void pcg_upd2_kernel(double* p, const double* w, double* sc, int n) {
+  const double beta = sc[2] / sc[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = w[i] + beta * p[i];
+}
+
+__global__ void scalar_copy_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
+
+// r = d - q
+__global__ void sub_kernel(const double* d, const double* q, double* r, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = d[i] - q[i];
+}
+
+// u_i += R_i alpha_i
+__global__ void add_Ralpha_kernel(DevPlan P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
+                                  double* u) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ndof; g += (int64_t)gridDim.x * blockDim.x) {
+    const SubInfo& S = P.sub[dofsub[g]];
+    const int i = (int)(g - S.dof);
+    double s = 0.0;
+    for (int k = 0; k < S.d; ++k) s += R[S.R + (int64_t)k * S.n + i] * alpha[S.alpha0 + k];
+    u[g] += s;
+  }
+}
+
+// z = A c (D x D row-major), warp per row
+__global__ void gemv_kernel(const double* A, const double* c, double* z, int D, double alpha) {
+  const int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / 32; row < D; row += gridDim.x * blockDim.x / 32) {
+    double acc = 0.0;
+    for (int j = lane; j < D; j += 32) acc += A[(int64_t)row * D + j] * c[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[row] = alpha * acc;
+  }
+}
+
+}  // namespace
+
+inline int grid_for(int64_t n, int per = 256, int cap = 152 * 16) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, cap));
+}
+
+size_t implicit_smem(int nmax) { return (size_t)nmax * 8; }
+
+void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
+                     const double* f, double* qi, double* u, int grid, size_t smem, cudaStream_t st) {
+  if (mode == 0) {
+    cudaFuncSetAttribute(implicit_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    implicit_kernel<0><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+  } else if (mode == 1) {
+    cudaFuncSetAttribute(implicit_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    implicit_kernel<1><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+  } else {
+    cudaFuncSetAttribute(implicit_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    implicit_kernel<2><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+  }
+}
+
+int implicit_occupancy(size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(implicit_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, implicit_kernel<0>, kThreads, smem);
+  return std::max(nb, 1);
+}
+
+void launch_gather_minus_c(const int* c0, const int* c1, int nlam, const double* qi, const double* c, double* q,
+                           cudaStream_t st) {
+  gather_minus_c_kernel<<<grid_for(nlam), 256, 0, st>>>(c0, c1, nlam, qi, c, q);
+}
+
+void launch_build_G(const DevPlan& P, const int* colsub, int64_t ncols, const double* R, double* G6,
+                    cudaStream_t st) {
+  build_G_kernel<<<grid_for(ncols), 256, 0, st>>>(P, colsub, ncols, R, G6);
+}
+
+void launch_rtf(const DevPlan& P, int nsub, const double* R, const double* f, double* e, cudaStream_t st) {
+  rtf_kernel<<<grid_for((int64_t)nsub * 6 * 32), 256, 0, st>>>(P, nsub, R, f, e);
+}
+
+void launch_gt(const DevPlan& P, int nsub, const double* G6, const double* x, double* c, cudaStream_t st) {
+  gt_kernel<<<grid_for((int64_t)nsub * 6 * 32), 256, 0, st>>>(P, nsub, G6, x, c);
+}
+
+void launch_gz(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+               const double* x, const double* z, double sgn, double* out, cudaStream_t st) {
+  gz_kernel<<<grid_for(nlam), 256, 0, st>>>(P, colsub, c0, c1, nlam, G6, x, z, sgn, out);
+}
+
+void launch_gtg(const int4* pairs, int npairs, const int2* plist, const double* G6, double* A, int D,
+                cudaStream_t st) {
+  if (npairs > 0) gtg_kernel<<<std::min(npairs, 152 * 32), 64, 0, st>>>(pairs, npairs, plist, G6, A, D);
+}
+
+void launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int ta, const double* B, int ldb,
+                   int tb, double beta, double* C, int ldc, int lower, int ktri, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + kT - 1) / kT, (M + kT - 1) / kT);
+  gemm64_kernel<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, lower, ktri);
+}
+
+void launch_potrf64(double* A, int lda, int n, double* Dinv, int* status, cudaStream_t st) {
+  potrf64_kernel<<<1, 256, 0, st>>>(A, lda, n, Dinv, status);
+}
+
+void launch_copy2d(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale,
+                   cudaStream_t st) {
+  if (rows > 0 && cols > 0)
+    copy2d_kernel<<<grid_for((int64_t)rows * cols), 256, 0, st>>>(src, lds, dst, ldd, rows, cols, scale);
+}
+
+void launch_dot(const double* x, const double* y, int n, double* part, int npart, double* out, cudaStream_t st) {
+  dot_partial_kernel<<<npart, 256, 0, st>>>(x, y, n, part);
+  dot_final_kernel<<<1, 1024, 0, st>>>(part, npart, out);
+}
+
+void launch_pcg_upd1(double* lam, double* r, const double* p, const double* q, const double* sc, int n,
+                     cudaStream_t st) {
+  pcg_upd1_kernel<<<grid_for(n), 256, 0, st>>>(lam, r, p, q, sc, n);
+}
+
+void launch_pcg_upd2(double* p, const double* w, double* sc, int n, cudaStream_t st) {
+  pcg_upd2_kernel<<<grid_for(n), 256, 0, st>>>(p, w, sc, n);
+}
+
+void launch_scalar_copy(double* sc, int dst, int src, cudaStream_t st) { scalar_copy_kernel<<<1, 1, 0, st>>>(sc, dst, src); }
+
+void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st) {
+  sub_kernel<<<grid_for(n), 256, 0, st>>>(d, q, r, n);
+}
+
+void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
+                       double* u, cudaStream_t st) {
+  add_Ralpha_kernel<<<grid_for(ndof), 256, 0, st>>>(P, dofsub, ndof, R, alpha, u);
+}
+
+void launch_gemv(const double* A, const double* c, double* z, int D, double alpha, cudaStream_t st) {
+  if (D > 0) gemv_kernel<<<grid_for((int64_t)D * 32), 256, 0, st>>>(A, c, z, D, alpha);
+}
+
+}  // namespace feti

@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
       }
       const int col = BJ * kM + cc * 32;
       const int bj = col / kT;
-      if (bi < S.nb && bj < S.nb && bj <= bi) {
-        float* dst = F + S.F + (int64_t)(bi * (bi + 1) / 2 + bj) * kT * kT + (row % kT) * kT + (col % kT);
+      if (bi < S.nb && bj < S.nb && bj <= bi && (row % kT) < tile_rows(S.nb, S.vr, bi)) {
+        float* dst = F + S.F + tile_offset(S.nb, S.vr, bi, bj) + (row % kT) * kT + (col % kT);
 #pragma unroll
         for (int e = 0; e < 32; e += 4)
           *reinterpret_cast<float4*>(dst + e) = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),

@@ -64,24 +64,28 @@ __global__ void __launch_bounds__(kThreads) syrk_f64_kernel(DevPlan P, const int
         __syncthreads();
       }
     }
-    double* Ft = F + S.F + (int64_t)t * kT * kT;
+    double* Ft = F + S.F + tile_offset(S.nb, S.vr, bi, bj);
+    const int nrow = tile_rows(S.nb, S.vr, bi);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Ft[(ty + 16 * u) * kT + tx + 16 * v] = acc[u][v];
+      for (int v = 0; v < 4; ++v)
+        if (ty + 16 * u < nrow) Ft[(ty + 16 * u) * kT + tx + 16 * v] = acc[u][v];
   }
 }
 
 // unpack F_i (sorted order) to a dense m x m in B-row order (test helper)
 template <typename TF>
-__global__ void unpack_F_kernel(const TF* Fsub, int m, int nb, const int* colperm, double* out) {
+__global__ void unpack_F_kernel(const TF* Fsub, int m, int nb, int vr, const int* colperm, double* out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < (int64_t)m * m; g += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(g / m), j = (int)(g % m);
-    int bi = i / kT, bj = j / kT;
-    double v;
-    if (bj <= bi) v = (double)Fsub[(int64_t)(bi * (bi + 1) / 2 + bj) * kT * kT + (i % kT) * kT + (j % kT)];
-    else v = (double)Fsub[(int64_t)(bj * (bj + 1) / 2 + bi) * kT * kT + (j % kT) * kT + (i % kT)];
-    out[(int64_t)colperm[i] * m + colperm[j]] = v;
+    if (j / kT > i / kT) {
+      int t = i;
+      i = j;
+      j = t;
+    }
+    const double v = (double)Fsub[tile_offset(nb, vr, i / kT, j / kT) + (i % kT) * kT + (j % kT)];
+    out[(int64_t)colperm[(int)(g / m)] * m + colperm[(int)(g % m)]] = v;
   }
 }
 
@@ -92,12 +96,13 @@ void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const doub
   syrk_f64_kernel<<<grid, kThreads, 0, st>>>(P, items, nitems, X, F);
 }
 
-void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, const int* colperm, double* out, cudaStream_t st) {
+void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, int vr, const int* colperm, double* out,
+                     cudaStream_t st) {
   int64_t tot = (int64_t)m * m;
   int grid = (int)std::min<int64_t>((tot + 255) / 256, 4096);
   if (grid < 1) grid = 1;
-  if (fp32) unpack_F_kernel<float><<<grid, 256, 0, st>>>((const float*)Fsub, m, nb, colperm, out);
-  else unpack_F_kernel<double><<<grid, 256, 0, st>>>((const double*)Fsub, m, nb, colperm, out);
+  if (fp32) unpack_F_kernel<float><<<grid, 256, 0, st>>>((const float*)Fsub, m, nb, vr, colperm, out);
+  else unpack_F_kernel<double><<<grid, 256, 0, st>>>((const double*)Fsub, m, nb, vr, colperm, out);
 }
 
 }  // namespace feti

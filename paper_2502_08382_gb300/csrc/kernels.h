@@ -18,12 +18,43 @@ void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const doub
                      cudaStream_t st);
 size_t apply_tiles_smem(bool fp32);
 void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
-                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int* colsub,
-                  const int* c0, const int* c1, int nlam, double* q, int grid, int* status, cudaStream_t st);
-void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, const int* colperm, double* out, cudaStream_t st);
+                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                  int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int* status,
+                  cudaStream_t st);
+void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, int vr, const int* colperm, double* out,
+                     cudaStream_t st);
 
-// implicit FP64 operator (eq. 11) and the vector kernels of PCPG / eqs. 5-8
-void launch_implicit(const DevPlan& P, const int* order, int nsub, int* queue, const double* p, double* qi,
-                     double* ws, int64_t ws_stride, int grid, size_t smem, cudaStream_t st);
+void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* qi, double* q, cudaStream_t st);
+
+// FP64 solve side: implicit operator (eq. 11), K_reg solves (eqs. 5, 7),
+// coarse problem and projector (eqs. 6-8), PCPG vectors (Algorithm 1)
+size_t implicit_smem(int nmax);
+int implicit_occupancy(size_t smem);
+void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
+                     const double* f, double* qi, double* u, int grid, size_t smem, cudaStream_t st);
+void launch_gather_minus_c(const int* c0, const int* c1, int nlam, const double* qi, const double* c, double* q,
+                           cudaStream_t st);
+void launch_build_G(const DevPlan& P, const int* colsub, int64_t ncols, const double* R, double* G6,
+                    cudaStream_t st);
+void launch_rtf(const DevPlan& P, int nsub, const double* R, const double* f, double* e, cudaStream_t st);
+void launch_gt(const DevPlan& P, int nsub, const double* G6, const double* x, double* c, cudaStream_t st);
+void launch_gz(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+               const double* x, const double* z, double sgn, double* out, cudaStream_t st);
+void launch_gtg(const int4* pairs, int npairs, const int2* plist, const double* G6, double* A, int D,
+                cudaStream_t st);
+void launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int ta, const double* B, int ldb,
+                   int tb, double beta, double* C, int ldc, int lower, int ktri, cudaStream_t st);
+void launch_potrf64(double* A, int lda, int n, double* Dinv, int* status, cudaStream_t st);
+void launch_copy2d(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale,
+                   cudaStream_t st);
+void launch_dot(const double* x, const double* y, int n, double* part, int npart, double* out, cudaStream_t st);
+void launch_pcg_upd1(double* lam, double* r, const double* p, const double* q, const double* sc, int n,
+                     cudaStream_t st);
+void launch_pcg_upd2(double* p, const double* w, double* sc, int n, cudaStream_t st);
+void launch_scalar_copy(double* sc, int dst, int src, cudaStream_t st);
+void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st);
+void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
+                       double* u, cudaStream_t st);
+void launch_gemv(const double* A, const double* c, double* z, int D, double alpha, cudaStream_t st);
 
 }  // namespace feti

@@ -105,3 +105,67 @@ def test_apply_mixed_matches_oracle(torch_cuda, prec):
     qo = O.apply_F(P, Fs, p)
     op.close()
     assert np.linalg.norm(q - qo) <= MIXED_TOL[prec] * np.linalg.norm(qo)
+
+
+# ---------------------------------------------------------------- implicit operator and solve
+
+
+@pytest.mark.parametrize("name", ["cfg1", "heat3d_ragged", "elast3d_2x2x2"])
+def test_implicit_apply_matches_oracle(torch_cuda, name):
+    """FP64 implicit operator B L^-T L^-1 B^T p (eq. 11) against B K_reg^-1 B^T p."""
+    torch = torch_cuda
+    P = CASES[name]()
+    op = _op(P)
+    Fs = [O.local_F(s) for s in P.subs]
+    p = seeded_vector(P.n_lambda, 5)
+    q = op.apply_implicit(torch.from_numpy(p).cuda()).cpu().numpy()
+    qo = O.apply_F(P, Fs, p)
+    op.close()
+    assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+
+
+def _split_u(P, u):
+    out, off = [], 0
+    for s in P.subs:
+        out.append(u[off:off + s.n])
+        off += s.n
+    return out
+
+
+def test_solve_closed_form_poisson(torch_cuda):
+    """Workload 1 solved on the GPU reproduces u = x - x^2/2 (FP64 path)."""
+    P = make_config(1)
+    op = _op(P, tol=1e-12, maxit=1000)
+    lam, alpha, u, info = op.solve()
+    X = P.global_solution_coords()[:, 0]
+    exact = X - X ** 2 / 2
+    us = _split_u(P, u.cpu().numpy())
+    op.close()
+    assert info["converged"], info
+    err = max(np.abs(ui - exact[s.l2g]).max() for s, ui in zip(P.subs, us))
+    assert err <= 1e-10 * 0.5, err
+
+
+@pytest.mark.parametrize("prec,kref", [("fp64", 0), ("split_bf16", 10), ("tf32", 5)])
+@pytest.mark.parametrize("name", ["heat2d_lognormal", "elast3d_small"])
+def test_solve_matches_monolithic(torch_cuda, name, prec, kref):
+    """FETI solution (PCPG + FP64 refinement, alpha, u) against the monolithic
+    FEM solve to 1e-10 relative."""
+    if name == "heat2d_lognormal":
+        P = make_problem(dim=2, physics="heat", cuts=[[6, 7, 5]] * 2, material="lognormal", sigma=1.0, seed=2)
+    else:
+        P = make_problem(dim=3, physics="elasticity", cuts=[[3, 2]] * 3, material="const", seed=0)
+    um = O.monolithic_solve(P)
+    op = _op(P, prec=prec, tol=1e-12, maxit=3000, refine_every=kref)
+    lam, alpha, u, info = op.solve()
+    us = _split_u(P, u.cpu().numpy())
+    # the multipliers keep the solvability condition G^T lambda = e (eq. 4)
+    G = O.G_matrix(P)
+    e = O.e_vector(P)
+    gte = G.T @ lam.cpu().numpy() - e
+    op.close()
+    print(f"{name} {prec}: iterations {info['iterations']} refinements {info['refinements']}")
+    assert info["converged"], info
+    err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P.subs, us))
+    assert err <= 1e-10 * np.abs(um).max(), err
+    assert np.abs(gte).max() <= 1e-10 * max(1.0, np.abs(e).max())
