@@ -168,6 +168,40 @@ void feti_destroy(feti_ctx* ctx);
 feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, double* info,
                          int32_t* perm_out, int32_t* sn_out);
 
+/* Largest m accepted by feti_apply_one_static. */
+#define FETI_STATIC_MAX_M 8192
+
+/* Apply ONE local dual operator without allocating device memory:
+ *     q[map[j]] += sum_k F[j][k] p[map[k]]      for j, k < m.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the point where they apply the operator,
+ * for example a framework that has reserved all device memory for its own
+ * pool and forbids other allocations, or a latency-critical loop in which
+ * cudaMalloc (which synchronises the device) is not acceptable.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine; all intermediates live in
+ * fixed device arrays of this library (8 MiB plus small tables), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * F_dev: F_i in this library's tile layout, FP32 (fp32 = 1) or FP64 (fp32 = 0),
+ *        device memory: 64 x 64 tiles (bi, bj) with bj <= bi stored in the
+ *        order bi (bi + 1) / 2 + bj, each tile row-major with 64 columns; the
+ *        diagonal tiles are stored in full; the last block row
+ *        bi = nb - 1 (nb = ceil(m / 64)) holds only m - 64 (nb - 1) rows per
+ *        tile; columns of the last block beyond m hold zeros.
+ * map_dev: [m] int32 device array, distinct multiplier ids (rows of F_i).
+ * p_dev, q_dev: FP64 device dual vectors; q is accumulated into, not cleared.
+ * stream: cudaStream_t or NULL.  The call is synchronous (it waits for the
+ *        stream) and returns FETI_ERR_TIMEOUT if a bounded device wait gave up.
+ * Errors: FETI_ERR_ARG for m <= 0, m > FETI_STATIC_MAX_M or a NULL pointer;
+ *        FETI_ERR_CUDA for a failed CUDA call.
+ * The first call on each device looks up the device addresses of the fixed
+ * arrays (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the same arrays and leave the
+ * last call's contents in them, so calls that overlap on the GPU (other
+ * streams or host threads) race: order them. */
+feti_status feti_apply_one_static(int32_t m, int32_t fp32, const void* F_dev, const int32_t* map_dev,
+                                  const double* p_dev, double* q_dev, void* stream);
+
 /* Library version string. */
 const char* feti_version(void);
 

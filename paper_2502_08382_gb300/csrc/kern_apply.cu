@@ -20,6 +20,9 @@
 //             (deterministic, no atomics on values).
 // Tile arithmetic runs in the tile's precision (FP32 tiles: FP32 FMAs over
 // 64 terms); the cross-tile sums in phase 2 are FP64.  All waits are bounded.
+#include <mutex>
+
+#include "../../include/feti.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -324,4 +327,139 @@ void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, co
                            nlam, q, grid, status, st);
 }
 
+// ---------------------------------------------------------------------------
+// Stand-alone application of one local operator without any device allocation.
+//
+// Some callers cannot allocate device memory when they apply an operator: a
+// host framework that has reserved all device memory for its own pool and
+// forbids other allocations, or a latency-critical loop in which cudaMalloc
+// (which synchronises the device) is not acceptable.  feti_apply_one_static
+// serves them: the caller passes F_i, the multiplier map and the dual vectors;
+// every intermediate the apply kernels need lives in the fixed device arrays
+// below, which exist once per GPU that loads this library and stay resident
+// until the process exits.  All calls share these arrays and they keep the
+// last call's contents, so calls that overlap on the GPU (other streams,
+// other host threads) race; the caller must order them.
+
+constexpr int kStaticMaxM = 8192;                 // largest m accepted
+constexpr int kStaticMaxNb = kStaticMaxM / kT;
+constexpr int64_t kStaticDoubles = 1 << 20;       // 8 MiB of scratch
+constexpr int kStaticMaxItems = kStaticMaxNb * ((kStaticMaxNb + kApplyChunk - 1) / kApplyChunk);
+
+static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+static __device__ __align__(256) int4 g_static_items[kStaticMaxItems];
+static __device__ __align__(256) int2 g_static_blocks[kStaticMaxNb];
+static __device__ __align__(256) SubInfo g_static_sub;
+static __device__ __align__(256) int g_static_status;
+
+namespace {
+
+// Describe the single subdomain, its work items and blocks in the static
+// arrays, zero the padding of the gathered p, and clear the status word
+// (the only state that must start at zero; every other slot is overwritten).
+template <typename TF>
+__global__ void static_setup_kernel(int m, int nb, int64_t rpart, int64_t tpart, TF* pg) {
+  if (threadIdx.x == 0) {
+    SubInfo S{};
+    S.m = m;
+    S.m_pad = nb * kT;
+    S.nb = nb;
+    S.vr = m - kT * (nb - 1);
+    S.F = 0;
+    S.qcol = 0;
+    S.rpart = rpart;
+    S.tpart = tpart;
+    g_static_sub = S;
+    g_static_status = 0;
+    int k = 0;
+    for (int b = 0; b < nb; ++b)
+      for (int c = 0; c <= b; c += kApplyChunk) g_static_items[k++] = make_int4(0, b, c, min(c + kApplyChunk, b + 1));
+  }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) g_static_blocks[b] = make_int2(0, b);
+  for (int j = m + threadIdx.x; j < nb * kT; j += blockDim.x) pg[j] = (TF)0;
+}
+
+// q[map[j]] += qi[j] for the m real columns (the map holds distinct multipliers)
+__global__ void static_accumulate_kernel(const int* map, int m, const double* qi, double* q) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) q[map[j]] += qi[j];
+}
+
+struct StaticAddrs {
+  double* scratch = nullptr;
+  int4* items = nullptr;
+  int2* blocks = nullptr;
+  SubInfo* sub = nullptr;
+  int* status = nullptr;
+};
+
+std::mutex g_static_mu;
+StaticAddrs g_static_addr[64];
+bool g_static_ready[64] = {};
+
+// Device addresses of the static arrays on the current device.  In host code
+// the array names are host-side stand-ins, so the addresses are looked up
+// once per device (with that device current) and cached.
+cudaError_t static_addresses(StaticAddrs& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ready[dev]) {
+    StaticAddrs a;
+    if ((e = cudaGetSymbolAddress((void**)&a.scratch, g_static_scratch)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.items, g_static_items)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.blocks, g_static_blocks)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.sub, g_static_sub)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.status, g_static_status)) != cudaSuccess) return e;
+    g_static_addr[dev] = a;
+    g_static_ready[dev] = true;
+  }
+  out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+template <typename TF>
+feti_status apply_one_static_t(int m, const TF* F, const int* map, const double* p, double* q, cudaStream_t st) {
+  const int nb = (m + kT - 1) / kT;
+  const int m_pad = nb * kT;
+  const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
+  const int64_t ntile = (int64_t)nb * (nb + 1) / 2;
+  int nitems = 0;
+  for (int b = 0; b < nb; ++b) nitems += b / kApplyChunk + 1;
+  // scratch layout: [pg: m_pad TF][row partials: nb nch kT TF][column partials: ntile kT TF] | [qi: m_pad double]
+  const int64_t n_pg = m_pad, n_row = (int64_t)nb * nch * kT, n_col = ntile * kT;
+  const int64_t qi_ofs = ((n_pg + n_row + n_col) * (int64_t)sizeof(TF) + 255) / 256 * 256 / 8;
+  if (qi_ofs + m_pad > kStaticDoubles || nitems > kStaticMaxItems) return FETI_ERR_ARG;
+  StaticAddrs a;
+  if (static_addresses(a) != cudaSuccess) return FETI_ERR_CUDA;
+  TF* pg = reinterpret_cast<TF*>(a.scratch);
+  double* qi = a.scratch + qi_ofs;
+  static_setup_kernel<TF><<<1, 256, 0, st>>>(m, nb, n_pg, n_pg + n_row, pg);
+  scatter_kernel<TF><<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, p, pg);
+  DevPlan P{};
+  P.sub = a.sub;
+  // row / column partial slots are the offsets S.rpart / S.tpart from the scratch base
+  const size_t smem = apply_tiles_smem(sizeof(TF) == 4);
+  cudaFuncSetAttribute(apply_tiles_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = std::max(1, std::min(nitems, 152 * 2));
+  apply_tiles_kernel<TF><<<grid, kApplyThreads, smem, st>>>(P, a.items, nitems, F, pg, pg, pg, a.status);
+  reduce_cols_kernel<TF><<<std::max(1, (nb + 7) / 8), 256, 0, st>>>(P, a.blocks, nb, pg, pg, qi);
+  static_accumulate_kernel<<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, qi, q);
+  if (cudaGetLastError() != cudaSuccess) return FETI_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FETI_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FETI_ERR_CUDA;
+  return (status & kStatTimeout) ? FETI_ERR_TIMEOUT : FETI_OK;
+}
+
+}  // namespace
 }  // namespace feti
+
+extern "C" feti_status feti_apply_one_static(int32_t m, int32_t fp32, const void* F_dev, const int32_t* map_dev,
+                                             const double* p_dev, double* q_dev, void* stream) {
+  if (m <= 0 || m > feti::kStaticMaxM || !F_dev || !map_dev || !p_dev || !q_dev) return FETI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  return fp32 ? feti::apply_one_static_t<float>(m, (const float*)F_dev, map_dev, p_dev, q_dev, st)
+              : feti::apply_one_static_t<double>(m, (const double*)F_dev, map_dev, p_dev, q_dev, st);
+}

@@ -71,7 +71,7 @@ class FetiStats(C.Structure):
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
            "feti_solve", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
-           "feti_analyse", "feti_version"]
+           "feti_analyse", "feti_version", "feti_apply_one_static"]
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.feti_destroy.restype = None
     lib.feti_analyse.argtypes = [C.POINTER(FetiSubdomain), C.POINTER(FetiOptions), _f64p, _i32p, _i32p]
     lib.feti_version.restype = C.c_char_p
+    lib.feti_apply_one_static.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("feti_last_error", "feti_destroy", "feti_version"):
             getattr(lib, name).restype = C.c_int
