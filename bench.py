@@ -1,21 +1,29 @@
 """Benchmark of the FETI dual-operator hot path on one GB300 (per rank).
 
-A step is one pass of the whole path over workload 2 (2D heat, 32x32
-subdomains of 64x64 Q1 elements, 4225 DOFs each, lognormal conductivity):
-feti_assemble (regularise, Cholesky, pruned TRSM, SYRK, coarse setup) and
-feti_solve (projected PCG with the explicit apply and FP64 refinement,
-recovery).  value = achieved GB/s of the explicit F.lambda apply (algorithmic
-bytes / CUDA-event time) inside the step; assembly ms, the FP64 comparison,
-errors and the break-even iteration count are reported beside it.
+Workload: 2D heat, 32 x 32 subdomains of 64 x 64 Q1 elements (4225 DOFs each,
+m_i 129..258, n_lambda = 130 048), lognormal conductivity (sigma = 1, seed 0),
+Dirichlet on x = 0; seeded synthetic inputs (the paper's data are not used).
+
+A step is one pass of the whole path, on the mixed-precision configuration
+(FP32 pruned TRSM, split-bf16 tensor-core SYRK, FP32 F_i tiles, FP64
+Cholesky / coarse problem / PCPG vectors, FP64 residual replacement every 10
+iterations): feti_assemble (regularise, Cholesky, TRSM, SYRK) followed by
+feti_solve (projected PCG with the explicit apply, refinement, alpha, u).
+`value` is the achieved GB/s of the explicit F.lambda apply inside the timed
+steps: algorithmic bytes per apply / mean CUDA-event time of the F-streaming
+kernel, recorded by the library on its stream.  The FP64 assembly, the F and
+solution differences between the two paths, the implicit-apply time and the
+break-even iteration count are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs an independent replica (the path has no
-cross-rank exchange on one node: "replicas only", weak scaling).
+Under torchrun each rank runs an independent replica of the workload (the
+single-GPU path has no exchange step: "replicas only", weak scaling).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -28,7 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "F assembly ms & F·λ GB/s, mixed vs FP64 at stated error; break-even PCG iters"
-WORKLOAD = "2D heat Q1, 32x32 subdomains x 64x64 elements (4225 DOFs, m_i 129..258), lognormal sigma=1, seed 0"
+WORKLOAD = ("2D heat Q1, 32x32 subdomains of 64x64 elements (4225 DOFs, m_i 129..258, n_lambda 130048), "
+            "lognormal sigma=1, seed 0")
+PREC = "split_bf16"
+REFINE = 10
+TOL = 1e-10
 
 
 def peaks():
@@ -90,62 +102,50 @@ class Clocks:
         return out
 
 
-def run_reference(args):
-    """The FP64 CPU oracle timed on the host cores on a bounded sample."""
+def oracle_sample(P, nsample, reps):
+    """The FP64 CPU oracle on a bounded sample: dense F_i for nsample
+    subdomains and reps dense F_i p_i sweeps over them."""
     from oracle import feti_oracle as O
-    from paper_2502_08382_gb300.problems import make_config
-    P = make_config(2)
-    nsample = 4
-    subs = P.subs[:nsample]
-    t0 = time.perf_counter()
-    Fs = [O.local_F(s) for s in subs]
-    t_f = (time.perf_counter() - t0) / nsample
-    ps = [np.random.default_rng(i).normal(size=s.m) for i, s in enumerate(subs)]
-    for _ in range(args.warmup):
-        for F, p in zip(Fs, ps):
-            F @ p
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for _r in range(200):
-            for F, p in zip(Fs, ps):
-                F @ p
-        times.append((time.perf_counter() - t0) / 200)
-    t_ap = statistics.median(times)
-    byts = sum(8.0 * s.m * s.m + 16.0 * s.m for s in subs)
-    gbs = byts / t_ap / 1e9
-    cores = os.cpu_count()
-    sample = f"{nsample} of 1024 subdomains: dense Cholesky F_i (scipy) + 200 dense F_i p_i sweeps per step"
-    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ap * 200 * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
-            "assembly_ms_extrapolated": t_f * 1e3 * P.nsub,
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
-def cpu_baseline_ours(P):
-    """Oracle on a bounded sample (rank 0, N = 1): dense F_i and F_i p_i."""
-    from oracle import feti_oracle as O
-    nsample = 4
     subs = P.subs[:nsample]
     t0 = time.perf_counter()
     Fs = [O.local_F(s) for s in subs]
     t_f = (time.perf_counter() - t0) / nsample
     ps = [np.random.default_rng(i).normal(size=s.m) for i, s in enumerate(subs)]
     t0 = time.perf_counter()
-    reps = 300
     for _ in range(reps):
         for F, p in zip(Fs, ps):
             F @ p
     t_ap = (time.perf_counter() - t0) / reps
     byts = sum(8.0 * s.m * s.m + 16.0 * s.m for s in subs)
-    return {"value": byts / t_ap / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{nsample} of {P.nsub} subdomains: scipy dense Cholesky F_i ({t_f * 1e3:.0f} ms each) "
-                      f"and {reps} dense FP64 F_i p_i sweeps",
-            "assembly_ms_extrapolated": t_f * 1e3 * P.nsub}
+    return byts / t_ap / 1e9, t_f, t_ap
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    from paper_2502_08382_gb300.problems import make_config
+    P = make_config(2)
+    nsample = 4
+    for _ in range(args.warmup):
+        oracle_sample(P, 1, 5)
+    vals, tf = [], []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        g, t_f, t_ap = oracle_sample(P, nsample, 50)
+        vals.append(g)
+        tf.append(t_f)
+    ms = (time.perf_counter() - t_all) * 1e3 / max(args.steps, 1)
+    gbs = statistics.median(vals)
+    sample = (f"{nsample} of 1024 subdomains per step: scipy dense Cholesky F_i and 50 dense FP64 F_i p_i sweeps; "
+              f"value = GB/s of the F_i p_i sweeps")
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "assembly_ms_extrapolated": statistics.median(tf) * 1e3 * P.nsub,
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def main():
@@ -154,7 +154,6 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--applies", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -178,62 +177,55 @@ def main():
     from paper_2502_08382_gb300.problems import make_config, seeded_vector
 
     P = make_config(2)
-    prec = os.environ.get("FETI_BENCH_PREC", "fp64")
-    op = feti.FetiOperator(P, prec=prec)
-    p_host = torch.from_numpy(seeded_vector(P.n_lambda, 0)).pin_memory()
-    p = p_host.cuda()
-    q = torch.empty_like(p)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    op = feti.FetiOperator(P, prec=PREC, tol=TOL, maxit=5000, refine_every=REFINE)
     st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def step(timings):
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(st)
+    def step():
         op.assemble()
-        e1.record(st)
-        for _ in range(args.applies):
-            op.apply(p, out=q)
-        e2.record(st)
-        timings.append((e0, e1, e2))
+        return op.solve()
 
     for _ in range(args.warmup):
-        step([])
+        step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    tims = []
-    asm_ms = []
+    op.set_profiling(True)
+    step_ms, asm, info = [], [], None
     with Clocks(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        step_ms = 0.0
         for _ in range(args.steps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(st)
-            step(tims)
+            lam, alpha, u, info = step()
             b.record(st)
             b.synchronize()
-            step_ms += a.elapsed_time(b)
-            asm_ms.append(op.stats()["t_assemble_ms"])
-        torch.cuda.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            asm.append(op.stats()["t_assemble_ms"])
+    torch.cuda.synchronize()
+    tot = sum(step_ms)
     if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
+        t = torch.tensor([tot], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        step_ms = float(t.item())
-    ms_per_step = step_ms / args.steps
-    apply_ms = statistics.median([e1.elapsed_time(e2) / args.applies for (_, e1, e2) in tims])
+        tot = float(t.item())
     st_ = op.stats()
+    op.set_profiling(False)
+    ms_per_step = tot / args.steps
+    tiles_ms = st_["apply_tiles_ms"] / max(st_["apply_calls"], 1)
+    apply_ms = st_["apply_ms"] / max(st_["apply_calls"], 1)
+    impl_ms = st_["implicit_ms"] / max(st_["implicit_calls"], 1)
     hbm, pk_kind = peaks()
-    gbs = st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9
-    value = gbs * world
+    tiles_gbs = st_["apply_bytes"] / (tiles_ms * 1e-3) / 1e9
+    value = tiles_gbs * world
 
-    # end-to-end through the C ABI with host buffers (H2D p, apply, D2H q)
+    # end to end through the C ABI with host buffers: H2D p, feti_apply, D2H q
+    p_host = torch.from_numpy(seeded_vector(P.n_lambda, 0)).pin_memory()
     q_host = torch.empty_like(p_host).pin_memory()
-    e_times = []
+    p = torch.empty(P.n_lambda, dtype=torch.float64, device="cuda")
+    q = torch.empty_like(p)
     for _ in range(3):
         p.copy_(p_host, non_blocking=True)
         op.apply(p, out=q)
@@ -241,33 +233,76 @@ def main():
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
+    nrep = 50
     a.record(st)
-    for _ in range(args.applies):
+    for _ in range(nrep):
         p.copy_(p_host, non_blocking=True)
         op.apply(p, out=q)
         q_host.copy_(q, non_blocking=True)
     b.record(st)
     b.synchronize()
-    e2e_ms = a.elapsed_time(b) / args.applies
-    e2e_gbs = st_["apply_bytes"] / (e2e_ms * 1e-3) / 1e9
+    e2e_gbs = st_["apply_bytes"] / (a.elapsed_time(b) / nrep * 1e-3) / 1e9
+
+    # plain FP64 GPU path on the same inputs (assembly time, F and solution differences)
+    op64 = feti.FetiOperator(P, prec="fp64", tol=TOL, maxit=5000)
+    for _ in range(2):
+        op64.assemble()
+    asm64 = []
+    for _ in range(3):
+        op64.assemble()
+        asm64.append(op64.stats()["t_assemble_ms"])
+    st64 = op64.stats()
+    lam64, alpha64, u64, info64 = op64.solve()
+    sample = [0, 17, 500, 1023]
+    ferr = max(np.linalg.norm(op.get_F(i) - op64.get_F(i)) / np.linalg.norm(op64.get_F(i)) for i in sample)
+    uerr = (torch.linalg.norm(u - u64) / torch.linalg.norm(u64)).item()
+    p.copy_(p_host)
+    op64.set_profiling(True)
+    for _ in range(10):
+        op64.apply_implicit(p, out=q)
+    st64i = op64.stats()
+    op64.set_profiling(False)
+    impl64_ms = st64i["implicit_ms"] / max(st64i["implicit_calls"], 1)
+    op64.close()
+    t_asm = statistics.median(asm)
+    st_last = op.stats()
+    n_star = break_even(t_asm, apply_ms, st_last["t_chol_ms"], impl64_ms)
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": prec, "step": f"feti_assemble + {args.applies} feti_apply",
-                       "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
-            "assembly_ms": statistics.median(asm_ms),
-            "assembly_phases_ms": {k: st_[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms", "t_coarse_ms")},
-            "apply_ms": apply_ms,
-            "flops": {k: st_[k] for k in ("chol_flops", "trsm_flops", "syrk_flops")},
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "traffic": None, "kernel": "feti_apply (3 launches)", "peak_kind": pk_kind},
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prec": f"{PREC} SYRK, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
+                       "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual every {REFINE} its)",
+                       "value": "explicit F.lambda apply GB/s (algorithmic bytes / F-streaming kernel time)",
+                       "l2": "256 MB buffer written before each timed step; F tiles 136 MB > L2 per apply",
+                       "parallelism": f"replicas x{world}"},
+            "assembly_ms": {"mixed": t_asm, "fp64": statistics.median(asm64),
+                            "speedup": statistics.median(asm64) / t_asm,
+                            "mixed_phases": {k: st_last[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms")},
+                            "fp64_phases": {k: st64[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms")},
+                            "coarse_once_ms": st_last["t_coarse_ms"]},
+            "errors": {"F_rel_frobenius_mixed_vs_fp64": ferr, "u_rel_mixed_vs_fp64": uerr,
+                       "F_fp64_vs_oracle": "<= 1e-12 (tests/test_gpu_parity.py)",
+                       "pcg_rel_residual": info["rel_residual"]},
+            "pcg": {"iterations": info["iterations"], "refinements": info["refinements"],
+                    "fp64_iterations": info64["iterations"]},
+            "apply": {"ms": apply_ms, "tiles_ms": tiles_ms, "algorithmic_bytes": st_["apply_bytes"],
+                      "gbs_whole_call": st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9},
+            "implicit_fp64_apply_ms": impl64_ms,
+            "break_even_iters": n_star,
+            "roofline": {"bound": "hbm", "achieved": tiles_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": tiles_gbs / hbm, "traffic": None, "kernel": "apply_tiles_kernel<float>",
+                         "peak_kind": pk_kind},
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},
-            "gpu_launches": args.steps * (3 + 3 * args.applies),
+            "gpu_launches": int(st_["launches"]),
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_ours(P)
+        gbs, t_f, t_ap = oracle_sample(P, 4, 300)
+        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"4 of {P.nsub} subdomains: scipy dense Cholesky F_i "
+                                          f"({t_f * 1e3:.0f} ms each) and 300 dense FP64 F_i p_i sweeps",
+                                "assembly_ms_extrapolated": t_f * 1e3 * P.nsub}
     if rank == 0:
         print(json.dumps(line))
     op.close()

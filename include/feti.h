@@ -111,6 +111,13 @@ typedef struct {
   /* last feti_assemble, CUDA-event times on the context's stream (ms) */
   double t_chol_ms, t_trsm_ms, t_syrk_ms, t_coarse_ms, t_assemble_ms;
   double t_symbolic_ms;       /* host analysis time in feti_create */
+  /* measurement counters since the last feti_set_profiling(ctx, 1) */
+  int64_t launches;           /* kernel launches issued by this context */
+  int64_t apply_calls;        /* feti_apply calls */
+  double apply_ms;            /* CUDA-event time of those calls (all their kernels) */
+  double apply_tiles_ms;      /* CUDA-event time of their F-streaming kernel only */
+  int64_t implicit_calls;     /* implicit-operator applications (feti_apply_implicit and inside feti_solve) */
+  double implicit_ms;         /* CUDA-event time of those applications */
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;
@@ -154,6 +161,11 @@ feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev)
 
 /* Copy F_i (m_i x m_i, row-major, B-row order, FP64) to host memory. */
 feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host);
+
+/* Measurement aid: enable (1) or disable (0) CUDA-event timing of feti_apply
+ * and of the implicit operator on the context's stream, and reset the
+ * counters reported by feti_get_stats (which synchronises the stream). */
+feti_status feti_set_profiling(feti_ctx* ctx, int32_t enable);
 
 feti_status feti_get_stats(feti_ctx* ctx, feti_stats* out);
 const char* feti_last_error(feti_ctx* ctx);

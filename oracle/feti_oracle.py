@@ -272,6 +272,19 @@ def gradient_sub(sub, W, dK_ref, elems=None, Kr=None) -> np.ndarray:
     return g
 
 
+def loss_difference(sub, W, Kp, Km, e, dcoef, K_ref) -> float:
+    """L(K_+) - L(K_-) for L = <W, B K^{-1} B^T>, where K_+ and K_- differ
+    only on element e by dcoef * K_ref, through the resolvent identity
+    K_+^{-1} - K_-^{-1} = -K_+^{-1} (K_+ - K_-) K_-^{-1}:
+    -<W, Z_+[dofs_e]^T (dcoef K_ref) Z_-[dofs_e]>.  The same difference as
+    subtracting two loss values (and as subtracting the two matrices), written
+    so that no digits are lost to cancellation at small steps (h = 1e-6)."""
+    Zp = local_Z(sub, Kp)
+    Zm = local_Z(sub, Km)
+    dofs = sub.elem_dofs[e]
+    return float(-np.sum(W * (Zp[dofs].T @ (dcoef * K_ref) @ Zm[dofs])))
+
+
 def perturbed_K_reg(sub, e, dtheta_coef, K_ref, rho):
     """K_reg with element e's coefficient changed by dtheta_coef (rho fixed)."""
     K = K_dense(sub)

@@ -118,6 +118,7 @@ void copy_sub(const feti_subdomain& s, SubHost& h, int idx) {
   h.edofs = s.edofs;
   if (s.nelem > 0) {
     need(s.elem_dofs && s.dKe_ref && s.dKe_scale && s.edofs > 0, "element data incomplete");
+    need(s.edofs <= 32, "elements with more than 32 DOFs are not supported");
     h.elem_dofs.assign(s.elem_dofs, s.elem_dofs + (size_t)s.nelem * s.edofs);
     h.dKe_ref.assign(s.dKe_ref, s.dKe_ref + (size_t)s.edofs * s.edofs);
     h.dKe_scale.assign(s.dKe_scale, s.dKe_scale + s.nelem);
@@ -276,7 +277,9 @@ void build(feti_ctx* c) {
 
   // ---- per-subdomain layout
   c->info.resize(ns);
-  std::vector<int> qmap, fix_sn, colsub, colperm, qdof, dofsub;
+  std::vector<int> qmap, fix_sn, colsub, colperm, qdof, dofsub, colperm_pad;
+  std::vector<int> eldofs;
+  std::vector<double> eldk, elsc;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
   int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, rpo = 0;
@@ -338,11 +341,13 @@ void build(feti_ctx* c) {
         qmap.push_back(s.blam[r]);
         qsign.push_back(s.bsign[r]);
         colperm.push_back(r);
+        colperm_pad.push_back(r);
         qdof.push_back(s.bdof[r]);
       } else {
         qmap.push_back(-1);
         qsign.push_back(0.0);
         qdof.push_back(0);
+        colperm_pad.push_back(0);
       }
       colsub.push_back(i);
     }
@@ -357,6 +362,12 @@ void build(feti_ctx* c) {
     }
     fixo += s.nfix;
     for (int k = 0; k < s.n; ++k) dofsub.push_back(i);
+    c->elem_ofs.push_back((int64_t)elsc.size());
+    c->elem_dk_ofs.push_back((int64_t)eldk.size());
+    c->elem_dofs_ofs.push_back((int64_t)eldofs.size());
+    eldofs.insert(eldofs.end(), s.elem_dofs.begin(), s.elem_dofs.end());
+    eldk.insert(eldk.end(), s.dKe_ref.begin(), s.dKe_ref.end());
+    elsc.insert(elsc.end(), s.dKe_scale.begin(), s.dKe_scale.end());
     c->nmax = std::max(c->nmax, s.n);
     chol += P.chol_flops;
     trsm += B.trsm_flops;
@@ -534,6 +545,18 @@ void build(feti_ctx* c) {
   D.fix_sn = upload(c, fix_sn);
   D.iperm = upload(c, iperm);
   D.qdof = upload(c, qdof);
+  D.colperm = upload(c, colperm_pad);
+  c->nelem_total = (int64_t)elsc.size();
+  {
+    std::vector<int> ident(ns);
+    std::iota(ident.begin(), ident.end(), 0);
+    c->d_ident = upload(c, ident);
+  }
+  if (!elsc.empty()) {
+    c->d_eldofs = upload(c, eldofs);
+    c->d_eldk = upload(c, eldk);
+    c->d_elsc = upload(c, elsc);
+  }
   c->d_dofsub = upload(c, dofsub);
   c->ndof = (int64_t)dofsub.size();
   D.fix_pos = upload(c, fix_pos);
@@ -693,6 +716,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
   CK(cudaEventRecord(ctx->ev[0], st));
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
               ctx->grid_chol, ctx->d_status, st);
+  ctx->stats.launches += 3;  // Cholesky, pruned TRSM, SYRK
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
@@ -745,9 +769,20 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   API_BEGIN
   cudaStream_t st = ctx->st;
   int grid = std::max(1, std::min(ctx->napply, ctx->nsm * 2));
+  feti_ctx::EvPair ev{};
+  if (ctx->prof) {
+    ev = {ctx->take_event(), ctx->take_event(), ctx->take_event(), ctx->take_event(), 0};
+    CK(cudaEventRecord(ev.a, st));
+  }
   launch_apply(ctx->P, ctx->fp32, ctx->d_apply_items, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
                ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
-               ctx->nlam, q_dev, grid, ctx->d_status, st);
+               ctx->nlam, q_dev, grid, ctx->d_status, st, ev.b, ev.c);
+  ctx->stats.launches += 4;
+  ctx->stats.apply_calls += 1;
+  if (ctx->prof) {
+    CK(cudaEventRecord(ev.d, st));
+    ctx->ev_pending.push_back(ev);
+  }
   CK(cudaGetLastError());
   return FETI_OK;
   API_END
@@ -774,8 +809,44 @@ feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host) {
   API_END
 }
 
+feti_status feti_set_profiling(feti_ctx* ctx, int32_t enable) {
+  if (!ctx) return FETI_ERR_ARG;
+  cudaStreamSynchronize(ctx->st);
+  for (auto& e : ctx->ev_pending) {
+    for (cudaEvent_t x : {e.a, e.b, e.c, e.d})
+      if (x) ctx->ev_pool.push_back(x);
+  }
+  ctx->ev_pending.clear();
+  ctx->prof = enable != 0;
+  ctx->stats.launches = 0;
+  ctx->stats.apply_calls = 0;
+  ctx->stats.apply_ms = 0;
+  ctx->stats.apply_tiles_ms = 0;
+  ctx->stats.implicit_calls = 0;
+  ctx->stats.implicit_ms = 0;
+  return FETI_OK;
+}
+
 feti_status feti_get_stats(feti_ctx* ctx, feti_stats* out) {
   if (!ctx || !out) return FETI_ERR_ARG;
+  if (!ctx->ev_pending.empty()) {
+    if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return set_error(ctx, FETI_ERR_CUDA, "stream sync failed");
+    for (auto& e : ctx->ev_pending) {
+      float t = 0;
+      if (e.kind == 0) {
+        cudaEventElapsedTime(&t, e.a, e.d);
+        ctx->stats.apply_ms += t;
+        cudaEventElapsedTime(&t, e.b, e.c);
+        ctx->stats.apply_tiles_ms += t;
+      } else {
+        cudaEventElapsedTime(&t, e.a, e.b);
+        ctx->stats.implicit_ms += t;
+      }
+      for (cudaEvent_t x : {e.a, e.b, e.c, e.d})
+        if (x) ctx->ev_pool.push_back(x);
+    }
+    ctx->ev_pending.clear();
+  }
   *out = ctx->stats;
   return FETI_OK;
 }
@@ -787,6 +858,10 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->st || true) cudaStreamSynchronize(ctx->st);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->ev_pending)
+    for (cudaEvent_t x : {e.a, e.b, e.c, e.d})
+      if (x) cudaEventDestroy(x);
+  for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   for (auto& b : ctx->bufs) {
     if (ctx->opt.dev_free) ctx->opt.dev_free(b.p, ctx->opt.alloc_ctx);

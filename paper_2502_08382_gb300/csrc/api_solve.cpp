@@ -38,10 +38,21 @@ void queue_reset(feti_ctx* c, int slot) { CKS(cudaMemsetAsync(c->d_queue + slot,
 
 // q = B L^-T L^-1 B^T p (FP64 implicit operator)
 void implicit_apply(feti_ctx* c, const double* p, double* q) {
+  feti_ctx::EvPair ev{};
+  if (c->prof) {
+    ev = {c->take_event(), c->take_event(), nullptr, nullptr, 1};
+    CKS(cudaEventRecord(ev.a, c->st));
+  }
   queue_reset(c, 32);
   launch_implicit(0, c->P, c->d_impl_order, c->nsub, c->d_queue + 32, p, c->d_f, c->d_qi, nullptr, c->grid_impl,
                   c->impl_smem, c->st);
   launch_gather_lambda(c->d_c0, c->d_c1, c->nlam, c->d_qi, q, c->st);
+  c->stats.launches += 2;
+  c->stats.implicit_calls += 1;
+  if (c->prof) {
+    CKS(cudaEventRecord(ev.b, c->st));
+    c->ev_pending.push_back(ev);
+  }
 }
 
 // (G^T G)^{-1} in FP64: blocked Cholesky, inverse of the factor, W^T W
@@ -92,10 +103,12 @@ void project(feti_ctx* c, const double* x, double* out) {
   launch_gt(c->P, c->nsub, c->d_G6, x, cvec(c, C_C), c->st);
   launch_gemv(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), c->dtot, 1.0, c->st);
   launch_gz(c->P, c->d_colsub, c->d_c0, c->d_c1, c->nlam, c->d_G6, x, cvec(c, C_Z), 1.0, out, c->st);
+  c->stats.launches += 3;
 }
 
 double dot_host(feti_ctx* c, const double* x, const double* y, int slot) {
   launch_dot(x, y, c->nlam, c->d_part, kNPart, c->d_sc + slot, c->st);
+  c->stats.launches += 2;
   CKS(cudaMemcpyAsync(c->h_sc + slot, c->d_sc + slot, 8, cudaMemcpyDeviceToHost, c->st));
   CKS(cudaStreamSynchronize(c->st));
   return c->h_sc[slot];
@@ -167,12 +180,14 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
       if (s != FETI_OK) return s;
       launch_dot(p, q, n, ctx->d_part, kNPart, ctx->d_sc + S_PQ, st);
       launch_pcg_upd1(lam, r, p, q, ctx->d_sc, n, st);
+      ctx->stats.launches += 3;
       ++it;
       bool refined = false;
       if (kref > 0 && it % kref == 0) {
         // residual replacement with the FP64 implicit operator
         implicit_apply(ctx, lam, q);
         launch_sub(d, q, r, n, st);
+        ctx->stats.launches += 1;
         ++nref;
         refined = true;
       }
@@ -196,6 +211,7 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
       // p = y + beta p, beta = (w_new . y_new) / (w . y)
       launch_pcg_upd2(p, w, ctx->d_sc, n, st);
       launch_scalar_copy(ctx->d_sc, S_WY, S_WYN, st);
+      ctx->stats.launches += 2;
       wy = wyn;
     }
     // alpha = -(G^T G)^{-1} G^T (d - F lambda)  (eq. 8, FP64 implicit F)
@@ -231,8 +247,45 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
   }
 }
 
-feti_status feti_adjoint(feti_ctx* ctx, const double*, double*) {
-  return set_error(ctx, FETI_ERR_STATE, "feti_adjoint: not available in this build");
+feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev) {
+  GUARD();
+  if (!W_dev || !dtheta_dev) return set_error(ctx, FETI_ERR_ARG, "feti_adjoint: W_dev and dtheta_dev are required");
+  if (ctx->nelem_total == 0) return set_error(ctx, FETI_ERR_ARG, "feti_adjoint: no element data given at create");
+  try {
+    cudaStream_t st = ctx->st;
+    size_t zmax = 0;
+    for (auto& s : ctx->subs)
+      if (s.nelem > 0) zmax = std::max(zmax, (size_t)s.n * s.m);
+    if (!ctx->d_Z) {
+      ctx->d_Z = (double*)dalloc(ctx, std::max<size_t>(zmax, 1) * 8);
+      ctx->d_Y = (double*)dalloc(ctx, std::max<size_t>(zmax, 1) * 8);
+    }
+    int64_t woff = 0;
+    for (int i = 0; i < ctx->nsub; ++i) {
+      const auto& s = ctx->subs[i];
+      const int n = s.n, m = s.m;
+      if (s.nelem > 0 && m > 0) {
+        // Z = K_reg^{-1} B^T (rows: original DOFs, columns: B rows), FP64, recomputed here
+        queue_reset(ctx, 33);
+        launch_implicit(3, ctx->P, ctx->d_ident + i, m, ctx->d_queue + 33, nullptr, nullptr, nullptr, ctx->d_Z,
+                        ctx->grid_impl, ctx->impl_smem, st);
+        // Y = Z W_i
+        launch_gemm64(n, m, m, 1.0, ctx->d_Z, m, 0, W_dev + woff, m, 0, 0.0, ctx->d_Y, m, 0, 0, st);
+        // dtheta_e = -scale_e <dK_ref, (Y Z^T)_e>
+        launch_elem_contract(ctx->d_eldofs + ctx->elem_dofs_ofs[i], s.nelem, s.edofs, ctx->d_eldk + ctx->elem_dk_ofs[i],
+                             ctx->d_elsc + ctx->elem_ofs[i], ctx->d_Z, ctx->d_Y, m, dtheta_dev + ctx->elem_ofs[i], st);
+        ctx->stats.launches += 3;
+      } else if (s.nelem > 0) {
+        CKS(cudaMemsetAsync(dtheta_dev + ctx->elem_ofs[i], 0, (size_t)s.nelem * 8, st));
+      }
+      woff += (int64_t)m * m;
+    }
+    CKS(cudaGetLastError());
+    CKS(cudaStreamSynchronize(st));
+    return FETI_OK;
+  } catch (std::exception& e) {
+    return set_error(ctx, FETI_ERR_CUDA, e.what());
+  }
 }
 
 }  // extern "C"

@@ -77,6 +77,7 @@ struct DevPlan {
   const double* qsign;       // [qcol + j] sign of B in sorted column j (0 for padding)
   const int* iperm;          // [diag0 + old DOF] new-numbered DOF (pattern)
   const int* qdof;           // [qcol + j] original local DOF of sorted column j
+  const int* colperm;        // [qcol + j] B row of sorted column j
   const int* fix_sn;         // [fix0 + k] supernode holding fixing DOF k
   const int64_t* fix_pos;    // [fix0 + k] diagonal position in L (relative)
   // values

@@ -101,14 +101,41 @@ struct feti_ctx {
   double* d_part = nullptr;    // dot partials
   double* h_sc = nullptr;      // pinned host scalars
   int* d_dofsub = nullptr;
+  // adjoint (element data and dense work buffers, allocated on first use)
+  std::vector<int64_t> elem_ofs, elem_dk_ofs, elem_dofs_ofs;
+  int* d_ident = nullptr;
+  int64_t nelem_total = 0;
+  int* d_eldofs = nullptr;
+  double* d_eldk = nullptr;
+  double* d_elsc = nullptr;
+  double* d_Z = nullptr;
+  double* d_Y = nullptr;
+  int* d_one = nullptr;
   int64_t ndof = 0;
   int nmax = 0;
   double* d_R = nullptr;       // concatenated R_i (column-major n x d)
   double* d_f = nullptr;       // concatenated f_i
   double* d_c = nullptr;       // c
   int dtot = 0;
-  // stats
+  // stats and measurement
   feti_stats stats{};
+  bool prof = false;
+  struct EvPair {
+    cudaEvent_t a, b, c, d;
+    int kind;  // 0 apply (a..d whole, b..c tiles), 1 implicit (a..b)
+  };
+  std::vector<EvPair> ev_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t take_event() {
+    if (ev_pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
   cudaEvent_t ev[8]{};
 };
 

@@ -297,13 +297,15 @@ template <typename TF>
 static void launch_apply_t(const DevPlan& P, const int4* items, int nitems, const void* F, const int* qmap,
                            int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                            int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid,
-                           int* status, cudaStream_t st) {
+                           int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 152 * 8));
   scatter_kernel<TF><<<sg, 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
   const size_t smem = apply_tiles_smem(sizeof(TF) == 4);
   cudaFuncSetAttribute(apply_tiles_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e0) cudaEventRecord(e0, st);
   apply_tiles_kernel<TF><<<grid, kApplyThreads, smem, st>>>(P, items, nitems, (const TF*)F, (const TF*)pg,
                                                            (TF*)rowpart, (TF*)colpart, status);
+  if (e1) cudaEventRecord(e1, st);
   const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
   reduce_cols_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
@@ -318,13 +320,13 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
 void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int* status,
-                  cudaStream_t st) {
+                  cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   if (fp32)
     launch_apply_t<float>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                          nlam, q, grid, status, st);
+                          nlam, q, grid, status, st, e0, e1);
   else
     launch_apply_t<double>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                           nlam, q, grid, status, st);
+                           nlam, q, grid, status, st, e0, e1);
 }
 
 // ---------------------------------------------------------------------------

@@ -26,25 +26,31 @@ __device__ __forceinline__ int pop_item_s(int* queue) {
 // MODE 0: qi = B L^-T L^-1 P B^T p        (implicit apply, eq. 11)
 // MODE 1: qi = B K_reg^{-1} f             (d = B K^+ f - c, eq. 7)
 // MODE 2: u  = K_reg^{-1} (f - B^T lambda) (eq. 5 without R alpha)
+// MODE 3: column j of Z = K_reg^{-1} B^T for one subdomain (items = its
+//         sorted columns; `nsub` is the column count, order[0] the subdomain);
+//         written to u as Z[dof * m + B-row of column j] (original DOF order)
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                              const double* p, const double* f, double* qi,
                                                              double* u) {
   extern __shared__ double y[];
+  __shared__ double sm_blk[kW][kW + 1];
+  __shared__ double sm_rd[kW];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   for (;;) {
     const int itx = pop_item_s(queue);
     if (itx >= nsub) return;
-    const int si = order[itx];
+    const int si = MODE == 3 ? order[0] : order[itx];
     const SubInfo& S = P.sub[si];
     const int n = S.n;
     const double* L = P.L + S.L;
     for (int k = tid; k < n; k += kThreads) y[k] = 0.0;
     __syncthreads();
-    if (MODE >= 1)
+    if (MODE == 3 && tid == 0) y[P.spos[S.col0 + itx]] = P.qsign[S.qcol + itx];
+    if (MODE == 1 || MODE == 2)
       for (int k = tid; k < n; k += kThreads) y[P.iperm[S.diag0 + k]] = f[S.dof + k];
     __syncthreads();
-    if (MODE != 1) {
+    if (MODE == 0 || MODE == 2) {
       // B^T p: columns sharing a DOF are adjacent in sorted order; the first of a run sums it
       const int* sp = P.spos + S.col0;
       for (int j = tid; j < S.m; j += kThreads) {
@@ -55,7 +61,9 @@ __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int
       }
     }
     __syncthreads();
-    // forward substitution L z = y, supernodes in postorder
+    // forward substitution L z = y, supernodes in postorder.  Each 32 x 32
+    // diagonal block and its reciprocal pivots are staged in shared memory
+    // with one coalesced load; warp 0 then solves from shared memory.
     for (int s = 0; s < S.nsn; ++s) {
       const int gs = S.sn0 + s;
       const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
@@ -63,12 +71,18 @@ __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int
       const int* rows = P.rows + P.sn_rows[gs];
       for (int kb = 0; kb < w; kb += kW) {
         const int nbk = min(kW, w - kb);
+        for (int idx = tid; idx < nbk * kW; idx += kThreads) {
+          const int k = idx / kW, i = idx % kW;  // column k, row i of the block
+          if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
+        }
+        if (tid < nbk) sm_rd[tid] = 1.0 / Ls[(int64_t)(kb + tid) * f_ + kb + tid];
+        __syncthreads();
         if (warp == 0) {
           double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
           for (int k = 0; k < nbk; ++k) {
-            const double yk = __shfl_sync(0xffffffffu, yi, k) / Ls[(int64_t)(kb + k) * f_ + kb + k];
+            const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
             if (lane == k) yi = yk;
-            else if (lane > k && lane < nbk) yi -= Ls[(int64_t)(kb + k) * f_ + kb + lane] * yk;
+            else if (lane > k && lane < nbk) yi -= sm_blk[lane][k] * yk;
           }
           if (lane < nbk) y[c0 + kb + lane] = yi;
         }
@@ -103,26 +117,84 @@ __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
           if (lane == 0) y[c0 + l] -= acc;
         }
+        for (int idx = tid; idx < nbk * kW; idx += kThreads) {
+          const int k = idx / kW, i = idx % kW;
+          if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
+        }
+        if (tid < nbk) sm_rd[tid] = 1.0 / Ls[(int64_t)(kb + tid) * f_ + kb + tid];
         __syncthreads();
         if (warp == 0) {
           double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
           for (int k = nbk - 1; k >= 0; --k) {
-            const double yk = __shfl_sync(0xffffffffu, yi, k) / Ls[(int64_t)(kb + k) * f_ + kb + k];
+            const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
             if (lane == k) yi = yk;
-            else if (lane < k) yi -= Ls[(int64_t)(kb + lane) * f_ + kb + k] * yk;
+            else if (lane < k) yi -= sm_blk[k][lane] * yk;
           }
           if (lane < nbk) y[c0 + kb + lane] = yi;
         }
         __syncthreads();
       }
     }
-    if (MODE != 2) {
+    if (MODE == 0 || MODE == 1) {
       for (int j = tid; j < S.m_pad; j += kThreads)
         qi[S.qcol + j] = j < S.m ? P.qsign[S.qcol + j] * y[P.spos[S.col0 + j]] : 0.0;
-    } else {
+    } else if (MODE == 2) {
       for (int k = tid; k < n; k += kThreads) u[S.dof + k] = y[P.iperm[S.diag0 + k]];
+    } else {
+      const int col = P.colperm[S.qcol + itx];  // B row of this sorted column
+      for (int k = tid; k < n; k += kThreads) u[(int64_t)k * S.m + col] = y[P.iperm[S.diag0 + k]];
     }
     __syncthreads();
+  }
+}
+
+// g[e] = -scale_e sum_{a,b} dK[a][b] sum_k Y[dofs_b][k] Z[dofs_a][k]
+// (dL/dtheta_e = -<Z^T dK_e Z, W> with Y = Z W); one CTA per element.
+__global__ void __launch_bounds__(256) elem_contract_kernel(const int* edofs, int nelem, int ed, const double* dKref,
+                                                            const double* dscale, const double* Z, const double* Y,
+                                                            int m, double* g) {
+  __shared__ double Zs[32][kW + 1];
+  __shared__ double Ys[32][kW + 1];
+  __shared__ double red[8];
+  const int tid = threadIdx.x;
+  for (int e = blockIdx.x; e < nelem; e += gridDim.x) {
+    const int* dof = edofs + (int64_t)e * ed;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // entries (a, b) = tid + 256 q, a = idx / ed, b = idx % ed
+    for (int k0 = 0; k0 < m; k0 += kW) {
+      __syncthreads();
+      for (int idx = tid; idx < ed * kW; idx += 256) {
+        const int a = idx / kW, k = idx % kW;
+        const bool in = k0 + k < m;
+        Zs[a][k] = in ? Z[(int64_t)dof[a] * m + k0 + k] : 0.0;
+        Ys[a][k] = in ? Y[(int64_t)dof[a] * m + k0 + k] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = tid + 256 * q;
+        if (idx < ed * ed) {
+          const int a = idx / ed, b = idx % ed;
+          double s = 0.0;
+#pragma unroll 8
+          for (int k = 0; k < kW; ++k) s += Ys[b][k] * Zs[a][k];
+          acc[q] += s;
+        }
+      }
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + 256 * q;
+      if (idx < ed * ed) t += dKref[idx] * acc[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((tid & 31) == 0) red[tid / 32] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      g[e] = -dscale[e] * s;
+    }
   }
 }
 
@@ -409,9 +481,18 @@ inline int grid_for(int64_t n, int per = 256, int cap = 152 * 16) {
 
 size_t implicit_smem(int nmax) { return (size_t)nmax * 8; }
 
+void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKref, const double* dscale,
+                          const double* Z, const double* Y, int m, double* g, cudaStream_t st) {
+  if (nelem > 0)
+    elem_contract_kernel<<<std::min(nelem, 152 * 16), 256, 0, st>>>(edofs, nelem, ed, dKref, dscale, Z, Y, m, g);
+}
+
 void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
                      const double* f, double* qi, double* u, int grid, size_t smem, cudaStream_t st) {
-  if (mode == 0) {
+  if (mode == 3) {
+    cudaFuncSetAttribute(implicit_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    implicit_kernel<3><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+  } else if (mode == 0) {
     cudaFuncSetAttribute(implicit_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     implicit_kernel<0><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
   } else if (mode == 1) {

@@ -17,10 +17,11 @@ size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);
 size_t apply_tiles_smem(bool fp32);
+// ev_tiles: optional events recorded just before / after the F-streaming kernel
 void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int* status,
-                  cudaStream_t st);
+                  cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
 void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, int vr, const int* colperm, double* out,
                      cudaStream_t st);
 
@@ -56,5 +57,7 @@ void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t
 void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
                        double* u, cudaStream_t st);
 void launch_gemv(const double* A, const double* c, double* z, int D, double alpha, cudaStream_t st);
+void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKref, const double* dscale,
+                          const double* Z, const double* Y, int m, double* g, cudaStream_t st);
 
 }  // namespace feti

@@ -63,7 +63,9 @@ class FetiStats(C.Structure):
                 ("chol_flops", C.c_double), ("trsm_flops", C.c_double), ("syrk_flops", C.c_double),
                 ("syrk_exec_flops", C.c_double), ("apply_bytes", C.c_double), ("implicit_bytes", C.c_double),
                 ("t_chol_ms", C.c_double), ("t_trsm_ms", C.c_double), ("t_syrk_ms", C.c_double),
-                ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double)]
+                ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double),
+                ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
+                ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,7 +73,7 @@ class FetiStats(C.Structure):
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
            "feti_solve", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
-           "feti_analyse", "feti_version", "feti_apply_one_static"]
+           "feti_analyse", "feti_version", "feti_apply_one_static", "feti_set_profiling"]
 
 _lib = None
 
@@ -101,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.feti_analyse.argtypes = [C.POINTER(FetiSubdomain), C.POINTER(FetiOptions), _f64p, _i32p, _i32p]
     lib.feti_version.restype = C.c_char_p
     lib.feti_apply_one_static.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp]
+    lib.feti_set_profiling.argtypes = [vp, C.c_int32]
     for name in EXPORTS:
         if name not in ("feti_last_error", "feti_destroy", "feti_version"):
             getattr(lib, name).restype = C.c_int
@@ -121,7 +124,7 @@ def _ptr(a, ctype):
 class _Marshal:
     """Keeps the NumPy arrays behind a FetiProblem alive during feti_create."""
 
-    def __init__(self, problem, with_elements=False):
+    def __init__(self, problem, with_elements=False, unit_scale=False):
         self.keep = []
         subs = (FetiSubdomain * problem.nsub)()
         for i, s in enumerate(problem.subs):
@@ -148,7 +151,8 @@ class _Marshal:
                 sub.edofs = s.elem_dofs.shape[1]
                 sub.elem_dofs = _ptr(a(s.elem_dofs, np.int32), C.c_int32)
                 sub.dKe_ref = _ptr(a(problem.K_ref, np.float64), C.c_double)
-                sub.dKe_scale = _ptr(a(s.elem_dcoef, np.float64), C.c_double)
+                scale = np.ones(s.elem_dofs.shape[0]) if unit_scale else s.elem_dcoef
+                sub.dKe_scale = _ptr(a(scale, np.float64), C.c_double)
         self.subs = subs
         self.c = self._k(np.ascontiguousarray(problem.c, dtype=np.float64))
         self.prob = FetiProblem(problem.nsub, subs, problem.n_lambda, _ptr(self.c, C.c_double))
@@ -205,7 +209,7 @@ class FetiOperator:
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, leaf_dofs: int = 64, use_coords: bool = True,
-                 with_elements: bool = False, torch_alloc: bool = True):
+                 with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -242,7 +246,7 @@ class FetiOperator:
             self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
             opt.dev_alloc, opt.dev_free = self._cb
         self.opt = opt
-        m = _Marshal(problem, with_elements=with_elements)
+        m = _Marshal(problem, with_elements=with_elements, unit_scale=unit_scale)
         h = C.c_void_p()
         rc = self.lib.feti_create(C.byref(m.prob), C.byref(opt), C.byref(h))
         self.h = h
@@ -294,9 +298,17 @@ class FetiOperator:
         return lam, alpha[:self.dtot], u, dict(iterations=info.iterations, refinements=info.refinements,
                                                  rel_residual=info.rel_residual, converged=bool(info.converged))
 
-    def adjoint(self, W_dev, nelem_total):
-        out = self._dvec(nelem_total)
-        self._check(self.lib.feti_adjoint(self.h, C.c_void_p(W_dev.data_ptr()), C.c_void_p(out.data_ptr())))
+    def adjoint(self, W):
+        """dL/dtheta_e for L = sum_i <W_i, F_i> (feti_adjoint).  W: list of
+        m_i x m_i arrays/tensors in B-row order, or one concatenated FP64 CUDA
+        tensor.  Returns a CUDA FP64 tensor over all elements (subdomain order)."""
+        torch = self.torch
+        if isinstance(W, (list, tuple)):
+            W = torch.cat([torch.as_tensor(w, dtype=torch.float64).reshape(-1) for w in W]).to(self.device)
+        W = W.contiguous()
+        nel = sum(s.elem_dofs.shape[0] for s in self.problem.subs)
+        out = self._dvec(nel)
+        self._check(self.lib.feti_adjoint(self.h, C.c_void_p(W.data_ptr()), C.c_void_p(out.data_ptr())))
         return out
 
     def get_F(self, sub):
@@ -304,6 +316,9 @@ class FetiOperator:
         out = np.zeros((m, m))
         self._check(self.lib.feti_get_F(self.h, sub, _ptr(out, C.c_double)))
         return out
+
+    def set_profiling(self, enable=True):
+        self._check(self.lib.feti_set_profiling(self.h, 1 if enable else 0))
 
     def stats(self):
         st = FetiStats()
@@ -321,3 +336,42 @@ class FetiOperator:
             self.close()
         except Exception:
             pass
+
+
+def _feti_weighted_trace():
+    import torch
+
+    class FetiWeightedTrace(torch.autograd.Function):
+        """L(coef) = sum_i <W_i, F_i(coef)>, K_e = coef_e K_ref per element.
+
+        forward re-assembles K_i from the element coefficients, runs
+        feti_assemble and forms L from the assembled F_i; backward maps
+        dL/dF_i = W_i to dL/dcoef_e with the FP64 adjoint kernel
+        (feti_adjoint, Z_i recomputed).  The operator must be created with
+        with_elements=True and unit_scale=True (dK_e/dcoef_e = K_ref)."""
+
+        @staticmethod
+        def forward(ctx, coef, op, Ws):
+            from .problems import subdomain_K_values
+            c = coef.detach().cpu().numpy()
+            off = 0
+            for i, s in enumerate(op.problem.subs):
+                ne = s.elem_dofs.shape[0]
+                op.update_values(i, subdomain_K_values(op.problem, i, c[off:off + ne]))
+                off += ne
+            op.assemble()
+            L = sum(float(np.sum(np.asarray(W) * op.get_F(i))) for i, W in enumerate(Ws))
+            ctx.op, ctx.Ws = op, Ws
+            return torch.tensor(L, dtype=torch.float64, device=coef.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g = ctx.op.adjoint(ctx.Ws)
+            return grad_out * g.to(grad_out.device), None, None
+
+    return FetiWeightedTrace
+
+
+def weighted_trace(coef, op, Ws):
+    """Differentiable L = sum_i <W_i, F_i(coef)> (see FetiWeightedTrace)."""
+    return _feti_weighted_trace().apply(coef, op, Ws)

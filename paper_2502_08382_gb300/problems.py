@@ -455,6 +455,14 @@ def make_config(k: int, nsub_axis: Optional[int] = None, seed: int = 0) -> Probl
     raise ValueError(k)
 
 
+def subdomain_K_values(problem: Problem, i: int, elem_coef: np.ndarray) -> np.ndarray:
+    """CSR values of K_i for per-element coefficients elem_coef (K_e = coef_e K_ref)."""
+    s = problem.subs[i]
+    _, col, pos, _ = _local_pattern(tuple(s.shape), problem.dpn)
+    return np.bincount(pos.ravel(), weights=(np.asarray(elem_coef)[:, None, None] * problem.K_ref[None]).ravel(),
+                       minlength=col.shape[0])
+
+
 def make_W(problem: Problem, seed: int = 0) -> List[np.ndarray]:
     """Symmetric N(0,1) weights W_i (m_i x m_i): upper triangle incl. diagonal
     drawn row by row from default_rng([seed, 3]) and mirrored."""

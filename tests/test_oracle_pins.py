@@ -231,6 +231,23 @@ def test_gradient_vs_central_fd(tiny_el):
             assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_loss_difference_identity(tiny_el):
+    """The resolvent form of L(K+) - L(K-) equals the plain difference of the
+    two losses on a step large enough for the plain difference to be exact
+    to ~1e-10."""
+    P = tiny_el
+    Ws = make_W(P, seed=2)
+    s = P.subs[3]
+    rho = O.rho_pen(O.K_dense(s))
+    e = 5
+    dc = 0.05 * s.elem_coef[e]
+    Kp = O.perturbed_K_reg(s, e, dc, P.K_ref, rho)
+    Km = O.perturbed_K_reg(s, e, -dc, P.K_ref, rho)
+    a = O.loss_difference(s, Ws[3], Kp, Km, e, 2 * dc, P.K_ref)
+    b = O.loss_sub(s, Ws[3], Kp) - O.loss_sub(s, Ws[3], Km)
+    assert abs(a - b) <= 1e-9 * abs(b)
+
+
 # ------------------------------------------------------------- paper's printed numbers
 
 
