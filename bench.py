@@ -287,6 +287,7 @@ def main():
             "pcg": {"iterations": info["iterations"], "refinements": info["refinements"],
                     "fp64_iterations": info64["iterations"]},
             "apply": {"ms": apply_ms, "tiles_ms": tiles_ms, "algorithmic_bytes": st_["apply_bytes"],
+                      "autotuned": {"stages": st_["apply_stages"], "grid": st_["apply_grid"]},
                       "gbs_whole_call": st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9},
             "implicit_fp64_apply_ms": impl64_ms,
             "break_even_iters": n_star,

@@ -118,6 +118,8 @@ typedef struct {
   double apply_tiles_ms;      /* CUDA-event time of their F-streaming kernel only */
   int64_t implicit_calls;     /* implicit-operator applications (feti_apply_implicit and inside feti_solve) */
   double implicit_ms;         /* CUDA-event time of those applications */
+  /* autotuner choice for the apply (after the first feti_assemble) */
+  int32_t apply_stages, apply_grid;
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;
@@ -196,8 +198,10 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
  *
  * F_dev: F_i in this library's tile layout, FP32 (fp32 = 1) or FP64 (fp32 = 0),
  *        device memory: 64 x 64 tiles (bi, bj) with bj <= bi stored in the
- *        order bi (bi + 1) / 2 + bj, each tile row-major with 64 columns; the
- *        diagonal tiles are stored in full; the last block row
+ *        order bi (bi + 1) / 2 + bj; inside a tile, row r holds 64 values whose
+ *        16-byte chunks are permuted: value (r, c) sits at
+ *        r * 64 + ((c / w) ^ (r % (64 / w))) * w + c % w, w = 16 / sizeof(value);
+ *        the diagonal tiles are stored in full; the last block row
  *        bi = nb - 1 (nb = ceil(m / 64)) holds only m - 64 (nb - 1) rows per
  *        tile; columns of the last block beyond m hold zeros.
  * map_dev: [m] int32 device array, distinct multiplier ids (rows of F_i).

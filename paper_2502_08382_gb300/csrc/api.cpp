@@ -324,7 +324,7 @@ void build(feti_ctx* c) {
     I.R = Ro;
     I.tpart = tpo;
     I.rpart = rpo;
-    rpo += (int64_t)B.nb * ((B.nb + kApplyChunk - 1) / kApplyChunk) * kT;
+    rpo += (int64_t)B.nb * ((B.nb + kApplyChunk - 1) / kApplyChunk) * kT * kApplyWarps;
     int ntile = B.nb * (B.nb + 1) / 2;
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
@@ -459,19 +459,37 @@ void build(feti_ctx* c) {
     return c->pats[c->subs[a].pat].nnzL > c->pats[c->subs[b].pat].nnzL;
   });
   std::vector<std::pair<double, int2>> sy;
-  std::vector<int4> api;
+  std::vector<TileDesc> tdesc;
+  std::vector<int> item_end;  // tile index one past each work item
   for (int i = 0; i < ns; ++i) {
     auto& B = c->bps[c->subs[i].bp];
     auto& P = c->pats[c->subs[i].pat];
+    auto& I = c->info[i];
     int ntile = B.nb * (B.nb + 1) / 2;
     for (int t = 0; t < ntile; ++t) {
       double cost = 1.0;
       for (int k = B.tile_off[t]; k < B.tile_off[t + 1]; ++k) cost += P.sn_w[B.tile_sn[k]];
       sy.push_back({cost, make_int2(i, t)});
     }
+    const int nch = (B.nb + kApplyChunk - 1) / kApplyChunk;
     for (int b = 0; b < B.nb; ++b)
-      for (int c = 0; c <= b; c += kApplyChunk) api.push_back(make_int4(i, b, c, std::min(c + kApplyChunk, b + 1)));
+      for (int ch = 0; ch * kApplyChunk <= b; ++ch) {
+        const int bj0 = ch * kApplyChunk, bj1 = std::min(bj0 + kApplyChunk, b + 1);
+        for (int bj = bj0; bj < bj1; ++bj) {
+          TileDesc d{};
+          d.f_ofs = I.F + tile_offset(B.nb, I.vr, b, bj);
+          d.rows = tile_rows(B.nb, I.vr, b);
+          d.flags = (bj == bj0 ? kTileFirst : 0) | (bj == bj1 - 1 ? kTileLast : 0);
+          d.prow = (int)(I.qcol + (int64_t)b * kT);
+          d.pcol = (int)(I.qcol + (int64_t)bj * kT);
+          d.col_slot = bj < b ? (int)(I.tpart / kT + (int64_t)b * (b + 1) / 2 + bj) : -1;
+          d.row_slot = (int)(I.rpart / (kT * kApplyWarps) + (int64_t)b * nch + ch);
+          tdesc.push_back(d);
+        }
+        item_end.push_back((int)tdesc.size());
+      }
   }
+  c->napply = (int)item_end.size();
   std::vector<std::pair<double, int2>> sy2;
   for (int i = 0; i < ns; ++i) {
     auto& B = c->bps[c->subs[i].bp];
@@ -495,7 +513,6 @@ void build(feti_ctx* c) {
     for (int b = 0; b < c->bps[c->subs[i].bp].nb; ++b) blocks.push_back(make_int2(i, b));
   c->nblocks = (int)blocks.size();
   c->nsyrk = (int)syi.size();
-  c->napply = (int)api.size();
 
   // ---- persistent grids and workspace
   int dev = 0;
@@ -591,7 +608,30 @@ void build(feti_ctx* c) {
   c->d_trsm_order = upload(c, order_t);
   c->d_impl_order = upload(c, order_i);
   c->d_syrk_items = upload(c, syi);
-  c->d_apply_items = upload(c, api);
+  {
+    // contiguous, item-aligned tile ranges per CTA of the apply, balanced by
+    // tile count, for every candidate stage count of the autotuner
+    c->d_tdesc = upload(c, tdesc);
+    const int cands[] = {2, 3, 4, 5, 6};
+    for (int ns : cands) {
+      if (!c->fp32 && ns > 3) continue;
+      const int occ = apply_max_ctas_per_sm(c->fp32, ns);
+      if (occ <= 0) continue;
+      const int G = std::max(1, std::min(c->napply, c->nsm * occ));
+      std::vector<int> cb(G + 1, 0);
+      const double per = (double)tdesc.size() / G;
+      int cta = 1;
+      for (size_t it = 0; it < item_end.size() && cta < G; ++it)
+        if (item_end[it] >= per * cta) cb[cta++] = item_end[it];
+      for (; cta <= G; ++cta) cb[cta] = (int)tdesc.size();
+      c->apply_cands.push_back({ns, G, upload(c, cb), 0.0});
+    }
+    if (c->apply_cands.empty()) throw CudaError("no launchable configuration of the apply kernel");
+    // default before tuning: the largest stage count that keeps 2 CTAs per SM
+    c->apply_pick = 0;
+    for (size_t k = 0; k < c->apply_cands.size(); ++k)
+      if (c->apply_cands[k].grid >= std::min(c->napply, 2 * c->nsm)) c->apply_pick = (int)k;
+  }
   c->d_syrk2_items = upload(c, sy2i);
   c->d_blocks = upload(c, blocks);
   c->d_colperm = upload(c, colperm);
@@ -711,6 +751,9 @@ feti_status feti_assemble(feti_ctx* ctx) {
   if (g != FETI_OK) return g;
   API_BEGIN
   cudaStream_t st = ctx->st;
+  if ((ctx->nsyrk2 > 0 && !ctx->d_syrk2_items) || (ctx->nsyrk > 0 && !ctx->d_syrk_items) || !ctx->d_tdesc ||
+      !ctx->d_blocks || ctx->apply_cands.empty())
+    throw CudaError("internal: a work list of the assembly or apply is missing");
   CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -753,6 +796,37 @@ feti_status feti_assemble(feti_ctx* ctx) {
   if (!ctx->coarse_ready) ctx->stats.t_coarse_ms = e34;
   ctx->coarse_ready = true;
   ctx->stats.t_assemble_ms = d;
+  if (!ctx->apply_tuned) {
+    // autotuner: time every launchable stage count of the apply on this problem, keep the fastest
+    double* pz = ctx->d_vec + (size_t)5 * ctx->nlam;
+    double* qz = ctx->d_vec + (size_t)6 * ctx->nlam;
+    CK(cudaMemsetAsync(pz, 0, (size_t)ctx->nlam * 8, st));
+    for (size_t k = 0; k < ctx->apply_cands.size(); ++k) {
+      auto& c2 = ctx->apply_cands[k];
+      for (int rep = 0; rep < 2; ++rep)
+        launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, c2.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, pz, ctx->d_pg,
+                     ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
+                     ctx->nlam, qz, c2.grid, ctx->d_status, st, nullptr, nullptr, c2.stages);
+      CK(cudaEventRecord(ctx->ev[5], st));
+      for (int rep = 0; rep < 5; ++rep)
+        launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, c2.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, pz, ctx->d_pg,
+                     ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
+                     ctx->nlam, qz, c2.grid, ctx->d_status, st, nullptr, nullptr, c2.stages);
+      CK(cudaEventRecord(ctx->ev[6], st));
+      CK(cudaEventSynchronize(ctx->ev[6]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[6]));
+      c2.ms = ms / 5;
+      if (ms / 5 < ctx->apply_cands[ctx->apply_pick].ms || ctx->apply_cands[ctx->apply_pick].ms == 0.0 ||
+          k == 0)
+        ctx->apply_pick = (int)k;
+    }
+    for (size_t k = 0; k < ctx->apply_cands.size(); ++k)
+      if (ctx->apply_cands[k].ms < ctx->apply_cands[ctx->apply_pick].ms) ctx->apply_pick = (int)k;
+    ctx->apply_tuned = true;
+    ctx->stats.apply_stages = ctx->apply_cands[ctx->apply_pick].stages;
+    ctx->stats.apply_grid = ctx->apply_cands[ctx->apply_pick].grid;
+  }
   int status = 0;
   CK(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status & kStatNotSPD) return set_error(ctx, FETI_ERR_NOT_SPD, "a Cholesky pivot was not positive");
@@ -768,15 +842,16 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_apply before feti_assemble");
   API_BEGIN
   cudaStream_t st = ctx->st;
-  int grid = std::max(1, std::min(ctx->napply, ctx->nsm * 2));
+  const auto& cand = ctx->apply_cands[ctx->apply_pick];
+  int grid = cand.grid;
   feti_ctx::EvPair ev{};
   if (ctx->prof) {
     ev = {ctx->take_event(), ctx->take_event(), ctx->take_event(), ctx->take_event(), 0};
     CK(cudaEventRecord(ev.a, st));
   }
-  launch_apply(ctx->P, ctx->fp32, ctx->d_apply_items, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
+  launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, cand.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
                ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
-               ctx->nlam, q_dev, grid, ctx->d_status, st, ev.b, ev.c);
+               ctx->nlam, q_dev, grid, ctx->d_status, st, ev.b, ev.c, cand.stages);
   ctx->stats.launches += 4;
   ctx->stats.apply_calls += 1;
   if (ctx->prof) {

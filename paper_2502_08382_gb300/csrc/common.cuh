@@ -14,6 +14,7 @@ constexpr int kT = 64;          // F tile edge
 constexpr int kThreads = 256;   // CTA size of the dense kernels
 constexpr int kNB = 32;         // panel block of the dense factorisation / solve
 constexpr int kApplyChunk = 8;  // tiles per apply work item (one tile row is cut into chunks)
+constexpr int kApplyWarps = 8;  // consumer warps of the apply; row partials are kept per warp
 
 struct SubInfo {
   int n, m, m_pad, nb, nsn, nact, d, nfix;
@@ -93,9 +94,29 @@ __host__ __device__ inline int64_t tile_offset(int nb, int vr, int bi, int bj) {
   return ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)bj * vr * kT;
 }
 __host__ __device__ inline int tile_rows(int nb, int vr, int bi) { return bi < nb - 1 ? kT : vr; }
+// Position of element (r, c) inside a stored tile: rows of kT values, the
+// 16-byte chunks of row r XOR-swizzled by r (so that 8 consecutive rows read
+// the same logical chunk from 8 different shared-memory banks).
+template <int ESZ>
+__host__ __device__ inline int tile_pos(int r, int c) {
+  constexpr int cw = 16 / ESZ, nch = kT / cw;
+  return r * kT + (((c / cw) ^ (r % nch)) * cw) + (c % cw);
+}
 __host__ __device__ inline int64_t F_size(int nb, int vr) {
   return nb == 0 ? 0 : ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)nb * vr * kT;
 }
+
+// One F tile of the explicit apply (host-built, 32 bytes).
+enum : int { kTileFirst = 1, kTileLast = 2 };
+struct __align__(16) TileDesc {
+  int64_t f_ofs;   // element offset of the tile in the F storage
+  int rows;        // stored rows (kT, or the ragged last block row)
+  int flags;       // kTileFirst / kTileLast of its work item
+  int prow;        // pg offset of the tile's row block
+  int pcol;        // pg offset of the tile's column block
+  int col_slot;    // column-partial slot (tile index in the subdomain's partial array + base), -1 on the diagonal
+  int row_slot;    // row-partial slot of the work item (written after its last tile)
+};
 
 // status word bits written by kernels
 enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };

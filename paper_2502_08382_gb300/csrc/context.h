@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/feti.h"
+#include "feti.h"
 #include "common.cuh"
 #include "symbolic.h"
 
@@ -70,7 +70,15 @@ struct feti_ctx {
   int* d_trsm_order = nullptr;
   int* d_impl_order = nullptr;
   int2* d_syrk_items = nullptr;
-  int4* d_apply_items = nullptr;
+  feti::TileDesc* d_tdesc = nullptr;
+  struct ApplyCand {
+    int stages, grid;
+    int* cta_begin;
+    double ms;
+  };
+  std::vector<ApplyCand> apply_cands;  // autotuner candidates of the apply
+  int apply_pick = 0;
+  bool apply_tuned = false;
   void* d_pg = nullptr;
   void* d_rowpart = nullptr;
   int2* d_syrk2_items = nullptr;
@@ -110,7 +118,6 @@ struct feti_ctx {
   double* d_elsc = nullptr;
   double* d_Z = nullptr;
   double* d_Y = nullptr;
-  int* d_one = nullptr;
   int64_t ndof = 0;
   int nmax = 0;
   double* d_R = nullptr;       // concatenated R_i (column-major n x d)

@@ -22,7 +22,7 @@
 // 64 terms); the cross-tile sums in phase 2 are FP64.  All waits are bounded.
 #include <mutex>
 
-#include "../../include/feti.h"
+#include "feti.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -97,19 +97,26 @@ __global__ void scatter_kernel(const int* qmap, int64_t ncols, const double* p, 
   }
 }
 
-template <typename TF>
-__global__ void __launch_bounds__(kApplyThreads, 2) apply_tiles_kernel(DevPlan P, const int4* items, int nitems,
-                                                                      const TF* F, const TF* pg, TF* rowpart,
-                                                                      TF* colpart, int* status) {
+// One stage: the tile, the two p segments it needs, and its descriptor.
+// NS = number of stages in the ring (the autotuner picks it per problem).
+template <typename TF, int NS>
+__global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDesc* desc, const int* cta_begin,
+                                                                   const TF* F, const TF* pg, TF* rowpart,
+                                                                   TF* colpart, int* status) {
   using C = ApplyCfg<TF>;
-  constexpr int S = C::kStages;
+  constexpr int S = NS;
+  constexpr int kMeta = 64;  // bytes of descriptor kept after the p segments
+  constexpr int kStride = C::kStageBytes + kMeta;
+  constexpr int cw = 16 / (int)sizeof(TF), nchk = kT / cw;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   __shared__ uint64_t full[S], empty[S];
   __shared__ TF cred[S][kConsumerWarps][kT];
   __shared__ int cnt[S];
+  __shared__ TileDesc dring[64];
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int t0 = cta_begin[blockIdx.x], t1 = cta_begin[blockIdx.x + 1];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(&full[s])));
@@ -123,135 +130,162 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_tiles_kernel(DevPlan P
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------ producer
-    uint32_t t = 0;
-    for (int ii = blockIdx.x; ii < nitems && !s_abort; ii += gridDim.x) {
-      const int4 it = items[ii];
-      const SubInfo& Sb = P.sub[it.x];
-      const int b = it.y;
-      for (int bj = it.z; bj < it.w; ++bj, ++t) {
-        const int st = t % S;
-        if (t >= S && !warp_wait(smem_u32a(&empty[st]), ((t / S) + 1) & 1)) {
-          s_abort = 1;
-          break;
-        }
-        if (lane == 0) {
-          const uint32_t stage = smem_u32a(smem + st * C::kStageBytes);
-          const uint32_t fb = smem_u32a(&full[st]);
-          const TF* src = F + Sb.F + tile_offset(Sb.nb, Sb.vr, b, bj);
-          const uint32_t tb = (uint32_t)tile_rows(Sb.nb, Sb.vr, b) * kT * (uint32_t)sizeof(TF);
-          expect_tx(fb, tb + 2 * kT * (uint32_t)sizeof(TF));
-          bulk_copy(stage, src, tb, fb);
-          bulk_copy(stage + C::kTileBytes, pg + Sb.qcol + b * kT, kT * sizeof(TF), fb);
-          bulk_copy(stage + C::kTileBytes + kT * sizeof(TF), pg + Sb.qcol + bj * kT, kT * sizeof(TF), fb);
-        }
+    uint32_t k = 0;
+    for (int t = t0; t < t1 && !s_abort; ++t, ++k) {
+      if (((t - t0) & 31) == 0) {
+        // prefetch the next 32 descriptors into a double-buffered ring
+        const int base = ((t - t0) >> 5) & 1;
+        if (t + lane < t1) dring[base * 32 + lane] = desc[t + lane];
         __syncwarp();
       }
+      const TileDesc d = dring[(((t - t0) >> 5) & 1) * 32 + ((t - t0) & 31)];
+      const int st = k % S;
+      if (k >= S && !warp_wait(smem_u32a(&empty[st]), ((k / S) + 1) & 1)) {
+        s_abort = 1;
+        break;
+      }
+      if (lane == 0) {
+        uint8_t* stage = smem + st * kStride;
+        *reinterpret_cast<TileDesc*>(stage + C::kStageBytes) = d;
+        const uint32_t sa = smem_u32a(stage);
+        const uint32_t fb = smem_u32a(&full[st]);
+        const uint32_t tb = (uint32_t)d.rows * kT * (uint32_t)sizeof(TF);
+        expect_tx(fb, tb + 2 * kT * (uint32_t)sizeof(TF));
+        bulk_copy(sa, F + d.f_ofs, tb, fb);
+        bulk_copy(sa + C::kTileBytes, pg + d.prow, kT * sizeof(TF), fb);
+        bulk_copy(sa + C::kTileBytes + kT * sizeof(TF), pg + d.pcol, kT * sizeof(TF), fb);
+      }
+      __syncwarp();
     }
-    // drain: every issued copy must land before the CTA exits
     if (s_abort) {
-      for (uint32_t u = (t > S ? t - S : 0); u < t; ++u) warp_wait(smem_u32a(&full[u % S]), (u / S) & 1);
+      for (uint32_t u = (k > S ? k - S : 0); u < k; ++u) warp_wait(smem_u32a(&full[u % S]), (u / S) & 1);
     }
     return;
   }
 
   // -------------------------------------------------------------- consumers
-  const int rg = tid / 16, cg = tid % 16;  // 4 x 4 block: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
-  uint32_t t = 0;
-  for (int ii = blockIdx.x; ii < nitems; ii += gridDim.x) {
-    const int4 it = items[ii];
-    const SubInfo& Sb = P.sub[it.x];
-    const int b = it.y;
-    TF racc[4] = {(TF)0, (TF)0, (TF)0, (TF)0};
-    bool ok = true;
-    for (int bj = it.z; bj < it.w; ++bj, ++t) {
-      const int st = t % S;
-      if (!warp_wait(smem_u32a(&full[st]), (t / S) & 1)) {
-        ok = false;
-        break;
-      }
-      const uint8_t* stage = smem + st * C::kStageBytes;
-      const TF* Ft = reinterpret_cast<const TF*>(stage);
-      const TF* pr = reinterpret_cast<const TF*>(stage + C::kTileBytes);
-      const TF* pc = pr + kT;
-      // rows at or beyond the tile's stored rows hold stale data: read as zero
-      const int nrow = tile_rows(Sb.nb, Sb.vr, b);
-      TF v[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const TF* rowp = Ft + (4 * rg + a) * kT + 4 * cg;
-        const bool in = 4 * rg + a < nrow;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[a][c] = in ? rowp[c] : (TF)0;
-      }
-      TF pcv[4], prv[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        pcv[c] = pc[4 * cg + c];
-        prv[c] = pr[4 * rg + c];
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        TF s = (TF)0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) s = fma(v[a][c], pcv[c], s);
-        racc[a] += s;
-      }
-      if (bj < b) {
-        TF cs[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          TF s = (TF)0;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) s = fma(v[a][c], prv[a], s);
-          cs[c] = s + __shfl_xor_sync(0xffffffffu, s, 16);  // the warp's two row groups
-        }
-        if (lane < 16) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) cred[st][warp][4 * cg + c] = cs[c];
-        }
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) {
-          __threadfence_block();
-          last = atomicAdd(&cnt[st], 1) == kConsumerWarps - 1;
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-          __threadfence_block();
-          for (int c = lane; c < kT; c += 32) {
-            TF s = (TF)0;
-#pragma unroll
-            for (int w = 0; w < kConsumerWarps; ++w) s += cred[st][w][c];
-            colpart[Sb.tpart + (int64_t)(b * (b + 1) / 2 + bj) * kT + c] = s;  // per-tile slots (unragged)
-          }
-          if (lane == 0) cnt[st] = 0;
-          __syncwarp();
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32a(&empty[st]));
-    }
-    if (!ok) {
+  // thread (rg, cg) holds the 4 x 4 block rows 4 rg .. 4 rg + 3, columns
+  // 4 cg .. 4 cg + 3 (one 16-byte chunk per row for FP32, two for FP64);
+  // the stored rows are chunk-swizzled (tile_pos), which keeps the reads of a
+  // quarter warp on distinct banks.  The column partial of an off-diagonal
+  // tile is summed over the 8 warps by the last warp to finish it.
+  const int rg = tid / 16, cg = tid % 16;
+  TF racc[4] = {(TF)0, (TF)0, (TF)0, (TF)0};
+  uint32_t k = 0;
+  for (int t = t0; t < t1; ++t, ++k) {
+    const int st = k % S;
+    if (!warp_wait(smem_u32a(&full[st]), (k / S) & 1)) {
       s_abort = 1;
       break;
     }
-    // row partial: reduce over the 16 column groups (lanes of a half warp)
+    const uint8_t* stage = smem + st * kStride;
+    const TileDesc d = *reinterpret_cast<const TileDesc*>(stage + C::kStageBytes);
+    const TF* Ft = reinterpret_cast<const TF*>(stage);
+    const TF* pr = reinterpret_cast<const TF*>(stage + C::kTileBytes);
+    const TF* pc = pr + kT;
+    TF v[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      TF s = racc[a];
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      racc[a] = s;
+      const int r = 4 * rg + a;
+      const bool in = r < d.rows;  // rows beyond the stored ones hold stale data: read as zero
+      if constexpr (sizeof(TF) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(Ft + r * kT + ((cg ^ (r % nchk)) * cw));
+        v[a][0] = in ? x.x : 0.f;
+        v[a][1] = in ? x.y : 0.f;
+        v[a][2] = in ? x.z : 0.f;
+        v[a][3] = in ? x.w : 0.f;
+      } else {
+        const double2 x0 = *reinterpret_cast<const double2*>(Ft + r * kT + (((2 * cg) ^ (r % nchk)) * cw));
+        const double2 x1 = *reinterpret_cast<const double2*>(Ft + r * kT + (((2 * cg + 1) ^ (r % nchk)) * cw));
+        v[a][0] = in ? x0.x : 0.0;
+        v[a][1] = in ? x0.y : 0.0;
+        v[a][2] = in ? x1.x : 0.0;
+        v[a][3] = in ? x1.y : 0.0;
+      }
     }
-    if (cg == 0) {
-      const int nch = (Sb.nb + kApplyChunk - 1) / kApplyChunk;
-      const int chunk = it.z / kApplyChunk;
-      TF* dst = rowpart + Sb.rpart + ((int64_t)b * nch + chunk) * kT + 4 * rg;
+    TF pcv[4], prv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) dst[a] = racc[a];
+    for (int c = 0; c < 4; ++c) {
+      pcv[c] = pc[4 * cg + c];
+      prv[c] = pr[4 * rg + c];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      TF s2 = (TF)0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s2 = fma(v[a][c], pcv[c], s2);
+      racc[a] += s2;
+    }
+    if (d.col_slot >= 0) {
+      TF cs[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        TF s2 = (TF)0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) s2 = fma(v[a][c], prv[a], s2);
+        cs[c] = s2 + __shfl_xor_sync(0xffffffffu, s2, 16);  // the warp's two row groups
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cred[st][warp][4 * cg + c] = cs[c];
+      }
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&cnt[st], 1) == kConsumerWarps - 1;
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        __threadfence_block();
+        for (int c = lane; c < kT; c += 32) {
+          TF s2 = (TF)0;
+#pragma unroll
+          for (int w = 0; w < kConsumerWarps; ++w) s2 += cred[st][w][c];
+          colpart[(int64_t)d.col_slot * kT + c] = s2;
+        }
+        if (lane == 0) cnt[st] = 0;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32a(&empty[st]));
+    if (d.flags & kTileLast) {
+      // row partial of the work item: reduce over the 16 column groups (lanes of a half warp)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        TF s2 = racc[a];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        racc[a] = (TF)0;
+        if (cg == 0) rowpart[(int64_t)d.row_slot * kApplyWarps * kT + 4 * rg + a] = s2;
+      }
     }
   }
   if (s_abort && tid == 0) atomicOr(status, kStatTimeout);
+}
+
+template <typename TF>
+size_t stage_smem(int ns) {
+  return (size_t)ns * (ApplyCfg<TF>::kStageBytes + 64) + 128;
+}
+
+// launch the staged kernel with ns stages (2..6)
+template <typename TF>
+void launch_tiles(int ns, int grid, cudaStream_t st, const TileDesc* desc, const int* cta_begin, const TF* F,
+                  const TF* pg, TF* rowpart, TF* colpart, int* status) {
+  const size_t smem = stage_smem<TF>(ns);
+#define FETI_TL(N)                                                                                                  \
+  case N:                                                                                                           \
+    cudaFuncSetAttribute(apply_tiles_kernel<TF, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+    apply_tiles_kernel<TF, N><<<grid, kApplyThreads, smem, st>>>(desc, cta_begin, F, pg, rowpart, colpart, status); \
+    break;
+  switch (ns) {
+    FETI_TL(2) FETI_TL(3) FETI_TL(4) FETI_TL(5) FETI_TL(6)
+    default:
+      break;
+  }
+#undef FETI_TL
 }
 
 // q_i[j] = (row partials of block b(j) over the item chunks) + (column
@@ -259,7 +293,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_tiles_kernel(DevPlan P
 // lanes over the 64 columns of the block.  FP64 sums in a fixed order.
 template <typename TF>
 __global__ void reduce_cols_kernel(DevPlan P, const int2* blocks, int nblocks, const TF* rowpart,
-                                   const TF* colpart, double* qi) {
+                                   const TF* colpart, double* qi, int nslots) {
   const int lane = threadIdx.x & 31;
   for (int wb = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wb < nblocks; wb += gridDim.x * blockDim.x / 32) {
     const int2 sb = blocks[wb];
@@ -269,7 +303,9 @@ __global__ void reduce_cols_kernel(DevPlan P, const int2* blocks, int nblocks, c
     const int64_t rp = S.rpart, tp = S.tpart, qc = S.qcol;
     for (int x = lane; x < kT; x += 32) {
       double s = 0.0;
-      for (int c = 0; c * kApplyChunk <= b; ++c) s += (double)rowpart[rp + ((int64_t)b * nch + c) * kT + x];
+      for (int c = 0; c * kApplyChunk <= b; ++c)
+        for (int w = 0; w < nslots; ++w)
+          s += (double)rowpart[rp + (((int64_t)b * nch + c) * kApplyWarps + w) * kT + x];
       for (int bi = b + 1; bi < nb; ++bi) s += (double)colpart[tp + (int64_t)(bi * (bi + 1) / 2 + b) * kT + x];
       qi[qc + b * kT + x] = s;
     }
@@ -289,25 +325,22 @@ __global__ void gather_lambda_kernel(const int* c0, const int* c1, int nlam, con
 }  // namespace
 
 size_t apply_tiles_smem(bool fp32) {
-  return fp32 ? (size_t)ApplyCfg<float>::kStages * ApplyCfg<float>::kStageBytes + 128
-              : (size_t)ApplyCfg<double>::kStages * ApplyCfg<double>::kStageBytes + 128;
+  return fp32 ? stage_smem<float>(ApplyCfg<float>::kStages) : stage_smem<double>(ApplyCfg<double>::kStages);
 }
 
 template <typename TF>
-static void launch_apply_t(const DevPlan& P, const int4* items, int nitems, const void* F, const int* qmap,
-                           int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
-                           int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid,
-                           int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+static void launch_apply_t(const DevPlan& P, const TileDesc* desc, const int* cta_begin, const void* F,
+                           const int* qmap, int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart,
+                           const int2* blocks, int nblocks, double* qi, const int* c0, const int* c1, int nlam,
+                           double* q, int grid, int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                           int stages) {
   const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 152 * 8));
   scatter_kernel<TF><<<sg, 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
-  const size_t smem = apply_tiles_smem(sizeof(TF) == 4);
-  cudaFuncSetAttribute(apply_tiles_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e0) cudaEventRecord(e0, st);
-  apply_tiles_kernel<TF><<<grid, kApplyThreads, smem, st>>>(P, items, nitems, (const TF*)F, (const TF*)pg,
-                                                           (TF*)rowpart, (TF*)colpart, status);
+  launch_tiles<TF>(stages, grid, st, desc, cta_begin, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart, status);
   if (e1) cudaEventRecord(e1, st);
   const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
-  reduce_cols_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi);
+  reduce_cols_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi, 1);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
   gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
 }
@@ -317,16 +350,32 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
   gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
 }
 
-void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, const void* F, const int* qmap,
-                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
-                  int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int* status,
-                  cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, const int* cta_begin, const void* F,
+                  const int* qmap, int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart,
+                  const int2* blocks, int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q,
+                  int grid, int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int stages) {
   if (fp32)
-    launch_apply_t<float>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                          nlam, q, grid, status, st, e0, e1);
+    launch_apply_t<float>(P, desc, cta_begin, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                          nlam, q, grid, status, st, e0, e1, stages);
   else
-    launch_apply_t<double>(P, items, nitems, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                           nlam, q, grid, status, st, e0, e1);
+    launch_apply_t<double>(P, desc, cta_begin, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                           nlam, q, grid, status, st, e0, e1, stages);
+}
+
+int apply_max_ctas_per_sm(bool fp32, int stages) {
+  int nb = 0;
+  if (fp32) {
+    const size_t smem = stage_smem<float>(stages);
+#define FETI_OCC(N)                                                                                      if (stages == N) {                                                                                       cudaFuncSetAttribute(apply_tiles_kernel<float, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, N>, kApplyThreads, smem);    }
+    FETI_OCC(2) FETI_OCC(3) FETI_OCC(4) FETI_OCC(5) FETI_OCC(6)
+#undef FETI_OCC
+  } else {
+    const size_t smem = stage_smem<double>(stages);
+#define FETI_OCC(N)                                                                                       if (stages == N) {                                                                                        cudaFuncSetAttribute(apply_tiles_kernel<double, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, N>, kApplyThreads, smem);    }
+    FETI_OCC(2) FETI_OCC(3) FETI_OCC(4) FETI_OCC(5) FETI_OCC(6)
+#undef FETI_OCC
+  }
+  return nb;
 }
 
 // ---------------------------------------------------------------------------
@@ -346,36 +395,56 @@ void launch_apply(const DevPlan& P, bool fp32, const int4* items, int nitems, co
 constexpr int kStaticMaxM = 8192;                 // largest m accepted
 constexpr int kStaticMaxNb = kStaticMaxM / kT;
 constexpr int64_t kStaticDoubles = 1 << 20;       // 8 MiB of scratch
-constexpr int kStaticMaxItems = kStaticMaxNb * ((kStaticMaxNb + kApplyChunk - 1) / kApplyChunk);
+constexpr int kStaticMaxTiles = kStaticMaxNb * (kStaticMaxNb + 1) / 2;
+constexpr int kStaticGrid = 152 * 2;
 
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
-static __device__ __align__(256) int4 g_static_items[kStaticMaxItems];
+static __device__ __align__(256) TileDesc g_static_desc[kStaticMaxTiles];
+static __device__ __align__(256) int g_static_cta[kStaticGrid + 1];
 static __device__ __align__(256) int2 g_static_blocks[kStaticMaxNb];
 static __device__ __align__(256) SubInfo g_static_sub;
 static __device__ __align__(256) int g_static_status;
 
 namespace {
 
-// Describe the single subdomain, its work items and blocks in the static
-// arrays, zero the padding of the gathered p, and clear the status word
-// (the only state that must start at zero; every other slot is overwritten).
+// Describe the single subdomain, its tile descriptors, CTA ranges and blocks
+// in the static arrays, zero the padding of the gathered p, and clear the
+// status word (the only state that must start at zero; every other slot is
+// overwritten).
 template <typename TF>
-__global__ void static_setup_kernel(int m, int nb, int64_t rpart, int64_t tpart, TF* pg) {
+__global__ void static_setup_kernel(int m, int nb, int64_t rpart, int64_t tpart, int grid, TF* pg) {
+  const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
+  const int vr = m - kT * (nb - 1);
   if (threadIdx.x == 0) {
     SubInfo S{};
     S.m = m;
     S.m_pad = nb * kT;
     S.nb = nb;
-    S.vr = m - kT * (nb - 1);
-    S.F = 0;
-    S.qcol = 0;
+    S.vr = vr;
     S.rpart = rpart;
     S.tpart = tpart;
     g_static_sub = S;
     g_static_status = 0;
-    int k = 0;
+    const int ntile = nb * (nb + 1) / 2;
+    int k = 0, cta = 1;
+    g_static_cta[0] = 0;
     for (int b = 0; b < nb; ++b)
-      for (int c = 0; c <= b; c += kApplyChunk) g_static_items[k++] = make_int4(0, b, c, min(c + kApplyChunk, b + 1));
+      for (int c = 0; c * kApplyChunk <= b; ++c) {
+        const int bj0 = c * kApplyChunk, bj1 = min(bj0 + kApplyChunk, b + 1);
+        for (int bj = bj0; bj < bj1; ++bj) {
+          TileDesc d;
+          d.f_ofs = tile_offset(nb, vr, b, bj);
+          d.rows = tile_rows(nb, vr, b);
+          d.flags = (bj == bj0 ? kTileFirst : 0) | (bj == bj1 - 1 ? kTileLast : 0);
+          d.prow = b * kT;
+          d.pcol = bj * kT;
+          d.col_slot = bj < b ? (int)(tpart / kT) + b * (b + 1) / 2 + bj : -1;
+          d.row_slot = (int)(rpart / (kT * kApplyWarps)) + b * nch + c;
+          g_static_desc[k++] = d;
+        }
+        if (cta < grid && (double)k >= (double)ntile * cta / grid) g_static_cta[cta++] = k;
+      }
+    for (; cta <= grid; ++cta) g_static_cta[cta] = k;
   }
   for (int b = threadIdx.x; b < nb; b += blockDim.x) g_static_blocks[b] = make_int2(0, b);
   for (int j = m + threadIdx.x; j < nb * kT; j += blockDim.x) pg[j] = (TF)0;
@@ -388,7 +457,8 @@ __global__ void static_accumulate_kernel(const int* map, int m, const double* qi
 
 struct StaticAddrs {
   double* scratch = nullptr;
-  int4* items = nullptr;
+  TileDesc* desc = nullptr;
+  int* cta = nullptr;
   int2* blocks = nullptr;
   SubInfo* sub = nullptr;
   int* status = nullptr;
@@ -410,7 +480,8 @@ cudaError_t static_addresses(StaticAddrs& out) {
   if (!g_static_ready[dev]) {
     StaticAddrs a;
     if ((e = cudaGetSymbolAddress((void**)&a.scratch, g_static_scratch)) != cudaSuccess) return e;
-    if ((e = cudaGetSymbolAddress((void**)&a.items, g_static_items)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.desc, g_static_desc)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&a.cta, g_static_cta)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.blocks, g_static_blocks)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.sub, g_static_sub)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.status, g_static_status)) != cudaSuccess) return e;
@@ -429,24 +500,24 @@ feti_status apply_one_static_t(int m, const TF* F, const int* map, const double*
   const int64_t ntile = (int64_t)nb * (nb + 1) / 2;
   int nitems = 0;
   for (int b = 0; b < nb; ++b) nitems += b / kApplyChunk + 1;
-  // scratch layout: [pg: m_pad TF][row partials: nb nch kT TF][column partials: ntile kT TF] | [qi: m_pad double]
-  const int64_t n_pg = m_pad, n_row = (int64_t)nb * nch * kT, n_col = ntile * kT;
+  const int grid = std::max(1, std::min(nitems, kStaticGrid));
+  // scratch layout: [pg: m_pad TF, padded][row partials: nb nch kApplyWarps kT TF][column partials: ntile kT TF]
+  //                 | [qi: m_pad double]
+  const int64_t n_pg = ((int64_t)m_pad + kT * kApplyWarps - 1) / (kT * kApplyWarps) * (kT * kApplyWarps);
+  const int64_t n_row = (int64_t)nb * nch * kT * kApplyWarps, n_col = ntile * kT;
   const int64_t qi_ofs = ((n_pg + n_row + n_col) * (int64_t)sizeof(TF) + 255) / 256 * 256 / 8;
-  if (qi_ofs + m_pad > kStaticDoubles || nitems > kStaticMaxItems) return FETI_ERR_ARG;
+  if (qi_ofs + m_pad > kStaticDoubles || ntile > kStaticMaxTiles) return FETI_ERR_ARG;
   StaticAddrs a;
   if (static_addresses(a) != cudaSuccess) return FETI_ERR_CUDA;
   TF* pg = reinterpret_cast<TF*>(a.scratch);
   double* qi = a.scratch + qi_ofs;
-  static_setup_kernel<TF><<<1, 256, 0, st>>>(m, nb, n_pg, n_pg + n_row, pg);
+  static_setup_kernel<TF><<<1, 256, 0, st>>>(m, nb, n_pg, n_pg + n_row, grid, pg);
   scatter_kernel<TF><<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, p, pg);
   DevPlan P{};
   P.sub = a.sub;
-  // row / column partial slots are the offsets S.rpart / S.tpart from the scratch base
-  const size_t smem = apply_tiles_smem(sizeof(TF) == 4);
-  cudaFuncSetAttribute(apply_tiles_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int grid = std::max(1, std::min(nitems, 152 * 2));
-  apply_tiles_kernel<TF><<<grid, kApplyThreads, smem, st>>>(P, a.items, nitems, F, pg, pg, pg, a.status);
-  reduce_cols_kernel<TF><<<std::max(1, (nb + 7) / 8), 256, 0, st>>>(P, a.blocks, nb, pg, pg, qi);
+  // row / column partial slots are offsets from the scratch base (S.rpart / S.tpart)
+  launch_tiles<TF>(ApplyCfg<TF>::kStages, grid, st, a.desc, a.cta, F, pg, pg, pg, a.status);
+  reduce_cols_kernel<TF><<<std::max(1, (nb + 7) / 8), 256, 0, st>>>(P, a.blocks, nb, pg, pg, qi, 1);
   static_accumulate_kernel<<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, qi, q);
   if (cudaGetLastError() != cudaSuccess) return FETI_ERR_CUDA;
   int status = 0;

@@ -298,11 +298,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
       const int col = BJ * kM + cc * 32;
       const int bj = col / kT;
       if (bi < S.nb && bj < S.nb && bj <= bi && (row % kT) < tile_rows(S.nb, S.vr, bi)) {
-        float* dst = F + S.F + tile_offset(S.nb, S.vr, bi, bj) + (row % kT) * kT + (col % kT);
+        float* tb = F + S.F + tile_offset(S.nb, S.vr, bi, bj);
 #pragma unroll
         for (int e = 0; e < 32; e += 4)
-          *reinterpret_cast<float4*>(dst + e) = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
-                                                            __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+          *reinterpret_cast<float4*>(tb + tile_pos<4>(row % kT, col % kT + e)) =
+              make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                          __uint_as_float(v[e + 3]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) syrk_f64_kernel(DevPlan P, const int
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v)
-        if (ty + 16 * u < nrow) Ft[(ty + 16 * u) * kT + tx + 16 * v] = acc[u][v];
+        if (ty + 16 * u < nrow) Ft[tile_pos<8>(ty + 16 * u, tx + 16 * v)] = acc[u][v];
   }
 }
 
@@ -84,7 +84,7 @@ __global__ void unpack_F_kernel(const TF* Fsub, int m, int nb, int vr, const int
       i = j;
       j = t;
     }
-    const double v = (double)Fsub[tile_offset(nb, vr, i / kT, j / kT) + (i % kT) * kT + (j % kT)];
+    const double v = (double)Fsub[tile_offset(nb, vr, i / kT, j / kT) + tile_pos<sizeof(TF)>(i % kT, j % kT)];
     out[(int64_t)colperm[(int)(g / m)] * m + colperm[(int)(g % m)]] = v;
   }
 }

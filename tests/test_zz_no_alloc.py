@@ -19,18 +19,26 @@ from paper_2502_08382_gb300.problems import make_problem, seeded_vector
 pytestmark = pytest.mark.gpu
 
 
-def _tiles(F):
-    """Lay a dense m x m symmetric F out as 64 x 64 lower tiles, the last block row ragged."""
+def _tiles(F, esz):
+    """Lay a dense m x m symmetric F out as 64 x 64 lower tiles in the documented
+    layout: the last block row ragged, 16-byte chunks of row r XOR-permuted by r."""
     m = F.shape[0]
     nb = (m + 63) // 64
     vr = m - 64 * (nb - 1)
     Fp = np.zeros((nb * 64, nb * 64))
     Fp[:m, :m] = F
+    w = 16 // esz
+    nch = 64 // w
     out = []
     for bi in range(nb):
         rows = 64 if bi < nb - 1 else vr
         for bj in range(bi + 1):
-            out.append(Fp[bi * 64:bi * 64 + rows, bj * 64:(bj + 1) * 64].ravel())
+            t = Fp[bi * 64:bi * 64 + rows, bj * 64:(bj + 1) * 64]
+            st = np.zeros_like(t)
+            for r in range(rows):
+                for c in range(64):
+                    st[r, ((c // w) ^ (r % nch)) * w + c % w] = t[r, c]
+            out.append(st.ravel())
     return np.concatenate(out)
 
 
@@ -49,7 +57,7 @@ def test_apply_one_static_matches_feti_apply(prec):
     dt = torch.float32 if prec != "fp64" else torch.float64
     Fdev, maps = [], []
     for i, s in enumerate(P.subs):
-        Fdev.append(torch.from_numpy(_tiles(op.get_F(i))).to(dt).cuda())
+        Fdev.append(torch.from_numpy(_tiles(op.get_F(i), 8 if prec == "fp64" else 4)).to(dt).cuda())
         maps.append(torch.from_numpy(np.asarray(s.B_lambda, dtype=np.int32)).cuda())
     p = torch.from_numpy(seeded_vector(P.n_lambda, 9)).cuda()
     q_ref = op.apply(p)
