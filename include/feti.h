@@ -89,7 +89,7 @@ typedef struct {
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
   void* stream;               /* cudaStream_t; NULL = legacy default stream */
-  int32_t leaf_dofs;          /* nested-dissection leaf size (0 = 64) */
+  int32_t leaf_dofs;          /* nested-dissection leaf size (0 = 16) */
   int32_t use_coords;         /* 1 = coordinate bisection when coords are given */
 } feti_options;
 
@@ -177,8 +177,10 @@ void feti_destroy(feti_ctx* ctx);
  * info[0..15] = {n, nsn, max_front, max_width, nnzL, chol_flops, Lsize,
  * m, Xsize, trsm_flops, syrk_flops, ntile_contrib, chol_stack, rhs_stack,
  * nroots, 0} and, if perm_out is not NULL, the fill-reducing permutation
- * (perm_out[new] = old DOF).  sn_out, if not NULL, receives
- * [nsn first columns..., nsn widths..., nsn parents...]. */
+ * (perm_out[new] = old DOF).  sn_out, if not NULL (room for 4 n ints),
+ * receives [nsn first columns..., nsn widths..., nsn parents (-1: root)...,
+ * nsn counts of rows below the diagonal block...] of the supernodes in
+ * postorder.  Errors: FETI_ERR_ARG for NULL sub/info or an invalid pattern. */
 feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, double* info,
                          int32_t* perm_out, int32_t* sn_out);
 

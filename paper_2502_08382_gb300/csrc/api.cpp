@@ -172,7 +172,7 @@ void build(feti_ctx* c) {
     }
   }
   SymbolicOptions so;
-  so.leaf_dofs = c->opt.leaf_dofs > 0 ? c->opt.leaf_dofs : 64;
+  so.leaf_dofs = c->opt.leaf_dofs > 0 ? c->opt.leaf_dofs : 16;
   so.use_coords = c->opt.use_coords != 0;
   c->pats.resize(pat_rep.size());
   parallel_for((int)pat_rep.size(), [&](int p) {
@@ -212,7 +212,9 @@ void build(feti_ctx* c) {
 
   // ---- concatenate pattern tables
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
-  std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs;
+  std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs;
+  std::vector<int> lvl_off, lvl_sn, pat_lvl0(c->pats.size());
+  int64_t max_usize = 0;
   std::vector<int> pat_sn0(c->pats.size());
   std::vector<int64_t> pat_diag0(c->pats.size());
   for (size_t p = 0; p < c->pats.size(); ++p) {
@@ -230,7 +232,16 @@ void build(feti_ctx* c) {
       Lofs.push_back(P.Lofs[s]);
       kmap_off.push_back(km0 + P.kmap_off[s]);
       upd_ofs.push_back(P.upd_stack_ofs[s]);
+      uofs.push_back(P.uofs[s]);
     }
+    pat_lvl0[p] = (int)lvl_off.size();
+    {
+      const int b0 = (int)lvl_sn.size();
+      for (int l = 0; l <= P.nlev; ++l) lvl_off.push_back(b0 + P.lvl_off[l]);
+      lvl_sn.insert(lvl_sn.end(), P.lvl_sn.begin(), P.lvl_sn.end());
+    }
+    max_usize = std::max(max_usize, P.usize);
+    c->impl_maxf = std::max(c->impl_maxf, P.max_f);
     rows.insert(rows.end(), P.rows.begin(), P.rows.end());
     ch_list.insert(ch_list.end(), P.ch_list.begin(), P.ch_list.end());
     rel.insert(rel.end(), P.rel.begin(), P.rel.end());
@@ -310,6 +321,8 @@ void build(feti_ctx* c) {
     I.t20 = bp_t20[s.bp];
     I.nb2 = B.nb2;
     I.vr = B.nb > 0 ? s.m - kT * (B.nb - 1) : 0;
+    I.nlev = P.nlev;
+    I.lvl0 = pat_lvl0[s.pat];
     I.fix0 = fixo;
     I.alpha0 = alo;
     I.kmapb = 0;
@@ -546,6 +559,9 @@ void build(feti_ctx* c) {
   D.kmap_dst = upload(c, kmap_dst);
   D.diag_src = upload(c, diag_src);
   D.upd_ofs = upload(c, upd_ofs);
+  D.lvl_off = upload(c, lvl_off);
+  D.lvl_sn = upload(c, lvl_sn);
+  D.uofs = upload(c, uofs);
   D.jb = upload(c, jb);
   D.je = upload(c, je);
   D.jo = upload(c, jo);
@@ -590,6 +606,7 @@ void build(feti_ctx* c) {
   D.Kval = c->d_Kval;
   c->d_L = (double*)dalloc(c, (size_t)Lo * 8);
   D.L = c->d_L;
+  D.dinv = (double*)dalloc(c, (size_t)std::max<int64_t>(c->ndof, 1) * 8);
   D.rho = (double*)dalloc(c, (size_t)ns * 8);
   c->d_X = dalloc(c, (size_t)Xo * esz);
   c->d_F = dalloc(c, (size_t)Fo * esz);
@@ -655,10 +672,12 @@ void build(feti_ctx* c) {
     CK(cudaMallocHost((void**)&c->h_sc, 16 * 8));
     launch_build_G(D, c->d_colsub, qo, c->d_R, c->d_G6, c->st);
     CK(cudaGetLastError());
-    size_t sm = implicit_smem(c->nmax);
+    size_t sm = implicit_smem(c->nmax, c->impl_maxf);
     if (sm > 227 * 1024) throw ArgError("subdomain too large for the shared-memory implicit solve");
     c->impl_smem = sm;
     c->grid_impl = std::min(ns, c->nsm * implicit_occupancy(sm));
+    c->ustride = std::max<int64_t>((max_usize + 31) / 32 * 32, 32);
+    c->d_uws = (double*)dalloc(c, (size_t)c->grid_impl * c->ustride * 8);
   }
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
   CK(cudaMemsetAsync(c->d_tpart, 0, (size_t)std::max<int64_t>(tpo, 1) * 8, c->st));
@@ -759,7 +778,8 @@ feti_status feti_assemble(feti_ctx* ctx) {
   CK(cudaEventRecord(ctx->ev[0], st));
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
               ctx->grid_chol, ctx->d_status, st);
-  ctx->stats.launches += 3;  // Cholesky, pruned TRSM, SYRK
+  launch_diag_recip(ctx->P, ctx->nsub, ctx->P.dinv, st);
+  ctx->stats.launches += 4;  // Cholesky, reciprocal pivots, pruned TRSM, SYRK
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
@@ -954,7 +974,7 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
     copy_sub(*sub, h, 0);
     SymbolicOptions so;
     if (opt) {
-      so.leaf_dofs = opt->leaf_dofs > 0 ? opt->leaf_dofs : 64;
+      so.leaf_dofs = opt->leaf_dofs > 0 ? opt->leaf_dofs : 16;
       so.use_coords = opt->use_coords != 0;
     }
     PatternPlan P;
@@ -972,6 +992,7 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
       std::copy(P.sn_c0.begin(), P.sn_c0.end(), sn_out);
       std::copy(P.sn_w.begin(), P.sn_w.end(), sn_out + P.nsn);
       std::copy(P.sn_parent.begin(), P.sn_parent.end(), sn_out + 2 * P.nsn);
+      std::copy(P.sn_r.begin(), P.sn_r.end(), sn_out + 3 * P.nsn);
     }
     return FETI_OK;
   } catch (std::exception& e) {

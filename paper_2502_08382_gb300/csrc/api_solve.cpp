@@ -44,7 +44,8 @@ void implicit_apply(feti_ctx* c, const double* p, double* q) {
     CKS(cudaEventRecord(ev.a, c->st));
   }
   queue_reset(c, 32);
-  launch_implicit(0, c->P, c->d_impl_order, c->nsub, c->d_queue + 32, p, c->d_f, c->d_qi, nullptr, c->grid_impl,
+  launch_implicit(0, c->P, c->d_impl_order, c->nsub, c->d_queue + 32, p, c->d_f, c->d_qi, nullptr, c->d_uws,
+                  c->ustride, c->nmax, c->impl_maxf, c->grid_impl,
                   c->impl_smem, c->st);
   launch_gather_lambda(c->d_c0, c->d_c1, c->nlam, c->d_qi, q, c->st);
   c->stats.launches += 2;
@@ -159,7 +160,7 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     // d = B K^+ f - c
     queue_reset(ctx, 32);
     launch_implicit(1, ctx->P, ctx->d_impl_order, ctx->nsub, ctx->d_queue + 32, nullptr, ctx->d_f, ctx->d_qi,
-                    nullptr, ctx->grid_impl, ctx->impl_smem, st);
+                    nullptr, ctx->d_uws, ctx->ustride, ctx->nmax, ctx->impl_maxf, ctx->grid_impl, ctx->impl_smem, st);
     launch_gather_minus_c(ctx->d_c0, ctx->d_c1, n, ctx->d_qi, ctx->d_c, d, st);
     // r0 = d - F lambda_0 (FP64 implicit), w0 = P r0, y0 = w0 (M = I), p0 = y0
     implicit_apply(ctx, lam, q);
@@ -226,7 +227,7 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     if (u_dev) {
       queue_reset(ctx, 32);
       launch_implicit(2, ctx->P, ctx->d_impl_order, ctx->nsub, ctx->d_queue + 32, lam, ctx->d_f, nullptr, u_dev,
-                      ctx->grid_impl, ctx->impl_smem, st);
+                      ctx->d_uws, ctx->ustride, ctx->nmax, ctx->impl_maxf, ctx->grid_impl, ctx->impl_smem, st);
       if (D > 0) launch_add_Ralpha(ctx->P, ctx->d_dofsub, ctx->ndof, ctx->d_R, alpha, u_dev, st);
     }
     CKS(cudaGetLastError());
@@ -268,7 +269,7 @@ feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev)
         // Z = K_reg^{-1} B^T (rows: original DOFs, columns: B rows), FP64, recomputed here
         queue_reset(ctx, 33);
         launch_implicit(3, ctx->P, ctx->d_ident + i, m, ctx->d_queue + 33, nullptr, nullptr, nullptr, ctx->d_Z,
-                        ctx->grid_impl, ctx->impl_smem, st);
+                        ctx->d_uws, ctx->ustride, ctx->nmax, ctx->impl_maxf, ctx->grid_impl, ctx->impl_smem, st);
         // Y = Z W_i
         launch_gemm64(n, m, m, 1.0, ctx->d_Z, m, 0, W_dev + woff, m, 0, 0.0, ctx->d_Y, m, 0, 0, st);
         // dtheta_e = -scale_e <dK_ref, (Y Z^T)_e>

@@ -28,6 +28,8 @@ struct SubInfo {
   int t20;           // bplan t2_off base (128 x 128 tiles)
   int nb2;           // 128-wide blocks
   int vr;            // rows of the last block row (m - kT (nb - 1)); that row stores only these
+  int nlev;          // levels of the supernodal tree
+  int lvl0;          // pattern level-offset base (lvl_off, nlev + 1 entries)
   int64_t kmapb;     // base of this pattern's kmap entries (kmap_off values are absolute)
   int64_t diag0;     // diag_src base
   int64_t Kval;      // subdomain K values base
@@ -61,6 +63,10 @@ struct DevPlan {
   const int* kmap_dst;       // relative to the subdomain's L base
   const int* diag_src;       // relative to the subdomain's K values
   const int64_t* upd_ofs;    // [sn] relative to the CTA stack
+  const int* lvl_off;        // [lvl0 + l] absolute offsets into lvl_sn
+  const int* lvl_sn;         // local supernode ids, level by level
+  const int64_t* uofs;       // [sn] update-vector offset of the supernode (relative to the CTA workspace)
+  double* dinv;              // [dof + j] reciprocal pivots 1 / L_jj (written after the factorisation)
   // bplan tables
   const int* jb;
   const int* je;

@@ -91,6 +91,9 @@ struct feti_ctx {
   int64_t ncols = 0;
   int grid_chol = 0, grid_trsm = 0, grid_impl = 0;
   size_t impl_smem = 0;
+  double* d_uws = nullptr;  // update vectors of the implicit solve, ustride doubles per CTA
+  int64_t ustride = 0;
+  int impl_maxf = 0;
   // solve-side data
   bool coarse_ready = false;
   int npairs = 0;

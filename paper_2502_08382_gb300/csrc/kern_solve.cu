@@ -23,6 +23,184 @@ __device__ __forceinline__ int pop_item_s(int* queue) {
   return item;
 }
 
+constexpr int kWF = 128;  // largest front handled by one warp (needs w <= 32)
+
+// One warp: forward step of a small supernode (w <= 32, w + r <= kWF).
+// Lane l keeps entry l of the column block in a register; the rows part
+// lives in registers b[q] (rows w + l + 32 q).  Columns of L are read
+// contiguously; pivots are multiplied by their precomputed reciprocals.
+__device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
+                                         double* ubuf, double* y, double* v, int lane) {
+  const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
+  const double* Ls = P.L + S.L + P.Lofs[gs];
+  for (int i = lane; i < f_; i += 32) v[i] = i < w ? y[c0 + i] : 0.0;
+  __syncwarp();
+  for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
+    const int gc = S.sn0 + P.ch_list[c];
+    const int rc = P.sn_r[gc];
+    const double* U = ubuf + P.uofs[gc];
+    const int* rl = P.rel + P.rel_off[gc];
+    for (int k = lane; k < rc; k += 32) v[rl[k]] += U[k];
+    __syncwarp();
+  }
+  double a = lane < w ? v[lane] : 0.0;
+  const double di = lane < w ? dinv[c0 + lane] : 0.0;
+  double b[kWF / 32];
+#pragma unroll
+  for (int q = 0; q < kWF / 32; ++q) {
+    const int i = w + lane + 32 * q;
+    b[q] = i < f_ ? v[i] : 0.0;
+  }
+  const int nq = (r + 31) / 32;  // warp-uniform
+  for (int j = 0; j < w; ++j) {
+    const double* col = Ls + (int64_t)j * f_;
+    const double zj = __shfl_sync(0xffffffffu, a * di, j);
+    if (lane == j) a = zj;
+    else if (lane > j && lane < w) a -= col[lane] * zj;
+    if (nq > 0) b[0] -= (w + lane < f_ ? col[w + lane] : 0.0) * zj;
+#pragma unroll
+    for (int q = 1; q < kWF / 32; ++q) {
+      if (q < nq) {
+        const int i = w + lane + 32 * q;
+        if (i < f_) b[q] -= col[i] * zj;
+      }
+    }
+  }
+  if (lane < w) y[c0 + lane] = a;
+  double* Us = ubuf + P.uofs[gs];
+#pragma unroll
+  for (int q = 0; q < kWF / 32; ++q) {
+    const int i = lane + 32 * q;
+    if (i < r) Us[i] = b[q];
+  }
+  __syncwarp();
+}
+
+// One warp: backward step of a small supernode.  The rows part
+// t_l = sum_i L21[i][l] x_rows[i] is split over G = 32 / 2^ceil(log2 w)
+// row groups per column (lane = l + wp g), reduced with shuffles; then lane
+// l owns x_l through the triangular sweep.
+__device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
+                                         double* y, double* v, int lane) {
+  const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
+  const double* Ls = P.L + S.L + P.Lofs[gs];
+  const int* rows = P.rows + P.sn_rows[gs];
+  for (int i = lane; i < r; i += 32) v[i] = y[rows[i]];
+  __syncwarp();
+  int wp = 1;
+  while (wp < w) wp <<= 1;
+  const int G = 32 / wp, l = lane % wp, g = lane / wp;
+  double t = 0.0;
+  if (l < w) {
+    const double* col = Ls + (int64_t)l * f_ + w;
+    for (int i = g; i < r; i += G) t += col[i] * v[i];
+  }
+  for (int o = wp; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  double x = lane < w ? y[c0 + lane] - t : 0.0;
+  const double di = lane < w ? dinv[c0 + lane] : 0.0;
+  for (int j = w - 1; j >= 0; --j) {
+    const double xj = __shfl_sync(0xffffffffu, x * di, j);
+    if (lane == j) x = xj;
+    else if (lane < j) x -= Ls[(int64_t)lane * f_ + j] * xj;
+  }
+  if (lane < w) y[c0 + lane] = x;
+  __syncwarp();
+}
+
+// Whole CTA: forward step of a large supernode on the shared front vector.
+// 32 x 32 diagonal blocks and their reciprocal pivots are staged in shared
+// memory and solved by warp 0; all threads apply the block's columns to the
+// rest of the front.
+__device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
+                                        double* ubuf, double* y, double* sf, double (*sm_blk)[kW + 1],
+                                        double* sm_rd, int tid) {
+  const int warp = tid / 32, lane = tid % 32;
+  const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
+  const double* Ls = P.L + S.L + P.Lofs[gs];
+  for (int i = tid; i < f_; i += kThreads) sf[i] = i < w ? y[c0 + i] : 0.0;
+  __syncthreads();
+  for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
+    const int gc = S.sn0 + P.ch_list[c];
+    const int rc = P.sn_r[gc];
+    const double* U = ubuf + P.uofs[gc];
+    const int* rl = P.rel + P.rel_off[gc];
+    for (int k = tid; k < rc; k += kThreads) sf[rl[k]] += U[k];
+    __syncthreads();
+  }
+  for (int kb = 0; kb < w; kb += kW) {
+    const int nbk = min(kW, w - kb);
+    for (int idx = tid; idx < nbk * kW; idx += kThreads) {
+      const int k = idx / kW, i = idx % kW;  // column k, row i of the block
+      if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
+    }
+    if (tid < nbk) sm_rd[tid] = dinv[c0 + kb + tid];
+    __syncthreads();
+    if (warp == 0) {
+      double yi = lane < nbk ? sf[kb + lane] : 0.0;
+      for (int k = 0; k < nbk; ++k) {
+        const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
+        if (lane == k) yi = yk;
+        else if (lane > k && lane < nbk) yi -= sm_blk[lane][k] * yk;
+      }
+      if (lane < nbk) sf[kb + lane] = yi;
+    }
+    __syncthreads();
+    for (int i = kb + nbk + tid; i < f_; i += kThreads) {
+      double acc = 0.0;
+      for (int k = 0; k < nbk; ++k) acc += Ls[(int64_t)(kb + k) * f_ + i] * sf[kb + k];
+      sf[i] -= acc;
+    }
+    __syncthreads();
+  }
+  double* Us = ubuf + P.uofs[gs];
+  for (int i = tid; i < f_; i += kThreads) {
+    if (i < w) y[c0 + i] = sf[i];
+    else Us[i - w] = sf[i];
+  }
+  __syncthreads();
+}
+
+// Whole CTA: backward step of a large supernode (x_rows already final).
+__device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
+                                        double* y, double (*sm_blk)[kW + 1], double* sm_rd, int tid) {
+  const int warp = tid / 32, lane = tid % 32;
+  const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
+  const double* Ls = P.L + S.L + P.Lofs[gs];
+  const int* rows = P.rows + P.sn_rows[gs];
+  for (int l = warp; l < w; l += kThreads / 32) {
+    double acc = 0.0;
+    for (int k = lane; k < r; k += 32) acc += Ls[(int64_t)l * f_ + w + k] * y[rows[k]];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[c0 + l] -= acc;
+  }
+  __syncthreads();
+  for (int kb = ((w - 1) / kW) * kW; kb >= 0; kb -= kW) {
+    const int nbk = min(kW, w - kb);
+    for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
+      double acc = 0.0;
+      for (int i = kb + nbk + lane; i < w; i += 32) acc += Ls[(int64_t)l * f_ + i] * y[c0 + i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[c0 + l] -= acc;
+    }
+    for (int idx = tid; idx < nbk * kW; idx += kThreads) {
+      const int k = idx / kW, i = idx % kW;
+      if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
+    }
+    if (tid < nbk) sm_rd[tid] = dinv[c0 + kb + tid];
+    __syncthreads();
+    if (warp == 0) {
+      double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
+      for (int k = nbk - 1; k >= 0; --k) {
+        const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
+        if (lane == k) yi = yk;
+        else if (lane < k) yi -= sm_blk[k][lane] * yk;
+      }
+      if (lane < nbk) y[c0 + kb + lane] = yi;
+    }
+    __syncthreads();
+  }
+}
+
 // MODE 0: qi = B L^-T L^-1 P B^T p        (implicit apply, eq. 11)
 // MODE 1: qi = B K_reg^{-1} f             (d = B K^+ f - c, eq. 7)
 // MODE 2: u  = K_reg^{-1} (f - B^T lambda) (eq. 5 without R alpha)
@@ -32,18 +210,22 @@ __device__ __forceinline__ int pop_item_s(int* queue) {
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                              const double* p, const double* f, double* qi,
-                                                             double* u) {
-  extern __shared__ double y[];
+                                                             double* u, double* uws, int64_t ustride, int nmax,
+                                                             int maxf) {
+  extern __shared__ double y[];  // [nmax] subdomain vector, [maxf] front, [8 kWF] warp fronts
   __shared__ double sm_blk[kW][kW + 1];
   __shared__ double sm_rd[kW];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  double* sfront = y + nmax;
+  double* wbuf = sfront + maxf;
+  double* ubuf = uws + (int64_t)blockIdx.x * ustride;
   for (;;) {
     const int itx = pop_item_s(queue);
     if (itx >= nsub) return;
     const int si = MODE == 3 ? order[0] : order[itx];
     const SubInfo& S = P.sub[si];
     const int n = S.n;
-    const double* L = P.L + S.L;
+    const double* dinv = P.dinv + S.dof;
     for (int k = tid; k < n; k += kThreads) y[k] = 0.0;
     __syncthreads();
     if (MODE == 3 && tid == 0) y[P.spos[S.col0 + itx]] = P.qsign[S.qcol + itx];
@@ -61,80 +243,50 @@ __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int
       }
     }
     __syncthreads();
-    // forward substitution L z = y, supernodes in postorder.  Each 32 x 32
-    // diagonal block and its reciprocal pivots are staged in shared memory
-    // with one coalesced load; warp 0 then solves from shared memory.
-    for (int s = 0; s < S.nsn; ++s) {
-      const int gs = S.sn0 + s;
-      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
-      const double* Ls = L + P.Lofs[gs];
-      const int* rows = P.rows + P.sn_rows[gs];
-      for (int kb = 0; kb < w; kb += kW) {
-        const int nbk = min(kW, w - kb);
-        for (int idx = tid; idx < nbk * kW; idx += kThreads) {
-          const int k = idx / kW, i = idx % kW;  // column k, row i of the block
-          if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
-        }
-        if (tid < nbk) sm_rd[tid] = 1.0 / Ls[(int64_t)(kb + tid) * f_ + kb + tid];
-        __syncthreads();
-        if (warp == 0) {
-          double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
-          for (int k = 0; k < nbk; ++k) {
-            const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
-            if (lane == k) yi = yk;
-            else if (lane > k && lane < nbk) yi -= sm_blk[lane][k] * yk;
-          }
-          if (lane < nbk) y[c0 + kb + lane] = yi;
-        }
-        __syncthreads();
-        for (int i = kb + nbk + tid; i < f_; i += kThreads) {
-          double acc = 0.0;
-          for (int k = 0; k < nbk; ++k) acc += Ls[(int64_t)(kb + k) * f_ + i] * y[c0 + kb + k];
-          const int tgt = i < w ? c0 + i : rows[i - w];
-          y[tgt] -= acc;
-        }
-        __syncthreads();
-      }
-    }
-    // backward substitution L^T x = z, supernodes in reverse postorder
-    for (int s = S.nsn - 1; s >= 0; --s) {
-      const int gs = S.sn0 + s;
-      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
-      const double* Ls = L + P.Lofs[gs];
-      const int* rows = P.rows + P.sn_rows[gs];
-      for (int l = warp; l < w; l += kThreads / 32) {
-        double acc = 0.0;
-        for (int k = lane; k < r; k += 32) acc += Ls[(int64_t)l * f_ + w + k] * y[rows[k]];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[c0 + l] -= acc;
+    // forward substitution L z = y, level by level from the leaves of the
+    // supernodal tree.  Supernodes of one level are independent: each one
+    // assembles its front vector from its own columns of y and the update
+    // vectors of its children (in fixed order, so the result is
+    // deterministic), solves with its diagonal block and writes its own
+    // update vector for the parent.  Small fronts take one warp each, large
+    // ones the whole CTA.
+    const int* lvo = P.lvl_off + S.lvl0;
+    const int* lsn = P.lvl_sn;
+    for (int l = 0; l < S.nlev; ++l) {
+      const int lo = lvo[l], hi = lvo[l + 1];
+      for (int it = lo + warp; it < hi; it += kThreads / 32) {
+        const int gs = S.sn0 + lsn[it];
+        const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+        if (w > 32 || f_ > kWF) continue;
+        fwd_warp(P, S, gs, dinv, ubuf, y, wbuf + warp * kWF, lane);
       }
       __syncthreads();
-      for (int kb = ((w - 1) / kW) * kW; kb >= 0; kb -= kW) {
-        const int nbk = min(kW, w - kb);
-        for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
-          double acc = 0.0;
-          for (int i = kb + nbk + lane; i < w; i += 32) acc += Ls[(int64_t)l * f_ + i] * y[c0 + i];
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) y[c0 + l] -= acc;
-        }
-        for (int idx = tid; idx < nbk * kW; idx += kThreads) {
-          const int k = idx / kW, i = idx % kW;
-          if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
-        }
-        if (tid < nbk) sm_rd[tid] = 1.0 / Ls[(int64_t)(kb + tid) * f_ + kb + tid];
-        __syncthreads();
-        if (warp == 0) {
-          double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
-          for (int k = nbk - 1; k >= 0; --k) {
-            const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
-            if (lane == k) yi = yk;
-            else if (lane < k) yi -= sm_blk[k][lane] * yk;
-          }
-          if (lane < nbk) y[c0 + kb + lane] = yi;
-        }
-        __syncthreads();
+      for (int it = lo; it < hi; ++it) {
+        const int gs = S.sn0 + lsn[it];
+        const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+        if (w <= 32 && f_ <= kWF) continue;
+        fwd_cta(P, S, gs, dinv, ubuf, y, sfront, sm_blk, sm_rd, tid);
       }
     }
+    // backward substitution L^T x = z, level by level from the roots; every
+    // supernode reads only ancestors' entries of x and writes its own columns
+    for (int l = S.nlev - 1; l >= 0; --l) {
+      const int lo = lvo[l], hi = lvo[l + 1];
+      for (int it = lo + warp; it < hi; it += kThreads / 32) {
+        const int gs = S.sn0 + lsn[it];
+        const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+        if (w > 32 || f_ > kWF) continue;
+        bwd_warp(P, S, gs, dinv, y, wbuf + warp * kWF, lane);
+      }
+      __syncthreads();
+      for (int it = lo; it < hi; ++it) {
+        const int gs = S.sn0 + lsn[it];
+        const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+        if (w <= 32 && f_ <= kWF) continue;
+        bwd_cta(P, S, gs, dinv, y, sm_blk, sm_rd, tid);
+      }
+    }
+    __syncthreads();
     if (MODE == 0 || MODE == 1) {
       for (int j = tid; j < S.m_pad; j += kThreads)
         qi[S.qcol + j] = j < S.m ? P.qsign[S.qcol + j] * y[P.spos[S.col0 + j]] : 0.0;
@@ -145,6 +297,21 @@ __global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int
       for (int k = tid; k < n; k += kThreads) u[(int64_t)k * S.m + col] = y[P.iperm[S.diag0 + k]];
     }
     __syncthreads();
+  }
+}
+
+// dinv[dof + j] = 1 / L_jj for every column of every subdomain (one
+// warp per supernode), so that the triangular solves multiply.
+__global__ void __launch_bounds__(256) diag_recip_kernel(DevPlan P, int nsub, double* dinv) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int si = blockIdx.x; si < nsub; si += gridDim.x) {
+    const SubInfo& S = P.sub[si];
+    for (int s = warp; s < S.nsn; s += 8) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+      const double* Ls = P.L + S.L + P.Lofs[gs];
+      for (int k = lane; k < w; k += 32) dinv[S.dof + c0 + k] = 1.0 / Ls[(int64_t)k * f_ + k];
+    }
   }
 }
 
@@ -479,7 +646,7 @@ inline int grid_for(int64_t n, int per = 256, int cap = 152 * 16) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, cap));
 }
 
-size_t implicit_smem(int nmax) { return (size_t)nmax * 8; }
+size_t implicit_smem(int nmax, int maxf) { return ((size_t)nmax + maxf + (kThreads / 32) * kWF) * 8; }
 
 void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKref, const double* dscale,
                           const double* Z, const double* Y, int m, double* g, cudaStream_t st) {
@@ -488,20 +655,29 @@ void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKr
 }
 
 void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
-                     const double* f, double* qi, double* u, int grid, size_t smem, cudaStream_t st) {
+                     const double* f, double* qi, double* u, double* uws, int64_t ustride, int nmax, int maxf,
+                     int grid, size_t smem, cudaStream_t st) {
   if (mode == 3) {
     cudaFuncSetAttribute(implicit_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    implicit_kernel<3><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+    implicit_kernel<3><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u, uws, ustride, nmax,
+                                                        maxf);
   } else if (mode == 0) {
     cudaFuncSetAttribute(implicit_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    implicit_kernel<0><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+    implicit_kernel<0><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u, uws, ustride, nmax,
+                                                        maxf);
   } else if (mode == 1) {
     cudaFuncSetAttribute(implicit_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    implicit_kernel<1><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+    implicit_kernel<1><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u, uws, ustride, nmax,
+                                                        maxf);
   } else {
     cudaFuncSetAttribute(implicit_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    implicit_kernel<2><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u);
+    implicit_kernel<2><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, p, f, qi, u, uws, ustride, nmax,
+                                                        maxf);
   }
+}
+
+void launch_diag_recip(const DevPlan& P, int nsub, double* dinv, cudaStream_t st) {
+  diag_recip_kernel<<<std::min(nsub, 152 * 8), 256, 0, st>>>(P, nsub, dinv);
 }
 
 int implicit_occupancy(size_t smem) {

@@ -516,6 +516,31 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
       if (col[k] == r) P.diag_src[r] = (int)k;
     if (P.diag_src[r] < 0) throw std::runtime_error("K has a structurally zero diagonal");
   }
+  // level schedule (height: leaves 0, parent = 1 + max child) and update vectors
+  {
+    std::vector<int> ht(ns, 0);
+    for (int s = 0; s < ns; ++s)
+      for (int c : kids[s]) ht[s] = std::max(ht[s], ht[c] + 1);
+    P.nlev = 0;
+    for (int s = 0; s < ns; ++s) P.nlev = std::max(P.nlev, ht[s] + 1);
+    std::vector<std::vector<int>> lv(P.nlev);
+    for (int s = 0; s < ns; ++s) lv[ht[s]].push_back(s);
+    P.lvl_off.assign(P.nlev + 1, 0);
+    for (int l = 0; l < P.nlev; ++l) {
+      std::stable_sort(lv[l].begin(), lv[l].end(), [&](int a, int b) {
+        return (int64_t)P.sn_w[a] * (P.sn_w[a] + P.sn_r[a]) < (int64_t)P.sn_w[b] * (P.sn_w[b] + P.sn_r[b]);
+      });
+      P.lvl_off[l + 1] = P.lvl_off[l] + (int)lv[l].size();
+      P.lvl_sn.insert(P.lvl_sn.end(), lv[l].begin(), lv[l].end());
+    }
+    P.uofs.assign(ns, 0);
+    int64_t u = 0;
+    for (int s = 0; s < ns; ++s) {
+      P.uofs[s] = u;
+      u += P.sn_r[s];
+    }
+    P.usize = u;
+  }
   // multifrontal update stack (postorder => children's blocks sit on top)
   P.upd_stack_ofs.assign(ns, 0);
   {

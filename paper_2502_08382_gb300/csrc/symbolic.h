@@ -41,6 +41,12 @@ struct PatternPlan {
   int64_t chol_front = 0;            // max r*r (doubles)
   int max_f = 0, max_w = 0;
   double chol_flops = 0, nnzL = 0;
+  // level schedule of the supernodal tree (height from the leaves), small
+  // supernodes before large ones inside a level; update-vector offsets
+  int nlev = 0;
+  std::vector<int> lvl_off, lvl_sn;
+  std::vector<int64_t> uofs;  // per supernode, offset of its r-vector
+  int64_t usize = 0;
 };
 
 struct BPlan {
@@ -60,7 +66,7 @@ struct BPlan {
 };
 
 struct SymbolicOptions {
-  int leaf_dofs = 64;
+  int leaf_dofs = 16;
   bool use_coords = true;
 };
 

@@ -177,7 +177,7 @@ def subdomain_struct(s, keep):
     return m.subs[0]
 
 
-def analyse(sub, leaf_dofs=64, use_coords=True):
+def analyse(sub, leaf_dofs=16, use_coords=True):
     """Host-only symbolic analysis of one subdomain (no GPU): returns a dict
     of the plan's statistics, the permutation and the supernode partition."""
     lib = load_library()
@@ -188,7 +188,7 @@ def analyse(sub, leaf_dofs=64, use_coords=True):
     opt.use_coords = 1 if use_coords else 0
     info = np.zeros(16)
     perm = np.zeros(sub.n, dtype=np.int32)
-    snb = np.zeros(3 * sub.n, dtype=np.int32)
+    snb = np.zeros(4 * sub.n, dtype=np.int32)
     rc = lib.feti_analyse(C.byref(st), C.byref(opt), _ptr(info, C.c_double), _ptr(perm, C.c_int32),
                           _ptr(snb, C.c_int32))
     if rc != FETI_OK:
@@ -201,6 +201,7 @@ def analyse(sub, leaf_dofs=64, use_coords=True):
     out["sn_c0"] = snb[:ns].copy()
     out["sn_w"] = snb[ns:2 * ns].copy()
     out["sn_parent"] = snb[2 * ns:3 * ns].copy()
+    out["sn_r"] = snb[3 * ns:4 * ns].copy()
     return out
 
 
@@ -209,7 +210,7 @@ class FetiOperator:
     feti_apply / feti_apply_implicit / feti_solve / feti_adjoint)."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
-                 refine_every: int = 0, leaf_dofs: int = 64, use_coords: bool = True,
+                 refine_every: int = 0, leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
         import torch
         self.torch = torch
