@@ -119,7 +119,7 @@ typedef struct {
   int64_t implicit_calls;     /* implicit-operator applications (feti_apply_implicit and inside feti_solve) */
   double implicit_ms;         /* CUDA-event time of those applications */
   /* autotuner choice for the apply (after the first feti_assemble) */
-  int32_t apply_stages, apply_grid;
+  int32_t apply_variant, apply_grid;  /* tile-kernel variant (0: 8-load batches, 1: 16) and grid */
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;
@@ -195,21 +195,21 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
  * pool and forbids other allocations, or a latency-critical loop in which
  * cudaMalloc (which synchronises the device) is not acceptable.  It calls no
  * cudaMalloc, cudaFree or other allocating routine; all intermediates live in
- * fixed device arrays of this library (8 MiB plus small tables), which every
+ * fixed device arrays of this library (12 MiB plus small tables), which every
  * GPU that loads the library holds until the process exits.
  *
  * F_dev: F_i in this library's tile layout, FP32 (fp32 = 1) or FP64 (fp32 = 0),
- *        device memory: 64 x 64 tiles (bi, bj) with bj <= bi stored in the
- *        order bi (bi + 1) / 2 + bj; inside a tile, row r holds 64 values whose
- *        16-byte chunks are permuted: value (r, c) sits at
- *        r * 64 + ((c / w) ^ (r % (64 / w))) * w + c % w, w = 16 / sizeof(value);
- *        the diagonal tiles are stored in full; the last block row
- *        bi = nb - 1 (nb = ceil(m / 64)) holds only m - 64 (nb - 1) rows per
- *        tile; columns of the last block beyond m hold zeros.
+ *        device memory, 16-byte aligned: 64 x 64 tiles (bi, bj) with bj <= bi
+ *        stored one after another in the order bi (bi + 1) / 2 + bj.  An
+ *        off-diagonal tile is row-major, 64 values per row; a diagonal tile
+ *        keeps, for each row r, only its first w ceil((r + 1) / w) values
+ *        (w = 16 / sizeof(value)), rows packed back to back, with zeros right
+ *        of the diagonal.  The last block row bi = nb - 1 (nb = ceil(m / 64))
+ *        holds only m - 64 (nb - 1) rows per tile; columns beyond m hold zeros.
  * map_dev: [m] int32 device array, distinct multiplier ids (rows of F_i).
  * p_dev, q_dev: FP64 device dual vectors; q is accumulated into, not cleared.
  * stream: cudaStream_t or NULL.  The call is synchronous (it waits for the
- *        stream) and returns FETI_ERR_TIMEOUT if a bounded device wait gave up.
+ *        stream).
  * Errors: FETI_ERR_ARG for m <= 0, m > FETI_STATIC_MAX_M or a NULL pointer;
  *        FETI_ERR_CUDA for a failed CUDA call.
  * The first call on each device looks up the device addresses of the fixed

@@ -15,6 +15,7 @@ dense NumPy/SciPy with no blocking or reordering beyond the definition:
   Schur route     F_i = B_T S^{-1} B_T^T, S = Schur complement of K_reg onto
                   the DOFs B touches                          (eq. 13)
   dual data       G = B R, e = R^T f, d = B K^+ f - c         (eqs. 6-7)
+  FETI residuals  K_i u_i + B_i^T lambda - f_i and B u - c     (eq. 3)
   projector       P = I - G (G^T G)^{-1} G^T                  (Sec. II)
   PCPG            Algorithm 1 with M = I, lambda_I = G (G^T G)^{-1} e
   recovery        alpha (eq. 8), u = K^+ (f - B^T lambda) + R alpha (eq. 5)
@@ -123,6 +124,33 @@ def G_matrix(problem) -> np.ndarray:
         G[lam, off:off + s.d] += s.B_sign[:, None] * s.R[s.B_dof, :]
         off += s.d
     return G
+
+
+def Gt_times(problem, lam: np.ndarray) -> np.ndarray:
+    """G^T lam = (R_i^T B_i^T lam)_i without forming G (G = B R, eqs. 6-7):
+    the subdomain's multipliers, signed, summed onto their DOFs, then R_i^T."""
+    out = []
+    for s in problem.subs:
+        v = np.zeros(s.n)
+        np.add.at(v, s.B_dof, s.B_sign * lam[np.asarray(s.B_lambda, dtype=np.int64)])
+        out.append(s.R.T @ v)
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def feti_equation_residuals(problem, lam, us):
+    """Residuals of the FETI system (eq. 3) for a computed (lambda, u):
+    per subdomain ||K_i u_i + B_i^T lambda - f_i|| / ||f_i - B_i^T lambda||
+    (the primal rows) and the gluing / Dirichlet rows B u - c."""
+    prim = []
+    Bu = -np.asarray(problem.c, dtype=np.float64).copy()
+    for s, u in zip(problem.subs, us):
+        K = sp.csr_matrix((s.K_val, s.K_col, s.K_rowptr), shape=(s.n, s.n))
+        btl = np.zeros(s.n)
+        np.add.at(btl, s.B_dof, s.B_sign * lam[np.asarray(s.B_lambda, dtype=np.int64)])
+        rhs = s.f - btl
+        prim.append(np.linalg.norm(K @ u - rhs) / max(np.linalg.norm(rhs), 1e-300))
+        np.add.at(Bu, np.asarray(s.B_lambda, dtype=np.int64), s.B_sign * u[s.B_dof])
+    return np.asarray(prim), Bu
 
 
 def e_vector(problem) -> np.ndarray:

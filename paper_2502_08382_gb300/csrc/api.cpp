@@ -293,7 +293,7 @@ void build(feti_ctx* c) {
   std::vector<double> eldk, elsc;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
-  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, rpo = 0;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
   int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0;
@@ -336,13 +336,12 @@ void build(feti_ctx* c) {
     I.dof = dofo;
     I.R = Ro;
     I.tpart = tpo;
-    I.rpart = rpo;
-    rpo += (int64_t)B.nb * ((B.nb + kApplyChunk - 1) / kApplyChunk) * kT * kApplyWarps;
+    I.rpart = 0;
     int ntile = B.nb * (B.nb + 1) / 2;
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
     Xo += B.Xsize;
-    Fo += F_size(B.nb, I.vr);
+    Fo += F_size_esz((int)esz, B.nb, I.vr);
     qo += B.m_pad;
     dofo += s.n;
     Ro += (int64_t)s.n * s.d;
@@ -392,7 +391,7 @@ void build(feti_ctx* c) {
     max_rhs = std::max(max_rhs, B.rhs_stack);
     max_rf = std::max(max_rf, B.rhs_front);
     apply_bytes += (double)esz * s.m * (s.m + 1) / 2.0 + (double)s.m * (4 + 8 + 8);
-    stored_bytes += (double)esz * F_size(B.nb, I.vr);
+    stored_bytes += (double)esz * F_size_esz((int)esz, B.nb, I.vr);
   }
   apply_bytes += (double)c->nlam * 16.0;
   c->ncols = qo;
@@ -473,7 +472,6 @@ void build(feti_ctx* c) {
   });
   std::vector<std::pair<double, int2>> sy;
   std::vector<TileDesc> tdesc;
-  std::vector<int> item_end;  // tile index one past each work item
   for (int i = 0; i < ns; ++i) {
     auto& B = c->bps[c->subs[i].bp];
     auto& P = c->pats[c->subs[i].pat];
@@ -484,25 +482,19 @@ void build(feti_ctx* c) {
       for (int k = B.tile_off[t]; k < B.tile_off[t + 1]; ++k) cost += P.sn_w[B.tile_sn[k]];
       sy.push_back({cost, make_int2(i, t)});
     }
-    const int nch = (B.nb + kApplyChunk - 1) / kApplyChunk;
+    // one descriptor per tile, in tile order (tile t of the list owns partial slot t)
     for (int b = 0; b < B.nb; ++b)
-      for (int ch = 0; ch * kApplyChunk <= b; ++ch) {
-        const int bj0 = ch * kApplyChunk, bj1 = std::min(bj0 + kApplyChunk, b + 1);
-        for (int bj = bj0; bj < bj1; ++bj) {
-          TileDesc d{};
-          d.f_ofs = I.F + tile_offset(B.nb, I.vr, b, bj);
-          d.rows = tile_rows(B.nb, I.vr, b);
-          d.flags = (bj == bj0 ? kTileFirst : 0) | (bj == bj1 - 1 ? kTileLast : 0);
-          d.prow = (int)(I.qcol + (int64_t)b * kT);
-          d.pcol = (int)(I.qcol + (int64_t)bj * kT);
-          d.col_slot = bj < b ? (int)(I.tpart / kT + (int64_t)b * (b + 1) / 2 + bj) : -1;
-          d.row_slot = (int)(I.rpart / (kT * kApplyWarps) + (int64_t)b * nch + ch);
-          tdesc.push_back(d);
-        }
-        item_end.push_back((int)tdesc.size());
+      for (int bj = 0; bj <= b; ++bj) {
+        TileDesc d{};
+        d.f_ofs = I.F + (c->fp32 ? tile_offset<4>(B.nb, I.vr, b, bj) : tile_offset<8>(B.nb, I.vr, b, bj));
+        d.rows = tile_rows(B.nb, I.vr, b);
+        d.flags = bj == b ? kTileDiag : 0;
+        d.prow = (int)(I.qcol + (int64_t)b * kT);
+        d.pcol = (int)(I.qcol + (int64_t)bj * kT);
+        tdesc.push_back(d);
       }
   }
-  c->napply = (int)item_end.size();
+  c->napply = (int)tdesc.size();
   std::vector<std::pair<double, int2>> sy2;
   for (int i = 0; i < ns; ++i) {
     auto& B = c->bps[c->subs[i].bp];
@@ -613,7 +605,7 @@ void build(feti_ctx* c) {
   c->d_ws = (double*)dalloc(c, (size_t)gw * c->ws_stride * 8);
   c->d_trow = (double*)dalloc(c, (size_t)qo * 8);
   c->d_tpart = (double*)dalloc(c, (size_t)std::max<int64_t>(tpo, 1) * 8);
-  c->d_rowpart = dalloc(c, (size_t)std::max<int64_t>(rpo, 1) * 8);
+  c->d_rowpart = dalloc(c, (size_t)std::max<int64_t>(tpo, 1) * 8);
   c->d_pg = dalloc(c, (size_t)qo * 8);
   c->d_qi = (double*)dalloc(c, (size_t)qo * 8);
   c->d_colsub = upload(c, colsub);
@@ -626,28 +618,18 @@ void build(feti_ctx* c) {
   c->d_impl_order = upload(c, order_i);
   c->d_syrk_items = upload(c, syi);
   {
-    // contiguous, item-aligned tile ranges per CTA of the apply, balanced by
-    // tile count, for every candidate stage count of the autotuner
+    // the apply deals tiles to warps round-robin; candidates of the autotuner:
+    // every variant of the tile kernel at its full occupancy (capped at one tile per warp)
     c->d_tdesc = upload(c, tdesc);
-    const int cands[] = {2, 3, 4, 5, 6};
-    for (int ns : cands) {
-      if (!c->fp32 && ns > 3) continue;
-      const int occ = apply_max_ctas_per_sm(c->fp32, ns);
+    const int wpc = apply_warps_per_cta();
+    for (int v = 0; v < apply_variants(); ++v) {
+      const int occ = apply_max_ctas_per_sm(c->fp32, v);
       if (occ <= 0) continue;
-      const int G = std::max(1, std::min(c->napply, c->nsm * occ));
-      std::vector<int> cb(G + 1, 0);
-      const double per = (double)tdesc.size() / G;
-      int cta = 1;
-      for (size_t it = 0; it < item_end.size() && cta < G; ++it)
-        if (item_end[it] >= per * cta) cb[cta++] = item_end[it];
-      for (; cta <= G; ++cta) cb[cta] = (int)tdesc.size();
-      c->apply_cands.push_back({ns, G, upload(c, cb), 0.0});
+      const int G = std::max(1, std::min((c->napply + wpc - 1) / wpc, c->nsm * occ));
+      c->apply_cands.push_back({v, G, 0.0});
     }
     if (c->apply_cands.empty()) throw CudaError("no launchable configuration of the apply kernel");
-    // default before tuning: the largest stage count that keeps 2 CTAs per SM
-    c->apply_pick = 0;
-    for (size_t k = 0; k < c->apply_cands.size(); ++k)
-      if (c->apply_cands[k].grid >= std::min(c->napply, 2 * c->nsm)) c->apply_pick = (int)k;
+    c->apply_pick = (int)c->apply_cands.size() - 1;
   }
   c->d_syrk2_items = upload(c, sy2i);
   c->d_blocks = upload(c, blocks);
@@ -817,34 +799,29 @@ feti_status feti_assemble(feti_ctx* ctx) {
   ctx->coarse_ready = true;
   ctx->stats.t_assemble_ms = d;
   if (!ctx->apply_tuned) {
-    // autotuner: time every launchable stage count of the apply on this problem, keep the fastest
+    // autotuner: time every variant of the apply tile kernel on this problem, keep the fastest
     double* pz = ctx->d_vec + (size_t)5 * ctx->nlam;
     double* qz = ctx->d_vec + (size_t)6 * ctx->nlam;
     CK(cudaMemsetAsync(pz, 0, (size_t)ctx->nlam * 8, st));
     for (size_t k = 0; k < ctx->apply_cands.size(); ++k) {
       auto& c2 = ctx->apply_cands[k];
-      for (int rep = 0; rep < 2; ++rep)
-        launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, c2.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, pz, ctx->d_pg,
-                     ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
-                     ctx->nlam, qz, c2.grid, ctx->d_status, st, nullptr, nullptr, c2.stages);
-      CK(cudaEventRecord(ctx->ev[5], st));
-      for (int rep = 0; rep < 5; ++rep)
-        launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, c2.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, pz, ctx->d_pg,
-                     ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
-                     ctx->nlam, qz, c2.grid, ctx->d_status, st, nullptr, nullptr, c2.stages);
+      for (int rep = 0; rep < 7; ++rep) {
+        if (rep == 2) CK(cudaEventRecord(ctx->ev[5], st));
+        launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, pz,
+                     ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0,
+                     ctx->d_c1, ctx->nlam, qz, c2.grid, c2.variant, st);
+      }
       CK(cudaEventRecord(ctx->ev[6], st));
       CK(cudaEventSynchronize(ctx->ev[6]));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[6]));
       c2.ms = ms / 5;
-      if (ms / 5 < ctx->apply_cands[ctx->apply_pick].ms || ctx->apply_cands[ctx->apply_pick].ms == 0.0 ||
-          k == 0)
-        ctx->apply_pick = (int)k;
     }
-    for (size_t k = 0; k < ctx->apply_cands.size(); ++k)
+    ctx->apply_pick = 0;
+    for (size_t k = 1; k < ctx->apply_cands.size(); ++k)
       if (ctx->apply_cands[k].ms < ctx->apply_cands[ctx->apply_pick].ms) ctx->apply_pick = (int)k;
     ctx->apply_tuned = true;
-    ctx->stats.apply_stages = ctx->apply_cands[ctx->apply_pick].stages;
+    ctx->stats.apply_variant = ctx->apply_cands[ctx->apply_pick].variant;
     ctx->stats.apply_grid = ctx->apply_cands[ctx->apply_pick].grid;
   }
   int status = 0;
@@ -869,9 +846,9 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
     ev = {ctx->take_event(), ctx->take_event(), ctx->take_event(), ctx->take_event(), 0};
     CK(cudaEventRecord(ev.a, st));
   }
-  launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, cand.cta_begin, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev,
-               ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1,
-               ctx->nlam, q_dev, grid, ctx->d_status, st, ev.b, ev.c, cand.stages);
+  launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev, ctx->d_pg,
+               ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1, ctx->nlam,
+               q_dev, grid, cand.variant, st, ev.b, ev.c);
   ctx->stats.launches += 4;
   ctx->stats.apply_calls += 1;
   if (ctx->prof) {

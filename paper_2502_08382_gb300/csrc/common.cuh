@@ -13,8 +13,6 @@ namespace feti {
 constexpr int kT = 64;          // F tile edge
 constexpr int kThreads = 256;   // CTA size of the dense kernels
 constexpr int kNB = 32;         // panel block of the dense factorisation / solve
-constexpr int kApplyChunk = 8;  // tiles per apply work item (one tile row is cut into chunks)
-constexpr int kApplyWarps = 8;  // consumer warps of the apply; row partials are kept per warp
 
 struct SubInfo {
   int n, m, m_pad, nb, nsn, nact, d, nfix;
@@ -39,9 +37,9 @@ struct SubInfo {
   int64_t qcol;      // subdomain sorted-column arrays base (m_pad entries)
   int64_t dof;       // subdomain DOF-vector base (n entries)
   int64_t R;         // subdomain R base (n*d, column-major)
-  int64_t trow;      // base of this subdomain's tile-row partials (nb*kT entries) == qcol
-  int64_t tpart;     // base of this subdomain's per-tile column partials (ntile*kT entries)
-  int64_t rpart;     // base of this subdomain's row partials (nb * ceil(nb / kApplyChunk) * kT entries)
+  int64_t trow;      // == qcol (unused)
+  int64_t tpart;     // first apply tile of this subdomain times kT (its row / column partial slots)
+  int64_t rpart;     // unused
 };
 
 struct DevPlan {
@@ -93,35 +91,49 @@ struct DevPlan {
   double* rho;               // [nsub]
 };
 
-// F_i storage: lower tiles (bi, bj), bj <= bi, tile rows kT wide; block row
-// bi < nb - 1 holds kT rows per tile, the last block row only S.vr rows.
+// F_i storage: lower tiles (bi, bj), bj <= bi, in the order bi (bi + 1) / 2 + bj.
+// Off-diagonal tiles are row-major kT x kT; block row bi < nb - 1 holds kT
+// rows per tile, the last block row only S.vr rows.  A diagonal tile keeps, for
+// each row r, only the 16-byte chunks up to and including the one that holds
+// column r (ceil((r + 1) / V) chunks of V = 16 / ESZ values), rows packed back
+// to back; the entries right of the diagonal inside that last chunk are zero.
+// Every tile and every row of a diagonal tile starts on a 16-byte boundary.
+template <int ESZ>
+__host__ __device__ inline int64_t diag_row_off(int r) {
+  constexpr int V = 16 / ESZ;
+  const int64_t q = r / V;
+  return (int64_t)V * ((int64_t)V * q * (q + 1) / 2 + (int64_t)(r - V * q) * (q + 1));
+}
+template <int ESZ>
 __host__ __device__ inline int64_t tile_offset(int nb, int vr, int bi, int bj) {
-  if (bi < nb - 1) return ((int64_t)bi * (bi + 1) / 2 + bj) * kT * kT;
-  return ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)bj * vr * kT;
+  const int64_t dk = diag_row_off<ESZ>(kT);
+  if (bi < nb - 1) return (int64_t)kT * kT * bi * (bi - 1) / 2 + (int64_t)bi * dk + (int64_t)bj * kT * kT;
+  const int64_t base = (int64_t)kT * kT * (nb - 1) * (nb - 2) / 2 + (int64_t)(nb - 1) * dk;
+  return base + (int64_t)bj * vr * kT;
 }
 __host__ __device__ inline int tile_rows(int nb, int vr, int bi) { return bi < nb - 1 ? kT : vr; }
-// Position of element (r, c) inside a stored tile: rows of kT values, the
-// 16-byte chunks of row r XOR-swizzled by r (so that 8 consecutive rows read
-// the same logical chunk from 8 different shared-memory banks).
+// element (r, c) of an off-diagonal tile / of a diagonal tile (c < V ceil((r + 1) / V))
+__host__ __device__ inline int tile_pos(int r, int c) { return r * kT + c; }
 template <int ESZ>
-__host__ __device__ inline int tile_pos(int r, int c) {
-  constexpr int cw = 16 / ESZ, nch = kT / cw;
-  return r * kT + (((c / cw) ^ (r % nch)) * cw) + (c % cw);
-}
+__host__ __device__ inline int64_t diag_pos(int r, int c) { return diag_row_off<ESZ>(r) + c; }
+template <int ESZ>
 __host__ __device__ inline int64_t F_size(int nb, int vr) {
-  return nb == 0 ? 0 : ((int64_t)(nb - 1) * nb / 2) * kT * kT + (int64_t)nb * vr * kT;
+  return nb == 0 ? 0 : tile_offset<ESZ>(nb, vr, nb - 1, nb - 1) + diag_row_off<ESZ>(vr);
+}
+__host__ __device__ inline int64_t F_size_esz(int esz, int nb, int vr) {
+  return esz == 4 ? F_size<4>(nb, vr) : F_size<8>(nb, vr);
 }
 
-// One F tile of the explicit apply (host-built, 32 bytes).
-enum : int { kTileFirst = 1, kTileLast = 2 };
+// One F tile of the explicit apply (host-built, 32 bytes).  Tile t of the
+// descriptor list owns row-partial slot t and column-partial slot t.
+enum : int { kTileDiag = 1 };
 struct __align__(16) TileDesc {
   int64_t f_ofs;   // element offset of the tile in the F storage
   int rows;        // stored rows (kT, or the ragged last block row)
-  int flags;       // kTileFirst / kTileLast of its work item
+  int flags;       // kTileDiag for a diagonal tile
   int prow;        // pg offset of the tile's row block
   int pcol;        // pg offset of the tile's column block
-  int col_slot;    // column-partial slot (tile index in the subdomain's partial array + base), -1 on the diagonal
-  int row_slot;    // row-partial slot of the work item (written after its last tile)
+  int pad0, pad1;
 };
 
 // status word bits written by kernels

@@ -72,8 +72,7 @@ struct feti_ctx {
   int2* d_syrk_items = nullptr;
   feti::TileDesc* d_tdesc = nullptr;
   struct ApplyCand {
-    int stages, grid;
-    int* cta_begin;
+    int variant, grid;  // tile-kernel variant (load batch) and grid
     double ms;
   };
   std::vector<ApplyCand> apply_cands;  // autotuner candidates of the apply

@@ -1,25 +1,24 @@
 // Explicit application q = F p (paper eq. 12 summed over subdomains, with
-// Algorithm 2's scatter / per-subdomain apply / gather), three launches:
+// Algorithm 2's scatter / per-subdomain apply / gather), four launches:
 //
 //  0. scatter: pg[j] = p[map_i(j)] for every sorted column j of every
 //             subdomain (Algorithm 2's scatter), in the tile precision;
-//  1. tiles:  a persistent, warp-specialised kernel streams the lower tiles
-//             of all F_i from HBM.  Lane 0 of warp 8 is the producer: for each
-//             tile it issues 1D bulk copies (cp.async.bulk + mbarrier
-//             complete_tx) of the contiguous 16 KB (FP32) / 32 KB (FP64) tile
-//             and of the two 64-entry segments of pg it needs into a ring of
-//             shared-memory stages.  Warps 0-7 consume: per tile the row partial F_t p_bj
-//             (accumulated over the work item) and, off the diagonal, the
-//             column partial F_t^T p_b.  A work item is up to kApplyChunk
-//             consecutive tiles (b, bj0..bj1) of one tile row (contiguous in
-//             memory).  Stages are released through per-stage `empty`
-//             mbarriers; the last consumer warp to finish a tile sums the 8
-//             per-warp column partials (no CTA-wide barrier in the loop).
-//  2. gather: q[lambda] = sum over the (at most two) subdomain columns of
-//             lambda of their row and column partials, in a fixed order
-//             (deterministic, no atomics on values).
-// Tile arithmetic runs in the tile's precision (FP32 tiles: FP32 FMAs over
-// 64 terms); the cross-tile sums in phase 2 are FP64.  All waits are bounded.
+//  1. tiles:  every warp streams whole F tiles from HBM straight into
+//             registers with 16-byte coalesced loads (each warp-wide load
+//             covers 512 contiguous bytes: two FP32 rows or one FP64 row),
+//             keeping two batches of BATCH loads in flight, and writes per
+//             tile t the row partial F_t p_bj (row slot t) and the column
+//             partial F_t^T p_bi (column slot t; for a diagonal tile only its
+//             strictly lower part, transposed).  Tiles are dealt to warps
+//             round-robin, so all warps stream neighbouring tiles together
+//             and the load is balanced to one tile;
+//  2. reduce: q_i[block b] = the row partials of tile row b plus the column
+//             partials of tile column b, in a fixed order, in FP64;
+//  3. gather: q[lambda] = sum over the (at most two) subdomain columns of
+//             lambda, in subdomain order (deterministic, no atomics).
+// Tile arithmetic runs in the tile's precision (FP32 tiles: FP32 FMAs); the
+// cross-tile sums in phase 2 are FP64.  Nothing waits on another warp.
+#include <algorithm>
 #include <mutex>
 
 #include "feti.h"
@@ -29,65 +28,23 @@
 namespace feti {
 namespace {
 
-constexpr int kConsumerWarps = 8;
-constexpr int kApplyThreads = (kConsumerWarps + 1) * 32;
+constexpr int kApplyThreads = 128;
+
 template <typename TF>
-struct ApplyCfg {
-  static constexpr int kStages = sizeof(TF) == 4 ? 5 : 2;
-  static constexpr int kTileBytes = kT * kT * (int)sizeof(TF);
-  static constexpr int kStageBytes = kTileBytes + 2 * kT * (int)sizeof(TF);
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
 };
 
-__device__ __forceinline__ uint32_t smem_u32a(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_test_a(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_try_a(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// lane 0 waits (try_wait, bounded by about 2e9 clock cycles), result broadcast to the warp
-__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity) {
-  int ok = 0;
-  if ((threadIdx.x & 31) == 0) {
-    const long long t0 = clock64();
-    while (!(ok = mbar_try_a(mbar, parity))) {
-      if (clock64() - t0 > 2000000000LL) break;
-    }
-  }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double comp(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 
 template <typename TF>
 __global__ void scatter_kernel(const int* qmap, int64_t ncols, const double* p, TF* pg) {
@@ -97,217 +54,184 @@ __global__ void scatter_kernel(const int* qmap, int64_t ncols, const double* p, 
   }
 }
 
-// One stage: the tile, the two p segments it needs, and its descriptor.
-// NS = number of stages in the ring (the autotuner picks it per problem).
-template <typename TF, int NS>
-__global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDesc* desc, const int* cta_begin,
-                                                                   const TF* F, const TF* pg, TF* rowpart,
-                                                                   TF* colpart, int* status) {
-  using C = ApplyCfg<TF>;
-  constexpr int S = NS;
-  constexpr int kMeta = 64;  // bytes of descriptor kept after the p segments
-  constexpr int kStride = C::kStageBytes + kMeta;
-  constexpr int cw = 16 / (int)sizeof(TF), nchk = kT / cw;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  __shared__ uint64_t full[S], empty[S];
-  __shared__ TF cred[S][kConsumerWarps][kT];
-  __shared__ int cnt[S];
-  __shared__ TileDesc dring[64];
-  __shared__ volatile int s_abort;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int t0 = cta_begin[blockIdx.x], t1 = cta_begin[blockIdx.x + 1];
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32a(&full[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32a(&empty[s])), "r"(kConsumerWarps));
-      cnt[s] = 0;
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  __syncthreads();
-
-  if (warp == kConsumerWarps) {
-    // ------------------------------------------------------------ producer
-    uint32_t k = 0;
-    for (int t = t0; t < t1 && !s_abort; ++t, ++k) {
-      if (((t - t0) & 31) == 0) {
-        // prefetch the next 32 descriptors into a double-buffered ring
-        const int base = ((t - t0) >> 5) & 1;
-        if (t + lane < t1) dring[base * 32 + lane] = desc[t + lane];
-        __syncwarp();
-      }
-      const TileDesc d = dring[(((t - t0) >> 5) & 1) * 32 + ((t - t0) & 31)];
-      const int st = k % S;
-      if (k >= S && !warp_wait(smem_u32a(&empty[st]), ((k / S) + 1) & 1)) {
-        s_abort = 1;
-        break;
-      }
-      if (lane == 0) {
-        uint8_t* stage = smem + st * kStride;
-        *reinterpret_cast<TileDesc*>(stage + C::kStageBytes) = d;
-        const uint32_t sa = smem_u32a(stage);
-        const uint32_t fb = smem_u32a(&full[st]);
-        const uint32_t tb = (uint32_t)d.rows * kT * (uint32_t)sizeof(TF);
-        expect_tx(fb, tb + 2 * kT * (uint32_t)sizeof(TF));
-        bulk_copy(sa, F + d.f_ofs, tb, fb);
-        bulk_copy(sa + C::kTileBytes, pg + d.prow, kT * sizeof(TF), fb);
-        bulk_copy(sa + C::kTileBytes + kT * sizeof(TF), pg + d.pcol, kT * sizeof(TF), fb);
-      }
-      __syncwarp();
-    }
-    if (s_abort) {
-      for (uint32_t u = (k > S ? k - S : 0); u < k; ++u) warp_wait(smem_u32a(&full[u % S]), (u / S) & 1);
-    }
-    return;
-  }
-
-  // -------------------------------------------------------------- consumers
-  // thread (rg, cg) holds the 4 x 4 block rows 4 rg .. 4 rg + 3, columns
-  // 4 cg .. 4 cg + 3 (one 16-byte chunk per row for FP32, two for FP64);
-  // the stored rows are chunk-swizzled (tile_pos), which keeps the reads of a
-  // quarter warp on distinct banks.  The column partial of an off-diagonal
-  // tile is summed over the 8 warps by the last warp to finish it.
-  const int rg = tid / 16, cg = tid % 16;
-  TF racc[4] = {(TF)0, (TF)0, (TF)0, (TF)0};
-  uint32_t k = 0;
-  for (int t = t0; t < t1; ++t, ++k) {
-    const int st = k % S;
-    if (!warp_wait(smem_u32a(&full[st]), (k / S) & 1)) {
-      s_abort = 1;
-      break;
-    }
-    const uint8_t* stage = smem + st * kStride;
-    const TileDesc d = *reinterpret_cast<const TileDesc*>(stage + C::kStageBytes);
-    const TF* Ft = reinterpret_cast<const TF*>(stage);
-    const TF* pr = reinterpret_cast<const TF*>(stage + C::kTileBytes);
-    const TF* pc = pr + kT;
-    TF v[4][4];
+// Reduce-scatter of N values per lane over the lanes that differ in bits
+// O, O/2, ..., 1 of the lane index: while N > 1 each step keeps half of the
+// values (the upper half where the lane's bit is set) and adds the partner's
+// other half; once one value is left, the remaining steps add it outright.
+// Afterwards lane l holds, in v[0], the total of value index
+// (l mod 2O) >> log2(2O / N_initial) (for N_initial <= 2O).
+template <typename TF, int N, int O>
+struct ReduceScatter {
+  __device__ __forceinline__ static void run(TF* v, int lane) {
+    if constexpr (O >= 1) {
+      if constexpr (N > 1) {
+        const bool up = (lane & O) != 0;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int r = 4 * rg + a;
-      const bool in = r < d.rows;  // rows beyond the stored ones hold stale data: read as zero
-      if constexpr (sizeof(TF) == 4) {
-        const float4 x = *reinterpret_cast<const float4*>(Ft + r * kT + ((cg ^ (r % nchk)) * cw));
-        v[a][0] = in ? x.x : 0.f;
-        v[a][1] = in ? x.y : 0.f;
-        v[a][2] = in ? x.z : 0.f;
-        v[a][3] = in ? x.w : 0.f;
-      } else {
-        const double2 x0 = *reinterpret_cast<const double2*>(Ft + r * kT + (((2 * cg) ^ (r % nchk)) * cw));
-        const double2 x1 = *reinterpret_cast<const double2*>(Ft + r * kT + (((2 * cg + 1) ^ (r % nchk)) * cw));
-        v[a][0] = in ? x0.x : 0.0;
-        v[a][1] = in ? x0.y : 0.0;
-        v[a][2] = in ? x1.x : 0.0;
-        v[a][3] = in ? x1.y : 0.0;
-      }
-    }
-    TF pcv[4], prv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      pcv[c] = pc[4 * cg + c];
-      prv[c] = pr[4 * rg + c];
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      TF s2 = (TF)0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s2 = fma(v[a][c], pcv[c], s2);
-      racc[a] += s2;
-    }
-    if (d.col_slot >= 0) {
-      TF cs[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        TF s2 = (TF)0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) s2 = fma(v[a][c], prv[a], s2);
-        cs[c] = s2 + __shfl_xor_sync(0xffffffffu, s2, 16);  // the warp's two row groups
-      }
-      if (lane < 16) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cred[st][warp][4 * cg + c] = cs[c];
-      }
-      __syncwarp();
-      int last = 0;
-      if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&cnt[st], 1) == kConsumerWarps - 1;
-      }
-      last = __shfl_sync(0xffffffffu, last, 0);
-      if (last) {
-        __threadfence_block();
-        for (int c = lane; c < kT; c += 32) {
-          TF s2 = (TF)0;
-#pragma unroll
-          for (int w = 0; w < kConsumerWarps; ++w) s2 += cred[st][w][c];
-          colpart[(int64_t)d.col_slot * kT + c] = s2;
+        for (int i = 0; i < N / 2; ++i) {
+          const TF send = up ? v[i] : v[i + N / 2];
+          const TF keep = up ? v[i + N / 2] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
         }
-        if (lane == 0) cnt[st] = 0;
-        __syncwarp();
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(smem_u32a(&empty[st]));
-    if (d.flags & kTileLast) {
-      // row partial of the work item: reduce over the 16 column groups (lanes of a half warp)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        TF s2 = racc[a];
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        racc[a] = (TF)0;
-        if (cg == 0) rowpart[(int64_t)d.row_slot * kApplyWarps * kT + 4 * rg + a] = s2;
+        ReduceScatter<TF, N / 2, O / 2>::run(v, lane);
+      } else {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+        ReduceScatter<TF, 1, O / 2>::run(v, lane);
       }
     }
   }
-  if (s_abort && tid == 0) atomicOr(status, kStatTimeout);
-}
+};
 
-template <typename TF>
-size_t stage_smem(int ns) {
-  return (size_t)ns * (ApplyCfg<TF>::kStageBytes + 64) + 128;
-}
+// Per-buffer state of one issued batch.
+template <typename TF, int BATCH>
+struct Batch {
+  typename Vec16<TF>::T v[BATCH];
+  typename Vec16<TF>::T pc;  // p of the tile's column block, this lane's chunk
+  TF pr;                     // p of one row of the batch (shuffled out per load)
+  int t, b, diag;
+};
 
-// launch the staged kernel with ns stages (2..6)
-template <typename TF>
-void launch_tiles(int ns, int grid, cudaStream_t st, const TileDesc* desc, const int* cta_begin, const TF* F,
-                  const TF* pg, TF* rowpart, TF* colpart, int* status) {
-  const size_t smem = stage_smem<TF>(ns);
-#define FETI_TL(N)                                                                                                  \
-  case N:                                                                                                           \
-    cudaFuncSetAttribute(apply_tiles_kernel<TF, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-    apply_tiles_kernel<TF, N><<<grid, kApplyThreads, smem, st>>>(desc, cta_begin, F, pg, rowpart, colpart, status); \
-    break;
-  switch (ns) {
-    FETI_TL(2) FETI_TL(3) FETI_TL(4) FETI_TL(5) FETI_TL(6)
-    default:
-      break;
+template <typename TF, int BATCH>
+struct TileStream {
+  using VT = typename Vec16<TF>::T;
+  static constexpr int V = 16 / (int)sizeof(TF);  // values per 16-byte chunk
+  static constexpr int NCH = kT / V;              // lanes per tile row
+  static constexpr int RPL = 32 / NCH;            // rows per warp-wide load
+  static constexpr int ROWS_B = BATCH * RPL;      // rows per batch
+  static constexpr int NBT = kT / ROWS_B;         // batches per tile
+  static_assert(NBT >= 1 && kT % ROWS_B == 0, "batch does not divide a tile");
+
+  const TileDesc* desc;
+  const TF* F;
+  const TF* pg;
+  int lane, cq, half, gw, nw, ntiles;
+  TileDesc dI;    // descriptor of the tile being issued
+  TileDesc dP;    // prefetched descriptor of the next tile of this warp
+
+  __device__ __forceinline__ void issue(int k, Batch<TF, BATCH>& B) {
+    const int j = k / NBT, b = k % NBT;
+    const int t = gw + j * nw;
+    if (b == 0 && k > 0) {
+      dI = dP;
+      const int tn = t + nw;
+      if (tn < ntiles) dP = desc[tn];
+    }
+    const TileDesc& d = dI;
+    const bool diag = (d.flags & kTileDiag) != 0;
+    B.t = t;
+    B.b = b;
+    B.diag = diag;
+    const TF* Ft = F + d.f_ofs;
+#pragma unroll
+    for (int i = 0; i < BATCH; ++i) {
+      const int r = b * ROWS_B + i * RPL + half;
+      const bool ok = r < d.rows && (!diag || cq * V <= r);
+      const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(r) : (int64_t)r * kT;
+      if (ok) B.v[i] = ld_stream(reinterpret_cast<const VT*>(Ft + off + cq * V));
+      else B.v[i] = VT{};
+    }
+    B.pc = *reinterpret_cast<const VT*>(pg + d.pcol + cq * V);
+    B.pr = pg[d.prow + b * ROWS_B + (lane % ROWS_B)];
   }
-#undef FETI_TL
+};
+
+template <typename TF, int BATCH>
+__device__ __forceinline__ void consume(const Batch<TF, BATCH>& B, TF* cacc, TF* rowpart, TF* colpart, int lane,
+                                        int cq, int half) {
+  using TS = TileStream<TF, BATCH>;
+  constexpr int V = TS::V, NCH = TS::NCH, RPL = TS::RPL, ROWS_B = TS::ROWS_B, NBT = TS::NBT;
+  TF rs[BATCH];
+#pragma unroll
+  for (int i = 0; i < BATCH; ++i) {
+    const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
+    TF s = (TF)0;
+#pragma unroll
+    for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
+    rs[i] = s;
+    const int r = B.b * ROWS_B + i * RPL + half;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const TF x = (B.diag && cq * V + e >= r) ? (TF)0 : comp(B.v[i], e);
+      cacc[e] = fma(x, pr, cacc[e]);
+    }
+  }
+  ReduceScatter<TF, BATCH, NCH / 2>::run(rs, lane);
+  constexpr int SPAN = NCH / BATCH;  // lanes holding the same row total
+  if (cq % SPAN == 0) {
+    const int r = B.b * ROWS_B + (cq / SPAN) * RPL + half;
+    rowpart[(int64_t)B.t * kT + r] = rs[0];
+  }
+  if (B.b == NBT - 1) {
+    if constexpr (RPL == 2) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) cacc[e] += __shfl_xor_sync(0xffffffffu, cacc[e], 16);
+    }
+    if (half == 0) {
+      using VT = typename Vec16<TF>::T;
+      VT o;
+      if constexpr (V == 4) o = VT{cacc[0], cacc[1], cacc[2], cacc[3]};
+      else o = VT{cacc[0], cacc[1]};
+      *reinterpret_cast<VT*>(colpart + (int64_t)B.t * kT + cq * V) = o;
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) cacc[e] = (TF)0;
+  }
 }
 
-// q_i[j] = (row partials of block b(j) over the item chunks) + (column
-// partials of the tiles below block b(j)); one warp per (subdomain, block),
-// lanes over the 64 columns of the block.  FP64 sums in a fixed order.
+template <typename TF, int BATCH>
+__global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDesc* __restrict__ desc, int ntiles,
+                                                                   const TF* __restrict__ F,
+                                                                   const TF* __restrict__ pg, TF* rowpart,
+                                                                   TF* colpart) {
+  using TS = TileStream<TF, BATCH>;
+  constexpr int V = TS::V, NBT = TS::NBT;
+  TS ts;
+  ts.desc = desc;
+  ts.F = F;
+  ts.pg = pg;
+  ts.lane = threadIdx.x & 31;
+  ts.cq = ts.lane % TS::NCH;
+  ts.half = ts.lane / TS::NCH;
+  ts.nw = gridDim.x * (blockDim.x / 32);
+  ts.gw = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  ts.ntiles = ntiles;
+  if (ts.gw >= ntiles) return;
+  const int my_tiles = (ntiles - 1 - ts.gw) / ts.nw + 1;
+  const int nitems = my_tiles * NBT;
+  ts.dI = desc[ts.gw];
+  ts.dP = ts.gw + ts.nw < ntiles ? desc[ts.gw + ts.nw] : ts.dI;
+  TF cacc[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) cacc[e] = (TF)0;
+  Batch<TF, BATCH> b0, b1;
+  ts.issue(0, b0);
+  int k = 0;
+  for (;;) {
+    if (k + 1 < nitems) ts.issue(k + 1, b1);
+    consume<TF, BATCH>(b0, cacc, rowpart, colpart, ts.lane, ts.cq, ts.half);
+    if (++k >= nitems) break;
+    if (k + 1 < nitems) ts.issue(k + 1, b0);
+    consume<TF, BATCH>(b1, cacc, rowpart, colpart, ts.lane, ts.cq, ts.half);
+    if (++k >= nitems) break;
+  }
+}
+
+// q_i[b kT + x] = sum_{bj <= b} rowpart[tile (b, bj)][x] + sum_{bi >= b} colpart[tile (bi, b)][x];
+// one warp per (subdomain, block), FP64 sums in a fixed order.
 template <typename TF>
-__global__ void reduce_cols_kernel(DevPlan P, const int2* blocks, int nblocks, const TF* rowpart,
-                                   const TF* colpart, double* qi, int nslots) {
+__global__ void reduce_tiles_kernel(DevPlan P, const int2* blocks, int nblocks, const TF* rowpart,
+                                    const TF* colpart, double* qi) {
   const int lane = threadIdx.x & 31;
   for (int wb = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wb < nblocks; wb += gridDim.x * blockDim.x / 32) {
     const int2 sb = blocks[wb];
     const SubInfo& S = P.sub[sb.x];
     const int b = sb.y, nb = S.nb;
-    const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
-    const int64_t rp = S.rpart, tp = S.tpart, qc = S.qcol;
+    const int64_t tb = S.tpart / kT;
     for (int x = lane; x < kT; x += 32) {
       double s = 0.0;
-      for (int c = 0; c * kApplyChunk <= b; ++c)
-        for (int w = 0; w < nslots; ++w)
-          s += (double)rowpart[rp + (((int64_t)b * nch + c) * kApplyWarps + w) * kT + x];
-      for (int bi = b + 1; bi < nb; ++bi) s += (double)colpart[tp + (int64_t)(bi * (bi + 1) / 2 + b) * kT + x];
-      qi[qc + b * kT + x] = s;
+      const int64_t r0 = tb + (int64_t)b * (b + 1) / 2;
+      for (int bj = 0; bj <= b; ++bj) s += (double)rowpart[(r0 + bj) * kT + x];
+      for (int bi = b; bi < nb; ++bi) s += (double)colpart[(tb + (int64_t)bi * (bi + 1) / 2 + b) * kT + x];
+      qi[S.qcol + (int64_t)b * kT + x] = s;
     }
   }
 }
@@ -322,25 +246,49 @@ __global__ void gather_lambda_kernel(const int* c0, const int* c1, int nlam, con
   }
 }
 
-}  // namespace
+template <typename TF, int BATCH>
+void set_tiles_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(apply_tiles_kernel<TF, BATCH>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    done = true;
+  }
+}
 
-size_t apply_tiles_smem(bool fp32) {
-  return fp32 ? stage_smem<float>(ApplyCfg<float>::kStages) : stage_smem<double>(ApplyCfg<double>::kStages);
+// variants of the tile kernel: 0 -> BATCH 8, 1 -> BATCH 16
+template <typename TF>
+void launch_tiles(int variant, int grid, cudaStream_t st, const TileDesc* desc, int ntiles, const TF* F,
+                  const TF* pg, TF* rowpart, TF* colpart) {
+  if (ntiles <= 0) return;
+  if (variant == 0) {
+    set_tiles_attr<TF, 8>();
+    apply_tiles_kernel<TF, 8><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart);
+  } else {
+    set_tiles_attr<TF, 16>();
+    apply_tiles_kernel<TF, 16><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart);
+  }
 }
 
 template <typename TF>
-static void launch_apply_t(const DevPlan& P, const TileDesc* desc, const int* cta_begin, const void* F,
-                           const int* qmap, int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart,
-                           const int2* blocks, int nblocks, double* qi, const int* c0, const int* c1, int nlam,
-                           double* q, int grid, int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
-                           int stages) {
+void launch_reduce(const DevPlan& P, const int2* blocks, int nblocks, const TF* rowpart, const TF* colpart,
+                   double* qi, cudaStream_t st) {
+  const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
+  reduce_tiles_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, rowpart, colpart, qi);
+}
+
+}  // namespace
+
+template <typename TF>
+static void launch_apply_t(const DevPlan& P, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
+                           int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                           int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid,
+                           int variant, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 152 * 8));
   scatter_kernel<TF><<<sg, 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
   if (e0) cudaEventRecord(e0, st);
-  launch_tiles<TF>(stages, grid, st, desc, cta_begin, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart, status);
+  launch_tiles<TF>(variant, grid, st, desc, ntiles, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart);
   if (e1) cudaEventRecord(e1, st);
-  const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
-  reduce_cols_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi, 1);
+  launch_reduce<TF>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi, st);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
   gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
 }
@@ -350,33 +298,33 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
   gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
 }
 
-void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, const int* cta_begin, const void* F,
-                  const int* qmap, int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart,
-                  const int2* blocks, int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q,
-                  int grid, int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int stages) {
+void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
+                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                  int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
+                  cudaStream_t st, cudaEvent_t ev_tiles0, cudaEvent_t ev_tiles1) {
   if (fp32)
-    launch_apply_t<float>(P, desc, cta_begin, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                          nlam, q, grid, status, st, e0, e1, stages);
+    launch_apply_t<float>(P, desc, ntiles, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                          nlam, q, grid, variant, st, ev_tiles0, ev_tiles1);
   else
-    launch_apply_t<double>(P, desc, cta_begin, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                           nlam, q, grid, status, st, e0, e1, stages);
+    launch_apply_t<double>(P, desc, ntiles, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
+                           nlam, q, grid, variant, st, ev_tiles0, ev_tiles1);
 }
 
-int apply_max_ctas_per_sm(bool fp32, int stages) {
+int apply_variants() { return 2; }
+
+int apply_max_ctas_per_sm(bool fp32, int variant) {
   int nb = 0;
   if (fp32) {
-    const size_t smem = stage_smem<float>(stages);
-#define FETI_OCC(N)                                                                                      if (stages == N) {                                                                                       cudaFuncSetAttribute(apply_tiles_kernel<float, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, N>, kApplyThreads, smem);    }
-    FETI_OCC(2) FETI_OCC(3) FETI_OCC(4) FETI_OCC(5) FETI_OCC(6)
-#undef FETI_OCC
+    if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, 8>, kApplyThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, 16>, kApplyThreads, 0);
   } else {
-    const size_t smem = stage_smem<double>(stages);
-#define FETI_OCC(N)                                                                                       if (stages == N) {                                                                                        cudaFuncSetAttribute(apply_tiles_kernel<double, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, N>, kApplyThreads, smem);    }
-    FETI_OCC(2) FETI_OCC(3) FETI_OCC(4) FETI_OCC(5) FETI_OCC(6)
-#undef FETI_OCC
+    if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, 8>, kApplyThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, 16>, kApplyThreads, 0);
   }
   return nb;
 }
+
+int apply_warps_per_cta() { return kApplyThreads / 32; }
 
 // ---------------------------------------------------------------------------
 // Stand-alone application of one local operator without any device allocation.
@@ -394,26 +342,25 @@ int apply_max_ctas_per_sm(bool fp32, int stages) {
 
 constexpr int kStaticMaxM = 8192;                 // largest m accepted
 constexpr int kStaticMaxNb = kStaticMaxM / kT;
-constexpr int64_t kStaticDoubles = 1 << 20;       // 8 MiB of scratch
 constexpr int kStaticMaxTiles = kStaticMaxNb * (kStaticMaxNb + 1) / 2;
-constexpr int kStaticGrid = 152 * 2;
+constexpr int64_t kStaticDoubles = 3 << 19;       // 12 MiB of scratch
+// worst case (m = kStaticMaxM, FP64 tiles): gathered p, row and column partials, q_i, 256-byte padding
+static_assert((int64_t)kStaticMaxM + 2LL * kStaticMaxTiles * kT + kStaticMaxM + 64 <= kStaticDoubles,
+              "static scratch too small for the largest accepted m");
+constexpr int kStaticGrid = 152 * 4;
 
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 static __device__ __align__(256) TileDesc g_static_desc[kStaticMaxTiles];
-static __device__ __align__(256) int g_static_cta[kStaticGrid + 1];
 static __device__ __align__(256) int2 g_static_blocks[kStaticMaxNb];
 static __device__ __align__(256) SubInfo g_static_sub;
-static __device__ __align__(256) int g_static_status;
 
 namespace {
 
-// Describe the single subdomain, its tile descriptors, CTA ranges and blocks
-// in the static arrays, zero the padding of the gathered p, and clear the
-// status word (the only state that must start at zero; every other slot is
-// overwritten).
+// Describe the single subdomain, its tile descriptors and blocks in the
+// static arrays and zero the padding of the gathered p (every other slot the
+// apply reads is overwritten before it is read, so nothing else needs clearing).
 template <typename TF>
-__global__ void static_setup_kernel(int m, int nb, int64_t rpart, int64_t tpart, int grid, TF* pg) {
-  const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
+__global__ void static_setup_kernel(int m, int nb, TF* pg) {
   const int vr = m - kT * (nb - 1);
   if (threadIdx.x == 0) {
     SubInfo S{};
@@ -421,30 +368,21 @@ __global__ void static_setup_kernel(int m, int nb, int64_t rpart, int64_t tpart,
     S.m_pad = nb * kT;
     S.nb = nb;
     S.vr = vr;
-    S.rpart = rpart;
-    S.tpart = tpart;
+    S.tpart = 0;
     g_static_sub = S;
-    g_static_status = 0;
-    const int ntile = nb * (nb + 1) / 2;
-    int k = 0, cta = 1;
-    g_static_cta[0] = 0;
-    for (int b = 0; b < nb; ++b)
-      for (int c = 0; c * kApplyChunk <= b; ++c) {
-        const int bj0 = c * kApplyChunk, bj1 = min(bj0 + kApplyChunk, b + 1);
-        for (int bj = bj0; bj < bj1; ++bj) {
-          TileDesc d;
-          d.f_ofs = tile_offset(nb, vr, b, bj);
-          d.rows = tile_rows(nb, vr, b);
-          d.flags = (bj == bj0 ? kTileFirst : 0) | (bj == bj1 - 1 ? kTileLast : 0);
-          d.prow = b * kT;
-          d.pcol = bj * kT;
-          d.col_slot = bj < b ? (int)(tpart / kT) + b * (b + 1) / 2 + bj : -1;
-          d.row_slot = (int)(rpart / (kT * kApplyWarps)) + b * nch + c;
-          g_static_desc[k++] = d;
-        }
-        if (cta < grid && (double)k >= (double)ntile * cta / grid) g_static_cta[cta++] = k;
-      }
-    for (; cta <= grid; ++cta) g_static_cta[cta] = k;
+  }
+  const int ntile = nb * (nb + 1) / 2;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+    int b = 0;
+    while ((b + 1) * (b + 2) / 2 <= t) ++b;
+    const int bj = t - b * (b + 1) / 2;
+    TileDesc d{};
+    d.f_ofs = tile_offset<(int)sizeof(TF)>(nb, vr, b, bj);
+    d.rows = tile_rows(nb, vr, b);
+    d.flags = bj == b ? kTileDiag : 0;
+    d.prow = b * kT;
+    d.pcol = bj * kT;
+    g_static_desc[t] = d;
   }
   for (int b = threadIdx.x; b < nb; b += blockDim.x) g_static_blocks[b] = make_int2(0, b);
   for (int j = m + threadIdx.x; j < nb * kT; j += blockDim.x) pg[j] = (TF)0;
@@ -458,10 +396,8 @@ __global__ void static_accumulate_kernel(const int* map, int m, const double* qi
 struct StaticAddrs {
   double* scratch = nullptr;
   TileDesc* desc = nullptr;
-  int* cta = nullptr;
   int2* blocks = nullptr;
   SubInfo* sub = nullptr;
-  int* status = nullptr;
 };
 
 std::mutex g_static_mu;
@@ -481,10 +417,8 @@ cudaError_t static_addresses(StaticAddrs& out) {
     StaticAddrs a;
     if ((e = cudaGetSymbolAddress((void**)&a.scratch, g_static_scratch)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.desc, g_static_desc)) != cudaSuccess) return e;
-    if ((e = cudaGetSymbolAddress((void**)&a.cta, g_static_cta)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.blocks, g_static_blocks)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void**)&a.sub, g_static_sub)) != cudaSuccess) return e;
-    if ((e = cudaGetSymbolAddress((void**)&a.status, g_static_status)) != cudaSuccess) return e;
     g_static_addr[dev] = a;
     g_static_ready[dev] = true;
   }
@@ -496,34 +430,29 @@ template <typename TF>
 feti_status apply_one_static_t(int m, const TF* F, const int* map, const double* p, double* q, cudaStream_t st) {
   const int nb = (m + kT - 1) / kT;
   const int m_pad = nb * kT;
-  const int nch = (nb + kApplyChunk - 1) / kApplyChunk;
   const int64_t ntile = (int64_t)nb * (nb + 1) / 2;
-  int nitems = 0;
-  for (int b = 0; b < nb; ++b) nitems += b / kApplyChunk + 1;
-  const int grid = std::max(1, std::min(nitems, kStaticGrid));
-  // scratch layout: [pg: m_pad TF, padded][row partials: nb nch kApplyWarps kT TF][column partials: ntile kT TF]
-  //                 | [qi: m_pad double]
-  const int64_t n_pg = ((int64_t)m_pad + kT * kApplyWarps - 1) / (kT * kApplyWarps) * (kT * kApplyWarps);
-  const int64_t n_row = (int64_t)nb * nch * kT * kApplyWarps, n_col = ntile * kT;
-  const int64_t qi_ofs = ((n_pg + n_row + n_col) * (int64_t)sizeof(TF) + 255) / 256 * 256 / 8;
+  // scratch layout: [pg: m_pad TF][row partials: ntile kT TF][column partials: ntile kT TF] | [qi: m_pad double]
+  const int64_t n_part = ntile * kT;
+  const int64_t qi_ofs = (((int64_t)m_pad + 2 * n_part) * (int64_t)sizeof(TF) + 255) / 256 * 256 / 8;
   if (qi_ofs + m_pad > kStaticDoubles || ntile > kStaticMaxTiles) return FETI_ERR_ARG;
   StaticAddrs a;
   if (static_addresses(a) != cudaSuccess) return FETI_ERR_CUDA;
   TF* pg = reinterpret_cast<TF*>(a.scratch);
+  TF* rowpart = pg + m_pad;
+  TF* colpart = rowpart + n_part;
   double* qi = a.scratch + qi_ofs;
-  static_setup_kernel<TF><<<1, 256, 0, st>>>(m, nb, n_pg, n_pg + n_row, grid, pg);
+  static_setup_kernel<TF><<<1, 256, 0, st>>>(m, nb, pg);
   scatter_kernel<TF><<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, p, pg);
+  const int wpc = kApplyThreads / 32;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ntile + wpc - 1) / wpc, kStaticGrid));
+  launch_tiles<TF>(0, grid, st, a.desc, (int)ntile, F, pg, rowpart, colpart);
   DevPlan P{};
   P.sub = a.sub;
-  // row / column partial slots are offsets from the scratch base (S.rpart / S.tpart)
-  launch_tiles<TF>(ApplyCfg<TF>::kStages, grid, st, a.desc, a.cta, F, pg, pg, pg, a.status);
-  reduce_cols_kernel<TF><<<std::max(1, (nb + 7) / 8), 256, 0, st>>>(P, a.blocks, nb, pg, pg, qi, 1);
+  launch_reduce<TF>(P, a.blocks, nb, rowpart, colpart, qi, st);
   static_accumulate_kernel<<<std::max(1, (m + 255) / 256), 256, 0, st>>>(map, m, qi, q);
   if (cudaGetLastError() != cudaSuccess) return FETI_ERR_CUDA;
-  int status = 0;
-  if (cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FETI_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return FETI_ERR_CUDA;
-  return (status & kStatTimeout) ? FETI_ERR_TIMEOUT : FETI_OK;
+  return FETI_OK;
 }
 
 }  // namespace

@@ -298,12 +298,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
       const int col = BJ * kM + cc * 32;
       const int bj = col / kT;
       if (bi < S.nb && bj < S.nb && bj <= bi && (row % kT) < tile_rows(S.nb, S.vr, bi)) {
-        float* tb = F + S.F + tile_offset(S.nb, S.vr, bi, bj);
+        float* tb = F + S.F + tile_offset<4>(S.nb, S.vr, bi, bj);
+        const int r = row % kT;
+        if (bj < bi) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 4)
-          *reinterpret_cast<float4*>(tb + tile_pos<4>(row % kT, col % kT + e)) =
-              make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
-                          __uint_as_float(v[e + 3]));
+          for (int e = 0; e < 32; e += 4)
+            *reinterpret_cast<float4*>(tb + tile_pos(r, col % kT + e)) =
+                make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                            __uint_as_float(v[e + 3]));
+        } else {
+          // diagonal tile: the chunks up to the one holding column r, zeros right of the diagonal
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const int c = col % kT + e;
+            if (c / 4 <= r / 4) {
+              float x[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) x[u] = c + u <= r ? __uint_as_float(v[e + u]) : 0.f;
+              *reinterpret_cast<float4*>(tb + diag_pos<4>(r, c)) = make_float4(x[0], x[1], x[2], x[3]);
+            }
+          }
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -1,10 +1,10 @@
 // FP64 SIMT SYRK F_i = X_i^T X_i into lower F tiles (paper Sec. IV, SYRK
 // path; the mixed-precision path uses the tensor-core kernel instead).
 //
-// F_i layout: the m_pad x m_pad matrix (columns in sorted order) is cut into
-// kT x kT tiles; only tiles (bi, bj) with bj <= bi are stored, tile index
-// bi (bi + 1) / 2 + bj, each tile row-major.  Diagonal tiles are stored in
-// full (both triangles), so one tile is one contiguous 16/32 KB block.
+// F_i layout (common.cuh): the m_pad x m_pad matrix (columns in sorted
+// order) is cut into kT x kT tiles; only tiles (bi, bj) with bj <= bi are
+// stored, tile index bi (bi + 1) / 2 + bj.  Off-diagonal tiles are row-major;
+// diagonal tiles keep only the 16-byte chunks of each row up to the diagonal.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -64,13 +64,17 @@ __global__ void __launch_bounds__(kThreads) syrk_f64_kernel(DevPlan P, const int
         __syncthreads();
       }
     }
-    double* Ft = F + S.F + tile_offset(S.nb, S.vr, bi, bj);
+    double* Ft = F + S.F + tile_offset<8>(S.nb, S.vr, bi, bj);
     const int nrow = tile_rows(S.nb, S.vr, bi);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (ty + 16 * u < nrow) Ft[tile_pos<8>(ty + 16 * u, tx + 16 * v)] = acc[u][v];
+      for (int v = 0; v < 4; ++v) {
+        const int r = ty + 16 * u, c = tx + 16 * v;
+        if (r >= nrow) continue;
+        if (bj < bi) Ft[tile_pos(r, c)] = acc[u][v];
+        else if (c / 2 <= r / 2) Ft[diag_pos<8>(r, c)] = c <= r ? acc[u][v] : 0.0;  // diagonal tile
+      }
   }
 }
 
@@ -79,12 +83,14 @@ template <typename TF>
 __global__ void unpack_F_kernel(const TF* Fsub, int m, int nb, int vr, const int* colperm, double* out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < (int64_t)m * m; g += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(g / m), j = (int)(g % m);
-    if (j / kT > i / kT) {
+    if (j / kT > i / kT || (j / kT == i / kT && j % kT > i % kT)) {  // F is symmetric: read the lower copy
       int t = i;
       i = j;
       j = t;
     }
-    const double v = (double)Fsub[tile_offset(nb, vr, i / kT, j / kT) + tile_pos<sizeof(TF)>(i % kT, j % kT)];
+    constexpr int E = (int)sizeof(TF);
+    const int64_t o = tile_offset<E>(nb, vr, i / kT, j / kT);
+    const double v = (double)Fsub[o + (i / kT == j / kT ? diag_pos<E>(i % kT, j % kT) : tile_pos(i % kT, j % kT))];
     out[(int64_t)colperm[(int)(g / m)] * m + colperm[(int)(g % m)]] = v;
   }
 }

@@ -16,14 +16,14 @@ void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float
 size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);
-size_t apply_tiles_smem(bool fp32);
-// ev_tiles: optional events recorded just before / after the F-streaming kernel
-void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, const int* cta_begin, const void* F,
-                  const int* qmap, int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart,
-                  const int2* blocks, int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q,
-                  int grid, int* status, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr,
-                  cudaEvent_t ev_tiles1 = nullptr, int stages = 4);
-int apply_max_ctas_per_sm(bool fp32, int stages);
+// ev_tiles0/1: optional events recorded just before / after the F-streaming kernel
+void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
+                  int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
+                  int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
+                  cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
+int apply_variants();
+int apply_max_ctas_per_sm(bool fp32, int variant);
+int apply_warps_per_cta();
 void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, int vr, const int* colperm, double* out,
                      cudaStream_t st);
 

@@ -1,0 +1,79 @@
+"""Run one phase of the dual-operator path on one workload, for profilers.
+
+    python -m paper_2502_08382_gb300.profile_case --config 2 --prec split_bf16 --phase apply --reps 5
+
+Builds the seeded workload, creates and assembles the operator once
+(untimed warm-up), then runs the chosen phase ``--reps`` times on the
+current stream and prints one JSON line with the mean CUDA-event time per
+repetition.  Phases:
+
+  assemble   feti_assemble (regularise, Cholesky, pruned TRSM, SYRK)
+  apply      feti_apply, explicit q = F p (scatter, F tiles, gather)
+  implicit   feti_apply_implicit, q = B L^-T L^-1 B^T p in FP64 (eq. 11)
+  solve      feti_solve (projected PCG with refinement, alpha, u)
+
+``--nsub-axis`` shrinks the workload to fewer subdomains of the same shape
+(smaller ncu captures).  Nothing here is used by the library itself.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--nsub-axis", type=int, default=None)
+    ap.add_argument("--prec", default="split_bf16", choices=["fp64", "tf32", "split_bf16"])
+    ap.add_argument("--phase", default="apply", choices=["assemble", "apply", "implicit", "solve"])
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--refine-every", type=int, default=10)
+    args = ap.parse_args()
+
+    import torch
+    from . import feti
+    from .problems import make_config, seeded_vector
+
+    torch.cuda.set_device(0)
+    P = make_config(args.config, nsub_axis=args.nsub_axis)
+    op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000,
+                           refine_every=args.refine_every if args.prec != "fp64" else 0)
+    op.assemble()
+    p = torch.from_numpy(seeded_vector(P.n_lambda, 0)).cuda()
+    q = torch.empty_like(p)
+    st = torch.cuda.current_stream()
+
+    info = {}
+
+    def run():
+        if args.phase == "assemble":
+            op.assemble()
+        elif args.phase == "apply":
+            op.apply(p, out=q)
+        elif args.phase == "implicit":
+            op.apply_implicit(p, out=q)
+        else:
+            info.update(op.solve()[3])
+
+    run()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(args.reps):
+        run()
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / max(args.reps, 1)
+    s = op.stats()
+    print(json.dumps({"config": args.config, "nsub": P.nsub, "prec": args.prec, "phase": args.phase,
+                      "reps": args.reps, "ms": ms, "device_bytes": s["device_bytes"],
+                      "apply_bytes": s["apply_bytes"], "implicit_bytes": s["implicit_bytes"],
+                      "chol_flops": s["chol_flops"], "trsm_flops": s["trsm_flops"],
+                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "solve": info}))
+    op.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,3 +146,60 @@ def test_nested_dissection_reduces_fill(lib):
     nd = float(_brute_fill(A[np.ix_(perm, perm)]).sum())
     assert nd < 0.5 * nat
     assert nd <= info["nnzL"] < 1.5 * nd
+
+
+# ---------------------------------------------------------------- input validation (host fault injection)
+#
+# feti_create validates every input on the host before it touches the GPU,
+# so malformed problems are rejected with FETI_ERR_ARG and a message here,
+# without a device.  Each case corrupts one field of a valid problem.
+
+
+def _create_status(P, corrupt):
+    import ctypes as C
+    lib = feti.load_library()
+    m = feti._Marshal(P)
+    corrupt(m)
+    h = C.c_void_p()
+    opt = feti.FetiOptions()
+    rc = lib.feti_create(C.byref(m.prob), C.byref(opt), C.byref(h))
+    msg = lib.feti_last_error(h).decode() if h else ""
+    if h:
+        lib.feti_destroy(h)
+    return rc, msg
+
+
+def _set_int(arr_ptr, idx, val):
+    arr_ptr[idx] = val
+
+
+BAD_INPUTS = {
+    "no_subdomains": (lambda m: setattr(m.prob, "nsub", 0), ""),
+    "nfix_ne_d": (lambda m: setattr(m.subs[0], "nfix", 0), "nfix must equal d"),
+    "B_two_entries": (lambda m: _set_int(m.subs[1].B_rowptr, 1, 2), "exactly one entry"),
+    "B_not_unit": (lambda m: _set_int(m.subs[0].B_val, 0, 0.5), "+1 or -1"),
+    "B_lambda_order": (lambda m: _set_int(m.subs[0].B_lambda, 1, -5), "strictly increasing"),
+    "K_col_range": (lambda m: _set_int(m.subs[2].K_col, 3, 10 ** 6), "out of range"),
+    "K_unsorted": (lambda m: (_set_int(m.subs[0].K_col, 1, m.subs[0].K_col[0])), "sorted and unique"),
+    "fix_range": (lambda m: _set_int(m.subs[0].fix_dofs, 0, -1), "fix DOF out of range"),
+    "B_dof_range": (lambda m: _set_int(m.subs[3].B_col, 0, 10 ** 6), "B column out of range"),
+}
+
+
+@pytest.mark.parametrize("name", list(BAD_INPUTS))
+def test_create_rejects_malformed_input(lib, name):
+    P = make_problem(dim=2, physics="heat", cuts=[[3, 4]] * 2, material="const", seed=0)
+    corrupt, words = BAD_INPUTS[name]
+    rc, msg = _create_status(P, corrupt)
+    assert rc == 1, (rc, msg)  # FETI_ERR_ARG
+    assert words in msg, msg
+
+
+def test_apply_one_static_rejects_sizes_on_host(lib):
+    """Sizes beyond the fixed scratch (and non-positive ones) are rejected
+    before any device work is issued."""
+    import ctypes as C
+    one = C.c_void_p(16)
+    for m in (0, -3, 8193, 1 << 20):
+        assert lib.feti_apply_one_static(m, 1, one, one, one, one, None) == 1
+    assert lib.feti_apply_one_static(64, 1, None, one, one, one, None) == 1

@@ -257,3 +257,16 @@ def test_break_even_formula(row):
     name = row[0]
     pe, ae, pi, ai, n = map(float, row[1:])
     assert break_even(pe, ae, pi, ai) == int(n), name
+
+
+def test_Gt_times_and_residuals(cfg1):
+    """G^T lam without forming G equals the dense G^T lam; the FETI equation
+    residuals vanish for the oracle's own converged solve and do not for a
+    perturbed multiplier vector."""
+    lam = np.random.default_rng(3).normal(size=cfg1.n_lambda)
+    assert np.allclose(O.Gt_times(cfg1, lam), O.G_matrix(cfg1).T @ lam, rtol=0, atol=1e-12)
+    res = O.feti_solve(cfg1, tol=1e-12)
+    prim, Bu = O.feti_equation_residuals(cfg1, res["lam"], res["u"])
+    assert prim.max() < 1e-12 and np.abs(Bu).max() < 1e-10
+    prim2, Bu2 = O.feti_equation_residuals(cfg1, res["lam"] + 1e-3 * lam, res["u"])
+    assert prim2.max() > 1e-6

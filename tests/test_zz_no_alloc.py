@@ -21,24 +21,28 @@ pytestmark = pytest.mark.gpu
 
 def _tiles(F, esz):
     """Lay a dense m x m symmetric F out as 64 x 64 lower tiles in the documented
-    layout: the last block row ragged, 16-byte chunks of row r XOR-permuted by r."""
+    layout: tiles (bi, bj <= bi) one after another, the last block row ragged;
+    off-diagonal tiles row-major; diagonal tiles keep for row r only the first
+    w ceil((r + 1) / w) values (w = 16 / esz), zeros right of the diagonal."""
     m = F.shape[0]
     nb = (m + 63) // 64
     vr = m - 64 * (nb - 1)
     Fp = np.zeros((nb * 64, nb * 64))
     Fp[:m, :m] = F
     w = 16 // esz
-    nch = 64 // w
     out = []
     for bi in range(nb):
         rows = 64 if bi < nb - 1 else vr
         for bj in range(bi + 1):
             t = Fp[bi * 64:bi * 64 + rows, bj * 64:(bj + 1) * 64]
-            st = np.zeros_like(t)
-            for r in range(rows):
-                for c in range(64):
-                    st[r, ((c // w) ^ (r % nch)) * w + c % w] = t[r, c]
-            out.append(st.ravel())
+            if bj < bi:
+                out.append(t.ravel())
+            else:
+                for r in range(rows):
+                    keep = w * ((r + 1 + w - 1) // w)
+                    row = t[r, :keep].copy()
+                    row[r + 1:] = 0.0
+                    out.append(row)
     return np.concatenate(out)
 
 
