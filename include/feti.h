@@ -82,7 +82,8 @@ typedef struct {
 typedef struct {
   feti_precision prec;
   int32_t refine_every;       /* PCPG: recompute the FP64 residual every k iterations (0 = never) */
-  double tol;                 /* PCPG: stop when ||P r|| <= tol * ||P r_0|| */
+  double tol;                 /* PCPG: stop when ||P r|| <= tol * ||P r_0||, or at the rounding level
+                                 ||P r|| <= 64 eps (||d|| + ||F lambda_0||) */
   int32_t maxit;
   int32_t recompute_X;        /* reserved: 1 = do not keep X_i after assembly */
   void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator (NULL: cudaMalloc) */
@@ -91,13 +92,16 @@ typedef struct {
   void* stream;               /* cudaStream_t; NULL = legacy default stream */
   int32_t leaf_dofs;          /* nested-dissection leaf size (0 = 16) */
   int32_t use_coords;         /* 1 = coordinate bisection when coords are given */
+  double refine_drop;         /* PCPG: also recompute the FP64 residual once ||P r|| has dropped by this
+                                 factor since the last recomputation (0 = off) */
 } feti_options;
 
 typedef struct {
   int32_t iterations;
   int32_t refinements;
-  double rel_residual;        /* ||P r|| / ||P r_0|| in FP64 at exit */
+  double rel_residual;        /* ||P r|| / ||P r_0|| at exit (FP64 residual when refinement is on) */
   int32_t converged;
+  double initial_residual;    /* ||P r_0|| (FP64) */
 } feti_solve_info;
 
 typedef struct {
@@ -150,8 +154,14 @@ feti_status feti_apply_implicit(feti_ctx* ctx, const double* p_dev, double* q_de
 /* Projected PCPG (Algorithm 1, M = I) for the dual problem (eq. 7), then
  * alpha (eq. 8) and u (eq. 5).  lambda_dev [n_lambda], alpha_dev [sum d_i],
  * u_dev [sum n_i] (subdomains concatenated in order); any may be NULL except
- * lambda_dev.  Synchronises.  Returns FETI_ERR_NOT_CONVERGED (informative)
- * when maxit is reached. */
+ * lambda_dev.  The iteration runs on the device with the explicit F_i; the
+ * host reads a small control block once per chunk of iterations.  With
+ * refine_every = k > 0 the residual is recomputed with the FP64 implicit
+ * operator (eq. 11) every k iterations, with refine_drop = f > 0 whenever
+ * ||P r|| has dropped by f since the last recomputation; with either on, the
+ * stopping rule is met only on such an FP64 residual.  Synchronises.
+ * Returns FETI_ERR_NOT_CONVERGED (informative) at maxit or on a breakdown
+ * (p.F p <= 0). */
 feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev,
                        feti_solve_info* info);
 

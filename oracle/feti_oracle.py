@@ -138,9 +138,10 @@ def Gt_times(problem, lam: np.ndarray) -> np.ndarray:
 
 
 def feti_equation_residuals(problem, lam, us):
-    """Residuals of the FETI system (eq. 3) for a computed (lambda, u):
-    per subdomain ||K_i u_i + B_i^T lambda - f_i|| / ||f_i - B_i^T lambda||
-    (the primal rows) and the gluing / Dirichlet rows B u - c."""
+    """Residuals of the FETI system (eq. 3) for a computed (lambda, u): per
+    subdomain the normwise backward error of the primal rows,
+    ||K_i u_i + B_i^T lambda - f_i|| / (||K_i||_F ||u_i|| + ||f_i - B_i^T lambda||),
+    and the gluing / Dirichlet rows B u - c."""
     prim = []
     Bu = -np.asarray(problem.c, dtype=np.float64).copy()
     for s, u in zip(problem.subs, us):
@@ -148,7 +149,8 @@ def feti_equation_residuals(problem, lam, us):
         btl = np.zeros(s.n)
         np.add.at(btl, s.B_dof, s.B_sign * lam[np.asarray(s.B_lambda, dtype=np.int64)])
         rhs = s.f - btl
-        prim.append(np.linalg.norm(K @ u - rhs) / max(np.linalg.norm(rhs), 1e-300))
+        scale = sp.linalg.norm(K) * np.linalg.norm(u) + np.linalg.norm(rhs)
+        prim.append(np.linalg.norm(K @ u - rhs) / max(scale, 1e-300))
         np.add.at(Bu, np.asarray(s.B_lambda, dtype=np.int64), s.B_sign * u[s.B_dof])
     return np.asarray(prim), Bu
 
@@ -185,7 +187,11 @@ class Projector:
 
 def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=False):
     """Algorithm 1 (PCPG) with M = I and lambda_I = G (G^T G)^{-1} e.
-    Stops when ||w_k|| <= tol * ||w_0||.  Returns (lambda, iterations, info)."""
+    Stops when ||w_k|| <= tol * ||w_0||, or when ||w_k|| has reached the
+    rounding level of the residual, ||w_k|| <= 64 eps (||d|| + ||F lambda_I||)
+    (Algorithm 1 only says "until convergence"; without the floor a problem
+    whose lambda_I already solves the dual problem could never stop, since
+    w_0 is then rounding noise).  Returns (lambda, iterations, info)."""
     if G is None:
         G = G_matrix(problem)
     if e is None:
@@ -195,7 +201,9 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
     P = Projector(G)
     Fop = lambda v: apply_F(problem, Fs, v)
     lam = G @ P.coarse_solve(e)
-    r = d - Fop(lam)
+    Flam = Fop(lam)
+    r = d - Flam
+    floor = 64.0 * np.finfo(np.float64).eps * (np.linalg.norm(d) + np.linalg.norm(Flam))
     w = P(r)
     y = P(w)            # y = P M w with M = I
     p = y.copy()
@@ -203,7 +211,7 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
     nw0 = float(np.linalg.norm(w))
     hist = [G.T @ lam - e] if history else None
     k = 0
-    if nw0 == 0.0:
+    if nw0 <= floor:
         return lam, 0, dict(P=P, G=G, d=d, e=e, hist=hist)
     while k < maxit:
         q = Fop(p)
@@ -219,7 +227,7 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
         k += 1
         if history:
             hist.append(G.T @ lam - e)
-        if np.linalg.norm(w) <= tol * nw0:
+        if np.linalg.norm(w) <= max(tol * nw0, floor):
             break
     return lam, k, dict(P=P, G=G, d=d, e=e, hist=hist)
 

@@ -212,7 +212,8 @@ void build(feti_ctx* c) {
 
   // ---- concatenate pattern tables
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
-  std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs;
+  std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs, usm_ofs;
+  std::vector<int> sn_small;
   std::vector<int> lvl_off, lvl_sn, pat_lvl0(c->pats.size());
   int64_t max_usize = 0;
   std::vector<int> pat_sn0(c->pats.size());
@@ -232,6 +233,8 @@ void build(feti_ctx* c) {
       Lofs.push_back(P.Lofs[s]);
       kmap_off.push_back(km0 + P.kmap_off[s]);
       upd_ofs.push_back(P.upd_stack_ofs[s]);
+      sn_small.push_back(P.sn_small[s]);
+      usm_ofs.push_back(P.usm_ofs[s]);
       uofs.push_back(P.uofs[s]);
     }
     pat_lvl0[p] = (int)lvl_off.size();
@@ -296,7 +299,7 @@ void build(feti_ctx* c) {
   int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
-  int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0;
+  int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0, max_usm = 0;
   size_t esz = c->fp32 ? 4 : 8;
   double apply_bytes = 0, stored_bytes = 0;
   c->colperm_ofs.resize(ns);
@@ -387,6 +390,7 @@ void build(feti_ctx* c) {
     syrke += B.syrk_exec_flops;
     implb += 2.0 * 8.0 * P.nnzL;
     max_chol = std::max(max_chol, P.chol_stack);
+    max_usm = std::max(max_usm, P.usm_size);
     max_cf = std::max(max_cf, P.chol_front);
     max_rhs = std::max(max_rhs, B.rhs_stack);
     max_rf = std::max(max_rf, B.rhs_front);
@@ -525,11 +529,12 @@ void build(feti_ctx* c) {
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev));
   c->nsm = prop.multiProcessorCount;
-  c->grid_chol = std::min(ns, c->nsm * 3);
+  c->grid_chol = std::min(ns, c->nsm * chol_ctas_per_sm());
   c->grid_trsm = std::min(ns, c->nsm * 3);
   c->chol_front = max_cf;
   c->rhs_front = max_rf;
-  c->ws_stride = std::max(max_cf + max_chol, max_rf + max_rhs);
+  c->chol_stack = max_chol;
+  c->ws_stride = std::max(max_cf + max_chol + max_usm, max_rf + max_rhs);
   c->ws_stride = (c->ws_stride + 31) / 32 * 32;
   int gw = std::max(c->grid_chol, c->grid_trsm);
 
@@ -554,6 +559,8 @@ void build(feti_ctx* c) {
   D.lvl_off = upload(c, lvl_off);
   D.lvl_sn = upload(c, lvl_sn);
   D.uofs = upload(c, uofs);
+  D.sn_small = upload(c, sn_small);
+  D.usm_ofs = upload(c, usm_ofs);
   D.jb = upload(c, jb);
   D.je = upload(c, je);
   D.jo = upload(c, jo);
@@ -650,8 +657,10 @@ void build(feti_ctx* c) {
     c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 8 * 8);
     c->d_cv = (double*)dalloc(c, (size_t)D2 * 4 * 8);
     c->d_sc = (double*)dalloc(c, 16 * 8);
-    c->d_part = (double*)dalloc(c, 1024 * 8);
+    c->d_part = (double*)dalloc(c, 2 * kPcgMaxBlocks * 8);
     CK(cudaMallocHost((void**)&c->h_sc, 16 * 8));
+    c->d_ctrl = (PcgCtrl*)dalloc(c, sizeof(PcgCtrl));
+    CK(cudaMallocHost((void**)&c->h_ctrl, sizeof(PcgCtrl)));
     launch_build_G(D, c->d_colsub, qo, c->d_R, c->d_G6, c->st);
     CK(cudaGetLastError());
     size_t sm = implicit_smem(c->nmax, c->impl_maxf);
@@ -759,6 +768,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   CK(cudaEventRecord(ctx->ev[0], st));
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
+              ctx->chol_stack,
               ctx->grid_chol, ctx->d_status, st);
   launch_diag_recip(ctx->P, ctx->nsub, ctx->P.dinv, st);
   ctx->stats.launches += 4;  // Cholesky, reciprocal pivots, pruned TRSM, SYRK
@@ -935,6 +945,10 @@ void feti_destroy(feti_ctx* ctx) {
       if (x) cudaEventDestroy(x);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  for (auto e : ctx->pcg_ev) cudaEventDestroy(e);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   for (auto& b : ctx->bufs) {
     if (ctx->opt.dev_free) ctx->opt.dev_free(b.p, ctx->opt.alloc_ctx);
     else if (!ctx->opt.dev_alloc) cudaFree(b.p);

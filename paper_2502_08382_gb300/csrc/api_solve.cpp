@@ -1,7 +1,10 @@
 // Solver-side entry points: implicit apply (eq. 11), projected PCG
 // (Algorithm 1 with M = I) with FP64 residual replacement, recovery of alpha
 // (eq. 8) and u (eq. 5), and the coarse problem set-up (eqs. 6-8).
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <vector>
 #include <stdexcept>
 #include <string>
 
@@ -22,12 +25,8 @@ struct CudaErr : std::runtime_error {
     if (e_ != cudaSuccess) throw CudaErr(std::string(#x) + ": " + cudaGetErrorString(e_));   \
   } while (0)
 
-constexpr int kNPart = 512;
-
 // vectors inside ctx->d_vec (each n_lambda long)
-enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0 };
-// scalars in ctx->d_sc
-enum { S_WY = 0, S_PQ = 1, S_WYN = 2, S_TMP = 3 };
+enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM };
 // coarse vectors in ctx->d_cv (each D long)
 enum { C_E = 0, C_C, C_Z, C_A };
 
@@ -95,24 +94,84 @@ void coarse_setup(feti_ctx* c) {
   CKS(cudaGetLastError());
 }
 
-// out = P x = x - G (G^T G)^{-1} G^T x
-void project(feti_ctx* c, const double* x, double* out) {
-  if (c->dtot == 0) {
-    if (out != x) CKS(cudaMemcpyAsync(out, x, (size_t)c->nlam * 8, cudaMemcpyDeviceToDevice, c->st));
-    return;
-  }
-  launch_gt(c->P, c->nsub, c->d_G6, x, cvec(c, C_C), c->st);
-  launch_gemv(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), c->dtot, 1.0, c->st);
-  launch_gz(c->P, c->d_colsub, c->d_c0, c->d_c1, c->nlam, c->d_G6, x, cvec(c, C_Z), 1.0, out, c->st);
-  c->stats.launches += 3;
+PcgCtrl* ctrl_dev(feti_ctx* c) { return c->d_ctrl; }
+int* active_dev(feti_ctx* c) { return reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_ctrl) + offsetof(PcgCtrl, active)); }
+
+// copy the control block to pinned host memory and wait for the stream
+const PcgCtrl& read_ctrl(feti_ctx* c) {
+  CKS(cudaMemcpyAsync(c->h_ctrl, c->d_ctrl, sizeof(PcgCtrl), cudaMemcpyDeviceToHost, c->st));
+  CKS(cudaStreamSynchronize(c->st));
+  return *c->h_ctrl;
 }
 
-double dot_host(feti_ctx* c, const double* x, const double* y, int slot) {
-  launch_dot(x, y, c->nlam, c->d_part, kNPart, c->d_sc + slot, c->st);
-  c->stats.launches += 2;
-  CKS(cudaMemcpyAsync(c->h_sc + slot, c->d_sc + slot, 8, cudaMemcpyDeviceToHost, c->st));
-  CKS(cudaStreamSynchronize(c->st));
-  return c->h_sc[slot];
+// One PCPG iteration (Algorithm 1, M = I) on the device, seven launches; every
+// kernel returns at once if the control block says the iteration has stopped.
+// ev (4 events or null): before the scatter, around the F-streaming kernel, after the gather.
+void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStream_t st, bool capture) {
+  const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+  const int n = c->nlam, D = c->dtot;
+  double *d = vec(c, V_D), *r = vec(c, V_R), *w = vec(c, V_W), *p = vec(c, V_P), *q = vec(c, V_Q);
+  PcgCtrl* ctrl = ctrl_dev(c);
+  const auto& cand = c->apply_cands[c->apply_pick];
+  if (ev) CKS(cudaEventRecordWithFlags(ev[0], st, evf));
+  launch_pcg_scatter(c->fp32, c->P.qmap, c->ncols, p, w, c->d_pg, ctrl, st);
+  launch_apply_core(c->P, c->fp32, c->d_tdesc, c->napply, c->d_F, c->d_pg, c->d_rowpart, c->d_tpart, c->d_blocks,
+                    c->nblocks, c->d_qi, cand.grid, cand.variant, active_dev(c), st, ev ? ev[1] : nullptr,
+                    ev ? ev[2] : nullptr, capture);
+  launch_pcg_gather_dot(c->d_c0, c->d_c1, n, c->d_qi, p, w, q, c->d_part, ctrl, st);
+  if (ev) CKS(cudaEventRecordWithFlags(ev[3], st, evf));
+  if (D > 0) {
+    launch_pcg_gt(c->P, c->nsub, c->d_G6, r, q, d, 0, cvec(c, C_C), ctrl, st);
+    launch_gemv_rows(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), D, ctrl, 0, st);
+  }
+  launch_pcg_update(c->P, c->d_colsub, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam,
+                    r, w, c->d_part + kPcgMaxBlocks, 0, ctrl, st);
+}
+
+int iteration_launches(feti_ctx* c) { return c->dtot > 0 ? 7 : 5; }
+
+// Capture `chunk` iterations on the private stream into one CUDA graph (once
+// per context and chunk size); replaying it enqueues the whole chunk at once.
+void build_chunk_graph(feti_ctx* c, double* lam, int chunk) {
+  if (c->pcg_exec && c->pcg_chunk == chunk) return;
+  if (c->pcg_exec) {
+    CKS(cudaGraphExecDestroy(c->pcg_exec));
+    c->pcg_exec = nullptr;
+  }
+  if (!c->cap_st) CKS(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  while ((int)c->pcg_ev.size() < 4 * chunk) {
+    cudaEvent_t e;
+    CKS(cudaEventCreate(&e));
+    c->pcg_ev.push_back(e);
+  }
+  cudaGraph_t g = nullptr;
+  CKS(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < chunk; ++k) enqueue_iteration(c, lam, &c->pcg_ev[4 * k], c->cap_st, true);
+  cudaError_t e = cudaStreamEndCapture(c->cap_st, &g);
+  if (e != cudaSuccess) throw CudaErr(std::string("capture of the PCPG chunk: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) throw CudaErr(std::string("instantiation of the PCPG chunk: ") + cudaGetErrorString(e));
+  c->pcg_chunk = chunk;
+}
+
+// Residual replacement with the FP64 implicit operator (eq. 11): q = F_64 lambda,
+// r = d - q, w = P r (mode 1), or the start of the iteration (mode 2, which also
+// sets ||w_0|| and the rounding floor).
+void enqueue_refresh(feti_ctx* c, double* lam, int mode) {
+  cudaStream_t st = c->st;
+  const int n = c->nlam, D = c->dtot;
+  double *d = vec(c, V_D), *r = vec(c, V_R), *w = vec(c, V_W), *p = vec(c, V_P), *q = vec(c, V_Q);
+  PcgCtrl* ctrl = ctrl_dev(c);
+  implicit_apply(c, lam, q);
+  if (mode == 2) launch_pcg_norms(d, q, n, ctrl, st);
+  if (D > 0) {
+    launch_pcg_gt(c->P, c->nsub, c->d_G6, r, q, d, 1, cvec(c, C_C), ctrl, st);
+    launch_gemv_rows(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), D, ctrl, 1, st);
+  }
+  launch_pcg_update(c->P, c->d_colsub, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam,
+                    r, w, c->d_part + kPcgMaxBlocks, mode, ctrl, st);
+  c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0);
 }
 
 }  // namespace
@@ -147,8 +206,8 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     cudaStream_t st = ctx->st;
     const int n = ctx->nlam;
     const int D = ctx->dtot;
-    double* lam = lambda_dev;
-    double *d = vec(ctx, V_D), *r = vec(ctx, V_R), *w = vec(ctx, V_W), *p = vec(ctx, V_P), *q = vec(ctx, V_Q);
+    double* lam = vec(ctx, V_LAM);  // the iteration runs on an internal lambda (fixed pointers in the graph)
+    double *d = vec(ctx, V_D), *r = vec(ctx, V_R), *q = vec(ctx, V_Q), *p = vec(ctx, V_P);
     // e = R^T f;  lambda_I = G (G^T G)^{-1} e
     if (D > 0) {
       launch_rtf(ctx->P, ctx->nsub, ctx->d_R, ctx->d_f, cvec(ctx, C_E), st);
@@ -162,64 +221,76 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     launch_implicit(1, ctx->P, ctx->d_impl_order, ctx->nsub, ctx->d_queue + 32, nullptr, ctx->d_f, ctx->d_qi,
                     nullptr, ctx->d_uws, ctx->ustride, ctx->nmax, ctx->impl_maxf, ctx->grid_impl, ctx->impl_smem, st);
     launch_gather_minus_c(ctx->d_c0, ctx->d_c1, n, ctx->d_qi, ctx->d_c, d, st);
-    // r0 = d - F lambda_0 (FP64 implicit), w0 = P r0, y0 = w0 (M = I), p0 = y0
-    implicit_apply(ctx, lam, q);
-    launch_sub(d, q, r, n, st);
-    project(ctx, r, w);
-    CKS(cudaMemcpyAsync(p, w, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
-    double wy = dot_host(ctx, w, w, S_WY);
-    const double nw0 = std::sqrt(wy);
+    // control block; p = 0 so that the first p = w + beta p (beta = 0) is w_0
     const double tol = ctx->opt.tol > 0 ? ctx->opt.tol : 1e-10;
     const int maxit = ctx->opt.maxit > 0 ? ctx->opt.maxit : 1000;
+    PcgCtrl h{};
+    h.tol = tol;
+    h.maxit = maxit;
+    h.active = 1;
+    *ctx->h_ctrl = h;
+    CKS(cudaMemcpyAsync(ctx->d_ctrl, ctx->h_ctrl, sizeof(PcgCtrl), cudaMemcpyHostToDevice, st));
+    CKS(cudaMemsetAsync(p, 0, (size_t)n * 8, st));
+    // r_0 = d - F_64 lambda_0, w_0 = P r_0 (FP64 implicit operator)
+    enqueue_refresh(ctx, lam, 2);
+    PcgCtrl cur = read_ctrl(ctx);
+    const double nw0 = cur.nw0;
     const int kref = ctx->opt.refine_every;
-    int it = 0, nref = 0;
-    bool conv = nw0 == 0.0;
-    double rel = nw0 == 0.0 ? 0.0 : 1.0;
-    while (!conv && it < maxit) {
-      // q = F p (explicit, stored precision); delta = (w.y) / (p.q)
-      feti_status s = feti_apply(ctx, p, q);
-      if (s != FETI_OK) return s;
-      launch_dot(p, q, n, ctx->d_part, kNPart, ctx->d_sc + S_PQ, st);
-      launch_pcg_upd1(lam, r, p, q, ctx->d_sc, n, st);
-      ctx->stats.launches += 3;
-      ++it;
-      bool refined = false;
-      if (kref > 0 && it % kref == 0) {
-        // residual replacement with the FP64 implicit operator
-        implicit_apply(ctx, lam, q);
-        launch_sub(d, q, r, n, st);
-        ctx->stats.launches += 1;
+    const double drop = ctx->opt.refine_drop;
+    const bool refine = kref > 0 || drop > 0.0;
+    // iterations are enqueued in chunks; the host reads the control block once per chunk
+    const int chunk = kref > 0 ? std::min(kref, 32) : 8;
+    int nref = 0, it_ref = 0;
+    double nw_ref = nw0;
+    bool conv = cur.conv != 0;
+    bool last_refresh = true;  // r holds d - F_64 lambda (true after the start and after a replacement)
+    if (!conv) build_chunk_graph(ctx, lam, chunk);
+    while (!conv && cur.it < maxit && !cur.breakdown) {
+      int todo = chunk;
+      if (kref > 0) todo = std::min(todo, std::max(1, kref - (cur.it - it_ref)));
+      const int it0 = cur.it;
+      if (todo == chunk) {
+        CKS(cudaGraphLaunch(ctx->pcg_exec, st));
+      } else {
+        for (int k = 0; k < todo; ++k) enqueue_iteration(ctx, lam, &ctx->pcg_ev[4 * k], st, false);
+      }
+      ctx->stats.launches += (int64_t)todo * iteration_launches(ctx);
+      cur = read_ctrl(ctx);
+      const int done = cur.it - it0;  // iterations that ran (later ones returned at once)
+      if (done > 0) last_refresh = false;
+      ctx->stats.apply_calls += done;
+      if (ctx->prof) {
+        for (int k = 0; k < done; ++k) {
+          float t = 0;
+          CKS(cudaEventElapsedTime(&t, ctx->pcg_ev[4 * k], ctx->pcg_ev[4 * k + 3]));
+          ctx->stats.apply_ms += t;
+          CKS(cudaEventElapsedTime(&t, ctx->pcg_ev[4 * k + 1], ctx->pcg_ev[4 * k + 2]));
+          ctx->stats.apply_tiles_ms += t;
+        }
+      }
+      if (cur.breakdown) break;
+      const bool due = refine && ((kref > 0 && cur.it - it_ref >= kref) || (drop > 0.0 && cur.nw <= drop * nw_ref) ||
+                                  cur.conv);
+      if (due) {
+        // residual replacement (and, after the recursive residual met the stopping rule, its FP64 check)
+        enqueue_refresh(ctx, lam, 1);
+        cur = read_ctrl(ctx);
+        last_refresh = true;
         ++nref;
-        refined = true;
+        it_ref = cur.it;
+        nw_ref = cur.nw;
       }
-      project(ctx, r, w);
-      double wyn = dot_host(ctx, w, w, S_WYN);
-      rel = std::sqrt(wyn) / nw0;
-      if (rel <= tol) {
-        if (kref > 0 && !refined) {
-          implicit_apply(ctx, lam, q);
-          launch_sub(d, q, r, n, st);
-          ++nref;
-          project(ctx, r, w);
-          wyn = dot_host(ctx, w, w, S_WYN);
-          rel = std::sqrt(wyn) / nw0;
-        }
-        if (rel <= tol) {
-          conv = true;
-          break;
-        }
-      }
-      // p = y + beta p, beta = (w_new . y_new) / (w . y)
-      launch_pcg_upd2(p, w, ctx->d_sc, n, st);
-      launch_scalar_copy(ctx->d_sc, S_WY, S_WYN, st);
-      ctx->stats.launches += 2;
-      wy = wyn;
+      conv = cur.conv != 0;
     }
-    // alpha = -(G^T G)^{-1} G^T (d - F lambda)  (eq. 8, FP64 implicit F)
+    CKS(cudaMemcpyAsync(lambda_dev, lam, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+    // alpha = -(G^T G)^{-1} G^T (d - F lambda)  (eq. 8, FP64 implicit F).  When the iteration
+    // ended on a residual replacement, r already is d - F_64 lambda for the final lambda.
     double* alpha = alpha_dev ? alpha_dev : cvec(ctx, C_A);
     if (D > 0) {
-      implicit_apply(ctx, lam, q);
-      launch_sub(d, q, r, n, st);
+      if (!last_refresh) {
+        implicit_apply(ctx, lam, q);
+        launch_sub(d, q, r, n, st);
+      }
       launch_gt(ctx->P, ctx->nsub, ctx->d_G6, r, cvec(ctx, C_C), st);
       launch_gemv(ctx->d_Ainv, cvec(ctx, C_C), alpha, D, -1.0, st);
     }
@@ -236,12 +307,14 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     CKS(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status & kStatTimeout) return set_error(ctx, FETI_ERR_TIMEOUT, "a bounded device wait gave up");
     if (info) {
-      info->iterations = it;
+      info->iterations = cur.it;
       info->refinements = nref;
-      info->rel_residual = rel;
+      info->rel_residual = cur.rel;
       info->converged = conv ? 1 : 0;
+      info->initial_residual = nw0;
     }
-    if (!conv) return set_error(ctx, FETI_ERR_NOT_CONVERGED, "PCPG reached maxit");
+    if (!conv) return set_error(ctx, FETI_ERR_NOT_CONVERGED,
+                                cur.breakdown ? "PCPG broke down (p.Fp <= 0)" : "PCPG reached maxit");
     return FETI_OK;
   } catch (std::exception& e) {
     return set_error(ctx, FETI_ERR_CUDA, e.what());

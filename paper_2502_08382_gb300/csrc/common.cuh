@@ -64,6 +64,8 @@ struct DevPlan {
   const int* lvl_off;        // [lvl0 + l] absolute offsets into lvl_sn
   const int* lvl_sn;         // local supernode ids, level by level
   const int64_t* uofs;       // [sn] update-vector offset of the supernode (relative to the CTA workspace)
+  const int* sn_small;       // [sn] 1: small-subtree supernode (warp-factored front)
+  const int64_t* usm_ofs;    // [sn] update-block slot of a small supernode (relative to the CTA's small region)
   double* dinv;              // [dof + j] reciprocal pivots 1 / L_jj (written after the factorisation)
   // bplan tables
   const int* jb;
@@ -135,6 +137,32 @@ struct __align__(16) TileDesc {
   int pcol;        // pg offset of the tile's column block
   int pad0, pad1;
 };
+
+// Control block of the projected CG (Algorithm 1), in device memory.  The
+// vector kernels read and update it; the host reads it once per chunk of
+// enqueued iterations.
+struct PcgCtrl {
+  double wy;      // w.w of the current iterate (M = I: y = w)
+  double wy_prev; // w.w before the last iteration's update (a residual replacement divides by it)
+  double pq;      // p.q of the current iteration
+  double delta;   // step length (w.w) / (p.q)
+  double beta;    // (w_new.w_new) / (w.w) for p <- w + beta p
+  double wyn;     // w.w after the update
+  double nw;      // ||w|| after the update
+  double nw0;     // ||w_0||
+  double tol;     // relative tolerance on ||w|| / ||w_0||
+  double floor;   // rounding level of the residual: 64 eps (||d|| + ||F lambda_0||)
+  double rel;     // ||w|| / ||w_0||
+  double dd, qq;  // ||d||^2 and ||F lambda_0||^2 (for the floor)
+  int active;     // 1 while iterating; kernels of later iterations return when 0
+  int it;         // iterations done
+  int maxit;
+  int conv;       // the last ||w|| met the stopping rule
+  int breakdown;  // p.q <= 0 was met
+  int cnt_dot, cnt_upd;  // arrival counters of the last-block reductions
+  int pad;
+};
+constexpr int kPcgMaxBlocks = 1184;  // block partials per reduction
 
 // status word bits written by kernels
 enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };

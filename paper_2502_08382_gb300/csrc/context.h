@@ -57,7 +57,7 @@ struct feti_ctx {
   void* d_X = nullptr;
   void* d_F = nullptr;
   double* d_ws = nullptr;
-  int64_t ws_stride = 0, chol_front = 0, rhs_front = 0;
+  int64_t ws_stride = 0, chol_front = 0, rhs_front = 0, chol_stack = 0;
   double* d_trow = nullptr;
   double* d_tpart = nullptr;
   double* d_qi = nullptr;
@@ -108,8 +108,14 @@ struct feti_ctx {
   double* d_vec = nullptr;     // PCPG vectors (7 x n_lambda)
   double* d_cv = nullptr;      // coarse vectors (4 x D)
   double* d_sc = nullptr;      // scalars
-  double* d_part = nullptr;    // dot partials
+  double* d_part = nullptr;    // block partials of the PCPG reductions (2 x kPcgMaxBlocks)
   double* h_sc = nullptr;      // pinned host scalars
+  feti::PcgCtrl* d_ctrl = nullptr;  // PCPG control block
+  feti::PcgCtrl* h_ctrl = nullptr;  // pinned host copy
+  cudaStream_t cap_st = nullptr;     // private stream on which a chunk of PCPG iterations is captured
+  cudaGraphExec_t pcg_exec = nullptr;  // captured chunk of iterations (replayed on st)
+  int pcg_chunk = 0;
+  std::vector<cudaEvent_t> pcg_ev;  // 4 events per captured iteration (apply timing)
   int* d_dofsub = nullptr;
   // adjoint (element data and dense work buffers, allocated on first use)
   std::vector<int64_t> elem_ofs, elem_dk_ofs, elem_dofs_ofs;

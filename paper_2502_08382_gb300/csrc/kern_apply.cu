@@ -6,8 +6,9 @@
 //  1. tiles:  every warp streams whole F tiles from HBM straight into
 //             registers with 16-byte coalesced loads (each warp-wide load
 //             covers 512 contiguous bytes: two FP32 rows or one FP64 row),
-//             keeping two batches of BATCH loads in flight, and writes per
-//             tile t the row partial F_t p_bj (row slot t) and the column
+//             keeping two batches of BATCH loads in flight (only the batches
+//             that hold stored rows), and writes per tile t the row partial
+//             F_t p_bj (row slot t, stored rows only) and the column
 //             partial F_t^T p_bi (column slot t; for a diagonal tile only its
 //             strictly lower part, transposed).  Tiles are dealt to warps
 //             round-robin, so all warps stream neighbouring tiles together
@@ -87,7 +88,7 @@ struct Batch {
   typename Vec16<TF>::T v[BATCH];
   typename Vec16<TF>::T pc;  // p of the tile's column block, this lane's chunk
   TF pr;                     // p of one row of the batch (shuffled out per load)
-  int t, b, diag;
+  int t, b, rows, diag;
 };
 
 template <typename TF, int BATCH>
@@ -107,6 +108,8 @@ struct TileStream {
   TileDesc dI;    // descriptor of the tile being issued
   TileDesc dP;    // prefetched descriptor of the next tile of this warp
 
+  // Item k of this warp = batch k % NBT of its tile k / NBT.  A batch that lies
+  // entirely below the stored rows (the ragged last block row) issues no load.
   __device__ __forceinline__ void issue(int k, Batch<TF, BATCH>& B) {
     const int j = k / NBT, b = k % NBT;
     const int t = gw + j * nw;
@@ -119,15 +122,30 @@ struct TileStream {
     const bool diag = (d.flags & kTileDiag) != 0;
     B.t = t;
     B.b = b;
+    B.rows = d.rows;
     B.diag = diag;
+    if (b * ROWS_B >= d.rows) return;  // empty batch (warp-uniform)
     const TF* Ft = F + d.f_ofs;
+    if (!diag && d.rows == kT) {
 #pragma unroll
-    for (int i = 0; i < BATCH; ++i) {
-      const int r = b * ROWS_B + i * RPL + half;
-      const bool ok = r < d.rows && (!diag || cq * V <= r);
-      const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(r) : (int64_t)r * kT;
-      if (ok) B.v[i] = ld_stream(reinterpret_cast<const VT*>(Ft + off + cq * V));
-      else B.v[i] = VT{};
+      for (int i = 0; i < BATCH; ++i) {
+        const int r = b * ROWS_B + i * RPL + half;
+        B.v[i] = ld_stream(reinterpret_cast<const VT*>(Ft + r * kT + cq * V));
+      }
+    } else {
+      // ragged or diagonal tile: every lane loads from a stored position (its row clamped
+      // to the last stored row, its chunk to the one holding the diagonal) and zeroes
+      // what lies outside, so no load sits behind a branch
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int r = b * ROWS_B + i * RPL + half;
+        const int rr = min(r, d.rows - 1);
+        const int cc = diag ? min(cq, rr / V) : cq;
+        const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(rr) : (int64_t)rr * kT;
+        const VT x = ld_stream(reinterpret_cast<const VT*>(Ft + off + cc * V));
+        const bool ok = r < d.rows && (!diag || cq * V <= r);
+        B.v[i] = ok ? x : VT{};
+      }
     }
     B.pc = *reinterpret_cast<const VT*>(pg + d.pcol + cq * V);
     B.pr = pg[d.prow + b * ROWS_B + (lane % ROWS_B)];
@@ -139,26 +157,39 @@ __device__ __forceinline__ void consume(const Batch<TF, BATCH>& B, TF* cacc, TF*
                                         int cq, int half) {
   using TS = TileStream<TF, BATCH>;
   constexpr int V = TS::V, NCH = TS::NCH, RPL = TS::RPL, ROWS_B = TS::ROWS_B, NBT = TS::NBT;
-  TF rs[BATCH];
+  if (B.b * ROWS_B < B.rows) {
+    TF rs[BATCH];
+    if (B.diag) {
 #pragma unroll
-  for (int i = 0; i < BATCH; ++i) {
-    const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
-    TF s = (TF)0;
+      for (int i = 0; i < BATCH; ++i) {
+        const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
+        TF s = (TF)0;
 #pragma unroll
-    for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
-    rs[i] = s;
-    const int r = B.b * ROWS_B + i * RPL + half;
+        for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
+        rs[i] = s;
+        const int r = B.b * ROWS_B + i * RPL + half;
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      const TF x = (B.diag && cq * V + e >= r) ? (TF)0 : comp(B.v[i], e);
-      cacc[e] = fma(x, pr, cacc[e]);
+        for (int e = 0; e < V; ++e) cacc[e] = fma(cq * V + e < r ? comp(B.v[i], e) : (TF)0, pr, cacc[e]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
+        TF s = (TF)0;
+#pragma unroll
+        for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
+        rs[i] = s;
+#pragma unroll
+        for (int e = 0; e < V; ++e) cacc[e] = fma(comp(B.v[i], e), pr, cacc[e]);
+      }
     }
-  }
-  ReduceScatter<TF, BATCH, NCH / 2>::run(rs, lane);
-  constexpr int SPAN = NCH / BATCH;  // lanes holding the same row total
-  if (cq % SPAN == 0) {
-    const int r = B.b * ROWS_B + (cq / SPAN) * RPL + half;
-    rowpart[(int64_t)B.t * kT + r] = rs[0];
+    ReduceScatter<TF, BATCH, NCH / 2>::run(rs, lane);
+    constexpr int SPAN = NCH / BATCH;  // lanes holding the same row total
+    if (cq % SPAN == 0) {
+      const int r = B.b * ROWS_B + (cq / SPAN) * RPL + half;
+      // rows beyond the stored ones are padding columns of q_i, never gathered: not written
+      if (r < B.rows) rowpart[(int64_t)B.t * kT + r] = rs[0];
+    }
   }
   if (B.b == NBT - 1) {
     if constexpr (RPL == 2) {
@@ -181,7 +212,8 @@ template <typename TF, int BATCH>
 __global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDesc* __restrict__ desc, int ntiles,
                                                                    const TF* __restrict__ F,
                                                                    const TF* __restrict__ pg, TF* rowpart,
-                                                                   TF* colpart) {
+                                                                   TF* colpart, const int* active) {
+  if (active && *active == 0) return;  // the iteration this launch belongs to has stopped
   using TS = TileStream<TF, BATCH>;
   constexpr int V = TS::V, NBT = TS::NBT;
   TS ts;
@@ -219,7 +251,8 @@ __global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDe
 // one warp per (subdomain, block), FP64 sums in a fixed order.
 template <typename TF>
 __global__ void reduce_tiles_kernel(DevPlan P, const int2* blocks, int nblocks, const TF* rowpart,
-                                    const TF* colpart, double* qi) {
+                                    const TF* colpart, double* qi, const int* active) {
+  if (active && *active == 0) return;
   const int lane = threadIdx.x & 31;
   for (int wb = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wb < nblocks; wb += gridDim.x * blockDim.x / 32) {
     const int2 sb = blocks[wb];
@@ -255,25 +288,28 @@ void set_tiles_attr() {
   }
 }
 
-// variants of the tile kernel: 0 -> BATCH 8, 1 -> BATCH 16
+// variants of the tile kernel: 0 -> BATCH 4, 1 -> BATCH 8, 2 -> BATCH 16
 template <typename TF>
 void launch_tiles(int variant, int grid, cudaStream_t st, const TileDesc* desc, int ntiles, const TF* F,
-                  const TF* pg, TF* rowpart, TF* colpart) {
+                  const TF* pg, TF* rowpart, TF* colpart, const int* active = nullptr) {
   if (ntiles <= 0) return;
   if (variant == 0) {
+    set_tiles_attr<TF, 4>();
+    apply_tiles_kernel<TF, 4><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
+  } else if (variant == 1) {
     set_tiles_attr<TF, 8>();
-    apply_tiles_kernel<TF, 8><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart);
+    apply_tiles_kernel<TF, 8><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
   } else {
     set_tiles_attr<TF, 16>();
-    apply_tiles_kernel<TF, 16><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart);
+    apply_tiles_kernel<TF, 16><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
   }
 }
 
 template <typename TF>
 void launch_reduce(const DevPlan& P, const int2* blocks, int nblocks, const TF* rowpart, const TF* colpart,
-                   double* qi, cudaStream_t st) {
+                   double* qi, cudaStream_t st, const int* active = nullptr) {
   const int rg = std::max(1, std::min((nblocks + 7) / 8, 152 * 16));
-  reduce_tiles_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, rowpart, colpart, qi);
+  reduce_tiles_kernel<TF><<<rg, 256, 0, st>>>(P, blocks, nblocks, rowpart, colpart, qi, active);
 }
 
 }  // namespace
@@ -310,19 +346,41 @@ void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles,
                            nlam, q, grid, variant, st, ev_tiles0, ev_tiles1);
 }
 
-int apply_variants() { return 2; }
-
-int apply_max_ctas_per_sm(bool fp32, int variant) {
-  int nb = 0;
+// The F-streaming part of the apply for the projected CG, whose scatter and
+// gather are fused into its vector kernels: tiles then reduce, both skipped
+// when *active == 0 (an iteration enqueued after the solve has stopped).
+void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
+                       void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
+                       int variant, const int* active, cudaStream_t st, cudaEvent_t ev_tiles0,
+                       cudaEvent_t ev_tiles1, bool ev_external) {
+  // under stream capture only an external record becomes a timed event-record node
+  const unsigned evf = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (ev_tiles0) cudaEventRecordWithFlags(ev_tiles0, st, evf);
   if (fp32) {
-    if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, 8>, kApplyThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<float, 16>, kApplyThreads, 0);
+    launch_tiles<float>(variant, grid, st, desc, ntiles, (const float*)F, (const float*)pg, (float*)rowpart,
+                        (float*)colpart, active);
+    if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
+    launch_reduce<float>(P, blocks, nblocks, (const float*)rowpart, (const float*)colpart, qi, st, active);
   } else {
-    if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, 8>, kApplyThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<double, 16>, kApplyThreads, 0);
+    launch_tiles<double>(variant, grid, st, desc, ntiles, (const double*)F, (const double*)pg, (double*)rowpart,
+                         (double*)colpart, active);
+    if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
+    launch_reduce<double>(P, blocks, nblocks, (const double*)rowpart, (const double*)colpart, qi, st, active);
   }
+}
+
+int apply_variants() { return 3; }
+
+template <typename TF>
+static int occ_tiles(int variant) {
+  int nb = 0;
+  if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 4>, kApplyThreads, 0);
+  else if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 8>, kApplyThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 16>, kApplyThreads, 0);
   return nb;
 }
+
+int apply_max_ctas_per_sm(bool fp32, int variant) { return fp32 ? occ_tiles<float>(variant) : occ_tiles<double>(variant); }
 
 int apply_warps_per_cta() { return kApplyThreads / 32; }
 

@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "symbolic.h"
 
 namespace feti {
 namespace {
@@ -189,14 +190,129 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
   }
 }
 
+// ---------------------------------------------------------------- packed fronts in shared memory
+//
+// A front of width f <= kMidFront is assembled as a packed lower triangle
+// (column-major: column k holds rows k .. f-1) in shared memory, its first w
+// columns are factored right-looking, and the team (one warp, or the whole
+// CTA) spreads each trailing update evenly over its threads, so no FP64 work
+// is spent on padding.  Entry (i, k), i >= k, sits at pidx(f, i, k).
+
+constexpr int kWarpSlot = kSmallFront * (kSmallFront + 1) / 2;           // doubles per warp
+constexpr int kFrontSmem = (8 * kWarpSlot > kMidFront * (kMidFront + 1) / 2 ? 8 * kWarpSlot
+                                                                            : kMidFront * (kMidFront + 1) / 2);
+static_assert(kThreads == 256, "the small-front phase assumes 8 warps per CTA");
+static_assert(sizeof(Smem) <= (size_t)kFrontSmem * 8, "the tiled path aliases the packed-front buffer");
+
+__device__ __forceinline__ int pidx(int f, int i, int k) { return k * f - (k * (k - 1)) / 2 + (i - k); }
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TEAM == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Update block of child gc: a small child's lives in the CTA's small region, others on the stack.
+__device__ __forceinline__ const double* child_update(const DevPlan& P, int gc, const double* stack,
+                                                      const double* smallreg) {
+  return P.sn_small[gc] ? smallreg + P.usm_ofs[gc] : stack + P.upd_ofs[gc];
+}
+
+// Assemble front gs (K entries, rho on fixing DOFs, children's update blocks),
+// factor its first w columns, store the f x w panel to L (zeros above the
+// diagonal) and, if Uout, the r x r update block (column-major) for the parent.
+template <int TEAM>
+__device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const double* K, double* L, double rho,
+                             double* Fp, const double* stack, const double* smallreg, double* Uout, int* bad,
+                             int tid) {
+  const int gs = S.sn0 + s;
+  const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
+  const int np = f * (f + 1) / 2;
+  const int64_t L0 = P.Lofs[gs];
+  for (int e = tid; e < np; e += TEAM) Fp[e] = 0.0;
+  team_sync<TEAM>();
+  for (int64_t kk = P.kmap_off[gs] + tid; kk < P.kmap_off[gs + 1]; kk += TEAM) {
+    const int64_t rel = P.kmap_dst[kk] - L0;  // column-major f x w panel position
+    Fp[pidx(f, (int)(rel % f), (int)(rel / f))] = K[P.kmap_src[kk]];
+  }
+  team_sync<TEAM>();
+  for (int k = tid; k < S.nfix; k += TEAM)
+    if (P.fix_sn[S.fix0 + k] == s) {
+      const int64_t rel = P.fix_pos[S.fix0 + k] - L0;
+      Fp[pidx(f, (int)(rel % f), (int)(rel / f))] += rho;
+    }
+  for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
+    const int gc = S.sn0 + P.ch_list[c];
+    const int rc = P.sn_r[gc];
+    const double* U = child_update(P, gc, stack, smallreg);
+    const int* rl = P.rel + P.rel_off[gc];
+    team_sync<TEAM>();
+    for (int b = 0; b < rc; ++b)
+      for (int a = b + tid; a < rc; a += TEAM) Fp[pidx(f, rl[a], rl[b])] += U[(int64_t)b * rc + a];
+  }
+  team_sync<TEAM>();
+  // right-looking partial factorisation of the first w columns
+  for (int j = 0; j < w; ++j) {
+    const int cj = pidx(f, j, j);
+    if (tid == 0) {
+      double pv = Fp[cj];
+      if (!(pv > 0.0)) {
+        *bad = 1;
+        pv = 1.0;
+      }
+      Fp[cj] = sqrt(pv);
+    }
+    team_sync<TEAM>();
+    const double inv = 1.0 / Fp[cj];
+    for (int i = j + 1 + tid; i < f; i += TEAM) Fp[cj + (i - j)] *= inv;
+    team_sync<TEAM>();
+    // trailing update A[i][k] -= L[i][j] L[k][j], k in (j, f), i in [k, f): element e of the packed
+    // trailing triangle goes to thread e mod TEAM; (k, rem) walks the columns
+    int k = j + 1, rem = tid;
+    while (k < f && rem >= f - k) {
+      rem -= f - k;
+      ++k;
+    }
+    while (k < f) {
+      const int i = k + rem;
+      const double lkj = Fp[cj + (k - j)];
+      const int pk = pidx(f, k, k);
+      Fp[pk + rem] = fma(-Fp[cj + (i - j)], lkj, Fp[pk + rem]);
+      rem += TEAM;
+      while (k < f && rem >= f - k) {
+        rem -= f - k;
+        ++k;
+      }
+    }
+    team_sync<TEAM>();
+  }
+  for (int idx = tid; idx < f * w; idx += TEAM) {
+    const int row = idx % f, col = idx / f;
+    L[L0 + idx] = row >= col ? Fp[pidx(f, row, col)] : 0.0;
+  }
+  if (Uout)
+    for (int idx = tid; idx < r * r; idx += TEAM) {
+      const int a = idx % r, b = idx / r;
+      Uout[idx] = a >= b ? Fp[pidx(f, w + a, w + b)] : 0.0;
+    }
+  team_sync<TEAM>();
+}
+
+// One CTA per subdomain (persistent, queue sorted by decreasing cost).
+// Phase 1: the small subtrees, level by level from the leaves, one warp per
+// front.  Phase 2: the remaining supernodes in postorder, fronts up to
+// kMidFront in shared memory across the CTA, larger ones by the tiled path.
 __global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          double* ws, int64_t ws_stride, int64_t front_sz,
-                                                         int* status) {
-  __shared__ Smem sm;
+                                                         int64_t stack_sz, int* status) {
+  extern __shared__ double dsm[];
+  Smem& sm = *reinterpret_cast<Smem*>(dsm);
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  __shared__ double red[kThreads / 32];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   double* W = ws + (int64_t)blockIdx.x * ws_stride;
   double* stack = W + front_sz;
+  double* smallreg = stack + stack_sz;
   for (;;) {
     int it = pop_item(queue);
     if (it >= nsub) return;
@@ -209,19 +325,37 @@ __global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int*
     double mx = 0.0;
     for (int i = tid; i < S.n; i += kThreads) mx = fmax(mx, K[P.diag_src[S.diag0 + i]]);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0) sm.red[tid >> 5] = mx;
+    if (lane == 0) red[warp] = mx;
     __syncthreads();
-    if (tid == 0) {
-      double m2 = sm.red[0];
-      for (int k = 1; k < kThreads / 32; ++k) m2 = fmax(m2, sm.red[k]);
-      sm.red[0] = m2;
-      P.rho[si] = m2;
+    double rho = red[0];
+    for (int k = 1; k < kThreads / 32; ++k) rho = fmax(rho, red[k]);
+    if (tid == 0) P.rho[si] = rho;
+    // phase 1: small subtrees, one warp per front
+    const int* lvo = P.lvl_off + S.lvl0;
+    double* Fw = dsm + warp * kWarpSlot;
+    for (int l = 0; l < S.nlev; ++l) {
+      bool any = false;
+      for (int q = lvo[l]; q < lvo[l + 1]; ++q) any |= P.sn_small[S.sn0 + P.lvl_sn[q]] != 0;
+      if (!any) continue;
+      for (int q = lvo[l] + warp; q < lvo[l + 1]; q += kThreads / 32) {
+        const int s = P.lvl_sn[q];
+        const int gs = S.sn0 + s;
+        if (!P.sn_small[gs]) continue;
+        double* Uout = P.sn_parent[gs] >= 0 ? smallreg + P.usm_ofs[gs] : nullptr;
+        packed_front<32>(P, S, s, K, L, rho, Fw, stack, smallreg, Uout, &bad, lane);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const double rho = sm.red[0];
+    // phase 2: the rest in postorder
     for (int s = 0; s < S.nsn; ++s) {
       const int gs = S.sn0 + s;
+      if (P.sn_small[gs]) continue;
       const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
+      double* Uout = P.sn_parent[gs] >= 0 ? stack + P.upd_ofs[gs] : nullptr;
+      if (f <= kMidFront) {
+        packed_front<kThreads>(P, S, s, K, L, rho, dsm, stack, smallreg, Uout, &bad, tid);
+        continue;
+      }
       double* Ls = L + P.Lofs[gs];
       for (int64_t idx = tid; idx < (int64_t)f * w; idx += kThreads) Ls[idx] = 0.0;
       for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) W[idx] = 0.0;
@@ -229,11 +363,12 @@ __global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int*
       for (int64_t k = P.kmap_off[gs] + tid; k < P.kmap_off[gs + 1]; k += kThreads)
         L[P.kmap_dst[k]] = K[P.kmap_src[k]];
       __syncthreads();
-      if (tid < S.nfix && P.fix_sn[S.fix0 + tid] == s) L[P.fix_pos[S.fix0 + tid]] += rho;
+      for (int k = tid; k < S.nfix; k += kThreads)
+        if (P.fix_sn[S.fix0 + k] == s) L[P.fix_pos[S.fix0 + k]] += rho;
       for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
         const int gc = S.sn0 + P.ch_list[c];
         const int rc = P.sn_r[gc];
-        const double* U = stack + P.upd_ofs[gc];
+        const double* U = child_update(P, gc, stack, smallreg);
         const int* rl = P.rel + P.rel_off[gc];
         __syncthreads();
         for (int64_t idx = tid; idx < (int64_t)rc * rc; idx += kThreads) {
@@ -248,10 +383,8 @@ __global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int*
       __syncthreads();
       factor_front(sm, Ls, f, w, W, r, &bad);
       __syncthreads();
-      if (P.sn_parent[gs] >= 0) {
-        double* dst = stack + P.upd_ofs[gs];
-        for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) dst[idx] = W[idx];
-      }
+      if (Uout)
+        for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) Uout[idx] = W[idx];
       __syncthreads();
     }
     if (tid == 0 && bad) atomicOr(status, kStatNotSPD);
@@ -411,8 +544,18 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
 }  // namespace
 
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int grid, int* status, cudaStream_t st) {
-  chol_kernel<<<grid, kThreads, 0, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, status);
+                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st) {
+  const int smem = kFrontSmem * 8;
+  cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  chol_kernel<<<grid, kThreads, smem, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, stack_sz, status);
+}
+
+int chol_ctas_per_sm() {
+  const int smem = kFrontSmem * 8;
+  cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chol_kernel, kThreads, smem);
+  return nb > 0 ? nb : 1;
 }
 
 void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,

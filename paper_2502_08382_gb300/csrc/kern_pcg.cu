@@ -1,0 +1,268 @@
+// Vector kernels of the projected conjugate gradient (Algorithm 1, M = I),
+// fused so that one iteration is seven launches and no host round trip:
+//
+//   1. scatter:  p <- w + beta p is formed on the fly and gathered into the
+//                tile precision, pg[j] = p[map(j)] (Algorithm 2's scatter);
+//   2-3.         the F-streaming tiles and the per-block reduce (kern_apply.cu);
+//   4. gather:   q = F p (Algorithm 2's gather), p <- w + beta p stored, and
+//                the dot p.q; the last block to finish sums the block partials
+//                in a fixed order and sets delta = (w.w) / (p.q);
+//   5. G^T x:    c = G^T (r - delta q)   (or G^T (d - F lambda) on a refresh);
+//   6. z = (G^T G)^{-1} c  (explicit FP64 inverse, eqs. 6-8);
+//   7. update:   lambda += delta p, r -= delta q (or r = d - F lambda),
+//                w = r - G z (the projector), the dot w.w; the last block
+//                sets beta, the relative residual and the stop flags.
+//
+// The control block lives in device memory; every kernel of an iteration
+// returns at once when `active` is 0, so the host can enqueue several
+// iterations ahead and read the control block once per chunk.  Dot products
+// are reduced in a fixed order (block partials summed by one block), so a
+// solve is bitwise reproducible.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace feti {
+namespace {
+
+constexpr int kVT = 256;  // threads per block of the vector kernels
+
+// Sum a double over the block in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+// Store the block partial; returns true (in every thread) for the last block
+// to arrive, after which all partials are visible to it.
+__device__ __forceinline__ bool last_block(double s, double* part, int* counter) {
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    is_last = atomicAdd(counter, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+// Fixed-order sum of the nb block partials by one block (thread 0 holds it).
+__device__ __forceinline__ double sum_partials(const double* part, int nb, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  return block_sum(s, red);
+}
+
+template <typename TF>
+__global__ void pcg_scatter_kernel(const int* qmap, int64_t ncols, const double* p, const double* w, TF* pg,
+                                   const PcgCtrl* ctrl) {
+  if (!ctrl->active) return;
+  const double beta = ctrl->beta;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ncols; g += (int64_t)gridDim.x * blockDim.x) {
+    const int lam = qmap[g];
+    pg[g] = lam >= 0 ? (TF)fma(beta, p[lam], w[lam]) : (TF)0;
+  }
+}
+
+__global__ void __launch_bounds__(kVT) pcg_gather_dot_kernel(const int* c0, const int* c1, int nlam,
+                                                             const double* qi, double* p, const double* w,
+                                                             double* q, double* part, PcgCtrl* ctrl) {
+  __shared__ double red[kVT / 32];
+  if (!ctrl->active) return;
+  const double beta = ctrl->beta;
+  double s = 0.0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int a = c0[l], b = c1[l];
+    double ql = a >= 0 ? qi[a] : 0.0;
+    if (b >= 0) ql += qi[b];
+    const double pl = fma(beta, p[l], w[l]);
+    p[l] = pl;
+    q[l] = ql;
+    s = fma(pl, ql, s);
+  }
+  s = block_sum(s, red);
+  if (last_block(s, part, &ctrl->cnt_dot)) {
+    const double pq = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      ctrl->pq = pq;
+      if (pq > 0.0 && isfinite(pq)) {
+        ctrl->delta = ctrl->wy / pq;
+      } else {  // breakdown: F p is not positive on p (Algorithm 1 needs F SPD on ker G^T)
+        ctrl->delta = 0.0;
+        ctrl->breakdown = 1;
+        ctrl->active = 0;
+      }
+      ctrl->cnt_dot = 0;
+    }
+  }
+}
+
+// c[alpha0 + k] = sum_j G[(qcol + j), k] x[map_j], x = r - delta q (mode 0) or d - q (mode 1);
+// one warp per (subdomain, k)
+__global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const double* r, const double* q,
+                              const double* d, int mode, double* c, const PcgCtrl* ctrl) {
+  if (mode == 0 && !ctrl->active) return;
+  const double delta = ctrl->delta;
+  const int lane = threadIdx.x & 31;
+  for (int wk = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wk < nsub * 6; wk += gridDim.x * blockDim.x / 32) {
+    const int si = wk / 6, k = wk % 6;
+    const SubInfo& S = P.sub[si];
+    if (k >= S.d) continue;
+    double acc = 0.0;
+    for (int j = lane; j < S.m; j += 32) {
+      const int l = P.qmap[S.qcol + j];
+      const double x = mode == 0 ? fma(-delta, q[l], r[l]) : d[l] - q[l];
+      acc = fma(G6[(S.qcol + j) * 6 + k], x, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c[S.alpha0 + k] = acc;
+  }
+}
+
+// z = A c with A dense D x D row-major; 4 rows per block, 2 warps per row, fixed-order sums
+__global__ void __launch_bounds__(kVT) gemv_rows_kernel(const double* A, const double* c, double* z, int D,
+                                                        const PcgCtrl* ctrl, int mode) {
+  __shared__ double red[kVT / 32];
+  if (ctrl && mode == 0 && !ctrl->active) return;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 4 + warp / 2, half = warp & 1;
+  double acc = 0.0;
+  if (row < D) {
+    const double* a = A + (int64_t)row * D;
+    for (int j = half * 32 + lane; j < D; j += 64) acc = fma(a[j], c[j], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x < 4 && blockIdx.x * 4 + threadIdx.x < D)
+    z[blockIdx.x * 4 + threadIdx.x] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+}
+
+// mode 0 (iteration): lambda += delta p, r -= delta q;  mode 1 (refresh): r = d - q;  mode 2 (start): as 1,
+// and the start values nw0 / floor are set.  Then w = r - G z and the dot w.w; the last block finishes.
+__global__ void __launch_bounds__(kVT) pcg_update_kernel(DevPlan P, const int* colsub, const int* c0, const int* c1,
+                                                         int nlam, const double* G6, const double* z,
+                                                         const double* p, const double* q, const double* d,
+                                                         double* lam, double* r, double* w, double* part,
+                                                         int mode, PcgCtrl* ctrl) {
+  __shared__ double red[kVT / 32];
+  if (mode == 0 && !ctrl->active) return;
+  const double delta = ctrl->delta;
+  double s = 0.0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    double rl;
+    if (mode == 0) {
+      lam[l] = fma(delta, p[l], lam[l]);
+      rl = fma(-delta, q[l], r[l]);
+    } else {
+      rl = d[l] - q[l];
+    }
+    r[l] = rl;
+    double gz = 0.0;
+    if (z) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int g = e == 0 ? c0[l] : c1[l];
+        if (g < 0) continue;
+        const SubInfo& S = P.sub[colsub[g]];
+        for (int k = 0; k < S.d; ++k) gz = fma(G6[(int64_t)g * 6 + k], z[S.alpha0 + k], gz);
+      }
+    }
+    const double wl = rl - gz;
+    w[l] = wl;
+    s = fma(wl, wl, s);
+  }
+  s = block_sum(s, red);
+  if (last_block(s, part, &ctrl->cnt_upd)) {
+    const double wyn = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      const double nw = sqrt(wyn);
+      ctrl->wyn = wyn;
+      ctrl->nw = nw;
+      if (mode == 2) {
+        // start: floor = 64 eps (||d|| + ||F lambda_0||) from the two norms stored before
+        ctrl->nw0 = nw;
+        ctrl->floor = 64.0 * 2.220446049250313e-16 * (sqrt(ctrl->dd) + sqrt(ctrl->qq));
+        ctrl->beta = 0.0;
+        ctrl->wy_prev = wyn;
+      } else if (mode == 0) {
+        ctrl->beta = ctrl->wy > 0.0 ? wyn / ctrl->wy : 0.0;
+        ctrl->wy_prev = ctrl->wy;
+      } else {
+        // the replaced residual takes the place of this iteration's recursive one:
+        // beta divides by the w.w the iteration started from
+        ctrl->beta = ctrl->wy_prev > 0.0 ? wyn / ctrl->wy_prev : 0.0;
+      }
+      ctrl->wy = wyn;
+      if (mode == 0) ctrl->it += 1;
+      ctrl->rel = ctrl->nw0 > 0.0 ? nw / ctrl->nw0 : 0.0;
+      ctrl->conv = (nw <= ctrl->tol * ctrl->nw0 || nw <= ctrl->floor) ? 1 : 0;
+      ctrl->active = (!ctrl->conv && !ctrl->breakdown && ctrl->it < ctrl->maxit) ? 1 : 0;
+      ctrl->cnt_upd = 0;
+    }
+  }
+}
+
+// dd = d.d and qq = q.q (for the rounding floor of the stopping rule), one block
+__global__ void __launch_bounds__(kVT) pcg_norms_kernel(const double* d, const double* q, int n, PcgCtrl* ctrl) {
+  __shared__ double red[kVT / 32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a = fma(d[i], d[i], a);
+    b = fma(q[i], q[i], b);
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    ctrl->dd = a;
+    ctrl->qq = b;
+  }
+}
+
+inline int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + kVT - 1) / kVT, kPcgMaxBlocks)); }
+
+}  // namespace
+
+int pcg_vector_grid(int n) { return vgrid(n); }
+
+void launch_pcg_scatter(bool fp32, const int* qmap, int64_t ncols, const double* p, const double* w, void* pg,
+                        const PcgCtrl* ctrl, cudaStream_t st) {
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + kVT - 1) / kVT, 152 * 8));
+  if (fp32) pcg_scatter_kernel<float><<<g, kVT, 0, st>>>(qmap, ncols, p, w, (float*)pg, ctrl);
+  else pcg_scatter_kernel<double><<<g, kVT, 0, st>>>(qmap, ncols, p, w, (double*)pg, ctrl);
+}
+
+void launch_pcg_gather_dot(const int* c0, const int* c1, int nlam, const double* qi, double* p, const double* w,
+                           double* q, double* part, PcgCtrl* ctrl, cudaStream_t st) {
+  pcg_gather_dot_kernel<<<vgrid(nlam), kVT, 0, st>>>(c0, c1, nlam, qi, p, w, q, part, ctrl);
+}
+
+void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* r, const double* q, const double* d,
+                   int mode, double* c, const PcgCtrl* ctrl, cudaStream_t st) {
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nsub * 6 * 32 + kVT - 1) / kVT, 152 * 16));
+  pcg_gt_kernel<<<g, kVT, 0, st>>>(P, nsub, G6, r, q, d, mode, c, ctrl);
+}
+
+void launch_gemv_rows(const double* A, const double* c, double* z, int D, const PcgCtrl* ctrl, int mode,
+                      cudaStream_t st) {
+  if (D > 0) gemv_rows_kernel<<<(D + 3) / 4, kVT, 0, st>>>(A, c, z, D, ctrl, mode);
+}
+
+void launch_pcg_update(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+                       const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
+                       double* w, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st) {
+  pcg_update_kernel<<<vgrid(nlam), kVT, 0, st>>>(P, colsub, c0, c1, nlam, G6, z, p, q, d, lam, r, w, part, mode,
+                                                 ctrl);
+}
+
+void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st) {
+  pcg_norms_kernel<<<1, kVT, 0, st>>>(d, q, n, ctrl);
+}
+
+}  // namespace feti

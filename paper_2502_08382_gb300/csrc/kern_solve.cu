@@ -52,18 +52,32 @@ __device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int
     b[q] = i < f_ ? v[i] : 0.0;
   }
   const int nq = (r + 31) / 32;  // warp-uniform
-  for (int j = 0; j < w; ++j) {
-    const double* col = Ls + (int64_t)j * f_;
-    const double zj = __shfl_sync(0xffffffffu, a * di, j);
-    if (lane == j) a = zj;
-    else if (lane > j && lane < w) a -= col[lane] * zj;
-    if (nq > 0) b[0] -= (w + lane < f_ ? col[w + lane] : 0.0) * zj;
+  // columns in groups of 4: the group's loads are issued together, so one
+  // global-memory latency is paid per group instead of per column
+  constexpr int kU = 4;
+  for (int j0 = 0; j0 < w; j0 += kU) {
+    double lt[kU], lb[kU][kWF / 32];
 #pragma unroll
-    for (int q = 1; q < kWF / 32; ++q) {
-      if (q < nq) {
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u;
+      const double* col = Ls + (int64_t)j * f_;
+      lt[u] = (j < w && lane > j && lane < w) ? col[lane] : 0.0;
+#pragma unroll
+      for (int q = 0; q < kWF / 32; ++q) {
         const int i = w + lane + 32 * q;
-        if (i < f_) b[q] -= col[i] * zj;
+        lb[u][q] = (j < w && q < nq && i < f_) ? col[i] : 0.0;
       }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u;
+      if (j >= w) break;
+      const double zj = __shfl_sync(0xffffffffu, a * di, j);
+      if (lane == j) a = zj;
+      else a -= lt[u] * zj;
+#pragma unroll
+      for (int q = 0; q < kWF / 32; ++q)
+        if (q < nq) b[q] -= lb[u][q] * zj;
     }
   }
   if (lane < w) y[c0 + lane] = a;
@@ -93,15 +107,27 @@ __device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int
   double t = 0.0;
   if (l < w) {
     const double* col = Ls + (int64_t)l * f_ + w;
-    for (int i = g; i < r; i += G) t += col[i] * v[i];
+#pragma unroll 4
+    for (int i = g; i < r; i += G) t = fma(col[i], v[i], t);
   }
   for (int o = wp; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   double x = lane < w ? y[c0 + lane] - t : 0.0;
   const double di = lane < w ? dinv[c0 + lane] : 0.0;
-  for (int j = w - 1; j >= 0; --j) {
-    const double xj = __shfl_sync(0xffffffffu, x * di, j);
-    if (lane == j) x = xj;
-    else if (lane < j) x -= Ls[(int64_t)lane * f_ + j] * xj;
+  for (int j0 = w - 1; j0 >= 0; j0 -= 4) {
+    double lr[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 - u;
+      lr[u] = (j >= 0 && lane < j) ? Ls[(int64_t)lane * f_ + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 - u;
+      if (j < 0) break;
+      const double xj = __shfl_sync(0xffffffffu, x * di, j);
+      if (lane == j) x = xj;
+      else x -= lr[u] * xj;
+    }
   }
   if (lane < w) y[c0 + lane] = x;
   __syncwarp();
@@ -147,7 +173,8 @@ __device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int 
     __syncthreads();
     for (int i = kb + nbk + tid; i < f_; i += kThreads) {
       double acc = 0.0;
-      for (int k = 0; k < nbk; ++k) acc += Ls[(int64_t)(kb + k) * f_ + i] * sf[kb + k];
+#pragma unroll 8
+      for (int k = 0; k < nbk; ++k) acc = fma(Ls[(int64_t)(kb + k) * f_ + i], sf[kb + k], acc);
       sf[i] -= acc;
     }
     __syncthreads();
@@ -169,7 +196,8 @@ __device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int 
   const int* rows = P.rows + P.sn_rows[gs];
   for (int l = warp; l < w; l += kThreads / 32) {
     double acc = 0.0;
-    for (int k = lane; k < r; k += 32) acc += Ls[(int64_t)l * f_ + w + k] * y[rows[k]];
+#pragma unroll 4
+    for (int k = lane; k < r; k += 32) acc = fma(Ls[(int64_t)l * f_ + w + k], y[rows[k]], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) y[c0 + l] -= acc;
   }
@@ -178,7 +206,8 @@ __device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int 
     const int nbk = min(kW, w - kb);
     for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
       double acc = 0.0;
-      for (int i = kb + nbk + lane; i < w; i += 32) acc += Ls[(int64_t)l * f_ + i] * y[c0 + i];
+#pragma unroll 4
+      for (int i = kb + nbk + lane; i < w; i += 32) acc = fma(Ls[(int64_t)l * f_ + i], y[c0 + i], acc);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) y[c0 + l] -= acc;
     }
@@ -208,7 +237,7 @@ __device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int 
 //         sorted columns; `nsub` is the column count, order[0] the subdomain);
 //         written to u as Z[dof * m + B-row of column j] (original DOF order)
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
+__global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                              const double* p, const double* f, double* qi,
                                                              double* u, double* uws, int64_t ustride, int nmax,
                                                              int maxf) {
@@ -568,50 +597,6 @@ __global__ void copy2d_kernel(const double* src, int lds, double* dst, int ldd, 
 
 // ---------------------------------------------------------------- vectors
 
-__global__ void dot_partial_kernel(const double* x, const double* y, int n, double* part) {
-  __shared__ double red[8];
-  double s = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i] * y[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[k];
-    part[blockIdx.x] = t;
-  }
-}
-
-__global__ void dot_final_kernel(const double* part, int np, double* out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[k];
-    *out = t;
-  }
-}
-
-// sc[0] = w.y (current), sc[1] = p.q, sc[2] = w.y (new)
-__global__ void pcg_upd1_kernel(double* lam, double* r, const double* p, const double* q, const double* sc, int n) {
-  const double delta = sc[0] / sc[1];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    lam[i] += delta * p[i];
-    r[i] -= delta * q[i];
-  }
-}
-
-__global__ void pcg_upd2_kernel(double* p, const double* w, double* sc, int n) {
-  const double beta = sc[2] / sc[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = w[i] + beta * p[i];
-}
-
-__global__ void scalar_copy_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
-
 // r = d - q
 __global__ void sub_kernel(const double* d, const double* q, double* r, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = d[i] - q[i];
@@ -731,22 +716,6 @@ void launch_copy2d(const double* src, int lds, double* dst, int ldd, int rows, i
   if (rows > 0 && cols > 0)
     copy2d_kernel<<<grid_for((int64_t)rows * cols), 256, 0, st>>>(src, lds, dst, ldd, rows, cols, scale);
 }
-
-void launch_dot(const double* x, const double* y, int n, double* part, int npart, double* out, cudaStream_t st) {
-  dot_partial_kernel<<<npart, 256, 0, st>>>(x, y, n, part);
-  dot_final_kernel<<<1, 1024, 0, st>>>(part, npart, out);
-}
-
-void launch_pcg_upd1(double* lam, double* r, const double* p, const double* q, const double* sc, int n,
-                     cudaStream_t st) {
-  pcg_upd1_kernel<<<grid_for(n), 256, 0, st>>>(lam, r, p, q, sc, n);
-}
-
-void launch_pcg_upd2(double* p, const double* w, double* sc, int n, cudaStream_t st) {
-  pcg_upd2_kernel<<<grid_for(n), 256, 0, st>>>(p, w, sc, n);
-}
-
-void launch_scalar_copy(double* sc, int dst, int src, cudaStream_t st) { scalar_copy_kernel<<<1, 1, 0, st>>>(sc, dst, src); }
 
 void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st) {
   sub_kernel<<<grid_for(n), 256, 0, st>>>(d, q, r, n);

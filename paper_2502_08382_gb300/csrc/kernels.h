@@ -8,7 +8,8 @@
 namespace feti {
 
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int grid, int* status, cudaStream_t st);
+                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st);
+int chol_ctas_per_sm();
 void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
                  int64_t ws_stride, int64_t front_sz, int grid, cudaStream_t st);
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
@@ -21,6 +22,10 @@ void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
                   cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
+void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
+                       void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
+                       int variant, const int* active, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr,
+                       cudaEvent_t ev_tiles1 = nullptr, bool ev_external = false);
 int apply_variants();
 int apply_max_ctas_per_sm(bool fp32, int variant);
 int apply_warps_per_cta();
@@ -52,11 +57,19 @@ void launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, 
 void launch_potrf64(double* A, int lda, int n, double* Dinv, int* status, cudaStream_t st);
 void launch_copy2d(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale,
                    cudaStream_t st);
-void launch_dot(const double* x, const double* y, int n, double* part, int npart, double* out, cudaStream_t st);
-void launch_pcg_upd1(double* lam, double* r, const double* p, const double* q, const double* sc, int n,
-                     cudaStream_t st);
-void launch_pcg_upd2(double* p, const double* w, double* sc, int n, cudaStream_t st);
-void launch_scalar_copy(double* sc, int dst, int src, cudaStream_t st);
+// projected CG (kern_pcg.cu)
+void launch_pcg_scatter(bool fp32, const int* qmap, int64_t ncols, const double* p, const double* w, void* pg,
+                        const PcgCtrl* ctrl, cudaStream_t st);
+void launch_pcg_gather_dot(const int* c0, const int* c1, int nlam, const double* qi, double* p, const double* w,
+                           double* q, double* part, PcgCtrl* ctrl, cudaStream_t st);
+void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* r, const double* q, const double* d,
+                   int mode, double* c, const PcgCtrl* ctrl, cudaStream_t st);
+void launch_gemv_rows(const double* A, const double* c, double* z, int D, const PcgCtrl* ctrl, int mode,
+                      cudaStream_t st);
+void launch_pcg_update(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+                       const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
+                       double* w, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st);
+void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st);
 void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st);
 void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
                        double* u, cudaStream_t st);

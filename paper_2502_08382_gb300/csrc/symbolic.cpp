@@ -559,6 +559,23 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
     P.chol_stack = peak;
     P.chol_front = fr;
   }
+  // small subtrees: factored level by level, one warp per front, so their update
+  // blocks live at the same time and get slots of their own
+  P.sn_small.assign(ns, 0);
+  P.usm_ofs.assign(ns, 0);
+  {
+    int64_t us = 0;
+    for (int s = 0; s < ns; ++s) {  // postorder: children first
+      bool sm = P.sn_w[s] + P.sn_r[s] <= kSmallFront;
+      for (int c : kids[s]) sm = sm && P.sn_small[c] != 0;
+      P.sn_small[s] = sm ? 1 : 0;
+      if (sm && P.sn_parent[s] >= 0) {
+        P.usm_ofs[s] = us;
+        us += (int64_t)P.sn_r[s] * P.sn_r[s];
+      }
+    }
+    P.usm_size = us;
+  }
 }
 
 void plan_rhs(const PatternPlan& P, int m, const int32_t* B_dof, BPlan& Bp) {

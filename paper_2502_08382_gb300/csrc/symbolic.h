@@ -14,6 +14,11 @@
 namespace feti {
 
 constexpr int kTile = 64;  // F tile edge (apply and SYRK)
+// Fronts up to kSmallFront wide whose whole subtree is as small are factored
+// by one warp each in shared memory; fronts up to kMidFront wide by the whole
+// CTA in shared memory; larger ones by the tiled CTA path.
+constexpr int kSmallFront = 46;
+constexpr int kMidFront = 128;
 
 // padded row length of a supernode X block (16-byte aligned rows)
 inline int xpad(int w) { return (w + 3) & ~3; }
@@ -38,6 +43,9 @@ struct PatternPlan {
   std::vector<int> diag_src;         // CSR index of each diagonal entry (old numbering)
   std::vector<int64_t> upd_stack_ofs;  // where the r x r update block of s lives
   int64_t chol_stack = 0;            // peak stack (doubles)
+  std::vector<int> sn_small;         // 1: the supernode and its whole subtree have fronts <= kSmallFront
+  std::vector<int64_t> usm_ofs;      // update block slot of a small supernode (own slots, no overlap)
+  int64_t usm_size = 0;              // doubles of all small update blocks
   int64_t chol_front = 0;            // max r*r (doubles)
   int max_f = 0, max_w = 0;
   double chol_flops = 0, nnzL = 0;

@@ -48,12 +48,12 @@ class FetiOptions(C.Structure):
     _fields_ = [("prec", C.c_int), ("refine_every", C.c_int32), ("tol", C.c_double), ("maxit", C.c_int32),
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
-                ("use_coords", C.c_int32)]
+                ("use_coords", C.c_int32), ("refine_drop", C.c_double)]
 
 
 class FetiSolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32), ("rel_residual", C.c_double),
-                ("converged", C.c_int32)]
+                ("converged", C.c_int32), ("initial_residual", C.c_double)]
 
 
 class FetiStats(C.Structure):
@@ -210,7 +210,7 @@ class FetiOperator:
     feti_apply / feti_apply_implicit / feti_solve / feti_adjoint)."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
-                 refine_every: int = 0, leaf_dofs: int = 16, use_coords: bool = True,
+                 refine_every: int = 0, refine_drop: float = 0.0, leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
         import torch
         self.torch = torch
@@ -226,6 +226,7 @@ class FetiOperator:
         opt = FetiOptions()
         opt.prec = PREC[prec]
         opt.refine_every = refine_every
+        opt.refine_drop = refine_drop
         opt.tol = tol
         opt.maxit = maxit
         opt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -298,7 +299,8 @@ class FetiOperator:
         if rc not in (FETI_OK, 4):
             self._check(rc)
         return lam, alpha[:self.dtot], u, dict(iterations=info.iterations, refinements=info.refinements,
-                                                 rel_residual=info.rel_residual, converged=bool(info.converged))
+                                                 rel_residual=info.rel_residual, converged=bool(info.converged),
+                                                 initial_residual=info.initial_residual)
 
     def adjoint(self, W):
         """dL/dtheta_e for L = sum_i <W_i, F_i> (feti_adjoint).  W: list of

@@ -28,7 +28,8 @@ def main():
     ap.add_argument("--prec", default="split_bf16", choices=["fp64", "tf32", "split_bf16"])
     ap.add_argument("--phase", default="apply", choices=["assemble", "apply", "implicit", "solve"])
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--refine-every", type=int, default=10)
+    ap.add_argument("--refine-every", type=int, default=0)
+    ap.add_argument("--refine-drop", type=float, default=1e-3)
     args = ap.parse_args()
 
     import torch
@@ -37,8 +38,9 @@ def main():
 
     torch.cuda.set_device(0)
     P = make_config(args.config, nsub_axis=args.nsub_axis)
-    op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000,
-                           refine_every=args.refine_every if args.prec != "fp64" else 0)
+    mixed = args.prec != "fp64"
+    op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000, refine_every=args.refine_every if mixed else 0,
+                           refine_drop=args.refine_drop if mixed else 0.0)
     op.assemble()
     p = torch.from_numpy(seeded_vector(P.n_lambda, 0)).cuda()
     q = torch.empty_like(p)
@@ -71,7 +73,8 @@ def main():
                       "reps": args.reps, "ms": ms, "device_bytes": s["device_bytes"],
                       "apply_bytes": s["apply_bytes"], "implicit_bytes": s["implicit_bytes"],
                       "chol_flops": s["chol_flops"], "trsm_flops": s["trsm_flops"],
-                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "solve": info}))
+                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "refine_drop": args.refine_drop,
+                      "solve": info, "launches": s["launches"]}))
     op.close()
 
 

@@ -72,7 +72,8 @@ def test_single_element_single_subdomain(torch_cuda, prec):
     lam, alpha, u, info = op.solve()
     um = O.monolithic_solve(P)
     op.close()
-    assert info["converged"], info
+    # lambda_I already solves this dual problem: the rounding floor of the stopping rule ends it at once
+    assert info["converged"] and info["iterations"] == 0, info
     assert np.abs(u.cpu().numpy() - um[s.l2g]).max() <= 1e-10 * max(1.0, np.abs(um).max())
 
 

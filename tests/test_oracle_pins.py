@@ -270,3 +270,16 @@ def test_Gt_times_and_residuals(cfg1):
     assert prim.max() < 1e-12 and np.abs(Bu).max() < 1e-10
     prim2, Bu2 = O.feti_equation_residuals(cfg1, res["lam"] + 1e-3 * lam, res["u"])
     assert prim2.max() > 1e-6
+
+
+def test_pcpg_degenerate_initial_guess():
+    """One Q1 element as one subdomain, u = 0 on x = 0: the two Dirichlet
+    multipliers and the constant kernel make lambda_I = G (G^T G)^{-1} e the
+    exact dual solution, so w_0 is rounding noise.  The rounding floor of the
+    stopping rule ends the iteration at once, and the primal solution equals
+    the monolithic one."""
+    P = make_problem(dim=2, physics="heat", cuts=[[1], [1]], material="const", seed=0)
+    res = O.feti_solve(P, tol=1e-12, maxit=50)
+    assert res["iterations"] == 0
+    um = O.monolithic_solve(P)
+    assert np.abs(res["u"][0] - um[P.subs[0].l2g]).max() <= 1e-12 * np.abs(um).max()
