@@ -37,8 +37,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "F assembly ms & F·λ GB/s, mixed vs FP64 at stated error; break-even PCG iters"
-WORKLOAD = ("2D heat Q1, 32x32 subdomains of 64x64 elements (4225 DOFs, m_i 129..258, n_lambda 130048), "
-            "lognormal sigma=1, seed 0")
+WORKLOADS = {
+    2: "2D heat Q1, 32x32 subdomains of 64x64 elements (4225 DOFs, m_i 129..258, n_lambda 130048), "
+       "lognormal sigma=1, seed 0",
+    3: "3D elasticity Hex8, 8x8x8 subdomains of 12^3 elements (6591 DOFs, n_lambda 664800), E=1, nu=0.3",
+    4: "3D heat Hex8, 120^3 box cut into 10x10x10 uneven subdomains (8..24 elements per axis, seed 0), "
+       "lognormal sigma=0.5",
+    5: "3D elasticity Hex8, 6x6x6 subdomains of 16^3 elements (14739 DOFs, n_lambda 473832), rho~U[0.1,1], E=rho^3",
+}
+WORKLOAD = WORKLOADS[2]
 PREC = "split_bf16"
 REFINE_DROP = 1e-3   # FP64 residual recomputed whenever ||P r|| has dropped by this factor
 TOL = 1e-10
@@ -103,6 +110,43 @@ class Clocks:
         return out
 
 
+# Peaks of the SIMT pipes, derived from GB300's unit counts at the 2070 MHz maximum SM clock:
+# FP64 1.25 TFLOP/s nominal (an FMA probe on this GPU measured 1.20), FP32 152 SMs x 128 FMA x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def other_rooflines(st, impl_ms, hbm):
+    """Rooflines of the assembly kernels and of the FP64 implicit operator (last assembly)."""
+    bf16, bf16_kind = bf16_peak()
+    out = {}
+    if st["t_chol_ms"] > 0:
+        a = st["chol_flops"] / (st["t_chol_ms"] * 1e-3) / 1e12
+        out["chol_kernel"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64"}
+    if st["t_trsm_ms"] > 0:
+        a = st["trsm_flops"] / (st["t_trsm_ms"] * 1e-3) / 1e12
+        out["trsm_kernel<float>"] = {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": a / FP32_PEAK_TFLOPS, "peak_kind": "derived FP32"}
+    if st["t_syrk_ms"] > 0:
+        a = 3 * st["syrk_flops"] / (st["t_syrk_ms"] * 1e-3) / 1e12  # split-bf16: 3 tensor products per FMA
+        out["syrk_tc_kernel"] = {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s",
+                                 "frac": a / bf16, "peak_kind": f"{bf16_kind} bf16"}
+    if impl_ms > 0:
+        a = st["implicit_bytes"] / (impl_ms * 1e-3) / 1e9
+        out["implicit_kernel<0>"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                                     "fp64_tflops": st["implicit_bytes"] / 4 / (impl_ms * 1e-3) / 1e12}
+    return out
+
+
 def oracle_sample(P, nsample, reps):
     """The FP64 CPU oracle on a bounded sample: dense F_i for nsample
     subdomains and reps dense F_i p_i sweeps over them."""
@@ -124,8 +168,8 @@ def oracle_sample(P, nsample, reps):
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores."""
     from paper_2502_08382_gb300.problems import make_config
-    P = make_config(2)
-    nsample = 4
+    P = make_config(args.workload)
+    nsample = 4 if args.workload == 2 else 1
     for _ in range(args.warmup):
         oracle_sample(P, 1, 5)
     vals, tf = [], []
@@ -141,7 +185,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "config": {"workload": WORKLOADS[args.workload]},
             "assembly_ms_extrapolated": statistics.median(tf) * 1e3 * P.nsub,
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -156,6 +200,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", type=int, default=2, choices=sorted(WORKLOADS),
+                    help="2 (default: the workload the metric is quoted on) or one of the 3D workloads")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -177,7 +223,7 @@ def main():
     from paper_2502_08382_gb300.metrics import break_even
     from paper_2502_08382_gb300.problems import make_config, seeded_vector
 
-    P = make_config(2)
+    P = make_config(args.workload)
     op = feti.FetiOperator(P, prec=PREC, tol=TOL, maxit=5000, refine_drop=REFINE_DROP)
     st = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -256,7 +302,7 @@ def main():
         asm64.append(op64.stats()["t_assemble_ms"])
     st64 = op64.stats()
     lam64, alpha64, u64, info64 = op64.solve()
-    sample = [0, 17, 500, 1023]
+    sample = sorted({0, P.nsub // 3, (2 * P.nsub) // 3, P.nsub - 1})
     ferr = max(np.linalg.norm(op.get_F(i) - op64.get_F(i)) / np.linalg.norm(op64.get_F(i)) for i in sample)
     uerr = (torch.linalg.norm(u - u64) / torch.linalg.norm(u64)).item()
     p.copy_(p_host)
@@ -274,7 +320,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": f"{PREC} SYRK, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
+            "config": {"workload": WORKLOADS[args.workload], "prec": f"{PREC} SYRK, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
                        "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual after each {1 / REFINE_DROP:.0e} drop)",
                        "value": "explicit F.lambda apply GB/s (algorithmic bytes / F-streaming kernel time)",
                        "l2": "256 MB buffer written before each timed step; F tiles 136 MB > L2 per apply",
@@ -297,15 +343,18 @@ def main():
             "roofline": {"bound": "hbm", "achieved": tiles_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": tiles_gbs / hbm, "traffic": None, "kernel": "apply_tiles_kernel<float>",
                          "peak_kind": pk_kind},
+            "roofline_other": other_rooflines(st_last, impl64_ms, hbm),
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},
             "gpu_launches": int(st_["launches"]),
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gbs, t_f, t_ap = oracle_sample(P, 4, 300)
+        ns_cpu = 4 if args.workload == 2 else 1
+        gbs, t_f, t_ap = oracle_sample(P, ns_cpu, 300 if args.workload == 2 else 20)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"4 of {P.nsub} subdomains: scipy dense Cholesky F_i "
-                                          f"({t_f * 1e3:.0f} ms each) and 300 dense FP64 F_i p_i sweeps",
+                                "sample": f"{ns_cpu} of {P.nsub} subdomains: scipy dense Cholesky F_i "
+                                          f"({t_f * 1e3:.0f} ms each) and {300 if args.workload == 2 else 20} "
+                                          f"dense FP64 F_i p_i sweeps",
                                 "assembly_ms_extrapolated": t_f * 1e3 * P.nsub}
     if rank == 0:
         print(json.dumps(line))

@@ -628,8 +628,8 @@ void build(feti_ctx* c) {
     // the apply deals tiles to warps round-robin; candidates of the autotuner:
     // every variant of the tile kernel at its full occupancy (capped at one tile per warp)
     c->d_tdesc = upload(c, tdesc);
-    const int wpc = apply_warps_per_cta();
     for (int v = 0; v < apply_variants(); ++v) {
+      const int wpc = apply_warps_per_cta(v);
       const int occ = apply_max_ctas_per_sm(c->fp32, v);
       if (occ <= 0) continue;
       const int G = std::max(1, std::min((c->napply + wpc - 1) / wpc, c->nsm * occ));
@@ -819,7 +819,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
         if (rep == 2) CK(cudaEventRecord(ctx->ev[5], st));
         launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, pz,
                      ctx->d_pg, ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0,
-                     ctx->d_c1, ctx->nlam, qz, c2.grid, c2.variant, st);
+                     ctx->d_c1, ctx->nlam, qz, c2.grid, c2.variant, ctx->d_status, st);
       }
       CK(cudaEventRecord(ctx->ev[6], st));
       CK(cudaEventSynchronize(ctx->ev[6]));
@@ -858,7 +858,7 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   }
   launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev, ctx->d_pg,
                ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1, ctx->nlam,
-               q_dev, grid, cand.variant, st, ev.b, ev.c);
+               q_dev, grid, cand.variant, ctx->d_status, st, ev.b, ev.c);
   ctx->stats.launches += 4;
   ctx->stats.apply_calls += 1;
   if (ctx->prof) {

@@ -116,7 +116,8 @@ void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStre
   if (ev) CKS(cudaEventRecordWithFlags(ev[0], st, evf));
   launch_pcg_scatter(c->fp32, c->P.qmap, c->ncols, p, w, c->d_pg, ctrl, st);
   launch_apply_core(c->P, c->fp32, c->d_tdesc, c->napply, c->d_F, c->d_pg, c->d_rowpart, c->d_tpart, c->d_blocks,
-                    c->nblocks, c->d_qi, cand.grid, cand.variant, active_dev(c), st, ev ? ev[1] : nullptr,
+                    c->nblocks, c->d_qi, cand.grid, cand.variant, active_dev(c), c->d_status, st,
+                    ev ? ev[1] : nullptr,
                     ev ? ev[2] : nullptr, capture);
   launch_pcg_gather_dot(c->d_c0, c->d_c1, n, c->d_qi, p, w, q, c->d_part, ctrl, st);
   if (ev) CKS(cudaEventRecordWithFlags(ev[3], st, evf));

@@ -133,18 +133,14 @@ struct TileStream {
         B.v[i] = ld_stream(reinterpret_cast<const VT*>(Ft + r * kT + cq * V));
       }
     } else {
-      // ragged or diagonal tile: every lane loads from a stored position (its row clamped
-      // to the last stored row, its chunk to the one holding the diagonal) and zeroes
-      // what lies outside, so no load sits behind a branch
+      // ragged or diagonal tile: only stored positions are loaded
 #pragma unroll
       for (int i = 0; i < BATCH; ++i) {
         const int r = b * ROWS_B + i * RPL + half;
-        const int rr = min(r, d.rows - 1);
-        const int cc = diag ? min(cq, rr / V) : cq;
-        const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(rr) : (int64_t)rr * kT;
-        const VT x = ld_stream(reinterpret_cast<const VT*>(Ft + off + cc * V));
         const bool ok = r < d.rows && (!diag || cq * V <= r);
-        B.v[i] = ok ? x : VT{};
+        const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(r) : (int64_t)r * kT;
+        if (ok) B.v[i] = ld_stream(reinterpret_cast<const VT*>(Ft + off + cq * V));
+        else B.v[i] = VT{};
       }
     }
     B.pc = *reinterpret_cast<const VT*>(pg + d.pcol + cq * V);
@@ -247,6 +243,213 @@ __global__ void __launch_bounds__(kApplyThreads) apply_tiles_kernel(const TileDe
   }
 }
 
+// ---------------------------------------------------------------- bulk-copy ring variant
+//
+// Every warp runs its own ring of S shared-memory stages.  A stage holds one
+// batch of one tile: the batch's stored rows (contiguous in F: one bulk copy),
+// the tile's column-block p and the batch's row p values.  Lane 0 arms the
+// stage's mbarrier with the byte count and issues the three copies; the warp
+// waits on the barrier (bounded), computes from shared memory, and re-arms the
+// stage with the item S ahead.  The copy engine does the address work and the
+// data in flight needs no registers.  No warp waits on another.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// every lane polls the barrier phase (bounded, about a second), so that each one
+// observes the completed copies; true only if the whole warp saw the phase complete
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  int ok = 0;
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) {
+      ok = 1;
+      break;
+    }
+    if (clock64() - t0 > 2000000000LL) break;
+  }
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+template <typename TF>
+struct RingCfg {
+  static constexpr int V = 16 / (int)sizeof(TF);
+  static constexpr int NCH = kT / V;
+  static constexpr int RPL = 32 / NCH;
+  static constexpr int BATCH = 16;
+  static constexpr int ROWS_B = BATCH * RPL;            // 32 (FP32) / 16 (FP64) rows per stage
+  static constexpr int DATA = ROWS_B * kT * (int)sizeof(TF);  // 8 KB
+  static constexpr int PC = kT * (int)sizeof(TF);
+  static constexpr int PR = ROWS_B * (int)sizeof(TF);
+  static constexpr int STAGE = DATA + PC + PR;          // multiple of 16 bytes
+  __host__ __device__ static constexpr size_t bars_ofs(int W, int S) { return (size_t)W * S * STAGE; }
+  __host__ __device__ static constexpr size_t meta_ofs(int W, int S) { return (bars_ofs(W, S) + (size_t)W * S * 8 + 15) / 16 * 16; }
+  __host__ __device__ static constexpr size_t smem(int W, int S) { return meta_ofs(W, S) + (size_t)W * S * 16 + 128; }
+};
+
+// Position of a warp in its sequence of (tile, batch) items: tiles gw, gw + nw,
+// ..., and inside a tile only the batches that hold stored rows.
+struct RingCursor {
+  int t, b;
+  TileDesc d;   // descriptor of tile t
+  TileDesc dn;  // prefetched descriptor of tile t + nw
+};
+
+template <int ROWS_B>
+__device__ __forceinline__ bool ring_advance(RingCursor& c, int nw, int ntiles, const TileDesc* desc) {
+  if ((c.b + 1) * ROWS_B < c.d.rows) {
+    ++c.b;
+    return true;
+  }
+  c.t += nw;
+  c.b = 0;
+  if (c.t >= ntiles) return false;
+  c.d = c.dn;
+  if (c.t + nw < ntiles) c.dn = desc[c.t + nw];
+  return true;
+}
+
+template <typename TF, int W, int S>
+__global__ void __launch_bounds__(W * 32) apply_ring_kernel(const TileDesc* __restrict__ desc, int ntiles,
+                                                            const TF* __restrict__ F, const TF* __restrict__ pg,
+                                                            TF* rowpart, TF* colpart, const int* active,
+                                                            int* status) {
+  if (active && *active == 0) return;
+  using C = RingCfg<TF>;
+  using VT = typename Vec16<TF>::T;
+  constexpr int V = C::V, NCH = C::NCH, RPL = C::RPL, BATCH = C::BATCH, ROWS_B = C::ROWS_B;
+  extern __shared__ __align__(128) uint8_t ring_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cq = lane % NCH, half = lane / NCH;
+  const int nw = gridDim.x * W, gw = blockIdx.x * W + warp;
+  if (gw >= ntiles) return;  // whole warp; warps own their rings, nothing is shared
+  uint8_t* ring = ring_smem + (size_t)warp * S * C::STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring_smem + C::bars_ofs(W, S)) + warp * S;
+  int4* meta = reinterpret_cast<int4*>(ring_smem + C::meta_ofs(W, S)) + warp * S;
+  if (lane == 0) {
+    for (int k = 0; k < S; ++k) bar_init(&bars[k]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  RingCursor ic;
+  ic.t = gw;
+  ic.b = 0;
+  ic.d = desc[gw];
+  ic.dn = gw + nw < ntiles ? desc[gw + nw] : ic.d;
+  bool more = true;
+  int issued = 0, consumed = 0;
+  auto issue = [&](int slot) {
+    if (lane == 0) {
+      const TileDesc& d = ic.d;
+      const bool diag = (d.flags & kTileDiag) != 0;
+      const int r0 = ic.b * ROWS_B, r1 = min(r0 + ROWS_B, d.rows);
+      const int64_t e0 = diag ? diag_row_off<(int)sizeof(TF)>(r0) : (int64_t)r0 * kT;
+      const int64_t e1 = diag ? diag_row_off<(int)sizeof(TF)>(r1) : (int64_t)r1 * kT;
+      const uint32_t bytes = (uint32_t)((e1 - e0) * (int64_t)sizeof(TF));
+      uint8_t* st = ring + (size_t)slot * C::STAGE;
+      meta[slot] = make_int4(ic.t, ic.b, d.rows, diag ? 1 : 0);
+      bar_expect(&bars[slot], bytes + C::PC + C::PR);
+      bulk_to_smem(st, F + d.f_ofs + e0, bytes, &bars[slot]);
+      bulk_to_smem(st + C::DATA, pg + d.pcol, C::PC, &bars[slot]);
+      bulk_to_smem(st + C::DATA + C::PC, pg + d.prow + r0, C::PR, &bars[slot]);
+    }
+  };
+  for (; issued < S && more; ++issued) {
+    issue(issued);
+    more = ring_advance<ROWS_B>(ic, nw, ntiles, desc);
+  }
+  __syncwarp();  // lane 0's stage metadata is visible to the warp
+  TF cacc[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) cacc[e] = (TF)0;
+  bool failed = false;
+  while (consumed < issued) {
+    const int slot = consumed % S;
+    if (!bar_wait(&bars[slot], (uint32_t)((consumed / S) & 1))) {
+      failed = true;
+      break;
+    }
+    const int4 mt = meta[slot];
+    const int t = mt.x, b = mt.y, rows = mt.z;
+    const bool diag = mt.w != 0;
+    const uint8_t* st = ring + (size_t)slot * C::STAGE;
+    const TF* sf = reinterpret_cast<const TF*>(st);
+    const VT pc = *reinterpret_cast<const VT*>(st + C::DATA + cq * 16);
+    const TF* prs = reinterpret_cast<const TF*>(st + C::DATA + C::PC);
+    const int r0 = b * ROWS_B;
+    const int64_t e0 = diag ? diag_row_off<(int)sizeof(TF)>(r0) : 0;
+    TF rs[BATCH];
+#pragma unroll
+    for (int i = 0; i < BATCH; ++i) {
+      const int r = r0 + i * RPL + half;
+      const bool ok = r < rows && (!diag || cq * V <= r);
+      const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(r) - e0 : (int64_t)(r - r0) * kT;
+      const VT v = ok ? *reinterpret_cast<const VT*>(sf + off + cq * V) : VT{};
+      const TF pr = prs[i * RPL + half];
+      TF s2 = (TF)0;
+#pragma unroll
+      for (int e = 0; e < V; ++e) s2 = fma(comp(v, e), comp(pc, e), s2);
+      rs[i] = s2;
+#pragma unroll
+      for (int e = 0; e < V; ++e) cacc[e] = fma((diag && cq * V + e >= r) ? (TF)0 : comp(v, e), pr, cacc[e]);
+    }
+    __syncwarp();  // the stage has been read by every lane: it may be refilled
+    ++consumed;
+    if (more) {
+      issue(slot);
+      ++issued;
+      more = ring_advance<ROWS_B>(ic, nw, ntiles, desc);
+    }
+    ReduceScatter<TF, BATCH, NCH / 2>::run(rs, lane);
+    constexpr int SPAN = NCH / BATCH;
+    if (cq % SPAN == 0) {
+      const int r = r0 + (cq / SPAN) * RPL + half;
+      if (r < rows) rowpart[(int64_t)t * kT + r] = rs[0];
+    }
+    if (r0 + ROWS_B >= rows) {  // last batch of the tile
+      if constexpr (RPL == 2) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) cacc[e] += __shfl_xor_sync(0xffffffffu, cacc[e], 16);
+      }
+      if (half == 0) {
+        VT o;
+        if constexpr (V == 4) o = VT{cacc[0], cacc[1], cacc[2], cacc[3]};
+        else o = VT{cacc[0], cacc[1]};
+        *reinterpret_cast<VT*>(colpart + (int64_t)t * kT + cq * V) = o;
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) cacc[e] = (TF)0;
+    }
+  }
+  if (failed) {
+    // a copy did not land in time: report it and wait (bounded) for the copies still in flight
+    if (lane == 0 && status) atomicOr(status, kStatTimeout);
+    for (; consumed < issued; ++consumed) bar_wait(&bars[consumed % S], (uint32_t)((consumed / S) & 1));
+  }
+}
+
 // q_i[b kT + x] = sum_{bj <= b} rowpart[tile (b, bj)][x] + sum_{bi >= b} colpart[tile (bi, b)][x];
 // one warp per (subdomain, block), FP64 sums in a fixed order.
 template <typename TF>
@@ -288,20 +491,43 @@ void set_tiles_attr() {
   }
 }
 
-// variants of the tile kernel: 0 -> BATCH 4, 1 -> BATCH 8, 2 -> BATCH 16
+// variants of the tile kernel: register pipeline with 4 / 8 / 16-load batches
+// (0, 1, 2), or per-warp bulk-copy rings of W warps x S stages: 4 x 3, 8 x 3, 2 x 6 (3, 4, 5)
+constexpr int kRingW[3] = {4, 8, 2};
+constexpr int kRingS[3] = {3, 3, 6};
+
+template <typename TF, int W, int S>
+void launch_ring(int grid, cudaStream_t st, const TileDesc* desc, int ntiles, const TF* F, const TF* pg, TF* rowpart,
+                 TF* colpart, const int* active, int* status) {
+  const size_t smem = RingCfg<TF>::smem(W, S);
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(apply_ring_kernel<TF, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done = true;
+  }
+  apply_ring_kernel<TF, W, S><<<grid, W * 32, smem, st>>>(desc, ntiles, F, pg, rowpart, colpart, active, status);
+}
+
 template <typename TF>
 void launch_tiles(int variant, int grid, cudaStream_t st, const TileDesc* desc, int ntiles, const TF* F,
-                  const TF* pg, TF* rowpart, TF* colpart, const int* active = nullptr) {
+                  const TF* pg, TF* rowpart, TF* colpart, const int* active = nullptr, int* status = nullptr) {
   if (ntiles <= 0) return;
-  if (variant == 0) {
-    set_tiles_attr<TF, 4>();
-    apply_tiles_kernel<TF, 4><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
-  } else if (variant == 1) {
-    set_tiles_attr<TF, 8>();
-    apply_tiles_kernel<TF, 8><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
-  } else {
-    set_tiles_attr<TF, 16>();
-    apply_tiles_kernel<TF, 16><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
+  switch (variant) {
+    case 0:
+      set_tiles_attr<TF, 4>();
+      apply_tiles_kernel<TF, 4><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
+      break;
+    case 1:
+      set_tiles_attr<TF, 8>();
+      apply_tiles_kernel<TF, 8><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
+      break;
+    case 2:
+      set_tiles_attr<TF, 16>();
+      apply_tiles_kernel<TF, 16><<<grid, kApplyThreads, 0, st>>>(desc, ntiles, F, pg, rowpart, colpart, active);
+      break;
+    case 3: launch_ring<TF, 4, 3>(grid, st, desc, ntiles, F, pg, rowpart, colpart, active, status); break;
+    case 4: launch_ring<TF, 8, 3>(grid, st, desc, ntiles, F, pg, rowpart, colpart, active, status); break;
+    default: launch_ring<TF, 2, 6>(grid, st, desc, ntiles, F, pg, rowpart, colpart, active, status); break;
   }
 }
 
@@ -318,11 +544,12 @@ template <typename TF>
 static void launch_apply_t(const DevPlan& P, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
                            int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                            int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid,
-                           int variant, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+                           int variant, int* status, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 152 * 8));
   scatter_kernel<TF><<<sg, 256, 0, st>>>(qmap, ncols, p, (TF*)pg);
   if (e0) cudaEventRecord(e0, st);
-  launch_tiles<TF>(variant, grid, st, desc, ntiles, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart);
+  launch_tiles<TF>(variant, grid, st, desc, ntiles, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart, nullptr,
+                   status);
   if (e1) cudaEventRecord(e1, st);
   launch_reduce<TF>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi, st);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
@@ -337,13 +564,13 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
 void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
-                  cudaStream_t st, cudaEvent_t ev_tiles0, cudaEvent_t ev_tiles1) {
+                  int* status, cudaStream_t st, cudaEvent_t ev_tiles0, cudaEvent_t ev_tiles1) {
   if (fp32)
     launch_apply_t<float>(P, desc, ntiles, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                          nlam, q, grid, variant, st, ev_tiles0, ev_tiles1);
+                          nlam, q, grid, variant, status, st, ev_tiles0, ev_tiles1);
   else
     launch_apply_t<double>(P, desc, ntiles, F, qmap, ncols, p, pg, rowpart, colpart, blocks, nblocks, qi, c0, c1,
-                           nlam, q, grid, variant, st, ev_tiles0, ev_tiles1);
+                           nlam, q, grid, variant, status, st, ev_tiles0, ev_tiles1);
 }
 
 // The F-streaming part of the apply for the projected CG, whose scatter and
@@ -351,38 +578,52 @@ void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles,
 // when *active == 0 (an iteration enqueued after the solve has stopped).
 void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
                        void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
-                       int variant, const int* active, cudaStream_t st, cudaEvent_t ev_tiles0,
+                       int variant, const int* active, int* status, cudaStream_t st, cudaEvent_t ev_tiles0,
                        cudaEvent_t ev_tiles1, bool ev_external) {
   // under stream capture only an external record becomes a timed event-record node
   const unsigned evf = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev_tiles0) cudaEventRecordWithFlags(ev_tiles0, st, evf);
   if (fp32) {
     launch_tiles<float>(variant, grid, st, desc, ntiles, (const float*)F, (const float*)pg, (float*)rowpart,
-                        (float*)colpart, active);
+                        (float*)colpart, active, status);
     if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
     launch_reduce<float>(P, blocks, nblocks, (const float*)rowpart, (const float*)colpart, qi, st, active);
   } else {
     launch_tiles<double>(variant, grid, st, desc, ntiles, (const double*)F, (const double*)pg, (double*)rowpart,
-                         (double*)colpart, active);
+                         (double*)colpart, active, status);
     if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
     launch_reduce<double>(P, blocks, nblocks, (const double*)rowpart, (const double*)colpart, qi, st, active);
   }
 }
 
-int apply_variants() { return 3; }
+int apply_variants() { return 6; }
+
+int apply_warps_per_cta(int variant) { return variant < 3 ? kApplyThreads / 32 : kRingW[variant - 3]; }
+
+template <typename TF, int W, int S>
+static int occ_ring() {
+  const size_t smem = RingCfg<TF>::smem(W, S);
+  cudaFuncSetAttribute(apply_ring_kernel<TF, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_ring_kernel<TF, W, S>, W * 32, smem);
+  return nb;
+}
 
 template <typename TF>
 static int occ_tiles(int variant) {
   int nb = 0;
-  if (variant == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 4>, kApplyThreads, 0);
-  else if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 8>, kApplyThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 16>, kApplyThreads, 0);
+  switch (variant) {
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 4>, kApplyThreads, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 8>, kApplyThreads, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, apply_tiles_kernel<TF, 16>, kApplyThreads, 0); break;
+    case 3: nb = occ_ring<TF, 4, 3>(); break;
+    case 4: nb = occ_ring<TF, 8, 3>(); break;
+    default: nb = occ_ring<TF, 2, 6>(); break;
+  }
   return nb;
 }
 
 int apply_max_ctas_per_sm(bool fp32, int variant) { return fp32 ? occ_tiles<float>(variant) : occ_tiles<double>(variant); }
-
-int apply_warps_per_cta() { return kApplyThreads / 32; }
 
 // ---------------------------------------------------------------------------
 // Stand-alone application of one local operator without any device allocation.

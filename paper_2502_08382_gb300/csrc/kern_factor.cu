@@ -251,33 +251,57 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
       for (int a = b + tid; a < rc; a += TEAM) Fp[pidx(f, rl[a], rl[b])] += U[(int64_t)b * rc + a];
   }
   team_sync<TEAM>();
-  // right-looking partial factorisation of the first w columns
-  for (int j = 0; j < w; ++j) {
-    const int cj = pidx(f, j, j);
-    if (tid == 0) {
-      double pv = Fp[cj];
-      if (!(pv > 0.0)) {
-        *bad = 1;
-        pv = 1.0;
+  // blocked right-looking partial factorisation of the first w columns: one warp
+  // factors kPB columns (warp syncs only), then the whole team applies their
+  // rank-kPB update to the trailing triangle, kPB FMAs per element
+  constexpr int kPB = 8;
+  const int lane = tid & 31;
+  for (int j0 = 0; j0 < w; j0 += kPB) {
+    const int jb = min(kPB, w - j0);
+    if (tid < 32) {
+      for (int j = j0; j < j0 + jb; ++j) {
+        const int cj = pidx(f, j, j);
+        if (lane == 0) {
+          double pv = Fp[cj];
+          if (!(pv > 0.0)) {
+            *bad = 1;
+            pv = 1.0;
+          }
+          Fp[cj] = sqrt(pv);
+        }
+        __syncwarp();
+        const double inv = 1.0 / Fp[cj];
+        for (int i = j + 1 + lane; i < f; i += 32) Fp[cj + (i - j)] *= inv;
+        __syncwarp();
+        // update the panel's later columns k in (j, j0 + jb), rows i >= k
+        for (int k = j + 1; k < j0 + jb; ++k) {
+          const double lkj = Fp[cj + (k - j)];
+          const int pk = pidx(f, k, k);
+          for (int i = k + lane; i < f; i += 32) Fp[pk + (i - k)] = fma(-Fp[cj + (i - j)], lkj, Fp[pk + (i - k)]);
+        }
+        __syncwarp();
       }
-      Fp[cj] = sqrt(pv);
     }
     team_sync<TEAM>();
-    const double inv = 1.0 / Fp[cj];
-    for (int i = j + 1 + tid; i < f; i += TEAM) Fp[cj + (i - j)] *= inv;
-    team_sync<TEAM>();
-    // trailing update A[i][k] -= L[i][j] L[k][j], k in (j, f), i in [k, f): element e of the packed
-    // trailing triangle goes to thread e mod TEAM; (k, rem) walks the columns
-    int k = j + 1, rem = tid;
+    // trailing update A[i][k] -= sum_{j in panel} L[i][j] L[k][j], k >= j0 + jb, i >= k:
+    // element e of the packed trailing triangle goes to thread e mod TEAM
+    const int k0 = j0 + jb;
+    int k = k0, rem = tid;
     while (k < f && rem >= f - k) {
       rem -= f - k;
       ++k;
     }
     while (k < f) {
       const int i = k + rem;
-      const double lkj = Fp[cj + (k - j)];
-      const int pk = pidx(f, k, k);
-      Fp[pk + rem] = fma(-Fp[cj + (i - j)], lkj, Fp[pk + rem]);
+      double acc = Fp[pidx(f, i, k)];
+#pragma unroll
+      for (int u = 0; u < kPB; ++u) {
+        if (u < jb) {
+          const int cj = pidx(f, j0 + u, j0 + u);
+          acc = fma(-Fp[cj + (i - j0 - u)], Fp[cj + (k - j0 - u)], acc);
+        }
+      }
+      Fp[pidx(f, i, k)] = acc;
       rem += TEAM;
       while (k < f && rem >= f - k) {
         rem -= f - k;

@@ -21,14 +21,14 @@ void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const doub
 void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
-                  cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
+                  int* status, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
 void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
                        void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
-                       int variant, const int* active, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr,
+                       int variant, const int* active, int* status, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr,
                        cudaEvent_t ev_tiles1 = nullptr, bool ev_external = false);
 int apply_variants();
 int apply_max_ctas_per_sm(bool fp32, int variant);
-int apply_warps_per_cta();
+int apply_warps_per_cta(int variant);
 void launch_unpack_F(const void* Fsub, bool fp32, int m, int nb, int vr, const int* colperm, double* out,
                      cudaStream_t st);
 
