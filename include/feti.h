@@ -94,6 +94,8 @@ typedef struct {
   int32_t use_coords;         /* 1 = coordinate bisection when coords are given */
   double refine_drop;         /* PCPG: also recompute the FP64 residual once ||P r|| has dropped by this
                                  factor since the last recomputation (0 = off) */
+  int32_t refine_restart;     /* PCPG: 1 = restart the search direction after each recomputation
+                                 (iterative refinement with inner CG solves); 0 = keep it */
 } feti_options;
 
 typedef struct {
@@ -164,6 +166,18 @@ feti_status feti_apply_implicit(feti_ctx* ctx, const double* p_dev, double* q_de
  * (p.F p <= 0). */
 feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev,
                        feti_solve_info* info);
+
+/* feti_solve started from a guess: on entry lambda_dev [n_lambda] holds
+ * lambda_g (for instance the previous step's solution in a multi-step
+ * simulation, Algorithm 2, after feti_update_values + feti_assemble), and the
+ * iteration starts from lambda_0 = lambda_I + P lambda_g, which satisfies
+ * G^T lambda_0 = e (eq. 4) for any guess.  The stopping rule keeps the
+ * reference norm of a cold start, ||P (d - F lambda_I)|| (one more FP64
+ * implicit application), so a good guess reaches the same accuracy in fewer
+ * iterations.  Outputs and errors as feti_solve; lambda_dev is overwritten
+ * with the solution. */
+feti_status feti_solve_warm(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev,
+                            feti_solve_info* info);
 
 /* Adjoint of L = sum_i <W_i, F_i>: dtheta[e] = -<Z_i^T dK_e Z_i, W_i> with
  * Z_i = K_reg,i^{-1} B_i^T (derivative of the inverse, rho held fixed).

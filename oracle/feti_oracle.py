@@ -185,13 +185,17 @@ class Projector:
         return x - self.G @ self.coarse_solve(self.G.T @ x)
 
 
-def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=False):
+def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=False, lam_guess=None):
     """Algorithm 1 (PCPG) with M = I and lambda_I = G (G^T G)^{-1} e.
     Stops when ||w_k|| <= tol * ||w_0||, or when ||w_k|| has reached the
     rounding level of the residual, ||w_k|| <= 64 eps (||d|| + ||F lambda_I||)
     (Algorithm 1 only says "until convergence"; without the floor a problem
     whose lambda_I already solves the dual problem could never stop, since
-    w_0 is then rounding noise).  Returns (lambda, iterations, info)."""
+    w_0 is then rounding noise).
+    lam_guess (a warm start, e.g. the previous step of Algorithm 2): the
+    iteration starts from lambda_I + P lam_guess, which keeps G^T lambda = e;
+    w_0 and the floor above stay those of lambda_I, so the stopping rule asks
+    for the same accuracy as a cold start.  Returns (lambda, iterations, info)."""
     if G is None:
         G = G_matrix(problem)
     if e is None:
@@ -205,13 +209,17 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
     r = d - Flam
     floor = 64.0 * np.finfo(np.float64).eps * (np.linalg.norm(d) + np.linalg.norm(Flam))
     w = P(r)
+    nw0 = float(np.linalg.norm(w))
+    if lam_guess is not None:
+        lam = lam + P(np.asarray(lam_guess, dtype=np.float64))
+        r = d - Fop(lam)
+        w = P(r)
+    hist = [G.T @ lam - e] if history else None
     y = P(w)            # y = P M w with M = I
     p = y.copy()
     wy = float(w @ y)
-    nw0 = float(np.linalg.norm(w))
-    hist = [G.T @ lam - e] if history else None
     k = 0
-    if nw0 <= floor:
+    if np.linalg.norm(w) <= max(tol * nw0, floor):
         return lam, 0, dict(P=P, G=G, d=d, e=e, hist=hist)
     while k < maxit:
         q = Fop(p)
@@ -251,14 +259,15 @@ def primal_solution(problem, lam, alpha, Krs=None):
     return us
 
 
-def feti_solve(problem, tol=1e-10, maxit=5000):
-    """Whole FETI solve in FP64: F_i, PCPG, alpha, u_i."""
+def feti_solve(problem, tol=1e-10, maxit=5000, lam_guess=None):
+    """Whole FETI solve in FP64: F_i, PCPG (warm-started from lam_guess if
+    given), alpha, u_i."""
     Krs = [K_reg(s) for s in problem.subs]
     Fs = [local_F(s, Kr) for s, Kr in zip(problem.subs, Krs)]
     G = G_matrix(problem)
     d = d_vector(problem, Krs)
     e = e_vector(problem)
-    lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e)
+    lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e, lam_guess=lam_guess)
     alpha = alpha_from_lambda(problem, Fs, lam, info["P"], d)
     us = primal_solution(problem, lam, alpha, Krs)
     return dict(lam=lam, alpha=alpha, u=us, iterations=its, Fs=Fs, G=G, d=d, e=e)

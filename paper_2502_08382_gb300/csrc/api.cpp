@@ -310,6 +310,7 @@ void build(feti_ctx* c) {
     SubInfo& I = c->info[i];
     I.n = s.n;
     I.m = s.m;
+    c->m_max = std::max(c->m_max, s.m);
     I.m_pad = B.m_pad;
     I.nb = B.nb;
     I.nsn = P.nsn;
@@ -426,6 +427,24 @@ void build(feti_ctx* c) {
       else if (c1[lam] < 0) c1[lam] = (int)(I.qcol + j);
       else throw ArgError("a multiplier touches more than two subdomains");
     }
+  }
+  // per multiplier: {tile base, (column << 8) | nb} of its first and second subdomain column (the PCPG
+  // gather), and {alpha0, d} of its first and second subdomain (the projector in the update)
+  std::vector<int4> lamcol(c->nlam, make_int4(0, 0, -1, 0)), lamg(c->nlam, make_int4(0, 0, 0, 0));
+  for (int l = 0; l < c->nlam; ++l) {
+    const int g[2] = {c0[l], c1[l]};
+    int v[4] = {0, 0, -1, 0}, a[4] = {0, 0, 0, 0};
+    for (int e = 0; e < 2; ++e) {
+      if (g[e] < 0) continue;
+      const auto& J = c->info[colsub[g[e]]];
+      if (J.nb > 255) throw ArgError("a subdomain has more than 255 64-wide blocks of multipliers");
+      v[2 * e] = (int)(J.tpart / kT);
+      v[2 * e + 1] = (int)((g[e] - J.qcol) << 8) | J.nb;
+      a[2 * e] = J.alpha0;
+      a[2 * e + 1] = J.d;
+    }
+    lamcol[l] = make_int4(v[0], v[1], v[2], v[3]);
+    lamg[l] = make_int4(a[0], a[1], a[2], a[3]);
   }
 
   // ---- coarse problem pairs: (i, k) blocks of G^T G and the sorted columns they pair
@@ -616,8 +635,12 @@ void build(feti_ctx* c) {
   c->d_pg = dalloc(c, (size_t)qo * 8);
   c->d_qi = (double*)dalloc(c, (size_t)qo * 8);
   c->d_colsub = upload(c, colsub);
+  D.colsub = c->d_colsub;
   c->d_c0 = upload(c, c0);
   c->d_c1 = upload(c, c1);
+  c->d_lamcol = upload(c, lamcol);
+  c->d_lamg = upload(c, lamg);
+  c->d_qcol = (double*)dalloc(c, (size_t)qo * 8);
   c->d_queue = (int*)dalloc(c, 64 * sizeof(int));
   c->d_status = (int*)dalloc(c, sizeof(int));
   c->d_chol_order = upload(c, order);
@@ -654,8 +677,8 @@ void build(feti_ctx* c) {
     c->d_Dinv = (double*)dalloc(c, (size_t)nblk * kT * kT * 8);
     c->d_Tp = (double*)dalloc(c, (size_t)D2 * kT * 8);
     c->d_Tb = (double*)dalloc(c, (size_t)D2 * kT * 8);
-    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 8 * 8);
-    c->d_cv = (double*)dalloc(c, (size_t)D2 * 4 * 8);
+    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 9 * 8);
+    c->d_cv = (double*)dalloc(c, (size_t)D2 * 5 * 8);
     c->d_sc = (double*)dalloc(c, 16 * 8);
     c->d_part = (double*)dalloc(c, 2 * kPcgMaxBlocks * 8);
     CK(cudaMallocHost((void**)&c->h_sc, 16 * 8));
@@ -770,12 +793,13 @@ feti_status feti_assemble(feti_ctx* ctx) {
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
               ctx->chol_stack,
               ctx->grid_chol, ctx->d_status, st);
-  launch_diag_recip(ctx->P, ctx->nsub, ctx->P.dinv, st);
-  ctx->stats.launches += 4;  // Cholesky, reciprocal pivots, pruned TRSM, SYRK
+  ctx->stats.launches += 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
               ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, st);
+  // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
+  launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, st);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
   if (ctx->fp32) {
@@ -859,7 +883,7 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev) {
   launch_apply(ctx->P, ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->ncols, p_dev, ctx->d_pg,
                ctx->d_rowpart, ctx->d_tpart, ctx->d_blocks, ctx->nblocks, ctx->d_qi, ctx->d_c0, ctx->d_c1, ctx->nlam,
                q_dev, grid, cand.variant, ctx->d_status, st, ev.b, ev.c);
-  ctx->stats.launches += 4;
+  ctx->stats.launches += 3;
   ctx->stats.apply_calls += 1;
   if (ctx->prof) {
     CK(cudaEventRecord(ev.d, st));

@@ -26,9 +26,10 @@ struct CudaErr : std::runtime_error {
   } while (0)
 
 // vectors inside ctx->d_vec (each n_lambda long)
-enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM };
+// V_Q: scratch of the FP64 implicit operator; V_QK: q_k = F p_k of the iteration
+enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM, V_QK };
 // coarse vectors in ctx->d_cv (each D long)
-enum { C_E = 0, C_C, C_Z, C_A };
+enum { C_E = 0, C_C, C_Z, C_A, C_GQ };
 
 double* vec(feti_ctx* c, int k) { return c->d_vec + (size_t)k * c->nlam; }
 double* cvec(feti_ctx* c, int k) { return c->d_cv + (size_t)k * std::max(c->dtot, 1); }
@@ -104,32 +105,30 @@ const PcgCtrl& read_ctrl(feti_ctx* c) {
   return *c->h_ctrl;
 }
 
-// One PCPG iteration (Algorithm 1, M = I) on the device, seven launches; every
+// One PCPG iteration (Algorithm 1, M = I) on the device, six launches; every
 // kernel returns at once if the control block says the iteration has stopped.
 // ev (4 events or null): before the scatter, around the F-streaming kernel, after the gather.
 void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStream_t st, bool capture) {
   const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   const int n = c->nlam, D = c->dtot;
-  double *d = vec(c, V_D), *r = vec(c, V_R), *w = vec(c, V_W), *p = vec(c, V_P), *q = vec(c, V_Q);
+  double *d = vec(c, V_D), *r = vec(c, V_R), *w = vec(c, V_W), *p = vec(c, V_P), *qk = vec(c, V_QK);
   PcgCtrl* ctrl = ctrl_dev(c);
   const auto& cand = c->apply_cands[c->apply_pick];
   if (ev) CKS(cudaEventRecordWithFlags(ev[0], st, evf));
-  launch_pcg_scatter(c->fp32, c->P.qmap, c->ncols, p, w, c->d_pg, ctrl, st);
-  launch_apply_core(c->P, c->fp32, c->d_tdesc, c->napply, c->d_F, c->d_pg, c->d_rowpart, c->d_tpart, c->d_blocks,
-                    c->nblocks, c->d_qi, cand.grid, cand.variant, active_dev(c), c->d_status, st,
-                    ev ? ev[1] : nullptr,
-                    ev ? ev[2] : nullptr, capture);
-  launch_pcg_gather_dot(c->d_c0, c->d_c1, n, c->d_qi, p, w, q, c->d_part, ctrl, st);
+  launch_apply_core(c->fp32, c->d_tdesc, c->napply, c->d_F, c->d_pg, c->d_rowpart, c->d_tpart, cand.grid,
+                    cand.variant, active_dev(c), c->d_status, st, ev ? ev[1] : nullptr, ev ? ev[2] : nullptr, capture);
+  launch_pcg_gather_dot(c->fp32, c->d_lamcol, c->d_c0, c->d_c1, n, c->d_rowpart, c->d_tpart, p, w, qk, c->d_qcol,
+                        c->d_part, ctrl, st);
   if (ev) CKS(cudaEventRecordWithFlags(ev[3], st, evf));
   if (D > 0) {
-    launch_pcg_gt(c->P, c->nsub, c->d_G6, r, q, d, 0, cvec(c, C_C), ctrl, st);
-    launch_gemv_rows(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), D, ctrl, 0, st);
+    launch_pcg_gt(c->P, c->nsub, c->d_G6, c->d_qcol, nullptr, nullptr, 0, cvec(c, C_GQ), ctrl, st);
+    launch_gemv_rows(c->d_Ainv, cvec(c, C_GQ), cvec(c, C_Z), D, ctrl, 0, st);
   }
-  launch_pcg_update(c->P, c->d_colsub, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam,
-                    r, w, c->d_part + kPcgMaxBlocks, 0, ctrl, st);
+  launch_pcg_update(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, qk, d, lam, r,
+                    w, c->d_pg, c->d_part + kPcgMaxBlocks, 0, ctrl, st);
 }
 
-int iteration_launches(feti_ctx* c) { return c->dtot > 0 ? 7 : 5; }
+int iteration_launches(feti_ctx* c) { return c->dtot > 0 ? 5 : 3; }
 
 // Capture `chunk` iterations on the private stream into one CUDA graph (once
 // per context and chunk size); replaying it enqueues the whole chunk at once.
@@ -167,11 +166,11 @@ void enqueue_refresh(feti_ctx* c, double* lam, int mode) {
   implicit_apply(c, lam, q);
   if (mode == 2) launch_pcg_norms(d, q, n, ctrl, st);
   if (D > 0) {
-    launch_pcg_gt(c->P, c->nsub, c->d_G6, r, q, d, 1, cvec(c, C_C), ctrl, st);
+    launch_pcg_gt(c->P, c->nsub, c->d_G6, nullptr, q, d, 1, cvec(c, C_C), ctrl, st);
     launch_gemv_rows(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), D, ctrl, 1, st);
   }
-  launch_pcg_update(c->P, c->d_colsub, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam,
-                    r, w, c->d_part + kPcgMaxBlocks, mode, ctrl, st);
+  launch_pcg_update(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam, r,
+                    w, c->d_pg, c->d_part + kPcgMaxBlocks, mode, ctrl, st);
   c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0);
 }
 
@@ -200,7 +199,12 @@ feti_status feti_apply_implicit(feti_ctx* ctx, const double* p_dev, double* q_de
   }
 }
 
-feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev, feti_solve_info* info) {
+}  // extern "C"
+
+namespace {
+
+feti_status solve_impl(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev, feti_solve_info* info,
+                       bool warm) {
   GUARD();
   if (!lambda_dev) return set_error(ctx, FETI_ERR_ARG, "feti_solve: lambda_dev is required");
   try {
@@ -229,11 +233,31 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
     h.tol = tol;
     h.maxit = maxit;
     h.active = 1;
+    h.restart = ctx->opt.refine_restart ? 1 : 0;
     *ctx->h_ctrl = h;
     CKS(cudaMemcpyAsync(ctx->d_ctrl, ctx->h_ctrl, sizeof(PcgCtrl), cudaMemcpyHostToDevice, st));
+    // p_{-1} = q_{-1} = 0 (beta = 0 at the start, but 0 * garbage need not be 0);
+    // padded B columns of pg stay 0
     CKS(cudaMemsetAsync(p, 0, (size_t)n * 8, st));
-    // r_0 = d - F_64 lambda_0, w_0 = P r_0 (FP64 implicit operator)
+    CKS(cudaMemsetAsync(vec(ctx, V_QK), 0, (size_t)n * 8, st));
+    CKS(cudaMemsetAsync(ctx->d_pg, 0, (size_t)ctx->ncols * (ctx->fp32 ? 4 : 8), st));
+    // r_0 = d - F_64 lambda_I, w_0 = P r_0 (FP64 implicit operator): the reference norm and the
+    // rounding floor of the stopping rule
     enqueue_refresh(ctx, lam, 2);
+    if (warm) {
+      // lambda_0 = lambda_g + G (G^T G)^{-1} (e - G^T lambda_g) = lambda_I + P lambda_g, then its residual
+      if (D > 0) {
+        launch_gt(ctx->P, ctx->nsub, ctx->d_G6, lambda_dev, cvec(ctx, C_C), st);
+        launch_sub(cvec(ctx, C_E), cvec(ctx, C_C), cvec(ctx, C_C), D, st);
+        launch_gemv(ctx->d_Ainv, cvec(ctx, C_C), cvec(ctx, C_Z), D, 1.0, st);
+        launch_gz(ctx->P, ctx->d_colsub, ctx->d_c0, ctx->d_c1, n, ctx->d_G6, lambda_dev, cvec(ctx, C_Z), -1.0, lam,
+                  st);
+        ctx->stats.launches += 4;
+      } else {
+        CKS(cudaMemcpyAsync(lam, lambda_dev, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+      }
+      enqueue_refresh(ctx, lam, 1);
+    }
     PcgCtrl cur = read_ctrl(ctx);
     const double nw0 = cur.nw0;
     const int kref = ctx->opt.refine_every;
@@ -320,6 +344,19 @@ feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
   } catch (std::exception& e) {
     return set_error(ctx, FETI_ERR_CUDA, e.what());
   }
+}
+
+}  // namespace
+
+extern "C" {
+
+feti_status feti_solve(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev, feti_solve_info* info) {
+  return solve_impl(ctx, lambda_dev, alpha_dev, u_dev, info, false);
+}
+
+feti_status feti_solve_warm(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, double* u_dev,
+                            feti_solve_info* info) {
+  return solve_impl(ctx, lambda_dev, alpha_dev, u_dev, info, true);
 }
 
 feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev) {

@@ -81,6 +81,7 @@ struct DevPlan {
   const int* t2_sn;
   // per subdomain
   const int* qmap;           // [qcol + j] global multiplier of sorted column j, -1 for padding
+  const int* colsub;         // [qcol + j] subdomain of sorted column j
   const double* qsign;       // [qcol + j] sign of B in sorted column j (0 for padding)
   const int* iperm;          // [diag0 + old DOF] new-numbered DOF (pattern)
   const int* qdof;           // [qcol + j] original local DOF of sorted column j
@@ -138,6 +139,42 @@ struct __align__(16) TileDesc {
   int pad0, pad1;
 };
 
+// (F_i p_i)[j] for column j of a subdomain whose tile partials start at tile
+// slot tb (nb blocks): the row partials of the tiles of its block row and the
+// column partials of the tiles of its block column, summed in FP64 in a fixed
+// order (bj = 0..b, then bi = b..nb-1).  The loads are issued eight at a time
+// so that they overlap; the additions keep that order.
+template <typename TF>
+__device__ __forceinline__ double colsum_at(int64_t tb, int nb, int j, const TF* rowpart, const TF* colpart) {
+  const int b = j / kT, x = j % kT;
+  const int nt = nb + 1;  // b + 1 row partials, nb - b column partials
+  const int64_t r0 = tb + (int64_t)b * (b + 1) / 2;
+  double s = 0.0;
+  for (int k0 = 0; k0 < nt; k0 += 8) {
+    TF v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u;
+      v[u] = (TF)0;
+      if (k <= b) v[u] = rowpart[(r0 + k) * kT + x];
+      else if (k < nt) {
+        const int bi = k - 1;  // b .. nb - 1
+        v[u] = colpart[(tb + (int64_t)bi * (bi + 1) / 2 + b) * kT + x];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < nt) s += (double)v[u];
+  }
+  return s;
+}
+
+// colsum_at for sorted column g of subdomain `sub`
+template <typename TF>
+__device__ __forceinline__ double tile_colsum(const SubInfo& S, int64_t g, const TF* rowpart, const TF* colpart) {
+  return colsum_at(S.tpart / kT, S.nb, (int)(g - S.qcol), rowpart, colpart);
+}
+
 // Control block of the projected CG (Algorithm 1), in device memory.  The
 // vector kernels read and update it; the host reads it once per chunk of
 // enqueued iterations.
@@ -159,6 +196,7 @@ struct PcgCtrl {
   int maxit;
   int conv;       // the last ||w|| met the stopping rule
   int breakdown;  // p.q <= 0 was met
+  int restart;    // 1: a residual replacement restarts the search direction (beta = 0)
   int cnt_dot, cnt_upd;  // arrival counters of the last-block reductions
   int pad;
 };

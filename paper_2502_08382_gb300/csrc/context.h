@@ -105,8 +105,12 @@ struct feti_ctx {
   double* d_Dinv = nullptr;    // inverses of the 64 x 64 diagonal factor blocks
   double* d_Tp = nullptr;      // D x 64 panel scratch
   double* d_Tb = nullptr;      // 64 x D row-block scratch
-  double* d_vec = nullptr;     // PCPG vectors (7 x n_lambda)
-  double* d_cv = nullptr;      // coarse vectors (4 x D)
+  int4* d_lamcol = nullptr;    // per multiplier: tile bases and columns of its subdomain columns (PCPG gather)
+  int4* d_lamg = nullptr;      // per multiplier: alpha0 and d of its subdomains (PCPG update)
+  double* d_qcol = nullptr;    // per B column: q of its multiplier (PCPG G^T q)
+  int m_max = 0;               // widest subdomain (B rows)
+  double* d_vec = nullptr;     // PCPG vectors (9 x n_lambda)
+  double* d_cv = nullptr;      // coarse vectors (5 x D)
   double* d_sc = nullptr;      // scalars
   double* d_part = nullptr;    // block partials of the PCPG reductions (2 x kPcgMaxBlocks)
   double* h_sc = nullptr;      // pinned host scalars

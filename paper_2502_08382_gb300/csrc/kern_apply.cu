@@ -1,5 +1,5 @@
 // Explicit application q = F p (paper eq. 12 summed over subdomains, with
-// Algorithm 2's scatter / per-subdomain apply / gather), four launches:
+// Algorithm 2's scatter / per-subdomain apply / gather), three launches:
 //
 //  0. scatter: pg[j] = p[map_i(j)] for every sorted column j of every
 //             subdomain (Algorithm 2's scatter), in the tile precision;
@@ -13,10 +13,10 @@
 //             strictly lower part, transposed).  Tiles are dealt to warps
 //             round-robin, so all warps stream neighbouring tiles together
 //             and the load is balanced to one tile;
-//  2. reduce: q_i[block b] = the row partials of tile row b plus the column
-//             partials of tile column b, in a fixed order, in FP64;
-//  3. gather: q[lambda] = sum over the (at most two) subdomain columns of
-//             lambda, in subdomain order (deterministic, no atomics).
+//  2. gather: q[lambda] = sum over the (at most two) subdomain columns of
+//             lambda of that column's tile partials (the row partials of its
+//             tile row and the column partials of its tile column), in FP64
+//             and in a fixed order (deterministic, no atomics).
 // Tile arithmetic runs in the tile's precision (FP32 tiles: FP32 FMAs); the
 // cross-tile sums in phase 2 are FP64.  Nothing waits on another warp.
 #include <algorithm>
@@ -472,6 +472,19 @@ __global__ void reduce_tiles_kernel(DevPlan P, const int2* blocks, int nblocks, 
   }
 }
 
+// q[lambda] = sum over its (at most two) subdomain columns of the tile partials
+// of that column (tile_colsum), in subdomain order
+template <typename TF>
+__global__ void gather_tiles_kernel(DevPlan P, const int* colsub, const int* c0, const int* c1, int nlam,
+                                    const TF* rowpart, const TF* colpart, double* q) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int a = c0[l], b = c1[l];
+    double s = a >= 0 ? tile_colsum(P.sub[colsub[a]], a, rowpart, colpart) : 0.0;
+    if (b >= 0) s += tile_colsum(P.sub[colsub[b]], b, rowpart, colpart);
+    q[l] = s;
+  }
+}
+
 // q[lambda] = its (at most two) subdomain contributions, in subdomain order
 __global__ void gather_lambda_kernel(const int* c0, const int* c1, int nlam, const double* qi, double* q) {
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
@@ -551,9 +564,8 @@ static void launch_apply_t(const DevPlan& P, const TileDesc* desc, int ntiles, c
   launch_tiles<TF>(variant, grid, st, desc, ntiles, (const TF*)F, (const TF*)pg, (TF*)rowpart, (TF*)colpart, nullptr,
                    status);
   if (e1) cudaEventRecord(e1, st);
-  launch_reduce<TF>(P, blocks, nblocks, (const TF*)rowpart, (const TF*)colpart, qi, st);
   const int gg = std::max(1, std::min((nlam + 255) / 256, 152 * 8));
-  gather_lambda_kernel<<<gg, 256, 0, st>>>(c0, c1, nlam, qi, q);
+  gather_tiles_kernel<TF><<<gg, 256, 0, st>>>(P, P.colsub, c0, c1, nlam, (const TF*)rowpart, (const TF*)colpart, q);
 }
 
 void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* qi, double* q, cudaStream_t st) {
@@ -574,12 +586,12 @@ void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles,
 }
 
 // The F-streaming part of the apply for the projected CG, whose scatter and
-// gather are fused into its vector kernels: tiles then reduce, both skipped
-// when *active == 0 (an iteration enqueued after the solve has stopped).
-void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
-                       void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
-                       int variant, const int* active, int* status, cudaStream_t st, cudaEvent_t ev_tiles0,
-                       cudaEvent_t ev_tiles1, bool ev_external) {
+// gather are fused into its vector kernels (the gather sums the tile
+// partials itself); skipped when *active == 0 (an iteration enqueued after
+// the solve has stopped).
+void launch_apply_core(bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg, void* rowpart,
+                       void* colpart, int grid, int variant, const int* active, int* status, cudaStream_t st,
+                       cudaEvent_t ev_tiles0, cudaEvent_t ev_tiles1, bool ev_external) {
   // under stream capture only an external record becomes a timed event-record node
   const unsigned evf = ev_external ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev_tiles0) cudaEventRecordWithFlags(ev_tiles0, st, evf);
@@ -587,12 +599,10 @@ void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int nt
     launch_tiles<float>(variant, grid, st, desc, ntiles, (const float*)F, (const float*)pg, (float*)rowpart,
                         (float*)colpart, active, status);
     if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
-    launch_reduce<float>(P, blocks, nblocks, (const float*)rowpart, (const float*)colpart, qi, st, active);
   } else {
     launch_tiles<double>(variant, grid, st, desc, ntiles, (const double*)F, (const double*)pg, (double*)rowpart,
                          (double*)colpart, active, status);
     if (ev_tiles1) cudaEventRecordWithFlags(ev_tiles1, st, evf);
-    launch_reduce<double>(P, blocks, nblocks, (const double*)rowpart, (const double*)colpart, qi, st, active);
   }
 }
 

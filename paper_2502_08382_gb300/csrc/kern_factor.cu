@@ -326,7 +326,7 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
 // Phase 1: the small subtrees, level by level from the leaves, one warp per
 // front.  Phase 2: the remaining supernodes in postorder, fronts up to
 // kMidFront in shared memory across the CTA, larger ones by the tiled path.
-__global__ void __launch_bounds__(kThreads, 3) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
+__global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          double* ws, int64_t ws_stride, int64_t front_sz,
                                                          int64_t stack_sz, int* status) {
   extern __shared__ double dsm[];

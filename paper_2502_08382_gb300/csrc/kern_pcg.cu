@@ -1,23 +1,26 @@
 // Vector kernels of the projected conjugate gradient (Algorithm 1, M = I),
-// fused so that one iteration is seven launches and no host round trip:
+// fused so that one iteration is five launches and no host round trip:
 //
-//   1. scatter:  p <- w + beta p is formed on the fly and gathered into the
-//                tile precision, pg[j] = p[map(j)] (Algorithm 2's scatter);
-//   2-3.         the F-streaming tiles and the per-block reduce (kern_apply.cu);
-//   4. gather:   q = F p (Algorithm 2's gather), p <- w + beta p stored, and
-//                the dot p.q; the last block to finish sums the block partials
-//                in a fixed order and sets delta = (w.w) / (p.q);
-//   5. G^T x:    c = G^T (r - delta q)   (or G^T (d - F lambda) on a refresh);
-//   6. z = (G^T G)^{-1} c  (explicit FP64 inverse, eqs. 6-8);
-//   7. update:   lambda += delta p, r -= delta q (or r = d - F lambda),
-//                w = r - G z (the projector), the dot w.w; the last block
-//                sets beta, the relative residual and the stop flags.
+//   1. tiles:    the F-streaming tile kernel (kern_apply.cu) on pg = B w_k,
+//                gathered into the tile precision by the previous update;
+//   2. gather:   f = F w_k from the tile partials (Algorithm 2's gather); by
+//                linearity of F, q_k = F p_k = f + beta q_{k-1} and
+//                p_k = w_k + beta p_{k-1}; the dot p.q, whose last block sets
+//                delta = (w.w) / (p.q); q_k is also written per B column;
+//   3. G^T q_k per subdomain, from the per-column copy;
+//   4. z -= delta (G^T G)^{-1} G^T q_k  (explicit FP64 inverse, eqs. 6-8): z
+//                follows r, z_k = (G^T G)^{-1} G^T r_k;
+//   5. update:   lambda += delta p, r -= delta q (or r = d - F lambda on a
+//                residual replacement), w = r - G z (the projector), the dot
+//                w.w and the scatter pg = B w for the next iteration; the last
+//                block sets beta, the relative residual and the stop flags.
 //
 // The control block lives in device memory; every kernel of an iteration
 // returns at once when `active` is 0, so the host can enqueue several
 // iterations ahead and read the control block once per chunk.  Dot products
 // are reduced in a fixed order (block partials summed by one block), so a
-// solve is bitwise reproducible.
+// solve is bitwise reproducible.  Per-multiplier index data is precomputed on
+// the host so that every thread starts its loads from one coalesced record.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -59,31 +62,29 @@ __device__ __forceinline__ double sum_partials(const double* part, int nb, doubl
   return block_sum(s, red);
 }
 
+// One thread per multiplier l.  lc[l] = {tile base, (column << 8) | nb} of
+// its first and second subdomain column (second tile base -1 if none): f =
+// colsum(first) + colsum(second), both in the fixed order of colsum_at.
 template <typename TF>
-__global__ void pcg_scatter_kernel(const int* qmap, int64_t ncols, const double* p, const double* w, TF* pg,
-                                   const PcgCtrl* ctrl) {
-  if (!ctrl->active) return;
-  const double beta = ctrl->beta;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ncols; g += (int64_t)gridDim.x * blockDim.x) {
-    const int lam = qmap[g];
-    pg[g] = lam >= 0 ? (TF)fma(beta, p[lam], w[lam]) : (TF)0;
-  }
-}
-
-__global__ void __launch_bounds__(kVT) pcg_gather_dot_kernel(const int* c0, const int* c1, int nlam,
-                                                             const double* qi, double* p, const double* w,
-                                                             double* q, double* part, PcgCtrl* ctrl) {
+__global__ void __launch_bounds__(kVT) pcg_gather_dot_kernel(const int4* lc, const int* c0, const int* c1, int nlam,
+                                                             const TF* rowpart, const TF* colpart, double* p,
+                                                             const double* w, double* q, double* qcol, double* part,
+                                                             PcgCtrl* ctrl) {
   __shared__ double red[kVT / 32];
   if (!ctrl->active) return;
   const double beta = ctrl->beta;
   double s = 0.0;
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
-    const int a = c0[l], b = c1[l];
-    double ql = a >= 0 ? qi[a] : 0.0;
-    if (b >= 0) ql += qi[b];
+    const int4 c = lc[l];
+    double f = colsum_at((int64_t)c.x, c.y & 255, c.y >> 8, rowpart, colpart);
+    if (c.z >= 0) f += colsum_at((int64_t)c.z, c.w & 255, c.w >> 8, rowpart, colpart);
+    const double ql = fma(beta, q[l], f);
     const double pl = fma(beta, p[l], w[l]);
-    p[l] = pl;
     q[l] = ql;
+    p[l] = pl;
+    qcol[c0[l]] = ql;
+    const int b = c1[l];
+    if (b >= 0) qcol[b] = ql;
     s = fma(pl, ql, s);
   }
   s = block_sum(s, red);
@@ -103,29 +104,37 @@ __global__ void __launch_bounds__(kVT) pcg_gather_dot_kernel(const int* c0, cons
   }
 }
 
-// c[alpha0 + k] = sum_j G[(qcol + j), k] x[map_j], x = r - delta q (mode 0) or d - q (mode 1);
-// one warp per (subdomain, k)
-__global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const double* r, const double* q,
+// c[alpha0 + k] = sum_j G[(qcol + j), k] x_j with x = the per-column copy of
+// q (mode 0, iteration) or (d - q)[map_j] (mode 1, residual replacement);
+// one warp per (subdomain, k), loads four columns ahead
+__global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const double* xcol, const double* q,
                               const double* d, int mode, double* c, const PcgCtrl* ctrl) {
   if (mode == 0 && !ctrl->active) return;
-  const double delta = ctrl->delta;
   const int lane = threadIdx.x & 31;
   for (int wk = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wk < nsub * 6; wk += gridDim.x * blockDim.x / 32) {
     const int si = wk / 6, k = wk % 6;
     const SubInfo& S = P.sub[si];
     if (k >= S.d) continue;
     double acc = 0.0;
+#pragma unroll 4
     for (int j = lane; j < S.m; j += 32) {
-      const int l = P.qmap[S.qcol + j];
-      const double x = mode == 0 ? fma(-delta, q[l], r[l]) : d[l] - q[l];
-      acc = fma(G6[(S.qcol + j) * 6 + k], x, acc);
+      const int64_t g = S.qcol + j;
+      double x;
+      if (mode == 0) {
+        x = xcol[g];
+      } else {
+        const int l = P.qmap[g];
+        x = d[l] - q[l];
+      }
+      acc = fma(G6[g * 6 + k], x, acc);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) c[S.alpha0 + k] = acc;
   }
 }
 
-// z = A c with A dense D x D row-major; 4 rows per block, 2 warps per row, fixed-order sums
+// mode 1: z = A c;  mode 0 (iteration): z -= delta A c.  A dense D x D
+// row-major; 4 rows per block, 2 warps per row, fixed-order sums
 __global__ void __launch_bounds__(kVT) gemv_rows_kernel(const double* A, const double* c, double* z, int D,
                                                         const PcgCtrl* ctrl, int mode) {
   __shared__ double red[kVT / 32];
@@ -140,17 +149,22 @@ __global__ void __launch_bounds__(kVT) gemv_rows_kernel(const double* A, const d
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) red[warp] = acc;
   __syncthreads();
-  if (threadIdx.x < 4 && blockIdx.x * 4 + threadIdx.x < D)
-    z[blockIdx.x * 4 + threadIdx.x] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+  if (threadIdx.x < 4 && blockIdx.x * 4 + threadIdx.x < D) {
+    const int64_t i = blockIdx.x * 4 + threadIdx.x;
+    const double v = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
+    z[i] = mode == 0 ? fma(-ctrl->delta, v, z[i]) : v;
+  }
 }
 
 // mode 0 (iteration): lambda += delta p, r -= delta q;  mode 1 (refresh): r = d - q;  mode 2 (start): as 1,
-// and the start values nw0 / floor are set.  Then w = r - G z and the dot w.w; the last block finishes.
-__global__ void __launch_bounds__(kVT) pcg_update_kernel(DevPlan P, const int* colsub, const int* c0, const int* c1,
-                                                         int nlam, const double* G6, const double* z,
-                                                         const double* p, const double* q, const double* d,
-                                                         double* lam, double* r, double* w, double* part,
-                                                         int mode, PcgCtrl* ctrl) {
+// and the start values nw0 / floor are set.  Then w = r - G z, the dot w.w and the scatter of w into the
+// tile precision for the next apply (pg at both B columns of the multiplier); the last block finishes.
+// lg[l] = {alpha0, d} of the first and the second subdomain of l (d = 0 if none).
+template <typename TF>
+__global__ void __launch_bounds__(kVT) pcg_update_kernel(const int4* lg, const int* c0, const int* c1, int nlam,
+                                                         const double* G6, const double* z, const double* p,
+                                                         const double* q, const double* d, double* lam, double* r,
+                                                         double* w, TF* pg, double* part, int mode, PcgCtrl* ctrl) {
   __shared__ double red[kVT / 32];
   if (mode == 0 && !ctrl->active) return;
   const double delta = ctrl->delta;
@@ -164,18 +178,17 @@ __global__ void __launch_bounds__(kVT) pcg_update_kernel(DevPlan P, const int* c
       rl = d[l] - q[l];
     }
     r[l] = rl;
+    const int g0 = c0[l], g1 = c1[l];
     double gz = 0.0;
     if (z) {
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int g = e == 0 ? c0[l] : c1[l];
-        if (g < 0) continue;
-        const SubInfo& S = P.sub[colsub[g]];
-        for (int k = 0; k < S.d; ++k) gz = fma(G6[(int64_t)g * 6 + k], z[S.alpha0 + k], gz);
-      }
+      const int4 a = lg[l];
+      for (int k = 0; k < a.y; ++k) gz = fma(G6[(int64_t)g0 * 6 + k], z[a.x + k], gz);
+      for (int k = 0; k < a.w; ++k) gz = fma(G6[(int64_t)g1 * 6 + k], z[a.z + k], gz);
     }
     const double wl = rl - gz;
     w[l] = wl;
+    pg[g0] = (TF)wl;
+    if (g1 >= 0) pg[g1] = (TF)wl;
     s = fma(wl, wl, s);
   }
   s = block_sum(s, red);
@@ -196,8 +209,9 @@ __global__ void __launch_bounds__(kVT) pcg_update_kernel(DevPlan P, const int* c
         ctrl->wy_prev = ctrl->wy;
       } else {
         // the replaced residual takes the place of this iteration's recursive one:
-        // beta divides by the w.w the iteration started from
-        ctrl->beta = ctrl->wy_prev > 0.0 ? wyn / ctrl->wy_prev : 0.0;
+        // beta divides by the w.w the iteration started from, or the search
+        // direction restarts (iterative refinement with inner CG solves)
+        ctrl->beta = ctrl->restart ? 0.0 : (ctrl->wy_prev > 0.0 ? wyn / ctrl->wy_prev : 0.0);
       }
       ctrl->wy = wyn;
       if (mode == 0) ctrl->it += 1;
@@ -231,22 +245,21 @@ inline int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>
 
 int pcg_vector_grid(int n) { return vgrid(n); }
 
-void launch_pcg_scatter(bool fp32, const int* qmap, int64_t ncols, const double* p, const double* w, void* pg,
-                        const PcgCtrl* ctrl, cudaStream_t st) {
-  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + kVT - 1) / kVT, 152 * 8));
-  if (fp32) pcg_scatter_kernel<float><<<g, kVT, 0, st>>>(qmap, ncols, p, w, (float*)pg, ctrl);
-  else pcg_scatter_kernel<double><<<g, kVT, 0, st>>>(qmap, ncols, p, w, (double*)pg, ctrl);
+void launch_pcg_gather_dot(bool fp32, const int4* lc, const int* c0, const int* c1, int nlam, const void* rowpart,
+                           const void* colpart, double* p, const double* w, double* q, double* qcol, double* part,
+                           PcgCtrl* ctrl, cudaStream_t st) {
+  if (fp32)
+    pcg_gather_dot_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(lc, c0, c1, nlam, (const float*)rowpart,
+                                                             (const float*)colpart, p, w, q, qcol, part, ctrl);
+  else
+    pcg_gather_dot_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(lc, c0, c1, nlam, (const double*)rowpart,
+                                                              (const double*)colpart, p, w, q, qcol, part, ctrl);
 }
 
-void launch_pcg_gather_dot(const int* c0, const int* c1, int nlam, const double* qi, double* p, const double* w,
-                           double* q, double* part, PcgCtrl* ctrl, cudaStream_t st) {
-  pcg_gather_dot_kernel<<<vgrid(nlam), kVT, 0, st>>>(c0, c1, nlam, qi, p, w, q, part, ctrl);
-}
-
-void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* r, const double* q, const double* d,
+void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* xcol, const double* q, const double* d,
                    int mode, double* c, const PcgCtrl* ctrl, cudaStream_t st) {
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nsub * 6 * 32 + kVT - 1) / kVT, 152 * 16));
-  pcg_gt_kernel<<<g, kVT, 0, st>>>(P, nsub, G6, r, q, d, mode, c, ctrl);
+  pcg_gt_kernel<<<g, kVT, 0, st>>>(P, nsub, G6, xcol, q, d, mode, c, ctrl);
 }
 
 void launch_gemv_rows(const double* A, const double* c, double* z, int D, const PcgCtrl* ctrl, int mode,
@@ -254,11 +267,15 @@ void launch_gemv_rows(const double* A, const double* c, double* z, int D, const 
   if (D > 0) gemv_rows_kernel<<<(D + 3) / 4, kVT, 0, st>>>(A, c, z, D, ctrl, mode);
 }
 
-void launch_pcg_update(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+void launch_pcg_update(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
                        const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
-                       double* w, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st) {
-  pcg_update_kernel<<<vgrid(nlam), kVT, 0, st>>>(P, colsub, c0, c1, nlam, G6, z, p, q, d, lam, r, w, part, mode,
-                                                 ctrl);
+                       double* w, void* pg, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st) {
+  if (fp32)
+    pcg_update_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z, p, q, d, lam, r, w, (float*)pg,
+                                                          part, mode, ctrl);
+  else
+    pcg_update_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z, p, q, d, lam, r, w, (double*)pg,
+                                                           part, mode, ctrl);
 }
 
 void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st) {

@@ -25,11 +25,17 @@ __device__ __forceinline__ int pop_item_s(int* queue) {
 
 constexpr int kWF = 128;  // largest front handled by one warp (needs w <= 32)
 
-// One warp: forward step of a small supernode (w <= 32, w + r <= kWF).
-// Lane l keeps entry l of the column block in a register; the rows part
-// lives in registers b[q] (rows w + l + 32 q).  Columns of L are read
-// contiguously; pivots are multiplied by their precomputed reciprocals.
-__device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
+// The implicit solves use L in unit-lower form, L = Lu D (D = diag of L),
+// written by unit_scale_kernel after the assembly: the panel holds Lu below
+// the diagonal and zeros on and above it, and d2[j] = 1 / L_jj^2.  Then
+// K_reg^{-1} y = Lu^{-T} D^{-2} Lu^{-1} y: the forward sweep needs no pivot
+// and its own entries are scaled by d2 once, the backward sweep none.
+
+// One warp: forward step of a small supernode (w <= 32, w + r <= kWF).  Lane
+// l keeps the front entries l + 32 q in registers; per column j, z_j comes
+// from lane j and every front row takes its update in one FMA (the zeros of
+// Lu on and above the diagonal leave the rows <= j unchanged).
+__device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int gs, const double* d2,
                                          double* ubuf, double* y, double* v, int lane) {
   const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
   const double* Ls = P.L + S.L + P.Lofs[gs];
@@ -43,49 +49,44 @@ __device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int
     for (int k = lane; k < rc; k += 32) v[rl[k]] += U[k];
     __syncwarp();
   }
-  double a = lane < w ? v[lane] : 0.0;
-  const double di = lane < w ? dinv[c0 + lane] : 0.0;
-  double b[kWF / 32];
+  const int nq = (f_ + 31) / 32;  // warp-uniform
+  double a[kWF / 32];
 #pragma unroll
   for (int q = 0; q < kWF / 32; ++q) {
-    const int i = w + lane + 32 * q;
-    b[q] = i < f_ ? v[i] : 0.0;
+    const int i = lane + 32 * q;
+    a[q] = (q < nq && i < f_) ? v[i] : 0.0;
   }
-  const int nq = (r + 31) / 32;  // warp-uniform
   // columns in groups of 4: the group's loads are issued together, so one
   // global-memory latency is paid per group instead of per column
   constexpr int kU = 4;
   for (int j0 = 0; j0 < w; j0 += kU) {
-    double lt[kU], lb[kU][kWF / 32];
+    double lc[kU][kWF / 32];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int j = j0 + u;
       const double* col = Ls + (int64_t)j * f_;
-      lt[u] = (j < w && lane > j && lane < w) ? col[lane] : 0.0;
 #pragma unroll
       for (int q = 0; q < kWF / 32; ++q) {
-        const int i = w + lane + 32 * q;
-        lb[u][q] = (j < w && q < nq && i < f_) ? col[i] : 0.0;
+        const int i = lane + 32 * q;
+        lc[u][q] = (j < w && q < nq && i < f_) ? col[i] : 0.0;
       }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int j = j0 + u;
       if (j >= w) break;
-      const double zj = __shfl_sync(0xffffffffu, a * di, j);
-      if (lane == j) a = zj;
-      else a -= lt[u] * zj;
+      const double zj = __shfl_sync(0xffffffffu, a[0], j);
 #pragma unroll
       for (int q = 0; q < kWF / 32; ++q)
-        if (q < nq) b[q] -= lb[u][q] * zj;
+        if (q < nq) a[q] = fma(-lc[u][q], zj, a[q]);
     }
   }
-  if (lane < w) y[c0 + lane] = a;
+  if (lane < w) y[c0 + lane] = a[0] * d2[c0 + lane];
   double* Us = ubuf + P.uofs[gs];
 #pragma unroll
   for (int q = 0; q < kWF / 32; ++q) {
     const int i = lane + 32 * q;
-    if (i < r) Us[i] = b[q];
+    if (i >= w && i < f_) Us[i - w] = a[q];
   }
   __syncwarp();
 }
@@ -94,8 +95,8 @@ __device__ __forceinline__ void fwd_warp(const DevPlan& P, const SubInfo& S, int
 // t_l = sum_i L21[i][l] x_rows[i] is split over G = 32 / 2^ceil(log2 w)
 // row groups per column (lane = l + wp g), reduced with shuffles; then lane
 // l owns x_l through the triangular sweep.
-__device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
-                                         double* y, double* v, int lane) {
+__device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int gs, double* y, double* v,
+                                         int lane) {
   const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
   const double* Ls = P.L + S.L + P.Lofs[gs];
   const int* rows = P.rows + P.sn_rows[gs];
@@ -112,7 +113,6 @@ __device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int
   }
   for (int o = wp; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   double x = lane < w ? y[c0 + lane] - t : 0.0;
-  const double di = lane < w ? dinv[c0 + lane] : 0.0;
   for (int j0 = w - 1; j0 >= 0; j0 -= 4) {
     double lr[4];
 #pragma unroll
@@ -124,9 +124,8 @@ __device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int
     for (int u = 0; u < 4; ++u) {
       const int j = j0 - u;
       if (j < 0) break;
-      const double xj = __shfl_sync(0xffffffffu, x * di, j);
-      if (lane == j) x = xj;
-      else x -= lr[u] * xj;
+      const double xj = __shfl_sync(0xffffffffu, x, j);
+      x = fma(-lr[u], xj, x);
     }
   }
   if (lane < w) y[c0 + lane] = x;
@@ -134,12 +133,10 @@ __device__ __forceinline__ void bwd_warp(const DevPlan& P, const SubInfo& S, int
 }
 
 // Whole CTA: forward step of a large supernode on the shared front vector.
-// 32 x 32 diagonal blocks and their reciprocal pivots are staged in shared
-// memory and solved by warp 0; all threads apply the block's columns to the
-// rest of the front.
-__device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
-                                        double* ubuf, double* y, double* sf, double (*sm_blk)[kW + 1],
-                                        double* sm_rd, int tid) {
+// 32 x 32 unit-lower diagonal blocks are staged in shared memory and solved
+// by warp 0; all threads apply the block's columns to the rest of the front.
+__device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int gs, const double* d2,
+                                        double* ubuf, double* y, double* sf, double (*sm_blk)[kW + 1], int tid) {
   const int warp = tid / 32, lane = tid % 32;
   const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
   const double* Ls = P.L + S.L + P.Lofs[gs];
@@ -159,14 +156,12 @@ __device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int 
       const int k = idx / kW, i = idx % kW;  // column k, row i of the block
       if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
     }
-    if (tid < nbk) sm_rd[tid] = dinv[c0 + kb + tid];
     __syncthreads();
     if (warp == 0) {
       double yi = lane < nbk ? sf[kb + lane] : 0.0;
       for (int k = 0; k < nbk; ++k) {
-        const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
-        if (lane == k) yi = yk;
-        else if (lane > k && lane < nbk) yi -= sm_blk[lane][k] * yk;
+        const double yk = __shfl_sync(0xffffffffu, yi, k);
+        yi = fma(-sm_blk[lane][k], yk, yi);  // zero on and above the diagonal
       }
       if (lane < nbk) sf[kb + lane] = yi;
     }
@@ -181,15 +176,15 @@ __device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int 
   }
   double* Us = ubuf + P.uofs[gs];
   for (int i = tid; i < f_; i += kThreads) {
-    if (i < w) y[c0 + i] = sf[i];
+    if (i < w) y[c0 + i] = sf[i] * d2[c0 + i];
     else Us[i - w] = sf[i];
   }
   __syncthreads();
 }
 
 // Whole CTA: backward step of a large supernode (x_rows already final).
-__device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int gs, const double* dinv,
-                                        double* y, double (*sm_blk)[kW + 1], double* sm_rd, int tid) {
+__device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int gs, double* y,
+                                        double (*sm_blk)[kW + 1], int tid) {
   const int warp = tid / 32, lane = tid % 32;
   const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
   const double* Ls = P.L + S.L + P.Lofs[gs];
@@ -215,14 +210,12 @@ __device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int 
       const int k = idx / kW, i = idx % kW;
       if (i < nbk) sm_blk[i][k] = (i >= k) ? Ls[(int64_t)(kb + k) * f_ + kb + i] : 0.0;
     }
-    if (tid < nbk) sm_rd[tid] = dinv[c0 + kb + tid];
     __syncthreads();
     if (warp == 0) {
       double yi = lane < nbk ? y[c0 + kb + lane] : 0.0;
       for (int k = nbk - 1; k >= 0; --k) {
-        const double yk = __shfl_sync(0xffffffffu, yi, k) * sm_rd[k];
-        if (lane == k) yi = yk;
-        else if (lane < k) yi -= sm_blk[k][lane] * yk;
+        const double yk = __shfl_sync(0xffffffffu, yi, k);
+        yi = fma(-sm_blk[k][lane], yk, yi);  // zero on and above the diagonal
       }
       if (lane < nbk) y[c0 + kb + lane] = yi;
     }
@@ -243,7 +236,6 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
                                                              int maxf) {
   extern __shared__ double y[];  // [nmax] subdomain vector, [maxf] front, [8 kWF] warp fronts
   __shared__ double sm_blk[kW][kW + 1];
-  __shared__ double sm_rd[kW];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   double* sfront = y + nmax;
   double* wbuf = sfront + maxf;
@@ -254,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
     const int si = MODE == 3 ? order[0] : order[itx];
     const SubInfo& S = P.sub[si];
     const int n = S.n;
-    const double* dinv = P.dinv + S.dof;
+    const double* d2 = P.dinv + S.dof;  // 1 / L_jj^2 (unit-lower form)
     for (int k = tid; k < n; k += kThreads) y[k] = 0.0;
     __syncthreads();
     if (MODE == 3 && tid == 0) y[P.spos[S.col0 + itx]] = P.qsign[S.qcol + itx];
@@ -287,14 +279,14 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
         const int gs = S.sn0 + lsn[it];
         const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
         if (w > 32 || f_ > kWF) continue;
-        fwd_warp(P, S, gs, dinv, ubuf, y, wbuf + warp * kWF, lane);
+        fwd_warp(P, S, gs, d2, ubuf, y, wbuf + warp * kWF, lane);
       }
       __syncthreads();
       for (int it = lo; it < hi; ++it) {
         const int gs = S.sn0 + lsn[it];
         const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
         if (w <= 32 && f_ <= kWF) continue;
-        fwd_cta(P, S, gs, dinv, ubuf, y, sfront, sm_blk, sm_rd, tid);
+        fwd_cta(P, S, gs, d2, ubuf, y, sfront, sm_blk, tid);
       }
     }
     // backward substitution L^T x = z, level by level from the roots; every
@@ -305,14 +297,14 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
         const int gs = S.sn0 + lsn[it];
         const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
         if (w > 32 || f_ > kWF) continue;
-        bwd_warp(P, S, gs, dinv, y, wbuf + warp * kWF, lane);
+        bwd_warp(P, S, gs, y, wbuf + warp * kWF, lane);
       }
       __syncthreads();
       for (int it = lo; it < hi; ++it) {
         const int gs = S.sn0 + lsn[it];
         const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
         if (w <= 32 && f_ <= kWF) continue;
-        bwd_cta(P, S, gs, dinv, y, sm_blk, sm_rd, tid);
+        bwd_cta(P, S, gs, y, sm_blk, tid);
       }
     }
     __syncthreads();
@@ -329,23 +321,40 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
   }
 }
 
-// dinv[dof + j] = 1 / L_jj for every column of every subdomain (one
-// warp per supernode), so that the triangular solves multiply.
-__global__ void __launch_bounds__(256) diag_recip_kernel(DevPlan P, int nsub, double* dinv) {
+// Unit-lower form of every factor, for the implicit solves (after the TRSM,
+// which uses L itself): column j of each panel is divided by L_jj, the
+// diagonal is set to zero and d2[dof + j] = 1 / L_jj^2.  One CTA per
+// subdomain: the pivots' reciprocals are gathered first (into d2), then every
+// panel is scaled with coalesced accesses, then d2 is squared.
+__global__ void __launch_bounds__(256) unit_scale_kernel(DevPlan P, int nsub, double* d2) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   for (int si = blockIdx.x; si < nsub; si += gridDim.x) {
     const SubInfo& S = P.sub[si];
+    double* inv = d2 + S.dof;
     for (int s = warp; s < S.nsn; s += 8) {
       const int gs = S.sn0 + s;
       const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
       const double* Ls = P.L + S.L + P.Lofs[gs];
-      for (int k = lane; k < w; k += 32) dinv[S.dof + c0 + k] = 1.0 / Ls[(int64_t)k * f_ + k];
+      for (int k = lane; k < w; k += 32) inv[c0 + k] = 1.0 / Ls[(int64_t)k * f_ + k];
     }
+    __syncthreads();
+    for (int s = warp; s < S.nsn; s += 8) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+      double* Ls = P.L + S.L + P.Lofs[gs];
+      const int ne = f_ * w;
+      for (int e = lane; e < ne; e += 32) {
+        const int k = e / f_, i = e - k * f_;
+        if (i > k) Ls[e] *= inv[c0 + k];
+        else if (i == k) Ls[e] = 0.0;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < S.n; j += blockDim.x) inv[j] *= inv[j];
+    __syncthreads();
   }
 }
 
-// g[e] = -scale_e sum_{a,b} dK[a][b] sum_k Y[dofs_b][k] Z[dofs_a][k]
-// (dL/dtheta_e = -<Z^T dK_e Z, W> with Y = Z W); one CTA per element.
 __global__ void __launch_bounds__(256) elem_contract_kernel(const int* edofs, int nelem, int ed, const double* dKref,
                                                             const double* dscale, const double* Z, const double* Y,
                                                             int m, double* g) {
@@ -661,8 +670,8 @@ void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int
   }
 }
 
-void launch_diag_recip(const DevPlan& P, int nsub, double* dinv, cudaStream_t st) {
-  diag_recip_kernel<<<std::min(nsub, 152 * 8), 256, 0, st>>>(P, nsub, dinv);
+void launch_unit_scale(const DevPlan& P, int nsub, double* d2, cudaStream_t st) {
+  unit_scale_kernel<<<std::min(nsub, 152 * 8), 256, 0, st>>>(P, nsub, d2);
 }
 
 int implicit_occupancy(size_t smem) {

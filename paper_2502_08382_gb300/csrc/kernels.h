@@ -22,10 +22,9 @@ void launch_apply(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles,
                   int64_t ncols, const double* p, void* pg, void* rowpart, void* colpart, const int2* blocks,
                   int nblocks, double* qi, const int* c0, const int* c1, int nlam, double* q, int grid, int variant,
                   int* status, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr);
-void launch_apply_core(const DevPlan& P, bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg,
-                       void* rowpart, void* colpart, const int2* blocks, int nblocks, double* qi, int grid,
-                       int variant, const int* active, int* status, cudaStream_t st, cudaEvent_t ev_tiles0 = nullptr,
-                       cudaEvent_t ev_tiles1 = nullptr, bool ev_external = false);
+void launch_apply_core(bool fp32, const TileDesc* desc, int ntiles, const void* F, const void* pg, void* rowpart,
+                       void* colpart, int grid, int variant, const int* active, int* status, cudaStream_t st,
+                       cudaEvent_t ev_tiles0 = nullptr, cudaEvent_t ev_tiles1 = nullptr, bool ev_external = false);
 int apply_variants();
 int apply_max_ctas_per_sm(bool fp32, int variant);
 int apply_warps_per_cta(int variant);
@@ -37,7 +36,7 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
 // FP64 solve side: implicit operator (eq. 11), K_reg solves (eqs. 5, 7),
 // coarse problem and projector (eqs. 6-8), PCPG vectors (Algorithm 1)
 size_t implicit_smem(int nmax, int maxf);
-void launch_diag_recip(const DevPlan& P, int nsub, double* dinv, cudaStream_t st);
+void launch_unit_scale(const DevPlan& P, int nsub, double* d2, cudaStream_t st);
 int implicit_occupancy(size_t smem);
 void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
                      const double* f, double* qi, double* u, double* uws, int64_t ustride, int nmax, int maxf,
@@ -58,17 +57,16 @@ void launch_potrf64(double* A, int lda, int n, double* Dinv, int* status, cudaSt
 void launch_copy2d(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale,
                    cudaStream_t st);
 // projected CG (kern_pcg.cu)
-void launch_pcg_scatter(bool fp32, const int* qmap, int64_t ncols, const double* p, const double* w, void* pg,
-                        const PcgCtrl* ctrl, cudaStream_t st);
-void launch_pcg_gather_dot(const int* c0, const int* c1, int nlam, const double* qi, double* p, const double* w,
-                           double* q, double* part, PcgCtrl* ctrl, cudaStream_t st);
-void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* r, const double* q, const double* d,
+void launch_pcg_gather_dot(bool fp32, const int4* lc, const int* c0, const int* c1, int nlam, const void* rowpart,
+                           const void* colpart, double* p, const double* w, double* q, double* qcol, double* part,
+                           PcgCtrl* ctrl, cudaStream_t st);
+void launch_pcg_gt(const DevPlan& P, int nsub, const double* G6, const double* xcol, const double* q, const double* d,
                    int mode, double* c, const PcgCtrl* ctrl, cudaStream_t st);
 void launch_gemv_rows(const double* A, const double* c, double* z, int D, const PcgCtrl* ctrl, int mode,
                       cudaStream_t st);
-void launch_pcg_update(const DevPlan& P, const int* colsub, const int* c0, const int* c1, int nlam, const double* G6,
+void launch_pcg_update(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
                        const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
-                       double* w, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st);
+                       double* w, void* pg, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st);
 void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st);
 void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st);
 void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,

@@ -17,8 +17,8 @@ constexpr int kTile = 64;  // F tile edge (apply and SYRK)
 // Fronts up to kSmallFront wide whose whole subtree is as small are factored
 // by one warp each in shared memory; fronts up to kMidFront wide by the whole
 // CTA in shared memory; larger ones by the tiled CTA path.
-constexpr int kSmallFront = 46;
-constexpr int kMidFront = 128;
+constexpr int kSmallFront = 40;
+constexpr int kMidFront = 112;
 
 // padded row length of a supernode X block (16-byte aligned rows)
 inline int xpad(int w) { return (w + 3) & ~3; }

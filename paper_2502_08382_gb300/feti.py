@@ -48,7 +48,7 @@ class FetiOptions(C.Structure):
     _fields_ = [("prec", C.c_int), ("refine_every", C.c_int32), ("tol", C.c_double), ("maxit", C.c_int32),
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
-                ("use_coords", C.c_int32), ("refine_drop", C.c_double)]
+                ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -73,7 +73,7 @@ class FetiStats(C.Structure):
 
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
-           "feti_solve", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
+           "feti_solve", "feti_solve_warm", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
            "feti_analyse", "feti_version", "feti_apply_one_static", "feti_set_profiling"]
 
 _lib = None
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.feti_apply.argtypes = [vp, vp, vp]
     lib.feti_apply_implicit.argtypes = [vp, vp, vp]
     lib.feti_solve.argtypes = [vp, vp, vp, vp, C.POINTER(FetiSolveInfo)]
+    lib.feti_solve_warm.argtypes = [vp, vp, vp, vp, C.POINTER(FetiSolveInfo)]
     lib.feti_adjoint.argtypes = [vp, vp, vp]
     lib.feti_get_F.argtypes = [vp, C.c_int32, _f64p]
     lib.feti_get_stats.argtypes = [vp, C.POINTER(FetiStats)]
@@ -210,7 +211,8 @@ class FetiOperator:
     feti_apply / feti_apply_implicit / feti_solve / feti_adjoint)."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
-                 refine_every: int = 0, refine_drop: float = 0.0, leaf_dofs: int = 16, use_coords: bool = True,
+                 refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
+                 leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
         import torch
         self.torch = torch
@@ -227,6 +229,7 @@ class FetiOperator:
         opt.prec = PREC[prec]
         opt.refine_every = refine_every
         opt.refine_drop = refine_drop
+        opt.refine_restart = 1 if refine_restart else 0
         opt.tol = tol
         opt.maxit = maxit
         opt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -289,13 +292,19 @@ class FetiOperator:
         self._check(self.lib.feti_apply_implicit(self.h, C.c_void_p(p.data_ptr()), C.c_void_p(q.data_ptr())))
         return q
 
-    def solve(self):
+    def solve(self, lambda_guess=None):
+        """PCPG solve (feti_solve); with lambda_guess (n_lambda values) it starts
+        from lambda_I + P lambda_guess (feti_solve_warm)."""
         lam = self._dvec(self.n_lambda)
         alpha = self._dvec(max(self.dtot, 1))
         u = self._dvec(self.sum_n)
         info = FetiSolveInfo()
-        rc = self.lib.feti_solve(self.h, C.c_void_p(lam.data_ptr()), C.c_void_p(alpha.data_ptr()),
-                                 C.c_void_p(u.data_ptr()), C.byref(info))
+        fn = self.lib.feti_solve
+        if lambda_guess is not None:
+            lam.copy_(self.torch.as_tensor(lambda_guess, dtype=self.torch.float64).reshape(-1))
+            fn = self.lib.feti_solve_warm
+        rc = fn(self.h, C.c_void_p(lam.data_ptr()), C.c_void_p(alpha.data_ptr()),
+                C.c_void_p(u.data_ptr()), C.byref(info))
         if rc not in (FETI_OK, 4):
             self._check(rc)
         return lam, alpha[:self.dtot], u, dict(iterations=info.iterations, refinements=info.refinements,

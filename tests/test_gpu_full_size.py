@@ -88,7 +88,7 @@ def test_workload2_full_solve_properties(torch_cuda, workload2):
     the FETI equations at full size."""
     from paper_2502_08382_gb300 import feti
     P = workload2
-    op = feti.FetiOperator(P, prec="split_bf16", tol=1e-10, maxit=5000, refine_drop=1e-3)
+    op = feti.FetiOperator(P, prec="split_bf16", tol=1e-10, maxit=5000, refine_drop=1e-3, refine_restart=True)
     op.assemble()
     lam, alpha, u, info = op.solve()
     lam = lam.cpu().numpy()

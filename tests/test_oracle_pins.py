@@ -283,3 +283,32 @@ def test_pcpg_degenerate_initial_guess():
     assert res["iterations"] == 0
     um = O.monolithic_solve(P)
     assert np.abs(res["u"][0] - um[P.subs[0].l2g]).max() <= 1e-12 * np.abs(um).max()
+
+
+def test_pcpg_warm_start(cfg1):
+    """A warm start lambda_I + P lambda_g (Algorithm 2's next step) keeps
+    G^T lambda = e from the first iterate; started from the dual solution it
+    stops at once; a guess in range(G) is removed by the projector, so the
+    iterates are those of the cold start; a guess near the solution converges
+    to the same (unique) lambda and primal solution in fewer iterations."""
+    Fs = [O.local_F(s) for s in cfg1.subs]
+    lam, its, info = O.pcpg(cfg1, Fs, tol=1e-12)
+    e = info["e"]
+    sc = np.linalg.norm(lam)
+    lam0, its0, _ = O.pcpg(cfg1, Fs, tol=1e-12, lam_guess=lam)
+    assert its0 == 0 and np.linalg.norm(lam0 - lam) <= 1e-11 * sc
+    G = info["G"]
+    rng = np.random.default_rng([5, 1])
+    lam_g, its_g, _ = O.pcpg(cfg1, Fs, tol=1e-12, lam_guess=G @ rng.normal(size=G.shape[1]))
+    assert its_g == its and np.linalg.norm(lam_g - lam) <= 1e-10 * sc
+    noise = rng.normal(size=cfg1.n_lambda)
+    guess = lam + 1e-6 * sc * noise / np.linalg.norm(noise)
+    lam_w, its_w, info_w = O.pcpg(cfg1, Fs, tol=1e-12, lam_guess=guess, history=True)
+    for h in info_w["hist"]:
+        assert np.abs(h).max() <= 1e-12 * max(1.0, np.abs(e).max())
+    assert 0 < its_w < its
+    assert np.linalg.norm(lam_w - lam) <= 1e-9 * sc
+    res = O.feti_solve(cfg1, tol=1e-12, lam_guess=guess)
+    um = O.monolithic_solve(cfg1)
+    err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
+    assert err <= 1e-10 * np.abs(um).max()
