@@ -141,15 +141,17 @@ struct __align__(16) TileDesc {
 
 // (F_i p_i)[j] for column j of a subdomain whose tile partials start at tile
 // slot tb (nb blocks): the row partials of the tiles of its block row and the
-// column partials of the tiles of its block column, summed in FP64 in a fixed
-// order (bj = 0..b, then bi = b..nb-1).  The loads are issued eight at a time
-// so that they overlap; the additions keep that order.
+// column partials of the tiles of its block column, summed in a fixed order
+// (bj = 0..b, then bi = b..nb-1) in the precision of the partials (FP64
+// conversion and addition run on a narrow pipe of this GPU; FP32 partials
+// are summed in FP32).  The loads are issued eight at a time so that they
+// overlap; the additions keep that order.
 template <typename TF>
 __device__ __forceinline__ double colsum_at(int64_t tb, int nb, int j, const TF* rowpart, const TF* colpart) {
   const int b = j / kT, x = j % kT;
   const int nt = nb + 1;  // b + 1 row partials, nb - b column partials
   const int64_t r0 = tb + (int64_t)b * (b + 1) / 2;
-  double s = 0.0;
+  TF s = (TF)0;
   for (int k0 = 0; k0 < nt; k0 += 8) {
     TF v[8];
 #pragma unroll
@@ -164,9 +166,9 @@ __device__ __forceinline__ double colsum_at(int64_t tb, int nb, int j, const TF*
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (k0 + u < nt) s += (double)v[u];
+      if (k0 + u < nt) s += v[u];
   }
-  return s;
+  return (double)s;
 }
 
 // colsum_at for sorted column g of subdomain `sub`
