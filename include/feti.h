@@ -119,13 +119,15 @@ typedef struct {
   double t_symbolic_ms;       /* host analysis time in feti_create */
   /* measurement counters since the last feti_set_profiling(ctx, 1) */
   int64_t launches;           /* kernel launches issued by this context */
-  int64_t apply_calls;        /* feti_apply calls */
-  double apply_ms;            /* CUDA-event time of those calls (all their kernels) */
+  int64_t apply_calls;        /* explicit applications: feti_apply calls and PCPG iterations */
+  double apply_ms;            /* CUDA-event time of those applications (feti_apply: scatter, tiles and
+                                 gather; a PCPG iteration: tiles and gather) */
   double apply_tiles_ms;      /* CUDA-event time of their F-streaming kernel only */
   int64_t implicit_calls;     /* implicit-operator applications (feti_apply_implicit and inside feti_solve) */
   double implicit_ms;         /* CUDA-event time of those applications */
   /* autotuner choice for the apply (after the first feti_assemble) */
-  int32_t apply_variant, apply_grid;  /* tile-kernel variant (0: 8-load batches, 1: 16) and grid */
+  int32_t apply_variant, apply_grid;  /* tile-kernel variant (0-2: register batches of 4, 8, 16 loads;
+                                         3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;
