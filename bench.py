@@ -142,10 +142,22 @@ def other_rooflines(st, impl_ms, hbm):
         out["syrk_tc_kernel"] = {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s",
                                  "frac": a / bf16, "peak_kind": f"{bf16_kind} bf16"}
     if impl_ms > 0:
-        a = st["implicit_bytes"] / (impl_ms * 1e-3) / 1e9
-        out["implicit_kernel<0>"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-                                     "fp64_tflops": st["implicit_bytes"] / 4 / (impl_ms * 1e-3) / 1e12}
+        # FP64-pipe bound (ncu: FP64 pipe ~2/3 active, DRAM ~12%): 2 FMAs per factor entry, forward and back
+        a = st["implicit_bytes"] / 4 / (impl_ms * 1e-3) / 1e12
+        g = st["implicit_bytes"] / (impl_ms * 1e-3) / 1e9
+        out["implicit_kernel<0>"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64",
+                                     "factor_gbs": g, "factor_gbs_frac_of_hbm": g / hbm}
     return out
+
+
+# Variant index of the apply autotuner -> kernel name.
+APPLY_KERNELS = ["apply_tiles_kernel<float, 4>", "apply_tiles_kernel<float, 8>", "apply_tiles_kernel<float, 16>",
+                 "apply_ring_kernel<float, 4, 3>", "apply_ring_kernel<float, 8, 3>", "apply_ring_kernel<float, 2, 6>"]
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the apply tile kernels, from ncu captures
+# (--set full) on the workload named; all variants read the same stored F bytes once.
+APPLY_TRAFFIC = {(2, "apply_tiles_kernel"): 138.71e6, (2, "apply_ring_kernel"): 139.66e6}
 
 
 def oracle_sample(P, nsample, reps):
@@ -269,6 +281,8 @@ def main():
     impl_ms = st_["implicit_ms"] / max(st_["implicit_calls"], 1)
     hbm, pk_kind = peaks()
     tiles_gbs = st_["apply_bytes"] / (tiles_ms * 1e-3) / 1e9
+    kname = APPLY_KERNELS[st_["apply_variant"]] if 0 <= st_["apply_variant"] < len(APPLY_KERNELS) else "apply"
+    traffic = APPLY_TRAFFIC.get((args.workload, kname.split("<")[0]))
     value = tiles_gbs * world
 
     # end to end through the C ABI with host buffers: H2D p, feti_apply, D2H q
@@ -343,8 +357,7 @@ def main():
             "implicit_fp64_apply_ms": impl64_ms,
             "break_even_iters": n_star,
             "roofline": {"bound": "hbm", "achieved": tiles_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": tiles_gbs / hbm, "traffic": None, "kernel": "apply_tiles_kernel<float>",
-                         "peak_kind": pk_kind},
+                         "frac": tiles_gbs / hbm, "traffic": traffic, "kernel": kname, "peak_kind": pk_kind},
             "roofline_other": other_rooflines(st_last, impl64_ms, hbm),
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},
