@@ -47,7 +47,7 @@ WORKLOADS = {
 }
 WORKLOAD = WORKLOADS[2]
 PREC = "split_bf16"
-REFINE_DROP = 1e-3   # FP64 residual recomputed whenever ||P r|| has dropped by this factor
+REFINE_DROP = 1e-4   # FP64 residual recomputed whenever ||P r|| has dropped by this factor
 REFINE_RESTART = True  # the search direction restarts after each FP64 residual (refinement with inner CG)
 TOL = 1e-10
 

@@ -793,11 +793,13 @@ feti_status feti_assemble(feti_ctx* ctx) {
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
               ctx->chol_stack,
               ctx->grid_chol, ctx->d_status, st);
-  ctx->stats.launches += 3;  // Cholesky, pruned TRSM (with the unit-lower scaling), SYRK
+  ctx->stats.launches += 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
               ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, st);
+  // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
+  launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, st);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
   if (ctx->fp32) {

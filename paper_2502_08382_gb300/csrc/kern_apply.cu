@@ -44,8 +44,37 @@ struct Vec16<double> {
 
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
-__device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-__device__ __forceinline__ double comp(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+// Per loaded 16-byte chunk v of a tile row: the row-dot part v . pc, and the
+// column partials cacc += v * pr.  FP32 uses the packed two-wide FMA of
+// sm_100+ (half the instructions of the scalar form; the column partials
+// round exactly as scalar FMAs would).
+__device__ __forceinline__ float dot16(const float4& v, const float4& pc) {
+  float2 d = __fmul2_rn(make_float2(v.x, v.y), make_float2(pc.x, pc.y));
+  d = __ffma2_rn(make_float2(v.z, v.w), make_float2(pc.z, pc.w), d);
+  return d.x + d.y;
+}
+__device__ __forceinline__ double dot16(const double2& v, const double2& pc) { return fma(v.y, pc.y, v.x * pc.x); }
+__device__ __forceinline__ void axpy16(const float4& v, float pr, float* cacc) {
+  const float2 pp = make_float2(pr, pr);
+  const float2 c01 = __ffma2_rn(make_float2(v.x, v.y), pp, make_float2(cacc[0], cacc[1]));
+  const float2 c23 = __ffma2_rn(make_float2(v.z, v.w), pp, make_float2(cacc[2], cacc[3]));
+  cacc[0] = c01.x;
+  cacc[1] = c01.y;
+  cacc[2] = c23.x;
+  cacc[3] = c23.y;
+}
+__device__ __forceinline__ void axpy16(const double2& v, double pr, double* cacc) {
+  cacc[0] = fma(v.x, pr, cacc[0]);
+  cacc[1] = fma(v.y, pr, cacc[1]);
+}
+// v with the components at column >= r (right of the diagonal of row r) set to zero
+__device__ __forceinline__ float4 mask_diag(const float4& v, int c0, int r) {
+  return make_float4(c0 < r ? v.x : 0.f, c0 + 1 < r ? v.y : 0.f, c0 + 2 < r ? v.z : 0.f, c0 + 3 < r ? v.w : 0.f);
+}
+__device__ __forceinline__ double2 mask_diag(const double2& v, int c0, int r) {
+  return make_double2(c0 < r ? v.x : 0.0, c0 + 1 < r ? v.y : 0.0);
+}
 
 template <typename TF>
 __global__ void scatter_kernel(const int* qmap, int64_t ncols, const double* p, TF* pg) {
@@ -156,27 +185,21 @@ __device__ __forceinline__ void consume(const Batch<TF, BATCH>& B, TF* cacc, TF*
   if (B.b * ROWS_B < B.rows) {
     TF rs[BATCH];
     if (B.diag) {
+      // the stored chunk of a diagonal row holds zeros right of the diagonal; the column
+      // partials must also leave out the diagonal itself (it is the row partial's)
 #pragma unroll
       for (int i = 0; i < BATCH; ++i) {
         const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
-        TF s = (TF)0;
-#pragma unroll
-        for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
-        rs[i] = s;
         const int r = B.b * ROWS_B + i * RPL + half;
-#pragma unroll
-        for (int e = 0; e < V; ++e) cacc[e] = fma(cq * V + e < r ? comp(B.v[i], e) : (TF)0, pr, cacc[e]);
+        rs[i] = dot16(B.v[i], B.pc);
+        axpy16(mask_diag(B.v[i], cq * V, r), pr, cacc);
       }
     } else {
 #pragma unroll
       for (int i = 0; i < BATCH; ++i) {
         const TF pr = __shfl_sync(0xffffffffu, B.pr, i * RPL + half);
-        TF s = (TF)0;
-#pragma unroll
-        for (int e = 0; e < V; ++e) s = fma(comp(B.v[i], e), comp(B.pc, e), s);
-        rs[i] = s;
-#pragma unroll
-        for (int e = 0; e < V; ++e) cacc[e] = fma(comp(B.v[i], e), pr, cacc[e]);
+        rs[i] = dot16(B.v[i], B.pc);
+        axpy16(B.v[i], pr, cacc);
       }
     }
     ReduceScatter<TF, BATCH, NCH / 2>::run(rs, lane);
@@ -408,12 +431,8 @@ __global__ void __launch_bounds__(W * 32) apply_ring_kernel(const TileDesc* __re
       const int64_t off = diag ? diag_row_off<(int)sizeof(TF)>(r) - e0 : (int64_t)(r - r0) * kT;
       const VT v = ok ? *reinterpret_cast<const VT*>(sf + off + cq * V) : VT{};
       const TF pr = prs[i * RPL + half];
-      TF s2 = (TF)0;
-#pragma unroll
-      for (int e = 0; e < V; ++e) s2 = fma(comp(v, e), comp(pc, e), s2);
-      rs[i] = s2;
-#pragma unroll
-      for (int e = 0; e < V; ++e) cacc[e] = fma((diag && cq * V + e >= r) ? (TF)0 : comp(v, e), pr, cacc[e]);
+      rs[i] = dot16(v, pc);
+      axpy16(diag ? mask_diag(v, cq * V, r) : v, pr, cacc);
     }
     __syncwarp();  // the stage has been read by every lane: it may be refilled
     ++consumed;

@@ -507,37 +507,6 @@ __device__ void solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
   }
 }
 
-// Unit-lower form of the factor of one subdomain, for the implicit solves:
-// column j of each panel is divided by L_jj, the diagonal is set to zero and
-// d2[j] = 1 / L_jj^2.  The whole CTA: the pivots' reciprocals are gathered
-// first (into d2), then every panel is scaled with coalesced accesses, then
-// d2 is squared.
-__device__ void unit_scale_sub(const DevPlan& P, const SubInfo& S, double* d2) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  double* L = P.L + S.L;
-  for (int s = warp; s < S.nsn; s += nw) {
-    const int gs = S.sn0 + s;
-    const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
-    const double* Ls = L + P.Lofs[gs];
-    for (int k = lane; k < w; k += 32) d2[c0 + k] = 1.0 / Ls[(int64_t)k * f_ + k];
-  }
-  __syncthreads();
-  for (int s = warp; s < S.nsn; s += nw) {
-    const int gs = S.sn0 + s;
-    const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
-    double* Ls = L + P.Lofs[gs];
-    const int ne = f_ * w;
-    for (int e = lane; e < ne; e += 32) {
-      const int k = e / f_, i = e - k * f_;
-      if (i > k) Ls[e] *= d2[c0 + k];
-      else if (i == k) Ls[e] = 0.0;
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < S.n; j += blockDim.x) d2[j] *= d2[j];
-  __syncthreads();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          T* X, T* ws, int64_t ws_stride, int64_t front_sz) {
@@ -593,8 +562,6 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
       }
       __syncthreads();
     }
-    // this CTA was the last user of L_i itself: leave it in unit-lower form for the implicit solves
-    unit_scale_sub(P, S, P.dinv + S.dof);
   }
 }
 

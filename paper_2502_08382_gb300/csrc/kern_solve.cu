@@ -26,7 +26,7 @@ __device__ __forceinline__ int pop_item_s(int* queue) {
 constexpr int kWF = 128;  // largest front handled by one warp (needs w <= 32)
 
 // The implicit solves use L in unit-lower form, L = Lu D (D = diag of L),
-// written by the TRSM kernel once it is done with L_i (unit_scale_sub): the panel holds Lu below
+// written by unit_scale_kernel after the assembly: the panel holds Lu below
 // the diagonal and zeros on and above it, and d2[j] = 1 / L_jj^2.  Then
 // K_reg^{-1} y = Lu^{-T} D^{-2} Lu^{-1} y: the forward sweep needs no pivot
 // and its own entries are scaled by d2 once, the backward sweep none.
@@ -317,6 +317,40 @@ __global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const 
       const int col = P.colperm[S.qcol + itx];  // B row of this sorted column
       for (int k = tid; k < n; k += kThreads) u[(int64_t)k * S.m + col] = y[P.iperm[S.diag0 + k]];
     }
+    __syncthreads();
+  }
+}
+
+// Unit-lower form of every factor, for the implicit solves (after the TRSM,
+// which uses L itself): column j of each panel is divided by L_jj, the
+// diagonal is set to zero and d2[dof + j] = 1 / L_jj^2.  One CTA per
+// subdomain: the pivots' reciprocals are gathered first (into d2), then every
+// panel is scaled with coalesced accesses, then d2 is squared.
+__global__ void __launch_bounds__(256) unit_scale_kernel(DevPlan P, int nsub, double* d2) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int si = blockIdx.x; si < nsub; si += gridDim.x) {
+    const SubInfo& S = P.sub[si];
+    double* inv = d2 + S.dof;
+    for (int s = warp; s < S.nsn; s += 8) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+      const double* Ls = P.L + S.L + P.Lofs[gs];
+      for (int k = lane; k < w; k += 32) inv[c0 + k] = 1.0 / Ls[(int64_t)k * f_ + k];
+    }
+    __syncthreads();
+    for (int s = warp; s < S.nsn; s += 8) {
+      const int gs = S.sn0 + s;
+      const int c0 = P.sn_c0[gs], w = P.sn_w[gs], f_ = w + P.sn_r[gs];
+      double* Ls = P.L + S.L + P.Lofs[gs];
+      const int ne = f_ * w;
+      for (int e = lane; e < ne; e += 32) {
+        const int k = e / f_, i = e - k * f_;
+        if (i > k) Ls[e] *= inv[c0 + k];
+        else if (i == k) Ls[e] = 0.0;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < S.n; j += blockDim.x) inv[j] *= inv[j];
     __syncthreads();
   }
 }
@@ -636,7 +670,9 @@ void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int
   }
 }
 
-
+void launch_unit_scale(const DevPlan& P, int nsub, double* d2, cudaStream_t st) {
+  unit_scale_kernel<<<std::min(nsub, 152 * 8), 256, 0, st>>>(P, nsub, d2);
+}
 
 int implicit_occupancy(size_t smem) {
   int nb = 0;

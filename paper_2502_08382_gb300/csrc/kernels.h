@@ -36,6 +36,7 @@ void launch_gather_lambda(const int* c0, const int* c1, int nlam, const double* 
 // FP64 solve side: implicit operator (eq. 11), K_reg solves (eqs. 5, 7),
 // coarse problem and projector (eqs. 6-8), PCPG vectors (Algorithm 1)
 size_t implicit_smem(int nmax, int maxf);
+void launch_unit_scale(const DevPlan& P, int nsub, double* d2, cudaStream_t st);
 int implicit_occupancy(size_t smem);
 void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
                      const double* f, double* qi, double* u, double* uws, int64_t ustride, int nmax, int maxf,

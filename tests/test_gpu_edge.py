@@ -4,6 +4,7 @@
 * a non-floating subdomain (d = 0, no regularisation): K_0 made SPD by a
   reaction term, so F_0 = B K_0^{-1} B^T and the FETI solve must match the
   monolithic solve of the same modified problem;
+* no coarse space at all (every subdomain non-floating, G empty, P = I);
 * apply of the zero vector (exact zeros) and of unit vectors (columns of F);
 * Algorithm 2's multi-step use: new K values with the same pattern, then
   re-assembly;
@@ -93,6 +94,29 @@ def test_non_floating_subdomain(torch_cuda, prec):
     um = O.monolithic_solve(P)
     op.close()
     assert info["converged"], info
+    err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P.subs, us))
+    assert err <= 1e-10 * np.abs(um).max(), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_no_coarse_space(torch_cuda, prec):
+    P = make_problem(dim=2, physics="heat", cuts=[[5, 6]] * 2, material="lognormal", sigma=0.7, seed=3)
+    for i in range(len(P.subs)):
+        P = _non_floating(P, i)
+    assert all(s.d == 0 for s in P.subs)
+    kw = dict(tol=1e-12, maxit=500)
+    if prec != "fp64":
+        kw.update(refine_drop=1e-3, refine_restart=True)
+    op = _op(P, prec=prec, **kw)
+    lam, alpha, u, info = op.solve()
+    ref = O.feti_solve(P, tol=1e-13)
+    um = O.monolithic_solve(P)
+    op.close()
+    assert info["converged"], info
+    assert alpha.numel() == 0
+    sc = np.linalg.norm(ref["lam"])
+    assert np.linalg.norm(lam.cpu().numpy() - ref["lam"]) <= 1e-9 * sc
+    us = _split(P, u.cpu().numpy())
     err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P.subs, us))
     assert err <= 1e-10 * np.abs(um).max(), err
 
