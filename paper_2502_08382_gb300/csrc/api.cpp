@@ -514,9 +514,20 @@ void build(feti_ctx* c) {
         d.flags = bj == b ? kTileDiag : 0;
         d.prow = (int)(I.qcol + (int64_t)b * kT);
         d.pcol = (int)(I.qcol + (int64_t)bj * kT);
+        d.slot = (int)tdesc.size();
         tdesc.push_back(d);
       }
   }
+  // the tile kernels give warp g the descriptors g, g + N, g + 2N, ...: with the largest tiles first, the
+  // k-th tiles of all warps are alike in size and the last round holds the smallest ones (ragged slivers)
+  std::stable_sort(tdesc.begin(), tdesc.end(), [&](const TileDesc& a, const TileDesc& b) {
+    auto bytes = [&](const TileDesc& d) {
+      const int64_t e = (d.flags & kTileDiag) ? (c->fp32 ? diag_row_off<4>(d.rows) : diag_row_off<8>(d.rows))
+                                               : (int64_t)d.rows * kT;
+      return e;
+    };
+    return bytes(a) > bytes(b);
+  });
   c->napply = (int)tdesc.size();
   std::vector<std::pair<double, int2>> sy2;
   for (int i = 0; i < ns; ++i) {

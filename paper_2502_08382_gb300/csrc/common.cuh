@@ -127,8 +127,10 @@ __host__ __device__ inline int64_t F_size_esz(int esz, int nb, int vr) {
   return esz == 4 ? F_size<4>(nb, vr) : F_size<8>(nb, vr);
 }
 
-// One F tile of the explicit apply (host-built, 32 bytes).  Tile t of the
-// descriptor list owns row-partial slot t and column-partial slot t.
+// One F tile of the explicit apply (host-built, 32 bytes).  The tile owns
+// row-partial slot `slot` and column-partial slot `slot` (its position in
+// the subdomain-major tile order); the descriptor list itself may be in any
+// order (largest tiles first, so that the warps' last tiles are small).
 enum : int { kTileDiag = 1 };
 struct __align__(16) TileDesc {
   int64_t f_ofs;   // element offset of the tile in the F storage
@@ -136,7 +138,8 @@ struct __align__(16) TileDesc {
   int flags;       // kTileDiag for a diagonal tile
   int prow;        // pg offset of the tile's row block
   int pcol;        // pg offset of the tile's column block
-  int pad0, pad1;
+  int slot;        // partial slot
+  int pad;
 };
 
 // (F_i p_i)[j] for column j of a subdomain whose tile partials start at tile

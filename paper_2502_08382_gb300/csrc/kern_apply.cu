@@ -149,7 +149,7 @@ struct TileStream {
     }
     const TileDesc& d = dI;
     const bool diag = (d.flags & kTileDiag) != 0;
-    B.t = t;
+    B.t = d.slot;
     B.b = b;
     B.rows = d.rows;
     B.diag = diag;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(W * 32) apply_ring_kernel(const TileDesc* __re
       const int64_t e1 = diag ? diag_row_off<(int)sizeof(TF)>(r1) : (int64_t)r1 * kT;
       const uint32_t bytes = (uint32_t)((e1 - e0) * (int64_t)sizeof(TF));
       uint8_t* st = ring + (size_t)slot * C::STAGE;
-      meta[slot] = make_int4(ic.t, ic.b, d.rows, diag ? 1 : 0);
+      meta[slot] = make_int4(d.slot, ic.b, d.rows, diag ? 1 : 0);
       bar_expect(&bars[slot], bytes + C::PC + C::PR);
       bulk_to_smem(st, F + d.f_ofs + e0, bytes, &bars[slot]);
       bulk_to_smem(st + C::DATA, pg + d.pcol, C::PC, &bars[slot]);
@@ -710,6 +710,7 @@ __global__ void static_setup_kernel(int m, int nb, TF* pg) {
     d.flags = bj == b ? kTileDiag : 0;
     d.prow = b * kT;
     d.pcol = bj * kT;
+    d.slot = t;
     g_static_desc[t] = d;
   }
   for (int b = threadIdx.x; b < nb; b += blockDim.x) g_static_blocks[b] = make_int2(0, b);
