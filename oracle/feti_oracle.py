@@ -170,6 +170,18 @@ def d_vector(problem, Krs=None) -> np.ndarray:
     return d
 
 
+def lumped_M(problem) -> np.ndarray:
+    """Lumped preconditioner M = sum_i B_i K_i B_i^T for Algorithm 1 (the
+    paper leaves M open): each subdomain's stiffness on its B-touched DOFs,
+    signed as B_i, added at its multipliers.  Dense n_lambda x n_lambda."""
+    M = np.zeros((problem.n_lambda, problem.n_lambda))
+    for s in problem.subs:
+        lam = np.asarray(s.B_lambda, dtype=np.int64)
+        Ks = K_dense(s)[np.ix_(s.B_dof, s.B_dof)]
+        np.add.at(M, (lam[:, None], lam[None, :]), s.B_sign[:, None] * s.B_sign[None, :] * Ks)
+    return M
+
+
 class Projector:
     """P = I - G (G^T G)^{-1} G^T (Sec. II)."""
 
@@ -185,8 +197,9 @@ class Projector:
         return x - self.G @ self.coarse_solve(self.G.T @ x)
 
 
-def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=False, lam_guess=None):
-    """Algorithm 1 (PCPG) with M = I and lambda_I = G (G^T G)^{-1} e.
+def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=False, lam_guess=None, M=None):
+    """Algorithm 1 (PCPG) with lambda_I = G (G^T G)^{-1} e and the
+    preconditioner M (a dense matrix; None: M = I), y = P M w.
     Stops when ||w_k|| <= tol * ||w_0||, or when ||w_k|| has reached the
     rounding level of the residual, ||w_k|| <= 64 eps (||d|| + ||F lambda_I||)
     (Algorithm 1 only says "until convergence"; without the floor a problem
@@ -215,7 +228,8 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
         r = d - Fop(lam)
         w = P(r)
     hist = [G.T @ lam - e] if history else None
-    y = P(w)            # y = P M w with M = I
+    Mop = (lambda v: v) if M is None else (lambda v: M @ v)
+    y = P(Mop(w))       # y = P M w
     p = y.copy()
     wy = float(w @ y)
     k = 0
@@ -227,7 +241,7 @@ def pcpg(problem, Fs, tol=1e-10, maxit=5000, G=None, d=None, e=None, history=Fal
         lam = lam + delta * p
         r = r - delta * q
         w = P(r)
-        y = P(w)
+        y = P(Mop(w))
         wy_new = float(w @ y)
         beta = wy_new / wy
         p = y + beta * p
@@ -259,15 +273,16 @@ def primal_solution(problem, lam, alpha, Krs=None):
     return us
 
 
-def feti_solve(problem, tol=1e-10, maxit=5000, lam_guess=None):
+def feti_solve(problem, tol=1e-10, maxit=5000, lam_guess=None, precond=None):
     """Whole FETI solve in FP64: F_i, PCPG (warm-started from lam_guess if
-    given), alpha, u_i."""
+    given; precond "lumped" for M = lumped_M, else M = I), alpha, u_i."""
     Krs = [K_reg(s) for s in problem.subs]
     Fs = [local_F(s, Kr) for s, Kr in zip(problem.subs, Krs)]
     G = G_matrix(problem)
     d = d_vector(problem, Krs)
     e = e_vector(problem)
-    lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e, lam_guess=lam_guess)
+    M = lumped_M(problem) if precond == "lumped" else None
+    lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e, lam_guess=lam_guess, M=M)
     alpha = alpha_from_lambda(problem, Fs, lam, info["P"], d)
     us = primal_solution(problem, lam, alpha, Krs)
     return dict(lam=lam, alpha=alpha, u=us, iterations=its, Fs=Fs, G=G, d=d, e=e)

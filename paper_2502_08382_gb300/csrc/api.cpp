@@ -807,8 +807,12 @@ feti_status feti_assemble(feti_ctx* ctx) {
   ctx->stats.launches += 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
-  launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
-              ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, st);
+  {
+    // mixed precision: the TRSM panel updates run on the tensor cores in the SYRK's format
+    const int tcmode = !ctx->fp32 ? 0 : (ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 2 : 1);
+    launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
+                ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, tcmode, ctx->d_status, st);
+  }
   // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
   launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, st);
   CK(cudaGetLastError());

@@ -11,7 +11,7 @@ void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, doubl
                  int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st);
 int chol_ctas_per_sm();
 void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
-                 int64_t ws_stride, int64_t front_sz, int grid, cudaStream_t st);
+                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int* status, cudaStream_t st);
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
                     int split, int* status, cudaStream_t st);
 size_t syrk_tc_smem(int split);

@@ -84,7 +84,7 @@ def test_non_floating_subdomain(torch_cuda, prec):
                                    seed=3), 2)
     assert P.subs[2].d == 0
     op = _op(P, prec=prec, tol=1e-12, maxit=500, refine_every=5 if prec != "fp64" else 0)
-    tol = 1e-12 if prec == "fp64" else 4e-3
+    tol = 1e-12 if prec == "fp64" else 1e-2  # TF32 TRSM and SYRK: ten TF32 roundoffs
     for i, s in enumerate(P.subs):
         Fo = O.local_F(s)
         assert np.linalg.norm(op.get_F(i) - Fo) <= tol * np.linalg.norm(Fo), i

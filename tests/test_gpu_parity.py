@@ -71,11 +71,13 @@ def test_apply_fp64_matches_oracle(torch_cuda, name):
     op.close()
 
 
-# Mixed precision: FP32 pruned TRSM + tensor-core SYRK, F_i stored as FP32 tiles.
-# Tolerances follow the operand precision of the SYRK: TF32 keeps 10 mantissa
-# bits (the tensor core drops the low 13 bits of each FP32 operand), split
-# bf16 keeps about 16 (hi*hi + hi*lo + lo*hi, the lo*lo term ~2^-16 dropped).
-MIXED_TOL = {"tf32": 4e-3, "split_bf16": 1e-4}
+# Mixed precision: pruned TRSM with tensor-core panel updates + tensor-core SYRK,
+# F_i stored as FP32 tiles.  Tolerances follow the operand precision on the
+# tensor cores: TF32 keeps 10 mantissa bits (unit roundoff 2^-11 = 4.9e-4;
+# with the TRSM panel updates and the SYRK both in TF32, an F_i error of about
+# ten roundoffs), split bf16 keeps about 16 (hi*hi + hi*lo + lo*hi, the lo*lo
+# term ~2^-16 dropped).
+MIXED_TOL = {"tf32": 1e-2, "split_bf16": 1e-4}
 
 
 @pytest.mark.parametrize("prec", ["tf32", "split_bf16"])

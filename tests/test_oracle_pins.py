@@ -312,3 +312,39 @@ def test_pcpg_warm_start(cfg1):
     um = O.monolithic_solve(cfg1)
     err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
     assert err <= 1e-10 * np.abs(um).max()
+
+
+def _global_B_and_K(problem):
+    """Global B (n_lambda x sum n_i) and block-diagonal K, assembled densely."""
+    ntot = sum(s.n for s in problem.subs)
+    B = np.zeros((problem.n_lambda, ntot))
+    K = np.zeros((ntot, ntot))
+    off = 0
+    for s in problem.subs:
+        lam = np.asarray(s.B_lambda, dtype=np.int64)
+        np.add.at(B, (lam, off + np.asarray(s.B_dof)), s.B_sign)
+        K[off:off + s.n, off:off + s.n] = O.K_dense(s)
+        off += s.n
+    return B, K
+
+
+def test_lumped_preconditioner(cfg1):
+    """M = sum_i B_i K_i B_i^T equals the global product B K B^T (block-diagonal
+    K, dense B), is symmetric positive semidefinite, and the preconditioned
+    PCPG reaches the same dual solution (unique: B has full row rank) and the
+    monolithic primal solution, keeping G^T lambda_k = e."""
+    M = O.lumped_M(cfg1)
+    B, K = _global_B_and_K(cfg1)
+    assert np.abs(M - B @ K @ B.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.abs(M - M.T).max() == 0.0
+    assert np.linalg.eigvalsh(M).min() >= -1e-10 * np.abs(M).max()
+    Fs = [O.local_F(s) for s in cfg1.subs]
+    lam0, its0, _ = O.pcpg(cfg1, Fs, tol=1e-12)
+    lam1, its1, info = O.pcpg(cfg1, Fs, tol=1e-12, M=M, history=True)
+    for h in info["hist"]:
+        assert np.abs(h).max() <= 1e-12 * max(1.0, np.abs(info["e"]).max())
+    assert np.linalg.norm(lam1 - lam0) <= 1e-9 * np.linalg.norm(lam0)
+    res = O.feti_solve(cfg1, tol=1e-12, precond="lumped")
+    um = O.monolithic_solve(cfg1)
+    err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
+    assert err <= 1e-10 * np.abs(um).max()
