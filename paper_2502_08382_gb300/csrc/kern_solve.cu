@@ -230,7 +230,7 @@ __device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int 
 //         sorted columns; `nsub` is the column count, order[0] the subdomain);
 //         written to u as Z[dof * m + B-row of column j] (original DOF order)
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 3) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
+__global__ void __launch_bounds__(kThreads, 4) implicit_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                              const double* p, const double* f, double* qi,
                                                              double* u, double* uws, int64_t ustride, int nmax,
                                                              int maxf) {
