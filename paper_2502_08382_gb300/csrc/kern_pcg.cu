@@ -243,8 +243,6 @@ inline int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>
 
 }  // namespace
 
-int pcg_vector_grid(int n) { return vgrid(n); }
-
 void launch_pcg_gather_dot(bool fp32, const int4* lc, const int* c0, const int* c1, int nlam, const void* rowpart,
                            const void* colpart, double* p, const double* w, double* q, double* qcol, double* part,
                            PcgCtrl* ctrl, cudaStream_t st) {
