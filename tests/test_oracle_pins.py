@@ -348,3 +348,41 @@ def test_lumped_preconditioner(cfg1):
     um = O.monolithic_solve(cfg1)
     err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
     assert err <= 1e-10 * np.abs(um).max()
+
+
+def test_q_recurrence_reading(cfg1):
+    """Reading C20: the CUDA path carries q_k = F p_k as F w_k + beta q_{k-1} and
+    z_k = (G^T G)^{-1} G^T r_k as z_k - delta (G^T G)^{-1} G^T q_k.  Written out
+    here in FP64 (test code, not the oracle), its iterates follow the oracle's
+    literal Algorithm 1 (M = I) to rounding and stop at the same iteration."""
+    Fs = [O.local_F(s) for s in cfg1.subs]
+    lam_ref, its_ref, info = O.pcpg(cfg1, Fs, tol=1e-10)
+    G, d, e, P = info["G"], info["d"], info["e"], info["P"]
+    F = lambda v: O.apply_F(cfg1, Fs, v)
+    lam = G @ P.coarse_solve(e)
+    Flam = F(lam)
+    r = d - Flam
+    floor = 64.0 * np.finfo(np.float64).eps * (np.linalg.norm(d) + np.linalg.norm(Flam))
+    z = P.coarse_solve(G.T @ r)
+    w = r - G @ z
+    nw0 = np.linalg.norm(w)
+    p = np.zeros_like(w)
+    q = np.zeros_like(w)
+    wy, beta, k = float(w @ w), 0.0, 0
+    while k < 5000:
+        f = F(w)                       # the apply streams F against w_k
+        q = f + beta * q               # q_k = F p_k
+        p = w + beta * p
+        delta = wy / float(p @ q)
+        lam = lam + delta * p
+        r = r - delta * q
+        z = z - delta * P.coarse_solve(G.T @ q)
+        w = r - G @ z
+        wy_new = float(w @ w)
+        beta, wy = wy_new / wy, wy_new
+        k += 1
+        if np.sqrt(wy) <= max(1e-10 * nw0, floor):
+            break
+    assert k == its_ref
+    assert np.linalg.norm(lam - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
+    assert np.linalg.norm(G.T @ lam - e) <= 1e-12 * max(1.0, np.linalg.norm(e))
