@@ -17,7 +17,10 @@ dense NumPy/SciPy with no blocking or reordering beyond the definition:
   dual data       G = B R, e = R^T f, d = B K^+ f - c         (eqs. 6-7)
   FETI residuals  K_i u_i + B_i^T lambda - f_i and B u - c     (eq. 3)
   projector       P = I - G (G^T G)^{-1} G^T                  (Sec. II)
-  PCPG            Algorithm 1 with M = I, lambda_I = G (G^T G)^{-1} e
+  PCPG            Algorithm 1, lambda_I = G (G^T G)^{-1} e, M = I or a given
+                  matrix (the lumped M = sum_i B_i K_i B_i^T is provided; the
+                  paper leaves M open), optionally warm-started from
+                  lambda_I + P lambda_g (Algorithm 2's next step)
   recovery        alpha (eq. 8), u = K^+ (f - B^T lambda) + R alpha (eq. 5)
   monolithic      K~ u~ = f~ with Dirichlet DOFs eliminated     (eq. 1)
   sensitivity     dL/dtheta_e = -<Z^T dK_e Z, W>, Z = K_reg^{-1} B^T
