@@ -18,8 +18,9 @@ dense NumPy/SciPy with no blocking or reordering beyond the definition:
   FETI residuals  K_i u_i + B_i^T lambda - f_i and B u - c     (eq. 3)
   projector       P = I - G (G^T G)^{-1} G^T                  (Sec. II)
   PCPG            Algorithm 1, lambda_I = G (G^T G)^{-1} e, M = I or a given
-                  matrix (the lumped M = sum_i B_i K_i B_i^T is provided; the
-                  paper leaves M open), optionally warm-started from
+                  matrix (the lumped M = sum_i B_i K_i B_i^T, and its B B^T
+                  scaled form, are provided; the paper leaves M open),
+                  optionally warm-started from
                   lambda_I + P lambda_g (Algorithm 2's next step)
   recovery        alpha (eq. 8), u = K^+ (f - B^T lambda) + R alpha (eq. 5)
   monolithic      K~ u~ = f~ with Dirichlet DOFs eliminated     (eq. 1)
@@ -185,6 +186,26 @@ def lumped_M(problem) -> np.ndarray:
     return M
 
 
+def BBt(problem) -> np.ndarray:
+    """B B^T (dense n_lambda x n_lambda): multipliers a, b couple when a
+    subdomain has rows for both on the same DOF (signs multiplied)."""
+    out = np.zeros((problem.n_lambda, problem.n_lambda))
+    for s in problem.subs:
+        lam = np.asarray(s.B_lambda, dtype=np.int64)
+        same = (np.asarray(s.B_dof)[:, None] == np.asarray(s.B_dof)[None, :]).astype(np.float64)
+        np.add.at(out, (lam[:, None], lam[None, :]), s.B_sign[:, None] * s.B_sign[None, :] * same)
+    return out
+
+
+def scaled_lumped_M(problem) -> np.ndarray:
+    """Lumped preconditioner with the B B^T scaling of the multipliers,
+    M = (B B^T)^{-1} (sum_i B_i K_i B_i^T) (B B^T)^{-1}: for gluing rows
+    between two subdomains it halves each side, for chained rows at cross
+    points it distributes them consistently, for Dirichlet rows it keeps 1."""
+    W = np.linalg.inv(BBt(problem))
+    return W @ lumped_M(problem) @ W
+
+
 class Projector:
     """P = I - G (G^T G)^{-1} G^T (Sec. II)."""
 
@@ -278,13 +299,13 @@ def primal_solution(problem, lam, alpha, Krs=None):
 
 def feti_solve(problem, tol=1e-10, maxit=5000, lam_guess=None, precond=None):
     """Whole FETI solve in FP64: F_i, PCPG (warm-started from lam_guess if
-    given; precond "lumped" for M = lumped_M, else M = I), alpha, u_i."""
+    given; precond "lumped" for M = scaled_lumped_M, else M = I), alpha, u_i."""
     Krs = [K_reg(s) for s in problem.subs]
     Fs = [local_F(s, Kr) for s, Kr in zip(problem.subs, Krs)]
     G = G_matrix(problem)
     d = d_vector(problem, Krs)
     e = e_vector(problem)
-    M = lumped_M(problem) if precond == "lumped" else None
+    M = scaled_lumped_M(problem) if precond == "lumped" else None
     lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e, lam_guess=lam_guess, M=M)
     alpha = alpha_from_lambda(problem, Fs, lam, info["P"], d)
     us = primal_solution(problem, lam, alpha, Krs)

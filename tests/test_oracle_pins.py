@@ -386,3 +386,36 @@ def test_q_recurrence_reading(cfg1):
     assert k == its_ref
     assert np.linalg.norm(lam - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
     assert np.linalg.norm(G.T @ lam - e) <= 1e-12 * max(1.0, np.linalg.norm(e))
+
+
+def test_scaled_lumped_preconditioner(tiny_el, cfg1):
+    """B B^T from the subdomain rows equals the global dense product; on
+    gluing-only multipliers it is 2 I; the scaled lumped M is symmetric PSD
+    and equals the global W B K B^T W; the preconditioned PCPG reaches the
+    same dual and primal solution in fewer iterations than M = I (workload 1:
+    57 -> 31; 3D elasticity: 363 -> 58 at tol 1e-10)."""
+    for P in (cfg1, tiny_el):
+        B, K = _global_B_and_K(P)
+        BB = O.BBt(P)
+        assert np.abs(BB - B @ B.T).max() == 0.0
+        W = np.linalg.inv(B @ B.T)
+        M = O.scaled_lumped_M(P)
+        assert np.abs(M - W @ B @ K @ B.T @ W).max() <= 1e-12 * np.abs(M).max()
+        assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+        assert np.linalg.eigvalsh((M + M.T) / 2).min() >= -1e-10 * np.abs(M).max()
+        Fs = [O.local_F(s) for s in P.subs]
+        lam0, its0, _ = O.pcpg(P, Fs, tol=1e-10)
+        lam1, its1, _ = O.pcpg(P, Fs, tol=1e-10, M=M)
+        assert its1 < its0, (its0, its1)
+        assert np.linalg.norm(lam1 - lam0) <= 1e-8 * np.linalg.norm(lam0)
+    owners = np.zeros(cfg1.n_lambda, dtype=int)
+    for s in cfg1.subs:
+        np.add.at(owners, np.asarray(s.B_lambda), 1)
+    BB = O.BBt(cfg1)
+    two = np.flatnonzero(owners == 2)
+    # a gluing multiplier between two subdomains only: B B^T row = 2 on the diagonal
+    assert np.all(np.diag(BB)[two] == 2.0)
+    res = O.feti_solve(cfg1, tol=1e-12, precond="lumped")
+    um = O.monolithic_solve(cfg1)
+    err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
+    assert err <= 1e-10 * np.abs(um).max()
