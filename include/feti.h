@@ -96,6 +96,9 @@ typedef struct {
                                  factor since the last recomputation (0 = off) */
   int32_t refine_restart;     /* PCPG: 1 = restart the search direction after each recomputation
                                  (iterative refinement with inner CG solves); 0 = keep it */
+  int32_t precond;            /* PCPG preconditioner M of Algorithm 1 (the paper leaves it open):
+                                 0 = none (M = I); 1 = lumped, M = W (sum_i B_i K_i B_i^T) W with
+                                 W = (B B^T)^{-1}, rebuilt from K at every feti_assemble */
 } feti_options;
 
 typedef struct {
@@ -155,7 +158,8 @@ feti_status feti_apply(feti_ctx* ctx, const double* p_dev, double* q_dev);
 /* Implicit application q = sum_i B_i L_i^{-T} L_i^{-1} B_i^T p (eq. 11) in FP64. */
 feti_status feti_apply_implicit(feti_ctx* ctx, const double* p_dev, double* q_dev);
 
-/* Projected PCPG (Algorithm 1, M = I) for the dual problem (eq. 7), then
+/* Projected PCPG (Algorithm 1; M = I, or the lumped preconditioner of options.precond) for the
+ * dual problem (eq. 7), then
  * alpha (eq. 8) and u (eq. 5).  lambda_dev [n_lambda], alpha_dev [sum d_i],
  * u_dev [sum n_i] (subdomains concatenated in order); any may be NULL except
  * lambda_dev.  The iteration runs on the device with the explicit F_i; the

@@ -13,6 +13,7 @@
 #include <unordered_map>
 
 #include "context.h"
+#include "precond.h"
 #include "kernels.h"
 
 using namespace feti;
@@ -650,6 +651,21 @@ void build(feti_ctx* c) {
   c->d_c0 = upload(c, c0);
   c->d_c1 = upload(c, c1);
   c->d_lamcol = upload(c, lamcol);
+  if (c->opt.precond == 1) {
+    LumpedPlan lp;
+    plan_lumped(c, lp);
+    c->precond = true;
+    c->d_w_off = upload(c, lp.w_off);
+    c->d_w_col = upload(c, lp.w_col);
+    c->d_w_val = upload(c, lp.w_val);
+    c->d_m_off = upload(c, lp.m_off);
+    c->d_m_col = upload(c, lp.m_col);
+    c->m_nnz = (int64_t)lp.m_col.size();
+    c->d_m_val = (double*)dalloc(c, (size_t)std::max<int64_t>(c->m_nnz, 1) * 8);
+    c->d_mc_off = upload(c, lp.c_off);
+    c->d_mc_kidx = upload(c, lp.c_kidx);
+    c->d_mc_sign = upload(c, lp.c_sign);
+  }
   c->d_lamg = upload(c, lamg);
   c->d_qcol = (double*)dalloc(c, (size_t)qo * 8);
   c->d_queue = (int*)dalloc(c, 64 * sizeof(int));
@@ -688,8 +704,8 @@ void build(feti_ctx* c) {
     c->d_Dinv = (double*)dalloc(c, (size_t)nblk * kT * kT * 8);
     c->d_Tp = (double*)dalloc(c, (size_t)D2 * kT * 8);
     c->d_Tb = (double*)dalloc(c, (size_t)D2 * kT * 8);
-    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 9 * 8);
-    c->d_cv = (double*)dalloc(c, (size_t)D2 * 5 * 8);
+    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 11 * 8);
+    c->d_cv = (double*)dalloc(c, (size_t)D2 * 7 * 8);
     c->d_sc = (double*)dalloc(c, 16 * 8);
     c->d_part = (double*)dalloc(c, 2 * kPcgMaxBlocks * 8);
     CK(cudaMallocHost((void**)&c->h_sc, 16 * 8));
@@ -747,6 +763,7 @@ feti_status feti_create(const feti_problem* prob, const feti_options* opt, feti_
     ctx->opt.use_coords = 1;
   }
   if (ctx->opt.prec < FETI_PREC_FP64 || ctx->opt.prec > FETI_PREC_SPLIT_BF16) throw ArgError("bad precision");
+  if (ctx->opt.precond < 0 || ctx->opt.precond > 1) throw ArgError("bad preconditioner (0 none, 1 lumped)");
   ctx->st = (cudaStream_t)ctx->opt.stream;
   ctx->fp32 = ctx->opt.prec != FETI_PREC_FP64;
   ctx->nsub = prob->nsub;
@@ -800,6 +817,11 @@ feti_status feti_assemble(feti_ctx* ctx) {
     throw CudaError("internal: a work list of the assembly or apply is missing");
   CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  if (ctx->precond) {
+    // the lumped preconditioner's values from the current K (they change with feti_update_values)
+    launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val, st);
+    ctx->stats.launches += 1;
+  }
   CK(cudaEventRecord(ctx->ev[0], st));
   launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
               ctx->chol_stack,

@@ -26,10 +26,11 @@ struct CudaErr : std::runtime_error {
   } while (0)
 
 // vectors inside ctx->d_vec (each n_lambda long)
-// V_Q: scratch of the FP64 implicit operator; V_QK: q_k = F p_k of the iteration
-enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM, V_QK };
+// V_Q: scratch of the FP64 implicit operator; V_QK: q_k = F p_k of the iteration;
+// V_Y = P M w and V_V = M w with the lumped preconditioner
+enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM, V_QK, V_Y, V_V };
 // coarse vectors in ctx->d_cv (each D long)
-enum { C_E = 0, C_C, C_Z, C_A, C_GQ };
+enum { C_E = 0, C_C, C_Z, C_A, C_GQ, C_C2, C_Z2 };
 
 double* vec(feti_ctx* c, int k) { return c->d_vec + (size_t)k * c->nlam; }
 double* cvec(feti_ctx* c, int k) { return c->d_cv + (size_t)k * std::max(c->dtot, 1); }
@@ -105,19 +106,38 @@ const PcgCtrl& read_ctrl(feti_ctx* c) {
   return *c->h_ctrl;
 }
 
-// One PCPG iteration (Algorithm 1, M = I) on the device, six launches; every
-// kernel returns at once if the control block says the iteration has stopped.
-// ev (4 events or null): before the scatter, around the F-streaming kernel, after the gather.
+// y = P M w with the lumped preconditioner, the scatter of y and the dot w.y
+// (mode 0: in an iteration; 1 / 2: after a residual replacement / at the start).
+void enqueue_precond(feti_ctx* c, int mode, cudaStream_t st) {
+  const int n = c->nlam, D = c->dtot;
+  PcgCtrl* ctrl = ctrl_dev(c);
+  double *w = vec(c, V_W), *y = vec(c, V_Y), *v = vec(c, V_V);
+  launch_lumped_apply(n, c->d_w_off, c->d_w_col, c->d_w_val, c->d_m_off, c->d_m_col, c->d_m_val, w, v, ctrl,
+                      mode == 0 ? 1 : 0, st);
+  if (D > 0) {
+    launch_pcg_gt(c->P, c->nsub, c->d_G6, nullptr, v, nullptr, mode == 0 ? 2 : 3, cvec(c, C_C2), ctrl, st);
+    launch_gemv_rows(c->d_Ainv, cvec(c, C_C2), cvec(c, C_Z2), D, ctrl, mode == 0 ? 2 : 1, st);
+  }
+  launch_pcg_proj(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z2) : nullptr, v, w, y, c->d_pg,
+                  c->d_part, mode, ctrl, st);
+}
+
+// One PCPG iteration (Algorithm 1) on the device: five launches with M = I,
+// nine with the lumped preconditioner; every kernel returns at once if the
+// control block says the iteration has stopped.
+// ev (4 events or null): before the tile kernel, around it, after the gather.
 void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStream_t st, bool capture) {
   const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   const int n = c->nlam, D = c->dtot;
+  const int pre = c->precond ? 1 : 0;
   double *d = vec(c, V_D), *r = vec(c, V_R), *w = vec(c, V_W), *p = vec(c, V_P), *qk = vec(c, V_QK);
+  double* y = pre ? vec(c, V_Y) : w;  // p_k = y_k + beta p_{k-1}, the apply streams F against y
   PcgCtrl* ctrl = ctrl_dev(c);
   const auto& cand = c->apply_cands[c->apply_pick];
   if (ev) CKS(cudaEventRecordWithFlags(ev[0], st, evf));
   launch_apply_core(c->fp32, c->d_tdesc, c->napply, c->d_F, c->d_pg, c->d_rowpart, c->d_tpart, cand.grid,
                     cand.variant, active_dev(c), c->d_status, st, ev ? ev[1] : nullptr, ev ? ev[2] : nullptr, capture);
-  launch_pcg_gather_dot(c->fp32, c->d_lamcol, c->d_c0, c->d_c1, n, c->d_rowpart, c->d_tpart, p, w, qk, c->d_qcol,
+  launch_pcg_gather_dot(c->fp32, c->d_lamcol, c->d_c0, c->d_c1, n, c->d_rowpart, c->d_tpart, p, y, qk, c->d_qcol,
                         c->d_part, ctrl, st);
   if (ev) CKS(cudaEventRecordWithFlags(ev[3], st, evf));
   if (D > 0) {
@@ -125,10 +145,13 @@ void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStre
     launch_gemv_rows(c->d_Ainv, cvec(c, C_GQ), cvec(c, C_Z), D, ctrl, 0, st);
   }
   launch_pcg_update(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, qk, d, lam, r,
-                    w, c->d_pg, c->d_part + kPcgMaxBlocks, 0, ctrl, st);
+                    w, c->d_pg, c->d_part + kPcgMaxBlocks, 0, pre, ctrl, st);
+  if (pre) enqueue_precond(c, 0, st);
 }
 
-int iteration_launches(feti_ctx* c) { return c->dtot > 0 ? 5 : 3; }
+int iteration_launches(feti_ctx* c) {
+  return (c->dtot > 0 ? 5 : 3) + (c->precond ? (c->dtot > 0 ? 4 : 2) : 0);
+}
 
 // Capture `chunk` iterations on the private stream into one CUDA graph (once
 // per context and chunk size); replaying it enqueues the whole chunk at once.
@@ -170,8 +193,9 @@ void enqueue_refresh(feti_ctx* c, double* lam, int mode) {
     launch_gemv_rows(c->d_Ainv, cvec(c, C_C), cvec(c, C_Z), D, ctrl, 1, st);
   }
   launch_pcg_update(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam, r,
-                    w, c->d_pg, c->d_part + kPcgMaxBlocks, mode, ctrl, st);
-  c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0);
+                    w, c->d_pg, c->d_part + kPcgMaxBlocks, mode, c->precond ? 1 : 0, ctrl, st);
+  if (c->precond) enqueue_precond(c, mode, st);
+  c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0) + (c->precond ? (D > 0 ? 4 : 2) : 0);
 }
 
 }  // namespace

@@ -202,8 +202,7 @@ struct PcgCtrl {
   int conv;       // the last ||w|| met the stopping rule
   int breakdown;  // p.q <= 0 was met
   int restart;    // 1: a residual replacement restarts the search direction (beta = 0)
-  int cnt_dot, cnt_upd;  // arrival counters of the last-block reductions
-  int pad;
+  int cnt_dot, cnt_upd, cnt_proj;  // arrival counters of the last-block reductions
 };
 constexpr int kPcgMaxBlocks = 1184;  // block partials per reduction
 

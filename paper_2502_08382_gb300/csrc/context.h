@@ -109,8 +109,20 @@ struct feti_ctx {
   int4* d_lamg = nullptr;      // per multiplier: alpha0 and d of its subdomains (PCPG update)
   double* d_qcol = nullptr;    // per B column: q of its multiplier (PCPG G^T q)
   int m_max = 0;               // widest subdomain (B rows)
-  double* d_vec = nullptr;     // PCPG vectors (9 x n_lambda)
-  double* d_cv = nullptr;      // coarse vectors (5 x D)
+  // lumped preconditioner M = W M_core W (options.precond = 1), see precond.cpp
+  bool precond = false;
+  int* d_w_off = nullptr;
+  int* d_w_col = nullptr;
+  double* d_w_val = nullptr;
+  int* d_m_off = nullptr;
+  int* d_m_col = nullptr;
+  double* d_m_val = nullptr;
+  int64_t* d_mc_off = nullptr;
+  int64_t* d_mc_kidx = nullptr;
+  double* d_mc_sign = nullptr;
+  int64_t m_nnz = 0;
+  double* d_vec = nullptr;     // PCPG vectors (11 x n_lambda)
+  double* d_cv = nullptr;      // coarse vectors (7 x D)
   double* d_sc = nullptr;      // scalars
   double* d_part = nullptr;    // block partials of the PCPG reductions (2 x kPcgMaxBlocks)
   double* h_sc = nullptr;      // pinned host scalars

@@ -105,11 +105,13 @@ __global__ void __launch_bounds__(kVT) pcg_gather_dot_kernel(const int4* lc, con
 }
 
 // c[alpha0 + k] = sum_j G[(qcol + j), k] x_j with x = the per-column copy of
-// q (mode 0, iteration) or (d - q)[map_j] (mode 1, residual replacement);
-// one warp per (subdomain, k), loads four columns ahead
+// q (mode 0, iteration), (d - q)[map_j] (mode 1, residual replacement) or
+// q[map_j] (mode 2 in an iteration, mode 3 in a replacement; the
+// preconditioned vector); modes 0 and 2 return at once when the iteration has
+// stopped.  One warp per (subdomain, k), loads four columns ahead.
 __global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const double* xcol, const double* q,
                               const double* d, int mode, double* c, const PcgCtrl* ctrl) {
-  if (mode == 0 && !ctrl->active) return;
+  if ((mode == 0 || mode == 2) && !ctrl->active) return;
   const int lane = threadIdx.x & 31;
   for (int wk = (blockIdx.x * blockDim.x + threadIdx.x) / 32; wk < nsub * 6; wk += gridDim.x * blockDim.x / 32) {
     const int si = wk / 6, k = wk % 6;
@@ -124,7 +126,7 @@ __global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const doubl
         x = xcol[g];
       } else {
         const int l = P.qmap[g];
-        x = d[l] - q[l];
+        x = mode == 1 ? d[l] - q[l] : q[l];
       }
       acc = fma(G6[g * 6 + k], x, acc);
     }
@@ -133,12 +135,13 @@ __global__ void pcg_gt_kernel(DevPlan P, int nsub, const double* G6, const doubl
   }
 }
 
-// mode 1: z = A c;  mode 0 (iteration): z -= delta A c.  A dense D x D
-// row-major; 4 rows per block, 2 warps per row, fixed-order sums
+// mode 1: z = A c;  mode 0 (iteration): z -= delta A c;  mode 2: z = A c in an
+// iteration.  Modes 0 and 2 return at once when the iteration has stopped.  A
+// dense D x D row-major; 4 rows per block, 2 warps per row, fixed-order sums
 __global__ void __launch_bounds__(kVT) gemv_rows_kernel(const double* A, const double* c, double* z, int D,
                                                         const PcgCtrl* ctrl, int mode) {
   __shared__ double red[kVT / 32];
-  if (ctrl && mode == 0 && !ctrl->active) return;
+  if (ctrl && mode != 1 && !ctrl->active) return;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int row = blockIdx.x * 4 + warp / 2, half = warp & 1;
   double acc = 0.0;
@@ -156,6 +159,25 @@ __global__ void __launch_bounds__(kVT) gemv_rows_kernel(const double* A, const d
   }
 }
 
+// beta and w.y after the dot wyn = w.y of the new iterate: mode 0 (iteration)
+// beta = wyn / (w.y before), mode 2 (start) beta = 0, mode 1 (residual
+// replacement) the replaced residual takes the place of this iteration's
+// recursive one: beta divides by the w.y the iteration started from, or the
+// search direction restarts (iterative refinement with inner CG solves).
+__device__ __forceinline__ void set_direction(PcgCtrl* ctrl, double wyn, int mode) {
+  ctrl->wyn = wyn;
+  if (mode == 2) {
+    ctrl->beta = 0.0;
+    ctrl->wy_prev = wyn;
+  } else if (mode == 0) {
+    ctrl->beta = ctrl->wy > 0.0 ? wyn / ctrl->wy : 0.0;
+    ctrl->wy_prev = ctrl->wy;
+  } else {
+    ctrl->beta = ctrl->restart ? 0.0 : (ctrl->wy_prev > 0.0 ? wyn / ctrl->wy_prev : 0.0);
+  }
+  ctrl->wy = wyn;
+}
+
 // mode 0 (iteration): lambda += delta p, r -= delta q;  mode 1 (refresh): r = d - q;  mode 2 (start): as 1,
 // and the start values nw0 / floor are set.  Then w = r - G z, the dot w.w and the scatter of w into the
 // tile precision for the next apply (pg at both B columns of the multiplier); the last block finishes.
@@ -164,7 +186,8 @@ template <typename TF>
 __global__ void __launch_bounds__(kVT) pcg_update_kernel(const int4* lg, const int* c0, const int* c1, int nlam,
                                                          const double* G6, const double* z, const double* p,
                                                          const double* q, const double* d, double* lam, double* r,
-                                                         double* w, TF* pg, double* part, int mode, PcgCtrl* ctrl) {
+                                                         double* w, TF* pg, double* part, int mode, int pre,
+                                                         PcgCtrl* ctrl) {
   __shared__ double red[kVT / 32];
   if (mode == 0 && !ctrl->active) return;
   const double delta = ctrl->delta;
@@ -187,38 +210,107 @@ __global__ void __launch_bounds__(kVT) pcg_update_kernel(const int4* lg, const i
     }
     const double wl = rl - gz;
     w[l] = wl;
-    pg[g0] = (TF)wl;
-    if (g1 >= 0) pg[g1] = (TF)wl;
+    if (!pre) {  // with a preconditioner the apply streams F against y = P M w, scattered later
+      pg[g0] = (TF)wl;
+      if (g1 >= 0) pg[g1] = (TF)wl;
+    }
     s = fma(wl, wl, s);
   }
   s = block_sum(s, red);
   if (last_block(s, part, &ctrl->cnt_upd)) {
     const double wyn = sum_partials(part, gridDim.x, red);
     if (threadIdx.x == 0) {
-      const double nw = sqrt(wyn);
-      ctrl->wyn = wyn;
+      const double nw = sqrt(wyn);  // wyn = w.w here
       ctrl->nw = nw;
       if (mode == 2) {
         // start: floor = 64 eps (||d|| + ||F lambda_0||) from the two norms stored before
         ctrl->nw0 = nw;
         ctrl->floor = 64.0 * 2.220446049250313e-16 * (sqrt(ctrl->dd) + sqrt(ctrl->qq));
-        ctrl->beta = 0.0;
-        ctrl->wy_prev = wyn;
-      } else if (mode == 0) {
-        ctrl->beta = ctrl->wy > 0.0 ? wyn / ctrl->wy : 0.0;
-        ctrl->wy_prev = ctrl->wy;
-      } else {
-        // the replaced residual takes the place of this iteration's recursive one:
-        // beta divides by the w.w the iteration started from, or the search
-        // direction restarts (iterative refinement with inner CG solves)
-        ctrl->beta = ctrl->restart ? 0.0 : (ctrl->wy_prev > 0.0 ? wyn / ctrl->wy_prev : 0.0);
       }
-      ctrl->wy = wyn;
+      if (!pre) set_direction(ctrl, wyn, mode);  // M = I: y = w
       if (mode == 0) ctrl->it += 1;
       ctrl->rel = ctrl->nw0 > 0.0 ? nw / ctrl->nw0 : 0.0;
       ctrl->conv = (nw <= ctrl->tol * ctrl->nw0 || nw <= ctrl->floor) ? 1 : 0;
       ctrl->active = (!ctrl->conv && !ctrl->breakdown && ctrl->it < ctrl->maxit) ? 1 : 0;
       ctrl->cnt_upd = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- lumped preconditioner
+//
+// M = W M_core W with W = (B B^T)^{-1} (small dense blocks, CSR) and
+// M_core = sum_i B_i K_i B_i^T (CSR over multipliers; its values are summed
+// from K at every assembly).  y = P M w needs v = M w, its projection and the
+// dot w.y; the apply of the next iteration then streams F against y.
+
+// mval[e] = sum of the entry's (sign, K value) contributions, in stored order
+__global__ void lumped_values_kernel(int64_t nnz, const int64_t* c_off, const int64_t* kidx, const double* sgn,
+                                     const double* Kval, double* mval) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int64_t k = c_off[e]; k < c_off[e + 1]; ++k) v = fma(sgn[k], Kval[kidx[k]], v);
+    mval[e] = v;
+  }
+}
+
+// v = W M_core W w, one thread per multiplier a:
+//   v_a = sum_{c in W row a} W_ac sum_{e in M_core row c} m_e sum_{f in W row col_e} W_{col_e f} w_f
+// (W's blocks are a node's few multipliers, so the redundant inner sums are short).
+__global__ void __launch_bounds__(kVT) lumped_apply_kernel(int nlam, const int* woff, const int* wcol,
+                                                           const double* wval, const int* moff, const int* mcol,
+                                                           const double* mval, const double* w, double* v,
+                                                           const PcgCtrl* ctrl, int iteration) {
+  if (iteration && !ctrl->active) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nlam; a += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = woff[a]; i < woff[a + 1]; ++i) {
+      const int c = wcol[i];
+      double sc = 0.0;
+      for (int e = moff[c]; e < moff[c + 1]; ++e) {
+        const int d = mcol[e];
+        double t = 0.0;
+        for (int f = woff[d]; f < woff[d + 1]; ++f) t = fma(wval[f], w[wcol[f]], t);
+        sc = fma(mval[e], t, sc);
+      }
+      acc = fma(wval[i], sc, acc);
+    }
+    v[a] = acc;
+  }
+}
+
+// y = v - G z2 (the projection of v = M w; z2 = (G^T G)^{-1} G^T v, or none
+// without a coarse space), the scatter of y into the tile precision for the
+// next apply, and the dot w.y; the last block sets beta and w.y (set_direction).
+// mode 0 (iteration) returns at once when the iteration has stopped.
+template <typename TF>
+__global__ void __launch_bounds__(kVT) pcg_proj_kernel(const int4* lg, const int* c0, const int* c1, int nlam,
+                                                       const double* G6, const double* z2, const double* v,
+                                                       const double* w, double* y, TF* pg, double* part, int mode,
+                                                       PcgCtrl* ctrl) {
+  __shared__ double red[kVT / 32];
+  if (mode == 0 && !ctrl->active) return;
+  double s = 0.0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int g0 = c0[l], g1 = c1[l];
+    double gz = 0.0;
+    if (z2) {
+      const int4 a = lg[l];
+      for (int k = 0; k < a.y; ++k) gz = fma(G6[(int64_t)g0 * 6 + k], z2[a.x + k], gz);
+      for (int k = 0; k < a.w; ++k) gz = fma(G6[(int64_t)g1 * 6 + k], z2[a.z + k], gz);
+    }
+    const double yl = v[l] - gz;
+    y[l] = yl;
+    pg[g0] = (TF)yl;
+    if (g1 >= 0) pg[g1] = (TF)yl;
+    s = fma(w[l], yl, s);
+  }
+  s = block_sum(s, red);
+  if (last_block(s, part, &ctrl->cnt_proj)) {
+    const double wyn = sum_partials(part, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      set_direction(ctrl, wyn, mode);
+      ctrl->cnt_proj = 0;
     }
   }
 }
@@ -267,13 +359,37 @@ void launch_gemv_rows(const double* A, const double* c, double* z, int D, const 
 
 void launch_pcg_update(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
                        const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
-                       double* w, void* pg, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st) {
+                       double* w, void* pg, double* part, int mode, int pre, PcgCtrl* ctrl, cudaStream_t st) {
   if (fp32)
     pcg_update_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z, p, q, d, lam, r, w, (float*)pg,
-                                                          part, mode, ctrl);
+                                                          part, mode, pre, ctrl);
   else
     pcg_update_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z, p, q, d, lam, r, w, (double*)pg,
-                                                           part, mode, ctrl);
+                                                           part, mode, pre, ctrl);
+}
+
+void launch_lumped_values(int64_t nnz, const int64_t* c_off, const int64_t* kidx, const double* sgn,
+                          const double* Kval, double* mval, cudaStream_t st) {
+  if (nnz <= 0) return;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nnz + kVT - 1) / kVT, 152 * 16));
+  lumped_values_kernel<<<g, kVT, 0, st>>>(nnz, c_off, kidx, sgn, Kval, mval);
+}
+
+void launch_lumped_apply(int nlam, const int* woff, const int* wcol, const double* wval, const int* moff,
+                         const int* mcol, const double* mval, const double* w, double* v, const PcgCtrl* ctrl,
+                         int iteration, cudaStream_t st) {
+  lumped_apply_kernel<<<vgrid(nlam), kVT, 0, st>>>(nlam, woff, wcol, wval, moff, mcol, mval, w, v, ctrl, iteration);
+}
+
+void launch_pcg_proj(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
+                     const double* z2, const double* v, const double* w, double* y, void* pg, double* part, int mode,
+                     PcgCtrl* ctrl, cudaStream_t st) {
+  if (fp32)
+    pcg_proj_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z2, v, w, y, (float*)pg, part, mode,
+                                                        ctrl);
+  else
+    pcg_proj_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(lg, c0, c1, nlam, G6, z2, v, w, y, (double*)pg, part, mode,
+                                                         ctrl);
 }
 
 void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st) {

@@ -66,7 +66,16 @@ void launch_gemv_rows(const double* A, const double* c, double* z, int D, const 
                       cudaStream_t st);
 void launch_pcg_update(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
                        const double* z, const double* p, const double* q, const double* d, double* lam, double* r,
-                       double* w, void* pg, double* part, int mode, PcgCtrl* ctrl, cudaStream_t st);
+                       double* w, void* pg, double* part, int mode, int pre, PcgCtrl* ctrl, cudaStream_t st);
+// lumped preconditioner (kern_pcg.cu)
+void launch_lumped_values(int64_t nnz, const int64_t* c_off, const int64_t* kidx, const double* sgn,
+                          const double* Kval, double* mval, cudaStream_t st);
+void launch_lumped_apply(int nlam, const int* woff, const int* wcol, const double* wval, const int* moff,
+                         const int* mcol, const double* mval, const double* w, double* v, const PcgCtrl* ctrl,
+                         int iteration, cudaStream_t st);
+void launch_pcg_proj(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
+                     const double* z2, const double* v, const double* w, double* y, void* pg, double* part, int mode,
+                     PcgCtrl* ctrl, cudaStream_t st);
 void launch_pcg_norms(const double* d, const double* q, int n, PcgCtrl* ctrl, cudaStream_t st);
 void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t st);
 void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,

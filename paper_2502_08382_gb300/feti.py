@@ -48,7 +48,8 @@ class FetiOptions(C.Structure):
     _fields_ = [("prec", C.c_int), ("refine_every", C.c_int32), ("tol", C.c_double), ("maxit", C.c_int32),
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
-                ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32)]
+                ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
+                ("precond", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -212,7 +213,7 @@ class FetiOperator:
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
-                 leaf_dofs: int = 16, use_coords: bool = True,
+                 precond: str = "none", leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
         import torch
         self.torch = torch
@@ -230,6 +231,7 @@ class FetiOperator:
         opt.refine_every = refine_every
         opt.refine_drop = refine_drop
         opt.refine_restart = 1 if refine_restart else 0
+        opt.precond = {"none": 0, "lumped": 1}[precond]
         opt.tol = tol
         opt.maxit = maxit
         opt.stream = C.c_void_p(self.stream.cuda_stream)

@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--refine-every", type=int, default=0)
     ap.add_argument("--refine-drop", type=float, default=1e-3)
     ap.add_argument("--restart", action="store_true", help="restart the CG direction after each FP64 residual")
+    ap.add_argument("--precond", default="none", choices=["none", "lumped"])
     args = ap.parse_args()
 
     import torch
@@ -41,7 +42,8 @@ def main():
     P = make_config(args.config, nsub_axis=args.nsub_axis)
     mixed = args.prec != "fp64"
     op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000, refine_every=args.refine_every if mixed else 0,
-                           refine_drop=args.refine_drop if mixed else 0.0, refine_restart=args.restart)
+                           refine_drop=args.refine_drop if mixed else 0.0, refine_restart=args.restart,
+                           precond=args.precond)
     op.assemble()
     p = torch.from_numpy(seeded_vector(P.n_lambda, 0)).cuda()
     q = torch.empty_like(p)
@@ -84,7 +86,7 @@ def main():
                       "reps": args.reps, "ms": ms, "device_bytes": s["device_bytes"],
                       "apply_bytes": s["apply_bytes"], "implicit_bytes": s["implicit_bytes"],
                       "chol_flops": s["chol_flops"], "trsm_flops": s["trsm_flops"],
-                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "refine_drop": args.refine_drop, "restart": args.restart,
+                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "refine_drop": args.refine_drop, "restart": args.restart, "precond": args.precond,
                       "solve": info, "launches": s["launches"], "profiled": prof}))
     op.close()
 

@@ -186,6 +186,22 @@ BAD_INPUTS = {
 }
 
 
+def test_create_rejects_bad_options(lib):
+    """Unknown precision or preconditioner codes are rejected on the host."""
+    import ctypes as C
+    P = make_problem(dim=2, physics="heat", cuts=[[3, 4]] * 2, material="const", seed=0)
+    for field, val, words in (("prec", 7, "bad precision"), ("precond", 5, "bad preconditioner")):
+        m = feti._Marshal(P)
+        opt = feti.FetiOptions()
+        setattr(opt, field, val)
+        h = C.c_void_p()
+        rc = lib.feti_create(C.byref(m.prob), C.byref(opt), C.byref(h))
+        msg = lib.feti_last_error(h).decode() if h else ""
+        if h:
+            lib.feti_destroy(h)
+        assert rc == 1 and words in msg, (field, rc, msg)
+
+
 @pytest.mark.parametrize("name", list(BAD_INPUTS))
 def test_create_rejects_malformed_input(lib, name):
     P = make_problem(dim=2, physics="heat", cuts=[[3, 4]] * 2, material="const", seed=0)
