@@ -209,7 +209,12 @@ def analyse(sub, leaf_dofs=16, use_coords=True):
 
 class FetiOperator:
     """Explicit FETI dual operator on one GPU (wraps feti_create / feti_assemble /
-    feti_apply / feti_apply_implicit / feti_solve / feti_adjoint)."""
+    feti_apply / feti_apply_implicit / feti_solve / feti_solve_warm / feti_adjoint).
+
+    prec: "fp64", "tf32" or "split_bf16" (tensor-core TRSM updates and SYRK,
+    FP32 F tiles); refine_every / refine_drop / refine_restart: the FP64
+    residual replacement of the mixed solve; precond: "none" (M = I) or
+    "lumped" (M = (BB^T)^-1 sum_i B_i K_i B_i^T (BB^T)^-1)."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
