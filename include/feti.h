@@ -214,6 +214,20 @@ void feti_destroy(feti_ctx* ctx);
 feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, double* info,
                          int32_t* perm_out, int32_t* sn_out);
 
+/* Host-only plan of the lumped preconditioner (options.precond = 1), for
+ * inspection; no device is touched.  M = W M_core W with W = (B B^T)^{-1}
+ * (CSR over multipliers: w_off [n_lambda + 1], w_col / w_val [sizes[0]]) and
+ * M_core = sum_i B_i K_i B_i^T (CSR: m_off [n_lambda + 1], m_col [sizes[1]];
+ * entry e's value is sum over k in [c_off[e], c_off[e + 1]) of
+ * c_sign[k] * K[c_kidx[k]], with K the subdomains' CSR values concatenated in
+ * order; c_off [sizes[1] + 1], c_kidx / c_sign [sizes[2]]).  Call with NULL
+ * arrays to get sizes = {nnz(W), nnz(M_core), contributions}; arrays are
+ * caller-owned host memory.  Errors: FETI_ERR_ARG for invalid input or a
+ * singular B B^T block (redundant multipliers). */
+feti_status feti_analyse_lumped(const feti_problem* prob, int64_t* sizes, int32_t* w_off, int32_t* w_col,
+                                double* w_val, int32_t* m_off, int32_t* m_col, int64_t* c_off, int64_t* c_kidx,
+                                double* c_sign);
+
 /* Largest m accepted by feti_apply_one_static. */
 #define FETI_STATIC_MAX_M 8192
 

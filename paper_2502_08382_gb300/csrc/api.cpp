@@ -1053,4 +1053,41 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
   }
 }
 
+feti_status feti_analyse_lumped(const feti_problem* prob, int64_t* sizes, int32_t* w_off, int32_t* w_col,
+                                double* w_val, int32_t* m_off, int32_t* m_col, int64_t* c_off, int64_t* c_kidx,
+                                double* c_sign) {
+  if (!prob || !sizes || prob->nsub <= 0 || prob->n_lambda < 0) return FETI_ERR_ARG;
+  feti_ctx tmp;  // host fields only: no device memory is touched
+  try {
+    tmp.nsub = prob->nsub;
+    tmp.nlam = prob->n_lambda;
+    tmp.subs.resize(prob->nsub);
+    tmp.info.resize(prob->nsub);
+    int64_t kofs = 0;
+    for (int i = 0; i < prob->nsub; ++i) {
+      copy_sub(prob->sub[i], tmp.subs[i], i);
+      for (int32_t l : tmp.subs[i].blam)
+        if (l < 0 || l >= prob->n_lambda) throw ArgError("B_lambda out of range");
+      tmp.info[i].Kval = kofs;
+      kofs += (int64_t)tmp.subs[i].col.size();
+    }
+    LumpedPlan lp;
+    plan_lumped(&tmp, lp);
+    sizes[0] = (int64_t)lp.w_col.size();
+    sizes[1] = (int64_t)lp.m_col.size();
+    sizes[2] = (int64_t)lp.c_kidx.size();
+    if (w_off) std::copy(lp.w_off.begin(), lp.w_off.end(), w_off);
+    if (w_col) std::copy(lp.w_col.begin(), lp.w_col.end(), w_col);
+    if (w_val) std::copy(lp.w_val.begin(), lp.w_val.end(), w_val);
+    if (m_off) std::copy(lp.m_off.begin(), lp.m_off.end(), m_off);
+    if (m_col) std::copy(lp.m_col.begin(), lp.m_col.end(), m_col);
+    if (c_off) std::copy(lp.c_off.begin(), lp.c_off.end(), c_off);
+    if (c_kidx) std::copy(lp.c_kidx.begin(), lp.c_kidx.end(), c_kidx);
+    if (c_sign) std::copy(lp.c_sign.begin(), lp.c_sign.end(), c_sign);
+    return FETI_OK;
+  } catch (std::exception&) {
+    return FETI_ERR_ARG;
+  }
+}
+
 }  // extern "C"

@@ -75,7 +75,7 @@ class FetiStats(C.Structure):
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
            "feti_solve", "feti_solve_warm", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
-           "feti_analyse", "feti_version", "feti_apply_one_static", "feti_set_profiling"]
+           "feti_analyse", "feti_analyse_lumped", "feti_version", "feti_apply_one_static", "feti_set_profiling"]
 
 _lib = None
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.feti_destroy.argtypes = [vp]
     lib.feti_destroy.restype = None
     lib.feti_analyse.argtypes = [C.POINTER(FetiSubdomain), C.POINTER(FetiOptions), _f64p, _i32p, _i32p]
+    lib.feti_analyse_lumped.argtypes = [C.POINTER(FetiProblem), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.feti_version.restype = C.c_char_p
     lib.feti_apply_one_static.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp]
     lib.feti_set_profiling.argtypes = [vp, C.c_int32]
@@ -395,3 +396,26 @@ def _feti_weighted_trace():
 def weighted_trace(coef, op, Ws):
     """Differentiable L = sum_i <W_i, F_i(coef)> (see FetiWeightedTrace)."""
     return _feti_weighted_trace().apply(coef, op, Ws)
+
+
+def lumped_plan(problem):
+    """Host plan of the lumped preconditioner (feti_analyse_lumped): returns
+    dict(w_off, w_col, w_val, m_off, m_col, c_off, c_kidx, c_sign) as NumPy
+    arrays.  No device is needed."""
+    lib = load_library()
+    m = _Marshal(problem)
+    sizes = np.zeros(3, dtype=np.int64)
+    nul = C.c_void_p()
+    rc = lib.feti_analyse_lumped(C.byref(m.prob), sizes.ctypes.data_as(C.c_void_p), *([nul] * 8))
+    if rc != FETI_OK:
+        raise FetiError(rc, "feti_analyse_lumped rejected the problem")
+    n = problem.n_lambda
+    out = dict(w_off=np.zeros(n + 1, np.int32), w_col=np.zeros(sizes[0], np.int32), w_val=np.zeros(sizes[0]),
+               m_off=np.zeros(n + 1, np.int32), m_col=np.zeros(sizes[1], np.int32),
+               c_off=np.zeros(sizes[1] + 1, np.int64), c_kidx=np.zeros(sizes[2], np.int64), c_sign=np.zeros(sizes[2]))
+    ptr = [out[k].ctypes.data_as(C.c_void_p) for k in ("w_off", "w_col", "w_val", "m_off", "m_col", "c_off",
+                                                        "c_kidx", "c_sign")]
+    rc = lib.feti_analyse_lumped(C.byref(m.prob), sizes.ctypes.data_as(C.c_void_p), *ptr)
+    if rc != FETI_OK:
+        raise FetiError(rc, "feti_analyse_lumped rejected the problem")
+    return out

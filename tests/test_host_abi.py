@@ -219,3 +219,30 @@ def test_apply_one_static_rejects_sizes_on_host(lib):
     for m in (0, -3, 8193, 1 << 20):
         assert lib.feti_apply_one_static(m, 1, one, one, one, one, None) == 1
     assert lib.feti_apply_one_static(64, 1, None, one, one, one, None) == 1
+
+
+def test_lumped_plan_matches_oracle(lib):
+    """The host plan of the lumped preconditioner (no device): W against the
+    oracle's (B B^T)^{-1}, the summed M_core contributions against the
+    oracle's sum_i B_i K_i B_i^T, and W M_core W against its scaled form."""
+    from oracle import feti_oracle as O
+    for P in (make_problem(dim=2, physics="heat", cuts=[[4, 5, 3]] * 2, material="lognormal", sigma=1.0, seed=3),
+              make_problem(dim=3, physics="elasticity", cuts=[[2, 3]] * 3, material="density", seed=3)):
+        pl = feti.lumped_plan(P)
+        n = P.n_lambda
+        W = np.zeros((n, n))
+        for a in range(n):
+            for k in range(pl["w_off"][a], pl["w_off"][a + 1]):
+                W[a, pl["w_col"][k]] = pl["w_val"][k]
+        Kall = np.concatenate([s.K_val for s in P.subs])
+        Mc = np.zeros((n, n))
+        for a in range(n):
+            for e in range(pl["m_off"][a], pl["m_off"][a + 1]):
+                c0, c1 = pl["c_off"][e], pl["c_off"][e + 1]
+                Mc[a, pl["m_col"][e]] = np.sum(pl["c_sign"][c0:c1] * Kall[pl["c_kidx"][c0:c1]])
+        Wo = np.linalg.inv(O.BBt(P))
+        Mo = O.lumped_M(P)
+        assert np.abs(W - Wo).max() <= 1e-12 * np.abs(Wo).max()
+        assert np.abs(Mc - Mo).max() <= 1e-12 * np.abs(Mo).max()
+        So = O.scaled_lumped_M(P)
+        assert np.abs(W @ Mc @ W - So).max() <= 1e-12 * np.abs(So).max()
