@@ -142,21 +142,26 @@ def Gt_times(problem, lam: np.ndarray) -> np.ndarray:
 
 
 def feti_equation_residuals(problem, lam, us):
-    """Residuals of the FETI system (eq. 3) for a computed (lambda, u): per
-    subdomain the normwise backward error of the primal rows,
-    ||K_i u_i + B_i^T lambda - f_i|| / (||K_i||_F ||u_i|| + ||f_i - B_i^T lambda||),
-    and the gluing / Dirichlet rows B u - c."""
-    prim = []
+    """Residuals of the FETI system (eq. 3) for a computed (lambda, u).  Per
+    subdomain, for the primal rows K_i u_i + B_i^T lambda - f_i:
+      forward   ||K_i u_i + B_i^T lambda - f_i|| / ||f_i - B_i^T lambda||,
+      backward  ||K_i u_i + B_i^T lambda - f_i|| / (||K_i||_F ||u_i|| + ||f_i - B_i^T lambda||)
+    (the normwise backward error, the quantity a backward-stable solve bounds
+    by a small multiple of the unit roundoff); and the gluing / Dirichlet rows
+    B u - c.  Returns (forward, backward, B u - c)."""
+    fwd, bwd = [], []
     Bu = -np.asarray(problem.c, dtype=np.float64).copy()
     for s, u in zip(problem.subs, us):
         K = sp.csr_matrix((s.K_val, s.K_col, s.K_rowptr), shape=(s.n, s.n))
         btl = np.zeros(s.n)
         np.add.at(btl, s.B_dof, s.B_sign * lam[np.asarray(s.B_lambda, dtype=np.int64)])
         rhs = s.f - btl
+        res = np.linalg.norm(K @ u - rhs)
+        fwd.append(res / max(np.linalg.norm(rhs), 1e-300))
         scale = sp.linalg.norm(K) * np.linalg.norm(u) + np.linalg.norm(rhs)
-        prim.append(np.linalg.norm(K @ u - rhs) / max(scale, 1e-300))
+        bwd.append(res / max(scale, 1e-300))
         np.add.at(Bu, np.asarray(s.B_lambda, dtype=np.int64), s.B_sign * u[s.B_dof])
-    return np.asarray(prim), Bu
+    return np.asarray(fwd), np.asarray(bwd), Bu
 
 
 def e_vector(problem) -> np.ndarray:

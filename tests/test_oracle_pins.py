@@ -266,10 +266,11 @@ def test_Gt_times_and_residuals(cfg1):
     lam = np.random.default_rng(3).normal(size=cfg1.n_lambda)
     assert np.allclose(O.Gt_times(cfg1, lam), O.G_matrix(cfg1).T @ lam, rtol=0, atol=1e-12)
     res = O.feti_solve(cfg1, tol=1e-12)
-    prim, Bu = O.feti_equation_residuals(cfg1, res["lam"], res["u"])
-    assert prim.max() < 1e-12 and np.abs(Bu).max() < 1e-10
-    prim2, Bu2 = O.feti_equation_residuals(cfg1, res["lam"] + 1e-3 * lam, res["u"])
-    assert prim2.max() > 1e-6
+    fwd, bwd, Bu = O.feti_equation_residuals(cfg1, res["lam"], res["u"])
+    assert fwd.max() < 1e-12 and bwd.max() < 1e-13 and np.abs(Bu).max() < 1e-10
+    assert np.all(bwd <= fwd)
+    fwd2, bwd2, Bu2 = O.feti_equation_residuals(cfg1, res["lam"] + 1e-3 * lam, res["u"])
+    assert fwd2.max() > 1e-6 and bwd2.max() > 1e-8
 
 
 def test_pcpg_degenerate_initial_guess():
