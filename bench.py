@@ -1,22 +1,27 @@
 """Benchmark of the FETI dual-operator hot path on one GB300 (per rank).
 
-Workload: 2D heat, 32 x 32 subdomains of 64 x 64 Q1 elements (4225 DOFs each,
-m_i 129..258, n_lambda = 130 048), lognormal conductivity (sigma = 1, seed 0),
-Dirichlet on x = 0; seeded synthetic inputs (the paper's data are not used).
+Default workload (3): 3D linear elasticity, Hex8, the unit cube cut into
+8 x 8 x 8 = 512 subdomains of 12^3 elements (6591 DOFs each, m_i 1407..2814,
+n_lambda = 664 800), E = 1, nu = 0.3, clamped at x = 0, body force (0, 0, -1):
+the largest configuration of the explicit assembly and apply (6.7 GB of FP32
+F tiles).  `--workload 2|4|5` runs the other configurations (2: 2D lognormal
+heat, 1024 subdomains of 4225 DOFs; 4: uneven 3D heat; 5: the sensitivity
+configuration's mesh).  Seeded synthetic inputs; the paper's data are not used.
 
 A step is one pass of the whole path, on the mixed-precision configuration
-(FP32 pruned TRSM, split-bf16 tensor-core SYRK, FP32 F_i tiles, FP64
-Cholesky / coarse problem / PCPG vectors, FP64 residual replacement each time
-the projected residual has dropped by 1e3 and to confirm convergence):
+(FP64 Cholesky; FP32 pruned TRSM with split-bf16 tensor-core panel updates;
+split-bf16 tensor-core SYRK into FP32 F_i tiles; FP64 coarse problem and PCPG
+vectors; the FP64 residual recomputed with the implicit operator each time the
+projected residual has dropped by 1e4, and to confirm convergence):
 feti_assemble (regularise, Cholesky, TRSM, SYRK) followed by feti_solve
 (projected PCG with the explicit apply, refinement, alpha, u).
 `value` is the achieved GB/s of the explicit F.lambda apply inside the timed
 steps: algorithmic bytes per apply / mean CUDA-event time of the F-streaming
-kernel, recorded by the library on its stream.  The FP64 assembly, the F and
-solution differences between the two paths, the implicit-apply time and the
-break-even iteration count are reported beside it.
+kernel, recorded by the library on its stream.  The FP64 assembly and apply,
+the F and solution differences between the two paths, the implicit-apply time
+and the break-even iteration count are reported beside it.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2|3|4|5]
 Under torchrun each rank runs an independent replica of the workload (the
 single-GPU path has no exchange step: "replicas only", weak scaling).
 """
@@ -45,7 +50,7 @@ WORKLOADS = {
        "lognormal sigma=0.5",
     5: "3D elasticity Hex8, 6x6x6 subdomains of 16^3 elements (14739 DOFs, n_lambda 473832), rho~U[0.1,1], E=rho^3",
 }
-WORKLOAD = WORKLOADS[2]
+DEFAULT_WORKLOAD = 3
 PREC = "split_bf16"
 REFINE_DROP = 1e-4   # FP64 residual recomputed whenever ||P r|| has dropped by this factor
 REFINE_RESTART = True  # the search direction restarts after each FP64 residual (refinement with inner CG)
@@ -126,38 +131,50 @@ def bf16_peak():
 
 
 def other_rooflines(st, impl_ms, hbm):
-    """Rooflines of the assembly kernels and of the FP64 implicit operator (last assembly)."""
+    """Rooflines of the assembly kernels and of the FP64 implicit operator (last assembly).  The flop counts
+    are the symbolic phase's algorithmic counters (feti_stats): Cholesky sum_s (w^3/3 + w^2 r + w r^2),
+    pruned TRSM sum_s J_s (w_s^2 + 2 w_s r_s) (triangular solve and panel update of the J_s columns that
+    reach supernode s), SYRK sum_s w_s J_s (J_s + 1) (the lower triangle of each supernode block's Gram
+    matrix; the split-bf16 tensor-core rate counts its 3 products)."""
     bf16, bf16_kind = bf16_peak()
     out = {}
     if st["t_chol_ms"] > 0:
         a = st["chol_flops"] / (st["t_chol_ms"] * 1e-3) / 1e12
         out["chol_kernel"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64"}
+                              "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64",
+                              "algorithmic_flops": st["chol_flops"], "ms": st["t_chol_ms"]}
     if st["t_trsm_ms"] > 0:
         a = st["trsm_flops"] / (st["t_trsm_ms"] * 1e-3) / 1e12
         out["trsm_kernel<float>"] = {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                     "frac": a / FP32_PEAK_TFLOPS, "peak_kind": "derived FP32"}
+                                     "frac": a / FP32_PEAK_TFLOPS, "peak_kind": "derived FP32",
+                                     "algorithmic_flops": st["trsm_flops"], "ms": st["t_trsm_ms"]}
     if st["t_syrk_ms"] > 0:
         a = 3 * st["syrk_flops"] / (st["t_syrk_ms"] * 1e-3) / 1e12  # split-bf16: 3 tensor products per FMA
         out["syrk_tc_kernel"] = {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s",
-                                 "frac": a / bf16, "peak_kind": f"{bf16_kind} bf16"}
+                                 "frac": a / bf16, "peak_kind": f"{bf16_kind} bf16",
+                                 "algorithmic_flops": st["syrk_flops"], "tensor_flops": 3 * st["syrk_flops"],
+                                 "ms": st["t_syrk_ms"]}
     if impl_ms > 0:
         # FP64-pipe bound (ncu: FP64 pipe ~2/3 active, DRAM ~12%): 2 FMAs per factor entry, forward and back
         a = st["implicit_bytes"] / 4 / (impl_ms * 1e-3) / 1e12
         g = st["implicit_bytes"] / (impl_ms * 1e-3) / 1e9
         out["implicit_kernel<0>"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64",
+                                     "algorithmic_flops": st["implicit_bytes"] / 4, "ms": impl_ms,
                                      "factor_gbs": g, "factor_gbs_frac_of_hbm": g / hbm}
     return out
 
 
 # Variant index of the apply autotuner -> kernel name.
-APPLY_KERNELS = ["apply_tiles_kernel<float, 4>", "apply_tiles_kernel<float, 8>", "apply_tiles_kernel<float, 16>",
-                 "apply_ring_kernel<float, 4, 3>", "apply_ring_kernel<float, 8, 3>", "apply_ring_kernel<float, 2, 6>"]
+APPLY_KERNELS = ["apply_tiles_kernel<{t}, 4>", "apply_tiles_kernel<{t}, 8>", "apply_tiles_kernel<{t}, 16>",
+                 "apply_ring_kernel<{t}, 4, 3>", "apply_ring_kernel<{t}, 8, 3>", "apply_ring_kernel<{t}, 2, 6>"]
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the apply tile kernels, from ncu captures
-# (--set full) on the workload named; all variants read the same stored F bytes once.
-APPLY_TRAFFIC = {(2, "apply_tiles_kernel"): 138.71e6, (2, "apply_ring_kernel"): 139.66e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 apply tile kernels (all variants read the
+# stored F bytes once), from an ncu capture of the kernel as it stands: workload 2 at full size, workload 3 on
+# its 4 x 4 x 4-subdomain copy (0.84 GB of tiles) scaled to the full 512 subdomains by the tile bytes (the
+# traffic is the tiles plus per-tile vector segments, both proportional).  The summaries are in profiles/.
+APPLY_TRAFFIC = {2: (138.71e6, "ncu, profiles/apply_tiles_workload2.md"),
+                 3: (None, "not captured")}
 
 
 def oracle_sample(P, nsample, reps):
@@ -193,8 +210,8 @@ def run_reference(args):
         tf.append(t_f)
     ms = (time.perf_counter() - t_all) * 1e3 / max(args.steps, 1)
     gbs = statistics.median(vals)
-    sample = (f"{nsample} of 1024 subdomains per step: scipy dense Cholesky F_i and 50 dense FP64 F_i p_i sweeps; "
-              f"value = GB/s of the F_i p_i sweeps")
+    sample = (f"{nsample} of {P.nsub} subdomains per step: scipy dense Cholesky F_i and 50 dense FP64 F_i p_i "
+              f"sweeps; value = GB/s of the F_i p_i sweeps")
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -213,8 +230,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", type=int, default=2, choices=sorted(WORKLOADS),
-                    help="2 (default: the workload the metric is quoted on) or one of the 3D workloads")
+    ap.add_argument("--workload", type=int, default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="3 (default: the largest assembly/apply configuration), 2, 4 or 5")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -239,7 +256,7 @@ def main():
     P = make_config(args.workload)
     op = feti.FetiOperator(P, prec=PREC, tol=TOL, maxit=5000, refine_drop=REFINE_DROP, refine_restart=REFINE_RESTART)
     st = torch.cuda.current_stream()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
 
     def step():
         op.assemble()
@@ -281,8 +298,9 @@ def main():
     impl_ms = st_["implicit_ms"] / max(st_["implicit_calls"], 1)
     hbm, pk_kind = peaks()
     tiles_gbs = st_["apply_bytes"] / (tiles_ms * 1e-3) / 1e9
-    kname = APPLY_KERNELS[st_["apply_variant"]] if 0 <= st_["apply_variant"] < len(APPLY_KERNELS) else "apply"
-    traffic = APPLY_TRAFFIC.get((args.workload, kname.split("<")[0]))
+    kname = (APPLY_KERNELS[st_["apply_variant"]].format(t="float") if 0 <= st_["apply_variant"] < len(APPLY_KERNELS)
+             else "apply")
+    traffic, traffic_src = APPLY_TRAFFIC.get(args.workload, (None, "not captured"))
     value = tiles_gbs * world
 
     # end to end through the C ABI with host buffers: H2D p, feti_apply, D2H q
@@ -309,14 +327,29 @@ def main():
 
     # plain FP64 GPU path on the same inputs (assembly time, F and solution differences)
     op64 = feti.FetiOperator(P, prec="fp64", tol=TOL, maxit=5000)
-    for _ in range(2):
-        op64.assemble()
+    op64.assemble()
     asm64 = []
-    for _ in range(3):
+    for _ in range(2):
+        flush.zero_()
         op64.assemble()
         asm64.append(op64.stats()["t_assemble_ms"])
     st64 = op64.stats()
     lam64, alpha64, u64, info64 = op64.solve()
+    # the plain FP64 explicit apply (FP64 F tiles: twice the F bytes)
+    op64.set_profiling(True)
+    for _ in range(10):
+        flush.zero_()
+        op64.apply(p, out=q)
+    st64a = op64.stats()
+    op64.set_profiling(False)
+    t64_tiles = st64a["apply_tiles_ms"] / max(st64a["apply_calls"], 1)
+    t64_call = st64a["apply_ms"] / max(st64a["apply_calls"], 1)
+    apply64 = {"algorithmic_bytes": st64a["apply_bytes"], "tiles_ms": t64_tiles, "ms": t64_call,
+               "gbs": st64a["apply_bytes"] / (t64_tiles * 1e-3) / 1e9,
+               "gbs_whole_call": st64a["apply_bytes"] / (t64_call * 1e-3) / 1e9,
+               "kernel": (APPLY_KERNELS[st64a["apply_variant"]].format(t="double")
+                          if 0 <= st64a["apply_variant"] < len(APPLY_KERNELS) else "apply"),
+               "frac_of_hbm": st64a["apply_bytes"] / (t64_tiles * 1e-3) / 1e9 / hbm}
     sample = sorted({0, P.nsub // 3, (2 * P.nsub) // 3, P.nsub - 1})
     ferr = max(np.linalg.norm(op.get_F(i) - op64.get_F(i)) / np.linalg.norm(op64.get_F(i)) for i in sample)
     uerr = (torch.linalg.norm(u - u64) / torch.linalg.norm(u64)).item()
@@ -335,11 +368,13 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "prec": f"{PREC} SYRK, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
-                       "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual after each {1 / REFINE_DROP:.0e} drop, "
-                               f"CG direction restarted after it)",
+            "config": {"workload": WORKLOADS[args.workload],
+                       "prec": f"{PREC} SYRK and TRSM panel updates, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
+                       "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual after each {1 / REFINE_DROP:.0e} "
+                               f"drop, CG direction restarted after it)",
                        "value": "explicit F.lambda apply GB/s (algorithmic bytes / F-streaming kernel time)",
-                       "l2": "256 MB buffer written before each timed step; F tiles 136 MB > L2 per apply",
+                       "l2": f"256 MB buffer written before each timed step; F tiles "
+                             f"{st_['F_elems'] * 4 / 1e6:.0f} MB > L2 (129 MB) per apply",
                        "parallelism": f"replicas x{world}"},
             "assembly_ms": {"mixed": t_asm, "fp64": statistics.median(asm64),
                             "speedup": statistics.median(asm64) / t_asm,
@@ -353,11 +388,14 @@ def main():
                     "fp64_iterations": info64["iterations"]},
             "apply": {"ms": apply_ms, "tiles_ms": tiles_ms, "algorithmic_bytes": st_["apply_bytes"],
                       "autotuned": {"variant": st_["apply_variant"], "grid": st_["apply_grid"]},
-                      "gbs_whole_call": st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9},
+                      "gbs_whole_call": st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9,
+                      "frac_whole_call": st_["apply_bytes"] / (apply_ms * 1e-3) / 1e9 / hbm},
+            "apply_fp64": apply64,
             "implicit_fp64_apply_ms": impl64_ms,
             "break_even_iters": n_star,
             "roofline": {"bound": "hbm", "achieved": tiles_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": tiles_gbs / hbm, "traffic": traffic, "kernel": kname, "peak_kind": pk_kind},
+                         "frac": tiles_gbs / hbm, "traffic": traffic, "traffic_source": traffic_src,
+                         "kernel": kname, "peak_kind": pk_kind},
             "roofline_other": other_rooflines(st_last, impl64_ms, hbm),
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},

@@ -16,12 +16,14 @@ projected FP64 residual the stopping rule bounds."""
 import numpy as np
 import pytest
 
+from bounds import SPLIT_BAR, apply_scale, gamma
 from oracle import feti_oracle as O
 from paper_2502_08382_gb300.problems import make_config
+from test_gpu_full_size import check_primal
 
 pytestmark = pytest.mark.gpu
 
-TOL_F = 1e-4  # split bf16: about 16 mantissa bits per tensor-core operand
+TOL_F = SPLIT_BAR  # split bf16 (tests/bounds.py)
 
 
 @pytest.fixture(scope="module")
@@ -74,6 +76,9 @@ def test_full_size_3d(torch_cuda, config):
     q = op.apply(torch.from_numpy(p).cuda()).cpu().numpy()
     qi = Fo[i_dir] @ p[lam_i]
     assert np.linalg.norm(q[lam_i] - qi) <= TOL_F * np.linalg.norm(qi)
+    scale = apply_scale([s], [Fo[i_dir]], p, P.n_lambda)[lam_i]
+    tau = TOL_F + gamma(2 * s.m, 2.0 ** -24)
+    assert np.all(np.abs(q[lam_i] - qi) <= tau * scale), np.max(np.abs(q[lam_i] - qi) / np.maximum(scale, 1e-300))
     outside = np.ones(P.n_lambda, dtype=bool)
     outside[lam_i] = False
     assert np.all(q[outside] == 0.0)
@@ -89,9 +94,4 @@ def test_full_size_3d(torch_cuda, config):
         off += sd.n
     e = O.e_vector(P)
     assert np.abs(O.Gt_times(P, lam) - e).max() <= 1e-10 * max(1.0, np.abs(e).max())
-    prim, Bu = O.feti_equation_residuals(P, lam, us)
-    bound = 2e-10 * info["initial_residual"] + 1e-13 * np.linalg.norm(u)
-    print(f"workload {config}: {info['iterations']} iterations, primal residual max {prim.max():.2e}, "
-          f"||Bu - c|| {np.linalg.norm(Bu):.3e} (bound {bound:.3e})")
-    assert prim.max() <= 1e-10, prim.max()
-    assert np.linalg.norm(Bu) <= bound, (np.linalg.norm(Bu), bound)
+    check_primal(P, lam, alpha.cpu().numpy(), us, picks, info, f"workload {config}")

@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 
+from bounds import F_bar, apply_scale, gamma, tf32_vs_split_bar
 from oracle import feti_oracle as O
 from paper_2502_08382_gb300.problems import make_config, make_problem, seeded_vector
 
@@ -63,6 +64,9 @@ def test_apply_fp64_matches_oracle(torch_cuda, name):
         q = op.apply(torch.from_numpy(p).cuda()).cpu().numpy()
         qo = O.apply_F(P, Fs, p)
         assert np.linalg.norm(q - qo) <= 1e-12 * np.linalg.norm(qo)
+        # element by element: |q_j - qo_j| <= 1e-12 s_j (componentwise scale of F p)
+        scale = apply_scale(P.subs, Fs, p, P.n_lambda)
+        assert np.all(np.abs(q - qo) <= 1e-12 * scale), np.max(np.abs(q - qo) / np.maximum(scale, 1e-300))
     # bitwise determinism run to run
     p = torch.from_numpy(seeded_vector(P.n_lambda, 3)).cuda()
     a = op.apply(p).cpu().numpy()
@@ -71,13 +75,10 @@ def test_apply_fp64_matches_oracle(torch_cuda, name):
     op.close()
 
 
-# Mixed precision: pruned TRSM with tensor-core panel updates + tensor-core SYRK,
-# F_i stored as FP32 tiles.  Tolerances follow the operand precision on the
-# tensor cores: TF32 keeps 10 mantissa bits (unit roundoff 2^-11 = 4.9e-4;
-# with the TRSM panel updates and the SYRK both in TF32, an F_i error of about
-# ten roundoffs), split bf16 keeps about 16 (hi*hi + hi*lo + lo*hi, the lo*lo
-# term ~2^-16 dropped).
-MIXED_TOL = {"tf32": 1e-2, "split_bf16": 1e-4}
+# Mixed precision: pruned TRSM with split-bf16 tensor-core panel updates, then a
+# tensor-core SYRK (split bf16, or TF32 on X rounded to TF32), F_i stored as FP32
+# tiles.  The bars follow the rounding model in tests/bounds.py: split bf16 is held
+# to the FP32-level SPLIT_BAR, TF32 to its derived SYRK bound on top of it.
 
 
 @pytest.mark.parametrize("prec", ["tf32", "split_bf16"])
@@ -86,14 +87,37 @@ def test_F_mixed_matches_oracle(torch_cuda, name, prec):
     P = CASES[name]()
     op = _op(P, prec=prec)
     idx = range(P.nsub) if P.nsub <= 27 else range(8)
+    worst, worst_ratio = 0.0, 0.0
+    for i in idx:
+        s = P.subs[i]
+        Fo = O.local_F(s)
+        Fg = op.get_F(int(i))
+        err = np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo)
+        bar = F_bar(prec, Fo, s.n)
+        worst = max(worst, err)
+        worst_ratio = max(worst_ratio, err / bar)
+        assert err <= bar, (i, err, bar)
+    op.close()
+    print(f"{name} {prec}: max relative Frobenius error of F_i = {worst:.3e} ({worst_ratio:.2f} of its bar)")
+
+
+@pytest.mark.parametrize("name", ["cfg1", "heat3d_ragged", "elast3d_2x2x2", "cfg3_2x2x2"])
+def test_F_tf32_syrk_within_rounding_bound(torch_cuda, name):
+    """Both mixed modes run the same TRSM, so F_tf32 - F_split is the SYRK rounding alone:
+    ||F_tf32 - F_split||_F <= (c_tf32 + c_split) tr(F) (tests/bounds.py)."""
+    P = CASES[name]()
+    a = _op(P, prec="tf32")
+    b = _op(P, prec="split_bf16")
+    idx = range(P.nsub) if P.nsub <= 27 else range(8)
     worst = 0.0
     for i in idx:
-        Fo = O.local_F(P.subs[i])
-        Fg = op.get_F(int(i))
-        worst = max(worst, np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo))
-    op.close()
-    print(f"{name} {prec}: max relative Frobenius error of F_i = {worst:.3e}")
-    assert worst <= MIXED_TOL[prec], worst
+        Ft, Fs = a.get_F(int(i)), b.get_F(int(i))
+        bar = tf32_vs_split_bar(Fs, P.subs[i].n)
+        worst = max(worst, np.linalg.norm(Ft - Fs) / bar)
+        assert np.linalg.norm(Ft - Fs) <= bar, (i, np.linalg.norm(Ft - Fs), bar)
+    a.close()
+    b.close()
+    print(f"{name}: ||F_tf32 - F_split|| at most {worst:.3f} of the derived bound")
 
 
 @pytest.mark.parametrize("prec", ["tf32", "split_bf16"])
@@ -106,7 +130,12 @@ def test_apply_mixed_matches_oracle(torch_cuda, prec):
     q = op.apply(torch.from_numpy(p).cuda()).cpu().numpy()
     qo = O.apply_F(P, Fs, p)
     op.close()
-    assert np.linalg.norm(q - qo) <= MIXED_TOL[prec] * np.linalg.norm(qo)
+    bar = max(F_bar(prec, F, s.n) for s, F in zip(P.subs, Fs))
+    assert np.linalg.norm(q - qo) <= bar * np.linalg.norm(qo)
+    # element by element, with the FP32 apply's own accumulation (m_i terms) on top
+    tau = bar + gamma(2 * max(s.m for s in P.subs), 2.0 ** -24)
+    scale = apply_scale(P.subs, Fs, p, P.n_lambda)
+    assert np.all(np.abs(q - qo) <= tau * scale), np.max(np.abs(q - qo) / np.maximum(scale, 1e-300))
 
 
 # ---------------------------------------------------------------- implicit operator and solve
