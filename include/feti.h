@@ -66,10 +66,12 @@ typedef struct {
   int32_t nfix;               /* fixing DOFs; must equal d (a generalised inverse needs it) */
   const int32_t* fix_dofs;    /* [nfix] DOFs penalised by rho = max diag K_i */
   const double* coords;       /* [n*3] node coordinates of each DOF, or NULL (ordering hint) */
-  int32_t nelem, edofs;       /* optional element data for feti_adjoint (0 if unused) */
+  int32_t nelem, edofs;       /* optional element data for feti_adjoint (0 if unused; edofs <= 32) */
   const int32_t* elem_dofs;   /* [nelem*edofs] local DOFs of each element */
-  const double* dKe_ref;      /* [edofs*edofs] shared reference element derivative */
-  const double* dKe_scale;    /* [nelem] d K_e / d theta_e = dKe_scale[e] * dKe_ref */
+  const double* dKe;          /* [nelem*edofs*edofs] d K_e / d theta_e of each element, row-major in the
+                                 element's DOF order; when NULL, the compact form below is used */
+  const double* dKe_ref;      /* [edofs*edofs] shared reference element derivative (compact form) */
+  const double* dKe_scale;    /* [nelem] compact form: d K_e / d theta_e = dKe_scale[e] * dKe_ref */
 } feti_subdomain;
 
 typedef struct {
@@ -85,7 +87,10 @@ typedef struct {
   double tol;                 /* PCPG: stop when ||P r|| <= tol * ||P r_0||, or at the rounding level
                                  ||P r|| <= 64 eps (||d|| + ||F lambda_0||) */
   int32_t maxit;
-  int32_t recompute_X;        /* reserved: 1 = do not keep X_i after assembly */
+  int32_t recompute_X;        /* 1 = do not keep X_i = L_i^{-1} P B_i^T after feti_assemble (it is an
+                                 intermediate of the assembly) nor the FP64 X_i of feti_adjoint after that
+                                 call: both are released and recomputed from L_i when next needed, for
+                                 problems where HBM is short; 0 = keep both buffers for reuse */
   void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator (NULL: cudaMalloc) */
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
@@ -99,6 +104,8 @@ typedef struct {
   int32_t precond;            /* PCPG preconditioner M of Algorithm 1 (the paper leaves it open):
                                  0 = none (M = I); 1 = lumped, M = W (sum_i B_i K_i B_i^T) W with
                                  W = (B B^T)^{-1}, rebuilt from K at every feti_assemble */
+  int64_t adjoint_work_bytes; /* device work budget of one feti_adjoint batch (dense n_i x 2 m_i arrays
+                                 of the subdomains in the batch); 0 = min(24 GiB, 45% of free memory) */
 } feti_options;
 
 typedef struct {
@@ -186,10 +193,24 @@ feti_status feti_solve_warm(feti_ctx* ctx, double* lambda_dev, double* alpha_dev
                             feti_solve_info* info);
 
 /* Adjoint of L = sum_i <W_i, F_i>: dtheta[e] = -<Z_i^T dK_e Z_i, W_i> with
- * Z_i = K_reg,i^{-1} B_i^T (derivative of the inverse, rho held fixed).
- * W_dev: per subdomain m_i x m_i row-major FP64 in B-row order, concatenated;
- * dtheta_dev: [sum nelem_i] device FP64.  Needs element data at create. */
+ * Z_i = K_reg,i^{-1} B_i^T (derivative of the inverse, rho held fixed), in
+ * FP64.  With K_reg = P^T L L^T P and L = L_u D (unit lower L_u):
+ * Z_i = P^T L_u^{-T} D^{-2} X_u and Y_i = Z_i W_i = P^T L_u^{-T} D^{-2} (X_u W_i)
+ * with X_u = L_u^{-1} P B_i^T from the pruned forward solve (recomputed here in
+ * FP64 from L), and dtheta_e = -sum_{a,b in e} (dK_e)_ab Y_i[b,:] . Z_i[a,:].
+ * Subdomains are processed in batches whose dense n_i x 2 m_i work arrays fit
+ * a device budget.  W_dev: per subdomain m_i x m_i row-major FP64 in B-row
+ * order, concatenated (W_i symmetric); dtheta_dev: [sum nelem_i] device FP64.
+ * Needs element data at create and a preceding feti_assemble.  Synchronises.
+ * Errors: FETI_ERR_ARG (no element data), FETI_ERR_STATE, FETI_ERR_ALLOC. */
 feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev);
+
+/* Weighted trace L = sum_i <W_i, F_i> of the assembled local operators (the
+ * loss whose gradient feti_adjoint returns).  W_dev as in feti_adjoint;
+ * L_dev: one device FP64 value, written (summed in a fixed order, so the
+ * result is reproducible).  Errors: FETI_ERR_ARG, FETI_ERR_STATE (before
+ * feti_assemble). */
+feti_status feti_weighted_trace(feti_ctx* ctx, const double* W_dev, double* L_dev);
 
 /* Copy F_i (m_i x m_i, row-major, B-row order, FP64) to host memory. */
 feti_status feti_get_F(feti_ctx* ctx, int32_t sub, double* out_host);
@@ -255,12 +276,18 @@ feti_status feti_analyse_lumped(const feti_problem* prob, int64_t* sizes, int32_
  * stream: cudaStream_t or NULL.  The call is synchronous (it waits for the
  *        stream).
  * Errors: FETI_ERR_ARG for m <= 0, m > FETI_STATIC_MAX_M or a NULL pointer;
- *        FETI_ERR_CUDA for a failed CUDA call.
+ *        FETI_ERR_CUDA for a failed CUDA call, and also, without launching
+ *        anything, when a CUDA error left by earlier work on the calling
+ *        thread is pending (it is not cleared, so its owner still sees it).
  * The first call on each device looks up the device addresses of the fixed
  * arrays (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the same arrays and leave the
- * last call's contents in them, so calls that overlap on the GPU (other
- * streams or host threads) race: order them. */
+ * before any stream capture.  CUDA loads this library's device code lazily, so
+ * the fixed arrays and the kernels become resident on a device at that first
+ * call: a caller that later reserves all free device memory for its own pool
+ * should make the first call before it does; from then on no call takes device
+ * memory.  All calls share the same arrays and leave the last call's contents
+ * in them, so calls that overlap on the GPU (other streams or host threads)
+ * race: order them. */
 feti_status feti_apply_one_static(int32_t m, int32_t fp32, const void* F_dev, const int32_t* map_dev,
                                   const double* p_dev, double* q_dev, void* stream);
 

@@ -25,7 +25,9 @@ dense NumPy/SciPy with no blocking or reordering beyond the definition:
   recovery        alpha (eq. 8), u = K^+ (f - B^T lambda) + R alpha (eq. 5)
   monolithic      K~ u~ = f~ with Dirichlet DOFs eliminated     (eq. 1)
   sensitivity     dL/dtheta_e = -<Z^T dK_e Z, W>, Z = K_reg^{-1} B^T
-                  (derivative of the inverse; rho held fixed)
+                  (derivative of the inverse; rho held fixed); exact loss
+                  differences for central differences, by the resolvent
+                  identity or by the Woodbury identity of a rank-k update
 
 Parity pins for each function live in tests/test_oracle_pins.py.
 """
@@ -372,6 +374,33 @@ def loss_difference(sub, W, Kp, Km, e, dcoef, K_ref) -> float:
     Zm = local_Z(sub, Km)
     dofs = sub.elem_dofs[e]
     return float(-np.sum(W * (Zp[dofs].T @ (dcoef * K_ref) @ Zm[dofs])))
+
+
+def loss_difference_lowrank(sub, W, cho, e, d_plus, d_minus, K_ref) -> float:
+    """L(K_+) - L(K_-) for L = <W, B K^{-1} B^T> with K_+- = K + d_+- U K_ref U^T
+    (U selects element e's DOFs), from ONE factorisation `cho` of K
+    (scipy cho_factor of K_reg, rho held fixed).  The Woodbury identity for a
+    low-rank update, (K + U C U^T)^{-1} = K^{-1} - K^{-1} U C (I + U^T K^{-1} U C)^{-1}
+    U^T K^{-1} (valid for a singular C such as an element stiffness), gives
+    B K_+-^{-1} B^T = F - Z_e M(d) Z_e^T with Z_e = B K^{-1} U (m x k) and
+    M(d) = d C (I + d S C)^{-1}, S = U^T K^{-1} U, so
+    L(K_+) - L(K_-) = -<W, Z_e (M(d_+) - M(d_-)) Z_e^T>.
+    The same number as loss_difference (two factorisations), at the cost of k
+    solves with an existing factor; no digits are lost to cancellation."""
+    dofs = np.asarray(sub.elem_dofs[e], dtype=np.int64)
+    k = dofs.size
+    E = np.zeros((sub.n, k))
+    E[dofs, np.arange(k)] = 1.0
+    X = sla.cho_solve(cho, E)                    # K^{-1} U
+    S = X[dofs, :]
+    Ze = sub.B_sign[:, None] * X[sub.B_dof, :]   # B K^{-1} U
+    C = np.asarray(K_ref, dtype=np.float64)
+
+    def M(d):
+        return d * C @ np.linalg.inv(np.eye(k) + d * S @ C)
+
+    D = M(d_plus) - M(d_minus)
+    return float(-np.sum(W * (Ze @ D @ Ze.T)))
 
 
 def perturbed_K_reg(sub, e, dtheta_coef, K_ref, rho):

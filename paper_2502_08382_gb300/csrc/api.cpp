@@ -44,6 +44,18 @@ void* dalloc(feti_ctx* c, size_t bytes) {
   return p;
 }
 
+void dfree(feti_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < c->bufs.size(); ++k)
+    if (c->bufs[k].p == p) {
+      if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_ctx);
+      else if (!c->opt.dev_alloc) cudaFree(p);
+      c->device_bytes -= c->bufs[k].bytes;
+      c->bufs.erase(c->bufs.begin() + (long)k);
+      return;
+    }
+}
+
 }  // namespace feti
 
 namespace {
@@ -118,11 +130,21 @@ void copy_sub(const feti_subdomain& s, SubHost& h, int idx) {
   h.nelem = s.nelem;
   h.edofs = s.edofs;
   if (s.nelem > 0) {
-    need(s.elem_dofs && s.dKe_ref && s.dKe_scale && s.edofs > 0, "element data incomplete");
+    need(s.elem_dofs && s.edofs > 0 && (s.dKe || (s.dKe_ref && s.dKe_scale)), "element data incomplete");
     need(s.edofs <= 32, "elements with more than 32 DOFs are not supported");
+    const size_t ee = (size_t)s.edofs * s.edofs;
     h.elem_dofs.assign(s.elem_dofs, s.elem_dofs + (size_t)s.nelem * s.edofs);
-    h.dKe_ref.assign(s.dKe_ref, s.dKe_ref + (size_t)s.edofs * s.edofs);
-    h.dKe_scale.assign(s.dKe_scale, s.dKe_scale + s.nelem);
+    if (s.dKe) {
+      // one derivative matrix per element
+      h.dKe.assign(s.dKe, s.dKe + (size_t)s.nelem * ee);
+      h.dKe_scale.assign(s.nelem, 1.0);
+      h.dk_stride = (int64_t)ee;
+    } else {
+      // compact form: a shared reference matrix times a per-element scale
+      h.dKe.assign(s.dKe_ref, s.dKe_ref + ee);
+      h.dKe_scale.assign(s.dKe_scale, s.dKe_scale + s.nelem);
+      h.dk_stride = 0;
+    }
     for (auto v : h.elem_dofs) need(v >= 0 && v < s.n, "element DOF out of range");
   }
 }
@@ -383,7 +405,7 @@ void build(feti_ctx* c) {
     c->elem_dk_ofs.push_back((int64_t)eldk.size());
     c->elem_dofs_ofs.push_back((int64_t)eldofs.size());
     eldofs.insert(eldofs.end(), s.elem_dofs.begin(), s.elem_dofs.end());
-    eldk.insert(eldk.end(), s.dKe_ref.begin(), s.dKe_ref.end());
+    eldk.insert(eldk.end(), s.dKe.begin(), s.dKe.end());
     elsc.insert(elsc.end(), s.dKe_scale.begin(), s.dKe_scale.end());
     c->nmax = std::max(c->nmax, s.n);
     chol += P.chol_flops;
@@ -817,6 +839,8 @@ feti_status feti_assemble(feti_ctx* ctx) {
     throw CudaError("internal: a work list of the assembly or apply is missing");
   CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  if (!ctx->d_X)  // released after the previous assembly (recompute_X)
+    ctx->d_X = dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * (ctx->fp32 ? 4 : 8));
   if (ctx->precond) {
     // the lumped preconditioner's values from the current K (they change with feti_update_values)
     launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val, st);
@@ -830,10 +854,13 @@ feti_status feti_assemble(feti_ctx* ctx) {
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   {
-    // mixed precision: the TRSM panel updates run on the tensor cores in the SYRK's format
-    const int tcmode = !ctx->fp32 ? 0 : (ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 2 : 1);
+    // mixed precision: the TRSM panel updates run on the tensor cores in split-bf16 in both mixed modes
+    // (about 16 operand bits, FP32 accumulation), so that X_i is FP32-accurate and the TF32 mode's extra
+    // error is that of its SYRK alone; in the TF32 mode X_i is rounded to TF32 for that SYRK
+    const int tcmode = ctx->fp32 ? 2 : 0;
+    const int tf32_out = ctx->fp32 && ctx->opt.prec == FETI_PREC_TF32 ? 1 : 0;
     launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
-                ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, tcmode, ctx->d_status, st);
+                ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, tcmode, tf32_out, ctx->d_status, st);
   }
   // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
   launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, st);
@@ -856,6 +883,11 @@ feti_status feti_assemble(feti_ctx* ctx) {
   }
   CK(cudaEventRecord(ctx->ev[4], st));
   CK(cudaStreamSynchronize(st));
+  if (ctx->opt.recompute_X) {
+    // X_i is an intermediate of the assembly: with recompute_X its memory goes back to the allocator
+    dfree(ctx, ctx->d_X);
+    ctx->d_X = nullptr;
+  }
   float a, b, cc, d;
   CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
   CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));

@@ -387,38 +387,186 @@ feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev)
   GUARD();
   if (!W_dev || !dtheta_dev) return set_error(ctx, FETI_ERR_ARG, "feti_adjoint: W_dev and dtheta_dev are required");
   if (ctx->nelem_total == 0) return set_error(ctx, FETI_ERR_ARG, "feti_adjoint: no element data given at create");
+  if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_adjoint before feti_assemble");
   try {
     cudaStream_t st = ctx->st;
-    size_t zmax = 0;
-    for (auto& s : ctx->subs)
-      if (s.nelem > 0) zmax = std::max(zmax, (size_t)s.n * s.m);
-    if (!ctx->d_Z) {
-      ctx->d_Z = (double*)dalloc(ctx, std::max<size_t>(zmax, 1) * 8);
-      ctx->d_Y = (double*)dalloc(ctx, std::max<size_t>(zmax, 1) * 8);
-    }
-    int64_t woff = 0;
-    for (int i = 0; i < ctx->nsub; ++i) {
-      const auto& s = ctx->subs[i];
-      const int n = s.n, m = s.m;
-      if (s.nelem > 0 && m > 0) {
-        // Z = K_reg^{-1} B^T (rows: original DOFs, columns: B rows), FP64, recomputed here
-        queue_reset(ctx, 33);
-        launch_implicit(3, ctx->P, ctx->d_ident + i, m, ctx->d_queue + 33, nullptr, nullptr, nullptr, ctx->d_Z,
-                        ctx->d_uws, ctx->ustride, ctx->nmax, ctx->impl_maxf, ctx->grid_impl, ctx->impl_smem, st);
-        // Y = Z W_i
-        launch_gemm64(n, m, m, 1.0, ctx->d_Z, m, 0, W_dev + woff, m, 0, 0.0, ctx->d_Y, m, 0, 0, st);
-        // dtheta_e = -scale_e <dK_ref, (Y Z^T)_e>
-        launch_elem_contract(ctx->d_eldofs + ctx->elem_dofs_ofs[i], s.nelem, s.edofs, ctx->d_eldk + ctx->elem_dk_ofs[i],
-                             ctx->d_elsc + ctx->elem_ofs[i], ctx->d_Z, ctx->d_Y, m, dtheta_dev + ctx->elem_ofs[i], st);
-        ctx->stats.launches += 3;
-      } else if (s.nelem > 0) {
-        CKS(cudaMemsetAsync(dtheta_dev + ctx->elem_ofs[i], 0, (size_t)s.nelem * 8, st));
-      }
-      woff += (int64_t)m * m;
-    }
+    const int ns = ctx->nsub;
+    // X_u = L_u^{-1} P B^T in FP64 for every subdomain: the pruned forward solve with the unit-lower factor
+    if (!ctx->d_Xu) ctx->d_Xu = (double*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 8);
+    queue_reset(ctx, 40);
+    launch_trsm(ctx->P, ctx->d_trsm_order, ns, ctx->d_queue + 40, ctx->d_Xu, false, ctx->d_ws, ctx->ws_stride,
+                ctx->rhs_front, ctx->grid_trsm, 0, 0, ctx->d_status, st, 1);
+    ctx->stats.launches += 1;
     CKS(cudaGetLastError());
+    // batches of subdomains whose dense V (n x 2 m_pad) and sorted W (m_pad^2) fit the work budget
+    size_t free_b = 0, total_b = 0;
+    CKS(cudaMemGetInfo(&free_b, &total_b));
+    const double cap = ctx->opt.adjoint_work_bytes > 0
+                           ? (double)ctx->opt.adjoint_work_bytes
+                           : std::min<double>(24.0 * (1 << 30), 0.45 * (double)(free_b + ctx->adj_work_bytes));
+    const int64_t budget = std::max<int64_t>((int64_t)(cap / 8), 1);
+    std::vector<int64_t> woff(ns + 1, 0);
+    for (int i = 0; i < ns; ++i) woff[i + 1] = woff[i] + (int64_t)ctx->subs[i].m * ctx->subs[i].m;
+    std::vector<std::vector<AdjBatch>> batches;
+    {
+      std::vector<AdjBatch> cur;
+      int64_t used = 0;
+      for (int i = 0; i < ns; ++i) {
+        const auto& s = ctx->subs[i];
+        if (s.nelem == 0) continue;
+        if (s.m == 0) {
+          CKS(cudaMemsetAsync(dtheta_dev + ctx->elem_ofs[i], 0, (size_t)s.nelem * 8, st));
+          continue;
+        }
+        const auto& I = ctx->info[i];
+        const int64_t need = (int64_t)s.n * 2 * I.m_pad + (int64_t)I.m_pad * I.m_pad;
+        if (!cur.empty() && used + need > budget) {
+          batches.push_back(cur);
+          cur.clear();
+          used = 0;
+        }
+        AdjBatch e{};
+        e.sub = i;
+        e.m = s.m;
+        e.m_pad = I.m_pad;
+        e.edofs = s.edofs;
+        e.nelem = s.nelem;
+        e.qcol = I.qcol;
+        e.w_src = woff[i];
+        e.v_ofs = used;
+        e.ws_ofs = used + (int64_t)s.n * 2 * I.m_pad;
+        e.el_dofs = ctx->elem_dofs_ofs[i];
+        e.el_dk = ctx->elem_dk_ofs[i];
+        e.el_out = ctx->elem_ofs[i];
+        e.dk_stride = s.dk_stride;
+        cur.push_back(e);
+        used += need;
+      }
+      if (!cur.empty()) batches.push_back(cur);
+    }
+    int64_t max_used = 0, max_nb = 0;
+    for (auto& b : batches) {
+      const AdjBatch& l = b.back();
+      max_used = std::max<int64_t>(max_used, l.ws_ofs + (int64_t)l.m_pad * l.m_pad);
+      max_nb = std::max<int64_t>(max_nb, (int64_t)b.size());
+    }
+    if (max_used * 8 > ctx->adj_work_bytes) {
+      dfree(ctx, ctx->d_adj_work);
+      ctx->d_adj_work = nullptr;
+      ctx->adj_work_bytes = 0;
+      ctx->d_adj_work = (double*)dalloc(ctx, (size_t)max_used * 8);
+      ctx->adj_work_bytes = max_used * 8;
+    }
+    if (max_nb > ctx->adj_batch_cap) {
+      dfree(ctx, ctx->d_adj_batch);
+      ctx->d_adj_batch = (AdjBatch*)dalloc(ctx, (size_t)max_nb * sizeof(AdjBatch));
+      ctx->adj_batch_cap = max_nb;
+    }
+    const int grid = ctx->nsm * 4;
+    for (auto& b : batches) {
+      const int nb = (int)b.size();
+      // work items: X_u W per (entry, active supernode, 64 own rows, kBuildCols columns), largest first;
+      // the backward solve per (entry, 64 columns), entries with the larger factor first
+      std::vector<std::pair<double, int4>> bi;
+      std::vector<std::pair<double, int2>> si;
+      int max_mpad = 0, max_nel = 0;
+      for (int e = 0; e < nb; ++e) {
+        const auto& s = ctx->subs[b[e].sub];
+        const auto& pat = ctx->pats[s.pat];
+        const auto& bp = ctx->bps[s.bp];
+        const int mp = b[e].m_pad;
+        max_mpad = std::max(max_mpad, mp);
+        max_nel = std::max(max_nel, b[e].nelem);
+        for (int a = 0; a < (int)bp.act.size(); ++a) {
+          const int sn = bp.act[a];
+          const int w = pat.sn_w[sn], J = bp.je[sn] - bp.jb[sn];
+          for (int k0 = 0; k0 < w; k0 += kT)
+            for (int cg = 0; cg < mp; cg += kBuildCols)
+              bi.push_back({(double)std::min(kT, w - k0) * J * std::min(kBuildCols, mp - cg),
+                            make_int4(e, a, k0, cg)});
+        }
+        for (int cb = 0; cb < 2 * mp / 64; ++cb) si.push_back({pat.nnzL, make_int2(e, cb)});
+      }
+      std::stable_sort(bi.begin(), bi.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+      std::stable_sort(si.begin(), si.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+      std::vector<int4> bv;
+      std::vector<int2> sv;
+      bv.reserve(bi.size());
+      sv.reserve(si.size());
+      for (auto& x : bi) bv.push_back(x.second);
+      for (auto& x : si) sv.push_back(x.second);
+      if ((int64_t)bv.size() > ctx->adj_items4_cap) {
+        dfree(ctx, ctx->d_adj_items4);
+        ctx->d_adj_items4 = (int4*)dalloc(ctx, bv.size() * sizeof(int4));
+        ctx->adj_items4_cap = (int64_t)bv.size();
+      }
+      if ((int64_t)sv.size() > ctx->adj_items2_cap) {
+        dfree(ctx, ctx->d_adj_items2);
+        ctx->d_adj_items2 = (int2*)dalloc(ctx, sv.size() * sizeof(int2));
+        ctx->adj_items2_cap = (int64_t)sv.size();
+      }
+      // the host vectors outlive the copies: the stream is synchronised at the end of each batch
+      CKS(cudaMemcpyAsync(ctx->d_adj_batch, b.data(), nb * sizeof(AdjBatch), cudaMemcpyHostToDevice, st));
+      if (!bv.empty())
+        CKS(cudaMemcpyAsync(ctx->d_adj_items4, bv.data(), bv.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+      CKS(cudaMemcpyAsync(ctx->d_adj_items2, sv.data(), sv.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+      const AdjBatch& l = b.back();
+      CKS(cudaMemsetAsync(ctx->d_adj_work, 0, (size_t)(l.ws_ofs + (int64_t)l.m_pad * l.m_pad) * 8, st));
+      launch_adj_wsort(ctx->d_adj_batch, nb, W_dev, ctx->P.colperm, ctx->d_adj_work, max_mpad, st);
+      queue_reset(ctx, 41);
+      launch_adj_build(ctx->P, ctx->d_adj_batch, ctx->d_adj_items4, (int)bv.size(), ctx->d_queue + 41, ctx->d_Xu,
+                       ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)bv.size())), st);
+      queue_reset(ctx, 42);
+      launch_adj_bsolve(ctx->P, ctx->d_adj_batch, ctx->d_adj_items2, (int)sv.size(), ctx->d_queue + 42,
+                        ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)sv.size())), st);
+      launch_adj_contract(ctx->P, ctx->d_adj_batch, nb, max_nel, ctx->d_eldofs, ctx->d_eldk, ctx->d_elsc,
+                          ctx->d_adj_work, dtheta_dev, st);
+      ctx->stats.launches += 4;
+      CKS(cudaGetLastError());
+      CKS(cudaStreamSynchronize(st));
+    }
     CKS(cudaStreamSynchronize(st));
+    int status = 0;
+    CKS(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & kStatTimeout) return set_error(ctx, FETI_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (ctx->opt.recompute_X) {
+      // HBM is short: nothing of the adjoint is kept between calls
+      dfree(ctx, ctx->d_Xu);
+      ctx->d_Xu = nullptr;
+      dfree(ctx, ctx->d_adj_work);
+      ctx->d_adj_work = nullptr;
+      ctx->adj_work_bytes = 0;
+    }
     return FETI_OK;
+  } catch (std::bad_alloc&) {
+    return set_error(ctx, FETI_ERR_ALLOC, "feti_adjoint: device allocation failed");
+  } catch (std::exception& e) {
+    return set_error(ctx, FETI_ERR_CUDA, e.what());
+  }
+}
+
+feti_status feti_weighted_trace(feti_ctx* ctx, const double* W_dev, double* L_dev) {
+  GUARD();
+  if (!W_dev || !L_dev) return set_error(ctx, FETI_ERR_ARG, "feti_weighted_trace: W_dev and L_dev are required");
+  if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_weighted_trace before feti_assemble");
+  try {
+    cudaStream_t st = ctx->st;
+    if (!ctx->d_woff) {
+      std::vector<int64_t> woff(ctx->nsub, 0);
+      for (int i = 1; i < ctx->nsub; ++i) woff[i] = woff[i - 1] + (int64_t)ctx->subs[i - 1].m * ctx->subs[i - 1].m;
+      ctx->d_woff = (int64_t*)dalloc(ctx, woff.size() * sizeof(int64_t));
+      CKS(cudaMemcpyAsync(ctx->d_woff, woff.data(), woff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      ctx->d_wt_part = (double*)dalloc(ctx, (size_t)std::max(ctx->napply, 1) * 8);
+      CKS(cudaStreamSynchronize(st));
+    }
+    launch_weighted_trace(ctx->fp32, ctx->d_tdesc, ctx->napply, ctx->d_F, ctx->P.qmap, ctx->P.colsub,
+                          ctx->P.colperm, ctx->P.sub, ctx->d_woff, W_dev, ctx->d_wt_part, L_dev,
+                          std::max(1, std::min(ctx->napply, ctx->nsm * 8)), st);
+    ctx->stats.launches += 2;
+    CKS(cudaGetLastError());
+    return FETI_OK;
+  } catch (std::bad_alloc&) {
+    return set_error(ctx, FETI_ERR_ALLOC, "feti_weighted_trace: device allocation failed");
   } catch (std::exception& e) {
     return set_error(ctx, FETI_ERR_CUDA, e.what());
   }

@@ -22,7 +22,8 @@ struct SubHost {
   std::vector<double> R, f, coords;
   std::vector<int32_t> fix;
   std::vector<int32_t> elem_dofs;
-  std::vector<double> dKe_ref, dKe_scale;
+  std::vector<double> dKe, dKe_scale;  // per element (dk_stride = edofs^2) or one shared matrix (0)
+  int64_t dk_stride = 0;
   int pat = -1, bp = -1;
 };
 
@@ -140,8 +141,17 @@ struct feti_ctx {
   int* d_eldofs = nullptr;
   double* d_eldk = nullptr;
   double* d_elsc = nullptr;
-  double* d_Z = nullptr;
-  double* d_Y = nullptr;
+  double* d_Xu = nullptr;          // FP64 X_u = L_u^{-1} P B^T of every subdomain (adjoint)
+  double* d_adj_work = nullptr;    // batch work arrays of the adjoint (V and sorted W)
+  int64_t adj_work_bytes = 0;
+  feti::AdjBatch* d_adj_batch = nullptr;
+  int64_t adj_batch_cap = 0;
+  int4* d_adj_items4 = nullptr;
+  int64_t adj_items4_cap = 0;
+  int2* d_adj_items2 = nullptr;
+  int64_t adj_items2_cap = 0;
+  int64_t* d_woff = nullptr;       // per subdomain offset of W_i (weighted trace)
+  double* d_wt_part = nullptr;     // per tile partials of the weighted trace
   int64_t ndof = 0;
   int nmax = 0;
   double* d_R = nullptr;       // concatenated R_i (column-major n x d)
@@ -173,4 +183,5 @@ struct feti_ctx {
 namespace feti {
 feti_status set_error(feti_ctx* c, feti_status s, const std::string& msg);
 void* dalloc(feti_ctx* c, size_t bytes);
+void dfree(feti_ctx* c, void* p);  // release a buffer from dalloc (no-op for nullptr)
 }  // namespace feti

@@ -757,6 +757,9 @@ cudaError_t static_addresses(StaticAddrs& out) {
 
 template <typename TF>
 feti_status apply_one_static_t(int m, const TF* F, const int* map, const double* p, double* q, cudaStream_t st) {
+  // an error left pending by earlier work on this thread belongs to that work: report it without
+  // clearing it (so its owner still sees it), and launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return FETI_ERR_CUDA;
   const int nb = (m + kT - 1) / kT;
   const int m_pad = nb * kT;
   const int64_t ntile = (int64_t)nb * (nb + 1) / 2;

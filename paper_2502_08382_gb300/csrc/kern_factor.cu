@@ -567,7 +567,7 @@ __device__ bool panel_update_tc(TcState& tc, const double* Ls, int f, int w, int
 // the solve's precision T from L_bb), so the block solve is a small GEMM.
 template <typename T>
 __device__ bool solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T* Xs, int wp, T* W2, int J,
-                            TcState* tc, int tcmode) {
+                            TcState* tc, int tcmode, int unit) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
   const int r = f - w;
   auto Di = reinterpret_cast<T (*)[kNB + 1]>(&sm.B[0][0]);
@@ -577,7 +577,9 @@ __device__ bool solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
       int i = idx % kNB, j = idx / kNB;
       sm.D[i][j] = (i < nbk && j <= i) ? (T)Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
     }
-    if (tid < kNB) sm.dinv[tid] = tid < nbk ? (T)(1.0 / Ls[(int64_t)(kb + tid) * f + kb + tid]) : (T)0;
+    // unit: L is in unit-lower form (pivots folded out after the assembly), its stored diagonal is zero
+    if (tid < kNB)
+      sm.dinv[tid] = tid < nbk ? (unit ? (T)1 : (T)(1.0 / Ls[(int64_t)(kb + tid) * f + kb + tid])) : (T)0;
     __syncthreads();
     if (warp == 0) warp_tri_inverse<T>(sm.D, sm.dinv, Di, nbk);
     __syncthreads();
@@ -654,11 +656,21 @@ __device__ bool solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
   return true;
 }
 
-// tcmode (FP32 X only): 0 = SIMT panel updates, 1 = TF32 tensor cores, 2 = split-bf16 tensor cores
+// Round an FP32 value to TF32 (10 explicit mantissa bits), to nearest with ties away from zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// tcmode (FP32 X only): 0 = SIMT panel updates, 1 = TF32 tensor cores, 2 = split-bf16 tensor cores.
+// tf32_out (FP32 X only): round each finished X block to TF32, so that the TF32 SYRK that reads it
+// multiplies operands rounded to nearest (the tensor cores would otherwise drop the low 13 bits).
+// unit (FP64 X only): solve with the unit-lower L_u that the assembly leaves (X_u = L_u^{-1} P B^T).
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          T* X, T* ws, int64_t ws_stride, int64_t front_sz,
-                                                         int tcmode, int* status) {
+                                                         int tcmode, int tf32_out, int unit, int* status) {
   __shared__ SolveSmem<T> sm;
   __shared__ uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -733,8 +745,13 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
         }
       }
       __syncthreads();
-      if (!solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode)) break;
+      if (!solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit)) break;
       __syncthreads();
+      if constexpr (sizeof(T) == 4) {
+        // X_s is final here (the parent reads only the bottom rows W2)
+        if (tf32_out)
+          for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) Xs[idx] = round_tf32(Xs[idx]);
+      }
       if (P.sn_parent[gs] >= 0) {
         T* dst = stack + P.rhs_ofs[bs];
         for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) dst[idx] = W2[idx];
@@ -775,15 +792,16 @@ int chol_ctas_per_sm() {
 }
 
 void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
-                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int* status, cudaStream_t st) {
+                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
+                 cudaStream_t st, int unit) {
   if (fp32) {
     const int smem = tcmode > 0 ? (tcmode == 2 ? 2 : 1) * (kTcOpA + kTcOpB) + 1024 : 0;
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, (float*)X, (float*)ws, 2 * ws_stride,
-                                                     front_sz, tcmode, status);
+                                                     front_sz, tcmode, tf32_out, 0, status);
   } else {
     trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, order, nsub, queue, (double*)X, ws, ws_stride, front_sz, 0,
-                                                   status);
+                                                   0, unit, status);
   }
 }
 

@@ -355,54 +355,6 @@ __global__ void __launch_bounds__(256) unit_scale_kernel(DevPlan P, int nsub, do
   }
 }
 
-__global__ void __launch_bounds__(256) elem_contract_kernel(const int* edofs, int nelem, int ed, const double* dKref,
-                                                            const double* dscale, const double* Z, const double* Y,
-                                                            int m, double* g) {
-  __shared__ double Zs[32][kW + 1];
-  __shared__ double Ys[32][kW + 1];
-  __shared__ double red[8];
-  const int tid = threadIdx.x;
-  for (int e = blockIdx.x; e < nelem; e += gridDim.x) {
-    const int* dof = edofs + (int64_t)e * ed;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // entries (a, b) = tid + 256 q, a = idx / ed, b = idx % ed
-    for (int k0 = 0; k0 < m; k0 += kW) {
-      __syncthreads();
-      for (int idx = tid; idx < ed * kW; idx += 256) {
-        const int a = idx / kW, k = idx % kW;
-        const bool in = k0 + k < m;
-        Zs[a][k] = in ? Z[(int64_t)dof[a] * m + k0 + k] : 0.0;
-        Ys[a][k] = in ? Y[(int64_t)dof[a] * m + k0 + k] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int idx = tid + 256 * q;
-        if (idx < ed * ed) {
-          const int a = idx / ed, b = idx % ed;
-          double s = 0.0;
-#pragma unroll 8
-          for (int k = 0; k < kW; ++k) s += Ys[b][k] * Zs[a][k];
-          acc[q] += s;
-        }
-      }
-    }
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = tid + 256 * q;
-      if (idx < ed * ed) t += dKref[idx] * acc[q];
-    }
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if ((tid & 31) == 0) red[tid / 32] = t;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += red[w];
-      g[e] = -dscale[e] * s;
-    }
-  }
-}
-
 // q[l] = qi[c0] + qi[c1] - c[l]
 __global__ void gather_minus_c_kernel(const int* c0, const int* c1, int nlam, const double* qi, const double* c,
                                       double* q) {
@@ -641,12 +593,6 @@ inline int grid_for(int64_t n, int per = 256, int cap = 152 * 16) {
 }
 
 size_t implicit_smem(int nmax, int maxf) { return ((size_t)nmax + maxf + (kThreads / 32) * kWF) * 8; }
-
-void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKref, const double* dscale,
-                          const double* Z, const double* Y, int m, double* g, cudaStream_t st) {
-  if (nelem > 0)
-    elem_contract_kernel<<<std::min(nelem, 152 * 16), 256, 0, st>>>(edofs, nelem, ed, dKref, dscale, Z, Y, m, g);
-}
 
 void launch_implicit(int mode, const DevPlan& P, const int* order, int nsub, int* queue, const double* p,
                      const double* f, double* qi, double* u, double* uws, int64_t ustride, int nmax, int maxf,

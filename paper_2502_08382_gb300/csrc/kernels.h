@@ -11,7 +11,8 @@ void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, doubl
                  int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st);
 int chol_ctas_per_sm();
 void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
-                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int* status, cudaStream_t st);
+                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
+                 cudaStream_t st, int unit = 0);
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
                     int split, int* status, cudaStream_t st);
 size_t syrk_tc_smem(int split);
@@ -81,7 +82,16 @@ void launch_sub(const double* d, const double* q, double* r, int n, cudaStream_t
 void launch_add_Ralpha(const DevPlan& P, const int* dofsub, int64_t ndof, const double* R, const double* alpha,
                        double* u, cudaStream_t st);
 void launch_gemv(const double* A, const double* c, double* z, int D, double alpha, cudaStream_t st);
-void launch_elem_contract(const int* edofs, int nelem, int ed, const double* dKref, const double* dscale,
-                          const double* Z, const double* Y, int m, double* g, cudaStream_t st);
-
+// FP64 adjoint in batches of subdomains and the weighted trace (kern_adjoint.cu)
+void launch_adj_wsort(const AdjBatch* B, int nb, const double* W, const int* colperm, double* work, int max_mpad,
+                      cudaStream_t st);
+void launch_adj_build(const DevPlan& P, const AdjBatch* B, const int4* items, int nitems, int* queue,
+                      const double* Xu, double* work, int grid, cudaStream_t st);
+void launch_adj_bsolve(const DevPlan& P, const AdjBatch* B, const int2* items, int nitems, int* queue, double* work,
+                       int grid, cudaStream_t st);
+void launch_adj_contract(const DevPlan& P, const AdjBatch* B, int nb, int max_nelem, const int* eldofs,
+                         const double* eldk, const double* elsc, const double* work, double* g, cudaStream_t st);
+void launch_weighted_trace(bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
+                           const int* colsub, const int* colperm, const SubInfo* sub, const int64_t* woff,
+                           const double* W, double* part, double* out, int grid, cudaStream_t st);
 }  // namespace feti

@@ -32,7 +32,8 @@ class FetiSubdomain(C.Structure):
                 ("K_val", _f64p), ("m", C.c_int32), ("B_rowptr", _i64p), ("B_col", _i32p),
                 ("B_val", _f64p), ("B_lambda", _i32p), ("d", C.c_int32), ("R", _f64p), ("f", _f64p),
                 ("nfix", C.c_int32), ("fix_dofs", _i32p), ("coords", _f64p), ("nelem", C.c_int32),
-                ("edofs", C.c_int32), ("elem_dofs", _i32p), ("dKe_ref", _f64p), ("dKe_scale", _f64p)]
+                ("edofs", C.c_int32), ("elem_dofs", _i32p), ("dKe", _f64p), ("dKe_ref", _f64p),
+                ("dKe_scale", _f64p)]
 
 
 class FetiProblem(C.Structure):
@@ -49,7 +50,7 @@ class FetiOptions(C.Structure):
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
                 ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -75,7 +76,8 @@ class FetiStats(C.Structure):
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
            "feti_solve", "feti_solve_warm", "feti_adjoint", "feti_get_F", "feti_get_stats", "feti_last_error", "feti_destroy",
-           "feti_analyse", "feti_analyse_lumped", "feti_version", "feti_apply_one_static", "feti_set_profiling"]
+           "feti_analyse", "feti_analyse_lumped", "feti_version", "feti_apply_one_static", "feti_set_profiling",
+           "feti_weighted_trace"]
 
 _lib = None
 
@@ -97,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.feti_solve.argtypes = [vp, vp, vp, vp, C.POINTER(FetiSolveInfo)]
     lib.feti_solve_warm.argtypes = [vp, vp, vp, vp, C.POINTER(FetiSolveInfo)]
     lib.feti_adjoint.argtypes = [vp, vp, vp]
+    lib.feti_weighted_trace.argtypes = [vp, vp, vp]
     lib.feti_get_F.argtypes = [vp, C.c_int32, _f64p]
     lib.feti_get_stats.argtypes = [vp, C.POINTER(FetiStats)]
     lib.feti_last_error.argtypes = [vp]
@@ -128,7 +131,7 @@ def _ptr(a, ctype):
 class _Marshal:
     """Keeps the NumPy arrays behind a FetiProblem alive during feti_create."""
 
-    def __init__(self, problem, with_elements=False, unit_scale=False):
+    def __init__(self, problem, with_elements=False, unit_scale=False, per_element=False):
         self.keep = []
         subs = (FetiSubdomain * problem.nsub)()
         for i, s in enumerate(problem.subs):
@@ -154,9 +157,14 @@ class _Marshal:
                 sub.nelem = s.elem_dofs.shape[0]
                 sub.edofs = s.elem_dofs.shape[1]
                 sub.elem_dofs = _ptr(a(s.elem_dofs, np.int32), C.c_int32)
-                sub.dKe_ref = _ptr(a(problem.K_ref, np.float64), C.c_double)
                 scale = np.ones(s.elem_dofs.shape[0]) if unit_scale else s.elem_dcoef
-                sub.dKe_scale = _ptr(a(scale, np.float64), C.c_double)
+                if per_element:
+                    # one d K_e / d theta_e matrix per element (the general form of the ABI)
+                    dke = scale[:, None, None] * np.asarray(problem.K_ref)[None]
+                    sub.dKe = _ptr(a(dke, np.float64), C.c_double)
+                else:
+                    sub.dKe_ref = _ptr(a(problem.K_ref, np.float64), C.c_double)
+                    sub.dKe_scale = _ptr(a(scale, np.float64), C.c_double)
         self.subs = subs
         self.c = self._k(np.ascontiguousarray(problem.c, dtype=np.float64))
         self.prob = FetiProblem(problem.nsub, subs, problem.n_lambda, _ptr(self.c, C.c_double))
@@ -220,7 +228,8 @@ class FetiOperator:
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
                  precond: str = "none", leaf_dofs: int = 16, use_coords: bool = True,
-                 with_elements: bool = False, unit_scale: bool = False, torch_alloc: bool = True):
+                 with_elements: bool = False, unit_scale: bool = False, per_element: bool = False,
+                 recompute_X: bool = False, adjoint_work_bytes: int = 0, torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -243,6 +252,8 @@ class FetiOperator:
         opt.stream = C.c_void_p(self.stream.cuda_stream)
         opt.leaf_dofs = leaf_dofs
         opt.use_coords = 1 if use_coords else 0
+        opt.recompute_X = 1 if recompute_X else 0
+        opt.adjoint_work_bytes = int(adjoint_work_bytes)
         self._cb = None
         if torch_alloc:
             dev = self.device.index
@@ -260,7 +271,7 @@ class FetiOperator:
             self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
             opt.dev_alloc, opt.dev_free = self._cb
         self.opt = opt
-        m = _Marshal(problem, with_elements=with_elements, unit_scale=unit_scale)
+        m = _Marshal(problem, with_elements=with_elements, unit_scale=unit_scale, per_element=per_element)
         h = C.c_void_p()
         rc = self.lib.feti_create(C.byref(m.prob), C.byref(opt), C.byref(h))
         self.h = h
@@ -323,13 +334,24 @@ class FetiOperator:
         """dL/dtheta_e for L = sum_i <W_i, F_i> (feti_adjoint).  W: list of
         m_i x m_i arrays/tensors in B-row order, or one concatenated FP64 CUDA
         tensor.  Returns a CUDA FP64 tensor over all elements (subdomain order)."""
-        torch = self.torch
-        if isinstance(W, (list, tuple)):
-            W = torch.cat([torch.as_tensor(w, dtype=torch.float64).reshape(-1) for w in W]).to(self.device)
-        W = W.contiguous()
+        W = self._W_dev(W)
         nel = sum(s.elem_dofs.shape[0] for s in self.problem.subs)
         out = self._dvec(nel)
         self._check(self.lib.feti_adjoint(self.h, C.c_void_p(W.data_ptr()), C.c_void_p(out.data_ptr())))
+        return out
+
+    def _W_dev(self, W):
+        torch = self.torch
+        if isinstance(W, (list, tuple)):
+            W = torch.cat([torch.as_tensor(w, dtype=torch.float64).reshape(-1) for w in W]).to(self.device)
+        return W.contiguous()
+
+    def weighted_trace(self, W):
+        """L = sum_i <W_i, F_i> of the assembled F_i (feti_weighted_trace); W as in adjoint.
+        Returns a one-element FP64 CUDA tensor."""
+        W = self._W_dev(W)
+        out = self._dvec(1)
+        self._check(self.lib.feti_weighted_trace(self.h, C.c_void_p(W.data_ptr()), C.c_void_p(out.data_ptr())))
         return out
 
     def get_F(self, sub):
@@ -365,11 +387,12 @@ def _feti_weighted_trace():
     class FetiWeightedTrace(torch.autograd.Function):
         """L(coef) = sum_i <W_i, F_i(coef)>, K_e = coef_e K_ref per element.
 
-        forward re-assembles K_i from the element coefficients, runs
-        feti_assemble and forms L from the assembled F_i; backward maps
-        dL/dF_i = W_i to dL/dcoef_e with the FP64 adjoint kernel
-        (feti_adjoint, Z_i recomputed).  The operator must be created with
-        with_elements=True and unit_scale=True (dK_e/dcoef_e = K_ref)."""
+        forward sets the CSR values of K_i from the element coefficients
+        (finite-element assembly of the inputs), runs feti_assemble and forms
+        L on the device (feti_weighted_trace); backward maps dL/dF_i = W_i to
+        dL/dcoef_e with the FP64 adjoint kernel (feti_adjoint, X_i recomputed
+        from L_i).  The operator must be created with with_elements=True and
+        unit_scale=True (dK_e/dcoef_e = K_ref)."""
 
         @staticmethod
         def forward(ctx, coef, op, Ws):
@@ -381,13 +404,14 @@ def _feti_weighted_trace():
                 op.update_values(i, subdomain_K_values(op.problem, i, c[off:off + ne]))
                 off += ne
             op.assemble()
-            L = sum(float(np.sum(np.asarray(W) * op.get_F(i))) for i, W in enumerate(Ws))
-            ctx.op, ctx.Ws = op, Ws
-            return torch.tensor(L, dtype=torch.float64, device=coef.device)
+            Wd = op._W_dev(Ws)
+            L = op.weighted_trace(Wd)[0]
+            ctx.op, ctx.Wd = op, Wd
+            return L.to(coef.device)
 
         @staticmethod
         def backward(ctx, grad_out):
-            g = ctx.op.adjoint(ctx.Ws)
+            g = ctx.op.adjoint(ctx.Wd)
             return grad_out * g.to(grad_out.device), None, None
 
     return FetiWeightedTrace

@@ -463,19 +463,23 @@ def subdomain_K_values(problem: Problem, i: int, elem_coef: np.ndarray) -> np.nd
                        minlength=col.shape[0])
 
 
-def make_W(problem: Problem, seed: int = 0) -> List[np.ndarray]:
-    """Symmetric N(0,1) weights W_i (m_i x m_i): upper triangle incl. diagonal
-    drawn row by row from default_rng([seed, 3]) and mirrored."""
-    rng = np.random.default_rng([seed, 3])
-    out = []
-    for s in problem.subs:
-        m = s.m
-        iu = np.triu_indices(m)
-        W = np.zeros((m, m))
-        W[iu] = rng.normal(0.0, 1.0, size=iu[0].shape[0])
-        W = W + np.triu(W, 1).T
-        out.append(W)
-    return out
+def make_W_sub(m: int, seed: int, i: int) -> np.ndarray:
+    """Symmetric N(0,1) weight W_i (m x m) of subdomain i: upper triangle incl.
+    the diagonal drawn row by row from default_rng([seed, 3, i]) and mirrored
+    (one stream per subdomain, so any subset can be drawn on its own)."""
+    rng = np.random.default_rng([seed, 3, i])
+    iu = np.triu_indices(m)
+    W = np.zeros((m, m))
+    W[iu] = rng.normal(0.0, 1.0, size=iu[0].shape[0])
+    return W + np.triu(W, 1).T
+
+
+def make_W(problem: Problem, seed: int = 0, only=None) -> List[np.ndarray]:
+    """W_i of every subdomain (make_W_sub); with `only` (subdomain indices) the
+    others are zero matrices."""
+    keep = None if only is None else set(int(i) for i in only)
+    return [make_W_sub(s.m, seed, i) if keep is None or i in keep else np.zeros((s.m, s.m))
+            for i, s in enumerate(problem.subs)]
 
 
 def seeded_vector(n: int, seed: int, purpose: int = 7) -> np.ndarray:

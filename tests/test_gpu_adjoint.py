@@ -95,3 +95,59 @@ def test_autograd_function(torch_cuda):
         go = O.gradient_sub(s, Ws[i], P.K_ref)  # uses elem_dcoef = 3 rho^2
         assert np.linalg.norm(g[off:off + ne] - go) <= 1e-10 * np.linalg.norm(go)
         off += ne
+
+
+def test_adjoint_forms_batches_and_recompute(torch_cuda):
+    """The same gradient from (a) the compact dK_e = scale_e K_ref form, (b) one
+    dK_e matrix per element, (c) a work budget that forces one subdomain per
+    batch, and (d) recompute_X (X_i released after the assembly and after the
+    adjoint, recomputed from L_i): (a), (c), (d) bitwise (each output is formed
+    by the same arithmetic in the same order), (b) to rounding."""
+    from paper_2502_08382_gb300 import feti
+    P = _problem()
+    Ws = make_W(P, seed=3)
+    ref = feti.FetiOperator(P, prec="split_bf16", with_elements=True)
+    ref.assemble()
+    g_a = ref.adjoint(Ws).cpu().numpy()
+    g_a2 = ref.adjoint(Ws).cpu().numpy()
+    ref.close()
+    per = feti.FetiOperator(P, prec="split_bf16", with_elements=True, per_element=True)
+    per.assemble()
+    g_b = per.adjoint(Ws).cpu().numpy()
+    per.close()
+    one = feti.FetiOperator(P, prec="split_bf16", with_elements=True, adjoint_work_bytes=1)
+    one.assemble()
+    g_c = one.adjoint(Ws).cpu().numpy()
+    one.close()
+    rec = feti.FetiOperator(P, prec="split_bf16", with_elements=True, recompute_X=True)
+    rec.assemble()
+    F0 = rec.get_F(2)
+    rec.assemble()  # X_i re-allocated and recomputed
+    assert np.array_equal(rec.get_F(2), F0)
+    g_d = rec.adjoint(Ws).cpu().numpy()
+    g_d2 = rec.adjoint(Ws).cpu().numpy()
+    rec.close()
+    assert np.array_equal(g_a, g_a2)
+    assert np.array_equal(g_a, g_c)
+    assert np.array_equal(g_a, g_d) and np.array_equal(g_a, g_d2)
+    assert np.linalg.norm(g_b - g_a) <= 1e-13 * np.linalg.norm(g_a)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_weighted_trace_matches_oracle(torch_cuda, prec):
+    """feti_weighted_trace against sum_i <W_i, F_i> of the oracle's F_i; the bar is
+    sum_i ||W_i||_F ||F_i||_F times the F bar of the precision."""
+    from bounds import F_bar
+    from paper_2502_08382_gb300 import feti
+    P = _problem()
+    Ws = make_W(P, seed=4)
+    op = feti.FetiOperator(P, prec=prec)
+    op.assemble()
+    L = op.weighted_trace(Ws).item()
+    L2 = op.weighted_trace(Ws).item()
+    op.close()
+    Fs = [O.local_F(s) for s in P.subs]
+    Lo = sum(float(np.sum(W * F)) for W, F in zip(Ws, Fs))
+    bar = sum(np.linalg.norm(W) * np.linalg.norm(F) * F_bar(prec, F, s.n) for W, F, s in zip(Ws, Fs, P.subs))
+    assert L == L2
+    assert abs(L - Lo) <= bar, (L, Lo, bar)

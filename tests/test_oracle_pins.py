@@ -213,7 +213,11 @@ def test_pcpg_invariants(cfg1):
 
 def test_gradient_vs_central_fd(tiny_el):
     """dL/drho_e from -<Z^T dK_e Z, W> against central differences
-    (h = 1e-6) of L = <W_i, F_i> with rho_pen frozen."""
+    (h = 1e-6) of L = <W_i, F_i> with rho_pen frozen.  The numerator
+    L(rho + h) - L(rho - h) is taken through the resolvent identity
+    (loss_difference, pinned against the plain difference below): subtracting
+    two loss values of size ~1e2-1e5 loses about seven digits at h = 1e-6,
+    which leaves the plain quotient only ~1e-6 accurate."""
     P = tiny_el
     Ws = make_W(P, seed=0)
     rng = np.random.default_rng([0, 4])
@@ -227,8 +231,11 @@ def test_gradient_vs_central_fd(tiny_el):
             hh = 1e-6
             Kp = O.perturbed_K_reg(s, e, (th + hh) ** 3 - th ** 3, P.K_ref, rho)
             Km = O.perturbed_K_reg(s, e, (th - hh) ** 3 - th ** 3, P.K_ref, rho)
-            fd = (O.loss_sub(s, Ws[si], Kp) - O.loss_sub(s, Ws[si], Km)) / (2 * hh)
+            dc = (th + hh) ** 3 - (th - hh) ** 3
+            fd = O.loss_difference(s, Ws[si], Kp, Km, e, dc, P.K_ref) / (2 * hh)
             assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd))
+            plain = (O.loss_sub(s, Ws[si], Kp) - O.loss_sub(s, Ws[si], Km)) / (2 * hh)
+            assert abs(plain - g[k]) <= 1e-4 * max(1.0, abs(plain))
 
 
 def test_loss_difference_identity(tiny_el):
@@ -246,6 +253,29 @@ def test_loss_difference_identity(tiny_el):
     a = O.loss_difference(s, Ws[3], Kp, Km, e, 2 * dc, P.K_ref)
     b = O.loss_sub(s, Ws[3], Kp) - O.loss_sub(s, Ws[3], Km)
     assert abs(a - b) <= 1e-9 * abs(b)
+
+
+def test_loss_difference_lowrank_matches_two_factorisations(tiny_el):
+    """The Woodbury form (one factorisation, element-rank update) gives the same
+    L(K+) - L(K-) as the resolvent form with two factorisations, at a large step
+    (where both are checked against the plain difference) and at h = 1e-6 in
+    rho_e with E_e = rho_e^3 (the central-difference step), on elements of
+    several subdomains."""
+    import scipy.linalg as sla
+    P = tiny_el
+    Ws = make_W(P, seed=2)
+    for si, e in ((3, 5), (0, 0), (7, 11)):
+        s = P.subs[si]
+        rho = O.rho_pen(O.K_dense(s))
+        cho = sla.cho_factor(O.K_reg(s), lower=True)
+        th = s.elem_coef[e] ** (1.0 / 3.0)
+        for dp, dm in ((0.05 * s.elem_coef[e], -0.05 * s.elem_coef[e]),
+                       ((th + 1e-6) ** 3 - th ** 3, (th - 1e-6) ** 3 - th ** 3)):
+            Kp = O.perturbed_K_reg(s, e, dp, P.K_ref, rho)
+            Km = O.perturbed_K_reg(s, e, dm, P.K_ref, rho)
+            a = O.loss_difference(s, Ws[si], Kp, Km, e, dp - dm, P.K_ref)
+            b = O.loss_difference_lowrank(s, Ws[si], cho, e, dp, dm, P.K_ref)
+            assert abs(a - b) <= 1e-9 * abs(a), (si, e, a, b)
 
 
 # ------------------------------------------------------------- paper's printed numbers
