@@ -138,6 +138,8 @@ typedef struct {
   /* autotuner choice for the apply (after the first feti_assemble) */
   int32_t apply_variant, apply_grid;  /* tile-kernel variant (0-2: register batches of 4, 8, 16 loads;
                                          3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
+  /* autotuner choice for the pruned TRSM (after the first feti_assemble) */
+  int32_t trsm_cols;          /* sorted columns per CTA work item (0: a whole subdomain per item) */
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;

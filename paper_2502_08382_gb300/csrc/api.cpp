@@ -583,7 +583,11 @@ void build(feti_ctx* c) {
   CK(cudaGetDeviceProperties(&prop, dev));
   c->nsm = prop.multiProcessorCount;
   c->grid_chol = std::min(ns, c->nsm * chol_ctas_per_sm());
-  c->grid_trsm = std::min(ns, c->nsm * 3);
+  {
+    int64_t max_items = 0;  // the finest TRSM work split (128 columns per item)
+    for (auto& sh : c->subs) max_items += std::max(1, (sh.m + 127) / 128);
+    c->grid_trsm = (int)std::min<int64_t>(max_items, c->nsm * 3);
+  }
   c->chol_front = max_cf;
   c->rhs_front = max_rf;
   c->chol_stack = max_chol;
@@ -694,6 +698,21 @@ void build(feti_ctx* c) {
   c->d_status = (int*)dalloc(c, sizeof(int));
   c->d_chol_order = upload(c, order);
   c->d_trsm_order = upload(c, order_t);
+  {
+    // TRSM work items: a whole subdomain per CTA, or blocks of cw sorted columns (the columns of X are
+    // independent); the autotuner times each at the first assembly
+    for (int cw : {0, 1024, 512, 256, 128}) {
+      if (cw > 0 && cw >= c->m_max) continue;
+      std::vector<int2> it;
+      for (int si : order_t) {
+        const int m = c->subs[si].m;
+        if (cw == 0 || m <= cw) it.push_back(make_int2(si, 0));
+        else
+          for (int ca = 0; ca < m; ca += cw) it.push_back(make_int2(si, ca));
+      }
+      c->trsm_cands.push_back({cw, upload(c, it), (int)it.size(), 0.0});
+    }
+  }
   c->d_impl_order = upload(c, order_i);
   c->d_syrk_items = upload(c, syi);
   {
@@ -837,45 +856,86 @@ feti_status feti_assemble(feti_ctx* ctx) {
   if ((ctx->nsyrk2 > 0 && !ctx->d_syrk2_items) || (ctx->nsyrk > 0 && !ctx->d_syrk_items) || !ctx->d_tdesc ||
       !ctx->d_blocks || ctx->apply_cands.empty())
     throw CudaError("internal: a work list of the assembly or apply is missing");
-  CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), st));
-  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   if (!ctx->d_X)  // released after the previous assembly (recompute_X)
     ctx->d_X = dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * (ctx->fp32 ? 4 : 8));
-  if (ctx->precond) {
-    // the lumped preconditioner's values from the current K (they change with feti_update_values)
-    launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val, st);
-    ctx->stats.launches += 1;
-  }
-  CK(cudaEventRecord(ctx->ev[0], st));
-  launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride, ctx->chol_front,
-              ctx->chol_stack,
-              ctx->grid_chol, ctx->d_status, st);
-  ctx->stats.launches += 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[1], st));
-  {
-    // mixed precision: the TRSM panel updates run on the tensor cores in split-bf16 in both mixed modes
-    // (about 16 operand bits, FP32 accumulation), so that X_i is FP32-accurate and the TF32 mode's extra
-    // error is that of its SYRK alone; in the TF32 mode X_i is rounded to TF32 for that SYRK
-    const int tcmode = ctx->fp32 ? 2 : 0;
-    const int tf32_out = ctx->fp32 && ctx->opt.prec == FETI_PREC_TF32 ? 1 : 0;
-    launch_trsm(ctx->P, ctx->d_trsm_order, ctx->nsub, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
-                ctx->ws_stride, ctx->rhs_front, ctx->grid_trsm, tcmode, tf32_out, ctx->d_status, st);
-  }
-  // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
-  launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, st);
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[2], st));
-  if (ctx->fp32) {
-    int split = ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 1 : 0;
-    launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, (float*)ctx->d_F,
-                   std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split, ctx->d_status, st);
+  // mixed precision: the TRSM panel updates run on the tensor cores in split-bf16 in both mixed modes
+  // (about 16 operand bits, FP32 accumulation), so that X_i is FP32-accurate and the TF32 mode's extra
+  // error is that of its SYRK alone; in the TF32 mode X_i is rounded to TF32 for that SYRK
+  const int tcmode = ctx->fp32 ? 2 : 0;
+  const int tf32_out = ctx->fp32 && ctx->opt.prec == FETI_PREC_TF32 ? 1 : 0;
+  auto run_trsm = [&](const feti_ctx::TrsmCand& tc, cudaStream_t s2) {
+    CK(cudaMemsetAsync(ctx->d_queue + 16, 0, sizeof(int), s2));
+    launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
+                ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), tcmode, tf32_out,
+                ctx->d_status, s2);
+  };
+  // the numeric phase as one sequence of launches (recorded once into a CUDA graph, see below)
+  auto enqueue = [&](cudaStream_t s2, unsigned evf) {
+    CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), s2));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s2));
+    if (ctx->precond)
+      // the lumped preconditioner's values from the current K (they change with feti_update_values)
+      launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val,
+                           s2);
+    CK(cudaEventRecordWithFlags(ctx->ev[0], s2, evf));
+    launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride,
+                ctx->chol_front, ctx->chol_stack, ctx->grid_chol, ctx->d_status, s2);
+    CK(cudaEventRecordWithFlags(ctx->ev[1], s2, evf));
+    if (!ctx->trsm_tuned) {
+      // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)
+      for (auto& tc : ctx->trsm_cands) {
+        CK(cudaEventRecord(ctx->ev[5], s2));
+        run_trsm(tc, s2);
+        CK(cudaEventRecord(ctx->ev[6], s2));
+        CK(cudaEventSynchronize(ctx->ev[6]));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[6]));
+        tc.ms = ms;
+      }
+      ctx->trsm_pick = 0;
+      for (size_t k = 1; k < ctx->trsm_cands.size(); ++k)
+        if (ctx->trsm_cands[k].ms < ctx->trsm_cands[ctx->trsm_pick].ms) ctx->trsm_pick = (int)k;
+      ctx->trsm_tuned = true;
+      ctx->stats.trsm_cols = ctx->trsm_cands[ctx->trsm_pick].cw;
+      CK(cudaEventRecord(ctx->ev[1], s2));
+    }
+    run_trsm(ctx->trsm_cands[ctx->trsm_pick], s2);
+    // the implicit solves take L in unit-lower form; the TRSM above was its last user as L
+    launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
+    CK(cudaEventRecordWithFlags(ctx->ev[2], s2, evf));
+    if (ctx->fp32) {
+      int split = ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 1 : 0;
+      launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, (float*)ctx->d_F,
+                     std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split, ctx->d_status, s2);
+    } else {
+      launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
+                      std::min(ctx->nsyrk, ctx->nsm * 8), s2);
+    }
+    CK(cudaEventRecordWithFlags(ctx->ev[3], s2, evf));
+  };
+  ctx->stats.launches += ctx->precond ? 5 : 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
+  if (ctx->asm_exec && ctx->asm_X == ctx->d_X) {
+    CK(cudaGraphLaunch(ctx->asm_exec, st));
   } else {
-    launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
-                    std::min(ctx->nsyrk, ctx->nsm * 8), st);
+    enqueue(st, cudaEventRecordDefault);
+    CK(cudaGetLastError());
+    if (ctx->trsm_tuned) {
+      // later assemblies replay the same launches from a CUDA graph, captured on a private stream (the
+      // events become record nodes, so the phase times stay measured); a new X buffer needs a new graph
+      if (ctx->asm_exec) CK(cudaGraphExecDestroy(ctx->asm_exec));
+      ctx->asm_exec = nullptr;
+      if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+      enqueue(ctx->cap_st, cudaEventRecordExternal);
+      CK(cudaStreamEndCapture(ctx->cap_st, &gr));
+      cudaError_t e = cudaGraphInstantiate(&ctx->asm_exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) throw CudaError(std::string("assembly graph: ") + cudaGetErrorString(e));
+      ctx->asm_X = ctx->d_X;
+    }
   }
   CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[3], st));
   if (!ctx->coarse_ready) {
     // G = B R does not depend on the values of K: the coarse problem is set up once
     coarse_setup_entry(ctx);
@@ -1040,6 +1100,7 @@ void feti_destroy(feti_ctx* ctx) {
   if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
   if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  if (ctx->asm_exec) cudaGraphExecDestroy(ctx->asm_exec);
   for (auto e : ctx->pcg_ev) cudaEventDestroy(e);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   for (auto& b : ctx->bufs) {

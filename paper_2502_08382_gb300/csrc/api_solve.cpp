@@ -394,8 +394,11 @@ feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev)
     // X_u = L_u^{-1} P B^T in FP64 for every subdomain: the pruned forward solve with the unit-lower factor
     if (!ctx->d_Xu) ctx->d_Xu = (double*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 8);
     queue_reset(ctx, 40);
-    launch_trsm(ctx->P, ctx->d_trsm_order, ns, ctx->d_queue + 40, ctx->d_Xu, false, ctx->d_ws, ctx->ws_stride,
-                ctx->rhs_front, ctx->grid_trsm, 0, 0, ctx->d_status, st, 1);
+    {
+      const auto& tc = ctx->trsm_cands[ctx->trsm_pick];
+      launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 40, ctx->d_Xu, false, ctx->d_ws,
+                  ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), 0, 0, ctx->d_status, st, 1);
+    }
     ctx->stats.launches += 1;
     CKS(cudaGetLastError());
     // batches of subdomains whose dense V (n x 2 m_pad) and sorted W (m_pad^2) fit the work budget

@@ -69,6 +69,15 @@ struct feti_ctx {
   int* d_status = nullptr;    // [1]
   int* d_chol_order = nullptr;
   int* d_trsm_order = nullptr;
+  struct TrsmCand {
+    int cw;           // columns per work item (0: a whole subdomain)
+    int2* d_items;    // (subdomain, first column), subdomains by decreasing TRSM cost
+    int nitems;
+    double ms;
+  };
+  std::vector<TrsmCand> trsm_cands;  // autotuner candidates of the pruned TRSM
+  int trsm_pick = 0;
+  bool trsm_tuned = false;
   int* d_impl_order = nullptr;
   int2* d_syrk_items = nullptr;
   feti::TileDesc* d_tdesc = nullptr;
@@ -129,7 +138,9 @@ struct feti_ctx {
   double* h_sc = nullptr;      // pinned host scalars
   feti::PcgCtrl* d_ctrl = nullptr;  // PCPG control block
   feti::PcgCtrl* h_ctrl = nullptr;  // pinned host copy
-  cudaStream_t cap_st = nullptr;     // private stream on which a chunk of PCPG iterations is captured
+  cudaStream_t cap_st = nullptr;     // private stream on which CUDA graphs are captured
+  cudaGraphExec_t asm_exec = nullptr;  // the numeric assembly (Cholesky, TRSM, scaling, SYRK), replayed on st
+  void* asm_X = nullptr;             // the X buffer the assembly graph was captured with
   cudaGraphExec_t pcg_exec = nullptr;  // captured chunk of iterations (replayed on st)
   int pcg_chunk = 0;
   std::vector<cudaEvent_t> pcg_ev;  // 4 events per captured iteration (apply timing)

@@ -667,10 +667,14 @@ __device__ __forceinline__ float round_tf32(float x) {
 // tf32_out (FP32 X only): round each finished X block to TF32, so that the TF32 SYRK that reads it
 // multiplies operands rounded to nearest (the tensor cores would otherwise drop the low 13 bits).
 // unit (FP64 X only): solve with the unit-lower L_u that the assembly leaves (X_u = L_u^{-1} P B^T).
+// Work items (subdomain, first sorted column ca) cover the columns [ca, ca + cw) (cw = 0: all of them):
+// the columns of X are independent, so a subdomain's columns can be split over several CTAs.  Every
+// supernode then handles J_s restricted to the block; the restricted ranges nest like J_s itself.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int* order, int nsub, int* queue,
-                                                         T* X, T* ws, int64_t ws_stride, int64_t front_sz,
-                                                         int tcmode, int tf32_out, int unit, int* status) {
+__global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2* items, int nitems, int cw,
+                                                         int* queue, T* X, T* ws, int64_t ws_stride,
+                                                         int64_t front_sz, int tcmode, int tf32_out, int unit,
+                                                         int* status) {
   __shared__ SolveSmem<T> sm;
   __shared__ uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -707,8 +711,9 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
   }
   for (;;) {
     int it = pop_item(queue);
-    if (it >= nsub) break;
-    const int si = order[it];
+    if (it >= nitems) break;
+    const int si = items[it].x;
+    const int ca = items[it].y, cb = cw > 0 ? ca + cw : 0x7fffffff;
     const SubInfo S = P.sub[si];
     const double* L = P.L + S.L;
     T* Xsub = X + S.X;
@@ -717,9 +722,10 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
       const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
       const int wp = (w + 3) & ~3;
-      const int jb = P.jb[bs], je = P.je[bs], jo = P.jo[bs];
+      const int jb = max(P.jb[bs], ca), je = min(P.je[bs], cb), jo = max(P.jo[bs], ca);
       const int J = je - jb;
-      T* Xs = Xsub + P.Xofs[bs];
+      if (J <= 0) continue;  // no column of this block reaches s (nor any of its descendants)
+      T* Xs = Xsub + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp;
       for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) Xs[idx] = (T)0;
       for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) W2[idx] = (T)0;
       __syncthreads();
@@ -730,9 +736,9 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int*
       for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
         const int lc = P.ch_list[c];
         const int gc = S.sn0 + lc, bc = S.bsn0 + lc;
-        const int Jc = P.je[bc] - P.jb[bc];
+        const int jbc = max(P.jb[bc], ca), Jc = min(P.je[bc], cb) - jbc;
         if (Jc <= 0) continue;
-        const int rc = P.sn_r[gc], coff = P.jb[bc] - jb;
+        const int rc = P.sn_r[gc], coff = jbc - jb;
         const T* U = stack + P.rhs_ofs[bc];
         const int* rl = P.rel + P.rel_off[gc];
         // children own disjoint column ranges: no conflicts between them
@@ -791,17 +797,17 @@ int chol_ctas_per_sm() {
   return nb > 0 ? nb : 1;
 }
 
-void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
-                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
+void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
+                 double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
                  cudaStream_t st, int unit) {
   if (fp32) {
     const int smem = tcmode > 0 ? (tcmode == 2 ? 2 : 1) * (kTcOpA + kTcOpB) + 1024 : 0;
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, order, nsub, queue, (float*)X, (float*)ws, 2 * ws_stride,
-                                                     front_sz, tcmode, tf32_out, 0, status);
+    trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, (float*)X, (float*)ws,
+                                                     2 * ws_stride, front_sz, tcmode, tf32_out, 0, status);
   } else {
-    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, order, nsub, queue, (double*)X, ws, ws_stride, front_sz, 0,
-                                                   0, unit, status);
+    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, items, nitems, cw, queue, (double*)X, ws, ws_stride,
+                                                   front_sz, 0, 0, unit, status);
   }
 }
 

@@ -10,8 +10,9 @@ namespace feti {
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
                  int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st);
 int chol_ctas_per_sm();
-void launch_trsm(const DevPlan& P, const int* order, int nsub, int* queue, void* X, bool fp32, double* ws,
-                 int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
+// items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
+void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
+                 double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
                  cudaStream_t st, int unit = 0);
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
                     int split, int* status, cudaStream_t st);

@@ -68,7 +68,7 @@ class FetiStats(C.Structure):
                 ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double),
                 ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double),
-                ("apply_variant", C.c_int32), ("apply_grid", C.c_int32)]
+                ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
