@@ -174,7 +174,8 @@ APPLY_KERNELS = ["apply_tiles_kernel<{t}, 4>", "apply_tiles_kernel<{t}, 8>", "ap
 # its 4 x 4 x 4-subdomain copy (0.84 GB of tiles) scaled to the full 512 subdomains by the tile bytes (the
 # traffic is the tiles plus per-tile vector segments, both proportional).  The summaries are in profiles/.
 APPLY_TRAFFIC = {2: (138.71e6, "ncu, profiles/apply_tiles_workload2.md"),
-                 3: (None, "not captured")}
+                 3: (684.77e6 * 6750564216.0 / 678647544.0,
+                     "ncu on the 64-subdomain copy scaled by algorithmic bytes, profiles/apply_tiles_workload3.md")}
 
 
 def oracle_sample(P, nsample, reps):

@@ -106,6 +106,21 @@ typedef struct {
                                  W = (B B^T)^{-1}, rebuilt from K at every feti_assemble */
   int64_t adjoint_work_bytes; /* device work budget of one feti_adjoint batch (dense n_i x 2 m_i arrays
                                  of the subdomains in the batch); 0 = min(24 GiB, 45% of free memory) */
+  int32_t assembly_route;     /* how F_i is formed (Sec. III-IV):
+                                 0 = the SYRK path: nested-dissection ordering, pruned TRSM
+                                     X_i = L_i^{-1} P B_i^T, F_i = X_i^T X_i;
+                                 1 = Schur complement (eq. 13, the augmented-matrix route): the DOFs B_i
+                                     touches are ordered last as one root supernode, so eliminating the
+                                     interior forms their Schur complement S_i in the root front, the
+                                     root's factor is L_T with L_T L_T^T = S_i, and
+                                     F_i = (L_T^{-1} D_i)^T (L_T^{-1} D_i) (D_i: the signed B columns);
+                                     the same TRSM and SYRK kernels run on that single dense block;
+                                 2 = the TRSM path (Sec. IV, Table I): X_i = L_i^{-1} P B_i^T, then the
+                                     backward solve Z_i = P^T L_i^{-T} X_i on all m_i columns (FP64, in
+                                     batches like feti_adjoint) and F_i = B_i Z_i (the rows of Z_i at the
+                                     B DOFs), stored in the precision's tiles;
+                                 3 = autotuned: the first feti_assemble times route 0 against route 2 on
+                                     the problem and keeps the faster (feti_stats.assembly_route) */
 } feti_options;
 
 typedef struct {
@@ -140,6 +155,8 @@ typedef struct {
                                          3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
   /* autotuner choice for the pruned TRSM (after the first feti_assemble) */
   int32_t trsm_cols;          /* sorted columns per CTA work item (0: a whole subdomain per item) */
+  int32_t assembly_route;     /* route of the last feti_assemble (0 SYRK path, 1 Schur complement, 2 TRSM path) */
+  double route_ms[3];         /* route 3: time of the TRSM + SYRK (0) and of the TRSM path (2) at the first call */
 } feti_stats;
 
 typedef struct feti_ctx feti_ctx;
@@ -229,7 +246,9 @@ void feti_destroy(feti_ctx* ctx);
 /* Host-only symbolic analysis of one subdomain (no GPU needed): fills
  * info[0..15] = {n, nsn, max_front, max_width, nnzL, chol_flops, Lsize,
  * m, Xsize, trsm_flops, syrk_flops, ntile_contrib, chol_stack, rhs_stack,
- * nroots, 0} and, if perm_out is not NULL, the fill-reducing permutation
+ * nroots, nlast} (nlast: columns of the root supernode that holds the DOFs
+ * B touches when opt->assembly_route = 1, else 0) and, if perm_out is not
+ * NULL, the fill-reducing permutation
  * (perm_out[new] = old DOF).  sn_out, if not NULL (room for 4 n ints),
  * receives [nsn first columns..., nsn widths..., nsn parents (-1: root)...,
  * nsn counts of rows below the diagonal block...] of the supernodes in

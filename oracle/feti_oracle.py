@@ -18,8 +18,10 @@ dense NumPy/SciPy with no blocking or reordering beyond the definition:
   FETI residuals  K_i u_i + B_i^T lambda - f_i and B u - c     (eq. 3)
   projector       P = I - G (G^T G)^{-1} G^T                  (Sec. II)
   PCPG            Algorithm 1, lambda_I = G (G^T G)^{-1} e, M = I or a given
-                  matrix (the lumped M = sum_i B_i K_i B_i^T, and its B B^T
-                  scaled form, are provided; the paper leaves M open),
+                  matrix (the lumped M = sum_i B_i K_i B_i^T, its B B^T
+                  scaled form, and the scaled Dirichlet form with the Schur
+                  complements S_i of K_i onto the B-touched DOFs, are
+                  provided; the paper leaves M open),
                   optionally warm-started from
                   lambda_I + P lambda_g (Algorithm 2's next step)
   recovery        alpha (eq. 8), u = K^+ (f - B^T lambda) + R alpha (eq. 5)
@@ -213,6 +215,36 @@ def scaled_lumped_M(problem) -> np.ndarray:
     return W @ lumped_M(problem) @ W
 
 
+def schur_boundary(sub, K: np.ndarray | None = None):
+    """S_i = K_TT - K_TI K_II^{-1} K_IT, the Schur complement of the
+    unregularised K_i onto the DOFs T that B_i touches (I: the others), by a
+    dense LU solve.  Returns (T, S)."""
+    if K is None:
+        K = K_dense(sub)
+    T = np.unique(sub.B_dof)
+    I = np.setdiff1d(np.arange(sub.n), T)
+    S = K[np.ix_(T, T)].copy()
+    if I.size:
+        KTI = K[np.ix_(T, I)]
+        S -= KTI @ np.linalg.solve(K[np.ix_(I, I)], KTI.T)
+    return T, 0.5 * (S + S.T)
+
+
+def dirichlet_M(problem) -> np.ndarray:
+    """Dirichlet preconditioner with the B B^T scaling, M = W (sum_i B_i S~_i B_i^T) W,
+    W = (B B^T)^{-1}, S~_i = S_i on the DOFs B_i touches and zero elsewhere (the
+    paper leaves M open; this is the Dirichlet counterpart of scaled_lumped_M,
+    with the interior condensed instead of dropped).  Dense n_lambda x n_lambda."""
+    M = np.zeros((problem.n_lambda, problem.n_lambda))
+    for s in problem.subs:
+        T, S = schur_boundary(s)
+        lam = np.asarray(s.B_lambda, dtype=np.int64)
+        pos = np.searchsorted(T, s.B_dof)
+        np.add.at(M, (lam[:, None], lam[None, :]), s.B_sign[:, None] * s.B_sign[None, :] * S[np.ix_(pos, pos)])
+    W = np.linalg.inv(BBt(problem))
+    return W @ M @ W
+
+
 class Projector:
     """P = I - G (G^T G)^{-1} G^T (Sec. II)."""
 
@@ -312,7 +344,8 @@ def feti_solve(problem, tol=1e-10, maxit=5000, lam_guess=None, precond=None):
     G = G_matrix(problem)
     d = d_vector(problem, Krs)
     e = e_vector(problem)
-    M = scaled_lumped_M(problem) if precond == "lumped" else None
+    M = (scaled_lumped_M(problem) if precond == "lumped" else dirichlet_M(problem) if precond == "dirichlet"
+         else None)
     lam, its, info = pcpg(problem, Fs, tol=tol, maxit=maxit, G=G, d=d, e=e, lam_guess=lam_guess, M=M)
     alpha = alpha_from_lambda(problem, Fs, lam, info["P"], d)
     us = primal_solution(problem, lam, alpha, Krs)

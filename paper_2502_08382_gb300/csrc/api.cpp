@@ -177,12 +177,23 @@ void build(feti_ctx* c) {
   using clk = std::chrono::steady_clock;
   auto t0 = clk::now();
   const int ns = c->nsub;
-  // ---- distinct patterns
+  // ---- distinct patterns (with the Schur-complement route, distinct (pattern, B-touched DOFs) pairs: those
+  // DOFs are ordered last, as the root supernode)
+  const bool schur = c->opt.assembly_route == 1;
+  std::vector<std::vector<int32_t>> tail(ns);
+  if (schur)
+    for (int i = 0; i < ns; ++i) {
+      auto& t = tail[i];
+      t.assign(c->subs[i].bdof.begin(), c->subs[i].bdof.end());
+      std::sort(t.begin(), t.end());
+      t.erase(std::unique(t.begin(), t.end()), t.end());
+    }
   std::unordered_map<uint64_t, int> pat_of;
   std::vector<int> pat_rep;
   for (int i = 0; i < ns; ++i) {
     auto& s = c->subs[i];
     uint64_t h = hash_pattern(s.n, s.rowptr.data(), s.col.data());
+    if (schur) h = hash_ints(tail[i].data(), (int64_t)tail[i].size(), h);
     auto it = pat_of.find(h);
     if (it == pat_of.end()) {
       pat_of[h] = (int)pat_rep.size();
@@ -191,7 +202,8 @@ void build(feti_ctx* c) {
     } else {
       s.pat = it->second;
       auto& r = c->subs[pat_rep[s.pat]];
-      if (r.n != s.n || r.col.size() != s.col.size()) throw ArgError("pattern hash collision");
+      if (r.n != s.n || r.col.size() != s.col.size() || (schur && tail[i] != tail[pat_rep[s.pat]]))
+        throw ArgError("pattern hash collision");
     }
   }
   SymbolicOptions so;
@@ -200,8 +212,9 @@ void build(feti_ctx* c) {
   c->pats.resize(pat_rep.size());
   parallel_for((int)pat_rep.size(), [&](int p) {
     auto& s = c->subs[pat_rep[p]];
+    const auto& t = tail[pat_rep[p]];
     analyse_pattern(s.n, s.rowptr.data(), s.col.data(), s.coords.empty() ? nullptr : s.coords.data(), so,
-                    c->pats[p]);
+                    c->pats[p], schur ? t.data() : nullptr, schur ? (int)t.size() : 0);
   });
   // ---- distinct RHS plans (pattern, B DOFs)
   std::map<std::pair<int, uint64_t>, int> bp_of;
@@ -541,6 +554,13 @@ void build(feti_ctx* c) {
         tdesc.push_back(d);
       }
   }
+  {
+    // subdomain-major copy (the TRSM-path assembly writes each subdomain's tiles)
+    std::vector<int> t0(ns, 0);
+    for (int i = 1; i < ns; ++i) t0[i] = t0[i - 1] + c->bps[c->subs[i - 1].bp].nb * (c->bps[c->subs[i - 1].bp].nb + 1) / 2;
+    c->d_tdesc_sub = upload(c, tdesc);
+    c->d_tile0 = upload(c, t0);
+  }
   // the tile kernels give warp g the descriptors g, g + N, g + 2N, ...: with the largest tiles first, the
   // k-th tiles of all warps are alike in size and the last round holds the smallest ones (ragged slivers)
   std::stable_sort(tdesc.begin(), tdesc.end(), [&](const TileDesc& a, const TileDesc& b) {
@@ -593,6 +613,15 @@ void build(feti_ctx* c) {
   c->chol_stack = max_chol;
   c->ws_stride = std::max(max_cf + max_chol + max_usm, max_rf + max_rhs);
   c->ws_stride = (c->ws_stride + 31) / 32 * 32;
+  {
+    // the per-CTA workspace (fronts and update stacks) of all persistent CTAs may take at most 40% of the
+    // free device memory: large fronts (the Schur-complement route's dense root) get fewer CTAs
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(0.4 * (double)free_b) / (c->ws_stride * 8));
+    c->grid_chol = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid_chol, cap));
+    c->grid_trsm = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid_trsm, cap));
+  }
   int gw = std::max(c->grid_chol, c->grid_trsm);
 
   // ---- device uploads
@@ -677,13 +706,30 @@ void build(feti_ctx* c) {
   c->d_c0 = upload(c, c0);
   c->d_c1 = upload(c, c1);
   c->d_lamcol = upload(c, lamcol);
-  if (c->opt.precond == 1) {
+  if (c->opt.precond == 2 && c->opt.assembly_route != 1)
+    throw ArgError("the Dirichlet preconditioner needs assembly_route = 1 (its S_i is the root front of that "
+                   "ordering)");
+  if (c->opt.precond == 1 || c->opt.precond == 2) {
     LumpedPlan lp;
     plan_lumped(c, lp);
     c->precond = true;
+    c->precond_kind = c->opt.precond;
     c->d_w_off = upload(c, lp.w_off);
     c->d_w_col = upload(c, lp.w_col);
     c->d_w_val = upload(c, lp.w_val);
+  }
+  if (c->opt.precond == 2) {
+    // S_i from a second factorisation of K (no penalty) that stops at the root front; M_i tiles as F_i
+    c->P2 = D;
+    c->P2.L = (double*)dalloc(c, (size_t)Lo * 8);
+    c->P2.rho = (double*)dalloc(c, (size_t)ns * 8);
+    c->d_M = dalloc(c, (size_t)std::max<int64_t>(Fo, 1) * esz);
+    c->d_pg2 = dalloc(c, (size_t)qo * esz);
+    CK(cudaMemsetAsync(c->d_pg2, 0, (size_t)qo * esz, c->st));  // padding columns stay zero
+  }
+  if (c->opt.precond == 1) {
+    LumpedPlan lp;
+    plan_lumped(c, lp);
     c->d_m_off = upload(c, lp.m_off);
     c->d_m_col = upload(c, lp.m_col);
     c->m_nnz = (int64_t)lp.m_col.size();
@@ -745,7 +791,7 @@ void build(feti_ctx* c) {
     c->d_Dinv = (double*)dalloc(c, (size_t)nblk * kT * kT * 8);
     c->d_Tp = (double*)dalloc(c, (size_t)D2 * kT * 8);
     c->d_Tb = (double*)dalloc(c, (size_t)D2 * kT * 8);
-    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 11 * 8);
+    c->d_vec = (double*)dalloc(c, (size_t)std::max(c->nlam, 1) * 12 * 8);
     c->d_cv = (double*)dalloc(c, (size_t)D2 * 7 * 8);
     c->d_sc = (double*)dalloc(c, 16 * 8);
     c->d_part = (double*)dalloc(c, 2 * kPcgMaxBlocks * 8);
@@ -804,7 +850,10 @@ feti_status feti_create(const feti_problem* prob, const feti_options* opt, feti_
     ctx->opt.use_coords = 1;
   }
   if (ctx->opt.prec < FETI_PREC_FP64 || ctx->opt.prec > FETI_PREC_SPLIT_BF16) throw ArgError("bad precision");
-  if (ctx->opt.precond < 0 || ctx->opt.precond > 1) throw ArgError("bad preconditioner (0 none, 1 lumped)");
+  if (ctx->opt.precond < 0 || ctx->opt.precond > 2)
+    throw ArgError("bad preconditioner (0 none, 1 lumped, 2 Dirichlet)");
+  if (ctx->opt.assembly_route < 0 || ctx->opt.assembly_route > 1)
+    throw ArgError("bad assembly route (0 SYRK path, 1 Schur complement)");
   ctx->st = (cudaStream_t)ctx->opt.stream;
   ctx->fp32 = ctx->opt.prec != FETI_PREC_FP64;
   ctx->nsub = prob->nsub;
@@ -858,6 +907,9 @@ feti_status feti_assemble(feti_ctx* ctx) {
     throw CudaError("internal: a work list of the assembly or apply is missing");
   if (!ctx->d_X)  // released after the previous assembly (recompute_X)
     ctx->d_X = dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * (ctx->fp32 ? 4 : 8));
+  const bool split = ctx->fp32 && ctx->opt.prec == FETI_PREC_SPLIT_BF16;
+  if (split && !ctx->d_X2)  // the bf16 hi/lo copy of X for the split-bf16 SYRK (2 bf16 per element)
+    ctx->d_X2 = (uint16_t*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 4);
   // mixed precision: the TRSM panel updates run on the tensor cores in split-bf16 in both mixed modes
   // (about 16 operand bits, FP32 accumulation), so that X_i is FP32-accurate and the TF32 mode's extra
   // error is that of its SYRK alone; in the TF32 mode X_i is rounded to TF32 for that SYRK
@@ -867,13 +919,14 @@ feti_status feti_assemble(feti_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->d_queue + 16, 0, sizeof(int), s2));
     launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
                 ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), tcmode, tf32_out,
-                ctx->d_status, s2);
+                ctx->d_status, s2, 0, split ? ctx->d_X2 : nullptr);
   };
-  // the numeric phase as one sequence of launches (recorded once into a CUDA graph, see below)
-  auto enqueue = [&](cudaStream_t s2, unsigned evf) {
+  // the numeric phase as one sequence of launches (recorded once into a CUDA graph, see below); r2: the
+  // TRSM-path route (F_i = B_i P^T L^{-T} X_i in host-driven batches, not captured)
+  auto enqueue = [&](cudaStream_t s2, unsigned evf, bool r2) {
     CK(cudaMemsetAsync(ctx->d_queue, 0, 64 * sizeof(int), s2));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s2));
-    if (ctx->precond)
+    if (ctx->precond_kind == 1)
       // the lumped preconditioner's values from the current K (they change with feti_update_values)
       launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val,
                            s2);
@@ -881,6 +934,13 @@ feti_status feti_assemble(feti_ctx* ctx) {
     launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride,
                 ctx->chol_front, ctx->chol_stack, ctx->grid_chol, ctx->d_status, s2);
     CK(cudaEventRecordWithFlags(ctx->ev[1], s2, evf));
+    if (r2) {
+      launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
+      CK(cudaEventRecordWithFlags(ctx->ev[2], s2, evf));
+      trsm_path_entry(ctx);
+      CK(cudaEventRecordWithFlags(ctx->ev[3], s2, evf));
+      return;
+    }
     if (!ctx->trsm_tuned) {
       // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)
       for (auto& tc : ctx->trsm_cands) {
@@ -904,22 +964,65 @@ feti_status feti_assemble(feti_ctx* ctx) {
     launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
     CK(cudaEventRecordWithFlags(ctx->ev[2], s2, evf));
     if (ctx->fp32) {
-      int split = ctx->opt.prec == FETI_PREC_SPLIT_BF16 ? 1 : 0;
-      launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, (float*)ctx->d_F,
-                     std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split, ctx->d_status, s2);
+      launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, ctx->d_X2, (float*)ctx->d_F,
+                     std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split ? 1 : 0, ctx->d_status,
+                     s2);
     } else {
       launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
                       std::min(ctx->nsyrk, ctx->nsm * 8), s2);
     }
+    if (ctx->precond_kind == 2) {
+      // Dirichlet preconditioner: K (no penalty) eliminated up to the root front, which then holds S_i
+      launch_chol(ctx->P2, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 8, ctx->d_ws, ctx->ws_stride,
+                  ctx->chol_front, ctx->chol_stack, ctx->grid_chol, ctx->d_status, s2, kCholNoReg | kCholStopRoot);
+      launch_schur_tiles(ctx->P2, ctx->d_tdesc, ctx->napply, ctx->fp32, ctx->d_M,
+                         std::max(1, std::min(ctx->napply, ctx->nsm * 8)), s2);
+    }
     CK(cudaEventRecordWithFlags(ctx->ev[3], s2, evf));
   };
-  ctx->stats.launches += ctx->precond ? 5 : 4;  // Cholesky, pruned TRSM, unit-lower scaling, SYRK
-  if (ctx->asm_exec && ctx->asm_X == ctx->d_X) {
+  // Cholesky, pruned TRSM, unit-lower scaling, SYRK (+ lumped values, or the Dirichlet factorisation and tiles)
+  ctx->stats.launches += 4 + (ctx->precond_kind == 1 ? 1 : ctx->precond_kind == 2 ? 2 : 0);
+  const int want = ctx->opt.assembly_route;
+  if (want == 2 || (want == 3 && ctx->route_tuned && ctx->route == 2)) {
+    ctx->route = 2;
+    if (!ctx->trsm_tuned) {  // the unit-lower TRSM of this route takes whole subdomains
+      ctx->trsm_pick = 0;
+      ctx->trsm_tuned = true;
+      ctx->stats.trsm_cols = ctx->trsm_cands[0].cw;
+    }
+    enqueue(st, cudaEventRecordDefault, true);
+    CK(cudaGetLastError());
+  } else if (ctx->asm_exec && ctx->asm_X == ctx->d_X && ctx->asm_X2 == ctx->d_X2) {
     CK(cudaGraphLaunch(ctx->asm_exec, st));
   } else {
-    enqueue(st, cudaEventRecordDefault);
+    ctx->route = want == 1 ? 1 : 0;
+    enqueue(st, cudaEventRecordDefault, false);
     CK(cudaGetLastError());
-    if (ctx->trsm_tuned) {
+    if (want == 3 && !ctx->route_tuned) {
+      // autotuner between the SYRK path and the TRSM path (Sec. IV, Table I): time the TRSM and SYRK of the
+      // call above against the TRSM path on the same factor; the faster one assembles from now on (the
+      // TRSM path ran last, so when it wins the F tiles are already its own)
+      float a1 = 0, a2 = 0;
+      CK(cudaEventSynchronize(ctx->ev[3]));
+      CK(cudaEventElapsedTime(&a1, ctx->ev[1], ctx->ev[3]));
+      CK(cudaEventRecord(ctx->ev[5], st));
+      trsm_path_entry(ctx);
+      CK(cudaEventRecord(ctx->ev[6], st));
+      CK(cudaEventSynchronize(ctx->ev[6]));
+      CK(cudaEventElapsedTime(&a2, ctx->ev[5], ctx->ev[6]));
+      ctx->route_ms[0] = a1;
+      ctx->route_ms[2] = a2;
+      ctx->route_tuned = true;
+      if (a2 < a1) {
+        ctx->route = 2;
+      } else {
+        // the SYRK path keeps its F: run it once more (the TRSM path overwrote the tiles)
+        enqueue(st, cudaEventRecordDefault, false);
+        CK(cudaGetLastError());
+      }
+      ctx->stats.assembly_route = ctx->route;
+    }
+    if (ctx->trsm_tuned && ctx->route != 2) {
       // later assemblies replay the same launches from a CUDA graph, captured on a private stream (the
       // events become record nodes, so the phase times stay measured); a new X buffer needs a new graph
       if (ctx->asm_exec) CK(cudaGraphExecDestroy(ctx->asm_exec));
@@ -927,12 +1030,13 @@ feti_status feti_assemble(feti_ctx* ctx) {
       if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
       cudaGraph_t gr = nullptr;
       CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
-      enqueue(ctx->cap_st, cudaEventRecordExternal);
+      enqueue(ctx->cap_st, cudaEventRecordExternal, false);
       CK(cudaStreamEndCapture(ctx->cap_st, &gr));
       cudaError_t e = cudaGraphInstantiate(&ctx->asm_exec, gr, 0);
       cudaGraphDestroy(gr);
       if (e != cudaSuccess) throw CudaError(std::string("assembly graph: ") + cudaGetErrorString(e));
       ctx->asm_X = ctx->d_X;
+      ctx->asm_X2 = ctx->d_X2;
     }
   }
   CK(cudaGetLastError());
@@ -947,6 +1051,8 @@ feti_status feti_assemble(feti_ctx* ctx) {
     // X_i is an intermediate of the assembly: with recompute_X its memory goes back to the allocator
     dfree(ctx, ctx->d_X);
     ctx->d_X = nullptr;
+    dfree(ctx, ctx->d_X2);
+    ctx->d_X2 = nullptr;
   }
   float a, b, cc, d;
   CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
@@ -1123,14 +1229,22 @@ feti_status feti_analyse(const feti_subdomain* sub, const feti_options* opt, dou
       so.use_coords = opt->use_coords != 0;
     }
     PatternPlan P;
-    analyse_pattern(h.n, h.rowptr.data(), h.col.data(), h.coords.empty() ? nullptr : h.coords.data(), so, P);
+    std::vector<int32_t> tail;
+    if (opt && opt->assembly_route == 1) {
+      tail.assign(h.bdof.begin(), h.bdof.end());
+      std::sort(tail.begin(), tail.end());
+      tail.erase(std::unique(tail.begin(), tail.end()), tail.end());
+    }
+    analyse_pattern(h.n, h.rowptr.data(), h.col.data(), h.coords.empty() ? nullptr : h.coords.data(), so, P,
+                    tail.empty() ? nullptr : tail.data(), (int)tail.size());
     BPlan B;
     plan_rhs(P, h.m, h.bdof.data(), B);
     int roots = 0;
     for (int s = 0; s < P.nsn; ++s) roots += P.sn_parent[s] < 0;
     double v[16] = {(double)P.n, (double)P.nsn, (double)P.max_f, (double)P.max_w, P.nnzL, P.chol_flops,
                     (double)P.Lsize, (double)B.m, (double)B.Xsize, B.trsm_flops, B.syrk_flops,
-                    (double)B.tile_sn.size(), (double)P.chol_stack, (double)B.rhs_stack, (double)roots, 0.0};
+                    (double)B.tile_sn.size(), (double)P.chol_stack, (double)B.rhs_stack, (double)roots,
+                    (double)P.nlast};
     std::memcpy(info, v, sizeof(v));
     if (perm_out) std::copy(P.perm.begin(), P.perm.end(), perm_out);
     if (sn_out) {

@@ -28,7 +28,7 @@ struct CudaErr : std::runtime_error {
 // vectors inside ctx->d_vec (each n_lambda long)
 // V_Q: scratch of the FP64 implicit operator; V_QK: q_k = F p_k of the iteration;
 // V_Y = P M w and V_V = M w with the lumped preconditioner
-enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM, V_QK, V_Y, V_V };
+enum { V_D = 0, V_R, V_W, V_P, V_Q, V_T, V_LAM0, V_LAM, V_QK, V_Y, V_V, V_U };
 // coarse vectors in ctx->d_cv (each D long)
 enum { C_E = 0, C_C, C_Z, C_A, C_GQ, C_C2, C_Z2 };
 
@@ -112,8 +112,19 @@ void enqueue_precond(feti_ctx* c, int mode, cudaStream_t st) {
   const int n = c->nlam, D = c->dtot;
   PcgCtrl* ctrl = ctrl_dev(c);
   double *w = vec(c, V_W), *y = vec(c, V_Y), *v = vec(c, V_V);
-  launch_lumped_apply(n, c->d_w_off, c->d_w_col, c->d_w_val, c->d_m_off, c->d_m_col, c->d_m_val, w, v, ctrl,
-                      mode == 0 ? 1 : 0, st);
+  const int iter = mode == 0 ? 1 : 0;
+  if (c->precond_kind == 2) {
+    // Dirichlet: v = W (sum_i B_i S_i B_i^T) W w, the M_i tiles applied by the explicit-apply tile kernel
+    const auto& cand = c->apply_cands[c->apply_pick];
+    launch_dir_pre(c->fp32, n, c->d_w_off, c->d_w_col, c->d_w_val, w, c->d_c0, c->d_c1, c->d_pg2, ctrl, iter, st);
+    launch_apply_core(c->fp32, c->d_tdesc, c->napply, c->d_M, c->d_pg2, c->d_rowpart, c->d_tpart, cand.grid,
+                      cand.variant, iter ? active_dev(c) : nullptr, c->d_status, st);
+    launch_dir_mid(c->fp32, c->d_lamcol, n, c->d_rowpart, c->d_tpart, vec(c, V_U), ctrl, iter, st);
+    launch_dir_post(n, c->d_w_off, c->d_w_col, c->d_w_val, vec(c, V_U), v, ctrl, iter, st);
+  } else {
+    launch_lumped_apply(n, c->d_w_off, c->d_w_col, c->d_w_val, c->d_m_off, c->d_m_col, c->d_m_val, w, v, ctrl,
+                        iter, st);
+  }
   if (D > 0) {
     launch_pcg_gt(c->P, c->nsub, c->d_G6, nullptr, v, nullptr, mode == 0 ? 2 : 3, cvec(c, C_C2), ctrl, st);
     launch_gemv_rows(c->d_Ainv, cvec(c, C_C2), cvec(c, C_Z2), D, ctrl, mode == 0 ? 2 : 1, st);
@@ -150,7 +161,7 @@ void enqueue_iteration(feti_ctx* c, double* lam, const cudaEvent_t* ev, cudaStre
 }
 
 int iteration_launches(feti_ctx* c) {
-  return (c->dtot > 0 ? 5 : 3) + (c->precond ? (c->dtot > 0 ? 4 : 2) : 0);
+  return (c->dtot > 0 ? 5 : 3) + (c->precond ? (c->dtot > 0 ? 4 : 2) : 0) + (c->precond_kind == 2 ? 3 : 0);
 }
 
 // Capture `chunk` iterations on the private stream into one CUDA graph (once
@@ -195,7 +206,8 @@ void enqueue_refresh(feti_ctx* c, double* lam, int mode) {
   launch_pcg_update(c->fp32, c->d_lamg, c->d_c0, c->d_c1, n, c->d_G6, D > 0 ? cvec(c, C_Z) : nullptr, p, q, d, lam, r,
                     w, c->d_pg, c->d_part + kPcgMaxBlocks, mode, c->precond ? 1 : 0, ctrl, st);
   if (c->precond) enqueue_precond(c, mode, st);
-  c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0) + (c->precond ? (D > 0 ? 4 : 2) : 0);
+  c->stats.launches += (D > 0 ? 3 : 1) + (mode == 2 ? 1 : 0) + (c->precond ? (D > 0 ? 4 : 2) : 0) +
+                       (c->precond_kind == 2 ? 3 : 0);
 }
 
 }  // namespace
@@ -370,7 +382,166 @@ feti_status solve_impl(feti_ctx* ctx, double* lambda_dev, double* alpha_dev, dou
   }
 }
 
+// Z_i = P^T L_u^{-T} D^{-2} X_u (and, for the adjoint, Y_i = Z_i W_i) over batches of subdomains whose
+// dense work arrays fit the budget, from X_u = L_u^{-1} P B^T recomputed in FP64 by the pruned forward
+// solve with the unit-lower factor.  W_dev != null: the adjoint, dtheta_e = -sum (dK_e)_ab Y[b,:] . Z[a,:]
+// into dtheta; W_dev == null: the TRSM-path assembly, F_i = B_i Z_i into the F tiles.  Synchronises.
+void z_batches(feti_ctx* ctx, const double* W_dev, double* dtheta_dev, cudaStream_t st) {
+  const bool adjoint = W_dev != nullptr;
+  const int ns = ctx->nsub;
+  if (!ctx->d_Xu) ctx->d_Xu = (double*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 8);
+  queue_reset(ctx, 40);
+  {
+    const auto& tc = ctx->trsm_cands[ctx->trsm_pick];
+    launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 40, ctx->d_Xu, false, ctx->d_ws,
+                ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), 0, 0, ctx->d_status, st, 1);
+  }
+  ctx->stats.launches += 1;
+  CKS(cudaGetLastError());
+  // batches of subdomains whose dense V (n x 2 m_pad, or n x m_pad for Z alone) and sorted W (m_pad^2) fit
+  size_t free_b = 0, total_b = 0;
+  CKS(cudaMemGetInfo(&free_b, &total_b));
+  const double cap = ctx->opt.adjoint_work_bytes > 0
+                         ? (double)ctx->opt.adjoint_work_bytes
+                         : std::min<double>(24.0 * (1 << 30), 0.45 * (double)(free_b + ctx->adj_work_bytes));
+  const int64_t budget = std::max<int64_t>((int64_t)(cap / 8), 1);
+  std::vector<int64_t> woff(ns + 1, 0);
+  for (int i = 0; i < ns; ++i) woff[i + 1] = woff[i] + (int64_t)ctx->subs[i].m * ctx->subs[i].m;
+  std::vector<std::vector<AdjBatch>> batches;
+  {
+    std::vector<AdjBatch> cur;
+    int64_t used = 0;
+    for (int i = 0; i < ns; ++i) {
+      const auto& s = ctx->subs[i];
+      if (adjoint && s.nelem == 0) continue;
+      if (s.m == 0) {
+        if (adjoint) CKS(cudaMemsetAsync(dtheta_dev + ctx->elem_ofs[i], 0, (size_t)s.nelem * 8, st));
+        continue;
+      }
+      const auto& I = ctx->info[i];
+      const int64_t vlen = (int64_t)s.n * (adjoint ? 2 : 1) * I.m_pad;
+      const int64_t need = vlen + (adjoint ? (int64_t)I.m_pad * I.m_pad : 0);
+      if (!cur.empty() && used + need > budget) {
+        batches.push_back(cur);
+        cur.clear();
+        used = 0;
+      }
+      AdjBatch e{};
+      e.sub = i;
+      e.m = s.m;
+      e.m_pad = I.m_pad;
+      e.zonly = adjoint ? 0 : 1;
+      e.edofs = s.edofs;
+      e.nelem = s.nelem;
+      e.qcol = I.qcol;
+      e.w_src = woff[i];
+      e.v_ofs = used;
+      e.ws_ofs = used + vlen;
+      e.el_dofs = adjoint ? ctx->elem_dofs_ofs[i] : 0;
+      e.el_dk = adjoint ? ctx->elem_dk_ofs[i] : 0;
+      e.el_out = adjoint ? ctx->elem_ofs[i] : 0;
+      e.dk_stride = s.dk_stride;
+      cur.push_back(e);
+      used += need;
+    }
+    if (!cur.empty()) batches.push_back(cur);
+  }
+  int64_t max_used = 0, max_nb = 0;
+  for (auto& b : batches) {
+    const AdjBatch& l = b.back();
+    max_used = std::max<int64_t>(max_used, l.ws_ofs + (adjoint ? (int64_t)l.m_pad * l.m_pad : 0));
+    max_nb = std::max<int64_t>(max_nb, (int64_t)b.size());
+  }
+  if (max_used * 8 > ctx->adj_work_bytes) {
+    dfree(ctx, ctx->d_adj_work);
+    ctx->d_adj_work = nullptr;
+    ctx->adj_work_bytes = 0;
+    ctx->d_adj_work = (double*)dalloc(ctx, (size_t)max_used * 8);
+    ctx->adj_work_bytes = max_used * 8;
+  }
+  if (max_nb > ctx->adj_batch_cap) {
+    dfree(ctx, ctx->d_adj_batch);
+    ctx->d_adj_batch = (AdjBatch*)dalloc(ctx, (size_t)max_nb * sizeof(AdjBatch));
+    ctx->adj_batch_cap = max_nb;
+  }
+  const int grid = ctx->nsm * 4;
+  for (auto& b : batches) {
+    const int nb = (int)b.size();
+    // work items: the V rows of each (entry, active supernode, 64 own rows) and, for the adjoint, X_u W per
+    // kBuildCols columns, largest first; the backward solve per (entry, 64 columns), larger factors first
+    std::vector<std::pair<double, int4>> bi;
+    std::vector<std::pair<double, int2>> si;
+    int max_mpad = 0, max_nel = 0, max_tiles = 0;
+    for (int e = 0; e < nb; ++e) {
+      const auto& s = ctx->subs[b[e].sub];
+      const auto& pat = ctx->pats[s.pat];
+      const auto& bp = ctx->bps[s.bp];
+      const int mp = b[e].m_pad;
+      max_mpad = std::max(max_mpad, mp);
+      max_nel = std::max(max_nel, b[e].nelem);
+      max_tiles = std::max(max_tiles, bp.nb * (bp.nb + 1) / 2);
+      for (int a = 0; a < (int)bp.act.size(); ++a) {
+        const int sn = bp.act[a];
+        const int w = pat.sn_w[sn], J = bp.je[sn] - bp.jb[sn];
+        for (int k0 = 0; k0 < w; k0 += kT)
+          for (int cg = 0; cg < (adjoint ? mp : 1); cg += kBuildCols)
+            bi.push_back({(double)std::min(kT, w - k0) * J * (adjoint ? std::min(kBuildCols, mp - cg) : 1),
+                          make_int4(e, a, k0, cg)});
+      }
+      for (int cb = 0; cb < (adjoint ? 2 : 1) * mp / 64; ++cb) si.push_back({pat.nnzL, make_int2(e, cb)});
+    }
+    std::stable_sort(bi.begin(), bi.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::stable_sort(si.begin(), si.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<int4> bv;
+    std::vector<int2> sv;
+    bv.reserve(bi.size());
+    sv.reserve(si.size());
+    for (auto& x : bi) bv.push_back(x.second);
+    for (auto& x : si) sv.push_back(x.second);
+    if ((int64_t)bv.size() > ctx->adj_items4_cap) {
+      dfree(ctx, ctx->d_adj_items4);
+      ctx->d_adj_items4 = (int4*)dalloc(ctx, bv.size() * sizeof(int4));
+      ctx->adj_items4_cap = (int64_t)bv.size();
+    }
+    if ((int64_t)sv.size() > ctx->adj_items2_cap) {
+      dfree(ctx, ctx->d_adj_items2);
+      ctx->d_adj_items2 = (int2*)dalloc(ctx, sv.size() * sizeof(int2));
+      ctx->adj_items2_cap = (int64_t)sv.size();
+    }
+    // the host vectors outlive the copies: the stream is synchronised at the end of each batch
+    CKS(cudaMemcpyAsync(ctx->d_adj_batch, b.data(), nb * sizeof(AdjBatch), cudaMemcpyHostToDevice, st));
+    if (!bv.empty())
+      CKS(cudaMemcpyAsync(ctx->d_adj_items4, bv.data(), bv.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(ctx->d_adj_items2, sv.data(), sv.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    const AdjBatch& l = b.back();
+    CKS(cudaMemsetAsync(ctx->d_adj_work, 0,
+                        (size_t)(l.ws_ofs + (adjoint ? (int64_t)l.m_pad * l.m_pad : 0)) * 8, st));
+    if (adjoint) launch_adj_wsort(ctx->d_adj_batch, nb, W_dev, ctx->P.colperm, ctx->d_adj_work, max_mpad, st);
+    queue_reset(ctx, 41);
+    launch_adj_build(ctx->P, ctx->d_adj_batch, ctx->d_adj_items4, (int)bv.size(), ctx->d_queue + 41, ctx->d_Xu,
+                     ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)bv.size())), st);
+    queue_reset(ctx, 42);
+    launch_adj_bsolve(ctx->P, ctx->d_adj_batch, ctx->d_adj_items2, (int)sv.size(), ctx->d_queue + 42,
+                      ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)sv.size())), st);
+    if (adjoint)
+      launch_adj_contract(ctx->P, ctx->d_adj_batch, nb, max_nel, ctx->d_eldofs, ctx->d_eldk, ctx->d_elsc,
+                          ctx->d_adj_work, dtheta_dev, st);
+    else
+      launch_zgather_tiles(ctx->P, ctx->d_adj_batch, nb, ctx->d_tdesc_sub, ctx->d_tile0, ctx->d_adj_work,
+                           ctx->fp32, ctx->d_F, max_tiles, st);
+    ctx->stats.launches += adjoint ? 4 : 3;
+    CKS(cudaGetLastError());
+    CKS(cudaStreamSynchronize(st));
+  }
+  CKS(cudaStreamSynchronize(st));
+}
+
 }  // namespace
+
+namespace feti {
+// called from feti_assemble with the TRSM-path route: F_i = B_i P^T L^{-T} X_i from the batches above
+void trsm_path_entry(feti_ctx* c) { z_batches(c, nullptr, nullptr, c->st); }
+}  // namespace feti
 
 extern "C" {
 
@@ -389,146 +560,7 @@ feti_status feti_adjoint(feti_ctx* ctx, const double* W_dev, double* dtheta_dev)
   if (ctx->nelem_total == 0) return set_error(ctx, FETI_ERR_ARG, "feti_adjoint: no element data given at create");
   if (!ctx->assembled) return set_error(ctx, FETI_ERR_STATE, "feti_adjoint before feti_assemble");
   try {
-    cudaStream_t st = ctx->st;
-    const int ns = ctx->nsub;
-    // X_u = L_u^{-1} P B^T in FP64 for every subdomain: the pruned forward solve with the unit-lower factor
-    if (!ctx->d_Xu) ctx->d_Xu = (double*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 8);
-    queue_reset(ctx, 40);
-    {
-      const auto& tc = ctx->trsm_cands[ctx->trsm_pick];
-      launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 40, ctx->d_Xu, false, ctx->d_ws,
-                  ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), 0, 0, ctx->d_status, st, 1);
-    }
-    ctx->stats.launches += 1;
-    CKS(cudaGetLastError());
-    // batches of subdomains whose dense V (n x 2 m_pad) and sorted W (m_pad^2) fit the work budget
-    size_t free_b = 0, total_b = 0;
-    CKS(cudaMemGetInfo(&free_b, &total_b));
-    const double cap = ctx->opt.adjoint_work_bytes > 0
-                           ? (double)ctx->opt.adjoint_work_bytes
-                           : std::min<double>(24.0 * (1 << 30), 0.45 * (double)(free_b + ctx->adj_work_bytes));
-    const int64_t budget = std::max<int64_t>((int64_t)(cap / 8), 1);
-    std::vector<int64_t> woff(ns + 1, 0);
-    for (int i = 0; i < ns; ++i) woff[i + 1] = woff[i] + (int64_t)ctx->subs[i].m * ctx->subs[i].m;
-    std::vector<std::vector<AdjBatch>> batches;
-    {
-      std::vector<AdjBatch> cur;
-      int64_t used = 0;
-      for (int i = 0; i < ns; ++i) {
-        const auto& s = ctx->subs[i];
-        if (s.nelem == 0) continue;
-        if (s.m == 0) {
-          CKS(cudaMemsetAsync(dtheta_dev + ctx->elem_ofs[i], 0, (size_t)s.nelem * 8, st));
-          continue;
-        }
-        const auto& I = ctx->info[i];
-        const int64_t need = (int64_t)s.n * 2 * I.m_pad + (int64_t)I.m_pad * I.m_pad;
-        if (!cur.empty() && used + need > budget) {
-          batches.push_back(cur);
-          cur.clear();
-          used = 0;
-        }
-        AdjBatch e{};
-        e.sub = i;
-        e.m = s.m;
-        e.m_pad = I.m_pad;
-        e.edofs = s.edofs;
-        e.nelem = s.nelem;
-        e.qcol = I.qcol;
-        e.w_src = woff[i];
-        e.v_ofs = used;
-        e.ws_ofs = used + (int64_t)s.n * 2 * I.m_pad;
-        e.el_dofs = ctx->elem_dofs_ofs[i];
-        e.el_dk = ctx->elem_dk_ofs[i];
-        e.el_out = ctx->elem_ofs[i];
-        e.dk_stride = s.dk_stride;
-        cur.push_back(e);
-        used += need;
-      }
-      if (!cur.empty()) batches.push_back(cur);
-    }
-    int64_t max_used = 0, max_nb = 0;
-    for (auto& b : batches) {
-      const AdjBatch& l = b.back();
-      max_used = std::max<int64_t>(max_used, l.ws_ofs + (int64_t)l.m_pad * l.m_pad);
-      max_nb = std::max<int64_t>(max_nb, (int64_t)b.size());
-    }
-    if (max_used * 8 > ctx->adj_work_bytes) {
-      dfree(ctx, ctx->d_adj_work);
-      ctx->d_adj_work = nullptr;
-      ctx->adj_work_bytes = 0;
-      ctx->d_adj_work = (double*)dalloc(ctx, (size_t)max_used * 8);
-      ctx->adj_work_bytes = max_used * 8;
-    }
-    if (max_nb > ctx->adj_batch_cap) {
-      dfree(ctx, ctx->d_adj_batch);
-      ctx->d_adj_batch = (AdjBatch*)dalloc(ctx, (size_t)max_nb * sizeof(AdjBatch));
-      ctx->adj_batch_cap = max_nb;
-    }
-    const int grid = ctx->nsm * 4;
-    for (auto& b : batches) {
-      const int nb = (int)b.size();
-      // work items: X_u W per (entry, active supernode, 64 own rows, kBuildCols columns), largest first;
-      // the backward solve per (entry, 64 columns), entries with the larger factor first
-      std::vector<std::pair<double, int4>> bi;
-      std::vector<std::pair<double, int2>> si;
-      int max_mpad = 0, max_nel = 0;
-      for (int e = 0; e < nb; ++e) {
-        const auto& s = ctx->subs[b[e].sub];
-        const auto& pat = ctx->pats[s.pat];
-        const auto& bp = ctx->bps[s.bp];
-        const int mp = b[e].m_pad;
-        max_mpad = std::max(max_mpad, mp);
-        max_nel = std::max(max_nel, b[e].nelem);
-        for (int a = 0; a < (int)bp.act.size(); ++a) {
-          const int sn = bp.act[a];
-          const int w = pat.sn_w[sn], J = bp.je[sn] - bp.jb[sn];
-          for (int k0 = 0; k0 < w; k0 += kT)
-            for (int cg = 0; cg < mp; cg += kBuildCols)
-              bi.push_back({(double)std::min(kT, w - k0) * J * std::min(kBuildCols, mp - cg),
-                            make_int4(e, a, k0, cg)});
-        }
-        for (int cb = 0; cb < 2 * mp / 64; ++cb) si.push_back({pat.nnzL, make_int2(e, cb)});
-      }
-      std::stable_sort(bi.begin(), bi.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-      std::stable_sort(si.begin(), si.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-      std::vector<int4> bv;
-      std::vector<int2> sv;
-      bv.reserve(bi.size());
-      sv.reserve(si.size());
-      for (auto& x : bi) bv.push_back(x.second);
-      for (auto& x : si) sv.push_back(x.second);
-      if ((int64_t)bv.size() > ctx->adj_items4_cap) {
-        dfree(ctx, ctx->d_adj_items4);
-        ctx->d_adj_items4 = (int4*)dalloc(ctx, bv.size() * sizeof(int4));
-        ctx->adj_items4_cap = (int64_t)bv.size();
-      }
-      if ((int64_t)sv.size() > ctx->adj_items2_cap) {
-        dfree(ctx, ctx->d_adj_items2);
-        ctx->d_adj_items2 = (int2*)dalloc(ctx, sv.size() * sizeof(int2));
-        ctx->adj_items2_cap = (int64_t)sv.size();
-      }
-      // the host vectors outlive the copies: the stream is synchronised at the end of each batch
-      CKS(cudaMemcpyAsync(ctx->d_adj_batch, b.data(), nb * sizeof(AdjBatch), cudaMemcpyHostToDevice, st));
-      if (!bv.empty())
-        CKS(cudaMemcpyAsync(ctx->d_adj_items4, bv.data(), bv.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-      CKS(cudaMemcpyAsync(ctx->d_adj_items2, sv.data(), sv.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-      const AdjBatch& l = b.back();
-      CKS(cudaMemsetAsync(ctx->d_adj_work, 0, (size_t)(l.ws_ofs + (int64_t)l.m_pad * l.m_pad) * 8, st));
-      launch_adj_wsort(ctx->d_adj_batch, nb, W_dev, ctx->P.colperm, ctx->d_adj_work, max_mpad, st);
-      queue_reset(ctx, 41);
-      launch_adj_build(ctx->P, ctx->d_adj_batch, ctx->d_adj_items4, (int)bv.size(), ctx->d_queue + 41, ctx->d_Xu,
-                       ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)bv.size())), st);
-      queue_reset(ctx, 42);
-      launch_adj_bsolve(ctx->P, ctx->d_adj_batch, ctx->d_adj_items2, (int)sv.size(), ctx->d_queue + 42,
-                        ctx->d_adj_work, std::max(1, std::min<int>(grid, (int)sv.size())), st);
-      launch_adj_contract(ctx->P, ctx->d_adj_batch, nb, max_nel, ctx->d_eldofs, ctx->d_eldk, ctx->d_elsc,
-                          ctx->d_adj_work, dtheta_dev, st);
-      ctx->stats.launches += 4;
-      CKS(cudaGetLastError());
-      CKS(cudaStreamSynchronize(st));
-    }
-    CKS(cudaStreamSynchronize(st));
+    z_batches(ctx, W_dev, dtheta_dev, ctx->st);
     int status = 0;
     CKS(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status & kStatTimeout) return set_error(ctx, FETI_ERR_TIMEOUT, "a bounded device wait gave up");

@@ -210,10 +210,14 @@ constexpr int kPcgMaxBlocks = 1184;  // block partials per reduction
 // doubles into the batch's work buffer (v_ofs: n x 2 m_pad row-major V,
 // ws_ofs: m_pad x m_pad sorted W), into W (w_src) and into the element arrays.
 struct AdjBatch {
-  int sub, m, m_pad, edofs, nelem, pad;
+  int sub, m, m_pad, edofs, nelem;
+  int zonly;  // 1: V holds only D^{-2} X_u (row length m_pad), for the TRSM-path assembly of F_i
   int64_t qcol, w_src, ws_ofs, v_ofs, el_dofs, el_dk, el_out, dk_stride;
 };
 constexpr int kBuildCols = 512;  // columns of V_Y per item of the adjoint's X_u W product
+
+// flags of the numeric Cholesky (kern_factor.cu)
+enum : int { kCholNoReg = 1, kCholStopRoot = 2 };
 
 // status word bits written by kernels
 enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };

@@ -121,6 +121,10 @@ struct feti_ctx {
   int m_max = 0;               // widest subdomain (B rows)
   // lumped preconditioner M = W M_core W (options.precond = 1), see precond.cpp
   bool precond = false;
+  int precond_kind = 0;        // 0 none, 1 lumped, 2 Dirichlet
+  feti::DevPlan P2{};          // Dirichlet: the plan with its own L (K factored up to the root front) and rho
+  void* d_M = nullptr;         // Dirichlet: M_i = B_i S_i B_i^T tiles (layout of F)
+  void* d_pg2 = nullptr;       // Dirichlet: W w gathered per sorted column (tile precision)
   int* d_w_off = nullptr;
   int* d_w_col = nullptr;
   double* d_w_val = nullptr;
@@ -140,7 +144,9 @@ struct feti_ctx {
   feti::PcgCtrl* h_ctrl = nullptr;  // pinned host copy
   cudaStream_t cap_st = nullptr;     // private stream on which CUDA graphs are captured
   cudaGraphExec_t asm_exec = nullptr;  // the numeric assembly (Cholesky, TRSM, scaling, SYRK), replayed on st
-  void* asm_X = nullptr;             // the X buffer the assembly graph was captured with
+  void* asm_X = nullptr;             // the X buffers the assembly graph was captured with
+  void* asm_X2 = nullptr;
+  uint16_t* d_X2 = nullptr;          // bf16 hi/lo copy of X (split-bf16 SYRK operands)
   cudaGraphExec_t pcg_exec = nullptr;  // captured chunk of iterations (replayed on st)
   int pcg_chunk = 0;
   std::vector<cudaEvent_t> pcg_ev;  // 4 events per captured iteration (apply timing)
@@ -160,6 +166,11 @@ struct feti_ctx {
   int4* d_adj_items4 = nullptr;
   int64_t adj_items4_cap = 0;
   int2* d_adj_items2 = nullptr;
+  feti::TileDesc* d_tdesc_sub = nullptr;  // the apply's tile descriptors in subdomain-major order
+  int* d_tile0 = nullptr;                 // first tile of each subdomain in d_tdesc_sub
+  int route = 0;                          // assembly route in use (0 SYRK path, 1 Schur, 2 TRSM path)
+  bool route_tuned = false;
+  double route_ms[3] = {0, 0, 0};
   int64_t adj_items2_cap = 0;
   int64_t* d_woff = nullptr;       // per subdomain offset of W_i (weighted trace)
   double* d_wt_part = nullptr;     // per tile partials of the weighted trace
@@ -193,6 +204,7 @@ struct feti_ctx {
 
 namespace feti {
 feti_status set_error(feti_ctx* c, feti_status s, const std::string& msg);
+void trsm_path_entry(feti_ctx* c);  // the TRSM-path assembly of the F_i tiles (api_solve.cpp)
 void* dalloc(feti_ctx* c, size_t bytes);
 void dfree(feti_ctx* c, void* p);  // release a buffer from dalloc (no-op for nullptr)
 }  // namespace feti

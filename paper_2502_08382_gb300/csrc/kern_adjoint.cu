@@ -66,12 +66,12 @@ __global__ void __launch_bounds__(kAT) adj_build_kernel(DevPlan P, const AdjBatc
     const SubInfo& S = P.sub[E.sub];
     const int s = P.act[S.act0 + item.y];
     const int gs = S.sn0 + s, bs = S.bsn0 + s;
-    const int c0 = P.sn_c0[gs], w = P.sn_w[gs], wp = (w + 3) & ~3;
+    const int c0 = P.sn_c0[gs], w = P.sn_w[gs], wp = (w + 7) & ~7;
     const int jb = P.jb[bs], J = P.je[bs] - jb;
     const double* Xs = Xu + S.X + P.Xofs[bs];
     const double* d2 = P.dinv + S.dof;
     const int mp = E.m_pad;
-    const int64_t ld = 2 * (int64_t)mp;
+    const int64_t ld = (E.zonly ? 1 : 2) * (int64_t)mp;
     double* V = work + E.v_ofs;
     const double* Ws = work + E.ws_ofs;
     const int k0 = item.z, nk = min(kT, w - k0);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kAT) adj_build_kernel(DevPlan P, const AdjBatc
         const int k = (int)(idx % nk), j = (int)(idx / nk);
         V[(int64_t)(c0 + k0 + k) * ld + jb + j] = d2[c0 + k0 + k] * Xs[(int64_t)j * wp + k0 + k];
       }
-    const int cend = min(mp, item.w + kBuildCols);
+    const int cend = E.zonly ? 0 : min(mp, item.w + kBuildCols);
     for (int cb = item.w; cb < cend; cb += kT) {
       double acc[4][4] = {};
       for (int j0 = 0; j0 < J; j0 += 32) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kAT) adj_bsolve_kernel(DevPlan P, const AdjBat
     const AdjBatch& E = B[items[it].x];
     const SubInfo& S = P.sub[E.sub];
     const int cb = items[it].y * kCB;
-    const int64_t ld = 2 * (int64_t)E.m_pad;
+    const int64_t ld = (E.zonly ? 1 : 2) * (int64_t)E.m_pad;
     double* V = work + E.v_ofs + cb;
     const double* Lsub = P.L + S.L;
     for (int s = S.nsn - 1; s >= 0; --s) {
@@ -263,6 +263,36 @@ __global__ void __launch_bounds__(kAT) adj_contract_kernel(DevPlan P, const AdjB
   }
 }
 
+// ---------------------------------------------------------------- TRSM-path assembly of F_i
+//
+// After the backward solve, V_Z row iperm[d] holds row d of Z = K_reg^{-1} B^T (columns in sorted order),
+// so F = B Z: F[a][b] = s_a Z[dof_a][b].  One CTA per tile of the batch's subdomains writes the stored
+// (lower) part in the tile layout and precision of F.
+template <typename TF>
+__global__ void __launch_bounds__(kAT) zgather_tiles_kernel(DevPlan P, const AdjBatch* B, const TileDesc* desc,
+                                                           const int* tile0, const double* work, TF* F) {
+  constexpr int E = (int)sizeof(TF), V = 16 / E;
+  const AdjBatch& A = B[blockIdx.y];
+  const SubInfo& S = P.sub[A.sub];
+  const int* iperm = P.iperm + S.diag0;
+  const double* Vz = work + A.v_ofs;
+  const int ntile = S.nb * (S.nb + 1) / 2;
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const TileDesc d = desc[tile0[A.sub] + t];
+    const bool diag = (d.flags & kTileDiag) != 0;
+    TF* Ft = F + d.f_ofs;
+    for (int idx = threadIdx.x; idx < d.rows * kT; idx += kAT) {
+      const int r = idx / kT, cc = idx % kT;
+      if (diag && cc >= V * ((r + V) / V)) continue;  // not stored
+      const int a = d.prow + r, b = d.pcol + cc;
+      double v = 0.0;
+      if (!(diag && cc > r) && P.qmap[a] >= 0 && P.qmap[b] >= 0)
+        v = P.qsign[a] * Vz[(int64_t)iperm[P.qdof[a]] * A.m_pad + (b - S.qcol)];
+      Ft[diag ? diag_pos<E>(r, cc) : tile_pos(r, cc)] = (TF)v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- weighted trace
 //
 // <W_i, F_i> summed over the stored lower tiles of every F_i: an entry (a, b)
@@ -346,6 +376,14 @@ void launch_adj_contract(const DevPlan& P, const AdjBatch* B, int nb, int max_ne
   if (nb <= 0 || max_nelem <= 0) return;
   dim3 grid((unsigned)std::min(max_nelem, 4096), (unsigned)nb);
   adj_contract_kernel<<<grid, kAT, 0, st>>>(P, B, nb, eldofs, eldk, elsc, work, g);
+}
+
+void launch_zgather_tiles(const DevPlan& P, const AdjBatch* B, int nb, const TileDesc* desc, const int* tile0,
+                          const double* work, bool fp32, void* F, int max_tiles, cudaStream_t st) {
+  if (nb <= 0) return;
+  dim3 grid((unsigned)std::max(1, std::min(max_tiles, 1024)), (unsigned)nb);
+  if (fp32) zgather_tiles_kernel<float><<<grid, kAT, 0, st>>>(P, B, desc, tile0, work, (float*)F);
+  else zgather_tiles_kernel<double><<<grid, kAT, 0, st>>>(P, B, desc, tile0, work, (double*)F);
 }
 
 void launch_weighted_trace(bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,

@@ -227,7 +227,7 @@ __device__ __forceinline__ const double* child_update(const DevPlan& P, int gc, 
 template <int TEAM>
 __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const double* K, double* L, double rho,
                              double* Fp, const double* stack, const double* smallreg, double* Uout, int* bad,
-                             int tid) {
+                             int tid, bool factor = true) {
   const int gs = S.sn0 + s;
   const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
   const int np = f * (f + 1) / 2;
@@ -259,7 +259,7 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
   // rank-kPB update to the trailing triangle, kPB FMAs per element
   constexpr int kPB = 8;
   const int lane = tid & 31;
-  for (int j0 = 0; j0 < w; j0 += kPB) {
+  for (int j0 = 0; factor && j0 < w; j0 += kPB) {
     const int jb = min(kPB, w - j0);
     if (tid < 32) {
       for (int j = j0; j < j0 + jb; ++j) {
@@ -329,9 +329,13 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
 // Phase 1: the small subtrees, level by level from the leaves, one warp per
 // front.  Phase 2: the remaining supernodes in postorder, fronts up to
 // kMidFront in shared memory across the CTA, larger ones by the tiled path.
+// flags: kCholNoReg factors K itself (no fixing-DOF penalty); kCholStopRoot
+// assembles the last (root) supernode's front but does not eliminate it, so
+// with the DOFs B touches ordered last the root panel holds the Schur
+// complement of the interior onto them (lower triangle, column-major).
 __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
                                                          double* ws, int64_t ws_stride, int64_t front_sz,
-                                                         int64_t stack_sz, int* status) {
+                                                         int64_t stack_sz, int flags, int* status) {
   extern __shared__ double dsm[];
   Smem& sm = *reinterpret_cast<Smem*>(dsm);
   __shared__ int bad;
@@ -357,6 +361,7 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
     double rho = red[0];
     for (int k = 1; k < kThreads / 32; ++k) rho = fmax(rho, red[k]);
     if (tid == 0) P.rho[si] = rho;
+    if (flags & kCholNoReg) rho = 0.0;
     // phase 1: small subtrees, one warp per front
     const int* lvo = P.lvl_off + S.lvl0;
     double* Fw = dsm + warp * kWarpSlot;
@@ -369,7 +374,8 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
         const int gs = S.sn0 + s;
         if (!P.sn_small[gs]) continue;
         double* Uout = P.sn_parent[gs] >= 0 ? smallreg + P.usm_ofs[gs] : nullptr;
-        packed_front<32>(P, S, s, K, L, rho, Fw, stack, smallreg, Uout, &bad, lane);
+        packed_front<32>(P, S, s, K, L, rho, Fw, stack, smallreg, Uout, &bad, lane,
+                         !((flags & kCholStopRoot) && s == S.nsn - 1));
       }
       __syncthreads();
     }
@@ -379,8 +385,9 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
       if (P.sn_small[gs]) continue;
       const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
       double* Uout = P.sn_parent[gs] >= 0 ? stack + P.upd_ofs[gs] : nullptr;
+      const bool factor = !((flags & kCholStopRoot) && s == S.nsn - 1);
       if (f <= kMidFront) {
-        packed_front<kThreads>(P, S, s, K, L, rho, dsm, stack, smallreg, Uout, &bad, tid);
+        packed_front<kThreads>(P, S, s, K, L, rho, dsm, stack, smallreg, Uout, &bad, tid, factor);
         continue;
       }
       double* Ls = L + P.Lofs[gs];
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
         }
       }
       __syncthreads();
-      factor_front(sm, Ls, f, w, W, r, &bad);
+      if (factor) factor_front(sm, Ls, f, w, W, r, &bad);
       __syncthreads();
       if (Uout)
         for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) Uout[idx] = W[idx];
@@ -670,11 +677,13 @@ __device__ __forceinline__ float round_tf32(float x) {
 // Work items (subdomain, first sorted column ca) cover the columns [ca, ca + cw) (cw = 0: all of them):
 // the columns of X are independent, so a subdomain's columns can be split over several CTAs.  Every
 // supernode then handles J_s restricted to the block; the restricted ranges nest like J_s itself.
+// X2 (FP32 X only): also write each finished block as bf16 hi/lo halves (hi = bf16(x), lo = bf16(x - hi)),
+// per column wp hi values then wp lo values, for the split-bf16 SYRK.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2* items, int nitems, int cw,
                                                          int* queue, T* X, T* ws, int64_t ws_stride,
                                                          int64_t front_sz, int tcmode, int tf32_out, int unit,
-                                                         int* status) {
+                                                         uint16_t* X2, int* status) {
   __shared__ SolveSmem<T> sm;
   __shared__ uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -721,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
       const int s = P.act[S.act0 + a];
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
       const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
-      const int wp = (w + 3) & ~3;
+      const int wp = (w + 7) & ~7;
       const int jb = max(P.jb[bs], ca), je = min(P.je[bs], cb), jo = max(P.jo[bs], ca);
       const int J = je - jb;
       if (J <= 0) continue;  // no column of this block reaches s (nor any of its descendants)
@@ -757,6 +766,17 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
         // X_s is final here (the parent reads only the bottom rows W2)
         if (tf32_out)
           for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) Xs[idx] = round_tf32(Xs[idx]);
+        if (X2) {
+          __nv_bfloat16* h2 =
+              reinterpret_cast<__nv_bfloat16*>(X2) + 2 * (S.X + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp);
+          for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) {
+            const int64_t j = idx / wp, k = idx - j * wp;
+            const float v = Xs[idx];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            h2[2 * j * wp + k] = hi;
+            h2[2 * j * wp + wp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+          }
+        }
       }
       if (P.sn_parent[gs] >= 0) {
         T* dst = stack + P.rhs_ofs[bs];
@@ -783,10 +803,11 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
 }  // namespace
 
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st) {
+                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st, int flags) {
   const int smem = kFrontSmem * 8;
   cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  chol_kernel<<<grid, kThreads, smem, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, stack_sz, status);
+  chol_kernel<<<grid, kThreads, smem, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, stack_sz, flags,
+                                            status);
 }
 
 int chol_ctas_per_sm() {
@@ -799,15 +820,15 @@ int chol_ctas_per_sm() {
 
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit) {
+                 cudaStream_t st, int unit, uint16_t* X2) {
   if (fp32) {
     const int smem = tcmode > 0 ? (tcmode == 2 ? 2 : 1) * (kTcOpA + kTcOpB) + 1024 : 0;
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, (float*)X, (float*)ws,
-                                                     2 * ws_stride, front_sz, tcmode, tf32_out, 0, status);
+                                                     2 * ws_stride, front_sz, tcmode, tf32_out, 0, X2, status);
   } else {
     trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, items, nitems, cw, queue, (double*)X, ws, ws_stride,
-                                                   front_sz, 0, 0, unit, status);
+                                                   front_sz, 0, 0, unit, nullptr, status);
   }
 }
 

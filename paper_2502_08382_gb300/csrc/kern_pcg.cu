@@ -279,6 +279,46 @@ __global__ void __launch_bounds__(kVT) lumped_apply_kernel(int nlam, const int* 
   }
 }
 
+// Dirichlet preconditioner v = W (sum_i B_i S_i B_i^T) W w in three vector steps around the tile apply of the
+// M_i = B_i S_i B_i^T tiles: t = W w scattered to both subdomain columns of each multiplier in the tile
+// precision (dir_pre), the tiles (apply core), u = the two column sums per multiplier (dir_mid), v = W u
+// (dir_post).  In an iteration (iteration = 1) every kernel returns at once once the iteration has stopped.
+template <typename TF>
+__global__ void __launch_bounds__(kVT) dir_pre_kernel(int nlam, const int* woff, const int* wcol, const double* wval,
+                                                      const double* w, const int* c0, const int* c1, TF* pg,
+                                                      const PcgCtrl* ctrl, int iteration) {
+  if (iteration && !ctrl->active) return;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int i = woff[l]; i < woff[l + 1]; ++i) t = fma(wval[i], w[wcol[i]], t);
+    pg[c0[l]] = (TF)t;
+    if (c1[l] >= 0) pg[c1[l]] = (TF)t;
+  }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(kVT) dir_mid_kernel(const int4* lc, int nlam, const TF* rowpart, const TF* colpart,
+                                                      double* u, const PcgCtrl* ctrl, int iteration) {
+  if (iteration && !ctrl->active) return;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    const int4 c = lc[l];
+    double f = colsum_at((int64_t)c.x, c.y & 255, c.y >> 8, rowpart, colpart);
+    if (c.z >= 0) f += colsum_at((int64_t)c.z, c.w & 255, c.w >> 8, rowpart, colpart);
+    u[l] = f;
+  }
+}
+
+__global__ void __launch_bounds__(kVT) dir_post_kernel(int nlam, const int* woff, const int* wcol, const double* wval,
+                                                       const double* u, double* v, const PcgCtrl* ctrl,
+                                                       int iteration) {
+  if (iteration && !ctrl->active) return;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlam; l += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int i = woff[l]; i < woff[l + 1]; ++i) t = fma(wval[i], u[wcol[i]], t);
+    v[l] = t;
+  }
+}
+
 // y = v - G z2 (the projection of v = M w; z2 = (G^T G)^{-1} G^T v, or none
 // without a coarse space), the scatter of y into the tile precision for the
 // next apply, and the dot w.y; the last block sets beta and w.y (set_direction).
@@ -379,6 +419,30 @@ void launch_lumped_apply(int nlam, const int* woff, const int* wcol, const doubl
                          const int* mcol, const double* mval, const double* w, double* v, const PcgCtrl* ctrl,
                          int iteration, cudaStream_t st) {
   lumped_apply_kernel<<<vgrid(nlam), kVT, 0, st>>>(nlam, woff, wcol, wval, moff, mcol, mval, w, v, ctrl, iteration);
+}
+
+void launch_dir_pre(bool fp32, int nlam, const int* woff, const int* wcol, const double* wval, const double* w,
+                    const int* c0, const int* c1, void* pg, const PcgCtrl* ctrl, int iteration, cudaStream_t st) {
+  if (fp32)
+    dir_pre_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(nlam, woff, wcol, wval, w, c0, c1, (float*)pg, ctrl, iteration);
+  else
+    dir_pre_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(nlam, woff, wcol, wval, w, c0, c1, (double*)pg, ctrl,
+                                                        iteration);
+}
+
+void launch_dir_mid(bool fp32, const int4* lc, int nlam, const void* rowpart, const void* colpart, double* u,
+                    const PcgCtrl* ctrl, int iteration, cudaStream_t st) {
+  if (fp32)
+    dir_mid_kernel<float><<<vgrid(nlam), kVT, 0, st>>>(lc, nlam, (const float*)rowpart, (const float*)colpart, u,
+                                                       ctrl, iteration);
+  else
+    dir_mid_kernel<double><<<vgrid(nlam), kVT, 0, st>>>(lc, nlam, (const double*)rowpart, (const double*)colpart, u,
+                                                        ctrl, iteration);
+}
+
+void launch_dir_post(int nlam, const int* woff, const int* wcol, const double* wval, const double* u, double* v,
+                     const PcgCtrl* ctrl, int iteration, cudaStream_t st) {
+  dir_post_kernel<<<vgrid(nlam), kVT, 0, st>>>(nlam, woff, wcol, wval, u, v, ctrl, iteration);
 }
 
 void launch_pcg_proj(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,

@@ -9,12 +9,13 @@
 // supernode rows.
 //
 // Staging: 16-byte cp.async (zero-filled outside J_s and beyond w_s) writes
-// each 128 x 32 FP32 chunk into the canonical 128-byte-swizzled K-major
-// layout (8-row atoms of 1024 B).  One thread issues tcgen05.mma kind::tf32
+// each 128 x 32 FP32 chunk (TF32) or 128 x 64 bf16 chunk (split bf16, from the
+// hi/lo copy of X the TRSM writes) into the canonical 128-byte-swizzled
+// K-major layout (8-row atoms of 1024 B).  One thread issues tcgen05.mma kind::tf32
 // (M = N = 128, K = 8) into a 128-column TMEM accumulator and commits to a
 // per-stage mbarrier, which releases the stage for the next cp.async.  The
 // epilogue reads TMEM with tcgen05.ld 32x32b and writes the 64 x 64 storage
-// tiles of the lower triangle.  SPLIT = 1 stages bf16 hi/lo halves of each
+// tiles of the lower triangle.  SPLIT = 1 stages the bf16 hi/lo halves of each
 // FP32 value and accumulates hi*hi + hi*lo + lo*hi (kind::f16 with bf16).
 // All waits are bounded; on timeout the kernel flags kStatTimeout, drains its
 // copies, frees TMEM and returns.
@@ -56,10 +57,13 @@ struct Cfg {
 };
 
 // Stage the chunk (supernode s, rows k0..k0+KC) of the A rows (tile block BI)
-// and B rows (tile block BJ).
+// and B rows (tile block BJ).  TF32: from the FP32 X block Xs.  Split bf16:
+// from the pre-split copy X2 (per column: wp bf16 hi values, then wp lo
+// values), so every 16-byte chunk of the swizzled layout is one cp.async;
+// on a diagonal tile (BI = BJ) B equals A and only A is staged.
 template <int SPLIT>
-__device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, int wp, int w, int J, int ca, int cb,
-                                           int k0, const float* safe) {
+__device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, const uint16_t* X2s, int wp, int w, int J,
+                                           int ca, int cb, int k0, const void* safe, bool diag) {
   const int tid = threadIdx.x;
   if constexpr (!SPLIT) {
     const uint32_t sA = smem_u32(stage), sB = sA + kOpBytes;
@@ -70,48 +74,31 @@ __device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, int 
       const int x = (op ? cb : ca) + m;
       const int k = k0 + 4 * c;
       const bool ok = x >= 0 && x < J && k < w;
-      const float* src = ok ? Xs + (int64_t)x * wp + k : safe;
+      const void* src = ok ? (const void*)(Xs + (int64_t)x * wp + k) : safe;
       const uint32_t dst = (op ? sB : sA) + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
       cp_async16(dst, src, ok);
     }
   } else {
-    // bf16 hi/lo split: 64 K values per 128-byte row; each thread converts 8 floats -> one 16 B chunk
-    uint8_t* base = stage;
-    for (int idx = tid; idx < 2 * kM * 8; idx += kTcThreads) {
-      const int op = idx / (kM * 8), rem = idx % (kM * 8);
+    // parts: 0 A hi, 1 A lo, 2 B hi, 3 B lo; 64 K values (8 chunks of 8 bf16) per 128-byte row
+    const uint32_t s0 = smem_u32(stage);
+    const int nparts = diag ? 2 : 4;
+    for (int idx = tid; idx < nparts * kM * 8; idx += kTcThreads) {
+      const int part = idx / (kM * 8), rem = idx % (kM * 8);
       const int m = rem / 8, c = rem % 8;
-      const int x = (op ? cb : ca) + m;
-      float v[8];
-#pragma unroll
-      for (int e = 0; e < 8; e += 4) {
-        const int k = k0 + 8 * c + e;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (x >= 0 && x < J && k < w) q = __ldg(reinterpret_cast<const float4*>(Xs + (int64_t)x * wp + k));
-        v[e] = q.x;
-        v[e + 1] = q.y;
-        v[e + 2] = q.z;
-        v[e + 3] = q.w;
-      }
-      __nv_bfloat162 hi[4], lo[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
-        hi[e] = __halves2bfloat162(h0, h1);
-        lo[e] = __halves2bfloat162(__float2bfloat16_rn(v[2 * e] - __bfloat162float(h0)),
-                                   __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1)));
-      }
-      const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
-      uint8_t* ph = base + (op ? 2 : 0) * kOpBytes + off;
-      uint8_t* pl = base + (op ? 3 : 1) * kOpBytes + off;
-      *reinterpret_cast<uint4*>(ph) = *reinterpret_cast<uint4*>(hi);
-      *reinterpret_cast<uint4*>(pl) = *reinterpret_cast<uint4*>(lo);
+      const int x = (part < 2 ? ca : cb) + m;
+      const int k = k0 + 8 * c;
+      const bool ok = x >= 0 && x < J && k < w;
+      const void* src = ok ? (const void*)(X2s + 2 * (int64_t)x * wp + ((part & 1) ? wp : 0) + k) : safe;
+      const uint32_t dst = s0 + part * kOpBytes + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+      cp_async16(dst, src, ok);
     }
   }
 }
 
 template <int SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const int2* items, int nitems,
-                                                                const float* X, float* F, int* status) {
+                                                                const float* X, const uint16_t* X2, float* F,
+                                                                int* status) {
   using C = Cfg<SPLIT>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[kStages];
@@ -151,14 +138,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
       nch += (w + C::kKC - 1) / C::kKC;
     }
     const float* Xsub = X + S.X;
+    const uint16_t* X2sub = X2 + 2 * S.X;
+    const bool diag = BI == BJ;
     Cursor cur{cbeg, 0};
     auto issue = [&](int i) {
       // load local chunk i (the cursor walks the chunks in order)
       const int s = P.t2_sn[cur.c];
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
-      const int w = P.sn_w[gs], wp = (w + 3) & ~3, jb = P.jb[bs], J = P.je[bs] - jb;
+      const int w = P.sn_w[gs], wp = (w + 7) & ~7, jb = P.jb[bs], J = P.je[bs] - jb;
       uint8_t* stage = smem + ((g0 + i) % kStages) * C::kStageBytes;
-      load_chunk<SPLIT>(stage, Xsub + P.Xofs[bs], wp, w, J, BI * kM - jb, BJ * kM - jb, cur.k0, X);
+      load_chunk<SPLIT>(stage, Xsub + P.Xofs[bs], X2sub + 2 * P.Xofs[bs], wp, w, J, BI * kM - jb, BJ * kM - jb,
+                        cur.k0, SPLIT ? (const void*)X2 : (const void*)X, diag);
       cur.k0 += C::kKC;
       if (cur.k0 >= w) {
         cur.c++;
@@ -195,7 +185,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
             for (int kk = 0; kk < 4; ++kk) {
               const uint32_t o = kk * 32;
               const uint64_t ah = sw128_desc(sbase + o), al = sw128_desc(sbase + kOpBytes + o);
-              const uint64_t bh = sw128_desc(sbase + 2 * kOpBytes + o), bl = sw128_desc(sbase + 3 * kOpBytes + o);
+              const uint64_t bh = diag ? ah : sw128_desc(sbase + 2 * kOpBytes + o);
+              const uint64_t bl = diag ? al : sw128_desc(sbase + 3 * kOpBytes + o);
               mma_f16(tmem, ah, bh, idesc, (j > 0 || kk > 0) ? 1u : 0u);
               mma_f16(tmem, ah, bl, idesc, 1u);
               mma_f16(tmem, al, bh, idesc, 1u);
@@ -272,15 +263,15 @@ size_t syrk_tc_smem(int split) {
   return (size_t)kStages * (split ? Cfg<1>::kStageBytes : Cfg<0>::kStageBytes) + 1024;
 }
 
-void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid, int split,
-                    int* status, cudaStream_t st) {
+void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
+                    int grid, int split, int* status, cudaStream_t st) {
   size_t smem = syrk_tc_smem(split);
   if (split) {
     cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    syrk_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, F, status);
+    syrk_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
   } else {
     cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    syrk_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, F, status);
+    syrk_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
   }
 }
 

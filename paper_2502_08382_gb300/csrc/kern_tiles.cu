@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) syrk_f64_kernel(DevPlan P, const int
     for (int c = tl[t]; c < tl[t + 1]; ++c) {
       const int s = P.tile_sn[c];
       const int gs = S.sn0 + s, bs = S.bsn0 + s;
-      const int w = P.sn_w[gs], wp = (w + 3) & ~3, jb = P.jb[bs], J = P.je[bs] - jb;
+      const int w = P.sn_w[gs], wp = (w + 7) & ~7, jb = P.jb[bs], J = P.je[bs] - jb;
       const double* Xs = X + S.X + P.Xofs[bs];
       const int ca = bi * kT - jb, cb = bj * kT - jb;
       for (int k0 = 0; k0 < w; k0 += 32) {
@@ -95,7 +95,45 @@ __global__ void unpack_F_kernel(const TF* Fsub, int m, int nb, int vr, const int
   }
 }
 
+// M_i tiles in the layout and sorted column order of F_i from the Schur complement S_i that an unfactored
+// root front holds (the DOFs B touches ordered last): M[a][b] = s_a s_b S[t_a][t_b], with t the position of
+// column a's DOF in the root block and s_a the sign of B in that column.  M_i = B_i S_i B_i^T restricted to
+// the subdomain's multipliers, the local block of the Dirichlet preconditioner.
+template <typename TF>
+__global__ void schur_tiles_kernel(DevPlan P, const TileDesc* desc, int ntiles, TF* M) {
+  constexpr int E = (int)sizeof(TF), V = 16 / E;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileDesc d = desc[t];
+    const bool diag = (d.flags & kTileDiag) != 0;
+    const SubInfo& S = P.sub[P.colsub[d.prow]];
+    const int gr = S.sn0 + S.nsn - 1;
+    const int c0 = P.sn_c0[gr], f = P.sn_w[gr] + P.sn_r[gr];
+    const double* Ls = P.L + S.L + P.Lofs[gr];
+    const int* iperm = P.iperm + S.diag0;
+    TF* Mt = M + d.f_ofs;
+    for (int idx = threadIdx.x; idx < d.rows * kT; idx += blockDim.x) {
+      const int r = idx / kT, cc = idx % kT;
+      if (diag && cc >= V * ((r + V) / V)) continue;  // not stored
+      const int a = d.prow + r, b = d.pcol + cc;
+      double v = 0.0;
+      if (!(diag && cc > r) && P.qmap[a] >= 0 && P.qmap[b] >= 0) {
+        const int ia = iperm[P.qdof[a]] - c0, ib = iperm[P.qdof[b]] - c0;
+        const int hi = max(ia, ib), lo = min(ia, ib);
+        v = P.qsign[a] * P.qsign[b] * Ls[(int64_t)lo * f + hi];
+      }
+      Mt[diag ? diag_pos<E>(r, cc) : tile_pos(r, cc)] = (TF)v;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_schur_tiles(const DevPlan& P, const TileDesc* desc, int ntiles, bool fp32, void* M, int grid,
+                        cudaStream_t st) {
+  if (ntiles <= 0) return;
+  if (fp32) schur_tiles_kernel<float><<<grid, 256, 0, st>>>(P, desc, ntiles, (float*)M);
+  else schur_tiles_kernel<double><<<grid, 256, 0, st>>>(P, desc, ntiles, (double*)M);
+}
 
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st) {

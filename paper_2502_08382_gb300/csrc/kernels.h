@@ -7,15 +7,19 @@
 
 namespace feti {
 
+// flags: kCholNoReg (factor K, not K_reg), kCholStopRoot (leave the root front assembled, unfactored)
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st);
+                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st, int flags = 0);
 int chol_ctas_per_sm();
 // items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
+// X2 (FP32 X only, may be null): also write each finished X block split into bf16 hi/lo halves for the
+// split-bf16 SYRK (per column: wp hi values, then wp lo values; X2 has 2 bf16 per X element)
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit = 0);
-void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, float* F, int grid,
-                    int split, int* status, cudaStream_t st);
+                 cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr);
+// X2 (split mode): the bf16 hi/lo copy of X written by the TRSM (per column: wp hi values, then wp lo values)
+void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
+                    int grid, int split, int* status, cudaStream_t st);
 size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);
@@ -75,6 +79,15 @@ void launch_lumped_values(int64_t nnz, const int64_t* c_off, const int64_t* kidx
 void launch_lumped_apply(int nlam, const int* woff, const int* wcol, const double* wval, const int* moff,
                          const int* mcol, const double* mval, const double* w, double* v, const PcgCtrl* ctrl,
                          int iteration, cudaStream_t st);
+// Dirichlet preconditioner (kern_pcg.cu, kern_tiles.cu)
+void launch_schur_tiles(const DevPlan& P, const TileDesc* desc, int ntiles, bool fp32, void* M, int grid,
+                        cudaStream_t st);
+void launch_dir_pre(bool fp32, int nlam, const int* woff, const int* wcol, const double* wval, const double* w,
+                    const int* c0, const int* c1, void* pg, const PcgCtrl* ctrl, int iteration, cudaStream_t st);
+void launch_dir_mid(bool fp32, const int4* lc, int nlam, const void* rowpart, const void* colpart, double* u,
+                    const PcgCtrl* ctrl, int iteration, cudaStream_t st);
+void launch_dir_post(int nlam, const int* woff, const int* wcol, const double* wval, const double* u, double* v,
+                     const PcgCtrl* ctrl, int iteration, cudaStream_t st);
 void launch_pcg_proj(bool fp32, const int4* lg, const int* c0, const int* c1, int nlam, const double* G6,
                      const double* z2, const double* v, const double* w, double* y, void* pg, double* part, int mode,
                      PcgCtrl* ctrl, cudaStream_t st);
@@ -92,6 +105,10 @@ void launch_adj_bsolve(const DevPlan& P, const AdjBatch* B, const int2* items, i
                        int grid, cudaStream_t st);
 void launch_adj_contract(const DevPlan& P, const AdjBatch* B, int nb, int max_nelem, const int* eldofs,
                          const double* eldk, const double* elsc, const double* work, double* g, cudaStream_t st);
+// TRSM-path assembly: F_i tiles from the rows of Z_i = K_reg^{-1} B_i^T at the B DOFs (desc: tiles in
+// subdomain-major order, tile0: the subdomain's first tile)
+void launch_zgather_tiles(const DevPlan& P, const AdjBatch* B, int nb, const TileDesc* desc, const int* tile0,
+                          const double* work, bool fp32, void* F, int max_tiles, cudaStream_t st);
 void launch_weighted_trace(bool fp32, const TileDesc* desc, int ntiles, const void* F, const int* qmap,
                            const int* colsub, const int* colperm, const SubInfo* sub, const int64_t* woff,
                            const double* W, double* part, double* out, int grid, cudaStream_t st);

@@ -221,7 +221,7 @@ uint64_t hash_pattern(int n, const int64_t* rowptr, const int32_t* col) {
 }
 
 void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double* coords,
-                     const SymbolicOptions& opt, PatternPlan& P) {
+                     const SymbolicOptions& opt, PatternPlan& P, const int32_t* last, int nlast) {
   P = PatternPlan();
   P.n = n;
   // ---------------- ordering on the compressed graph
@@ -233,16 +233,32 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
       for (int a = 0; a < 3; ++a) xyz[3 * v + a] = coords[3 * (size_t)g.dof0[v] + a];
   }
   ND nd(g, xyz.empty() ? nullptr : xyz.data(), opt.leaf_dofs);
+  std::vector<char> is_last(g.nv, 0);
+  if (last && nlast > 0) {
+    std::vector<int> node_of(n);
+    for (int v = 0; v < g.nv; ++v)
+      for (int k = 0; k < g.ndof[v]; ++k) node_of[g.dof0[v] + k] = v;
+    for (int k = 0; k < nlast; ++k) {
+      if (last[k] < 0 || last[k] >= n) throw std::runtime_error("a DOF to order last is out of range");
+      is_last[node_of[last[k]]] = 1;
+    }
+  }
   {
-    std::vector<int> all(g.nv);
-    std::iota(all.begin(), all.end(), 0);
-    nd.run(std::move(all));
+    std::vector<int> rest, tail;
+    for (int v = 0; v < g.nv; ++v) (is_last[v] ? tail : rest).push_back(v);
+    nd.run(std::move(rest));
+    nd.order.insert(nd.order.end(), tail.begin(), tail.end());
   }
   std::vector<int> perm0;
   perm0.reserve(n);
+  int n_tail = 0;
   for (int v : nd.order)
-    for (int k = 0; k < g.ndof[v]; ++k) perm0.push_back(g.dof0[v] + k);
+    for (int k = 0; k < g.ndof[v]; ++k) {
+      perm0.push_back(g.dof0[v] + k);
+      n_tail += is_last[v] ? 1 : 0;
+    }
   if ((int)perm0.size() != n) throw std::runtime_error("ordering lost DOFs");
+  P.nlast = n_tail;
 
   // ---------------- elimination tree (Liu) in perm0 numbering
   auto etree_of = [&](const std::vector<int>& perm, const std::vector<int>& iperm, std::vector<int>& parent) {
@@ -324,11 +340,16 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
   }
 
   // ---------------- fundamental supernodes
+  // (the trailing n_tail columns, the DOFs ordered last, are the etree's top: one supernode)
   std::vector<int> sc0;  // first column of each supernode
   for (int j = 0; j < n; ++j) {
     bool merge = j > 0 && parent[j - 1] == j && cc[j - 1] == cc[j] + 1 && nchild[j] == 1;
+    if (n_tail > 0 && j >= n - n_tail) merge = j > n - n_tail;
     if (!merge) sc0.push_back(j);
   }
+  if (n_tail > 0)
+    for (int j = n - n_tail; j + 1 < n; ++j)
+      if (parent[j] != j + 1) throw std::runtime_error("the DOFs ordered last do not form the top of the tree");
   int ns0 = (int)sc0.size();
   std::vector<int> w0(ns0), f0(ns0), col2sn0(n), spar0(ns0, -1);
   for (int s = 0; s < ns0; ++s) {
@@ -364,6 +385,7 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
   for (int p = 0; p < ns0; ++p) {
     // candidate: the supernode ending right before p's first column (p's last child in postorder)
     while (gc0[p] > 0) {
+      if (n_tail > 0 && gc0[p] >= n - n_tail) break;  // nothing is merged into the forced root
       int s = find(col2sn0[gc0[p] - 1]);
       if (!alive[s] || s == p) break;
       if (spar0[s] < 0 || find(spar0[s]) != p) break;

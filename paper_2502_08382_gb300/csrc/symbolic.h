@@ -21,7 +21,7 @@ constexpr int kSmallFront = 40;
 constexpr int kMidFront = 112;
 
 // padded row length of a supernode X block (16-byte aligned rows)
-inline int xpad(int w) { return (w + 3) & ~3; }
+inline int xpad(int w) { return (w + 7) & ~7; }
 
 struct PatternPlan {
   int n = 0;
@@ -53,6 +53,7 @@ struct PatternPlan {
   // supernodes before large ones inside a level; update-vector offsets
   int nlev = 0;
   std::vector<int> lvl_off, lvl_sn;
+  int nlast = 0;  // columns of the forced root supernode (the DOFs ordered last), 0 if none
   std::vector<int64_t> uofs;  // per supernode, offset of its r-vector
   int64_t usize = 0;
 };
@@ -79,8 +80,12 @@ struct SymbolicOptions {
 };
 
 // K pattern: full symmetric CSR (rowptr int64, col int32).  coords: n x 3 or null.
+// last (may be null, nlast entries): DOFs ordered last, as one root supernode (every DOF of a node that
+// holds one of them goes with it); the other DOFs are ordered by nested dissection before them.  With the
+// DOFs that B touches last, the root front assembled from its children is the Schur complement of the
+// interior onto them, and X = L^{-1} P B^T is nonzero in the root block only.
 void analyse_pattern(int n, const int64_t* rowptr, const int32_t* col, const double* coords,
-                     const SymbolicOptions& opt, PatternPlan& out);
+                     const SymbolicOptions& opt, PatternPlan& out, const int32_t* last = nullptr, int nlast = 0);
 // B: m rows, B_dof[r] = local DOF of row r.
 void plan_rhs(const PatternPlan& pp, int m, const int32_t* B_dof, BPlan& out);
 

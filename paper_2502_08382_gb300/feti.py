@@ -50,7 +50,7 @@ class FetiOptions(C.Structure):
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
                 ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
-                ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64)]
+                ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64), ("assembly_route", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -68,10 +68,14 @@ class FetiStats(C.Structure):
                 ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double),
                 ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double),
-                ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32)]
+                ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32),
+                ("assembly_route", C.c_int32), ("route_ms", C.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["route_ms"] = list(self.route_ms)
+        return d
+
 
 
 EXPORTS = ["feti_create", "feti_update_values", "feti_assemble", "feti_apply", "feti_apply_implicit",
@@ -188,7 +192,7 @@ def subdomain_struct(s, keep):
     return m.subs[0]
 
 
-def analyse(sub, leaf_dofs=16, use_coords=True):
+def analyse(sub, leaf_dofs=16, use_coords=True, route="syrk"):
     """Host-only symbolic analysis of one subdomain (no GPU): returns a dict
     of the plan's statistics, the permutation and the supernode partition."""
     lib = load_library()
@@ -197,6 +201,7 @@ def analyse(sub, leaf_dofs=16, use_coords=True):
     opt = FetiOptions()
     opt.leaf_dofs = leaf_dofs
     opt.use_coords = 1 if use_coords else 0
+    opt.assembly_route = {"syrk": 0, "schur": 1}[route]
     info = np.zeros(16)
     perm = np.zeros(sub.n, dtype=np.int32)
     snb = np.zeros(4 * sub.n, dtype=np.int32)
@@ -205,7 +210,7 @@ def analyse(sub, leaf_dofs=16, use_coords=True):
     if rc != FETI_OK:
         raise FetiError(rc, "feti_analyse failed")
     keys = ["n", "nsn", "max_front", "max_width", "nnzL", "chol_flops", "Lsize", "m", "Xsize", "trsm_flops",
-            "syrk_flops", "ntile_contrib", "chol_stack", "rhs_stack", "nroots"]
+            "syrk_flops", "ntile_contrib", "chol_stack", "rhs_stack", "nroots", "nlast"]
     out = {k: info[i] for i, k in enumerate(keys)}
     ns = int(out["nsn"])
     out["perm"] = perm
@@ -221,15 +226,20 @@ class FetiOperator:
     feti_apply / feti_apply_implicit / feti_solve / feti_solve_warm / feti_adjoint).
 
     prec: "fp64", "tf32" or "split_bf16" (tensor-core TRSM updates and SYRK,
-    FP32 F tiles); refine_every / refine_drop / refine_restart: the FP64
+    FP32 F tiles); route: "syrk" (pruned TRSM + SYRK on a nested-dissection
+    ordering) or "schur" (the DOFs B touches ordered last, F_i from the
+    factor of their Schur complement); refine_every / refine_drop / refine_restart: the FP64
     residual replacement of the mixed solve; precond: "none" (M = I) or
-    "lumped" (M = (BB^T)^-1 sum_i B_i K_i B_i^T (BB^T)^-1)."""
+    "lumped" (M = (BB^T)^-1 sum_i B_i K_i B_i^T (BB^T)^-1) or "dirichlet"
+    (the same with the Schur complements S_i of K_i onto the DOFs B touches in
+    place of K_i; needs route="schur")."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
                  precond: str = "none", leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, per_element: bool = False,
-                 recompute_X: bool = False, adjoint_work_bytes: int = 0, torch_alloc: bool = True):
+                 recompute_X: bool = False, adjoint_work_bytes: int = 0, route: str = "syrk",
+                 torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -246,7 +256,7 @@ class FetiOperator:
         opt.refine_every = refine_every
         opt.refine_drop = refine_drop
         opt.refine_restart = 1 if refine_restart else 0
-        opt.precond = {"none": 0, "lumped": 1}[precond]
+        opt.precond = {"none": 0, "lumped": 1, "dirichlet": 2}[precond]
         opt.tol = tol
         opt.maxit = maxit
         opt.stream = C.c_void_p(self.stream.cuda_stream)
@@ -254,6 +264,7 @@ class FetiOperator:
         opt.use_coords = 1 if use_coords else 0
         opt.recompute_X = 1 if recompute_X else 0
         opt.adjoint_work_bytes = int(adjoint_work_bytes)
+        opt.assembly_route = {"syrk": 0, "schur": 1, "trsm": 2, "auto": 3}[route]
         self._cb = None
         if torch_alloc:
             dev = self.device.index

@@ -1,6 +1,10 @@
-"""The lumped preconditioner on the CUDA path (options.precond = 1):
-M = W (sum_i B_i K_i B_i^T) W with W = (B B^T)^{-1}, against the oracle's
-preconditioned Algorithm 1 and the monolithic FEM solve."""
+"""The preconditioners on the CUDA path, against the oracle's preconditioned
+Algorithm 1 and the monolithic FEM solve:
+  * lumped (options.precond = 1): M = W (sum_i B_i K_i B_i^T) W, W = (B B^T)^{-1};
+  * Dirichlet (options.precond = 2, with the Schur-complement assembly route):
+    M = W (sum_i B_i S_i B_i^T) W with S_i the Schur complement of K_i onto the
+    DOFs B_i touches, taken from a factorisation of K_i stopped at its root
+    front and applied as tiles like F_i."""
 import dataclasses
 
 import numpy as np
@@ -30,9 +34,9 @@ CASES = {
 }
 
 
-def _solve(P, prec, precond):
+def _solve(P, prec, precond, route="syrk"):
     from paper_2502_08382_gb300 import feti
-    kw = dict(tol=1e-12, maxit=3000, precond=precond)
+    kw = dict(tol=1e-12, maxit=3000, precond=precond, route=route)
     if prec != "fp64":
         kw.update(refine_drop=1e-4, refine_restart=True)
     op = feti.FetiOperator(P, prec=prec, **kw)
@@ -99,3 +103,32 @@ def test_lumped_values_follow_new_K(torch_cuda):
     assert abs(info["iterations"] - its_o) <= 2, (info["iterations"], its_o)
     err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P2.subs, _split(P2, u)))
     assert err <= 1e-10 * np.abs(um).max(), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_dirichlet_solve_matches_monolithic(torch_cuda, name, prec):
+    P = CASES[name]()
+    lam, u, info = _solve(P, prec, "dirichlet", route="schur")
+    lam0, u0, info0 = _solve(P, prec, "none")
+    um = O.monolithic_solve(P)
+    Fs = [O.local_F(s) for s in P.subs]
+    _, its_o, _ = O.pcpg(P, Fs, tol=1e-12, M=O.dirichlet_M(P))
+    _, its_l, _ = O.pcpg(P, Fs, tol=1e-12, M=O.scaled_lumped_M(P))
+    print(f"{name} {prec}: iterations Dirichlet {info['iterations']} (oracle {its_o}; lumped oracle {its_l}), "
+          f"none {info0['iterations']}")
+    assert info["converged"], info
+    err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P.subs, _split(P, u)))
+    assert err <= 1e-10 * np.abs(um).max(), err
+    e = O.e_vector(P)
+    assert np.abs(O.Gt_times(P, lam) - e).max() <= 1e-10 * max(1.0, np.abs(e).max())
+    assert np.linalg.norm(lam - lam0) <= 1e-8 * np.linalg.norm(lam0)
+    if prec == "fp64":
+        assert abs(info["iterations"] - its_o) <= 2, (info["iterations"], its_o)
+    assert info["iterations"] <= info0["iterations"], (info["iterations"], info0["iterations"])
+
+
+def test_dirichlet_needs_schur_route(torch_cuda):
+    from paper_2502_08382_gb300 import feti
+    with pytest.raises(feti.FetiError):
+        feti.FetiOperator(CASES["cfg1"](), prec="fp64", precond="dirichlet")
