@@ -31,7 +31,8 @@ def main():
     ap.add_argument("--refine-every", type=int, default=0)
     ap.add_argument("--refine-drop", type=float, default=1e-3)
     ap.add_argument("--restart", action="store_true", help="restart the CG direction after each FP64 residual")
-    ap.add_argument("--precond", default="none", choices=["none", "lumped"])
+    ap.add_argument("--precond", default="none", choices=["none", "lumped", "dirichlet"])
+    ap.add_argument("--route", default="syrk", choices=["syrk", "schur", "trsm", "auto"])
     args = ap.parse_args()
 
     import torch
@@ -43,7 +44,7 @@ def main():
     mixed = args.prec != "fp64"
     op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000, refine_every=args.refine_every if mixed else 0,
                            refine_drop=args.refine_drop if mixed else 0.0, refine_restart=args.restart,
-                           precond=args.precond)
+                           precond=args.precond, route=args.route)
     op.assemble()
     p = torch.from_numpy(seeded_vector(P.n_lambda, 0)).cuda()
     q = torch.empty_like(p)
@@ -86,8 +87,11 @@ def main():
                       "reps": args.reps, "ms": ms, "device_bytes": s["device_bytes"],
                       "apply_bytes": s["apply_bytes"], "implicit_bytes": s["implicit_bytes"],
                       "chol_flops": s["chol_flops"], "trsm_flops": s["trsm_flops"],
-                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every, "refine_drop": args.refine_drop, "restart": args.restart, "precond": args.precond,
-                      "solve": info, "launches": s["launches"], "profiled": prof}))
+                      "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every,
+                      "refine_drop": args.refine_drop, "restart": args.restart, "precond": args.precond,
+                      "route": args.route, "route_used": s["assembly_route"], "route_ms": s["route_ms"],
+                      "phases_ms": {k: s[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms")},
+                      "trsm_cols": s["trsm_cols"], "solve": info, "launches": s["launches"], "profiled": prof}))
     op.close()
 
 
