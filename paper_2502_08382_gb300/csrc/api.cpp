@@ -691,6 +691,7 @@ void build(feti_ctx* c) {
   D.Kval = c->d_Kval;
   c->d_L = (double*)dalloc(c, (size_t)Lo * 8);
   D.L = c->d_L;
+  if (c->fp32) c->d_L32 = (float*)dalloc(c, (size_t)std::max<int64_t>(Lo, 1) * 4);
   D.dinv = (double*)dalloc(c, (size_t)std::max<int64_t>(c->ndof, 1) * 8);
   D.rho = (double*)dalloc(c, (size_t)ns * 8);
   c->d_X = dalloc(c, (size_t)Xo * esz);
@@ -852,8 +853,8 @@ feti_status feti_create(const feti_problem* prob, const feti_options* opt, feti_
   if (ctx->opt.prec < FETI_PREC_FP64 || ctx->opt.prec > FETI_PREC_SPLIT_BF16) throw ArgError("bad precision");
   if (ctx->opt.precond < 0 || ctx->opt.precond > 2)
     throw ArgError("bad preconditioner (0 none, 1 lumped, 2 Dirichlet)");
-  if (ctx->opt.assembly_route < 0 || ctx->opt.assembly_route > 1)
-    throw ArgError("bad assembly route (0 SYRK path, 1 Schur complement)");
+  if (ctx->opt.assembly_route < 0 || ctx->opt.assembly_route > 3)
+    throw ArgError("bad assembly route (0 SYRK path, 1 Schur complement, 2 TRSM path, 3 autotuned 0 / 2)");
   ctx->st = (cudaStream_t)ctx->opt.stream;
   ctx->fp32 = ctx->opt.prec != FETI_PREC_FP64;
   ctx->nsub = prob->nsub;
@@ -919,7 +920,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->d_queue + 16, 0, sizeof(int), s2));
     launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
                 ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), tcmode, tf32_out,
-                ctx->d_status, s2, 0, split ? ctx->d_X2 : nullptr);
+                ctx->d_status, s2, 0, split ? ctx->d_X2 : nullptr, ctx->d_L32);
   };
   // the numeric phase as one sequence of launches (recorded once into a CUDA graph, see below); r2: the
   // TRSM-path route (F_i = B_i P^T L^{-T} X_i in host-driven batches, not captured)
@@ -941,6 +942,8 @@ feti_status feti_assemble(feti_ctx* ctx) {
       CK(cudaEventRecordWithFlags(ctx->ev[3], s2, evf));
       return;
     }
+    if (ctx->fp32)  // the mixed TRSM reads an FP32 copy of the factor
+      launch_l32(ctx->P.L, ctx->d_L32, ctx->stats.L_doubles, ctx->nsm * 8, s2);
     if (!ctx->trsm_tuned) {
       // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)
       for (auto& tc : ctx->trsm_cands) {
@@ -1020,7 +1023,6 @@ feti_status feti_assemble(feti_ctx* ctx) {
         enqueue(st, cudaEventRecordDefault, false);
         CK(cudaGetLastError());
       }
-      ctx->stats.assembly_route = ctx->route;
     }
     if (ctx->trsm_tuned && ctx->route != 2) {
       // later assemblies replay the same launches from a CUDA graph, captured on a private stream (the
@@ -1040,6 +1042,8 @@ feti_status feti_assemble(feti_ctx* ctx) {
     }
   }
   CK(cudaGetLastError());
+  ctx->stats.assembly_route = ctx->route;
+  for (int k = 0; k < 3; ++k) ctx->stats.route_ms[k] = ctx->route_ms[k];
   if (!ctx->coarse_ready) {
     // G = B R does not depend on the values of K: the coarse problem is set up once
     coarse_setup_entry(ctx);

@@ -147,6 +147,7 @@ struct feti_ctx {
   void* asm_X = nullptr;             // the X buffers the assembly graph was captured with
   void* asm_X2 = nullptr;
   uint16_t* d_X2 = nullptr;          // bf16 hi/lo copy of X (split-bf16 SYRK operands)
+  float* d_L32 = nullptr;            // FP32 copy of L for the mixed TRSM
   cudaGraphExec_t pcg_exec = nullptr;  // captured chunk of iterations (replayed on st)
   int pcg_chunk = 0;
   std::vector<cudaEvent_t> pcg_ev;  // 4 events per captured iteration (apply timing)

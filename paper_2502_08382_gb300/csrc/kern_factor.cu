@@ -457,99 +457,104 @@ struct TcState {
 };
 
 template <int MODE>
-__device__ bool panel_update_tc(TcState& tc, const double* Ls, int f, int w, int kb, int nbk, const float* Xs, int wp,
-                                float* Xw, float* W2, int r, int J) {
+__device__ bool panel_update_tc(TcState& tc, const float* Ls, int f, int rbeg, int rend, int kbeg, int kend,
+                                const float* Xs, int wp, float* Xw, float* W2, int w, int r, int J) {
+  // C[rbeg .. rend) -= L[rbeg .. rend, kbeg .. kend) X[kbeg .. kend) (C = own rows of X below w, W2 beyond),
+  // accumulated in TMEM over 32-deep chunks of K and written back once per 128 x 64 tile
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int i0 = kb + nbk;
   const uint32_t sA = smem_u32(tc.smem), sB = sA + (MODE == 2 ? 2 : 1) * kTcOpA;
   constexpr uint32_t idesc = idesc_m128(MODE == 2 ? 1u : 2u, (uint32_t)kTcCols);
-  for (int ri = i0; ri < f; ri += kTcRows) {
+  for (int ri = rbeg; ri < rend; ri += kTcRows) {
     for (int cj = 0; cj < J; cj += kTcCols) {
-      // stage A: row m, 16-byte chunk c (K values 4c..4c+3 in TF32, 8c..8c+7 in bf16)
-      for (int idx = tid; idx < kTcRows * 8; idx += kThreads) {
-        const int m = idx % kTcRows, c = idx / kTcRows;
-        const int i = ri + m;
-        const uint32_t off = (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
-        if constexpr (MODE == 1) {
-          float v[4];
+      for (int kc = kbeg; kc < kend; kc += kNB) {
+        const int nk = min(kNB, kend - kc);
+        // stage A: row m, 16-byte chunk c (K values 4c..4c+3 in TF32, 8c..8c+7 in bf16)
+        for (int idx = tid; idx < kTcRows * 8; idx += kThreads) {
+          const int m = idx % kTcRows, c = idx / kTcRows;
+          const int i = ri + m;
+          const uint32_t off = (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+          if constexpr (MODE == 1) {
+            float v[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 4 * c + e;
-            v[e] = (i < f && k < nbk) ? (float)Ls[(int64_t)(kb + k) * f + i] : 0.f;
-          }
-          *reinterpret_cast<float4*>(tc.smem + off) = make_float4(v[0], v[1], v[2], v[3]);
-        } else {
-          __nv_bfloat16 hi[8], lo[8];
+            for (int e = 0; e < 4; ++e) {
+              const int k = 4 * c + e;
+              v[e] = (i < rend && k < nk) ? Ls[(int64_t)(kc + k) * f + i] : 0.f;
+            }
+            *reinterpret_cast<float4*>(tc.smem + off) = make_float4(v[0], v[1], v[2], v[3]);
+          } else {
+            __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int k = 8 * c + e;
-            const float x = (i < f && k < nbk) ? (float)Ls[(int64_t)(kb + k) * f + i] : 0.f;
-            hi[e] = __float2bfloat16_rn(x);
-            lo[e] = __float2bfloat16_rn(x - __bfloat162float(hi[e]));
+            for (int e = 0; e < 8; ++e) {
+              const int k = 8 * c + e;
+              const float x = (i < rend && k < nk) ? Ls[(int64_t)(kc + k) * f + i] : 0.f;
+              hi[e] = __float2bfloat16_rn(x);
+              lo[e] = __float2bfloat16_rn(x - __bfloat162float(hi[e]));
+            }
+            *reinterpret_cast<uint4*>(tc.smem + off) = *reinterpret_cast<uint4*>(hi);
+            *reinterpret_cast<uint4*>(tc.smem + kTcOpA + off) = *reinterpret_cast<uint4*>(lo);
           }
-          *reinterpret_cast<uint4*>(tc.smem + off) = *reinterpret_cast<uint4*>(hi);
-          *reinterpret_cast<uint4*>(tc.smem + kTcOpA + off) = *reinterpret_cast<uint4*>(lo);
         }
-      }
-      // stage B: right-hand-side column n, its solved K values of this block
-      for (int idx = tid; idx < kTcCols * 8; idx += kThreads) {
-        const int n = idx % kTcCols, c = idx / kTcCols;
-        const int j = cj + n;
-        const uint32_t off = (n >> 3) * 1024 + (n & 7) * 128 + ((c ^ (n & 7)) << 4);
-        uint8_t* bB = tc.smem + (MODE == 2 ? 2 : 1) * kTcOpA;
-        if constexpr (MODE == 1) {
-          float v[4];
+        // stage B: right-hand-side column n, its solved K values kc .. kc + nk
+        for (int idx = tid; idx < kTcCols * 8; idx += kThreads) {
+          const int n = idx % kTcCols, c = idx / kTcCols;
+          const int j = cj + n;
+          const uint32_t off = (n >> 3) * 1024 + (n & 7) * 128 + ((c ^ (n & 7)) << 4);
+          uint8_t* bB = tc.smem + (MODE == 2 ? 2 : 1) * kTcOpA;
+          if constexpr (MODE == 1) {
+            float v[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 4 * c + e;
-            v[e] = (j < J && k < nbk) ? Xs[(int64_t)j * wp + kb + k] : 0.f;
-          }
-          *reinterpret_cast<float4*>(bB + off) = make_float4(v[0], v[1], v[2], v[3]);
-        } else {
-          __nv_bfloat16 hi[8], lo[8];
+            for (int e = 0; e < 4; ++e) {
+              const int k = 4 * c + e;
+              v[e] = (j < J && k < nk) ? Xs[(int64_t)j * wp + kc + k] : 0.f;
+            }
+            *reinterpret_cast<float4*>(bB + off) = make_float4(v[0], v[1], v[2], v[3]);
+          } else {
+            __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int k = 8 * c + e;
-            const float x = (j < J && k < nbk) ? Xs[(int64_t)j * wp + kb + k] : 0.f;
-            hi[e] = __float2bfloat16_rn(x);
-            lo[e] = __float2bfloat16_rn(x - __bfloat162float(hi[e]));
+            for (int e = 0; e < 8; ++e) {
+              const int k = 8 * c + e;
+              const float x = (j < J && k < nk) ? Xs[(int64_t)j * wp + kc + k] : 0.f;
+              hi[e] = __float2bfloat16_rn(x);
+              lo[e] = __float2bfloat16_rn(x - __bfloat162float(hi[e]));
+            }
+            *reinterpret_cast<uint4*>(bB + off) = *reinterpret_cast<uint4*>(hi);
+            *reinterpret_cast<uint4*>(bB + kTcOpB + off) = *reinterpret_cast<uint4*>(lo);
           }
-          *reinterpret_cast<uint4*>(bB + off) = *reinterpret_cast<uint4*>(hi);
-          *reinterpret_cast<uint4*>(bB + kTcOpB + off) = *reinterpret_cast<uint4*>(lo);
         }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t acc0 = kc > kbeg ? 1u : 0u;
+          if constexpr (MODE == 1) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)  // K = 8 per MMA, 32 B of each 128-byte row
+              mma_tf32(tc.tmem, sw128_desc(sA + kk * 32), sw128_desc(sB + kk * 32), idesc, (kk > 0) ? 1u : acc0);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {  // K = 16 per MMA; the chunk's 32 values fill half of each row
+              const uint64_t ah = sw128_desc(sA + kk * 32), al = sw128_desc(sA + kTcOpA + kk * 32);
+              const uint64_t bh = sw128_desc(sB + kk * 32), bl = sw128_desc(sB + kTcOpB + kk * 32);
+              mma_f16(tc.tmem, ah, bh, idesc, (kk > 0) ? 1u : acc0);
+              mma_f16(tc.tmem, ah, bl, idesc, 1u);
+              mma_f16(tc.tmem, al, bh, idesc, 1u);
+            }
+          }
+          mma_commit(smem_u32(tc.mbar));
+          if (!mbar_wait(smem_u32(tc.mbar), tc.phase & 1)) *tc.abort = 1;
+        }
+        __syncthreads();
+        tc.phase++;
+        if (*tc.abort) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if constexpr (MODE == 1) {
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)  // K = 8 per MMA, 32 B of each 128-byte row
-            mma_tf32(tc.tmem, sw128_desc(sA + kk * 32), sw128_desc(sB + kk * 32), idesc, kk > 0 ? 1u : 0u);
-        } else {
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {  // K = 16 per MMA; the block's 32 values fill half of each row
-            const uint64_t ah = sw128_desc(sA + kk * 32), al = sw128_desc(sA + kTcOpA + kk * 32);
-            const uint64_t bh = sw128_desc(sB + kk * 32), bl = sw128_desc(sB + kTcOpB + kk * 32);
-            mma_f16(tc.tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
-            mma_f16(tc.tmem, ah, bl, idesc, 1u);
-            mma_f16(tc.tmem, al, bh, idesc, 1u);
-          }
-        }
-        mma_commit(smem_u32(tc.mbar));
-        if (!mbar_wait(smem_u32(tc.mbar), tc.phase & 1)) *tc.abort = 1;
       }
-      __syncthreads();
-      tc.phase++;
-      if (*tc.abort) return false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows), columns 32 (w / 4) .. + 31
       {
         const int q = warp % 4, ch = warp / 4;
         uint32_t v[32];
         tmem_ld32(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
         const int i = ri + q * 32 + lane;
-        if (i < f) {
+        if (i < rend) {
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int j = cj + ch * 32 + e;
@@ -567,26 +572,72 @@ __device__ bool panel_update_tc(TcState& tc, const double* Ls, int f, int w, int
   return true;
 }
 
+// SIMT update of the same form for smaller fronts: C[rbeg .. rend) -= L[., kbeg .. kend) X[kbeg .. kend),
+// 64 x 64 register tiles accumulated over 32-deep chunks of K, written back once per tile.
+template <typename T>
+__device__ void panel_update_simt(SolveSmem<T>& sm, const T* Ls, int f, int rbeg, int rend, int kbeg, int kend,
+                                  T* Xs, int wp, T* W2, int w, int r, int J) {
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
+  const int TR = (rend - rbeg + kT - 1) / kT, TC = (J + kT - 1) / kT;
+  for (int ti = 0; ti < TR; ++ti) {
+    for (int tcol = 0; tcol < TC; ++tcol) {
+      const int ri = rbeg + ti * kT, cj = tcol * kT;
+      // rows tx + 16u (all 16 tx per warp), columns ty + 16v (ty = 2 warp, 2 warp + 1)
+      const int nu = groups16(rend - ri), nv = groups16(J - cj - 2 * warp);
+      T acc[4][4] = {};
+      for (int kc = kbeg; kc < kend; kc += kNB) {
+        const int nk = min(kNB, kend - kc);
+        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
+          int x = idx % kT, k = idx / kT;
+          sm.A[k][x] = (k < nk && ri + x < rend) ? Ls[(int64_t)(kc + k) * f + ri + x] : (T)0;
+        }
+        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
+          int k = idx % kNB, y = idx / kNB;
+          sm.B[k][y] = (k < nk && cj + y < J) ? Xs[(int64_t)(cj + y) * wp + kc + k] : (T)0;
+        }
+        __syncthreads();
+        tile_mma_dispatch<T, false>(sm.A, sm.B, nk, acc, tx, ty, nu, nv);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        int col = cj + ty + 16 * v;
+        if (v >= nv || col >= J) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int i = ri + tx + 16 * u;
+          if (u >= nu || i >= rend) continue;
+          if (i < w) Xs[(int64_t)col * wp + i] -= acc[u][v];
+          else W2[(int64_t)col * r + (i - w)] -= acc[u][v];
+        }
+      }
+    }
+  }
+}
+
 // Forward solve of one RHS front: X_s = L_ss^{-1} X_s, then C -= L_rs X_s
 // (C = the r bottom rows).  Column-major fronts: column j of X_s is
 // Xs[j * wp + 0 .. w), column j of the bottom block is W2[j * r + 0 .. r).
-// Each 32-row diagonal block is applied as its explicit inverse (computed in
-// the solve's precision T from L_bb), so the block solve is a small GEMM.
+// L is read in the solve's precision T (the mixed path reads the FP32 copy of
+// L).  The own rows are solved right-looking in 32-row blocks: each block is
+// applied as its explicit inverse (a small GEMM), then the own rows below it
+// are updated.  The bottom rows are updated once at the end with K = w
+// (accumulated over all blocks before one write-back of W2).
 template <typename T>
-__device__ bool solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T* Xs, int wp, T* W2, int J,
+__device__ bool solve_front(SolveSmem<T>& sm, const T* Ls, int f, int w, T* Xs, int wp, T* W2, int J,
                             TcState* tc, int tcmode, int unit) {
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
+  const int tid = threadIdx.x, warp = tid / 32;
   const int r = f - w;
   auto Di = reinterpret_cast<T (*)[kNB + 1]>(&sm.B[0][0]);
   for (int kb = 0; kb < w; kb += kNB) {
     const int nbk = min(kNB, w - kb);
     for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
       int i = idx % kNB, j = idx / kNB;
-      sm.D[i][j] = (i < nbk && j <= i) ? (T)Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
+      sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
     }
     // unit: L is in unit-lower form (pivots folded out after the assembly), its stored diagonal is zero
     if (tid < kNB)
-      sm.dinv[tid] = tid < nbk ? (unit ? (T)1 : (T)(1.0 / Ls[(int64_t)(kb + tid) * f + kb + tid])) : (T)0;
+      sm.dinv[tid] = tid < nbk ? (unit ? (T)1 : (T)1 / Ls[(int64_t)(kb + tid) * f + kb + tid]) : (T)0;
     __syncthreads();
     if (warp == 0) warp_tri_inverse<T>(sm.D, sm.dinv, Di, nbk);
     __syncthreads();
@@ -617,48 +668,30 @@ __device__ bool solve_front(SolveSmem<T>& sm, const double* Ls, int f, int w, T*
         __syncthreads();
       }
     }
+    // the own rows below the block
     const int i0 = kb + nbk;
+    if (i0 < w) {
+      if constexpr (sizeof(T) == 4) {
+        if (tcmode > 0 && w - i0 >= kTcMinRows) {
+          const bool ok = tcmode == 1 ? panel_update_tc<1>(*tc, Ls, f, i0, w, kb, i0, Xs, wp, Xs, W2, w, r, J)
+                                      : panel_update_tc<2>(*tc, Ls, f, i0, w, kb, i0, Xs, wp, Xs, W2, w, r, J);
+          if (!ok) return false;
+          continue;
+        }
+      }
+      panel_update_simt<T>(sm, Ls, f, i0, w, kb, i0, Xs, wp, W2, w, r, J);
+    }
+  }
+  // the bottom rows: W2 -= L_rs X_s, K = w
+  if (r > 0) {
     if constexpr (sizeof(T) == 4) {
-      if (tcmode > 0 && f - i0 >= kTcMinRows) {
-        // the panel update on the tensor cores (the diagonal block above stays a small SIMT GEMM)
-        const bool ok = tcmode == 1 ? panel_update_tc<1>(*tc, Ls, f, w, kb, nbk, Xs, wp, Xs, W2, f - w, J)
-                                    : panel_update_tc<2>(*tc, Ls, f, w, kb, nbk, Xs, wp, Xs, W2, f - w, J);
-        if (!ok) return false;
-        continue;
+      if (tcmode > 0 && r >= kTcMinRows) {
+        const bool ok = tcmode == 1 ? panel_update_tc<1>(*tc, Ls, f, w, f, 0, w, Xs, wp, Xs, W2, w, r, J)
+                                    : panel_update_tc<2>(*tc, Ls, f, w, f, 0, w, Xs, wp, Xs, W2, w, r, J);
+        return ok;
       }
     }
-    const int TR = (f - i0 + kT - 1) / kT, TC = (J + kT - 1) / kT;
-    for (int ti = 0; ti < TR; ++ti) {
-      for (int tc = 0; tc < TC; ++tc) {
-        const int ri = i0 + ti * kT, cj = tc * kT;
-        for (int idx = tid; idx < nbk * kT; idx += kThreads) {
-          int x = idx % kT, k = idx / kT;
-          sm.A[k][x] = (ri + x < f) ? (T)Ls[(int64_t)(kb + k) * f + ri + x] : (T)0;
-        }
-        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
-          int k = idx % kNB, y = idx / kNB;
-          sm.B[k][y] = (k < nbk && cj + y < J) ? Xs[(int64_t)(cj + y) * wp + kb + k] : (T)0;
-        }
-        __syncthreads();
-        T acc[4][4] = {};
-        // rows tx + 16u (all 16 tx per warp), columns ty + 16v (ty = 2 warp, 2 warp + 1)
-        const int nu = groups16(f - ri), nv = groups16(J - cj - 2 * warp);
-        tile_mma_dispatch<T, false>(sm.A, sm.B, nbk, acc, tx, ty, nu, nv);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          int col = cj + ty + 16 * v;
-          if (v >= nv || col >= J) continue;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            int i = ri + tx + 16 * u;
-            if (u >= nu || i >= f) continue;
-            if (i < w) Xs[(int64_t)col * wp + i] -= acc[u][v];
-            else W2[(int64_t)col * r + (i - w)] -= acc[u][v];
-          }
-        }
-        __syncthreads();
-      }
-    }
+    panel_update_simt<T>(sm, Ls, f, w, f, 0, w, Xs, wp, W2, w, r, J);
   }
   return true;
 }
@@ -679,9 +712,10 @@ __device__ __forceinline__ float round_tf32(float x) {
 // supernode then handles J_s restricted to the block; the restricted ranges nest like J_s itself.
 // X2 (FP32 X only): also write each finished block as bf16 hi/lo halves (hi = bf16(x), lo = bf16(x - hi)),
 // per column wp hi values then wp lo values, for the split-bf16 SYRK.
+// LT: the factor in the solve's precision (the FP32 copy of L for T = float, L itself for T = double).
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2* items, int nitems, int cw,
-                                                         int* queue, T* X, T* ws, int64_t ws_stride,
+                                                         int* queue, const T* LT, T* X, T* ws, int64_t ws_stride,
                                                          int64_t front_sz, int tcmode, int tf32_out, int unit,
                                                          uint16_t* X2, int* status) {
   __shared__ SolveSmem<T> sm;
@@ -724,7 +758,7 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
     const int si = items[it].x;
     const int ca = items[it].y, cb = cw > 0 ? ca + cw : 0x7fffffff;
     const SubInfo S = P.sub[si];
-    const double* L = P.L + S.L;
+    const T* L = LT + S.L;
     T* Xsub = X + S.X;
     for (int a = 0; a < S.nact; ++a) {
       const int s = P.act[S.act0 + a];
@@ -800,7 +834,24 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
   }
 }
 
+// FP32 copy of the factor for the mixed-precision TRSM (one conversion per entry instead of one per use;
+// FP64 -> FP32 conversions run on the narrow FP64 pipe of this GPU)
+__global__ void __launch_bounds__(256) l32_kernel(const double* __restrict__ L, float* __restrict__ L32, int64_t n) {
+  const int64_t n2 = n / 2;
+  const double2* L2 = reinterpret_cast<const double2*>(L);
+  float2* O2 = reinterpret_cast<float2*>(L32);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = L2[i];
+    O2[i] = make_float2((float)v.x, (float)v.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) L32[n - 1] = (float)L[n - 1];
+}
+
 }  // namespace
+
+void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st) {
+  if (n > 0) l32_kernel<<<grid, 256, 0, st>>>(L, L32, n);
+}
 
 void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
                  int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st, int flags) {
@@ -820,14 +871,14 @@ int chol_ctas_per_sm() {
 
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit, uint16_t* X2) {
+                 cudaStream_t st, int unit, uint16_t* X2, const float* L32) {
   if (fp32) {
     const int smem = tcmode > 0 ? (tcmode == 2 ? 2 : 1) * (kTcOpA + kTcOpB) + 1024 : 0;
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, (float*)X, (float*)ws,
+    trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, L32, (float*)X, (float*)ws,
                                                      2 * ws_stride, front_sz, tcmode, tf32_out, 0, X2, status);
   } else {
-    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, items, nitems, cw, queue, (double*)X, ws, ws_stride,
+    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, items, nitems, cw, queue, P.L, (double*)X, ws, ws_stride,
                                                    front_sz, 0, 0, unit, nullptr, status);
   }
 }

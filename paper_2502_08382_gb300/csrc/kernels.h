@@ -14,9 +14,11 @@ int chol_ctas_per_sm();
 // items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
 // X2 (FP32 X only, may be null): also write each finished X block split into bf16 hi/lo halves for the
 // split-bf16 SYRK (per column: wp hi values, then wp lo values; X2 has 2 bf16 per X element)
+// L32 (FP32 X only): the FP32 copy of L (launch_l32)
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr);
+                 cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr, const float* L32 = nullptr);
+void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st);
 // X2 (split mode): the bf16 hi/lo copy of X written by the TRSM (per column: wp hi values, then wp lo values)
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
                     int grid, int split, int* status, cudaStream_t st);
