@@ -255,7 +255,9 @@ def main():
     from paper_2502_08382_gb300.problems import make_config, seeded_vector
 
     P = make_config(args.workload)
-    op = feti.FetiOperator(P, prec=PREC, tol=TOL, maxit=5000, refine_drop=REFINE_DROP, refine_restart=REFINE_RESTART)
+    sens = args.workload == 5  # the sensitivity workload: the adjoint is timed too
+    op = feti.FetiOperator(P, prec=PREC, tol=TOL, maxit=5000, refine_drop=REFINE_DROP, refine_restart=REFINE_RESTART,
+                           with_elements=sens)
     st = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
 
@@ -325,6 +327,31 @@ def main():
     b.record(st)
     b.synchronize()
     e2e_gbs = st_["apply_bytes"] / (a.elapsed_time(b) / nrep * 1e-3) / 1e9
+
+    adjoint = None
+    if sens:
+        # dL/drho_e for L = sum_i <W_i, F_i> with seeded symmetric N(0, 1) W_i drawn on the device (timing only;
+        # the tests check the adjoint against the oracle): the batched FP64 adjoint with X_i recomputed
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        Wd = torch.empty(sum(s.m * s.m for s in P.subs), dtype=torch.float64, device="cuda")
+        off = 0
+        for s_ in P.subs:
+            A = torch.randn(s_.m, s_.m, generator=gen, dtype=torch.float64, device="cuda")
+            Wd[off:off + s_.m * s_.m] = ((A + A.T) * 0.5 ** 0.5).reshape(-1)
+            off += s_.m * s_.m
+        op.assemble()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        g = op.adjoint(Wd)
+        b.record(st)
+        b.synchronize()
+        adjoint = {"ms": a.elapsed_time(b), "elements": int(g.numel()),
+                   "what": "feti_adjoint over all 216 subdomains (FP64 X_u recomputed, Z and Y by backward solves, "
+                           "element contraction), one call"}
+        del Wd, g
 
     # plain FP64 GPU path on the same inputs (assembly time, F and solution differences)
     op64 = feti.FetiOperator(P, prec="fp64", tol=TOL, maxit=5000)
@@ -401,6 +428,7 @@ def main():
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},
             "gpu_launches": int(st_["launches"]),
+            "adjoint": adjoint,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns_cpu = 4 if args.workload == 2 else 1
