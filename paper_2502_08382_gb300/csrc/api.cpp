@@ -604,8 +604,8 @@ void build(feti_ctx* c) {
   c->nsm = prop.multiProcessorCount;
   c->grid_chol = std::min(ns, c->nsm * chol_ctas_per_sm());
   {
-    int64_t max_items = 0;  // the finest TRSM work split (128 columns per item)
-    for (auto& sh : c->subs) max_items += std::max(1, (sh.m + 127) / 128);
+    int64_t max_items = 0;  // the finest TRSM work split (64 columns per item)
+    for (auto& sh : c->subs) max_items += std::max(1, (sh.m + 63) / 64);
     c->grid_trsm = (int)std::min<int64_t>(max_items, c->nsm * 3);
   }
   c->chol_front = max_cf;
@@ -748,7 +748,7 @@ void build(feti_ctx* c) {
   {
     // TRSM work items: a whole subdomain per CTA, or blocks of cw sorted columns (the columns of X are
     // independent); the autotuner times each at the first assembly
-    for (int cw : {0, 1024, 512, 256, 128}) {
+    for (int cw : {0, 1024, 512, 256, 128, 64}) {
       if (cw > 0 && cw >= c->m_max) continue;
       std::vector<int2> it;
       for (int si : order_t) {

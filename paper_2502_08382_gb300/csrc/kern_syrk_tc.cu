@@ -30,7 +30,14 @@ namespace {
 
 constexpr int kM = 128;
 constexpr int kStages = 3;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
+constexpr int kMetaCap = 512;  // contributions per tile whose metadata is staged in shared memory
+
+// what the loader needs of one contributing supernode block
+struct Meta {
+  long long xofs;  // X offset of the block (elements, relative to the subdomain's X)
+  int wp, w, jb, J;
+};
 constexpr uint32_t kTmemCols = 128;
 
 __device__ __forceinline__ void tile2_of(int t, int& bi, int& bj) {
@@ -104,6 +111,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
   __shared__ uint64_t mbar[kStages];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
+  __shared__ Meta meta[kMetaCap];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
@@ -132,9 +140,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
     tile2_of(t2, BI, BJ);
     const int* tl = P.t2_off + S.t20;
     const int cbeg = tl[t2], cend = tl[t2 + 1];
+    // the tile's contributing blocks, staged once (the chunk loop then reads no dependent global data)
+    auto meta_of = [&](int c) {
+      const int s = P.t2_sn[c];
+      const int gs = S.sn0 + s, bs = S.bsn0 + s;
+      Meta m;
+      m.w = P.sn_w[gs];
+      m.wp = (m.w + 7) & ~7;
+      m.jb = P.jb[bs];
+      m.J = P.je[bs] - m.jb;
+      m.xofs = P.Xofs[bs];
+      return m;
+    };
+    const bool staged = cend - cbeg <= kMetaCap;
+    if (staged)
+      for (int c = cbeg + tid; c < cend; c += kTcThreads) meta[c - cbeg] = meta_of(c);
+    __syncthreads();
     int nch = 0;
     for (int c = cbeg; c < cend; ++c) {
-      int w = P.sn_w[S.sn0 + P.t2_sn[c]];
+      const int w = staged ? meta[c - cbeg].w : P.sn_w[S.sn0 + P.t2_sn[c]];
       nch += (w + C::kKC - 1) / C::kKC;
     }
     const float* Xsub = X + S.X;
@@ -143,14 +167,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
     Cursor cur{cbeg, 0};
     auto issue = [&](int i) {
       // load local chunk i (the cursor walks the chunks in order)
-      const int s = P.t2_sn[cur.c];
-      const int gs = S.sn0 + s, bs = S.bsn0 + s;
-      const int w = P.sn_w[gs], wp = (w + 7) & ~7, jb = P.jb[bs], J = P.je[bs] - jb;
+      const Meta m = staged ? meta[cur.c - cbeg] : meta_of(cur.c);
       uint8_t* stage = smem + ((g0 + i) % kStages) * C::kStageBytes;
-      load_chunk<SPLIT>(stage, Xsub + P.Xofs[bs], X2sub + 2 * P.Xofs[bs], wp, w, J, BI * kM - jb, BJ * kM - jb,
+      load_chunk<SPLIT>(stage, Xsub + m.xofs, X2sub + 2 * m.xofs, m.wp, m.w, m.J, BI * kM - m.jb, BJ * kM - m.jb,
                         cur.k0, SPLIT ? (const void*)X2 : (const void*)X, diag);
       cur.k0 += C::kKC;
-      if (cur.k0 >= w) {
+      if (cur.k0 >= m.w) {
         cur.c++;
         cur.k0 = 0;
       }
@@ -205,14 +227,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     g0 += nch;
-    // epilogue: warp w owns tile rows 32w .. 32w+31 (TMEM lanes)
-    const int row = BI * kM + warp * 32 + lane;
+    // epilogue: warp w owns tile rows 32 (w % 4) .. + 31 (its TMEM lane quarter) and the column chunks
+    // 2 (w / 4), 2 (w / 4) + 1 of 32 columns
+    const int quarter = warp % 4;
+    const int row = BI * kM + quarter * 32 + lane;
     const int bi = row / kT;
 #pragma unroll 1
-    for (int cc = 0; cc < 4; ++cc) {
+    for (int cc = 2 * (warp / 4); cc < 2 * (warp / 4) + 2; ++cc) {
       uint32_t v[32];
       if (nch > 0) {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + cc * 32, v);
       } else {
 #pragma unroll
         for (int e = 0; e < 32; ++e) v[e] = 0u;
