@@ -178,6 +178,19 @@ APPLY_TRAFFIC = {2: (138.71e6, "ncu, profiles/apply_tiles_workload2.md"),
                      "ncu on the 64-subdomain copy scaled by algorithmic bytes, profiles/apply_tiles_workload3.md")}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of per-rank timings over all ranks (a barrier follows), so that the
+    job's throughput is the work of all ranks over the slowest rank's time.  One rank: returned as given."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return [float(x) for x in t.tolist()]
+
+
 def oracle_sample(P, nsample, reps):
     """The FP64 CPU oracle on a bounded sample: dense F_i for nsample
     subdomains and reps dense F_i p_i sweeps over them."""
@@ -287,17 +300,13 @@ def main():
             asm.append(op.stats()["t_assemble_ms"])
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    tot = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        tot = float(t.item())
     st_ = op.stats()
     op.set_profiling(False)
+    # replicas: every rank did the same work; the job's rate is N x the work over the slowest rank's time
+    tot, tiles_ms, apply_ms = max_over_ranks(
+        [sum(step_ms), st_["apply_tiles_ms"] / max(st_["apply_calls"], 1), st_["apply_ms"] / max(st_["apply_calls"], 1)],
+        "cuda")
     ms_per_step = tot / args.steps
-    tiles_ms = st_["apply_tiles_ms"] / max(st_["apply_calls"], 1)
-    apply_ms = st_["apply_ms"] / max(st_["apply_calls"], 1)
     impl_ms = st_["implicit_ms"] / max(st_["implicit_calls"], 1)
     hbm, pk_kind = peaks()
     tiles_gbs = st_["apply_bytes"] / (tiles_ms * 1e-3) / 1e9
