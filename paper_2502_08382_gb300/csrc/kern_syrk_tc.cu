@@ -281,6 +281,257 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
   }
 }
 
+// ---------------------------------------------------------------- warp-specialised split-bf16 SYRK
+//
+// The same tiles, K chunks and operand layout as syrk_tc_kernel<1>, with the roles split so that loads, MMAs
+// and the write-back overlap: four producer warps keep kWsStages chunks of cp.async copies in flight (each
+// thread waits for its own oldest group, fences it for the tensor cores and arrives on that stage's "full"
+// barrier), one thread issues the MMAs of a chunk once its stage is full and commits them to the stage's
+// "empty" barrier, and four epilogue warps drain a double-buffered TMEM accumulator (tile t uses columns
+// 128 (t mod 2) ..) while the next tile is multiplied.  Every wait is bounded; a timeout stops all roles,
+// the issuer waits for its MMAs, TMEM is freed and kStatTimeout is reported.
+constexpr int kWsProd = 4;                                 // producer warps
+constexpr int kWsThreads = 32 * (kWsProd + 1 + 4);         // producers, MMA issuer, epilogue
+constexpr int kWsStages = 3;
+constexpr uint32_t kWsTmemCols = 256;                      // two 128-column accumulators
+constexpr int kWsStageBytes = 4 * kOpBytes;                // A hi, A lo, B hi, B lo
+
+// wait on an mbarrier phase, giving up on a timeout (flagged) or when another role has given up
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+  for (int i = 0; i < (1 << 25); ++i) {
+    if (mbar_test(mbar, parity)) return true;
+    if (*abort) return false;
+    __nanosleep(32);
+  }
+  *abort = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1) syrk_ws_kernel(DevPlan P, const int2* items, int nitems,
+                                                               const uint16_t* X2, float* F, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[kWsStages], empty[kWsStages], accf[2], acce[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ int p_stop;  // the producers' copy of s_abort, read by all of them between two barriers
+  __shared__ Meta meta[kMetaCap];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  constexpr int kProdThreads = 32 * kWsProd;
+
+  if (warp == kWsProd) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kWsTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < kWsStages; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[k])), "r"(kProdThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[k])));
+    }
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[a])), "r"(128));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp < kWsProd) {
+    // ------------------------------------------------ producers
+    uint32_t cg = 0;  // chunks issued by this CTA
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      // every producer thread passes the named barrier equally often: the stop decision is taken between
+      // two barriers from one read of the flag
+      asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
+      if (tid == 0) p_stop = s_abort;
+      asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
+      if (p_stop) break;
+      const int si = items[it].x, t2 = items[it].y;
+      const SubInfo S = P.sub[si];
+      int BI, BJ;
+      tile2_of(t2, BI, BJ);
+      const int* tl = P.t2_off + S.t20;
+      const int cbeg = tl[t2], cend = tl[t2 + 1];
+      auto meta_of = [&](int c) {
+        const int sn = P.t2_sn[c];
+        const int gs = S.sn0 + sn, bs = S.bsn0 + sn;
+        Meta m;
+        m.w = P.sn_w[gs];
+        m.wp = (m.w + 7) & ~7;
+        m.jb = P.jb[bs];
+        m.J = P.je[bs] - m.jb;
+        m.xofs = P.Xofs[bs];
+        return m;
+      };
+      const bool staged = cend - cbeg <= kMetaCap;
+      // (the barriers above also order the previous tile's reads of meta before these writes)
+      if (staged)
+        for (int c = cbeg + tid; c < cend; c += kProdThreads) meta[c - cbeg] = meta_of(c);
+      asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
+      const uint16_t* X2sub = X2 + 2 * S.X;
+      const bool diag = BI == BJ;
+      const int nparts = diag ? 2 : 4;
+      for (int c = cbeg; c < cend && !s_abort; ++c) {
+        const Meta m = staged ? meta[c - cbeg] : meta_of(c);
+        const uint16_t* X2s = X2sub + 2 * m.xofs;
+        const int ca = BI * kM - m.jb, cbb = BJ * kM - m.jb;
+        for (int k0 = 0; k0 < m.w; k0 += 64, ++cg) {
+          const int st = (int)(cg % kWsStages);
+          if (cg >= kWsStages && !ws_wait(smem_u32(&empty[st]), ((cg / kWsStages) - 1) & 1, &s_abort)) break;
+          const uint32_t s0 = smem_u32(smem + st * kWsStageBytes);
+          for (int idx = tid; idx < nparts * kM * 8; idx += kProdThreads) {
+            const int part = idx / (kM * 8), rem = idx % (kM * 8);
+            const int mrow = rem / 8, c8 = rem % 8;
+            const int x = (part < 2 ? ca : cbb) + mrow;
+            const int k = k0 + 8 * c8;
+            const bool ok = x >= 0 && x < m.J && k < m.w;
+            const void* src = ok ? (const void*)(X2s + 2 * (int64_t)x * m.wp + ((part & 1) ? m.wp : 0) + k)
+                                 : (const void*)X2;
+            cp_async16(s0 + part * kOpBytes + (mrow >> 3) * 1024 + (mrow & 7) * 128 + ((c8 ^ (mrow & 7)) << 4), src,
+                       ok);
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (cg >= kWsStages - 1) {
+            // this thread's copies of chunk cg - (kWsStages - 1) have landed: fence them for the tensor cores
+            asm volatile("cp.async.wait_group %0;" ::"n"(kWsStages - 1) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[(cg - (kWsStages - 1)) %
+                                                                                            kWsStages])));
+          }
+        }
+      }
+    }
+    // the last chunks
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t nout = cg < (uint32_t)(kWsStages - 1) ? cg : (uint32_t)(kWsStages - 1);
+    for (uint32_t k = cg - nout; k < cg; ++k)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[k % kWsStages])));
+  } else if (warp == kWsProd) {
+    // ------------------------------------------------ MMA issuer (lane 0; the warp computes the chunk counts)
+    constexpr uint32_t idesc = idesc_mn128(1u);
+    uint32_t cg = 0, tl_count = 0;
+    bool issued = false;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++tl_count) {
+      if (__shfl_sync(0xffffffffu, (int)s_abort, 0)) break;  // one decision for the whole warp
+      const int si = items[it].x, t2 = items[it].y;
+      const SubInfo S = P.sub[si];
+      int BI, BJ;
+      tile2_of(t2, BI, BJ);
+      const int* tl = P.t2_off + S.t20;
+      const int cbeg = tl[t2], cend = tl[t2 + 1];
+      int nch = 0;
+      for (int c = cbeg + lane; c < cend; c += 32) nch += (P.sn_w[S.sn0 + P.t2_sn[c]] + 63) / 64;
+      for (int o = 16; o > 0; o >>= 1) nch += __shfl_xor_sync(0xffffffffu, nch, o);
+      const bool diag = BI == BJ;
+      const uint32_t a = tl_count % 2;
+      if (lane == 0) {
+        bool ok = true;
+        if (tl_count >= 2) ok = ws_wait(smem_u32(&acce[a]), ((tl_count / 2) - 1) & 1, &s_abort);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + a * 128;
+        for (int i = 0; i < nch && ok; ++i, ++cg) {
+          const int st = (int)(cg % kWsStages);
+          if (!ws_wait(smem_u32(&full[st]), (cg / kWsStages) & 1, &s_abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sbase = smem_u32(smem + st * kWsStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = kk * 32;
+            const uint64_t ah = sw128_desc(sbase + o), al = sw128_desc(sbase + kOpBytes + o);
+            const uint64_t bh = diag ? ah : sw128_desc(sbase + 2 * kOpBytes + o);
+            const uint64_t bl = diag ? al : sw128_desc(sbase + 3 * kOpBytes + o);
+            mma_f16(d, ah, bh, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_f16(d, ah, bl, idesc, 1u);
+            mma_f16(d, al, bh, idesc, 1u);
+          }
+          mma_commit(smem_u32(&empty[st]));
+          issued = true;
+        }
+        mma_commit(smem_u32(&accf[a]));  // the tile's accumulator is complete (at once if nothing was issued)
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && issued) {
+      // every MMA has completed before TMEM is released (also after a timeout)
+      mma_commit(smem_u32(&drain));
+      if (!mbar_wait(smem_u32(&drain), 0)) s_abort = 1;
+    }
+  } else {
+    // ------------------------------------------------ epilogue: TMEM lane quarter warp % 4, all 128 columns
+    const int quarter = warp % 4;
+    uint32_t tl_count = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++tl_count) {
+      const int si = items[it].x, t2 = items[it].y;
+      const SubInfo S = P.sub[si];
+      int BI, BJ;
+      tile2_of(t2, BI, BJ);
+      const int* tl = P.t2_off + S.t20;
+      const bool empty_tile = tl[t2 + 1] == tl[t2];
+      const uint32_t a = tl_count % 2;
+      // lane 0 waits, the warp follows its outcome (tcgen05.ld below needs every lane)
+      int ok = 0;
+      if (lane == 0) ok = ws_wait(smem_u32(&accf[a]), (tl_count / 2) & 1, &s_abort) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = BI * kM + quarter * 32 + lane;
+      const int bi = row / kT;
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v[32];
+        if (!empty_tile) {
+          tmem_ld32(tmem + a * 128 + ((uint32_t)(quarter * 32) << 16) + cc * 32, v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] = 0u;
+        }
+        const int col = BJ * kM + cc * 32;
+        const int bj = col / kT;
+        if (bi < S.nb && bj < S.nb && bj <= bi && (row % kT) < tile_rows(S.nb, S.vr, bi)) {
+          float* tb = F + S.F + tile_offset<4>(S.nb, S.vr, bi, bj);
+          const int r = row % kT;
+          if (bj < bi) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              *reinterpret_cast<float4*>(tb + tile_pos(r, col % kT + e)) =
+                  make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                              __uint_as_float(v[e + 3]));
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4) {
+              const int c = col % kT + e;
+              if (c / 4 <= r / 4) {
+                float x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = c + u <= r ? __uint_as_float(v[e + u]) : 0.f;
+                *reinterpret_cast<float4*>(tb + diag_pos<4>(r, c)) = make_float4(x[0], x[1], x[2], x[3]);
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a])));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_abort && tid == 0) atomicOr(status, kStatTimeout);
+  if (warp == kWsProd) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWsTmemCols));
+  }
+}
+
 }  // namespace
 
 size_t syrk_tc_smem(int split) {
@@ -291,8 +542,9 @@ void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float
                     int grid, int split, int* status, cudaStream_t st) {
   size_t smem = syrk_tc_smem(split);
   if (split) {
-    cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    syrk_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
+    const int ws_smem = kWsStages * kWsStageBytes + 1024;
+    cudaFuncSetAttribute(syrk_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ws_smem);
+    syrk_ws_kernel<<<grid, kWsThreads, ws_smem, st>>>(P, items, nitems, X2, F, status);
   } else {
     cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     syrk_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
