@@ -155,6 +155,8 @@ typedef struct {
                                          3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
   /* autotuner choice for the pruned TRSM (after the first feti_assemble) */
   int32_t trsm_cols;          /* sorted columns per CTA work item (0: a whole subdomain per item) */
+  int32_t syrk_variant;       /* split-bf16 SYRK kernel picked by the autotuner (0: all threads load, one issues;
+                                 1: warp-specialised producers / issuer / epilogue) */
   int32_t assembly_route;     /* route of the last feti_assemble (0 SYRK path, 1 Schur complement, 2 TRSM path) */
   double route_ms[3];         /* route 3: time of the TRSM + SYRK (0) and of the TRSM path (2) at the first call */
 } feti_stats;

@@ -967,9 +967,27 @@ feti_status feti_assemble(feti_ctx* ctx) {
     launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
     CK(cudaEventRecordWithFlags(ctx->ev[2], s2, evf));
     if (ctx->fp32) {
-      launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, ctx->d_X2, (float*)ctx->d_F,
-                     std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split ? 1 : 0, ctx->d_status,
-                     s2);
+      auto run_syrk = [&](int variant) {
+        launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, ctx->d_X2, (float*)ctx->d_F,
+                       std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split ? 1 : 0, ctx->d_status,
+                       s2, variant);
+      };
+      if (split && !ctx->syrk_tuned) {
+        // autotuner: the two split-bf16 SYRK kernels on this problem (the same F bitwise), the faster kept
+        float ms[2] = {0, 0};
+        for (int v = 0; v < 2; ++v) {
+          CK(cudaEventRecord(ctx->ev[5], s2));
+          run_syrk(v);
+          CK(cudaEventRecord(ctx->ev[6], s2));
+          CK(cudaEventSynchronize(ctx->ev[6]));
+          CK(cudaEventElapsedTime(&ms[v], ctx->ev[5], ctx->ev[6]));
+        }
+        ctx->syrk_variant = ms[1] < ms[0] ? 1 : 0;
+        ctx->syrk_tuned = true;
+        ctx->stats.syrk_variant = ctx->syrk_variant;
+        CK(cudaEventRecord(ctx->ev[2], s2));
+      }
+      run_syrk(ctx->syrk_variant);
     } else {
       launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
                       std::min(ctx->nsyrk, ctx->nsm * 8), s2);

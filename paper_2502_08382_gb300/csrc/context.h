@@ -78,6 +78,8 @@ struct feti_ctx {
   std::vector<TrsmCand> trsm_cands;  // autotuner candidates of the pruned TRSM
   int trsm_pick = 0;
   bool trsm_tuned = false;
+  int syrk_variant = 0;              // split-bf16 SYRK kernel picked by the autotuner
+  bool syrk_tuned = false;
   int* d_impl_order = nullptr;
   int2* d_syrk_items = nullptr;
   feti::TileDesc* d_tdesc = nullptr;

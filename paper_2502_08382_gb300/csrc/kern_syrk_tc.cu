@@ -539,12 +539,15 @@ size_t syrk_tc_smem(int split) {
 }
 
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
-                    int grid, int split, int* status, cudaStream_t st) {
+                    int grid, int split, int* status, cudaStream_t st, int variant) {
   size_t smem = syrk_tc_smem(split);
-  if (split) {
+  if (split && variant == 1) {
     const int ws_smem = kWsStages * kWsStageBytes + 1024;
     cudaFuncSetAttribute(syrk_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ws_smem);
     syrk_ws_kernel<<<grid, kWsThreads, ws_smem, st>>>(P, items, nitems, X2, F, status);
+  } else if (split) {
+    cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    syrk_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
   } else {
     cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     syrk_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);

@@ -20,8 +20,10 @@ void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* q
                  cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr, const float* L32 = nullptr);
 void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st);
 // X2 (split mode): the bf16 hi/lo copy of X written by the TRSM (per column: wp hi values, then wp lo values)
+// variant (split mode): 0 = all threads load then one thread issues; 1 = warp-specialised (producer warps,
+// issuer, epilogue warps on a double-buffered accumulator); the assembly's autotuner picks one per problem
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
-                    int grid, int split, int* status, cudaStream_t st);
+                    int grid, int split, int* status, cudaStream_t st, int variant = 0);
 size_t syrk_tc_smem(int split);
 void launch_syrk_f64(const DevPlan& P, const int2* items, int nitems, const double* X, double* F, int grid,
                      cudaStream_t st);

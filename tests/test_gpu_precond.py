@@ -132,3 +132,32 @@ def test_dirichlet_needs_schur_route(torch_cuda):
     from paper_2502_08382_gb300 import feti
     with pytest.raises(feti.FetiError):
         feti.FetiOperator(CASES["cfg1"](), prec="fp64", precond="dirichlet")
+
+
+def test_dirichlet_values_follow_new_K(torch_cuda):
+    """Algorithm 2's next step with the Dirichlet preconditioner: after new K values the re-assembly (replayed from
+    its CUDA graph) factors the new K up to the root front again, so S_i follows K: the iterations match the
+    oracle's Dirichlet-preconditioned solve of the new problem, and so does the solution."""
+    from paper_2502_08382_gb300 import feti
+    P = CASES["heat2d_lognormal"]()
+    op = feti.FetiOperator(P, prec="fp64", tol=1e-12, maxit=3000, precond="dirichlet", route="schur")
+    op.assemble()
+    op.assemble()  # the second assembly is the graph replay
+    rng = np.random.default_rng([7, 5])
+    subs = []
+    for i, s in enumerate(P.subs):
+        coef = s.elem_coef * rng.uniform(0.2, 5.0, size=s.elem_dofs.shape[0])
+        subs.append(dataclasses.replace(s, elem_coef=coef, K_val=subdomain_K_values(P, i, coef)))
+        op.update_values(i, subs[-1].K_val)
+    P2 = dataclasses.replace(P, subs=subs)
+    op.assemble()
+    lam, alpha, u, info = op.solve()
+    u = u.cpu().numpy()
+    op.close()
+    Fs = [O.local_F(s) for s in P2.subs]
+    _, its_o, _ = O.pcpg(P2, Fs, tol=1e-12, M=O.dirichlet_M(P2))
+    um = O.monolithic_solve(P2)
+    assert info["converged"], info
+    assert abs(info["iterations"] - its_o) <= 2, (info["iterations"], its_o)
+    err = max(np.abs(ui - um[s.l2g]).max() for s, ui in zip(P2.subs, _split(P2, u)))
+    assert err <= 1e-10 * np.abs(um).max(), err
