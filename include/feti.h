@@ -121,6 +121,11 @@ typedef struct {
                                      B DOFs), stored in the precision's tiles;
                                  3 = autotuned: the first feti_assemble times route 0 against route 2 on
                                      the problem and keeps the faster (feti_stats.assembly_route) */
+  int32_t chol_split;         /* work items of the batched Cholesky: 0 = autotuned at the first
+                                 feti_assemble; 1 = one subdomain per CTA; 2 = subtree tasks (heavy
+                                 subtrees of the supernodal tree factored by CTAs of their own, a parent
+                                 task after its children), so that large subdomains spread over several
+                                 SMs.  The factor is the same bit for bit either way */
 } feti_options;
 
 typedef struct {
@@ -155,6 +160,8 @@ typedef struct {
                                          3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
   /* autotuner choice for the pruned TRSM (after the first feti_assemble) */
   int32_t trsm_cols;          /* sorted columns per CTA work item (0: a whole subdomain per item) */
+  int32_t chol_tasks;         /* Cholesky work items the autotuner kept: the subdomains, or the tasks of the
+                                 subtree split when that was faster */
   int32_t syrk_variant;       /* split-bf16 SYRK kernel picked by the autotuner (0: all threads load, one issues;
                                  1: warp-specialised producers / issuer / epilogue) */
   int32_t assembly_route;     /* route of the last feti_assemble (0 SYRK path, 1 Schur complement, 2 TRSM path) */

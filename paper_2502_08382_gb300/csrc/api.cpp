@@ -242,6 +242,19 @@ void build(feti_ctx* c) {
     c->bp_pat[b] = s.pat;
     plan_rhs(c->pats[s.pat], s.m, s.bdof.data(), c->bps[b]);
   });
+  {
+    // Cholesky tasks: split heavy subtrees so that the factorisation's work units are at most about a quarter
+    // of the average work per persistent CTA (large subdomains get several CTAs; uniform ones balance better)
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    double total = 0;
+    for (auto& sh : c->subs) total += c->pats[sh.pat].chol_flops;
+    const double slots = (double)std::max(1, nsm * chol_ctas_per_sm());
+    const double target = total / (4.0 * slots);
+    for (auto& P : c->pats) plan_tasks(P, target);
+  }
   c->stats.t_symbolic_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
   c->stats.npatterns = (int)c->pats.size();
   c->stats.nbplans = (int)c->bps.size();
@@ -249,7 +262,8 @@ void build(feti_ctx* c) {
   // ---- concatenate pattern tables
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
   std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs, usm_ofs;
-  std::vector<int> sn_small;
+  std::vector<int> sn_small, sn_task;
+  std::vector<int64_t> sn_hoff;
   std::vector<int> lvl_off, lvl_sn, pat_lvl0(c->pats.size());
   int64_t max_usize = 0;
   std::vector<int> pat_sn0(c->pats.size());
@@ -271,6 +285,8 @@ void build(feti_ctx* c) {
       upd_ofs.push_back(P.upd_stack_ofs[s]);
       sn_small.push_back(P.sn_small[s]);
       usm_ofs.push_back(P.usm_ofs[s]);
+      sn_task.push_back(P.sn_task[s]);
+      sn_hoff.push_back(P.sn_hoff[s]);
       uofs.push_back(P.uofs[s]);
     }
     pat_lvl0[p] = (int)lvl_off.size();
@@ -332,7 +348,7 @@ void build(feti_ctx* c) {
   std::vector<double> eldk, elsc;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
-  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, hbo = 0;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
   int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0, max_usm = 0;
@@ -377,6 +393,8 @@ void build(feti_ctx* c) {
     I.R = Ro;
     I.tpart = tpo;
     I.rpart = 0;
+    I.hbase = hbo;
+    hbo += P.hsize;
     int ntile = B.nb * (B.nb + 1) / 2;
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
@@ -647,6 +665,9 @@ void build(feti_ctx* c) {
   D.uofs = upload(c, uofs);
   D.sn_small = upload(c, sn_small);
   D.usm_ofs = upload(c, usm_ofs);
+  D.sn_task = upload(c, sn_task);
+  D.sn_hoff = upload(c, sn_hoff);
+  c->d_hand = (double*)dalloc(c, (size_t)std::max<int64_t>(hbo, 1) * 8);
   D.jb = upload(c, jb);
   D.je = upload(c, je);
   D.jo = upload(c, jo);
@@ -744,6 +765,39 @@ void build(feti_ctx* c) {
   c->d_queue = (int*)dalloc(c, 64 * sizeof(int));
   c->d_status = (int*)dalloc(c, sizeof(int));
   c->d_chol_order = upload(c, order);
+  {
+    // Cholesky work items: whole subdomains (cost order), and the tasks of the split, children before
+    // parents (by task height), heavier first
+    std::vector<int4> whole;
+    for (int si : order) whole.push_back(make_int4(si, 0, 0, -1));
+    std::vector<std::pair<std::pair<int, double>, int4>> tk;
+    std::vector<int> nchild;
+    int base = 0;
+    for (int i = 0; i < ns; ++i) {
+      const auto& P = c->pats[c->subs[i].pat];
+      for (int t = 0; t < P.ntask; ++t) {
+        nchild.push_back(P.task_nchild[t]);
+        tk.push_back({{P.task_height[t], -P.task_cost[t]},
+                      make_int4(i, t, base + t, P.task_parent[t] >= 0 ? base + P.task_parent[t] : -1)});
+      }
+      base += P.ntask;
+    }
+    std::stable_sort(tk.begin(), tk.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    std::vector<int4> split;
+    for (auto& x : tk) split.push_back(x.second);
+    c->d_chol_items[0] = upload(c, whole);
+    c->d_chol_items[1] = upload(c, split);
+    c->chol_nitems[0] = (int)whole.size();
+    c->chol_nitems[1] = (int)split.size();
+    c->ntask_total = base;
+    D.task_nchild = upload(c, nchild);
+    c->P2.task_nchild = D.task_nchild;
+    c->d_tdone = (int*)dalloc(c, (size_t)std::max(base, 1) * sizeof(int));
+    // nothing to split: the whole-subdomain items only
+    if (c->opt.chol_split < 0 || c->opt.chol_split > 2) throw ArgError("bad chol_split (0 auto, 1 whole, 2 tasks)");
+    c->chol_pick = c->opt.chol_split == 2 ? 1 : 0;
+    c->chol_tuned = c->opt.chol_split != 0 || (int)split.size() == ns;
+  }
   c->d_trsm_order = upload(c, order_t);
   {
     // TRSM work items: a whole subdomain per CTA, or blocks of cw sorted columns (the columns of X are
@@ -931,9 +985,30 @@ feti_status feti_assemble(feti_ctx* ctx) {
       // the lumped preconditioner's values from the current K (they change with feti_update_values)
       launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val,
                            s2);
+    auto run_chol = [&](int v, const DevPlan& P, int qslot, int flags) {
+      CK(cudaMemsetAsync(ctx->d_queue + qslot, 0, sizeof(int), s2));
+      if (v) CK(cudaMemsetAsync(ctx->d_tdone, 0, (size_t)std::max(ctx->ntask_total, 1) * sizeof(int), s2));
+      launch_chol(P, ctx->d_chol_items[v], ctx->chol_nitems[v], v, ctx->d_queue + qslot, ctx->d_tdone, ctx->d_hand,
+                  ctx->d_ws, ctx->ws_stride, ctx->chol_front, ctx->chol_stack,
+                  std::min(ctx->grid_chol, ctx->chol_nitems[v]), ctx->d_status, s2, flags);
+    };
+    if (!ctx->chol_tuned) {
+      // autotuner: whole subdomains per CTA against the subtree tasks (the same factor bitwise), faster kept
+      float ms[2] = {0, 0};
+      run_chol(0, ctx->P, 0, 0);  // untimed: module loading and first-touch costs stay out of the comparison
+      for (int v = 0; v < 2; ++v) {
+        CK(cudaEventRecord(ctx->ev[5], s2));
+        run_chol(v, ctx->P, 0, 0);
+        CK(cudaEventRecord(ctx->ev[6], s2));
+        CK(cudaEventSynchronize(ctx->ev[6]));
+        CK(cudaEventElapsedTime(&ms[v], ctx->ev[5], ctx->ev[6]));
+      }
+      ctx->chol_pick = ms[1] < ms[0] ? 1 : 0;
+      ctx->chol_tuned = true;
+    }
+    ctx->stats.chol_tasks = ctx->chol_pick ? ctx->chol_nitems[1] : ctx->chol_nitems[0];
     CK(cudaEventRecordWithFlags(ctx->ev[0], s2, evf));
-    launch_chol(ctx->P, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 0, ctx->d_ws, ctx->ws_stride,
-                ctx->chol_front, ctx->chol_stack, ctx->grid_chol, ctx->d_status, s2);
+    run_chol(ctx->chol_pick, ctx->P, 0, 0);
     CK(cudaEventRecordWithFlags(ctx->ev[1], s2, evf));
     if (r2) {
       launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
@@ -994,8 +1069,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
     }
     if (ctx->precond_kind == 2) {
       // Dirichlet preconditioner: K (no penalty) eliminated up to the root front, which then holds S_i
-      launch_chol(ctx->P2, ctx->d_chol_order, ctx->nsub, ctx->d_queue + 8, ctx->d_ws, ctx->ws_stride,
-                  ctx->chol_front, ctx->chol_stack, ctx->grid_chol, ctx->d_status, s2, kCholNoReg | kCholStopRoot);
+      run_chol(ctx->chol_pick, ctx->P2, 8, kCholNoReg | kCholStopRoot);
       launch_schur_tiles(ctx->P2, ctx->d_tdesc, ctx->napply, ctx->fp32, ctx->d_M,
                          std::max(1, std::min(ctx->napply, ctx->nsm * 8)), s2);
     }

@@ -40,6 +40,7 @@ struct SubInfo {
   int64_t trow;      // == qcol (unused)
   int64_t tpart;     // first apply tile of this subdomain times kT (its row / column partial slots)
   int64_t rpart;     // unused
+  int64_t hbase;     // base of this subdomain's Cholesky hand-over slots (doubles)
 };
 
 struct DevPlan {
@@ -66,6 +67,9 @@ struct DevPlan {
   const int64_t* uofs;       // [sn] update-vector offset of the supernode (relative to the CTA workspace)
   const int* sn_small;       // [sn] 1: small-subtree supernode (warp-factored front)
   const int64_t* usm_ofs;    // [sn] update-block slot of a small supernode (relative to the CTA's small region)
+  const int* sn_task;        // [sn] Cholesky task of the supernode (local to the pattern's split)
+  const int64_t* sn_hoff;    // [sn] hand-over slot of a split root (relative to the subdomain's hbase), -1 if none
+  const int* task_nchild;    // [global task] child tasks to wait for
   double* dinv;              // [dof + j] reciprocal pivots 1 / L_jj (written after the factorisation)
   // bplan tables
   const int* jb;

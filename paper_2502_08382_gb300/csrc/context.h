@@ -78,6 +78,13 @@ struct feti_ctx {
   std::vector<TrsmCand> trsm_cands;  // autotuner candidates of the pruned TRSM
   int trsm_pick = 0;
   bool trsm_tuned = false;
+  int4* d_chol_items[2] = {nullptr, nullptr};  // Cholesky items: whole subdomains / subtree tasks
+  int chol_nitems[2] = {0, 0};
+  int chol_pick = 0;                 // the autotuner's choice of the two
+  bool chol_tuned = false;
+  int ntask_total = 0;
+  int* d_tdone = nullptr;            // per global task: child tasks finished
+  double* d_hand = nullptr;          // hand-over slots of split subtree roots
   int syrk_variant = 0;              // split-bf16 SYRK kernel picked by the autotuner
   bool syrk_tuned = false;
   int* d_impl_order = nullptr;

@@ -215,9 +215,11 @@ __device__ __forceinline__ void team_sync() {
   else __syncthreads();
 }
 
-// Update block of child gc: a small child's lives in the CTA's small region, others on the stack.
+// Update block of child gc: a small child's lives in the CTA's small region, a split root's (a child factored
+// by another task) in its hand-over slot, others on the stack.
 __device__ __forceinline__ const double* child_update(const DevPlan& P, int gc, const double* stack,
-                                                      const double* smallreg) {
+                                                      const double* smallreg, const double* hand) {
+  if (hand && P.sn_hoff[gc] >= 0) return hand + P.sn_hoff[gc];
   return P.sn_small[gc] ? smallreg + P.usm_ofs[gc] : stack + P.upd_ofs[gc];
 }
 
@@ -227,7 +229,7 @@ __device__ __forceinline__ const double* child_update(const DevPlan& P, int gc, 
 template <int TEAM>
 __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const double* K, double* L, double rho,
                              double* Fp, const double* stack, const double* smallreg, double* Uout, int* bad,
-                             int tid, bool factor = true) {
+                             int tid, bool factor = true, const double* hand = nullptr) {
   const int gs = S.sn0 + s;
   const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
   const int np = f * (f + 1) / 2;
@@ -247,11 +249,11 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
   for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
     const int gc = S.sn0 + P.ch_list[c];
     const int rc = P.sn_r[gc];
-    const double* U = child_update(P, gc, stack, smallreg);
+    const double* U = child_update(P, gc, stack, smallreg, hand);
     const int* rl = P.rel + P.rel_off[gc];
     team_sync<TEAM>();
     for (int b = 0; b < rc; ++b)
-      for (int a = b + tid; a < rc; a += TEAM) Fp[pidx(f, rl[a], rl[b])] += U[(int64_t)b * rc + a];
+      for (int a = b + tid; a < rc; a += TEAM) Fp[pidx(f, rl[a], rl[b])] += __ldcg(U + (int64_t)b * rc + a);
   }
   team_sync<TEAM>();
   // blocked right-looking partial factorisation of the first w columns: one warp
@@ -333,9 +335,16 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
 // assembles the last (root) supernode's front but does not eliminate it, so
 // with the DOFs B touches ordered last the root panel holds the Schur
 // complement of the interior onto them (lower triangle, column-major).
-__global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int* order, int nsub, int* queue,
-                                                         double* ws, int64_t ws_stride, int64_t front_sz,
-                                                         int64_t stack_sz, int flags, int* status) {
+// Work items (subdomain, task, global task id, parent's global task id).  use_tasks = 0: an item is a whole
+// subdomain.  use_tasks = 1: an item is one task of the plan's split (plan_tasks): it factors only the
+// supernodes of that task, first waiting (bounded) until its child tasks have finished (they precede it in
+// the item list, so they have been taken by running CTAs), reads the update blocks of split children from
+// their hand-over slots, writes its own root's there when that root is split, and counts itself done at its
+// parent task.
+__global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4* items, int nitems, int use_tasks,
+                                                         int* queue, int* tdone, double* hand_all, double* ws,
+                                                         int64_t ws_stride, int64_t front_sz, int64_t stack_sz,
+                                                         int flags, int* status) {
   extern __shared__ double dsm[];
   Smem& sm = *reinterpret_cast<Smem*>(dsm);
   __shared__ int bad;
@@ -346,11 +355,35 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
   double* smallreg = stack + stack_sz;
   for (;;) {
     int it = pop_item(queue);
-    if (it >= nsub) return;
-    const int si = order[it];
+    if (it >= nitems) return;
+    const int4 item = items[it];
+    const int si = item.x, task = item.y;
     const SubInfo S = P.sub[si];
     const double* K = P.Kval + S.Kval;
     double* L = P.L + S.L;
+    double* hand = use_tasks ? hand_all + S.hbase : nullptr;
+    if (use_tasks && P.task_nchild[item.z] > 0) {
+      // the child tasks were taken before this one and are running: wait for them (bounded)
+      if (tid == 0) {
+        int ok = 0;
+        for (int i = 0; i < (1 << 26); ++i) {
+          if (*(volatile int*)(tdone + item.z) >= P.task_nchild[item.z]) {
+            ok = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (!ok) atomicOr(status, kStatTimeout);
+        __threadfence();
+        bad = ok ? 0 : 2;
+        // given up (status set): still count this task done at its parent, so that a failure does not make
+        // every ancestor wait out its own limit
+        if (!ok && item.w >= 0) atomicAdd(tdone + item.w, 1);
+      }
+      __syncthreads();
+      if (bad == 2) continue;
+    }
+    __syncthreads();
     if (tid == 0) bad = 0;
     // rho = max diag K_i (fixing-node penalty)
     double mx = 0.0;
@@ -367,12 +400,15 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
     double* Fw = dsm + warp * kWarpSlot;
     for (int l = 0; l < S.nlev; ++l) {
       bool any = false;
-      for (int q = lvo[l]; q < lvo[l + 1]; ++q) any |= P.sn_small[S.sn0 + P.lvl_sn[q]] != 0;
+      for (int q = lvo[l]; q < lvo[l + 1]; ++q) {
+        const int gq = S.sn0 + P.lvl_sn[q];
+        any |= P.sn_small[gq] != 0 && (!use_tasks || P.sn_task[gq] == task);
+      }
       if (!any) continue;
       for (int q = lvo[l] + warp; q < lvo[l + 1]; q += kThreads / 32) {
         const int s = P.lvl_sn[q];
         const int gs = S.sn0 + s;
-        if (!P.sn_small[gs]) continue;
+        if (!P.sn_small[gs] || (use_tasks && P.sn_task[gs] != task)) continue;
         double* Uout = P.sn_parent[gs] >= 0 ? smallreg + P.usm_ofs[gs] : nullptr;
         packed_front<32>(P, S, s, K, L, rho, Fw, stack, smallreg, Uout, &bad, lane,
                          !((flags & kCholStopRoot) && s == S.nsn - 1));
@@ -382,12 +418,13 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
     // phase 2: the rest in postorder
     for (int s = 0; s < S.nsn; ++s) {
       const int gs = S.sn0 + s;
-      if (P.sn_small[gs]) continue;
+      if (P.sn_small[gs] || (use_tasks && P.sn_task[gs] != task)) continue;
       const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
-      double* Uout = P.sn_parent[gs] >= 0 ? stack + P.upd_ofs[gs] : nullptr;
+      double* Uout = P.sn_parent[gs] < 0 ? nullptr
+                     : (hand && P.sn_hoff[gs] >= 0) ? hand + P.sn_hoff[gs] : stack + P.upd_ofs[gs];
       const bool factor = !((flags & kCholStopRoot) && s == S.nsn - 1);
       if (f <= kMidFront) {
-        packed_front<kThreads>(P, S, s, K, L, rho, dsm, stack, smallreg, Uout, &bad, tid, factor);
+        packed_front<kThreads>(P, S, s, K, L, rho, dsm, stack, smallreg, Uout, &bad, tid, factor, hand);
         continue;
       }
       double* Ls = L + P.Lofs[gs];
@@ -402,14 +439,14 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
       for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
         const int gc = S.sn0 + P.ch_list[c];
         const int rc = P.sn_r[gc];
-        const double* U = child_update(P, gc, stack, smallreg);
+        const double* U = child_update(P, gc, stack, smallreg, hand);
         const int* rl = P.rel + P.rel_off[gc];
         __syncthreads();
         for (int64_t idx = tid; idx < (int64_t)rc * rc; idx += kThreads) {
           int a = (int)(idx % rc), b = (int)(idx / rc);
           if (a < b) continue;
           int ra = rl[a], rb = rl[b];
-          double v = U[idx];
+          double v = __ldcg(U + idx);
           if (rb < w) Ls[(int64_t)rb * f + ra] += v;
           else W[(int64_t)(rb - w) * r + (ra - w)] += v;
         }
@@ -421,7 +458,14 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int*
         for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) Uout[idx] = W[idx];
       __syncthreads();
     }
-    if (tid == 0 && bad) atomicOr(status, kStatNotSPD);
+    __syncthreads();
+    if (tid == 0) {
+      if (bad) atomicOr(status, kStatNotSPD);
+      if (use_tasks && item.w >= 0) {
+        __threadfence();  // this task's factor panels and hand-over block before the count
+        atomicAdd(tdone + item.w, 1);
+      }
+    }
   }
 }
 
@@ -853,12 +897,13 @@ void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t s
   if (n > 0) l32_kernel<<<grid, 256, 0, st>>>(L, L32, n);
 }
 
-void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st, int flags) {
+void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks, int* queue, int* tdone,
+                 double* hand, double* ws, int64_t ws_stride, int64_t front_sz, int64_t stack_sz, int grid,
+                 int* status, cudaStream_t st, int flags) {
   const int smem = kFrontSmem * 8;
   cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  chol_kernel<<<grid, kThreads, smem, st>>>(P, order, nsub, queue, ws, ws_stride, front_sz, stack_sz, flags,
-                                            status);
+  chol_kernel<<<grid, kThreads, smem, st>>>(P, items, nitems, use_tasks, queue, tdone, hand, ws, ws_stride, front_sz,
+                                            stack_sz, flags, status);
 }
 
 int chol_ctas_per_sm() {

@@ -7,9 +7,12 @@
 
 namespace feti {
 
-// flags: kCholNoReg (factor K, not K_reg), kCholStopRoot (leave the root front assembled, unfactored)
-void launch_chol(const DevPlan& P, const int* order, int nsub, int* queue, double* ws, int64_t ws_stride,
-                 int64_t front_sz, int64_t stack_sz, int grid, int* status, cudaStream_t st, int flags = 0);
+// flags: kCholNoReg (factor K, not K_reg), kCholStopRoot (leave the root front assembled, unfactored).
+// items (subdomain, task, global task id, parent's global task id); use_tasks = 0: whole subdomains.
+// tdone: per global task, child tasks finished (zeroed before the launch); hand: hand-over slots.
+void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks, int* queue, int* tdone,
+                 double* hand, double* ws, int64_t ws_stride, int64_t front_sz, int64_t stack_sz, int grid,
+                 int* status, cudaStream_t st, int flags = 0);
 int chol_ctas_per_sm();
 // items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
 // X2 (FP32 X only, may be null): also write each finished X block split into bf16 hi/lo halves for the

@@ -600,6 +600,54 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
   }
 }
 
+void plan_tasks(PatternPlan& P, double target) {
+  const int ns = P.nsn;
+  std::vector<double> own(ns, 0.0), sub(ns, 0.0);
+  for (int s = 0; s < ns; ++s) {
+    const double w = P.sn_w[s], f = w + P.sn_r[s];
+    double fl = 0;
+    for (int k = 0; k < (int)w; ++k) {
+      const double rem = f - k - 1;
+      fl += 1 + rem + rem * (rem + 1);
+    }
+    own[s] = fl;
+  }
+  for (int s = 0; s < ns; ++s) {  // postorder: children first
+    sub[s] += own[s];
+    if (P.sn_parent[s] >= 0) sub[P.sn_parent[s]] += sub[s];
+  }
+  P.sn_task.assign(ns, 0);
+  P.sn_hoff.assign(ns, -1);
+  P.task_parent.assign(1, -1);
+  P.task_cost.assign(1, 0.0);
+  P.hsize = 0;
+  // from the roots down (reverse postorder): a non-small supernode with a heavy subtree and a parent starts a
+  // task of its own below its parent's task; everything else joins its parent's task
+  for (int s = ns - 1; s >= 0; --s) {
+    const int p = P.sn_parent[s];
+    if (p < 0) {
+      P.sn_task[s] = 0;
+    } else if (target > 0 && !P.sn_small[s] && sub[s] > target && P.sn_r[s] > 0) {
+      const int t = (int)P.task_parent.size();
+      P.task_parent.push_back(P.sn_task[p]);
+      P.task_cost.push_back(0.0);
+      P.sn_task[s] = t;
+      P.sn_hoff[s] = P.hsize;
+      P.hsize += (int64_t)P.sn_r[s] * P.sn_r[s];
+    } else {
+      P.sn_task[s] = P.sn_task[p];
+    }
+    P.task_cost[P.sn_task[s]] += own[s];
+  }
+  P.ntask = (int)P.task_parent.size();
+  P.task_nchild.assign(P.ntask, 0);
+  P.task_height.assign(P.ntask, 0);
+  for (int t = 1; t < P.ntask; ++t) P.task_nchild[P.task_parent[t]]++;
+  // tasks are numbered parents first, so heights follow from the highest numbers down
+  for (int t = P.ntask - 1; t >= 1; --t)
+    P.task_height[P.task_parent[t]] = std::max(P.task_height[P.task_parent[t]], P.task_height[t] + 1);
+}
+
 void plan_rhs(const PatternPlan& P, int m, const int32_t* B_dof, BPlan& Bp) {
   Bp = BPlan();
   Bp.m = m;

@@ -56,7 +56,22 @@ struct PatternPlan {
   int nlast = 0;  // columns of the forced root supernode (the DOFs ordered last), 0 if none
   std::vector<int64_t> uofs;  // per supernode, offset of its r-vector
   int64_t usize = 0;
+  // Cholesky work split (plan_tasks): the supernodal tree cut into tasks at the roots of heavy subtrees;
+  // task 0 holds the tree's roots, a task's parent waits for it, and a split root's update block goes to
+  // a hand-over slot instead of the CTA stack
+  int ntask = 1;
+  std::vector<int> sn_task;        // local task of each supernode
+  std::vector<int64_t> sn_hoff;    // hand-over slot of a split root (doubles, relative), -1 otherwise
+  std::vector<int> task_parent;    // parent task (-1 for task 0)
+  std::vector<int> task_nchild;    // child tasks
+  std::vector<int> task_height;    // 0 for tasks without child tasks, else 1 + the tallest child
+  std::vector<double> task_cost;   // Cholesky flops of the task's own supernodes
+  int64_t hsize = 0;               // doubles of all hand-over slots
 };
+
+// Cut the pattern's supernodal tree into Cholesky tasks: a child subtree whose flops exceed `target` becomes
+// a task of its own (recursively), so that one large subdomain can be factored by several CTAs.
+void plan_tasks(PatternPlan& P, double target);
 
 struct BPlan {
   int m = 0, m_pad = 0, nb = 0;

@@ -50,7 +50,8 @@ class FetiOptions(C.Structure):
                 ("recompute_X", C.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
                 ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
-                ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64), ("assembly_route", C.c_int32)]
+                ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64), ("assembly_route", C.c_int32),
+                ("chol_split", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -69,7 +70,8 @@ class FetiStats(C.Structure):
                 ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double),
                 ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32),
-                ("syrk_variant", C.c_int32), ("assembly_route", C.c_int32), ("route_ms", C.c_double * 3)]
+                ("chol_tasks", C.c_int32), ("syrk_variant", C.c_int32), ("assembly_route", C.c_int32),
+                ("route_ms", C.c_double * 3)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -232,14 +234,15 @@ class FetiOperator:
     residual replacement of the mixed solve; precond: "none" (M = I) or
     "lumped" (M = (BB^T)^-1 sum_i B_i K_i B_i^T (BB^T)^-1) or "dirichlet"
     (the same with the Schur complements S_i of K_i onto the DOFs B touches in
-    place of K_i; needs route="schur")."""
+    place of K_i; needs route="schur"); chol_split: "auto" (autotuned), "whole"
+    (one subdomain per CTA) or "tasks" (heavy subtrees on CTAs of their own)."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
                  precond: str = "none", leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, per_element: bool = False,
                  recompute_X: bool = False, adjoint_work_bytes: int = 0, route: str = "syrk",
-                 torch_alloc: bool = True):
+                 chol_split: str = "auto", torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -265,6 +268,7 @@ class FetiOperator:
         opt.recompute_X = 1 if recompute_X else 0
         opt.adjoint_work_bytes = int(adjoint_work_bytes)
         opt.assembly_route = {"syrk": 0, "schur": 1, "trsm": 2, "auto": 3}[route]
+        opt.chol_split = {"auto": 0, "whole": 1, "tasks": 2}[chol_split]
         self._cb = None
         if torch_alloc:
             dev = self.device.index
