@@ -4,7 +4,7 @@ a CTA of its own, its root's update block handed to the parent task through
 global memory, the parent task waiting, bounded, for its children).  Each
 supernode's arithmetic and the order of its children's extend-adds are the
 same either way, so the factor, and with it F_i, must agree bit for bit; the
-split must actually create tasks on these cases; and F_i meets the oracle's
+split must actually create tasks on the 3D cases; and F_i meets the oracle's
 bar.  The Dirichlet preconditioner's factorisation (stopped at the root
 front) runs through the same tasks."""
 import numpy as np
@@ -56,7 +56,10 @@ def test_subtree_tasks_same_factor(torch_cuda, name, prec, route):
     Fw, sw = _assemble(P, prec, route, "whole")
     Ft, stt = _assemble(P, prec, route, "tasks")
     assert sw["chol_tasks"] == P.nsub
-    assert stt["chol_tasks"] > P.nsub, stt["chol_tasks"]
+    # the 2D case's subtrees are all warp-sized (nothing to split); the 3D ones have tasks
+    assert stt["chol_tasks"] >= P.nsub
+    if P.dim == 3:
+        assert stt["chol_tasks"] > P.nsub, stt["chol_tasks"]
     for i in range(P.nsub):
         assert np.array_equal(Fw[i], Ft[i]), i
     worst = 0.0
