@@ -263,7 +263,11 @@ void build(feti_ctx* c) {
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
   std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs, usm_ofs;
   std::vector<int> sn_small, sn_task;
-  std::vector<int64_t> sn_hoff;
+  std::vector<int64_t> sn_hoff, lh_ofs;
+  // mixed precision: the fronts the large-front TRSM takes (a bottom block of 128 rows or more, or 256 own rows
+  // or more) get a row-major bf16 hi/lo copy of their panel, pat_lh elements per pattern
+  std::vector<int64_t> pat_lh(c->pats.size(), 0);
+  auto lh_big = [&](const PatternPlan& P, int s) { return c->fp32 && (P.sn_r[s] >= 128 || P.sn_w[s] >= 256); };
   std::vector<int> lvl_off, lvl_sn, pat_lvl0(c->pats.size());
   int64_t max_usize = 0;
   std::vector<int> pat_sn0(c->pats.size());
@@ -287,6 +291,8 @@ void build(feti_ctx* c) {
       usm_ofs.push_back(P.usm_ofs[s]);
       sn_task.push_back(P.sn_task[s]);
       sn_hoff.push_back(P.sn_hoff[s]);
+      lh_ofs.push_back(lh_big(P, s) ? pat_lh[p] : -1);
+      if (lh_big(P, s)) pat_lh[p] += (int64_t)(P.sn_w[s] + P.sn_r[s]) * 2 * ((P.sn_w[s] + 7) & ~7);
       uofs.push_back(P.uofs[s]);
     }
     pat_lvl0[p] = (int)lvl_off.size();
@@ -348,7 +354,8 @@ void build(feti_ctx* c) {
   std::vector<double> eldk, elsc;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
-  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, hbo = 0;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, hbo = 0, lho = 0;
+  std::vector<int2> l16_items;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
   int64_t max_chol = 0, max_rhs = 0, max_cf = 0, max_rf = 0, max_usm = 0;
@@ -395,6 +402,10 @@ void build(feti_ctx* c) {
     I.rpart = 0;
     I.hbase = hbo;
     hbo += P.hsize;
+    I.lh = lho;
+    lho += pat_lh[s.pat];
+    for (int q = 0; q < P.nsn; ++q)
+      if (lh_big(P, q)) l16_items.push_back(make_int2(i, q));
     int ntile = B.nb * (B.nb + 1) / 2;
     Kofs += (int64_t)s.col.size();
     Lo += P.Lsize;
@@ -625,6 +636,8 @@ void build(feti_ctx* c) {
     int64_t max_items = 0;  // the finest TRSM work split (64 columns per item)
     for (auto& sh : c->subs) max_items += std::max(1, (sh.m + 63) / 64);
     c->grid_trsm = (int)std::min<int64_t>(max_items, c->nsm * 3);
+    // the mixed TRSM holds the tensor-core stage ring in shared memory: fewer resident CTAs
+    c->grid_trsm32 = (int)std::min<int64_t>(c->grid_trsm, (int64_t)c->nsm * trsm_ctas_per_sm(true, 2));
   }
   c->chol_front = max_cf;
   c->rhs_front = max_rf;
@@ -639,6 +652,7 @@ void build(feti_ctx* c) {
     const int64_t cap = std::max<int64_t>(1, (int64_t)(0.4 * (double)free_b) / (c->ws_stride * 8));
     c->grid_chol = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid_chol, cap));
     c->grid_trsm = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid_trsm, cap));
+    c->grid_trsm32 = std::max(1, std::min(c->grid_trsm32, c->grid_trsm));
   }
   int gw = std::max(c->grid_chol, c->grid_trsm);
 
@@ -667,6 +681,12 @@ void build(feti_ctx* c) {
   D.usm_ofs = upload(c, usm_ofs);
   D.sn_task = upload(c, sn_task);
   D.sn_hoff = upload(c, sn_hoff);
+  D.lh_ofs = upload(c, lh_ofs);
+  if (c->fp32) {
+    D.LH = (uint16_t*)dalloc(c, (size_t)std::max<int64_t>(lho, 8) * 2);
+    c->d_l16_items = upload(c, l16_items);
+    c->n_l16 = (int)l16_items.size();
+  }
   c->d_hand = (double*)dalloc(c, (size_t)std::max<int64_t>(hbo, 1) * 8);
   D.jb = upload(c, jb);
   D.je = upload(c, je);
@@ -963,7 +983,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
   if (!ctx->d_X)  // released after the previous assembly (recompute_X)
     ctx->d_X = dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * (ctx->fp32 ? 4 : 8));
   const bool split = ctx->fp32 && ctx->opt.prec == FETI_PREC_SPLIT_BF16;
-  if (split && !ctx->d_X2)  // the bf16 hi/lo copy of X for the split-bf16 SYRK (2 bf16 per element)
+  if (ctx->fp32 && !ctx->d_X2)  // the bf16 hi/lo copy of X (GEMM operand of the large fronts; split-bf16 SYRK)
     ctx->d_X2 = (uint16_t*)dalloc(ctx, (size_t)std::max<int64_t>(ctx->stats.X_elems, 1) * 4);
   // mixed precision: the TRSM panel updates run on the tensor cores in split-bf16 in both mixed modes
   // (about 16 operand bits, FP32 accumulation), so that X_i is FP32-accurate and the TF32 mode's extra
@@ -973,8 +993,9 @@ feti_status feti_assemble(feti_ctx* ctx) {
   auto run_trsm = [&](const feti_ctx::TrsmCand& tc, cudaStream_t s2) {
     CK(cudaMemsetAsync(ctx->d_queue + 16, 0, sizeof(int), s2));
     launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
-                ctx->ws_stride, ctx->rhs_front, std::min(ctx->grid_trsm, tc.nitems), tcmode, tf32_out,
-                ctx->d_status, s2, 0, split ? ctx->d_X2 : nullptr, ctx->d_L32);
+                ctx->ws_stride, ctx->rhs_front, std::min(ctx->fp32 ? ctx->grid_trsm32 : ctx->grid_trsm, tc.nitems),
+                tcmode, tf32_out,
+                ctx->d_status, s2, 0, ctx->d_X2, ctx->d_L32, split ? 1 : 0);
   };
   // the numeric phase as one sequence of launches (recorded once into a CUDA graph, see below); r2: the
   // TRSM-path route (F_i = B_i P^T L^{-T} X_i in host-driven batches, not captured)
@@ -1017,8 +1038,11 @@ feti_status feti_assemble(feti_ctx* ctx) {
       CK(cudaEventRecordWithFlags(ctx->ev[3], s2, evf));
       return;
     }
-    if (ctx->fp32)  // the mixed TRSM reads an FP32 copy of the factor
+    if (ctx->fp32) {
+      // the mixed TRSM reads an FP32 copy of the factor, and its large fronts a row-major bf16 hi/lo copy
       launch_l32(ctx->P.L, ctx->d_L32, ctx->stats.L_doubles, ctx->nsm * 8, s2);
+      launch_l16(ctx->P, ctx->d_l16_items, ctx->n_l16, ctx->d_L32, ctx->P.LH, ctx->nsm * 4, s2);
+    }
     if (!ctx->trsm_tuned) {
       // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)
       for (auto& tc : ctx->trsm_cands) {

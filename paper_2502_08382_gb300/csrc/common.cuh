@@ -41,6 +41,7 @@ struct SubInfo {
   int64_t tpart;     // first apply tile of this subdomain times kT (its row / column partial slots)
   int64_t rpart;     // unused
   int64_t hbase;     // base of this subdomain's Cholesky hand-over slots (doubles)
+  int64_t lh;        // base of this subdomain's row-major bf16 hi/lo panels (LH, elements)
 };
 
 struct DevPlan {
@@ -70,6 +71,9 @@ struct DevPlan {
   const int* sn_task;        // [sn] Cholesky task of the supernode (local to the pattern's split)
   const int64_t* sn_hoff;    // [sn] hand-over slot of a split root (relative to the subdomain's hbase), -1 if none
   const int* task_nchild;    // [global task] child tasks to wait for
+  const int64_t* lh_ofs;     // [sn] offset of the supernode's row-major hi/lo panel in LH (relative to the
+                             // subdomain's lh), -1 for fronts the large-front TRSM does not take
+  uint16_t* LH;              // row-major bf16 hi/lo copies of the large panels (mixed precision)
   double* dinv;              // [dof + j] reciprocal pivots 1 / L_jj (written after the factorisation)
   // bplan tables
   const int* jb;

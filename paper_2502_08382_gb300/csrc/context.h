@@ -85,6 +85,8 @@ struct feti_ctx {
   int ntask_total = 0;
   int* d_tdone = nullptr;            // per global task: child tasks finished
   double* d_hand = nullptr;          // hand-over slots of split subtree roots
+  int2* d_l16_items = nullptr;       // (subdomain, supernode) of the panels with a row-major hi/lo copy
+  int n_l16 = 0;
   int syrk_variant = 0;              // split-bf16 SYRK kernel picked by the autotuner
   bool syrk_tuned = false;
   int* d_impl_order = nullptr;
@@ -108,6 +110,7 @@ struct feti_ctx {
   int nsyrk = 0, napply = 0;
   int64_t ncols = 0;
   int grid_chol = 0, grid_trsm = 0, grid_impl = 0;
+  int grid_trsm32 = 0;  // CTAs of the mixed-precision TRSM (its occupancy with the tensor-core stage ring)
   size_t impl_smem = 0;
   double* d_uws = nullptr;  // update vectors of the implicit solve, ustride doubles per CTA
   int64_t ustride = 0;

@@ -492,11 +492,20 @@ constexpr uint32_t kTrsmTmemCols = 64;
 constexpr int kTcMinRows = 128;  // smaller updates stay on the SIMT path (its per-tile set-up costs more there)
 constexpr int kTcOpA = kTcRows * 128, kTcOpB = kTcCols * 128;
 
+// Pipelined GEMM of the large fronts (gemm_tc): a ring of kGS stages, each holding one 64-deep K chunk of
+// A (128 rows) and B (64 columns) as bf16 hi and lo halves in the 128-byte-swizzled K-major layout.
+constexpr int kGS = 2;
+constexpr int kGOpA = kTcRows * 128, kGOpB = kTcCols * 128;
+constexpr int kGStage = 2 * kGOpA + 2 * kGOpB;  // 48 KB
+constexpr int kTrsmDyn = 1024 + kGS * kGStage;  // dynamic shared memory of trsm_kernel<float> with tensor cores
+
 struct TcState {
-  uint8_t* smem;     // 1024-aligned operand buffers: A (hi, lo), B (hi, lo)
+  uint8_t* smem;     // 1024-aligned operand buffers: A (hi, lo), B (hi, lo); also the GEMM stage ring
   uint64_t* mbar;
+  uint64_t* gbar;    // kGS stage barriers of the pipelined GEMM
   uint32_t tmem;
   uint32_t phase;    // commits so far (mbarrier parity)
+  uint32_t g;        // GEMM chunks committed so far (stage = g % kGS, parity = (g / kGS) & 1)
   int* abort;        // shared flag: a bounded wait gave up
 };
 
@@ -659,6 +668,175 @@ __device__ void panel_update_simt(SolveSmem<T>& sm, const T* Ls, int f, int rbeg
   }
 }
 
+// C[rbeg, rend) x [0, J) -= A[rbeg, rend) x [kbeg, kend) . B[kbeg, kend) x [0, J) on the tensor cores in split
+// bf16 (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), for the large fronts.  A is the row-major hi/lo copy
+// of the supernode's panel (row i: lwp hi values, then lwp lo values; zero beyond w), B the bf16 hi/lo copy of
+// X_s (column j: wp hi values, then wp lo values; zero beyond w).  kbeg is a multiple of 8 and every K value
+// in [kbeg, kend) rounded up to 8 lies inside the padding.  Tiles of 128 rows x 64 columns, K in chunks of 64
+// (one swizzled 128-byte row per operand row): all threads stage chunks by cp.async into the kGS-stage ring,
+// running ahead across tile boundaries, one thread issues each chunk's MMAs and commits them to its stage's
+// mbarrier (which frees the stage), and after a tile's last chunk the CTA subtracts the accumulator from C
+// (rows below w: the own rows of X_s; the others: W2).  Every wait is bounded.
+__device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int rend, int kbeg, int kend,
+                        const uint16_t* X2s, int wp, float* Xs, float* W2, int w, int r, int J) {
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int ntm = (rend - rbeg + kTcRows - 1) / kTcRows, ntn = (J + kTcCols - 1) / kTcCols;
+  const int nck = (kend - kbeg + 63) / 64;
+  const int total = ntm * ntn * nck;
+  if (rend <= rbeg || J <= 0 || kend <= kbeg) return true;
+  const uint32_t sb0 = smem_u32(tc.smem);
+  const uint32_t g0 = tc.g;
+  constexpr uint32_t idesc = idesc_m128(1u, (uint32_t)kTcCols);
+  auto load = [&](int q, uint32_t sbase) {
+    const int ck = q % nck, t = q / nck, tn = t % ntn, tm = t / ntn;
+    const int k0 = kbeg + ck * 64, i0 = rbeg + tm * kTcRows, j0 = tn * kTcCols;
+    for (int idx = tid; idx < 2 * kTcRows * 8 + 2 * kTcCols * 8; idx += kThreads) {
+      uint32_t dst;
+      const void* src;
+      bool ok;
+      if (idx < 2 * kTcRows * 8) {
+        const int part = idx / (kTcRows * 8), rem = idx % (kTcRows * 8), m = rem / 8, c = rem % 8;
+        const int i = i0 + m, k = k0 + 8 * c;
+        ok = i < rend && k < kend;
+        src = ok ? (const void*)(LH + (int64_t)i * 2 * lwp + (part ? lwp : 0) + k) : (const void*)LH;
+        dst = sbase + part * kGOpA + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+      } else {
+        const int id2 = idx - 2 * kTcRows * 8;
+        const int part = id2 / (kTcCols * 8), rem = id2 % (kTcCols * 8), n = rem / 8, c = rem % 8;
+        const int j = j0 + n, k = k0 + 8 * c;
+        ok = j < J && k < kend;
+        src = ok ? (const void*)(X2s + (int64_t)j * 2 * wp + (part ? wp : 0) + k) : (const void*)X2s;
+        dst = sbase + 2 * kGOpA + part * kGOpB + (n >> 3) * 1024 + (n & 7) * 128 + ((c ^ (n & 7)) << 4);
+      }
+      cp_async16(dst, src, ok);
+    }
+  };
+  bool ok = true;
+  for (int i = 0; i < total + kGS - 1; ++i) {
+    if (i < total) {
+      if (i >= kGS) {  // the stage's previous chunk must have been multiplied
+        const uint32_t gp = g0 + i - kGS;
+        if (tid == 0 && !mbar_wait(smem_u32(&tc.gbar[gp % kGS]), (gp / kGS) & 1)) *tc.abort = 1;
+        __syncthreads();
+        if (*tc.abort) {
+          ok = false;
+          break;
+        }
+      }
+      load(i, sb0 + ((g0 + i) % kGS) * kGStage);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int j = i - (kGS - 1);
+    if (j < 0 || j >= total) continue;
+    asm volatile("cp.async.wait_group %0;" ::"n"(kGS - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int ck = j % nck;
+    const uint32_t st = (g0 + j) % kGS;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sA = sb0 + st * kGStage, sB = sA + 2 * kGOpA;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {  // K = 16 per MMA, 32 B of each 128-byte row
+        const uint64_t ah = sw128_desc(sA + kk * 32), al = sw128_desc(sA + kGOpA + kk * 32);
+        const uint64_t bh = sw128_desc(sB + kk * 32), bl = sw128_desc(sB + kGOpB + kk * 32);
+        mma_f16(tc.tmem, ah, bh, idesc, (ck > 0 || kk > 0) ? 1u : 0u);
+        mma_f16(tc.tmem, ah, bl, idesc, 1u);
+        mma_f16(tc.tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(smem_u32(&tc.gbar[st]));
+    }
+    if (ck != nck - 1) continue;
+    // the tile's last chunk: wait for its MMAs, then C -= accumulator
+    if (tid == 0 && !mbar_wait(smem_u32(&tc.gbar[st]), ((g0 + j) / kGS) & 1)) *tc.abort = 1;
+    __syncthreads();
+    if (*tc.abort) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+      const int t = j / nck, tn = t % ntn, tm = t / ntn;
+      const int ri = rbeg + tm * kTcRows, cj = tn * kTcCols;
+      const int q = warp % 4, ch = warp / 4;
+      uint32_t v[32];
+      tmem_ld32(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
+      const int row = ri + q * 32 + lane;
+      if (row < rend) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int col = cj + ch * 32 + e;
+          if (col < J) {
+            if (row < w) Xs[(int64_t)col * wp + row] -= __uint_as_float(v[e]);
+            else W2[(int64_t)col * r + (row - w)] -= __uint_as_float(v[e]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok) asm volatile("cp.async.wait_all;" ::: "memory");
+  tc.g = g0 + total;
+  return ok;
+}
+
+// Write the bf16 hi/lo copy of rows [ka, kb) of X_s (column j: wp hi values, then wp lo values).
+__device__ __forceinline__ void write_x2(const float* Xs, int wp, uint16_t* X2s, int ka, int kb, int J) {
+  const int nk = kb - ka;
+  __nv_bfloat16* h2 = reinterpret_cast<__nv_bfloat16*>(X2s);
+  for (int64_t idx = threadIdx.x; idx < (int64_t)nk * J; idx += kThreads) {
+    const int64_t j = idx / nk;
+    const int k = ka + (int)(idx - j * nk);
+    const float v = Xs[j * wp + k];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    h2[2 * j * wp + k] = hi;
+    h2[2 * j * wp + wp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// Diagonal step of the forward solve: X_b <- L_bb^{-1} X_b for the rows [kb, kb + nbk) of X_s (all J columns),
+// with L_bb^{-1} formed explicitly by one warp (a 32 x 32 triangular inverse) and applied as a small GEMM.
+template <typename T>
+__device__ void diag_block(SolveSmem<T>& sm, const T* Ls, int f, int kb, int nbk, T* Xs, int wp, int J, int unit) {
+  const int tid = threadIdx.x, warp = tid / 32;
+  auto Di = reinterpret_cast<T (*)[kNB + 1]>(&sm.B[0][0]);
+  for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
+    int i = idx % kNB, j = idx / kNB;
+    sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
+  }
+  // unit: L is in unit-lower form (pivots folded out after the assembly), its stored diagonal is zero
+  if (tid < kNB) sm.dinv[tid] = tid < nbk ? (unit ? (T)1 : (T)1 / Ls[(int64_t)(kb + tid) * f + kb + tid]) : (T)0;
+  __syncthreads();
+  if (warp == 0) warp_tri_inverse<T>(sm.D, sm.dinv, Di, nbk);
+  __syncthreads();
+  // X_b <- Di X_b for 64 columns at a time: column y = tid % 64, rows jg*8 .. jg*8+7
+  const int y = tid % kT, jg = tid / kT;
+  for (int cj = 0; cj < J; cj += kT) {
+    for (int idx = tid; idx < kNB * kT; idx += kThreads) {
+      int k = idx % kNB, yy = idx / kNB;
+      sm.A[k][yy] = (k < nbk && cj + yy < J) ? Xs[(int64_t)(cj + yy) * wp + kb + k] : (T)0;
+    }
+    __syncthreads();
+    if (jg * 8 < nbk && cj + (y & ~31) < J) {
+      T acc[8] = {};
+      for (int k = 0; k <= min(nbk - 1, jg * 8 + 7); ++k) {
+        const T a = sm.A[k][y];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = fma(Di[jg * 8 + jj][k], a, acc[jj]);
+      }
+      if (cj + y < J) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = jg * 8 + jj;
+          if (j < nbk) Xs[(int64_t)(cj + y) * wp + kb + j] = acc[jj];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Forward solve of one RHS front: X_s = L_ss^{-1} X_s, then C -= L_rs X_s
 // (C = the r bottom rows).  Column-major fronts: column j of X_s is
 // Xs[j * wp + 0 .. w), column j of the bottom block is W2[j * r + 0 .. r).
@@ -670,48 +848,10 @@ __device__ void panel_update_simt(SolveSmem<T>& sm, const T* Ls, int f, int rbeg
 template <typename T>
 __device__ bool solve_front(SolveSmem<T>& sm, const T* Ls, int f, int w, T* Xs, int wp, T* W2, int J,
                             TcState* tc, int tcmode, int unit) {
-  const int tid = threadIdx.x, warp = tid / 32;
   const int r = f - w;
-  auto Di = reinterpret_cast<T (*)[kNB + 1]>(&sm.B[0][0]);
   for (int kb = 0; kb < w; kb += kNB) {
     const int nbk = min(kNB, w - kb);
-    for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
-      int i = idx % kNB, j = idx / kNB;
-      sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : (T)0;
-    }
-    // unit: L is in unit-lower form (pivots folded out after the assembly), its stored diagonal is zero
-    if (tid < kNB)
-      sm.dinv[tid] = tid < nbk ? (unit ? (T)1 : (T)1 / Ls[(int64_t)(kb + tid) * f + kb + tid]) : (T)0;
-    __syncthreads();
-    if (warp == 0) warp_tri_inverse<T>(sm.D, sm.dinv, Di, nbk);
-    __syncthreads();
-    {
-      // X_b <- Di X_b for 64 columns at a time: column y = tid % 64, rows jg*8 .. jg*8+7
-      const int y = tid % kT, jg = tid / kT;
-      for (int cj = 0; cj < J; cj += kT) {
-        for (int idx = tid; idx < kNB * kT; idx += kThreads) {
-          int k = idx % kNB, yy = idx / kNB;
-          sm.A[k][yy] = (k < nbk && cj + yy < J) ? Xs[(int64_t)(cj + yy) * wp + kb + k] : (T)0;
-        }
-        __syncthreads();
-        if (jg * 8 < nbk && cj + (y & ~31) < J) {
-          T acc[8] = {};
-          for (int k = 0; k <= min(nbk - 1, jg * 8 + 7); ++k) {
-            const T a = sm.A[k][y];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) acc[jj] = fma(Di[jg * 8 + jj][k], a, acc[jj]);
-          }
-          if (cj + y < J) {
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = jg * 8 + jj;
-              if (j < nbk) Xs[(int64_t)(cj + y) * wp + kb + j] = acc[jj];
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
+    diag_block<T>(sm, Ls, f, kb, nbk, Xs, wp, J, unit);
     // the own rows below the block
     const int i0 = kb + nbk;
     if (i0 < w) {
@@ -740,6 +880,32 @@ __device__ bool solve_front(SolveSmem<T>& sm, const T* Ls, int f, int w, T* Xs, 
   return true;
 }
 
+// Forward solve of a large front on the tensor cores (mixed precision): the own rows in blocks of 128, each
+// solved by four diagonal steps of 32 rows (the rows inside the block updated on the SIMT path), its rows
+// written as bf16 hi/lo (the B operand of the later GEMMs and of the split-bf16 SYRK), then the own rows below
+// it updated with K = 128 by the pipelined GEMM; finally the bottom rows, W2 -= L_rs X_s with K = w, by the same
+// GEMM.  LH: the row-major hi/lo copy of the panel (launch_l16).  X2s: the hi/lo copy of X_s.
+__device__ bool solve_front_big(SolveSmem<float>& sm, const float* Ls, const uint16_t* LH, int f, int w, float* Xs,
+                                int wp, float* W2, int J, uint16_t* X2s, TcState& tc) {
+  const int r = f - w;
+  for (int k0 = 0; k0 < w; k0 += kTcRows) {
+    const int e0 = min(w, k0 + kTcRows);
+    for (int kb = k0; kb < e0; kb += kNB) {
+      const int nbk = min(kNB, e0 - kb);
+      diag_block<float>(sm, Ls, f, kb, nbk, Xs, wp, J, 0);
+      const int i0 = kb + nbk;
+      if (i0 < e0) panel_update_simt<float>(sm, Ls, f, i0, e0, kb, i0, Xs, wp, W2, w, r, J);
+    }
+    __syncthreads();
+    // the finished rows as bf16 hi/lo (after the last block also the zero padding rows up to wp)
+    write_x2(Xs, wp, X2s, k0, e0 == w ? wp : e0, J);
+    __syncthreads();
+    if (e0 < w && !gemm_tc(tc, LH, wp, e0, w, k0, e0, X2s, wp, Xs, W2, w, r, J)) return false;
+  }
+  if (r > 0 && !gemm_tc(tc, LH, wp, w, f, 0, w, X2s, wp, Xs, W2, w, r, J)) return false;
+  return true;
+}
+
 // Round an FP32 value to TF32 (10 explicit mantissa bits), to nearest with ties away from zero.
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
@@ -758,15 +924,19 @@ __device__ __forceinline__ float round_tf32(float x) {
 // per column wp hi values then wp lo values, for the split-bf16 SYRK.
 // LT: the factor in the solve's precision (the FP32 copy of L for T = float, L itself for T = double).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2* items, int nitems, int cw,
-                                                         int* queue, const T* LT, T* X, T* ws, int64_t ws_stride,
-                                                         int64_t front_sz, int tcmode, int tf32_out, int unit,
-                                                         uint16_t* X2, int* status) {
-  __shared__ SolveSmem<T> sm;
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 3)
+    trsm_kernel(DevPlan P, const int2* items, int nitems, int cw, int* queue, const T* LT, T* X, T* ws,
+                int64_t ws_stride, int64_t front_sz, int tcmode, int tf32_out, int unit, uint16_t* X2, int x2_out,
+                int* status) {
   __shared__ uint64_t tc_mbar;
+  __shared__ uint64_t tc_gbar[kGS];
   __shared__ uint32_t tc_tmem;
   __shared__ int tc_abort;
   extern __shared__ uint8_t tc_raw[];
+  // the SIMT solve's buffers share the dynamic shared memory with the tensor-core operand buffers (never in
+  // use at the same time)
+  uint8_t* dyn = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+  SolveSmem<T>& sm = *reinterpret_cast<SolveSmem<T>*>(dyn);
   const int tid = threadIdx.x;
   T* W2 = ws + (int64_t)blockIdx.x * ws_stride;
   T* stack = W2 + front_sz;
@@ -783,16 +953,19 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
     }
     if (tid == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tc_mbar)));
+      for (int k = 0; k < kGS; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tc_gbar[k])));
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       tc_abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    tc.smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    tc.smem = dyn;
     tc.mbar = &tc_mbar;
+    tc.gbar = tc_gbar;
     tc.tmem = tc_tmem;
     tc.phase = 0;
+    tc.g = 0;
     tc.abort = &tc_abort;
   }
   }
@@ -838,13 +1011,23 @@ __global__ void __launch_bounds__(kThreads, 3) trsm_kernel(DevPlan P, const int2
         }
       }
       __syncthreads();
-      if (!solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit)) break;
+      // large fronts of the tensor-core path: the blocked solve with pipelined GEMMs
+      const int64_t lho = (sizeof(T) == 4 && tcmode == 2) ? P.lh_ofs[gs] : -1;
+      uint16_t* X2s = X2 ? X2 + 2 * (S.X + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp) : nullptr;
+      bool ok;
+      if constexpr (sizeof(T) == 4) {
+        ok = lho >= 0 && X2s ? solve_front_big(sm, L + P.Lofs[gs], P.LH + S.lh + lho, f, w, Xs, wp, W2, J, X2s, tc)
+                             : solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
+      } else {
+        ok = solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
+      }
+      if (!ok) break;
       __syncthreads();
       if constexpr (sizeof(T) == 4) {
         // X_s is final here (the parent reads only the bottom rows W2)
         if (tf32_out)
           for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) Xs[idx] = round_tf32(Xs[idx]);
-        if (X2) {
+        if (X2 && x2_out && !(lho >= 0)) {
           __nv_bfloat16* h2 =
               reinterpret_cast<__nv_bfloat16*>(X2) + 2 * (S.X + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp);
           for (int64_t idx = tid; idx < (int64_t)wp * J; idx += kThreads) {
@@ -891,7 +1074,47 @@ __global__ void __launch_bounds__(256) l32_kernel(const double* __restrict__ L, 
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) L32[n - 1] = (float)L[n - 1];
 }
 
+// Row-major bf16 hi/lo copy of the large panels for the tensor-core TRSM: row i of the f x w panel as lwp hi
+// values then lwp lo values (hi = bf16(x), lo = bf16(x - hi) of the FP32 entry, zero for k >= w), so that
+// every 16-byte piece of a K-major operand row is one cp.async.  One CTA per panel, 32 x 32 tiles transposed
+// through shared memory.
+__global__ void __launch_bounds__(256) l16_kernel(DevPlan P, const int2* items, int nitems, const float* L32,
+                                                  uint16_t* LH) {
+  __shared__ float t[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const SubInfo S = P.sub[items[it].x];
+    const int gs = S.sn0 + items[it].y;
+    const int w = P.sn_w[gs], f = w + P.sn_r[gs], lwp = (w + 7) & ~7;
+    const float* Lp = L32 + S.L + P.Lofs[gs];
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(LH + S.lh + P.lh_ofs[gs]);
+    for (int i0 = 0; i0 < f; i0 += 32)
+      for (int k0 = 0; k0 < lwp; k0 += 32) {
+        for (int kk = ty; kk < 32; kk += 8) {
+          const int k = k0 + kk, i = i0 + tx;
+          t[kk][tx] = (i < f && k < w) ? Lp[(int64_t)k * f + i] : 0.f;
+        }
+        __syncthreads();
+        for (int ii = ty; ii < 32; ii += 8) {
+          const int i = i0 + ii, k = k0 + tx;
+          if (i < f && k < lwp) {
+            const float v = t[tx][ii];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            out[(int64_t)i * 2 * lwp + k] = hi;
+            out[(int64_t)i * 2 * lwp + lwp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+          }
+        }
+        __syncthreads();
+      }
+  }
+}
+
 }  // namespace
+
+void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, int grid,
+                cudaStream_t st) {
+  if (nitems > 0) l16_kernel<<<std::min(grid, nitems), 256, 0, st>>>(P, items, nitems, L32, LH);
+}
 
 void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st) {
   if (n > 0) l32_kernel<<<grid, 256, 0, st>>>(L, L32, n);
@@ -914,18 +1137,38 @@ int chol_ctas_per_sm() {
   return nb > 0 ? nb : 1;
 }
 
+static int trsm_smem(bool fp32, int tcmode) {
+  if (!fp32) return 1024 + (int)sizeof(SolveSmem<double>);
+  return tcmode > 0 ? kTrsmDyn : 1024 + (int)sizeof(SolveSmem<float>);
+}
+
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit, uint16_t* X2, const float* L32) {
+                 cudaStream_t st, int unit, uint16_t* X2, const float* L32, int x2_out) {
+  const int smem = trsm_smem(fp32, tcmode);
   if (fp32) {
-    const int smem = tcmode > 0 ? (tcmode == 2 ? 2 : 1) * (kTcOpA + kTcOpB) + 1024 : 0;
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, L32, (float*)X, (float*)ws,
-                                                     2 * ws_stride, front_sz, tcmode, tf32_out, 0, X2, status);
+                                                     2 * ws_stride, front_sz, tcmode, tf32_out, 0, X2, x2_out,
+                                                     status);
   } else {
-    trsm_kernel<double><<<grid, kThreads, 0, st>>>(P, items, nitems, cw, queue, P.L, (double*)X, ws, ws_stride,
-                                                   front_sz, 0, 0, unit, nullptr, status);
+    cudaFuncSetAttribute(trsm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    trsm_kernel<double><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, P.L, (double*)X, ws, ws_stride,
+                                                      front_sz, 0, 0, unit, nullptr, 0, status);
   }
+}
+
+int trsm_ctas_per_sm(bool fp32, int tcmode) {
+  const int smem = trsm_smem(fp32, tcmode);
+  int nb = 0;
+  if (fp32) {
+    cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trsm_kernel<float>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(trsm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trsm_kernel<double>, kThreads, smem);
+  }
+  return nb > 0 ? nb : 1;
 }
 
 }  // namespace feti

@@ -15,12 +15,18 @@ void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks,
                  int* status, cudaStream_t st, int flags = 0);
 int chol_ctas_per_sm();
 // items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
-// X2 (FP32 X only, may be null): also write each finished X block split into bf16 hi/lo halves for the
-// split-bf16 SYRK (per column: wp hi values, then wp lo values; X2 has 2 bf16 per X element)
+// X2 (FP32 X only, may be null): the bf16 hi/lo copy of X (per column: wp hi values, then wp lo values; 2 bf16
+// per X element): the large fronts (P.lh_ofs >= 0, tcmode 2) use it as GEMM operand; with x2_out every
+// finished block is written to it (the split-bf16 SYRK reads it)
 // L32 (FP32 X only): the FP32 copy of L (launch_l32)
 void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* queue, void* X, bool fp32,
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
-                 cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr, const float* L32 = nullptr);
+                 cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr, const float* L32 = nullptr, int x2_out = 0);
+int trsm_ctas_per_sm(bool fp32, int tcmode);
+// the row-major bf16 hi/lo copies of the large panels (P.LH) from the FP32 copy of L; items: (subdomain, local
+// supernode) of every panel with P.lh_ofs >= 0
+void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, int grid,
+                cudaStream_t st);
 void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st);
 // X2 (split mode): the bf16 hi/lo copy of X written by the TRSM (per column: wp hi values, then wp lo values)
 // variant (split mode): 0 = all threads load then one thread issues; 1 = warp-specialised (producer warps,
