@@ -160,6 +160,7 @@ typedef struct {
                                          3-5: bulk-copy rings of 4x3, 8x3, 2x6 warps x stages) and grid */
   /* autotuner choice for the pruned TRSM (after the first feti_assemble) */
   int32_t trsm_cols;          /* sorted columns per CTA work item (0: a whole subdomain per item) */
+  int32_t trsm_grid;          /* persistent CTAs of the TRSM launch */
   int32_t chol_tasks;         /* Cholesky work items the autotuner kept: the subdomains, or the tasks of the
                                  subtree split when that was faster */
   int32_t syrk_variant;       /* split-bf16 SYRK kernel picked by the autotuner (0: all threads load, one issues;

@@ -263,10 +263,10 @@ void build(feti_ctx* c) {
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
   std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs, usm_ofs;
   std::vector<int> sn_small, sn_task;
-  std::vector<int64_t> sn_hoff, lh_ofs;
+  std::vector<int64_t> sn_hoff, lh_ofs, di_ofs;
   // mixed precision: the fronts the large-front TRSM takes (a bottom block of 128 rows or more, or 256 own rows
   // or more) get a row-major bf16 hi/lo copy of their panel, pat_lh elements per pattern
-  std::vector<int64_t> pat_lh(c->pats.size(), 0);
+  std::vector<int64_t> pat_lh(c->pats.size(), 0), pat_di(c->pats.size(), 0);
   auto lh_big = [&](const PatternPlan& P, int s) { return c->fp32 && (P.sn_r[s] >= 128 || P.sn_w[s] >= 256); };
   std::vector<int> lvl_off, lvl_sn, pat_lvl0(c->pats.size());
   int64_t max_usize = 0;
@@ -292,7 +292,11 @@ void build(feti_ctx* c) {
       sn_task.push_back(P.sn_task[s]);
       sn_hoff.push_back(P.sn_hoff[s]);
       lh_ofs.push_back(lh_big(P, s) ? pat_lh[p] : -1);
-      if (lh_big(P, s)) pat_lh[p] += (int64_t)(P.sn_w[s] + P.sn_r[s]) * 2 * ((P.sn_w[s] + 7) & ~7);
+      di_ofs.push_back(lh_big(P, s) ? pat_di[p] : -1);
+      if (lh_big(P, s)) {
+        pat_lh[p] += (int64_t)(P.sn_w[s] + P.sn_r[s]) * 2 * ((P.sn_w[s] + 7) & ~7);
+        pat_di[p] += (int64_t)((P.sn_w[s] + 127) / 128) * 4 * 32 * 32;
+      }
       uofs.push_back(P.uofs[s]);
     }
     pat_lvl0[p] = (int)lvl_off.size();
@@ -354,7 +358,7 @@ void build(feti_ctx* c) {
   std::vector<double> eldk, elsc;
   std::vector<double> qsign;
   std::vector<int64_t> fix_pos;
-  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, hbo = 0, lho = 0;
+  int64_t Kofs = 0, Lo = 0, Xo = 0, Fo = 0, qo = 0, dofo = 0, Ro = 0, tpo = 0, hbo = 0, lho = 0, dio = 0;
   std::vector<int2> l16_items;
   int fixo = 0, alo = 0;
   double chol = 0, trsm = 0, syrk = 0, syrke = 0, implb = 0;
@@ -404,6 +408,8 @@ void build(feti_ctx* c) {
     hbo += P.hsize;
     I.lh = lho;
     lho += pat_lh[s.pat];
+    I.di = dio;
+    dio += pat_di[s.pat];
     for (int q = 0; q < P.nsn; ++q)
       if (lh_big(P, q)) l16_items.push_back(make_int2(i, q));
     int ntile = B.nb * (B.nb + 1) / 2;
@@ -682,8 +688,10 @@ void build(feti_ctx* c) {
   D.sn_task = upload(c, sn_task);
   D.sn_hoff = upload(c, sn_hoff);
   D.lh_ofs = upload(c, lh_ofs);
+  D.di_ofs = upload(c, di_ofs);
   if (c->fp32) {
     D.LH = (uint16_t*)dalloc(c, (size_t)std::max<int64_t>(lho, 8) * 2);
+    D.DI = (float*)dalloc(c, (size_t)std::max<int64_t>(dio, 8) * 4);
     c->d_l16_items = upload(c, l16_items);
     c->n_l16 = (int)l16_items.size();
   }
@@ -990,6 +998,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
   // error is that of its SYRK alone; in the TF32 mode X_i is rounded to TF32 for that SYRK
   const int tcmode = ctx->fp32 ? 2 : 0;
   const int tf32_out = ctx->fp32 && ctx->opt.prec == FETI_PREC_TF32 ? 1 : 0;
+  ctx->stats.trsm_grid = ctx->fp32 ? ctx->grid_trsm32 : ctx->grid_trsm;
   auto run_trsm = [&](const feti_ctx::TrsmCand& tc, cudaStream_t s2) {
     CK(cudaMemsetAsync(ctx->d_queue + 16, 0, sizeof(int), s2));
     launch_trsm(ctx->P, tc.d_items, tc.nitems, tc.cw, ctx->d_queue + 16, ctx->d_X, ctx->fp32, ctx->d_ws,
@@ -1041,7 +1050,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
     if (ctx->fp32) {
       // the mixed TRSM reads an FP32 copy of the factor, and its large fronts a row-major bf16 hi/lo copy
       launch_l32(ctx->P.L, ctx->d_L32, ctx->stats.L_doubles, ctx->nsm * 8, s2);
-      launch_l16(ctx->P, ctx->d_l16_items, ctx->n_l16, ctx->d_L32, ctx->P.LH, ctx->nsm * 4, s2);
+      launch_l16(ctx->P, ctx->d_l16_items, ctx->n_l16, ctx->d_L32, ctx->P.LH, ctx->P.DI, ctx->nsm * 4, s2);
     }
     if (!ctx->trsm_tuned) {
       // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)

@@ -42,6 +42,7 @@ struct SubInfo {
   int64_t rpart;     // unused
   int64_t hbase;     // base of this subdomain's Cholesky hand-over slots (doubles)
   int64_t lh;        // base of this subdomain's row-major bf16 hi/lo panels (LH, elements)
+  int64_t di;        // base of this subdomain's inverted 32 x 32 diagonal blocks of the large panels (DI, floats)
 };
 
 struct DevPlan {
@@ -74,6 +75,9 @@ struct DevPlan {
   const int64_t* lh_ofs;     // [sn] offset of the supernode's row-major hi/lo panel in LH (relative to the
                              // subdomain's lh), -1 for fronts the large-front TRSM does not take
   uint16_t* LH;              // row-major bf16 hi/lo copies of the large panels (mixed precision)
+  const int64_t* di_ofs;     // [sn] offset of the supernode's inverted diagonal blocks in DI (relative to the
+                             // subdomain's di; 4 blocks of 32 x 32 per 128 own rows), -1 where lh_ofs is -1
+  float* DI;                 // inverses of the 32 x 32 diagonal blocks of the large panels (FP32)
   double* dinv;              // [dof + j] reciprocal pivots 1 / L_jj (written after the factorisation)
   // bplan tables
   const int* jb;

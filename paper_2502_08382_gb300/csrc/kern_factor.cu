@@ -492,12 +492,14 @@ constexpr uint32_t kTrsmTmemCols = 64;
 constexpr int kTcMinRows = 128;  // smaller updates stay on the SIMT path (its per-tile set-up costs more there)
 constexpr int kTcOpA = kTcRows * 128, kTcOpB = kTcCols * 128;
 
-// Pipelined GEMM of the large fronts (gemm_tc): a ring of kGS stages, each holding one 64-deep K chunk of
-// A (128 rows) and B (64 columns) as bf16 hi and lo halves in the 128-byte-swizzled K-major layout.
-constexpr int kGS = 2;
-constexpr int kGOpA = kTcRows * 128, kGOpB = kTcCols * 128;
-constexpr int kGStage = 2 * kGOpA + 2 * kGOpB;  // 48 KB
-constexpr int kTrsmDyn = 1024 + kGS * kGStage;  // dynamic shared memory of trsm_kernel<float> with tensor cores
+// Pipelined GEMM of the large fronts (gemm_tc): a ring of kGS stages, each holding one 32-deep K chunk of
+// A (128 rows) and B (64 columns) as bf16 hi and lo halves in the 64-byte-swizzled K-major layout (rows of
+// 64 bytes, 8-row atoms of 512 bytes), small enough that three CTAs stay resident per SM for the SIMT parts.
+constexpr int kGS = 3;
+constexpr int kGK = 32;                          // K values per chunk
+constexpr int kGOpA = kTcRows * 64, kGOpB = kTcCols * 64;
+constexpr int kGStage = 2 * kGOpA + 2 * kGOpB;  // 24 KB
+constexpr int kTrsmDyn = 1024 + (kGS * kGStage > 2 * (kTcOpA + kTcOpB) ? kGS * kGStage : 2 * (kTcOpA + kTcOpB));
 
 struct TcState {
   uint8_t* smem;     // 1024-aligned operand buffers: A (hi, lo), B (hi, lo); also the GEMM stage ring
@@ -604,16 +606,18 @@ __device__ bool panel_update_tc(TcState& tc, const float* Ls, int f, int rbeg, i
       // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows), columns 32 (w / 4) .. + 31
       {
         const int q = warp % 4, ch = warp / 4;
-        uint32_t v[32];
-        tmem_ld32(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
         const int i = ri + q * 32 + lane;
-        if (i < rend) {
+        float* dst = i < w ? Xw + i : W2 + (i - w);
+        const int64_t ld = i < w ? wp : r;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v[16];
+          tmem_ld16(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32 + h * 16, v);
+          if (i < rend) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int j = cj + ch * 32 + e;
-            if (j < J) {
-              if (i < w) Xw[(int64_t)j * wp + i] -= __uint_as_float(v[e]);
-              else W2[(int64_t)j * r + (i - w)] -= __uint_as_float(v[e]);
+            for (int e = 0; e < 16; ++e) {
+              const int j = cj + ch * 32 + h * 16 + e;
+              if (j < J) dst[(int64_t)j * ld] -= __uint_as_float(v[e]);
             }
           }
         }
@@ -672,8 +676,8 @@ __device__ void panel_update_simt(SolveSmem<T>& sm, const T* Ls, int f, int rbeg
 // bf16 (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), for the large fronts.  A is the row-major hi/lo copy
 // of the supernode's panel (row i: lwp hi values, then lwp lo values; zero beyond w), B the bf16 hi/lo copy of
 // X_s (column j: wp hi values, then wp lo values; zero beyond w).  kbeg is a multiple of 8 and every K value
-// in [kbeg, kend) rounded up to 8 lies inside the padding.  Tiles of 128 rows x 64 columns, K in chunks of 64
-// (one swizzled 128-byte row per operand row): all threads stage chunks by cp.async into the kGS-stage ring,
+// in [kbeg, kend) rounded up to 8 lies inside the padding.  Tiles of 128 rows x 64 columns, K in chunks of 32
+// (one swizzled 64-byte row per operand row): all threads stage chunks by cp.async into the kGS-stage ring,
 // running ahead across tile boundaries, one thread issues each chunk's MMAs and commits them to its stage's
 // mbarrier (which frees the stage), and after a tile's last chunk the CTA subtracts the accumulator from C
 // (rows below w: the own rows of X_s; the others: W2).  Every wait is bounded.
@@ -681,7 +685,7 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
                         const uint16_t* X2s, int wp, float* Xs, float* W2, int w, int r, int J) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntm = (rend - rbeg + kTcRows - 1) / kTcRows, ntn = (J + kTcCols - 1) / kTcCols;
-  const int nck = (kend - kbeg + 63) / 64;
+  const int nck = (kend - kbeg + kGK - 1) / kGK;
   const int total = ntm * ntn * nck;
   if (rend <= rbeg || J <= 0 || kend <= kbeg) return true;
   const uint32_t sb0 = smem_u32(tc.smem);
@@ -689,24 +693,25 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
   constexpr uint32_t idesc = idesc_m128(1u, (uint32_t)kTcCols);
   auto load = [&](int q, uint32_t sbase) {
     const int ck = q % nck, t = q / nck, tn = t % ntn, tm = t / ntn;
-    const int k0 = kbeg + ck * 64, i0 = rbeg + tm * kTcRows, j0 = tn * kTcCols;
-    for (int idx = tid; idx < 2 * kTcRows * 8 + 2 * kTcCols * 8; idx += kThreads) {
+    const int k0 = kbeg + ck * kGK, i0 = rbeg + tm * kTcRows, j0 = tn * kTcCols;
+    // 4 pieces of 16 B (8 bf16) per 64-byte row
+    for (int idx = tid; idx < 2 * kTcRows * 4 + 2 * kTcCols * 4; idx += kThreads) {
       uint32_t dst;
       const void* src;
       bool ok;
-      if (idx < 2 * kTcRows * 8) {
-        const int part = idx / (kTcRows * 8), rem = idx % (kTcRows * 8), m = rem / 8, c = rem % 8;
+      if (idx < 2 * kTcRows * 4) {
+        const int part = idx / (kTcRows * 4), rem = idx % (kTcRows * 4), m = rem / 4, c = rem % 4;
         const int i = i0 + m, k = k0 + 8 * c;
         ok = i < rend && k < kend;
         src = ok ? (const void*)(LH + (int64_t)i * 2 * lwp + (part ? lwp : 0) + k) : (const void*)LH;
-        dst = sbase + part * kGOpA + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
+        dst = sbase + part * kGOpA + (m >> 3) * 512 + (m & 7) * 64 + ((c ^ ((m >> 1) & 3)) << 4);
       } else {
-        const int id2 = idx - 2 * kTcRows * 8;
-        const int part = id2 / (kTcCols * 8), rem = id2 % (kTcCols * 8), n = rem / 8, c = rem % 8;
+        const int id2 = idx - 2 * kTcRows * 4;
+        const int part = id2 / (kTcCols * 4), rem = id2 % (kTcCols * 4), n = rem / 4, c = rem % 4;
         const int j = j0 + n, k = k0 + 8 * c;
         ok = j < J && k < kend;
         src = ok ? (const void*)(X2s + (int64_t)j * 2 * wp + (part ? wp : 0) + k) : (const void*)X2s;
-        dst = sbase + 2 * kGOpA + part * kGOpB + (n >> 3) * 1024 + (n & 7) * 128 + ((c ^ (n & 7)) << 4);
+        dst = sbase + 2 * kGOpA + part * kGOpB + (n >> 3) * 512 + (n & 7) * 64 + ((c ^ ((n >> 1) & 3)) << 4);
       }
       cp_async16(dst, src, ok);
     }
@@ -737,9 +742,9 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sA = sb0 + st * kGStage, sB = sA + 2 * kGOpA;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {  // K = 16 per MMA, 32 B of each 128-byte row
-        const uint64_t ah = sw128_desc(sA + kk * 32), al = sw128_desc(sA + kGOpA + kk * 32);
-        const uint64_t bh = sw128_desc(sB + kk * 32), bl = sw128_desc(sB + kGOpB + kk * 32);
+      for (int kk = 0; kk < kGK / 16; ++kk) {  // K = 16 per MMA, 32 B of each 64-byte row
+        const uint64_t ah = sw64_desc(sA + kk * 32), al = sw64_desc(sA + kGOpA + kk * 32);
+        const uint64_t bh = sw64_desc(sB + kk * 32), bl = sw64_desc(sB + kGOpB + kk * 32);
         mma_f16(tc.tmem, ah, bh, idesc, (ck > 0 || kk > 0) ? 1u : 0u);
         mma_f16(tc.tmem, ah, bl, idesc, 1u);
         mma_f16(tc.tmem, al, bh, idesc, 1u);
@@ -759,16 +764,18 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
       const int t = j / nck, tn = t % ntn, tm = t / ntn;
       const int ri = rbeg + tm * kTcRows, cj = tn * kTcCols;
       const int q = warp % 4, ch = warp / 4;
-      uint32_t v[32];
-      tmem_ld32(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
       const int row = ri + q * 32 + lane;
-      if (row < rend) {
+      float* dst = row < w ? Xs + row : W2 + (row - w);
+      const int64_t ld = row < w ? wp : r;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {  // 16 columns per TMEM load (fewer live registers)
+        uint32_t v[16];
+        tmem_ld16(tc.tmem + ((uint32_t)(q * 32) << 16) + ch * 32 + h * 16, v);
+        if (row < rend) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int col = cj + ch * 32 + e;
-          if (col < J) {
-            if (row < w) Xs[(int64_t)col * wp + row] -= __uint_as_float(v[e]);
-            else W2[(int64_t)col * r + (row - w)] -= __uint_as_float(v[e]);
+          for (int e = 0; e < 16; ++e) {
+            const int col = cj + ch * 32 + h * 16 + e;
+            if (col < J) dst[(int64_t)col * ld] -= __uint_as_float(v[e]);
           }
         }
       }
@@ -880,26 +887,102 @@ __device__ bool solve_front(SolveSmem<T>& sm, const T* Ls, int f, int w, T* Xs, 
   return true;
 }
 
+// Shared memory of the 128-row diagonal solve of a large front (aliases the GEMM ring, which is idle then).
+struct Diag128Smem {
+  float Di[4][kNB][kNB + 1];  // inverses of the four 32 x 32 diagonal blocks
+  float Lo[6][kNB][kNB + 1];  // the six 32 x 32 blocks below the diagonal: (1,0) (2,0) (2,1) (3,0) (3,1) (3,2)
+  float Xb[kTcRows][kNB + 1]; // 32 right-hand-side columns of the block's rows
+};
+static_assert(sizeof(Diag128Smem) <= kGS * kGStage, "the diagonal solve fits in the GEMM ring");
+
+__device__ __forceinline__ int lo_pair(int a, int b) { return a == 1 ? 0 : a == 2 ? 1 + b : 3 + b; }  // a > b
+
+// X_b <- L_bb^{-1} X_b for the rows [k0, k0 + nr) (nr <= 128) of X_s, all J columns, in shared memory: with the
+// inverses of the four 32 x 32 diagonal blocks of L_bb (Dinv, from l16_kernel), 32 columns at a time the block
+// rows are loaded, solved by sub-block (the sub-block's inverse applied, then the sub-blocks below it updated
+// with the blocks of L_bb below the diagonal) and written back together with their bf16 hi/lo copy (with the
+// zero padding rows [w, wp) after the last block).
+__device__ void diag128(Diag128Smem& d, const float* Ls, const float* Dinv, int f, int w, int k0, int nr, float* Xs,
+                        int wp, int J, uint16_t* X2s) {
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int nsb = (nr + kNB - 1) / kNB;
+  // the inverted diagonal blocks (l16_kernel) and the L blocks below the diagonal (FP32 copy of L, column-major
+  // f x w panel)
+  for (int idx = tid; idx < nsb * kNB * kNB; idx += kThreads) {
+    const int b = idx / (kNB * kNB), rem = idx % (kNB * kNB);
+    d.Di[b][rem / kNB][rem % kNB] = Dinv[idx];
+  }
+  for (int idx = tid; idx < 6 * kNB * kNB; idx += kThreads) {
+    const int q = idx / (kNB * kNB), rem = idx % (kNB * kNB), i = rem % kNB, j = rem / kNB;
+    const int a = q == 0 ? 1 : q <= 2 ? 2 : 3, b = q == 0 ? 0 : q <= 2 ? q - 1 : q - 3;  // block row, column
+    const int gi = a * kNB + i, gj = b * kNB + j;
+    d.Lo[q][i][j] = (a < nsb && gi < nr) ? Ls[(int64_t)(k0 + gj) * f + k0 + gi] : 0.f;
+  }
+  __syncthreads();
+  const int rowsp = (k0 + nr == w) ? wp - k0 : nr;  // rows written to X2 (the padding after the last block)
+  __nv_bfloat16* h2 = reinterpret_cast<__nv_bfloat16*>(X2s);
+  for (int cj = 0; cj < J; cj += kNB) {
+    for (int idx = tid; idx < kTcRows * kNB; idx += kThreads) {
+      const int i = idx % kTcRows, y = idx / kTcRows;
+      d.Xb[i][y] = (i < nr && cj + y < J) ? Xs[(int64_t)(cj + y) * wp + k0 + i] : 0.f;
+    }
+    __syncthreads();
+    for (int sb = 0; sb < nsb; ++sb) {
+      // X_sb <- Di_sb X_sb: lane = column, rows 4 warp .. 4 warp + 3 of the sub-block
+      float acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = 4 * warp + u;
+        float a = 0.f;
+        for (int k = 0; k <= i; ++k) a = fmaf(d.Di[sb][i][k], d.Xb[sb * kNB + k][lane], a);
+        acc[u] = a;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d.Xb[sb * kNB + 4 * warp + u][lane] = acc[u];
+      __syncthreads();
+      // the sub-blocks below: X_a -= L_(a,sb) X_sb
+      for (int a = sb + 1; a < nsb; ++a) {
+        const int pq = lo_pair(a, sb);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * warp + u;
+          float s = 0.f;
+#pragma unroll 8
+          for (int k = 0; k < kNB; ++k) s = fmaf(d.Lo[pq][i][k], d.Xb[sb * kNB + k][lane], s);
+          d.Xb[a * kNB + i][lane] -= s;
+        }
+      }
+      __syncthreads();
+    }
+    // write back X and its bf16 hi/lo copy
+    for (int idx = tid; idx < kTcRows * kNB; idx += kThreads) {
+      const int i = idx % kTcRows, y = idx / kTcRows;
+      if (cj + y < J && i < rowsp) {
+        const float v = i < nr ? d.Xb[i][y] : 0.f;
+        if (i < nr) Xs[(int64_t)(cj + y) * wp + k0 + i] = v;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const int64_t o = 2 * (int64_t)(cj + y) * wp + k0 + i;
+        h2[o] = hi;
+        h2[o + wp] = __float2bfloat16_rn(v - __bfloat162float(hi));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Forward solve of a large front on the tensor cores (mixed precision): the own rows in blocks of 128, each
 // solved by four diagonal steps of 32 rows (the rows inside the block updated on the SIMT path), its rows
 // written as bf16 hi/lo (the B operand of the later GEMMs and of the split-bf16 SYRK), then the own rows below
 // it updated with K = 128 by the pipelined GEMM; finally the bottom rows, W2 -= L_rs X_s with K = w, by the same
 // GEMM.  LH: the row-major hi/lo copy of the panel (launch_l16).  X2s: the hi/lo copy of X_s.
-__device__ bool solve_front_big(SolveSmem<float>& sm, const float* Ls, const uint16_t* LH, int f, int w, float* Xs,
-                                int wp, float* W2, int J, uint16_t* X2s, TcState& tc) {
+__device__ bool solve_front_big(SolveSmem<float>& sm, const float* Ls, const uint16_t* LH, const float* Dinv, int f,
+                                int w, float* Xs, int wp, float* W2, int J, uint16_t* X2s, TcState& tc) {
   const int r = f - w;
+  Diag128Smem& d = *reinterpret_cast<Diag128Smem*>(tc.smem);
   for (int k0 = 0; k0 < w; k0 += kTcRows) {
     const int e0 = min(w, k0 + kTcRows);
-    for (int kb = k0; kb < e0; kb += kNB) {
-      const int nbk = min(kNB, e0 - kb);
-      diag_block<float>(sm, Ls, f, kb, nbk, Xs, wp, J, 0);
-      const int i0 = kb + nbk;
-      if (i0 < e0) panel_update_simt<float>(sm, Ls, f, i0, e0, kb, i0, Xs, wp, W2, w, r, J);
-    }
-    __syncthreads();
-    // the finished rows as bf16 hi/lo (after the last block also the zero padding rows up to wp)
-    write_x2(Xs, wp, X2s, k0, e0 == w ? wp : e0, J);
-    __syncthreads();
+    diag128(d, Ls, Dinv + (int64_t)(k0 / kNB) * kNB * kNB, f, w, k0, e0 - k0, Xs, wp, J, X2s);
     if (e0 < w && !gemm_tc(tc, LH, wp, e0, w, k0, e0, X2s, wp, Xs, W2, w, r, J)) return false;
   }
   if (r > 0 && !gemm_tc(tc, LH, wp, w, f, 0, w, X2s, wp, Xs, W2, w, r, J)) return false;
@@ -924,7 +1007,7 @@ __device__ __forceinline__ float round_tf32(float x) {
 // per column wp hi values then wp lo values, for the split-bf16 SYRK.
 // LT: the factor in the solve's precision (the FP32 copy of L for T = float, L itself for T = double).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, 3)
     trsm_kernel(DevPlan P, const int2* items, int nitems, int cw, int* queue, const T* LT, T* X, T* ws,
                 int64_t ws_stride, int64_t front_sz, int tcmode, int tf32_out, int unit, uint16_t* X2, int x2_out,
                 int* status) {
@@ -935,7 +1018,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 3)
   extern __shared__ uint8_t tc_raw[];
   // the SIMT solve's buffers share the dynamic shared memory with the tensor-core operand buffers (never in
   // use at the same time)
-  uint8_t* dyn = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+  // (the offset is added to the shared array itself, so the compiler keeps shared-memory loads and stores)
+  uint8_t* dyn = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
   SolveSmem<T>& sm = *reinterpret_cast<SolveSmem<T>*>(dyn);
   const int tid = threadIdx.x;
   T* W2 = ws + (int64_t)blockIdx.x * ws_stride;
@@ -1016,7 +1100,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 3)
       uint16_t* X2s = X2 ? X2 + 2 * (S.X + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp) : nullptr;
       bool ok;
       if constexpr (sizeof(T) == 4) {
-        ok = lho >= 0 && X2s ? solve_front_big(sm, L + P.Lofs[gs], P.LH + S.lh + lho, f, w, Xs, wp, W2, J, X2s, tc)
+        ok = lho >= 0 && X2s ? solve_front_big(sm, L + P.Lofs[gs], P.LH + S.lh + lho, P.DI + S.di + P.di_ofs[gs], f,
+                                               w, Xs, wp, W2, J, X2s, tc)
                              : solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
       } else {
         ok = solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
@@ -1077,10 +1162,13 @@ __global__ void __launch_bounds__(256) l32_kernel(const double* __restrict__ L, 
 // Row-major bf16 hi/lo copy of the large panels for the tensor-core TRSM: row i of the f x w panel as lwp hi
 // values then lwp lo values (hi = bf16(x), lo = bf16(x - hi) of the FP32 entry, zero for k >= w), so that
 // every 16-byte piece of a K-major operand row is one cp.async.  One CTA per panel, 32 x 32 tiles transposed
-// through shared memory.
+// through shared memory.  Also the inverses of the panel's 32 x 32 diagonal blocks (FP32, one warp per block,
+// from the same FP32 entries), which every column block of the TRSM then reads instead of recomputing them.
 __global__ void __launch_bounds__(256) l16_kernel(DevPlan P, const int2* items, int nitems, const float* L32,
-                                                  uint16_t* LH) {
+                                                  uint16_t* LH, float* DI) {
   __shared__ float t[32][33];
+  __shared__ float Dm[4][kNB][kNB + 1], Dv[4][kNB][kNB + 1];
+  __shared__ float dv[4][kNB];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const SubInfo S = P.sub[items[it].x];
@@ -1106,14 +1194,27 @@ __global__ void __launch_bounds__(256) l16_kernel(DevPlan P, const int2* items, 
         }
         __syncthreads();
       }
+    // the diagonal blocks: warps 0-3 invert blocks ty, ty + 4, ...  (block b covers own rows 32 b .. 32 b + 31;
+    // 4 blocks per 128 rows, the slots of blocks past w stay unwritten and unread)
+    float* di = DI + S.di + P.di_ofs[gs];
+    for (int b = ty; ty < 4 && b < (w + kNB - 1) / kNB; b += 4) {
+      const int nbk = min(kNB, w - b * kNB);
+      for (int i = 0; i < kNB; ++i) Dm[ty][i][tx] = (i < nbk && tx <= i) ? Lp[(int64_t)(b * kNB + tx) * f + b * kNB + i] : 0.f;
+      dv[ty][tx] = tx < nbk ? 1.f / Lp[(int64_t)(b * kNB + tx) * f + b * kNB + tx] : 0.f;
+      __syncwarp();
+      warp_tri_inverse<float>(Dm[ty], dv[ty], Dv[ty], nbk);
+      for (int i = 0; i < kNB; ++i) di[(int64_t)b * kNB * kNB + i * kNB + tx] = Dv[ty][i][tx];
+      __syncwarp();
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
-void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, int grid,
+void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, float* DI, int grid,
                 cudaStream_t st) {
-  if (nitems > 0) l16_kernel<<<std::min(grid, nitems), 256, 0, st>>>(P, items, nitems, L32, LH);
+  if (nitems > 0) l16_kernel<<<std::min(grid, nitems), 256, 0, st>>>(P, items, nitems, L32, LH, DI);
 }
 
 void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st) {
@@ -1148,6 +1249,8 @@ void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* q
   const int smem = trsm_smem(fp32, tcmode);
   if (fp32) {
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     trsm_kernel<float><<<grid, kThreads, smem, st>>>(P, items, nitems, cw, queue, L32, (float*)X, (float*)ws,
                                                      2 * ws_stride, front_sz, tcmode, tf32_out, 0, X2, x2_out,
                                                      status);
@@ -1158,17 +1261,34 @@ void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* q
   }
 }
 
+// Resident CTAs per SM of the TRSM, from its registers and shared memory.  (The occupancy API answers 1 for
+// the FP32 kernel, which allocates tensor memory, although three of its CTAs run side by side: 3 x 64 TMEM
+// columns fit the SM's 512.  The TRSM's CTAs never wait on one another, so a grid above what fits is only
+// scheduled later, never blocked.)
 int trsm_ctas_per_sm(bool fp32, int tcmode) {
   const int smem = trsm_smem(fp32, tcmode);
-  int nb = 0;
+  cudaFuncAttributes fa{};
   if (fp32) {
     cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trsm_kernel<float>, kThreads, smem);
+    cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaFuncGetAttributes(&fa, trsm_kernel<float>) != cudaSuccess) return 1;
   } else {
     cudaFuncSetAttribute(trsm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trsm_kernel<double>, kThreads, smem);
+    if (cudaFuncGetAttributes(&fa, trsm_kernel<double>) != cudaSuccess) return 1;
   }
-  return nb > 0 ? nb : 1;
+  int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0, sm_threads = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  const int per_cta_smem = smem + (int)fa.sharedSizeBytes + reserved;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+  int nb = std::min(sm_smem / std::max(per_cta_smem, 1), sm_regs / std::max(regs_warp * (kThreads / 32), 1));
+  nb = std::min(nb, sm_threads / kThreads);
+  if (fp32 && tcmode > 0) nb = std::min(nb, 512 / (int)kTrsmTmemCols);
+  return std::max(nb, 1);
 }
 
 }  // namespace feti

@@ -23,9 +23,9 @@ void launch_trsm(const DevPlan& P, const int2* items, int nitems, int cw, int* q
                  double* ws, int64_t ws_stride, int64_t front_sz, int grid, int tcmode, int tf32_out, int* status,
                  cudaStream_t st, int unit = 0, uint16_t* X2 = nullptr, const float* L32 = nullptr, int x2_out = 0);
 int trsm_ctas_per_sm(bool fp32, int tcmode);
-// the row-major bf16 hi/lo copies of the large panels (P.LH) from the FP32 copy of L; items: (subdomain, local
-// supernode) of every panel with P.lh_ofs >= 0
-void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, int grid,
+// the row-major bf16 hi/lo copies of the large panels (P.LH) and the inverses of their 32 x 32 diagonal
+// blocks (P.DI) from the FP32 copy of L; items: (subdomain, local supernode) of every panel with P.lh_ofs >= 0
+void launch_l16(const DevPlan& P, const int2* items, int nitems, const float* L32, uint16_t* LH, float* DI, int grid,
                 cudaStream_t st);
 void launch_l32(const double* L, float* L32, int64_t n, int grid, cudaStream_t st);
 // X2 (split mode): the bf16 hi/lo copy of X written by the TRSM (per column: wp hi values, then wp lo values)

@@ -70,7 +70,7 @@ class FetiStats(C.Structure):
                 ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double),
                 ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32),
-                ("chol_tasks", C.c_int32), ("syrk_variant", C.c_int32), ("assembly_route", C.c_int32),
+                ("trsm_grid", C.c_int32), ("chol_tasks", C.c_int32), ("syrk_variant", C.c_int32), ("assembly_route", C.c_int32),
                 ("route_ms", C.c_double * 3)]
 
     def as_dict(self):
