@@ -139,7 +139,11 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
       int i = idx % nbk, j = idx / nbk;
       if (i >= j) Ls[(int64_t)(kb + j) * f + kb + i] = sm.D[i][j];
     }
-    // panel: rows below the block solve x L_bb^T = a, one thread per row, 64 rows at a time
+    // panel: the rows below the block solve x L_bb^T = a, i.e. x = L_bb^{-1} a per row, with L_bb^{-1} formed
+    // once by warp 0: 64 rows at a time, each row's 32 outputs split over four threads (8 each), so that all
+    // threads work and no thread runs a dependent substitution chain
+    auto Di = reinterpret_cast<double (*)[kNB + 1]>(&sm.B[0][0]);
+    if (warp == 0) warp_tri_inverse<double>(sm.D, sm.dinv, Di, nbk);
     const int i0 = kb + nbk;
     for (int ri = i0; ri < f; ri += kT) {
       for (int idx = tid; idx < nbk * kT; idx += kThreads) {
@@ -147,13 +151,18 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
         sm.A[k][xx] = (ri + xx < f) ? Ls[(int64_t)(kb + k) * f + ri + xx] : 0.0;
       }
       __syncthreads();
-      if (tid < kT && ri + tid < f) {
-        for (int k = 0; k < nbk; ++k) {
-          double s = sm.A[k][tid];
-          for (int l = 0; l < k; ++l) s = fma(-sm.D[k][l], sm.A[l][tid], s);
-          s *= sm.dinv[k];
-          sm.A[k][tid] = s;
-          Ls[(int64_t)(kb + k) * f + ri + tid] = s;
+      {
+        const int xx = tid % kT, jg = tid / kT;
+        if (ri + xx < f && jg * 8 < nbk) {
+          double acc[8] = {};
+          for (int k = 0; k <= min(nbk - 1, jg * 8 + 7); ++k) {
+            const double a = sm.A[k][xx];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = fma(Di[jg * 8 + jj][k], a, acc[jj]);
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            if (jg * 8 + jj < nbk) Ls[(int64_t)(kb + jg * 8 + jj) * f + ri + xx] = acc[jj];
         }
       }
       __syncthreads();
@@ -442,13 +451,30 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
         const double* U = child_update(P, gc, stack, smallreg, hand);
         const int* rl = P.rel + P.rel_off[gc];
         __syncthreads();
-        for (int64_t idx = tid; idx < (int64_t)rc * rc; idx += kThreads) {
-          int a = (int)(idx % rc), b = (int)(idx / rc);
-          if (a < b) continue;
-          int ra = rl[a], rb = rl[b];
-          double v = __ldcg(U + idx);
-          if (rb < w) Ls[(int64_t)rb * f + ra] += v;
-          else W[(int64_t)(rb - w) * r + (ra - w)] += v;
+        // four elements per thread and step, their loads issued before their read-modify-writes (distinct
+        // targets: rel is one-to-one)
+        const int64_t n = (int64_t)rc * rc;
+        for (int64_t base = tid; base < n; base += 4 * kThreads) {
+          double* dst[4];
+          double v[4], cur[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t idx = base + (int64_t)u * kThreads;
+            dst[u] = nullptr;
+            if (idx < n) {
+              const int b = (int)(idx / rc), a = (int)(idx - (int64_t)b * rc);
+              if (a >= b) {
+                const int ra = rl[a], rb = rl[b];
+                v[u] = __ldcg(U + idx);
+                dst[u] = rb < w ? Ls + (int64_t)rb * f + ra : W + (int64_t)(rb - w) * r + (ra - w);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cur[u] = dst[u] ? *dst[u] : 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (dst[u]) *dst[u] = cur[u] + v[u];
         }
       }
       __syncthreads();
@@ -680,9 +706,11 @@ __device__ void panel_update_simt(SolveSmem<T>& sm, const T* Ls, int f, int rbeg
 // (one swizzled 64-byte row per operand row): all threads stage chunks by cp.async into the kGS-stage ring,
 // running ahead across tile boundaries, one thread issues each chunk's MMAs and commits them to its stage's
 // mbarrier (which frees the stage), and after a tile's last chunk the CTA subtracts the accumulator from C
-// (rows below w: the own rows of X_s; the others: W2).  Every wait is bounded.
+// (rows below w: the own rows of X_s; the others: W2, or with W2out, W2out = W2 - accumulator, the parent's
+// update block written in place).  Every wait is bounded.
 __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int rend, int kbeg, int kend,
-                        const uint16_t* X2s, int wp, float* Xs, float* W2, int w, int r, int J) {
+                        const uint16_t* X2s, int wp, float* Xs, float* W2, int w, int r, int J,
+                        float* W2out = nullptr) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntm = (rend - rbeg + kTcRows - 1) / kTcRows, ntn = (J + kTcCols - 1) / kTcCols;
   const int nck = (kend - kbeg + kGK - 1) / kGK;
@@ -765,7 +793,8 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
       const int ri = rbeg + tm * kTcRows, cj = tn * kTcCols;
       const int q = warp % 4, ch = warp / 4;
       const int row = ri + q * 32 + lane;
-      float* dst = row < w ? Xs + row : W2 + (row - w);
+      const float* src = row < w ? Xs + row : W2 + (row - w);
+      float* dst = row < w ? Xs + row : (W2out ? W2out : W2) + (row - w);
       const int64_t ld = row < w ? wp : r;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {  // 16 columns per TMEM load (fewer live registers)
@@ -775,7 +804,7 @@ __device__ bool gemm_tc(TcState& tc, const uint16_t* LH, int lwp, int rbeg, int 
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int col = cj + ch * 32 + h * 16 + e;
-            if (col < J) dst[(int64_t)col * ld] -= __uint_as_float(v[e]);
+            if (col < J) dst[(int64_t)col * ld] = src[(int64_t)col * ld] - __uint_as_float(v[e]);
           }
         }
       }
@@ -901,9 +930,10 @@ __device__ __forceinline__ int lo_pair(int a, int b) { return a == 1 ? 0 : a == 
 // inverses of the four 32 x 32 diagonal blocks of L_bb (Dinv, from l16_kernel), 32 columns at a time the block
 // rows are loaded, solved by sub-block (the sub-block's inverse applied, then the sub-blocks below it updated
 // with the blocks of L_bb below the diagonal) and written back together with their bf16 hi/lo copy (with the
-// zero padding rows [w, wp) after the last block).
+// zero padding rows [w, wp) after the last block).  keep_x = false: the solved rows go to the hi/lo copy only
+// (nothing reads their FP32 values afterwards when the SYRK takes the hi/lo copy).
 __device__ void diag128(Diag128Smem& d, const float* Ls, const float* Dinv, int f, int w, int k0, int nr, float* Xs,
-                        int wp, int J, uint16_t* X2s) {
+                        int wp, int J, uint16_t* X2s, bool keep_x) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nsb = (nr + kNB - 1) / kNB;
   // the inverted diagonal blocks (l16_kernel) and the L blocks below the diagonal (FP32 copy of L, column-major
@@ -960,7 +990,7 @@ __device__ void diag128(Diag128Smem& d, const float* Ls, const float* Dinv, int 
       const int i = idx % kTcRows, y = idx / kTcRows;
       if (cj + y < J && i < rowsp) {
         const float v = i < nr ? d.Xb[i][y] : 0.f;
-        if (i < nr) Xs[(int64_t)(cj + y) * wp + k0 + i] = v;
+        if (keep_x && i < nr) Xs[(int64_t)(cj + y) * wp + k0 + i] = v;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const int64_t o = 2 * (int64_t)(cj + y) * wp + k0 + i;
         h2[o] = hi;
@@ -977,15 +1007,16 @@ __device__ void diag128(Diag128Smem& d, const float* Ls, const float* Dinv, int 
 // it updated with K = 128 by the pipelined GEMM; finally the bottom rows, W2 -= L_rs X_s with K = w, by the same
 // GEMM.  LH: the row-major hi/lo copy of the panel (launch_l16).  X2s: the hi/lo copy of X_s.
 __device__ bool solve_front_big(SolveSmem<float>& sm, const float* Ls, const uint16_t* LH, const float* Dinv, int f,
-                                int w, float* Xs, int wp, float* W2, int J, uint16_t* X2s, TcState& tc) {
+                                int w, float* Xs, int wp, float* W2, int J, uint16_t* X2s, TcState& tc, bool keep_x,
+                                float* Uout) {
   const int r = f - w;
   Diag128Smem& d = *reinterpret_cast<Diag128Smem*>(tc.smem);
   for (int k0 = 0; k0 < w; k0 += kTcRows) {
     const int e0 = min(w, k0 + kTcRows);
-    diag128(d, Ls, Dinv + (int64_t)(k0 / kNB) * kNB * kNB, f, w, k0, e0 - k0, Xs, wp, J, X2s);
+    diag128(d, Ls, Dinv + (int64_t)(k0 / kNB) * kNB * kNB, f, w, k0, e0 - k0, Xs, wp, J, X2s, keep_x);
     if (e0 < w && !gemm_tc(tc, LH, wp, e0, w, k0, e0, X2s, wp, Xs, W2, w, r, J)) return false;
   }
-  if (r > 0 && !gemm_tc(tc, LH, wp, w, f, 0, w, X2s, wp, Xs, W2, w, r, J)) return false;
+  if (r > 0 && !gemm_tc(tc, LH, wp, w, f, 0, w, X2s, wp, Xs, W2, w, r, J, Uout)) return false;
   return true;
 }
 
@@ -1085,13 +1116,28 @@ __global__ void __launch_bounds__(kThreads, 3)
         const int rc = P.sn_r[gc], coff = jbc - jb;
         const T* U = stack + P.rhs_ofs[bc];
         const int* rl = P.rel + P.rel_off[gc];
-        // children own disjoint column ranges: no conflicts between them
-        for (int64_t idx = tid; idx < (int64_t)rc * Jc; idx += kThreads) {
-          int col = (int)(idx / rc), a2 = (int)(idx % rc);
-          int ra = rl[a2];
-          T v = U[idx];
-          if (ra < w) Xs[(int64_t)(coff + col) * wp + ra] += v;
-          else W2[(int64_t)(coff + col) * r + (ra - w)] += v;
+        // children own disjoint column ranges: no conflicts between them.  Four elements per thread and step,
+        // their loads issued before their read-modify-writes (the targets are distinct: rel is one-to-one)
+        const int64_t n = (int64_t)rc * Jc;
+        for (int64_t base = tid; base < n; base += 4 * kThreads) {
+          T* dst[4];
+          T v[4], cur[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t idx = base + (int64_t)u * kThreads;
+            dst[u] = nullptr;
+            if (idx < n) {
+              const int col = (int)(idx / rc), a2 = (int)(idx - (int64_t)col * rc);
+              const int ra = rl[a2];
+              v[u] = U[idx];
+              dst[u] = ra < w ? Xs + (int64_t)(coff + col) * wp + ra : W2 + (int64_t)(coff + col) * r + (ra - w);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cur[u] = dst[u] ? *dst[u] : (T)0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (dst[u]) *dst[u] = cur[u] + v[u];
         }
       }
       __syncthreads();
@@ -1100,8 +1146,11 @@ __global__ void __launch_bounds__(kThreads, 3)
       uint16_t* X2s = X2 ? X2 + 2 * (S.X + P.Xofs[bs] + (int64_t)(jb - P.jb[bs]) * wp) : nullptr;
       bool ok;
       if constexpr (sizeof(T) == 4) {
+        // the parent's update block is written by the bottom GEMM's epilogue (after the children's blocks on the
+        // stack, which it may overwrite, have been read)
         ok = lho >= 0 && X2s ? solve_front_big(sm, L + P.Lofs[gs], P.LH + S.lh + lho, P.DI + S.di + P.di_ofs[gs], f,
-                                               w, Xs, wp, W2, J, X2s, tc)
+                                               w, Xs, wp, W2, J, X2s, tc, !x2_out,
+                                               P.sn_parent[gs] >= 0 ? stack + P.rhs_ofs[bs] : nullptr)
                              : solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
       } else {
         ok = solve_front<T>(sm, L + P.Lofs[gs], f, w, Xs, wp, W2, J, &tc, tcmode, unit);
@@ -1124,7 +1173,7 @@ __global__ void __launch_bounds__(kThreads, 3)
           }
         }
       }
-      if (P.sn_parent[gs] >= 0) {
+      if (P.sn_parent[gs] >= 0 && !(lho >= 0 && X2s && r > 0)) {
         T* dst = stack + P.rhs_ofs[bs];
         for (int64_t idx = tid; idx < (int64_t)r * J; idx += kThreads) dst[idx] = W2[idx];
       }
