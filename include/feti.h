@@ -126,6 +126,8 @@ typedef struct {
                                  subtrees of the supernodal tree factored by CTAs of their own, a parent
                                  task after its children), so that large subdomains spread over several
                                  SMs.  The factor is the same bit for bit either way */
+  int32_t syrk_kernel;        /* split-bf16 SYRK kernel: 0 = autotuned at the first feti_assemble; 1, 2, 3 =
+                                 feti_stats.syrk_variant 0, 1, 2 (the same F bit for bit) */
 } feti_options;
 
 typedef struct {
@@ -164,7 +166,8 @@ typedef struct {
   int32_t chol_tasks;         /* Cholesky work items the autotuner kept: the subdomains, or the tasks of the
                                  subtree split when that was faster */
   int32_t syrk_variant;       /* split-bf16 SYRK kernel picked by the autotuner (0: all threads load, one issues;
-                                 1: warp-specialised producers / issuer / epilogue) */
+                                 1: warp-specialised producers / issuer / epilogue; 2: as 0 with 32-deep chunks
+                                 and two CTAs per SM) */
   int32_t assembly_route;     /* route of the last feti_assemble (0 SYRK path, 1 Schur complement, 2 TRSM path) */
   double route_ms[3];         /* route 3: time of the TRSM + SYRK (0) and of the TRSM path (2) at the first call */
 } feti_stats;

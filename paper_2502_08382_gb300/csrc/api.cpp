@@ -825,6 +825,12 @@ void build(feti_ctx* c) {
     if (c->opt.chol_split < 0 || c->opt.chol_split > 2) throw ArgError("bad chol_split (0 auto, 1 whole, 2 tasks)");
     c->chol_pick = c->opt.chol_split == 2 ? 1 : 0;
     c->chol_tuned = c->opt.chol_split != 0 || (int)split.size() == ns;
+    if (c->opt.syrk_kernel < 0 || c->opt.syrk_kernel > 3) throw ArgError("bad syrk_kernel (0 auto, 1-3 a kernel)");
+    if (c->opt.syrk_kernel > 0) {
+      c->syrk_variant = c->opt.syrk_kernel - 1;
+      c->syrk_tuned = true;
+      c->stats.syrk_variant = c->syrk_variant;
+    }
   }
   c->d_trsm_order = upload(c, order_t);
   {
@@ -1077,25 +1083,28 @@ feti_status feti_assemble(feti_ctx* ctx) {
     if (ctx->fp32) {
       auto run_syrk = [&](int variant) {
         launch_syrk_tc(ctx->P, ctx->d_syrk2_items, ctx->nsyrk2, (const float*)ctx->d_X, ctx->d_X2, (float*)ctx->d_F,
-                       std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split ? 1 : 2))), split ? 1 : 0, ctx->d_status,
-                       s2, variant);
+                       std::max(1, std::min(ctx->nsyrk2, ctx->nsm * (split && variant != 2 ? 1 : 2))), split ? 1 : 0,
+                       ctx->d_status, s2, variant);
       };
       if (split && !ctx->syrk_tuned) {
-        // autotuner: the two split-bf16 SYRK kernels on this problem (the same F bitwise), the faster kept
-        float ms[2] = {0, 0};
-        for (int v = 0; v < 2; ++v) {
+        // autotuner: the three split-bf16 SYRK kernels on this problem (the same F bitwise), the fastest kept
+        float ms[3] = {0, 0, 0};
+        for (int v = 0; v < 3; ++v) {
           CK(cudaEventRecord(ctx->ev[5], s2));
           run_syrk(v);
           CK(cudaEventRecord(ctx->ev[6], s2));
           CK(cudaEventSynchronize(ctx->ev[6]));
           CK(cudaEventElapsedTime(&ms[v], ctx->ev[5], ctx->ev[6]));
         }
-        ctx->syrk_variant = ms[1] < ms[0] ? 1 : 0;
+        ctx->syrk_variant = 0;
+        for (int v = 1; v < 3; ++v)
+          if (ms[v] < ms[ctx->syrk_variant]) ctx->syrk_variant = v;
         ctx->syrk_tuned = true;
         ctx->stats.syrk_variant = ctx->syrk_variant;
         CK(cudaEventRecord(ctx->ev[2], s2));
       }
       run_syrk(ctx->syrk_variant);
+      ctx->stats.syrk_variant = ctx->syrk_variant;
     } else {
       launch_syrk_f64(ctx->P, ctx->d_syrk_items, ctx->nsyrk, (const double*)ctx->d_X, (double*)ctx->d_F,
                       std::min(ctx->nsyrk, ctx->nsm * 8), s2);

@@ -56,11 +56,15 @@ struct Cursor {
 // bytes of one operand buffer (128 rows x 128 B)
 constexpr int kOpBytes = kM * 128;
 
+// SPLIT: 0 = TF32; 1 = split bf16, 64-deep chunks in the 128-byte swizzle (one CTA per SM); 2 = split bf16,
+// 32-deep chunks in the 64-byte swizzle (half the stage, two CTAs per SM; the same MMAs in the same order)
 template <int SPLIT>
 struct Cfg {
-  static constexpr int kKC = SPLIT ? 64 : 32;            // K values per chunk (one swizzled row)
+  static constexpr int kKC = SPLIT == 1 ? 64 : 32;       // K values per chunk (one swizzled row)
   static constexpr int kOps = SPLIT ? 4 : 2;             // A(hi,lo), B(hi,lo) or A, B
-  static constexpr int kStageBytes = kOps * kOpBytes;
+  static constexpr int kRowBytes = SPLIT == 2 ? 64 : 128;
+  static constexpr int kOp = kM * kRowBytes;             // bytes of one operand part
+  static constexpr int kStageBytes = kOps * kOp;
 };
 
 // Stage the chunk (supernode s, rows k0..k0+KC) of the A rows (tile block BI)
@@ -85,7 +89,7 @@ __device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, cons
       const uint32_t dst = (op ? sB : sA) + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
       cp_async16(dst, src, ok);
     }
-  } else {
+  } else if constexpr (SPLIT == 1) {
     // parts: 0 A hi, 1 A lo, 2 B hi, 3 B lo; 64 K values (8 chunks of 8 bf16) per 128-byte row
     const uint32_t s0 = smem_u32(stage);
     const int nparts = diag ? 2 : 4;
@@ -99,11 +103,25 @@ __device__ __forceinline__ void load_chunk(uint8_t* stage, const float* Xs, cons
       const uint32_t dst = s0 + part * kOpBytes + (m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4);
       cp_async16(dst, src, ok);
     }
+  } else {
+    // the same parts with 32 K values (4 chunks of 8 bf16) per 64-byte row, 64-byte swizzle
+    const uint32_t s0 = smem_u32(stage);
+    const int nparts = diag ? 2 : 4;
+    for (int idx = tid; idx < nparts * kM * 4; idx += kTcThreads) {
+      const int part = idx / (kM * 4), rem = idx % (kM * 4);
+      const int m = rem / 4, c = rem % 4;
+      const int x = (part < 2 ? ca : cb) + m;
+      const int k = k0 + 8 * c;
+      const bool ok = x >= 0 && x < J && k < w;
+      const void* src = ok ? (const void*)(X2s + 2 * (int64_t)x * wp + ((part & 1) ? wp : 0) + k) : safe;
+      const uint32_t dst = s0 + part * Cfg<2>::kOp + (m >> 3) * 512 + (m & 7) * 64 + ((c ^ ((m >> 1) & 3)) << 4);
+      cp_async16(dst, src, ok);
+    }
   }
 }
 
 template <int SPLIT>
-__global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const int2* items, int nitems,
+__global__ void __launch_bounds__(kTcThreads, SPLIT == 2 ? 2 : 1) syrk_tc_kernel(DevPlan P, const int2* items, int nitems,
                                                                 const float* X, const uint16_t* X2, float* F,
                                                                 int* status) {
   using C = Cfg<SPLIT>;
@@ -131,6 +149,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = idesc_mn128(SPLIT ? 1u : 2u);
+  constexpr int kOpB = Cfg<SPLIT>::kOp;
   uint32_t g0 = 0;  // chunks issued by this CTA so far (stage = g % kStages)
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -204,11 +223,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) syrk_tc_kernel(DevPlan P, const
             }
           } else {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < C::kKC / 16; ++kk) {
               const uint32_t o = kk * 32;
-              const uint64_t ah = sw128_desc(sbase + o), al = sw128_desc(sbase + kOpBytes + o);
-              const uint64_t bh = diag ? ah : sw128_desc(sbase + 2 * kOpBytes + o);
-              const uint64_t bl = diag ? al : sw128_desc(sbase + 3 * kOpBytes + o);
+              auto dsc = [](uint32_t a) { return SPLIT == 2 ? sw64_desc(a) : sw128_desc(a); };
+              const uint64_t ah = dsc(sbase + o), al = dsc(sbase + kOpB + o);
+              const uint64_t bh = diag ? ah : dsc(sbase + 2 * kOpB + o);
+              const uint64_t bl = diag ? al : dsc(sbase + 3 * kOpB + o);
               mma_f16(tmem, ah, bh, idesc, (j > 0 || kk > 0) ? 1u : 0u);
               mma_f16(tmem, ah, bl, idesc, 1u);
               mma_f16(tmem, al, bh, idesc, 1u);
@@ -535,13 +555,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) syrk_ws_kernel(DevPlan P, const
 }  // namespace
 
 size_t syrk_tc_smem(int split) {
-  return (size_t)kStages * (split ? Cfg<1>::kStageBytes : Cfg<0>::kStageBytes) + 1024;
+  return (size_t)kStages * (split == 2 ? Cfg<2>::kStageBytes : split ? Cfg<1>::kStageBytes : Cfg<0>::kStageBytes) +
+         1024;
 }
 
 void launch_syrk_tc(const DevPlan& P, const int2* items, int nitems, const float* X, const uint16_t* X2, float* F,
                     int grid, int split, int* status, cudaStream_t st, int variant) {
-  size_t smem = syrk_tc_smem(split);
-  if (split && variant == 1) {
+  size_t smem = syrk_tc_smem(split && variant == 2 ? 2 : split);
+  if (split && variant == 2) {
+    cudaFuncSetAttribute(syrk_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    syrk_tc_kernel<2><<<grid, kTcThreads, smem, st>>>(P, items, nitems, X, X2, F, status);
+  } else if (split && variant == 1) {
     const int ws_smem = kWsStages * kWsStageBytes + 1024;
     cudaFuncSetAttribute(syrk_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ws_smem);
     syrk_ws_kernel<<<grid, kWsThreads, ws_smem, st>>>(P, items, nitems, X2, F, status);
