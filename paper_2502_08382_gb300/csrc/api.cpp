@@ -1056,7 +1056,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
     if (ctx->fp32) {
       // the mixed TRSM reads an FP32 copy of the factor, and its large fronts a row-major bf16 hi/lo copy
       launch_l32(ctx->P.L, ctx->d_L32, ctx->stats.L_doubles, ctx->nsm * 8, s2);
-      launch_l16(ctx->P, ctx->d_l16_items, ctx->n_l16, ctx->d_L32, ctx->P.LH, ctx->P.DI, ctx->nsm * 4, s2);
+      launch_l16(ctx->P, ctx->d_l16_items, ctx->n_l16, ctx->d_L32, ctx->P.LH, ctx->P.DI, ctx->nsm * 6, s2);
     }
     if (!ctx->trsm_tuned) {
       // autotuner: time every work split of the TRSM on this problem (X is the same bitwise for all)

@@ -1210,52 +1210,60 @@ __global__ void __launch_bounds__(256) l32_kernel(const double* __restrict__ L, 
 
 // Row-major bf16 hi/lo copy of the large panels for the tensor-core TRSM: row i of the f x w panel as lwp hi
 // values then lwp lo values (hi = bf16(x), lo = bf16(x - hi) of the FP32 entry, zero for k >= w), so that
-// every 16-byte piece of a K-major operand row is one cp.async.  One CTA per panel, 32 x 32 tiles transposed
-// through shared memory.  Also the inverses of the panel's 32 x 32 diagonal blocks (FP32, one warp per block,
-// from the same FP32 entries), which every column block of the TRSM then reads instead of recomputing them.
+// every 16-byte piece of a K-major operand row is one cp.async.  Each warp transposes 32 x 32 tiles of a
+// panel on its own (no CTA-wide barrier: the eight warps of a CTA keep eight tiles in flight).  Also the
+// inverses of the panel's 32 x 32 diagonal blocks (FP32, one warp per block, from the same FP32 entries), which
+// every column block of the TRSM then reads instead of recomputing them.
 __global__ void __launch_bounds__(256) l16_kernel(DevPlan P, const int2* items, int nitems, const float* L32,
                                                   uint16_t* LH, float* DI) {
-  __shared__ float t[32][33];
-  __shared__ float Dm[4][kNB][kNB + 1], Dv[4][kNB][kNB + 1];
+  __shared__ float t[8][32][33];
   __shared__ float dv[4][kNB];
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32, wq = threadIdx.x / 32;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const SubInfo S = P.sub[items[it].x];
     const int gs = S.sn0 + items[it].y;
     const int w = P.sn_w[gs], f = w + P.sn_r[gs], lwp = (w + 7) & ~7;
     const float* Lp = L32 + S.L + P.Lofs[gs];
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(LH + S.lh + P.lh_ofs[gs]);
-    for (int i0 = 0; i0 < f; i0 += 32)
-      for (int k0 = 0; k0 < lwp; k0 += 32) {
-        for (int kk = ty; kk < 32; kk += 8) {
-          const int k = k0 + kk, i = i0 + tx;
-          t[kk][tx] = (i < f && k < w) ? Lp[(int64_t)k * f + i] : 0.f;
-        }
-        __syncthreads();
-        for (int ii = ty; ii < 32; ii += 8) {
-          const int i = i0 + ii, k = k0 + tx;
-          if (i < f && k < lwp) {
-            const float v = t[tx][ii];
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            out[(int64_t)i * 2 * lwp + k] = hi;
-            out[(int64_t)i * 2 * lwp + lwp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-          }
-        }
-        __syncthreads();
+    const int nti = (f + 31) / 32, ntk = (lwp + 31) / 32;
+    for (int q = wq; q < nti * ntk; q += 8) {
+      const int i0 = (q / ntk) * 32, k0 = (q % ntk) * 32;
+      // lane = row: column k of the tile is 32 consecutive rows of the column-major panel
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = k0 + kk, i = i0 + lane;
+        t[wq][kk][lane] = (i < f && k < w) ? Lp[(int64_t)k * f + i] : 0.f;
       }
-    // the diagonal blocks: warps 0-3 invert blocks ty, ty + 4, ...  (block b covers own rows 32 b .. 32 b + 31;
-    // 4 blocks per 128 rows, the slots of blocks past w stay unwritten and unread)
-    float* di = DI + S.di + P.di_ofs[gs];
-    for (int b = ty; ty < 4 && b < (w + kNB - 1) / kNB; b += 4) {
-      const int nbk = min(kNB, w - b * kNB);
-      for (int i = 0; i < kNB; ++i) Dm[ty][i][tx] = (i < nbk && tx <= i) ? Lp[(int64_t)(b * kNB + tx) * f + b * kNB + i] : 0.f;
-      dv[ty][tx] = tx < nbk ? 1.f / Lp[(int64_t)(b * kNB + tx) * f + b * kNB + tx] : 0.f;
       __syncwarp();
-      warp_tri_inverse<float>(Dm[ty], dv[ty], Dv[ty], nbk);
-      for (int i = 0; i < kNB; ++i) di[(int64_t)b * kNB * kNB + i * kNB + tx] = Dv[ty][i][tx];
+      // lane = column: row i of the tile is 32 consecutive entries of the row-major copy
+      for (int ii = 0; ii < 32; ++ii) {
+        const int i = i0 + ii, k = k0 + lane;
+        if (i < f && k < lwp) {
+          const float v = t[wq][lane][ii];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+          out[(int64_t)i * 2 * lwp + k] = hi;
+          out[(int64_t)i * 2 * lwp + lwp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+      }
       __syncwarp();
     }
+    // the diagonal blocks: warps 0-3 invert blocks wq, wq + 4, ... (the L block in t[wq], its inverse in
+    // t[wq + 4], free once every warp has finished its tiles); block b covers own rows 32 b .. 32 b + 31, 4 blocks
+    // per 128 rows, the slots of blocks past w stay unwritten and unread
     __syncthreads();
+    float* di = DI + S.di + P.di_ofs[gs];
+    for (int b = wq; wq < 4 && b < (w + kNB - 1) / kNB; b += 4) {
+      const int nbk = min(kNB, w - b * kNB);
+      for (int j = 0; j < kNB; ++j)  // lane = row, one column at a time (coalesced)
+        t[wq][lane][j] = (lane < nbk && j <= lane) ? Lp[(int64_t)(b * kNB + j) * f + b * kNB + lane] : 0.f;
+      dv[wq][lane] = lane < nbk ? 1.f / Lp[(int64_t)(b * kNB + lane) * f + b * kNB + lane] : 0.f;
+      __syncwarp();
+      warp_tri_inverse<float>(reinterpret_cast<const float (*)[kNB + 1]>(&t[wq][0][0]), dv[wq],
+                              reinterpret_cast<float (*)[kNB + 1]>(&t[wq + 4][0][0]), nbk);
+      for (int i = 0; i < kNB; ++i) di[(int64_t)b * kNB * kNB + i * kNB + lane] = t[wq + 4][i][lane];
+      __syncwarp();
+    }
+    __syncthreads();  // t is free again for the next panel's tiles
   }
 }
 
