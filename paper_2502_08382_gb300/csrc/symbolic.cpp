@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <stdexcept>
 
@@ -581,22 +582,66 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
     P.chol_stack = peak;
     P.chol_front = fr;
   }
-  // small subtrees: factored level by level, one warp per front, so their update
-  // blocks live at the same time and get slots of their own
+  // small subtrees: factored level by level, one warp per front, so an update block cannot live on the
+  // postorder stack.  A block is written at its supernode's level and read at its parent's (levels are
+  // separated by a CTA barrier), or in phase 2 when the parent is not small; slots are assigned first-fit at
+  // the level a block is written, reusing the space of blocks whose readers ran at an earlier level, so the
+  // small region holds the live blocks only (and stays in L2)
   P.sn_small.assign(ns, 0);
   P.usm_ofs.assign(ns, 0);
   {
-    int64_t us = 0;
     for (int s = 0; s < ns; ++s) {  // postorder: children first
       bool sm = P.sn_w[s] + P.sn_r[s] <= kSmallFront;
       for (int c : kids[s]) sm = sm && P.sn_small[c] != 0;
       P.sn_small[s] = sm ? 1 : 0;
-      if (sm && P.sn_parent[s] >= 0) {
-        P.usm_ofs[s] = us;
-        us += (int64_t)P.sn_r[s] * P.sn_r[s];
+    }
+    std::vector<int> ht(ns, 0);
+    for (int s = 0; s < ns; ++s)
+      for (int c : kids[s]) ht[s] = std::max(ht[s], ht[c] + 1);
+    const int nl = P.nlev;
+    std::vector<std::vector<int>> born(nl), dies(nl + 1);
+    for (int s = 0; s < ns; ++s)
+      if (P.sn_small[s] && P.sn_parent[s] >= 0) {
+        born[ht[s]].push_back(s);
+        const int pr = P.sn_parent[s];
+        dies[P.sn_small[pr] ? ht[pr] : nl].push_back(s);  // nl: read in phase 2, never freed
+      }
+    std::map<int64_t, int64_t> freel;  // offset -> size of free intervals
+    int64_t top = 0;
+    auto release = [&](int64_t o, int64_t sz) {
+      auto it = freel.emplace(o, sz).first;
+      auto nx = std::next(it);
+      if (nx != freel.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        freel.erase(nx);
+      }
+      if (it != freel.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+          pv->second += it->second;
+          freel.erase(it);
+        }
+      }
+    };
+    for (int l = 0; l < nl; ++l) {
+      if (l > 0)
+        for (int s : dies[l - 1]) release(P.usm_ofs[s], (int64_t)P.sn_r[s] * P.sn_r[s]);
+      for (int s : born[l]) {
+        const int64_t sz = (int64_t)P.sn_r[s] * P.sn_r[s];
+        auto it = freel.begin();
+        while (it != freel.end() && it->second < sz) ++it;
+        if (it != freel.end()) {
+          P.usm_ofs[s] = it->first;
+          const int64_t o = it->first + sz, rest = it->second - sz;
+          freel.erase(it);
+          if (rest > 0) freel.emplace(o, rest);
+        } else {
+          P.usm_ofs[s] = top;
+          top += sz;
+        }
       }
     }
-    P.usm_size = us;
+    P.usm_size = top;
   }
 }
 
