@@ -268,7 +268,7 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
   // blocked right-looking partial factorisation of the first w columns: one warp
   // factors kPB columns (warp syncs only), then the whole team applies their
   // rank-kPB update to the trailing triangle, kPB FMAs per element
-  constexpr int kPB = TEAM == 32 ? 8 : 16;
+  constexpr int kPB = 8;
   const int lane = tid & 31;
   for (int j0 = 0; factor && j0 < w; j0 += kPB) {
     const int jb = min(kPB, w - j0);
