@@ -89,9 +89,9 @@ __device__ void warp_chol(T (*D)[kNB + 1], T* dinv, int nbk, int* bad) {
         if (bad) *bad = 1;
         d = (T)1;
       }
-      d = sqrt(d);
-      D[k][k] = d;
-      dinv[k] = (T)1 / d;
+      const T rs = rsqrt(d);  // pivot d / sqrt(d) and its reciprocal from one FP64 sequence
+      D[k][k] = d * rs;
+      dinv[k] = rs;
     }
     __syncwarp();
     if (lane > k && lane < nbk) D[lane][k] *= dinv[k];
@@ -275,16 +275,21 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
     if (tid < 32) {
       for (int j = j0; j < j0 + jb; ++j) {
         const int cj = pidx(f, j, j);
+        // one reciprocal square root by lane 0 gives both the pivot (pv / sqrt(pv)) and the column scale, so
+        // the warp spends one FP64 sequence per column instead of a square root plus a division on every lane
+        // (this GPU's FP64 pipe is narrow and the small fronts have short columns)
+        double rs = 0.0;
         if (lane == 0) {
           double pv = Fp[cj];
           if (!(pv > 0.0)) {
             *bad = 1;
             pv = 1.0;
           }
-          Fp[cj] = sqrt(pv);
+          rs = rsqrt(pv);
+          Fp[cj] = pv * rs;
         }
+        const double inv = __shfl_sync(0xffffffffu, rs, 0);
         __syncwarp();
-        const double inv = 1.0 / Fp[cj];
         for (int i = j + 1 + lane; i < f; i += 32) Fp[cj + (i - j)] *= inv;
         __syncwarp();
         // update the panel's later columns k in (j, j0 + jb), rows i >= k
