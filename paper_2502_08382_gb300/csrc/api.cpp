@@ -253,7 +253,10 @@ void build(feti_ctx* c) {
     for (auto& sh : c->subs) total += c->pats[sh.pat].chol_flops;
     const double slots = (double)std::max(1, nsm * chol_ctas_per_sm());
     const double target = total / (4.0 * slots);
-    for (auto& P : c->pats) plan_tasks(P, target);
+    // fronts at least 384 wide (and their ancestors) go to the tensor-core Cholesky unless switched off
+    if (c->opt.chol_tc < 0 || c->opt.chol_tc > 1) throw ArgError("bad chol_tc (0 tensor cores for large fronts, 1 off)");
+    const int big_f = c->opt.chol_tc == 1 ? 0 : 384;
+    for (auto& P : c->pats) plan_tasks(P, target, big_f);
   }
   c->stats.t_symbolic_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
   c->stats.npatterns = (int)c->pats.size();
@@ -262,7 +265,7 @@ void build(feti_ctx* c) {
   // ---- concatenate pattern tables
   std::vector<int> sn_c0, sn_w, sn_r, sn_parent, rows, ch_off, ch_list, rel, kmap_src, kmap_dst, diag_src, iperm;
   std::vector<int64_t> sn_rows, rel_off, Lofs, kmap_off, upd_ofs, uofs, usm_ofs;
-  std::vector<int> sn_small, sn_task;
+  std::vector<int> sn_small, sn_task, sn_big;
   std::vector<int64_t> sn_hoff, lh_ofs, di_ofs;
   // mixed precision: the fronts the large-front TRSM takes (a bottom block of 128 rows or more, or 256 own rows
   // or more) get a row-major bf16 hi/lo copy of their panel, pat_lh elements per pattern
@@ -291,6 +294,7 @@ void build(feti_ctx* c) {
       usm_ofs.push_back(P.usm_ofs[s]);
       sn_task.push_back(P.sn_task[s]);
       sn_hoff.push_back(P.sn_hoff[s]);
+      sn_big.push_back(P.sn_big[s]);
       lh_ofs.push_back(lh_big(P, s) ? pat_lh[p] : -1);
       di_ofs.push_back(lh_big(P, s) ? pat_di[p] : -1);
       if (lh_big(P, s)) {
@@ -686,6 +690,7 @@ void build(feti_ctx* c) {
   D.sn_small = upload(c, sn_small);
   D.usm_ofs = upload(c, usm_ofs);
   D.sn_task = upload(c, sn_task);
+  D.sn_big = upload(c, sn_big);
   D.sn_hoff = upload(c, sn_hoff);
   D.lh_ofs = upload(c, lh_ofs);
   D.di_ofs = upload(c, di_ofs);
@@ -805,6 +810,7 @@ void build(feti_ctx* c) {
       const auto& P = c->pats[c->subs[i].pat];
       for (int t = 0; t < P.ntask; ++t) {
         nchild.push_back(P.task_nchild[t]);
+        if (t == 0 && P.has_big) continue;  // the large fronts: the tensor-core kernel's item
         tk.push_back({{P.task_height[t], -P.task_cost[t]},
                       make_int4(i, t, base + t, P.task_parent[t] >= 0 ? base + P.task_parent[t] : -1)});
       }
@@ -821,6 +827,34 @@ void build(feti_ctx* c) {
     D.task_nchild = upload(c, nchild);
     c->P2.task_nchild = D.task_nchild;
     c->d_tdone = (int*)dalloc(c, (size_t)std::max(base, 1) * sizeof(int));
+    // the tensor-core Cholesky's items: subdomains with large fronts, the most work first; its scratch per CTA:
+    // 8 slices x 128 bf16 and a row exponent for every row of the largest such front
+    {
+      std::vector<std::pair<double, int>> bi;
+      int fmax = 0;
+      for (int i = 0; i < ns; ++i) {
+        const auto& P = c->pats[c->subs[i].pat];
+        if (!P.has_big) continue;
+        double cost = 0;
+        for (int q = 0; q < P.nsn; ++q)
+          if (P.sn_big[q]) {
+            const double f = P.sn_w[q] + P.sn_r[q];
+            cost += f * f * P.sn_w[q];
+            fmax = std::max(fmax, (int)f);
+          }
+        bi.push_back({-cost, i});
+      }
+      std::stable_sort(bi.begin(), bi.end());
+      std::vector<int> tci;
+      for (auto& x : bi) tci.push_back(x.second);
+      c->n_tc_items = (int)tci.size();
+      if (c->n_tc_items > 0) {
+        c->d_tc_items = upload(c, tci);
+        c->grid_tc = std::min(c->nsm, std::min(c->n_tc_items, c->grid_chol));
+        c->slice_stride = ((int64_t)fmax * (8 * 128 + 2) + 127) / 128 * 128;
+        c->d_slices = (uint16_t*)dalloc(c, (size_t)c->grid_tc * c->slice_stride * 2);
+      }
+    }
     // nothing to split: the whole-subdomain items only
     if (c->opt.chol_split < 0 || c->opt.chol_split > 2) throw ArgError("bad chol_split (0 auto, 1 whole, 2 tasks)");
     c->chol_pick = c->opt.chol_split == 2 ? 1 : 0;
@@ -1024,9 +1058,17 @@ feti_status feti_assemble(feti_ctx* ctx) {
     auto run_chol = [&](int v, const DevPlan& P, int qslot, int flags) {
       CK(cudaMemsetAsync(ctx->d_queue + qslot, 0, sizeof(int), s2));
       if (v) CK(cudaMemsetAsync(ctx->d_tdone, 0, (size_t)std::max(ctx->ntask_total, 1) * sizeof(int), s2));
+      const int fl = flags | (ctx->n_tc_items > 0 ? kCholSkipBig : 0);
       launch_chol(P, ctx->d_chol_items[v], ctx->chol_nitems[v], v, ctx->d_queue + qslot, ctx->d_tdone, ctx->d_hand,
                   ctx->d_ws, ctx->ws_stride, ctx->chol_front, ctx->chol_stack,
-                  std::min(ctx->grid_chol, ctx->chol_nitems[v]), ctx->d_status, s2, flags);
+                  std::min(ctx->grid_chol, ctx->chol_nitems[v]), ctx->d_status, s2, fl);
+      if (ctx->n_tc_items > 0) {
+        // the large fronts on the tensor cores, after everything below them
+        CK(cudaMemsetAsync(ctx->d_queue + qslot + 1, 0, sizeof(int), s2));
+        launch_chol_tc(P, ctx->d_tc_items, ctx->n_tc_items, ctx->d_queue + qslot + 1, ctx->d_hand, ctx->d_ws,
+                       ctx->ws_stride, ctx->chol_front, ctx->d_slices, ctx->slice_stride, ctx->grid_tc, ctx->d_status,
+                       s2, flags);
+      }
     };
     if (!ctx->chol_tuned) {
       // autotuner: whole subdomains per CTA against the subtree tasks (the same factor bitwise), faster kept

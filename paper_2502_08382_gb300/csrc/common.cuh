@@ -72,6 +72,7 @@ struct DevPlan {
   const int* sn_task;        // [sn] Cholesky task of the supernode (local to the pattern's split)
   const int64_t* sn_hoff;    // [sn] hand-over slot of a split root (relative to the subdomain's hbase), -1 if none
   const int* task_nchild;    // [global task] child tasks to wait for
+  const int* sn_big;         // [sn] 1: factored by the tensor-core Cholesky kernel (large front or ancestor)
   const int64_t* lh_ofs;     // [sn] offset of the supernode's row-major hi/lo panel in LH (relative to the
                              // subdomain's lh), -1 for fronts the large-front TRSM does not take
   uint16_t* LH;              // row-major bf16 hi/lo copies of the large panels (mixed precision)
@@ -229,7 +230,7 @@ struct AdjBatch {
 constexpr int kBuildCols = 512;  // columns of V_Y per item of the adjoint's X_u W product
 
 // flags of the numeric Cholesky (kern_factor.cu)
-enum : int { kCholNoReg = 1, kCholStopRoot = 2 };
+enum : int { kCholNoReg = 1, kCholStopRoot = 2, kCholSkipBig = 4 };
 
 // status word bits written by kernels
 enum : int { kStatNotSPD = 1, kStatTimeout = 2, kStatBadPlan = 4 };

@@ -85,6 +85,10 @@ struct feti_ctx {
   int ntask_total = 0;
   int* d_tdone = nullptr;            // per global task: child tasks finished
   double* d_hand = nullptr;          // hand-over slots of split subtree roots
+  int* d_tc_items = nullptr;         // subdomains with fronts for the tensor-core Cholesky
+  int n_tc_items = 0, grid_tc = 0;
+  uint16_t* d_slices = nullptr;      // its per-CTA scratch (bf16 slices and row exponents)
+  int64_t slice_stride = 0;
   int2* d_l16_items = nullptr;       // (subdomain, supernode) of the panels with a row-major hi/lo copy
   int n_l16 = 0;
   int syrk_variant = 0;              // split-bf16 SYRK kernel picked by the autotuner

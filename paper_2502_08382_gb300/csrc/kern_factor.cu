@@ -123,11 +123,16 @@ __device__ void warp_tri_inverse(const T (*D)[kNB + 1], const T* dinv, T (*Di)[k
 
 // Partial dense factorisation of one front: eliminate the first w columns of
 // the (w+r) x (w+r) symmetric front held as Ls (column-major f x w) and W
-// (column-major r x r, lower part used).
-__device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int r, int* bad) {
+// (column-major r x r, lower part used).  With a column range: eliminate the
+// columns [kB, kE) only and apply their updates to the columns below ce only
+// (the tensor-core Cholesky updates the rest itself).
+__device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int r, int* bad, int kB = 0,
+                             int kE = -1, int ce = -1) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, warp = tid / 32;
-  for (int kb = 0; kb < w; kb += kNB) {
-    const int nbk = min(kNB, w - kb);
+  if (kE < 0) kE = w;
+  if (ce < 0) ce = f;
+  for (int kb = kB; kb < kE; kb += kNB) {
+    const int nbk = min(kNB, kE - kb);
     for (int idx = tid; idx < kNB * kNB; idx += kThreads) {
       int i = idx % kNB, j = idx / kNB;
       sm.D[i][j] = (i < nbk && j <= i) ? Ls[(int64_t)(kb + j) * f + kb + i] : 0.0;
@@ -173,6 +178,7 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
     for (int ti = 0; ti < T; ++ti) {
       for (int tj = 0; tj <= ti; ++tj) {
         const int ri = i0 + ti * kT, cj = i0 + tj * kT;
+        if (cj >= ce) break;
         for (int idx = tid; idx < nbk * kT; idx += kThreads) {
           int x = idx % kT, k = idx / kT;
           const double* col = Ls + (int64_t)(kb + k) * f;
@@ -190,7 +196,7 @@ __device__ void factor_front(Smem& sm, double* Ls, int f, int w, double* W, int 
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             int j = cj + tx + 16 * v;
-            if (u < nu && v < nv && i < f && j <= i) {
+            if (u < nu && v < nv && i < f && j <= i && j < ce) {
               double* p = (j < w) ? Ls + (int64_t)j * f + i : W + (int64_t)(j - w) * r + (i - w);
               *p -= acc[u][v];
             }
@@ -341,6 +347,57 @@ __device__ void packed_front(const DevPlan& P, const SubInfo& S, int s, const do
   team_sync<TEAM>();
 }
 
+// Assemble a front of the tiled path in global memory: the f x w panel Ls (column-major, in the factor's
+// storage) and the r x r bottom block W, from the K entries, the fixing-DOF penalty rho and the children's update
+// blocks (stack, small region or hand-over slot).
+__device__ void assemble_tiled(const DevPlan& P, const SubInfo& S, int s, const double* K, double* L, double rho,
+                               double* W, const double* stack, const double* smallreg, const double* hand) {
+  const int tid = threadIdx.x;
+  const int gs = S.sn0 + s;
+  const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
+  double* Ls = L + P.Lofs[gs];
+  for (int64_t idx = tid; idx < (int64_t)f * w; idx += kThreads) Ls[idx] = 0.0;
+  for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) W[idx] = 0.0;
+  __syncthreads();
+  for (int64_t k = P.kmap_off[gs] + tid; k < P.kmap_off[gs + 1]; k += kThreads)
+    L[P.kmap_dst[k]] = K[P.kmap_src[k]];
+  __syncthreads();
+  for (int k = tid; k < S.nfix; k += kThreads)
+    if (P.fix_sn[S.fix0 + k] == s) L[P.fix_pos[S.fix0 + k]] += rho;
+  for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
+    const int gc = S.sn0 + P.ch_list[c];
+    const int rc = P.sn_r[gc];
+    const double* U = child_update(P, gc, stack, smallreg, hand);
+    const int* rl = P.rel + P.rel_off[gc];
+    __syncthreads();
+    // four elements per thread and step, their loads issued before their read-modify-writes (distinct
+    // targets: rel is one-to-one)
+    const int64_t n = (int64_t)rc * rc;
+    for (int64_t base = tid; base < n; base += 4 * kThreads) {
+      double* dst[4];
+      double v[4], cur[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t idx = base + (int64_t)u * kThreads;
+        dst[u] = nullptr;
+        if (idx < n) {
+          const int b = (int)(idx / rc), a = (int)(idx - (int64_t)b * rc);
+          if (a >= b) {
+            const int ra = rl[a], rb = rl[b];
+            v[u] = __ldcg(U + idx);
+            dst[u] = rb < w ? Ls + (int64_t)rb * f + ra : W + (int64_t)(rb - w) * r + (ra - w);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cur[u] = dst[u] ? *dst[u] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (dst[u]) *dst[u] = cur[u] + v[u];
+    }
+  }
+}
+
 // One CTA per subdomain (persistent, queue sorted by decreasing cost).
 // Phase 1: the small subtrees, level by level from the leaves, one warp per
 // front.  Phase 2: the remaining supernodes in postorder, fronts up to
@@ -375,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
     const SubInfo S = P.sub[si];
     const double* K = P.Kval + S.Kval;
     double* L = P.L + S.L;
-    double* hand = use_tasks ? hand_all + S.hbase : nullptr;
+    double* hand = hand_all + S.hbase;  // hand-over slots of split roots (also when one CTA takes the subdomain)
     if (use_tasks && P.task_nchild[item.z] > 0) {
       // the child tasks were taken before this one and are running: wait for them (bounded)
       if (tid == 0) {
@@ -423,7 +480,9 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
         const int s = P.lvl_sn[q];
         const int gs = S.sn0 + s;
         if (!P.sn_small[gs] || (use_tasks && P.sn_task[gs] != task)) continue;
-        double* Uout = P.sn_parent[gs] >= 0 ? smallreg + P.usm_ofs[gs] : nullptr;
+        // a small subtree whose parent is factored by another task hands its update block over
+        double* Uout = P.sn_parent[gs] < 0 ? nullptr
+                       : P.sn_hoff[gs] >= 0 ? hand + P.sn_hoff[gs] : smallreg + P.usm_ofs[gs];
         packed_front<32>(P, S, s, K, L, rho, Fw, stack, smallreg, Uout, &bad, lane,
                          !((flags & kCholStopRoot) && s == S.nsn - 1));
       }
@@ -433,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
     for (int s = 0; s < S.nsn; ++s) {
       const int gs = S.sn0 + s;
       if (P.sn_small[gs] || (use_tasks && P.sn_task[gs] != task)) continue;
+      if ((flags & kCholSkipBig) && P.sn_big[gs]) continue;  // the tensor-core kernel's fronts
       const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
       double* Uout = P.sn_parent[gs] < 0 ? nullptr
                      : (hand && P.sn_hoff[gs] >= 0) ? hand + P.sn_hoff[gs] : stack + P.upd_ofs[gs];
@@ -442,46 +502,7 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
         continue;
       }
       double* Ls = L + P.Lofs[gs];
-      for (int64_t idx = tid; idx < (int64_t)f * w; idx += kThreads) Ls[idx] = 0.0;
-      for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) W[idx] = 0.0;
-      __syncthreads();
-      for (int64_t k = P.kmap_off[gs] + tid; k < P.kmap_off[gs + 1]; k += kThreads)
-        L[P.kmap_dst[k]] = K[P.kmap_src[k]];
-      __syncthreads();
-      for (int k = tid; k < S.nfix; k += kThreads)
-        if (P.fix_sn[S.fix0 + k] == s) L[P.fix_pos[S.fix0 + k]] += rho;
-      for (int c = P.ch_off[gs]; c < P.ch_off[gs + 1]; ++c) {
-        const int gc = S.sn0 + P.ch_list[c];
-        const int rc = P.sn_r[gc];
-        const double* U = child_update(P, gc, stack, smallreg, hand);
-        const int* rl = P.rel + P.rel_off[gc];
-        __syncthreads();
-        // four elements per thread and step, their loads issued before their read-modify-writes (distinct
-        // targets: rel is one-to-one)
-        const int64_t n = (int64_t)rc * rc;
-        for (int64_t base = tid; base < n; base += 4 * kThreads) {
-          double* dst[4];
-          double v[4], cur[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int64_t idx = base + (int64_t)u * kThreads;
-            dst[u] = nullptr;
-            if (idx < n) {
-              const int b = (int)(idx / rc), a = (int)(idx - (int64_t)b * rc);
-              if (a >= b) {
-                const int ra = rl[a], rb = rl[b];
-                v[u] = __ldcg(U + idx);
-                dst[u] = rb < w ? Ls + (int64_t)rb * f + ra : W + (int64_t)(rb - w) * r + (ra - w);
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) cur[u] = dst[u] ? *dst[u] : 0.0;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (dst[u]) *dst[u] = cur[u] + v[u];
-        }
-      }
+      assemble_tiled(P, S, s, K, L, rho, W, stack, smallreg, hand);
       __syncthreads();
       if (factor) factor_front(sm, Ls, f, w, W, r, &bad);
       __syncthreads();
@@ -497,6 +518,319 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
         atomicAdd(tdone + item.w, 1);
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------- tensor-core Cholesky of the large fronts
+//
+// The fronts at least big_f wide and their ancestors (the top of each supernodal tree) are factored by
+// chol_tc_kernel after chol_kernel has done everything below them.  A front's w own columns go in blocks of
+// 128: the block's columns are eliminated on the FP64 pipe (32-column steps, their updates applied to the
+// block's own columns only), and then the trailing matrix C = front[kE:, kE:] (its lower triangle, in Ls and W)
+// takes the block's rank-128 update C -= A A^T, A = Ls[kE:, kB:kE], on the tensor cores by exact slicing of
+// FP64 into bf16 integers (the Ozaki scheme): each row i of A is scaled by a power of two 2^(e_i - 6) with
+// e_i the largest exponent in the row, and its 56 leading fixed-point bits are cut into 8 signed 7-bit
+// integers s_p (p = 0 most significant), each exact in bf16, so A_ik = 2^(e_i - 6) sum_p s_p,ik 2^(-7p) up to
+// 2^(e_i - 55).  The products of slices p, q (p + q <= 7, 36 pairs) are summed over K = 128 on the tensor cores
+// with FP32 accumulation, one TMEM accumulator per d = p + q: every partial sum is an integer below
+// (d + 1) 128 127^2 < 2^24, so the FP32 sums are exact.  The epilogue combines them,
+// sum_k A_ik A_jk = 2^(e_i + e_j - 40) (sum_{d <= 4} acc_d 2^(7 (4 - d)) + sum_{d >= 5} acc_d 2^(7 (4 - d))),
+// the first sum exactly in 64-bit integers, the small rest in FP32, and applies C_ij -= that with one FP64 FMA.
+// The dropped pairs (p + q >= 8) and the cut bits leave an error of order K 2^-55 |e_i-scale| |e_j-scale|,
+// the size of FP64 rounding in the same product.
+constexpr int kOzS = 8;                              // slices of 7 bits
+constexpr int kOzK = 128;                            // columns of one panel block (K of one update)
+constexpr int kOzKC = 32;                            // K per stage: one 64-byte swizzled row per operand row
+constexpr int kOzN = 64;                             // C tile: 128 rows x 64 columns
+constexpr int kOzM = 128;                            // rows of a C tile (the MMA M)
+constexpr int kOzOpA = kOzM * 64, kOzOpB = kOzN * 64;
+constexpr int kOzStage = kOzS * (kOzOpA + kOzOpB);   // 96 KB: all slices of A and B for one 32-deep chunk
+constexpr int kOzStages = 2;
+constexpr int kCholTcDyn = 1024 + kOzStages * kOzStage;
+static_assert(sizeof(Smem) <= kOzStages * kOzStage, "the FP64 steps' buffers alias the stage ring");
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+
+// Slices of A = Ls[i0 + i, kb0 + k] (i < n = f - i0, k < K = ke0 - kb0 <= 128, zero for k >= K): row exponent
+// EX[i] and SL[(p n + i) 128 + k] = bf16(s_p,ik).  A warp takes 32 rows (lane = row: the loads of one column
+// are contiguous).
+__device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint16_t* SL, int* EX) {
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int n = f - i0, K = ke0 - kb0;
+  for (int rb = warp * 32; rb < n; rb += kThreads) {
+    const int i = rb + lane;
+    const bool ok = i < n;
+    int e = -1074;
+    for (int k = 0; k < K; ++k) {
+      const double x = ok ? Ls[(int64_t)(kb0 + k) * f + i0 + i] : 0.0;
+      const int be = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+      if (be) e = max(e, be - 1023);
+    }
+    if (ok) EX[i] = e;
+    for (int kc = 0; kc < kOzK; kc += 8) {
+      uint32_t pk[kOzS][4];
+#pragma unroll
+      for (int kk = 0; kk < 8; kk += 2) {
+        int sv[2][kOzS];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = kc + kk + h;
+          const double x = (ok && k < K) ? Ls[(int64_t)(kb0 + k) * f + i0 + i] : 0.0;
+          const long long b = __double_as_longlong(x);
+          const int be = (int)((b >> 52) & 0x7FF);
+          unsigned long long F = 0;
+          if (be) {
+            const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);
+            const int sh = (be - 1023) - e + 3;  // <= 3: F < 2^56
+            F = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ULL);
+          }
+          const bool neg = b < 0;
+#pragma unroll
+          for (int p = 0; p < kOzS; ++p) {
+            const int v = (int)((F >> (49 - 7 * p)) & 127ULL);
+            sv[h][p] = neg ? -v : v;
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p) {
+          const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[0][p]));
+          const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[1][p]));
+          pk[p][kk / 2] = lo | (hi << 16);
+        }
+      }
+      if (ok)
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p)
+          *reinterpret_cast<uint4*>(SL + ((int64_t)p * n + i) * kOzK + kc) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+    }
+  }
+}
+
+// C -= A A^T on the lower triangle of the trailing matrix (rows and columns [i0, f); columns < w in Ls, the
+// others in W) from the slices.  Tiles of 128 rows x 64 columns with a column block not right of the rows;
+// per 32-deep chunk all threads stage the 8 slices of the tile's A rows and B rows by cp.async into a
+// kOzStages ring, one thread issues the 36 x 2 MMAs (slice pair p, q into accumulator p + q at TMEM column
+// 64 (p + q)) and commits them to the stage's mbarrier; after a tile's last chunk the CTA combines the eight
+// accumulators (epilogue above).  Every wait is bounded.
+__device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t& g, int* abort_flag,
+                          const uint16_t* SL, const int* EX, int n, int K, double* Ls, int f, int w, double* W,
+                          int r, int i0) {
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int ntm = (n + kOzM - 1) / kOzM;
+  int ntile = 0;  // tiles (tm, tn) with tn <= 2 tm + 1, tn < ceil(n / 64)
+  const int ntnmax = (n + kOzN - 1) / kOzN;
+  for (int tm = 0; tm < ntm; ++tm) ntile += min(2 * tm + 2, ntnmax);
+  const int nck = (K + kOzKC - 1) / kOzKC;
+  const int total = ntile * nck;
+  if (total == 0) return true;
+  const uint32_t sb0 = smem_u32(ring);
+  const uint32_t g0 = g;
+  constexpr uint32_t idesc = idesc_m128(1u, (uint32_t)kOzN);
+  auto tile_of = [&](int t, int& tm, int& tn) {
+    tm = 0;
+    for (;;) {
+      const int c = min(2 * tm + 2, ntnmax);
+      if (t < c) break;
+      t -= c;
+      ++tm;
+    }
+    tn = t;
+  };
+  auto load = [&](int q, uint32_t sbase) {
+    const int ck = q % nck;
+    int tm, tn;
+    tile_of(q / nck, tm, tn);
+    const int k0 = ck * kOzKC, ia = tm * kOzM, ib = tn * kOzN;
+    // A: 8 slices x 128 rows x 4 pieces of 16 B; B: 8 slices x 64 rows x 4 pieces
+    for (int idx = tid; idx < kOzS * (kOzM + kOzN) * 4; idx += kThreads) {
+      const int p = idx / ((kOzM + kOzN) * 4), rem = idx % ((kOzM + kOzN) * 4);
+      const bool isA = rem < kOzM * 4;
+      const int rr = isA ? rem : rem - kOzM * 4, m = rr / 4, c = rr % 4;
+      const int row = (isA ? ia : ib) + m;
+      const bool ok = row < n;
+      const void* src = ok ? (const void*)(SL + ((int64_t)p * n + row) * kOzK + k0 + 8 * c) : (const void*)SL;
+      const uint32_t dst = sbase + (isA ? p * kOzOpA : kOzS * kOzOpA + p * kOzOpB) + (m >> 3) * 512 + (m & 7) * 64 +
+                           ((c ^ ((m >> 1) & 3)) << 4);
+      cp_async16(dst, src, ok);
+    }
+  };
+  bool okall = true;
+  for (int i = 0; i < total + kOzStages - 1; ++i) {
+    if (i < total) {
+      if (i >= kOzStages) {
+        const uint32_t gp = g0 + i - kOzStages;
+        if (tid == 0 && !mbar_wait(smem_u32(&gbar[gp % kOzStages]), (gp / kOzStages) & 1)) *abort_flag = 1;
+        __syncthreads();
+        if (*abort_flag) {
+          okall = false;
+          break;
+        }
+      }
+      load(i, sb0 + ((g0 + i) % kOzStages) * kOzStage);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int j = i - (kOzStages - 1);
+    if (j < 0 || j >= total) continue;
+    asm volatile("cp.async.wait_group %0;" ::"n"(kOzStages - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int ck = j % nck;
+    const uint32_t st = (g0 + j) % kOzStages;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sA = sb0 + st * kOzStage, sB = sA + kOzS * kOzOpA;
+#pragma unroll 1
+      for (int p = 0; p < kOzS; ++p)
+#pragma unroll 1
+        for (int q = 0; q < kOzS - p; ++q)
+#pragma unroll
+          for (int kk = 0; kk < kOzKC / 16; ++kk)
+            mma_f16(tmem + (uint32_t)((p + q) * kOzN), sw64_desc(sA + p * kOzOpA + kk * 32),
+                    sw64_desc(sB + q * kOzOpB + kk * 32), idesc, (ck > 0 || p > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&gbar[st]));
+    }
+    if (ck != nck - 1) continue;
+    if (tid == 0 && !mbar_wait(smem_u32(&gbar[st]), ((g0 + j) / kOzStages) & 1)) *abort_flag = 1;
+    __syncthreads();
+    if (*abort_flag) {
+      okall = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+      int tm, tn;
+      tile_of(j / nck, tm, tn);
+      const int q4 = warp % 4, h = warp / 4;
+      const int ri = tm * kOzM + q4 * 32 + lane;  // row of C (relative to i0)
+      const int gi = i0 + ri;
+      const int ei = ri < n ? EX[ri] : 0;
+#pragma unroll 1
+      for (int cg = 0; cg < 4; ++cg) {
+        const int cbase = tn * kOzN + h * 32 + cg * 8;  // first column of this group (relative to i0)
+        uint32_t a[kOzS][8];
+#pragma unroll
+        for (int d = 0; d < kOzS; ++d)
+          tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * kOzN + h * 32 + cg * 8), a[d]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (ri < n) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int cj = cbase + e, gj = i0 + cj;
+            if (cj < n && gj <= gi) {
+              long long I = 0;
+#pragma unroll
+              for (int d = 0; d <= 4; ++d)
+                I += (long long)__float2int_rn(__uint_as_float(a[d][e])) << (7 * (4 - d));
+              const float small = fmaf(fmaf(__uint_as_float(a[7][e]), 0x1p-7f, __uint_as_float(a[6][e])), 0x1p-7f,
+                                       __uint_as_float(a[5][e])) * 0x1p-7f;
+              const double t = (double)I + (double)small;
+              const int ex = ei + EX[cj] - 40;
+              const double sc = ex >= -1022 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
+              double* pc = gj < w ? Ls + (int64_t)gj * f + gi : W + (int64_t)(gj - w) * r + (gi - w);
+              *pc = fma(-t, sc, *pc);
+            }
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!okall) asm volatile("cp.async.wait_all;" ::: "memory");
+  g = g0 + total;
+  return okall;
+}
+
+// The large fronts (P.sn_big) of each subdomain in postorder, one subdomain per CTA and item (one CTA per SM:
+// the stage ring takes 193 KB of shared memory and the eight accumulators all 512 TMEM columns).  The fronts'
+// children outside the set handed their update blocks over (chol_kernel ran first); inside the set they go
+// through the CTA's stack as in chol_kernel.  The same flags as chol_kernel.
+__global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const int* items, int nitems, int* queue,
+                                                            double* hand_all, double* ws, int64_t ws_stride,
+                                                            int64_t front_sz, uint16_t* slices,
+                                                            int64_t slice_stride, int flags, int* status) {
+  extern __shared__ uint8_t oz_raw[];
+  uint8_t* ring = oz_raw + ((1024u - (smem_u32(oz_raw) & 1023u)) & 1023u);
+  Smem& sm = *reinterpret_cast<Smem*>(ring);  // the FP64 steps' buffers (never in use with the ring)
+  __shared__ uint64_t gbar[kOzStages];
+  __shared__ uint32_t tmem_s;
+  __shared__ int abort_s, bad;
+  __shared__ double red[kThreads / 32];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < kOzStages; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gbar[k])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_s = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_s;
+  uint32_t g = 0;
+  double* W = ws + (int64_t)blockIdx.x * ws_stride;
+  double* stack = W + front_sz;
+  uint16_t* SL = slices + (int64_t)blockIdx.x * slice_stride;
+  for (;;) {
+    const int it = pop_item(queue);
+    if (it >= nitems) break;
+    const int si = items[it];
+    const SubInfo S = P.sub[si];
+    const double* K = P.Kval + S.Kval;
+    double* L = P.L + S.L;
+    const double* hand = hand_all + S.hbase;
+    if (tid == 0) bad = 0;
+    double mx = 0.0;  // rho = max diag K_i, as in chol_kernel
+    for (int i = tid; i < S.n; i += kThreads) mx = fmax(mx, K[P.diag_src[S.diag0 + i]]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    double rho = red[0];
+    for (int k = 1; k < kThreads / 32; ++k) rho = fmax(rho, red[k]);
+    if (flags & kCholNoReg) rho = 0.0;
+    __syncthreads();
+    for (int s = 0; s < S.nsn && !abort_s; ++s) {
+      const int gs = S.sn0 + s;
+      if (!P.sn_big[gs]) continue;
+      const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
+      double* Ls = L + P.Lofs[gs];
+      assemble_tiled(P, S, s, K, L, rho, W, stack, nullptr, hand);
+      __syncthreads();
+      if (!((flags & kCholStopRoot) && s == S.nsn - 1)) {
+        for (int kB = 0; kB < w; kB += kOzK) {
+          const int kE = min(w, kB + kOzK);
+          factor_front(sm, Ls, f, w, W, r, &bad, kB, kE, kE);
+          __syncthreads();
+          if (kE < f) {
+            int* EX = reinterpret_cast<int*>(SL + (int64_t)kOzS * (f - kE) * kOzK);
+            oz_slice(Ls, f, kE, kB, kE, SL, EX);
+            __syncthreads();
+            if (!oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE)) break;
+          }
+        }
+      }
+      __syncthreads();
+      if (P.sn_parent[gs] >= 0)
+        for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) stack[P.upd_ofs[gs] + idx] = W[idx];
+      __syncthreads();
+    }
+    if (tid == 0 && bad) atomicOr(status, kStatNotSPD);
+    if (abort_s) break;
+  }
+  if (tid == 0 && abort_s) atomicOr(status, kStatTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
 }
 
@@ -1290,6 +1624,15 @@ void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks,
   cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   chol_kernel<<<grid, kThreads, smem, st>>>(P, items, nitems, use_tasks, queue, tdone, hand, ws, ws_stride, front_sz,
                                             stack_sz, flags, status);
+}
+
+void launch_chol_tc(const DevPlan& P, const int* items, int nitems, int* queue, double* hand, double* ws,
+                    int64_t ws_stride, int64_t front_sz, uint16_t* slices, int64_t slice_stride, int grid, int* status,
+                    cudaStream_t st, int flags) {
+  if (nitems <= 0) return;
+  cudaFuncSetAttribute(chol_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholTcDyn);
+  chol_tc_kernel<<<std::min(grid, nitems), kThreads, kCholTcDyn, st>>>(P, items, nitems, queue, hand, ws, ws_stride,
+                                                                       front_sz, slices, slice_stride, flags, status);
 }
 
 int chol_ctas_per_sm() {

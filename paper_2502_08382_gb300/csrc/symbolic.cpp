@@ -645,7 +645,7 @@ void analyse_pattern(int n, const int64_t* rp, const int32_t* col, const double*
   }
 }
 
-void plan_tasks(PatternPlan& P, double target) {
+void plan_tasks(PatternPlan& P, double target, int big_f) {
   const int ns = P.nsn;
   std::vector<double> own(ns, 0.0), sub(ns, 0.0);
   for (int s = 0; s < ns; ++s) {
@@ -661,18 +661,32 @@ void plan_tasks(PatternPlan& P, double target) {
     sub[s] += own[s];
     if (P.sn_parent[s] >= 0) sub[P.sn_parent[s]] += sub[s];
   }
+  // the large fronts (at least big_f wide) and all their ancestors: the top of the tree, factored by the
+  // tensor-core kernel after everything below it
+  P.sn_big.assign(ns, 0);
+  P.has_big = false;
+  if (big_f > 0) {
+    for (int s = 0; s < ns; ++s) {  // postorder: a supernode is seen before its parent
+      if (!P.sn_small[s] && P.sn_w[s] + P.sn_r[s] >= big_f) P.sn_big[s] = 1;
+      if (P.sn_big[s] && P.sn_parent[s] >= 0) P.sn_big[P.sn_parent[s]] = 1;
+    }
+    for (int s = 0; s < ns; ++s) P.has_big = P.has_big || P.sn_big[s];
+  }
   P.sn_task.assign(ns, 0);
   P.sn_hoff.assign(ns, -1);
   P.task_parent.assign(1, -1);
   P.task_cost.assign(1, 0.0);
   P.hsize = 0;
   // from the roots down (reverse postorder): a non-small supernode with a heavy subtree and a parent starts a
-  // task of its own below its parent's task; everything else joins its parent's task
+  // task of its own below its parent's task, and so does every supernode outside the large set whose parent
+  // is in it (the large set is task 0, factored by another kernel: its children hand their update blocks over);
+  // everything else joins its parent's task
   for (int s = ns - 1; s >= 0; --s) {
     const int p = P.sn_parent[s];
     if (p < 0) {
       P.sn_task[s] = 0;
-    } else if (target > 0 && !P.sn_small[s] && sub[s] > target && P.sn_r[s] > 0) {
+    } else if ((P.sn_big[p] && !P.sn_big[s]) ||
+               (target > 0 && !P.sn_small[s] && !P.sn_big[s] && sub[s] > target && P.sn_r[s] > 0)) {
       const int t = (int)P.task_parent.size();
       P.task_parent.push_back(P.sn_task[p]);
       P.task_cost.push_back(0.0);

@@ -51,7 +51,7 @@ class FetiOptions(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
                 ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
                 ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64), ("assembly_route", C.c_int32),
-                ("chol_split", C.c_int32), ("syrk_kernel", C.c_int32)]
+                ("chol_split", C.c_int32), ("syrk_kernel", C.c_int32), ("chol_tc", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -236,14 +236,16 @@ class FetiOperator:
     (the same with the Schur complements S_i of K_i onto the DOFs B touches in
     place of K_i; needs route="schur"); chol_split: "auto" (autotuned), "whole"
     (one subdomain per CTA) or "tasks" (heavy subtrees on CTAs of their own); syrk_kernel: -1 (autotuned)
-    or the split-bf16 SYRK kernel 0, 1, 2 to use."""
+    or the split-bf16 SYRK kernel 0, 1, 2 to use; chol_tc: the large fronts' updates on
+    the tensor cores (exact bf16 slicing) or all of the Cholesky on the FP64 pipe."""
 
     def __init__(self, problem, prec: str = "fp64", tol: float = 1e-10, maxit: int = 2000,
                  refine_every: int = 0, refine_drop: float = 0.0, refine_restart: bool = False,
                  precond: str = "none", leaf_dofs: int = 16, use_coords: bool = True,
                  with_elements: bool = False, unit_scale: bool = False, per_element: bool = False,
                  recompute_X: bool = False, adjoint_work_bytes: int = 0, route: str = "syrk",
-                 chol_split: str = "auto", syrk_kernel: int = -1, torch_alloc: bool = True):
+                 chol_split: str = "auto", syrk_kernel: int = -1, chol_tc: bool = True,
+                 torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -271,6 +273,7 @@ class FetiOperator:
         opt.assembly_route = {"syrk": 0, "schur": 1, "trsm": 2, "auto": 3}[route]
         opt.chol_split = {"auto": 0, "whole": 1, "tasks": 2}[chol_split]
         opt.syrk_kernel = 0 if syrk_kernel < 0 else syrk_kernel + 1
+        opt.chol_tc = 0 if chol_tc else 1
         self._cb = None
         if torch_alloc:
             dev = self.device.index

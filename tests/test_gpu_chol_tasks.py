@@ -106,3 +106,30 @@ def test_autotuned_split_reports_its_choice(torch_cuda):
     assert st["chol_tasks"] >= P.nsub
     Fo = O.local_F(P.subs[0])
     assert np.linalg.norm(F0 - Fo) <= F_bar("fp64", Fo, P.subs[0].n) * np.linalg.norm(Fo)
+
+
+@pytest.mark.parametrize("route", ["syrk", "schur"])
+@pytest.mark.parametrize("name", ["elast3d_one_large", "cfg3_2x2x2"])
+def test_tensor_core_cholesky(torch_cuda, name, route):
+    """The large fronts' rank-128 updates on the tensor cores (exact bf16 slicing, options.chol_tc = 0) against
+    the FP64-pipe Cholesky (chol_tc = 1): F_i within the FP64 bar of the oracle either way, and the two within
+    the same bar of each other."""
+    from paper_2502_08382_gb300 import feti
+    P = make_config(3, nsub_axis=2) if name == "cfg3_2x2x2" else CASES[name]()
+    Fs = {}
+    for tc in (True, False):
+        op = feti.FetiOperator(P, prec="fp64", route=route, chol_tc=tc)
+        op.assemble()
+        Fs[tc] = [op.get_F(i) for i in range(P.nsub)]
+        op.close()
+    worst = 0.0
+    for i, s in enumerate(P.subs):
+        Fo = O.local_F(s)
+        bar = F_bar("fp64", Fo, s.n)
+        for tc in (True, False):
+            err = np.linalg.norm(Fs[tc][i] - Fo) / np.linalg.norm(Fo)
+            assert err <= bar, (tc, i, err)
+        d = np.linalg.norm(Fs[True][i] - Fs[False][i]) / np.linalg.norm(Fo)
+        worst = max(worst, np.linalg.norm(Fs[True][i] - Fo) / np.linalg.norm(Fo) / bar)
+        assert d <= bar, (i, d)
+    print(f"{name} {route}: tensor-core Cholesky F_i at most {worst:.3f} of the FP64 bar")
