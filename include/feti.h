@@ -151,6 +151,7 @@ typedef struct {
   double implicit_bytes;      /* factor bytes read by one implicit apply */
   /* last feti_assemble, CUDA-event times on the context's stream (ms) */
   double t_chol_ms, t_trsm_ms, t_syrk_ms, t_coarse_ms, t_assemble_ms;
+  double t_chol_tc_ms;        /* the part of t_chol_ms spent in the tensor-core kernel of the large fronts */
   double t_symbolic_ms;       /* host analysis time in feti_create */
   /* measurement counters since the last feti_set_profiling(ctx, 1) */
   int64_t launches;           /* kernel launches issued by this context */

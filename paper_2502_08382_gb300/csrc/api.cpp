@@ -803,20 +803,22 @@ void build(feti_ctx* c) {
     // parents (by task height), heavier first
     std::vector<int4> whole;
     for (int si : order) whole.push_back(make_int4(si, 0, 0, -1));
-    std::vector<std::pair<std::pair<int, double>, int4>> tk;
-    std::vector<int> nchild;
+    std::vector<std::pair<std::pair<int, double>, int4>> tk, tkb;
+    std::vector<int> nchild, nbig;
     int base = 0;
     for (int i = 0; i < ns; ++i) {
       const auto& P = c->pats[c->subs[i].pat];
       for (int t = 0; t < P.ntask; ++t) {
         nchild.push_back(P.task_nchild[t]);
-        if (t == 0 && P.has_big) continue;  // the large fronts: the tensor-core kernel's item
-        tk.push_back({{P.task_height[t], -P.task_cost[t]},
-                      make_int4(i, t, base + t, P.task_parent[t] >= 0 ? base + P.task_parent[t] : -1)});
+        nbig.push_back(P.task_nbig[t]);
+        const int4 item = make_int4(i, t, base + t, P.task_parent[t] >= 0 ? base + P.task_parent[t] : -1);
+        // the large fronts' tasks are the tensor-core kernel's items
+        (P.task_big[t] ? tkb : tk).push_back({{P.task_height[t], -P.task_cost[t]}, item});
       }
       base += P.ntask;
     }
     std::stable_sort(tk.begin(), tk.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    std::stable_sort(tkb.begin(), tkb.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     std::vector<int4> split;
     for (auto& x : tk) split.push_back(x.second);
     c->d_chol_items[0] = upload(c, whole);
@@ -826,32 +828,25 @@ void build(feti_ctx* c) {
     c->ntask_total = base;
     D.task_nchild = upload(c, nchild);
     c->P2.task_nchild = D.task_nchild;
+    D.task_nbig = upload(c, nbig);
+    c->P2.task_nbig = D.task_nbig;
     c->d_tdone = (int*)dalloc(c, (size_t)std::max(base, 1) * sizeof(int));
-    // the tensor-core Cholesky's items: subdomains with large fronts, the most work first; its scratch per CTA:
-    // 8 slices x 128 bf16 and a row exponent for every row of the largest such front
+    // the tensor-core Cholesky's items: the large tasks, children first; its scratch per CTA: the bf16 slices and
+    // a row exponent for every row of the largest such front
     {
-      std::vector<std::pair<double, int>> bi;
       int fmax = 0;
       for (int i = 0; i < ns; ++i) {
         const auto& P = c->pats[c->subs[i].pat];
-        if (!P.has_big) continue;
-        double cost = 0;
         for (int q = 0; q < P.nsn; ++q)
-          if (P.sn_big[q]) {
-            const double f = P.sn_w[q] + P.sn_r[q];
-            cost += f * f * P.sn_w[q];
-            fmax = std::max(fmax, (int)f);
-          }
-        bi.push_back({-cost, i});
+          if (P.sn_big[q]) fmax = std::max(fmax, P.sn_w[q] + P.sn_r[q]);
       }
-      std::stable_sort(bi.begin(), bi.end());
-      std::vector<int> tci;
-      for (auto& x : bi) tci.push_back(x.second);
+      std::vector<int4> tci;
+      for (auto& x : tkb) tci.push_back(x.second);
       c->n_tc_items = (int)tci.size();
       if (c->n_tc_items > 0) {
         c->d_tc_items = upload(c, tci);
         c->grid_tc = std::min(c->nsm, std::min(c->n_tc_items, c->grid_chol));
-        c->slice_stride = ((int64_t)fmax * (8 * 128 + 2) + 127) / 128 * 128;
+        c->slice_stride = chol_tc_scratch(fmax);
         c->d_slices = (uint16_t*)dalloc(c, (size_t)c->grid_tc * c->slice_stride * 2);
       }
     }
@@ -1055,7 +1050,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
       // the lumped preconditioner's values from the current K (they change with feti_update_values)
       launch_lumped_values(ctx->m_nnz, ctx->d_mc_off, ctx->d_mc_kidx, ctx->d_mc_sign, ctx->d_Kval, ctx->d_m_val,
                            s2);
-    auto run_chol = [&](int v, const DevPlan& P, int qslot, int flags) {
+    auto run_chol = [&](int v, const DevPlan& P, int qslot, int flags, bool mark = false) {
       CK(cudaMemsetAsync(ctx->d_queue + qslot, 0, sizeof(int), s2));
       if (v) CK(cudaMemsetAsync(ctx->d_tdone, 0, (size_t)std::max(ctx->ntask_total, 1) * sizeof(int), s2));
       const int fl = flags | (ctx->n_tc_items > 0 ? kCholSkipBig : 0);
@@ -1064,10 +1059,12 @@ feti_status feti_assemble(feti_ctx* ctx) {
                   std::min(ctx->grid_chol, ctx->chol_nitems[v]), ctx->d_status, s2, fl);
       if (ctx->n_tc_items > 0) {
         // the large fronts on the tensor cores, after everything below them
+        if (mark) CK(cudaEventRecordWithFlags(ctx->ev[7], s2, evf));
         CK(cudaMemsetAsync(ctx->d_queue + qslot + 1, 0, sizeof(int), s2));
-        launch_chol_tc(P, ctx->d_tc_items, ctx->n_tc_items, ctx->d_queue + qslot + 1, ctx->d_hand, ctx->d_ws,
-                       ctx->ws_stride, ctx->chol_front, ctx->d_slices, ctx->slice_stride, ctx->grid_tc, ctx->d_status,
-                       s2, flags);
+        CK(cudaMemsetAsync(ctx->d_tdone, 0, (size_t)std::max(ctx->ntask_total, 1) * sizeof(int), s2));
+        launch_chol_tc(P, ctx->d_tc_items, ctx->n_tc_items, ctx->d_queue + qslot + 1, ctx->d_tdone, ctx->d_hand,
+                       ctx->d_ws, ctx->ws_stride, ctx->chol_front, ctx->d_slices, ctx->slice_stride, ctx->grid_tc,
+                       ctx->d_status, s2, flags);
       }
     };
     if (!ctx->chol_tuned) {
@@ -1086,7 +1083,7 @@ feti_status feti_assemble(feti_ctx* ctx) {
     }
     ctx->stats.chol_tasks = ctx->chol_pick ? ctx->chol_nitems[1] : ctx->chol_nitems[0];
     CK(cudaEventRecordWithFlags(ctx->ev[0], s2, evf));
-    run_chol(ctx->chol_pick, ctx->P, 0, 0);
+    run_chol(ctx->chol_pick, ctx->P, 0, 0, true);
     CK(cudaEventRecordWithFlags(ctx->ev[1], s2, evf));
     if (r2) {
       launch_unit_scale(ctx->P, ctx->nsub, ctx->P.dinv, s2);
@@ -1240,6 +1237,12 @@ feti_status feti_assemble(feti_ctx* ctx) {
   CK(cudaEventElapsedTime(&cc, ctx->ev[2], ctx->ev[3]));
   CK(cudaEventElapsedTime(&d, ctx->ev[0], ctx->ev[4]));
   ctx->stats.t_chol_ms = a;
+  ctx->stats.t_chol_tc_ms = 0;
+  if (ctx->n_tc_items > 0 && ctx->route != 2) {
+    float tcm = 0;
+    CK(cudaEventElapsedTime(&tcm, ctx->ev[7], ctx->ev[1]));
+    ctx->stats.t_chol_tc_ms = tcm;
+  }
   ctx->stats.t_trsm_ms = b;
   ctx->stats.t_syrk_ms = cc;
   float e34;

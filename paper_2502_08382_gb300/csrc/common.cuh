@@ -73,6 +73,7 @@ struct DevPlan {
   const int64_t* sn_hoff;    // [sn] hand-over slot of a split root (relative to the subdomain's hbase), -1 if none
   const int* task_nchild;    // [global task] child tasks to wait for
   const int* sn_big;         // [sn] 1: factored by the tensor-core Cholesky kernel (large front or ancestor)
+  const int* task_nbig;      // [global task] large child tasks (the tensor-core kernel waits for them)
   const int64_t* lh_ofs;     // [sn] offset of the supernode's row-major hi/lo panel in LH (relative to the
                              // subdomain's lh), -1 for fronts the large-front TRSM does not take
   uint16_t* LH;              // row-major bf16 hi/lo copies of the large panels (mixed precision)

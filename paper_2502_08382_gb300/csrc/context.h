@@ -85,7 +85,7 @@ struct feti_ctx {
   int ntask_total = 0;
   int* d_tdone = nullptr;            // per global task: child tasks finished
   double* d_hand = nullptr;          // hand-over slots of split subtree roots
-  int* d_tc_items = nullptr;         // subdomains with fronts for the tensor-core Cholesky
+  int4* d_tc_items = nullptr;        // the large fronts' tasks (the tensor-core Cholesky's items)
   int n_tc_items = 0, grid_tc = 0;
   uint16_t* d_slices = nullptr;      // its per-CTA scratch (bf16 slices and row exponents)
   int64_t slice_stride = 0;

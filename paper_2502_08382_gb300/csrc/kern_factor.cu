@@ -529,22 +529,23 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
 // block's own columns only), and then the trailing matrix C = front[kE:, kE:] (its lower triangle, in Ls and W)
 // takes the block's rank-128 update C -= A A^T, A = Ls[kE:, kB:kE], on the tensor cores by exact slicing of
 // FP64 into bf16 integers (the Ozaki scheme): each row i of A is scaled by a power of two 2^(e_i - 6) with
-// e_i the largest exponent in the row, and its 56 leading fixed-point bits are cut into 8 signed 7-bit
+// e_i the largest exponent in the row, and its 63 leading fixed-point bits are cut into 9 signed 7-bit
 // integers s_p (p = 0 most significant), each exact in bf16, so A_ik = 2^(e_i - 6) sum_p s_p,ik 2^(-7p) up to
-// 2^(e_i - 55).  The products of slices p, q (p + q <= 7, 36 pairs) are summed over K = 128 on the tensor cores
-// with FP32 accumulation, one TMEM accumulator per d = p + q: every partial sum is an integer below
-// (d + 1) 128 127^2 < 2^24, so the FP32 sums are exact.  The epilogue combines them,
+// 2^(e_i - 62).  The products of slices p, q (p + q <= 8, 45 pairs) are summed over K = 128 on the tensor cores
+// with FP32 accumulation, one TMEM accumulator per d = p + q.  For d <= 4 every partial sum is an integer below
+// (d + 1) 128 127^2 < 2^24, so those FP32 sums are exact; for d >= 5 the sum is below 2^(-35) of the leading
+// term and its FP32 rounding below 2^(-59) of it.  The epilogue combines them,
 // sum_k A_ik A_jk = 2^(e_i + e_j - 40) (sum_{d <= 4} acc_d 2^(7 (4 - d)) + sum_{d >= 5} acc_d 2^(7 (4 - d))),
 // the first sum exactly in 64-bit integers, the small rest in FP32, and applies C_ij -= that with one FP64 FMA.
-// The dropped pairs (p + q >= 8) and the cut bits leave an error of order K 2^-55 |e_i-scale| |e_j-scale|,
-// the size of FP64 rounding in the same product.
-constexpr int kOzS = 8;                              // slices of 7 bits
+// The dropped pairs (p + q >= 9) and the cut bits leave an error of order K 2^-62 2^(e_i + e_j), below FP64
+// rounding in the same product unless an entry is 2^9 below its row's largest.
+constexpr int kOzS = 9;                              // slices of 7 bits
 constexpr int kOzK = 128;                            // columns of one panel block (K of one update)
 constexpr int kOzKC = 32;                            // K per stage: one 64-byte swizzled row per operand row
-constexpr int kOzN = 64;                             // C tile: 128 rows x 64 columns
+constexpr int kOzN = 32;                             // C tile: 128 rows x 32 columns (9 accumulators x 32 TMEM columns)
 constexpr int kOzM = 128;                            // rows of a C tile (the MMA M)
 constexpr int kOzOpA = kOzM * 64, kOzOpB = kOzN * 64;
-constexpr int kOzStage = kOzS * (kOzOpA + kOzOpB);   // 96 KB: all slices of A and B for one 32-deep chunk
+constexpr int kOzStage = kOzS * (kOzOpA + kOzOpB);   // 90 KB: all slices of A and B for one 32-deep chunk
 constexpr int kOzStages = 2;
 constexpr int kCholTcDyn = 1024 + kOzStages * kOzStage;
 static_assert(sizeof(Smem) <= kOzStages * kOzStage, "the FP64 steps' buffers alias the stage ring");
@@ -585,13 +586,13 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
           unsigned long long F = 0;
           if (be) {
             const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);
-            const int sh = (be - 1023) - e + 3;  // <= 3: F < 2^56
+            const int sh = (be - 1023) - e + 10;  // <= 10: F < 2^63
             F = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ULL);
           }
           const bool neg = b < 0;
 #pragma unroll
           for (int p = 0; p < kOzS; ++p) {
-            const int v = (int)((F >> (49 - 7 * p)) & 127ULL);
+            const int v = (int)((F >> (56 - 7 * p)) & 127ULL);
             sv[h][p] = neg ? -v : v;
           }
         }
@@ -621,9 +622,10 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
                           int r, int i0) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntm = (n + kOzM - 1) / kOzM;
-  int ntile = 0;  // tiles (tm, tn) with tn <= 2 tm + 1, tn < ceil(n / 64)
+  constexpr int kTnPerTm = kOzM / kOzN;  // column blocks per row block
+  int ntile = 0;  // tiles (tm, tn) with a column block not right of the row block: tn < (tm + 1) kTnPerTm
   const int ntnmax = (n + kOzN - 1) / kOzN;
-  for (int tm = 0; tm < ntm; ++tm) ntile += min(2 * tm + 2, ntnmax);
+  for (int tm = 0; tm < ntm; ++tm) ntile += min((tm + 1) * kTnPerTm, ntnmax);
   const int nck = (K + kOzKC - 1) / kOzKC;
   const int total = ntile * nck;
   if (total == 0) return true;
@@ -633,7 +635,7 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
   auto tile_of = [&](int t, int& tm, int& tn) {
     tm = 0;
     for (;;) {
-      const int c = min(2 * tm + 2, ntnmax);
+      const int c = min((tm + 1) * kTnPerTm, ntnmax);
       if (t < c) break;
       t -= c;
       ++tm;
@@ -704,17 +706,17 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
     {
       int tm, tn;
       tile_of(j / nck, tm, tn);
-      const int q4 = warp % 4, h = warp / 4;
+      const int q4 = warp % 4, h = warp / 4;  // TMEM lane quarter (rows), column half
       const int ri = tm * kOzM + q4 * 32 + lane;  // row of C (relative to i0)
       const int gi = i0 + ri;
       const int ei = ri < n ? EX[ri] : 0;
 #pragma unroll 1
-      for (int cg = 0; cg < 4; ++cg) {
-        const int cbase = tn * kOzN + h * 32 + cg * 8;  // first column of this group (relative to i0)
+      for (int cg = 0; cg < kOzN / 16; ++cg) {
+        const int cbase = tn * kOzN + h * (kOzN / 2) + cg * 8;  // first column of this group (relative to i0)
         uint32_t a[kOzS][8];
 #pragma unroll
         for (int d = 0; d < kOzS; ++d)
-          tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * kOzN + h * 32 + cg * 8), a[d]);
+          tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * kOzN + h * (kOzN / 2) + cg * 8), a[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (ri < n) {
 #pragma unroll
@@ -725,8 +727,9 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
 #pragma unroll
               for (int d = 0; d <= 4; ++d)
                 I += (long long)__float2int_rn(__uint_as_float(a[d][e])) << (7 * (4 - d));
-              const float small = fmaf(fmaf(__uint_as_float(a[7][e]), 0x1p-7f, __uint_as_float(a[6][e])), 0x1p-7f,
-                                       __uint_as_float(a[5][e])) * 0x1p-7f;
+              float small = 0.f;  // sum_{d >= 5} acc_d 2^(-7 (d - 4)), Horner from the smallest
+#pragma unroll
+              for (int d = kOzS - 1; d >= 5; --d) small = (small + __uint_as_float(a[d][e])) * 0x1p-7f;
               const double t = (double)I + (double)small;
               const int ex = ei + EX[cj] - 40;
               const double sc = ex >= -1022 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
@@ -745,13 +748,15 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
   return okall;
 }
 
-// The large fronts (P.sn_big) of each subdomain in postorder, one subdomain per CTA and item (one CTA per SM:
-// the stage ring takes 193 KB of shared memory and the eight accumulators all 512 TMEM columns).  The fronts'
-// children outside the set handed their update blocks over (chol_kernel ran first); inside the set they go
-// through the CTA's stack as in chol_kernel.  The same flags as chol_kernel.
-__global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const int* items, int nitems, int* queue,
-                                                            double* hand_all, double* ws, int64_t ws_stride,
-                                                            int64_t front_sz, uint16_t* slices,
+// The large fronts (P.sn_big), one task of the plan's split per item (subdomain, task, global task id, parent's
+// global task id), children before parents; one CTA per SM (the stage ring takes 181 KB of shared memory and
+// the nine accumulators 288 of the 512 TMEM columns), all resident.  The fronts' children outside the set
+// handed their update blocks over (chol_kernel ran first); a large child task's block comes from its hand-over
+// slot after a bounded wait on the task's counter of finished large children (tdone), others through the
+// CTA's stack as in chol_kernel.  The same flags as chol_kernel.
+__global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const int4* items, int nitems, int* queue,
+                                                            int* tdone, double* hand_all, double* ws,
+                                                            int64_t ws_stride, int64_t front_sz, uint16_t* slices,
                                                             int64_t slice_stride, int flags, int* status) {
   extern __shared__ uint8_t oz_raw[];
   uint8_t* ring = oz_raw + ((1024u - (smem_u32(oz_raw) & 1023u)) & 1023u);
@@ -782,12 +787,35 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
   for (;;) {
     const int it = pop_item(queue);
     if (it >= nitems) break;
-    const int si = items[it];
+    const int4 item = items[it];
+    const int si = item.x, task = item.y;
     const SubInfo S = P.sub[si];
     const double* K = P.Kval + S.Kval;
     double* L = P.L + S.L;
-    const double* hand = hand_all + S.hbase;
-    if (tid == 0) bad = 0;
+    double* hand = hand_all + S.hbase;
+    if (tid == 0) {
+      bad = 0;
+      // the large child tasks were taken before this one and are running: wait for them (bounded)
+      int ok = 1;
+      if (P.task_nbig[item.z] > 0) {
+        ok = 0;
+        for (int i = 0; i < (1 << 26); ++i) {
+          if (*(volatile int*)(tdone + item.z) >= P.task_nbig[item.z]) {
+            ok = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+      if (!ok) {
+        atomicOr(status, kStatTimeout);
+        bad = 2;
+        if (item.w >= 0) atomicAdd(tdone + item.w, 1);  // no cascade of waits above a failure
+      }
+    }
+    __syncthreads();
+    if (bad == 2) continue;
     double mx = 0.0;  // rho = max diag K_i, as in chol_kernel
     for (int i = tid; i < S.n; i += kThreads) mx = fmax(mx, K[P.diag_src[S.diag0 + i]]);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -799,7 +827,7 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
     __syncthreads();
     for (int s = 0; s < S.nsn && !abort_s; ++s) {
       const int gs = S.sn0 + s;
-      if (!P.sn_big[gs]) continue;
+      if (!P.sn_big[gs] || P.sn_task[gs] != task) continue;
       const int w = P.sn_w[gs], r = P.sn_r[gs], f = w + r;
       double* Ls = L + P.Lofs[gs];
       assemble_tiled(P, S, s, K, L, rho, W, stack, nullptr, hand);
@@ -818,11 +846,19 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
         }
       }
       __syncthreads();
-      if (P.sn_parent[gs] >= 0)
-        for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) stack[P.upd_ofs[gs] + idx] = W[idx];
+      if (P.sn_parent[gs] >= 0) {
+        double* Uout = P.sn_hoff[gs] >= 0 ? hand + P.sn_hoff[gs] : stack + P.upd_ofs[gs];
+        for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) Uout[idx] = W[idx];
+      }
       __syncthreads();
     }
-    if (tid == 0 && bad) atomicOr(status, kStatNotSPD);
+    if (tid == 0) {
+      if (bad) atomicOr(status, kStatNotSPD);
+      if (item.w >= 0 && !abort_s) {
+        __threadfence();  // the task's factor panels and hand-over block before the count
+        atomicAdd(tdone + item.w, 1);
+      }
+    }
     if (abort_s) break;
   }
   if (tid == 0 && abort_s) atomicOr(status, kStatTimeout);
@@ -1626,14 +1662,17 @@ void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks,
                                             stack_sz, flags, status);
 }
 
-void launch_chol_tc(const DevPlan& P, const int* items, int nitems, int* queue, double* hand, double* ws,
-                    int64_t ws_stride, int64_t front_sz, uint16_t* slices, int64_t slice_stride, int grid, int* status,
-                    cudaStream_t st, int flags) {
+void launch_chol_tc(const DevPlan& P, const int4* items, int nitems, int* queue, int* tdone, double* hand,
+                    double* ws, int64_t ws_stride, int64_t front_sz, uint16_t* slices, int64_t slice_stride, int grid,
+                    int* status, cudaStream_t st, int flags) {
   if (nitems <= 0) return;
   cudaFuncSetAttribute(chol_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholTcDyn);
-  chol_tc_kernel<<<std::min(grid, nitems), kThreads, kCholTcDyn, st>>>(P, items, nitems, queue, hand, ws, ws_stride,
-                                                                       front_sz, slices, slice_stride, flags, status);
+  chol_tc_kernel<<<std::min(grid, nitems), kThreads, kCholTcDyn, st>>>(P, items, nitems, queue, tdone, hand, ws,
+                                                                       ws_stride, front_sz, slices, slice_stride,
+                                                                       flags, status);
 }
+
+int64_t chol_tc_scratch(int fmax) { return ((int64_t)fmax * (kOzS * kOzK + 2) + 127) / 128 * 128; }
 
 int chol_ctas_per_sm() {
   const int smem = kFrontSmem * 8;

@@ -14,12 +14,12 @@ void launch_chol(const DevPlan& P, const int4* items, int nitems, int use_tasks,
                  double* hand, double* ws, int64_t ws_stride, int64_t front_sz, int64_t stack_sz, int grid,
                  int* status, cudaStream_t st, int flags = 0);
 int chol_ctas_per_sm();
-// the large fronts (P.sn_big) after launch_chol with kCholSkipBig: items = subdomains with such fronts, one CTA
-// per SM (grid <= SMs), slices: per CTA slice_stride uint16 of scratch (8 x 128 bf16 + 2 per row of the largest
-// front)
-void launch_chol_tc(const DevPlan& P, const int* items, int nitems, int* queue, double* hand, double* ws,
-                    int64_t ws_stride, int64_t front_sz, uint16_t* slices, int64_t slice_stride, int grid, int* status,
-                    cudaStream_t st, int flags);
+// the large fronts (P.sn_big) after launch_chol with kCholSkipBig: items = the large tasks (subdomain, task,
+// global task, parent's global task) children first, tdone zeroed, one CTA per SM (grid <= SMs), slices: per CTA slice_stride = chol_tc_scratch(largest front) uint16 of scratch
+int64_t chol_tc_scratch(int fmax);  // uint16 elements of the per-CTA scratch for fronts up to fmax wide
+void launch_chol_tc(const DevPlan& P, const int4* items, int nitems, int* queue, int* tdone, double* hand,
+                    double* ws, int64_t ws_stride, int64_t front_sz, uint16_t* slices, int64_t slice_stride, int grid,
+                    int* status, cudaStream_t st, int flags);
 // items: (subdomain, first sorted column) pairs, each covering cw columns (cw = 0: all columns)
 // X2 (FP32 X only, may be null): the bf16 hi/lo copy of X (per column: wp hi values, then wp lo values; 2 bf16
 // per X element): the large fronts (P.lh_ofs >= 0, tcmode 2) use it as GEMM operand; with x2_out every

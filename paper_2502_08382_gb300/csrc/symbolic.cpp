@@ -679,14 +679,14 @@ void plan_tasks(PatternPlan& P, double target, int big_f) {
   P.hsize = 0;
   // from the roots down (reverse postorder): a non-small supernode with a heavy subtree and a parent starts a
   // task of its own below its parent's task, and so does every supernode outside the large set whose parent
-  // is in it (the large set is task 0, factored by another kernel: its children hand their update blocks over);
-  // everything else joins its parent's task
+  // is in it (the large set's tasks are factored by another kernel, after the others: their children hand their
+  // update blocks over); everything else joins its parent's task.  A task is large if its root is.
   for (int s = ns - 1; s >= 0; --s) {
     const int p = P.sn_parent[s];
     if (p < 0) {
       P.sn_task[s] = 0;
     } else if ((P.sn_big[p] && !P.sn_big[s]) ||
-               (target > 0 && !P.sn_small[s] && !P.sn_big[s] && sub[s] > target && P.sn_r[s] > 0)) {
+               (target > 0 && !P.sn_small[s] && sub[s] > target && P.sn_r[s] > 0)) {
       const int t = (int)P.task_parent.size();
       P.task_parent.push_back(P.sn_task[p]);
       P.task_cost.push_back(0.0);
@@ -701,7 +701,14 @@ void plan_tasks(PatternPlan& P, double target, int big_f) {
   P.ntask = (int)P.task_parent.size();
   P.task_nchild.assign(P.ntask, 0);
   P.task_height.assign(P.ntask, 0);
-  for (int t = 1; t < P.ntask; ++t) P.task_nchild[P.task_parent[t]]++;
+  P.task_big.assign(P.ntask, 0);
+  P.task_nbig.assign(P.ntask, 0);
+  for (int s = 0; s < ns; ++s)
+    if (P.sn_big[s]) P.task_big[P.sn_task[s]] = 1;  // a task holds large supernodes only or none
+  for (int t = 1; t < P.ntask; ++t) {
+    P.task_nchild[P.task_parent[t]]++;
+    if (P.task_big[t]) P.task_nbig[P.task_parent[t]]++;
+  }
   // tasks are numbered parents first, so heights follow from the highest numbers down
   for (int t = P.ntask - 1; t >= 1; --t)
     P.task_height[P.task_parent[t]] = std::max(P.task_height[P.task_parent[t]], P.task_height[t] + 1);

@@ -67,14 +67,16 @@ struct PatternPlan {
   std::vector<int> task_height;    // 0 for tasks without child tasks, else 1 + the tallest child
   std::vector<double> task_cost;   // Cholesky flops of the task's own supernodes
   int64_t hsize = 0;               // doubles of all hand-over slots
-  std::vector<int> sn_big;         // 1: a front at least big_f wide or an ancestor of one (task 0 then)
+  std::vector<int> sn_big;         // 1: a front at least big_f wide or an ancestor of one
   bool has_big = false;
+  std::vector<int> task_big;       // 1: the task's supernodes are large (the tensor-core Cholesky's)
+  std::vector<int> task_nbig;      // large child tasks
 };
 
 // Cut the pattern's supernodal tree into Cholesky tasks: a child subtree whose flops exceed `target` becomes
 // a task of its own (recursively), so that one large subdomain can be factored by several CTAs.  big_f > 0:
-// the fronts at least big_f wide and their ancestors form task 0 (the tensor-core Cholesky's work), and every
-// other child of that set starts a task of its own.
+// the fronts at least big_f wide and their ancestors (the tensor-core Cholesky's work) form tasks of their own,
+// cut by the same rule, and every other child of that set starts a task.
 void plan_tasks(PatternPlan& P, double target, int big_f = 0);
 
 struct BPlan {

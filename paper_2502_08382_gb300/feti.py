@@ -66,7 +66,8 @@ class FetiStats(C.Structure):
                 ("chol_flops", C.c_double), ("trsm_flops", C.c_double), ("syrk_flops", C.c_double),
                 ("syrk_exec_flops", C.c_double), ("apply_bytes", C.c_double), ("implicit_bytes", C.c_double),
                 ("t_chol_ms", C.c_double), ("t_trsm_ms", C.c_double), ("t_syrk_ms", C.c_double),
-                ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_symbolic_ms", C.c_double),
+                ("t_coarse_ms", C.c_double), ("t_assemble_ms", C.c_double), ("t_chol_tc_ms", C.c_double),
+                ("t_symbolic_ms", C.c_double),
                 ("launches", C.c_int64), ("apply_calls", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_tiles_ms", C.c_double), ("implicit_calls", C.c_int64), ("implicit_ms", C.c_double),
                 ("apply_variant", C.c_int32), ("apply_grid", C.c_int32), ("trsm_cols", C.c_int32),

@@ -91,7 +91,7 @@ def main():
                       "syrk_flops": s["syrk_flops"], "refine_every": args.refine_every,
                       "refine_drop": args.refine_drop, "restart": args.restart, "precond": args.precond,
                       "route": args.route, "route_used": s["assembly_route"], "route_ms": s["route_ms"],
-                      "phases_ms": {k: s[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms")},
+                      "phases_ms": {k: s[k] for k in ("t_chol_ms", "t_chol_tc_ms", "t_trsm_ms", "t_syrk_ms")},
                       "trsm_cols": s["trsm_cols"], "trsm_grid": s["trsm_grid"], "syrk_variant": s["syrk_variant"], "chol_tasks": s["chol_tasks"], "chol_split": args.chol_split,
                       "solve": info, "launches": s["launches"], "profiled": prof}))
     op.close()
