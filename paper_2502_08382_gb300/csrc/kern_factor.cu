@@ -572,7 +572,8 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
       if (be) e = max(e, be - 1023);
     }
     if (ok) EX[i] = e;
-    for (int kc = 0; kc < kOzK; kc += 8) {
+    const int kpad = (K + kOzKC - 1) / kOzKC * kOzKC;  // the chunks the update reads
+    for (int kc = 0; kc < kpad; kc += 8) {
       uint32_t pk[kOzS][4];
 #pragma unroll
       for (int kk = 0; kk < 8; kk += 2) {
@@ -611,20 +612,21 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
   }
 }
 
-// C -= A A^T on the lower triangle of the trailing matrix (rows and columns [i0, f); columns < w in Ls, the
-// others in W) from the slices.  Tiles of 128 rows x 64 columns with a column block not right of the rows;
+// C -= A A^T on the lower triangle of the trailing matrix (rows [i0, f), columns [i0, ce); columns < w in Ls,
+// the others in W) from the slices.  Tiles of 128 rows x 64 columns with a column block not right of the rows;
 // per 32-deep chunk all threads stage the 8 slices of the tile's A rows and B rows by cp.async into a
 // kOzStages ring, one thread issues the 36 x 2 MMAs (slice pair p, q into accumulator p + q at TMEM column
 // 64 (p + q)) and commits them to the stage's mbarrier; after a tile's last chunk the CTA combines the eight
 // accumulators (epilogue above).  Every wait is bounded.
 __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t& g, int* abort_flag,
                           const uint16_t* SL, const int* EX, int n, int K, double* Ls, int f, int w, double* W,
-                          int r, int i0) {
+                          int r, int i0, int ce) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int ntm = (n + kOzM - 1) / kOzM;
+  const int nce = ce - i0;               // columns of C
   constexpr int kTnPerTm = kOzM / kOzN;  // column blocks per row block
   int ntile = 0;  // tiles (tm, tn) with a column block not right of the row block: tn < (tm + 1) kTnPerTm
-  const int ntnmax = (n + kOzN - 1) / kOzN;
+  const int ntnmax = (nce + kOzN - 1) / kOzN;
   for (int tm = 0; tm < ntm; ++tm) ntile += min((tm + 1) * kTnPerTm, ntnmax);
   const int nck = (K + kOzKC - 1) / kOzKC;
   const int total = ntile * nck;
@@ -722,7 +724,7 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int cj = cbase + e, gj = i0 + cj;
-            if (cj < n && gj <= gi) {
+            if (cj < nce && gj <= gi) {
               long long I = 0;
 #pragma unroll
               for (int d = 0; d <= 4; ++d)
@@ -833,15 +835,28 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
       assemble_tiled(P, S, s, K, L, rho, W, stack, nullptr, hand);
       __syncthreads();
       if (!((flags & kCholStopRoot) && s == S.nsn - 1)) {
-        for (int kB = 0; kB < w; kB += kOzK) {
+        bool okf = true;
+        for (int kB = 0; kB < w && okf; kB += kOzK) {
           const int kE = min(w, kB + kOzK);
-          factor_front(sm, Ls, f, w, W, r, &bad, kB, kE, kE);
-          __syncthreads();
-          if (kE < f) {
+          // the block's 32-column steps: the pivot block and the panel below it on the FP64 pipe, the rank-32
+          // update of the block's later columns on the tensor cores
+          for (int kb = kB; kb < kE && okf; kb += kNB) {
+            const int ke = min(kE, kb + kNB);
+            factor_front(sm, Ls, f, w, W, r, &bad, kb, ke, ke);
+            __syncthreads();
+            if (ke < kE) {
+              int* EX = reinterpret_cast<int*>(SL + (int64_t)kOzS * (f - ke) * kOzK);
+              oz_slice(Ls, f, ke, kb, ke, SL, EX);
+              __syncthreads();
+              okf = oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - ke, ke - kb, Ls, f, w, W, r, ke, kE);
+            }
+          }
+          // the rank-128 update of the rest of the front
+          if (okf && kE < f) {
             int* EX = reinterpret_cast<int*>(SL + (int64_t)kOzS * (f - kE) * kOzK);
             oz_slice(Ls, f, kE, kB, kE, SL, EX);
             __syncthreads();
-            if (!oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE)) break;
+            okf = oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE, f);
           }
         }
       }
