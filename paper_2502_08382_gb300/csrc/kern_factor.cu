@@ -556,13 +556,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
-// Slices of A = Ls[i0 + i, kb0 + k] (i < n = f - i0, k < K = ke0 - kb0 <= 128, zero for k >= K): row exponent
-// EX[i] and SL[(p n + i) 128 + k] = bf16(s_p,ik).  A warp takes 32 rows (lane = row: the loads of one column
-// are contiguous).
+// Layout of the slices in the per-CTA scratch: for slice p and 32-deep chunk c, the rows one after another
+// (npad = rows rounded up to 128), each row 32 bf16 = 64 bytes with its four 16-byte pieces already in the
+// 64-byte swizzle of an 8-row atom (piece q of row r at q ^ ((r >> 1) & 3)): any 8-row-aligned run of rows of
+// one (p, c) is a ready MMA operand, loaded by one bulk copy.
+__device__ __forceinline__ int64_t oz_row(int p, int c, int npad, int r) {
+  return ((int64_t)(p * (kOzK / kOzKC) + c) * npad + r) * kOzKC;
+}
+
+// Slices of A = Ls[i0 + i, kb0 + k] (i < n = f - i0, k < K = ke0 - kb0 <= 128; zero for k >= K and for the
+// padding rows): row exponent EX[i] and the slices in the layout above.  A warp takes 32 rows (lane = row: the
+// loads of one column are contiguous).
 __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint16_t* SL, int* EX) {
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int n = f - i0, K = ke0 - kb0;
-  for (int rb = warp * 32; rb < n; rb += kThreads) {
+  const int n = f - i0, K = ke0 - kb0, npad = (n + kOzM - 1) / kOzM * kOzM;
+  const int nch = (K + kOzKC - 1) / kOzKC;  // the chunks the update reads
+  for (int rb = warp * 32; rb < npad; rb += kThreads) {
     const int i = rb + lane;
     const bool ok = i < n;
     int e = -1074;
@@ -572,8 +581,7 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
       if (be) e = max(e, be - 1023);
     }
     if (ok) EX[i] = e;
-    const int kpad = (K + kOzKC - 1) / kOzKC * kOzKC;  // the chunks the update reads
-    for (int kc = 0; kc < kpad; kc += 8) {
+    for (int kc = 0; kc < nch * kOzKC; kc += 8) {
       uint32_t pk[kOzS][4];
 #pragma unroll
       for (int kk = 0; kk < 8; kk += 2) {
@@ -604,25 +612,41 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
           pk[p][kk / 2] = lo | (hi << 16);
         }
       }
-      if (ok)
+      const int c = kc / kOzKC, q = (kc % kOzKC) / 8;
 #pragma unroll
-        for (int p = 0; p < kOzS; ++p)
-          *reinterpret_cast<uint4*>(SL + ((int64_t)p * n + i) * kOzK + kc) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+      for (int p = 0; p < kOzS; ++p)
+        *reinterpret_cast<uint4*>(SL + oz_row(p, c, npad, i) + ((q ^ ((i >> 1) & 3)) * 8)) =
+            make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
     }
   }
 }
 
+// the row exponents follow the slices of an n-row A
+__device__ __forceinline__ int* oz_ex(uint16_t* SL, int n) {
+  const int npad = (n + kOzM - 1) / kOzM * kOzM;
+  return reinterpret_cast<int*>(SL + oz_row(kOzS, 0, npad, 0));
+}
+
+__device__ __forceinline__ void oz_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void oz_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // C -= A A^T on the lower triangle of the trailing matrix (rows [i0, f), columns [i0, ce); columns < w in Ls,
-// the others in W) from the slices.  Tiles of 128 rows x 64 columns with a column block not right of the rows;
-// per 32-deep chunk all threads stage the 8 slices of the tile's A rows and B rows by cp.async into a
-// kOzStages ring, one thread issues the 36 x 2 MMAs (slice pair p, q into accumulator p + q at TMEM column
-// 64 (p + q)) and commits them to the stage's mbarrier; after a tile's last chunk the CTA combines the eight
-// accumulators (epilogue above).  Every wait is bounded.
-__device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t& g, int* abort_flag,
-                          const uint16_t* SL, const int* EX, int n, int K, double* Ls, int f, int w, double* W,
-                          int r, int i0, int ce) {
+// the others in W) from the slices.  Tiles of 128 rows x 32 columns with a column block not right of the row
+// block; per 32-deep chunk thread 0 loads the 9 A and 9 B slice operands with 18 bulk copies completing on the
+// stage's "full" mbarrier, then (one chunk behind) issues the 45 x 2 MMAs (slice pair p, q into accumulator
+// p + q at TMEM column 32 (p + q)) and commits them to the stage's "empty" mbarrier; after a tile's last chunk
+// the CTA combines the nine accumulators (epilogue above).  Every wait is bounded.
+__device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_t tmem, uint32_t& g,
+                          int* abort_flag, const uint16_t* SL, const int* EX, int n, int K, double* Ls, int f, int w,
+                          double* W, int r, int i0, int ce) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int ntm = (n + kOzM - 1) / kOzM;
+  const int ntm = (n + kOzM - 1) / kOzM, npad = ntm * kOzM;
   const int nce = ce - i0;               // columns of C
   constexpr int kTnPerTm = kOzM / kOzN;  // column blocks per row block
   int ntile = 0;  // tiles (tm, tn) with a column block not right of the row block: tn < (tm + 1) kTnPerTm
@@ -644,61 +668,65 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
     }
     tn = t;
   };
-  auto load = [&](int q, uint32_t sbase) {
+  int last_load = -1, last_mma = -1;  // thread 0: for the drain after a wait gave up
+  auto load = [&](int q) {  // thread 0: the 18 bulk copies of chunk q into its stage
+    last_load = q;
+    const uint32_t st = (g0 + q) % kOzStages, sbase = sb0 + st * kOzStage;
+    const uint32_t full = smem_u32(&fbar[st]);
     const int ck = q % nck;
     int tm, tn;
     tile_of(q / nck, tm, tn);
-    const int k0 = ck * kOzKC, ia = tm * kOzM, ib = tn * kOzN;
-    // A: 8 slices x 128 rows x 4 pieces of 16 B; B: 8 slices x 64 rows x 4 pieces
-    for (int idx = tid; idx < kOzS * (kOzM + kOzN) * 4; idx += kThreads) {
-      const int p = idx / ((kOzM + kOzN) * 4), rem = idx % ((kOzM + kOzN) * 4);
-      const bool isA = rem < kOzM * 4;
-      const int rr = isA ? rem : rem - kOzM * 4, m = rr / 4, c = rr % 4;
-      const int row = (isA ? ia : ib) + m;
-      const bool ok = row < n;
-      const void* src = ok ? (const void*)(SL + ((int64_t)p * n + row) * kOzK + k0 + 8 * c) : (const void*)SL;
-      const uint32_t dst = sbase + (isA ? p * kOzOpA : kOzS * kOzOpA + p * kOzOpB) + (m >> 3) * 512 + (m & 7) * 64 +
-                           ((c ^ ((m >> 1) & 3)) << 4);
-      cp_async16(dst, src, ok);
+    oz_expect(full, (uint32_t)kOzStage);
+#pragma unroll 1
+    for (int p = 0; p < kOzS; ++p) {
+      oz_bulk(sbase + p * kOzOpA, SL + oz_row(p, ck, npad, tm * kOzM), kOzOpA, full);
+      oz_bulk(sbase + kOzS * kOzOpA + p * kOzOpB, SL + oz_row(p, ck, npad, tn * kOzN), kOzOpB, full);
     }
   };
   bool okall = true;
-  for (int i = 0; i < total + kOzStages - 1; ++i) {
-    if (i < total) {
-      if (i >= kOzStages) {
-        const uint32_t gp = g0 + i - kOzStages;
-        if (tid == 0 && !mbar_wait(smem_u32(&gbar[gp % kOzStages]), (gp / kOzStages) & 1)) *abort_flag = 1;
-        __syncthreads();
-        if (*abort_flag) {
-          okall = false;
-          break;
-        }
-      }
-      load(i, sb0 + ((g0 + i) % kOzStages) * kOzStage);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    const int j = i - (kOzStages - 1);
-    if (j < 0 || j >= total) continue;
-    asm volatile("cp.async.wait_group %0;" ::"n"(kOzStages - 1) : "memory");
+  __syncthreads();  // the slices are written and the ring's earlier generic use is over
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    for (int q = 0; q < kOzStages - 1 && q < total; ++q) load(q);
+  }
+  for (int j = 0; j < total; ++j) {
     const int ck = j % nck;
     const uint32_t st = (g0 + j) % kOzStages;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sA = sb0 + st * kOzStage, sB = sA + kOzS * kOzOpA;
+    if (tid == 0 && !*abort_flag) {  // after a wait gave up nothing more is issued or waited for
+      bool ok = true;
+      // the next chunk's stage: free once the MMAs of the chunk that used it have completed
+      const int q = j + kOzStages - 1;
+      if (q < total) {
+        if (q >= kOzStages) {
+          const uint32_t gp = g0 + q - kOzStages;
+          ok = mbar_wait(smem_u32(&gbar[gp % kOzStages]), (gp / kOzStages) & 1);
+        }
+        if (ok) load(q);
+      }
+      if (ok) ok = mbar_wait(smem_u32(&fbar[st]), ((g0 + j) / kOzStages) & 1);
+      if (!ok) {
+        *abort_flag = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sA = sb0 + st * kOzStage, sB = sA + kOzS * kOzOpA;
 #pragma unroll 1
-      for (int p = 0; p < kOzS; ++p)
+        for (int p = 0; p < kOzS; ++p)
 #pragma unroll 1
-        for (int q = 0; q < kOzS - p; ++q)
+          for (int qq = 0; qq < kOzS - p; ++qq)
 #pragma unroll
-          for (int kk = 0; kk < kOzKC / 16; ++kk)
-            mma_f16(tmem + (uint32_t)((p + q) * kOzN), sw64_desc(sA + p * kOzOpA + kk * 32),
-                    sw64_desc(sB + q * kOzOpB + kk * 32), idesc, (ck > 0 || p > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(smem_u32(&gbar[st]));
+            for (int kk = 0; kk < kOzKC / 16; ++kk)
+              mma_f16(tmem + (uint32_t)((p + qq) * kOzN), sw64_desc(sA + p * kOzOpA + kk * 32),
+                      sw64_desc(sB + qq * kOzOpB + kk * 32), idesc, (ck > 0 || p > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&gbar[st]));
+        last_mma = j;
+      }
     }
-    if (ck != nck - 1) continue;
-    if (tid == 0 && !mbar_wait(smem_u32(&gbar[st]), ((g0 + j) / kOzStages) & 1)) *abort_flag = 1;
+    if (ck != nck - 1) {
+      if (tid == 0 && *abort_flag) okall = false;
+      continue;
+    }
+    if (tid == 0 && !*abort_flag && !mbar_wait(smem_u32(&gbar[st]), ((g0 + j) / kOzStages) & 1)) *abort_flag = 1;
     __syncthreads();
     if (*abort_flag) {
       okall = false;
@@ -745,7 +773,19 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint32_t tmem, uint32_t
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
-  if (!okall) asm volatile("cp.async.wait_all;" ::: "memory");
+  // a wait given up may leave copies or MMAs in flight: wait (bounded) for the last ones issued
+  if (tid == 0 && *abort_flag) {
+    if (last_mma >= 0) {
+      const uint32_t gq = g0 + last_mma;
+      mbar_wait(smem_u32(&gbar[gq % kOzStages]), (gq / kOzStages) & 1);
+    }
+    if (last_load > last_mma) {
+      const uint32_t gq = g0 + last_load;
+      mbar_wait(smem_u32(&fbar[gq % kOzStages]), (gq / kOzStages) & 1);
+    }
+  }
+  __syncthreads();
+  okall = !*abort_flag;
   g = g0 + total;
   return okall;
 }
@@ -763,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
   extern __shared__ uint8_t oz_raw[];
   uint8_t* ring = oz_raw + ((1024u - (smem_u32(oz_raw) & 1023u)) & 1023u);
   Smem& sm = *reinterpret_cast<Smem*>(ring);  // the FP64 steps' buffers (never in use with the ring)
-  __shared__ uint64_t gbar[kOzStages];
+  __shared__ uint64_t gbar[kOzStages], fbar[kOzStages];  // per stage: MMAs done ("empty"), copies landed ("full")
   __shared__ uint32_t tmem_s;
   __shared__ int abort_s, bad;
   __shared__ double red[kThreads / 32];
@@ -774,7 +814,10 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int k = 0; k < kOzStages; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gbar[k])));
+    for (int k = 0; k < kOzStages; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gbar[k])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar[k])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
   }
@@ -845,18 +888,16 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
             factor_front(sm, Ls, f, w, W, r, &bad, kb, ke, ke);
             __syncthreads();
             if (ke < kE) {
-              int* EX = reinterpret_cast<int*>(SL + (int64_t)kOzS * (f - ke) * kOzK);
+              int* EX = oz_ex(SL, f - ke);
               oz_slice(Ls, f, ke, kb, ke, SL, EX);
-              __syncthreads();
-              okf = oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - ke, ke - kb, Ls, f, w, W, r, ke, kE);
+              okf = oz_update(ring, gbar, fbar, tmem, g, &abort_s, SL, EX, f - ke, ke - kb, Ls, f, w, W, r, ke, kE);
             }
           }
           // the rank-128 update of the rest of the front
           if (okf && kE < f) {
-            int* EX = reinterpret_cast<int*>(SL + (int64_t)kOzS * (f - kE) * kOzK);
+            int* EX = oz_ex(SL, f - kE);
             oz_slice(Ls, f, kE, kB, kE, SL, EX);
-            __syncthreads();
-            okf = oz_update(ring, gbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE, f);
+            okf = oz_update(ring, gbar, fbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE, f);
           }
         }
       }
@@ -1687,7 +1728,10 @@ void launch_chol_tc(const DevPlan& P, const int4* items, int nitems, int* queue,
                                                                        flags, status);
 }
 
-int64_t chol_tc_scratch(int fmax) { return ((int64_t)fmax * (kOzS * kOzK + 2) + 127) / 128 * 128; }
+int64_t chol_tc_scratch(int fmax) {
+  const int64_t npad = (fmax + kOzM - 1) / kOzM * kOzM;
+  return (npad * (kOzS * kOzK + 2) + 127) / 128 * 128;
+}
 
 int chol_ctas_per_sm() {
   const int smem = kFrontSmem * 8;
