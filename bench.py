@@ -142,7 +142,11 @@ def other_rooflines(st, impl_ms, hbm):
         a = st["chol_flops"] / (st["t_chol_ms"] * 1e-3) / 1e12
         out["chol_kernel"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": a / FP64_PEAK_TFLOPS, "peak_kind": "derived FP64",
-                              "algorithmic_flops": st["chol_flops"], "ms": st["t_chol_ms"]}
+                              "algorithmic_flops": st["chol_flops"], "ms": st["t_chol_ms"],
+                              "tc_kernel_ms": st.get("t_chol_tc_ms", 0.0),
+                              "note": "FP64 flops of the factorisation over both Cholesky kernels; the rank-32 and "
+                                      "rank-128 updates of the fronts at least 384 wide run on the tensor cores "
+                                      "(exact bf16 slicing, chol_tc_kernel), so frac is against the FP64 pipe only"}
     if st["t_trsm_ms"] > 0:
         a = st["trsm_flops"] / (st["t_trsm_ms"] * 1e-3) / 1e12
         out["trsm_kernel<float>"] = {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
