@@ -532,13 +532,14 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
 // e_i the largest exponent in the row, and its 63 leading fixed-point bits are cut into 9 signed 7-bit
 // integers s_p (p = 0 most significant), each exact in bf16, so A_ik = 2^(e_i - 6) sum_p s_p,ik 2^(-7p) up to
 // 2^(e_i - 62).  The products of slices p, q (p + q <= 8, 45 pairs) are summed over K = 128 on the tensor cores
-// with FP32 accumulation, one TMEM accumulator per d = p + q.  For d <= 4 every partial sum is an integer below
-// (d + 1) 128 127^2 < 2^24, so those FP32 sums are exact; for d >= 5 the sum is below 2^(-35) of the leading
-// term and its FP32 rounding below 2^(-59) of it.  The epilogue combines them,
+// with FP32 accumulation, one TMEM accumulator per d = p + q.  For d <= 7 every partial sum is an integer below
+// (d + 1) 128 127^2 < 2^24, so those FP32 sums are exact (d = 8 may round by one unit, at 2^-56 of the leading
+// scale).  The epilogue combines them,
 // sum_k A_ik A_jk = 2^(e_i + e_j - 40) (sum_{d <= 4} acc_d 2^(7 (4 - d)) + sum_{d >= 5} acc_d 2^(7 (4 - d))),
-// the first sum exactly in 64-bit integers, the small rest in FP32, and applies C_ij -= that with one FP64 FMA.
-// The dropped pairs (p + q >= 9) and the cut bits leave an error of order K 2^-62 2^(e_i + e_j), below FP64
-// rounding in the same product unless an entry is 2^9 below its row's largest.
+// the first sum exactly in 64-bit integers, the small rest in FP32 (its rounding below 2^-53 of K sigma_i sigma_j,
+// sigma = 2^(e + 1)), and applies C_ij -= that with one FP64 FMA.  The dropped pairs (p + q >= 9) and the cut
+// bits add below K 2^(e_i + e_j - 58): the whole error stays below K 2^-52 sigma_i sigma_j, inside FP64's own
+// normwise bound for the same dot product (tests/test_slicing_model.py checks the model on the host).
 constexpr int kOzS = 9;                              // slices of 7 bits
 constexpr int kOzK = 128;                            // columns of one panel block (K of one update)
 constexpr int kOzKC = 32;                            // K per stage: one 64-byte swizzled row per operand row
