@@ -541,13 +541,15 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
 // bits add below K 2^(e_i + e_j - 58): the whole error stays below K 2^-52 sigma_i sigma_j, inside FP64's own
 // normwise bound for the same dot product (tests/test_slicing_model.py checks the model on the host).
 constexpr int kOzS = 9;                              // slices of 7 bits
+constexpr int kOzAcc = 8;  // accumulators: d = 0 .. 6, and d = 7 with the d = 8 products (B slices scaled by 2^-7)
 constexpr int kOzK = 128;                            // columns of one panel block (K of one update)
 constexpr int kOzKC = 32;                            // K per stage: one 64-byte swizzled row per operand row
 constexpr int kOzN = 32;                             // C tile: 128 rows x 32 columns (9 accumulators x 32 TMEM columns)
 constexpr int kOzM = 128;                            // rows of a C tile (the MMA M)
 constexpr int kOzOpA = kOzM * 64, kOzOpB = kOzN * 64;
-constexpr int kOzStage = kOzS * (kOzOpA + kOzOpB);   // 90 KB: all slices of A and B for one 32-deep chunk
+constexpr int kOzStage = kOzS * (kOzOpA + 2 * kOzOpB);  // 108 KB: A slices, B slices, B slices x 2^-7 of a chunk
 constexpr int kOzStages = 2;
+constexpr int kOzSetCols = kOzAcc * kOzN;               // TMEM columns of one accumulator set (two sets)
 constexpr int kCholTcDyn = 1024 + kOzStages * kOzStage;
 static_assert(sizeof(Smem) <= kOzStages * kOzStage, "the FP64 steps' buffers alias the stage ring");
 
@@ -557,7 +559,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
-// Layout of the slices in the per-CTA scratch: for slice p and 32-deep chunk c, the rows one after another
+// Layout of the slices in the per-CTA scratch: for slice p (p >= 9: slice p - 9 times 2^-7) and 32-deep chunk c,
+// the rows one after another
 // (npad = rows rounded up to 128), each row 32 bf16 = 64 bytes with its four 16-byte pieces already in the
 // 64-byte swizzle of an 8-row atom (piece q of row r at q ^ ((r >> 1) & 3)): any 8-row-aligned run of rows of
 // one (p, c) is a ready MMA operand, loaded by one bulk copy.
@@ -583,7 +586,7 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
     }
     if (ok) EX[i] = e;
     for (int kc = 0; kc < nch * kOzKC; kc += 8) {
-      uint32_t pk[kOzS][4];
+      uint32_t pk[kOzS][4], pks[kOzS][4];
 #pragma unroll
       for (int kk = 0; kk < 8; kk += 2) {
         int sv[2][kOzS];
@@ -611,13 +614,20 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
           const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[0][p]));
           const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[1][p]));
           pk[p][kk / 2] = lo | (hi << 16);
+          // the same integer times 2^-7 (exact in bf16): the B operand of the d = 8 products
+          const uint32_t los = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[0][p] * 0x1p-7f));
+          const uint32_t his = __bfloat16_as_ushort(__float2bfloat16_rn((float)sv[1][p] * 0x1p-7f));
+          pks[p][kk / 2] = los | (his << 16);
         }
       }
       const int c = kc / kOzKC, q = (kc % kOzKC) / 8;
 #pragma unroll
-      for (int p = 0; p < kOzS; ++p)
-        *reinterpret_cast<uint4*>(SL + oz_row(p, c, npad, i) + ((q ^ ((i >> 1) & 3)) * 8)) =
-            make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+      for (int p = 0; p < kOzS; ++p) {
+        const int64_t o = ((q ^ ((i >> 1) & 3)) * 8);
+        *reinterpret_cast<uint4*>(SL + oz_row(p, c, npad, i) + o) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+        *reinterpret_cast<uint4*>(SL + oz_row(kOzS + p, c, npad, i) + o) =
+            make_uint4(pks[p][0], pks[p][1], pks[p][2], pks[p][3]);
+      }
     }
   }
 }
@@ -625,7 +635,7 @@ __device__ void oz_slice(const double* Ls, int f, int i0, int kb0, int ke0, uint
 // the row exponents follow the slices of an n-row A
 __device__ __forceinline__ int* oz_ex(uint16_t* SL, int n) {
   const int npad = (n + kOzM - 1) / kOzM * kOzM;
-  return reinterpret_cast<int*>(SL + oz_row(kOzS, 0, npad, 0));
+  return reinterpret_cast<int*>(SL + oz_row(2 * kOzS, 0, npad, 0));
 }
 
 __device__ __forceinline__ void oz_expect(uint32_t bar, uint32_t bytes) {
@@ -639,14 +649,18 @@ __device__ __forceinline__ void oz_bulk(uint32_t dst, const void* src, uint32_t 
 
 // C -= A A^T on the lower triangle of the trailing matrix (rows [i0, f), columns [i0, ce); columns < w in Ls,
 // the others in W) from the slices.  Tiles of 128 rows x 32 columns with a column block not right of the row
-// block; per 32-deep chunk thread 0 loads the 9 A and 9 B slice operands with 18 bulk copies completing on the
-// stage's "full" mbarrier, then (one chunk behind) issues the 45 x 2 MMAs (slice pair p, q into accumulator
-// p + q at TMEM column 32 (p + q)) and commits them to the stage's "empty" mbarrier; after a tile's last chunk
-// the CTA combines the nine accumulators (epilogue above).  Every wait is bounded.
-__device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_t tmem, uint32_t& g,
-                          int* abort_flag, const uint16_t* SL, const int* EX, int n, int K, double* Ls, int f, int w,
-                          double* W, int r, int i0, int ce) {
+// block.  Warp 0 (one thread) loads each 32-deep chunk with 27 bulk copies (A slices, B slices, scaled B slices)
+// completing on the stage's "full" mbarrier and, one chunk behind, issues its 45 x 2 MMAs (slice pair p, q into
+// accumulator min(p + q, 7) of the tile's accumulator set: TMEM columns 256 (tile mod 2) + 32 accumulator) and
+// commits them to the stage's "empty" mbarrier, and after a tile's last chunk to the set's "accumulators full"
+// mbarrier.  Warps 4-7 combine the accumulators of each tile (epilogue above) while warp 0 already multiplies
+// the next tile into the other set, and release the set on its "accumulators empty" mbarrier (one arrival per
+// warp).  tcnt counts the CTA's tiles (the sets' phases).  Every wait is bounded.
+__device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint64_t* afull, uint64_t* aempty,
+                          uint32_t tmem, uint32_t& g, uint32_t& tcnt, int* abort_flag, const uint16_t* SL,
+                          const int* EX, int n, int K, double* Ls, int f, int w, double* W, int r, int i0, int ce) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  volatile int* abortv = abort_flag;
   const int ntm = (n + kOzM - 1) / kOzM, npad = ntm * kOzM;
   const int nce = ce - i0;               // columns of C
   constexpr int kTnPerTm = kOzM / kOzN;  // column blocks per row block
@@ -657,7 +671,7 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_
   const int total = ntile * nck;
   if (total == 0) return true;
   const uint32_t sb0 = smem_u32(ring);
-  const uint32_t g0 = g;
+  const uint32_t g0 = g, t0 = tcnt;
   constexpr uint32_t idesc = idesc_m128(1u, (uint32_t)kOzN);
   auto tile_of = [&](int t, int& tm, int& tn) {
     tm = 0;
@@ -669,85 +683,103 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_
     }
     tn = t;
   };
-  int last_load = -1, last_mma = -1;  // thread 0: for the drain after a wait gave up
-  auto load = [&](int q) {  // thread 0: the 18 bulk copies of chunk q into its stage
-    last_load = q;
-    const uint32_t st = (g0 + q) % kOzStages, sbase = sb0 + st * kOzStage;
-    const uint32_t full = smem_u32(&fbar[st]);
-    const int ck = q % nck;
-    int tm, tn;
-    tile_of(q / nck, tm, tn);
-    oz_expect(full, (uint32_t)kOzStage);
-#pragma unroll 1
-    for (int p = 0; p < kOzS; ++p) {
-      oz_bulk(sbase + p * kOzOpA, SL + oz_row(p, ck, npad, tm * kOzM), kOzOpA, full);
-      oz_bulk(sbase + kOzS * kOzOpA + p * kOzOpB, SL + oz_row(p, ck, npad, tn * kOzN), kOzOpB, full);
-    }
-  };
-  bool okall = true;
   __syncthreads();  // the slices are written and the ring's earlier generic use is over
-  if (tid == 0) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int q = 0; q < kOzStages - 1 && q < total; ++q) load(q);
-  }
-  for (int j = 0; j < total; ++j) {
-    const int ck = j % nck;
-    const uint32_t st = (g0 + j) % kOzStages;
-    if (tid == 0 && !*abort_flag) {  // after a wait gave up nothing more is issued or waited for
-      bool ok = true;
-      // the next chunk's stage: free once the MMAs of the chunk that used it have completed
-      const int q = j + kOzStages - 1;
-      if (q < total) {
-        if (q >= kOzStages) {
-          const uint32_t gp = g0 + q - kOzStages;
-          ok = mbar_wait(smem_u32(&gbar[gp % kOzStages]), (gp / kOzStages) & 1);
+  if (warp == 0) {
+    if (lane == 0) {
+      int last_load = -1, last_mma = -1;
+      auto load = [&](int q) {  // the 27 bulk copies of chunk q into its stage
+        last_load = q;
+        const uint32_t st = (g0 + q) % kOzStages, sbase = sb0 + st * kOzStage;
+        const uint32_t full = smem_u32(&fbar[st]);
+        const int ck = q % nck;
+        int tm, tn;
+        tile_of(q / nck, tm, tn);
+        oz_expect(full, (uint32_t)kOzStage);
+#pragma unroll 1
+        for (int p = 0; p < kOzS; ++p) {
+          oz_bulk(sbase + p * kOzOpA, SL + oz_row(p, ck, npad, tm * kOzM), kOzOpA, full);
+          oz_bulk(sbase + kOzS * kOzOpA + p * kOzOpB, SL + oz_row(p, ck, npad, tn * kOzN), kOzOpB, full);
+          oz_bulk(sbase + kOzS * (kOzOpA + kOzOpB) + p * kOzOpB, SL + oz_row(kOzS + p, ck, npad, tn * kOzN), kOzOpB,
+                  full);
         }
-        if (ok) load(q);
-      }
-      if (ok) ok = mbar_wait(smem_u32(&fbar[st]), ((g0 + j) / kOzStages) & 1);
-      if (!ok) {
-        *abort_flag = 1;
-      } else {
+      };
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bool ok = true;
+      load(0);
+      for (int j = 0; j < total && ok; ++j) {
+        const int ck = j % nck, tile = j / nck;
+        const uint32_t st = (g0 + j) % kOzStages, tg = t0 + tile, set = tg & 1;
+        const int q = j + 1;  // the next chunk: its stage is free once the MMAs of the chunk that used it are done
+        if (q < total) {
+          if (q >= kOzStages) {
+            const uint32_t gp = g0 + q - kOzStages;
+            ok = mbar_wait(smem_u32(&gbar[gp % kOzStages]), (gp / kOzStages) & 1);
+          }
+          if (ok) load(q);
+        }
+        // a tile's first chunk: its accumulator set is free once the epilogue of the tile two before is done
+        if (ok && ck == 0 && tg >= 2) ok = mbar_wait(smem_u32(&aempty[set]), ((tg >> 1) - 1) & 1);
+        if (ok) ok = mbar_wait(smem_u32(&fbar[st]), ((g0 + j) / kOzStages) & 1);
+        if (ok && *abortv) ok = false;
+        if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sA = sb0 + st * kOzStage, sB = sA + kOzS * kOzOpA;
+        const uint32_t sA = sb0 + st * kOzStage, sB = sA + kOzS * kOzOpA, sBs = sB + kOzS * kOzOpB;
+        const uint32_t acc0 = tmem + set * kOzSetCols;
 #pragma unroll 1
         for (int p = 0; p < kOzS; ++p)
 #pragma unroll 1
-          for (int qq = 0; qq < kOzS - p; ++qq)
+          for (int qq = 0; qq < kOzS - p; ++qq) {
+            const bool d8 = p + qq == kOzAcc;  // the d = 8 pairs go into accumulator 7 with B scaled by 2^-7
+            const uint32_t acc = acc0 + (uint32_t)((d8 ? kOzAcc - 1 : p + qq) * kOzN);
+            const uint32_t bq = (d8 ? sBs : sB) + qq * kOzOpB;
 #pragma unroll
             for (int kk = 0; kk < kOzKC / 16; ++kk)
-              mma_f16(tmem + (uint32_t)((p + qq) * kOzN), sw64_desc(sA + p * kOzOpA + kk * 32),
-                      sw64_desc(sB + qq * kOzOpB + kk * 32), idesc, (ck > 0 || p > 0 || kk > 0) ? 1u : 0u);
+              mma_f16(acc, sw64_desc(sA + p * kOzOpA + kk * 32), sw64_desc(bq + kk * 32), idesc,
+                      (ck > 0 || p > 0 || kk > 0 || d8) ? 1u : 0u);
+          }
         mma_commit(smem_u32(&gbar[st]));
+        if (ck == nck - 1) mma_commit(smem_u32(&afull[set]));
         last_mma = j;
       }
+      if (!ok) {
+        *abortv = 1;
+        // wait (bounded) for the last copies and MMAs issued
+        if (last_mma >= 0) {
+          const uint32_t gq = g0 + last_mma;
+          mbar_wait(smem_u32(&gbar[gq % kOzStages]), (gq / kOzStages) & 1);
+        }
+        if (last_load > last_mma) {
+          const uint32_t gq = g0 + last_load;
+          mbar_wait(smem_u32(&fbar[gq % kOzStages]), (gq / kOzStages) & 1);
+        }
+      }
     }
-    if (ck != nck - 1) {
-      if (tid == 0 && *abort_flag) okall = false;
-      continue;
-    }
-    if (tid == 0 && !*abort_flag && !mbar_wait(smem_u32(&gbar[st]), ((g0 + j) / kOzStages) & 1)) *abort_flag = 1;
-    __syncthreads();
-    if (*abort_flag) {
-      okall = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
+    __syncwarp();
+  } else if (warp >= 4) {
+    const int q4 = warp % 4;  // TMEM lane quarter: rows q4 * 32 .. + 31 of the tile
+    for (int tile = 0; tile < ntile; ++tile) {
+      const uint32_t tg = t0 + tile, set = tg & 1;
+      int ok = 1;
+      if (lane == 0) ok = !*abortv && mbar_wait(smem_u32(&afull[set]), (tg >> 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *abortv = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int tm, tn;
-      tile_of(j / nck, tm, tn);
-      const int q4 = warp % 4, h = warp / 4;  // TMEM lane quarter (rows), column half
+      tile_of(tile, tm, tn);
       const int ri = tm * kOzM + q4 * 32 + lane;  // row of C (relative to i0)
       const int gi = i0 + ri;
       const int ei = ri < n ? EX[ri] : 0;
 #pragma unroll 1
-      for (int cg = 0; cg < kOzN / 16; ++cg) {
-        const int cbase = tn * kOzN + h * (kOzN / 2) + cg * 8;  // first column of this group (relative to i0)
-        uint32_t a[kOzS][8];
+      for (int cg = 0; cg < kOzN / 8; ++cg) {
+        const int cbase = tn * kOzN + cg * 8;  // first column of this group (relative to i0)
+        uint32_t a[kOzAcc][8];
 #pragma unroll
-        for (int d = 0; d < kOzS; ++d)
-          tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * kOzN + h * (kOzN / 2) + cg * 8), a[d]);
+        for (int d = 0; d < kOzAcc; ++d)
+          tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(set * kOzSetCols + d * kOzN + cg * 8), a[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (ri < n) {
 #pragma unroll
@@ -760,7 +792,7 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_
                 I += (long long)__float2int_rn(__uint_as_float(a[d][e])) << (7 * (4 - d));
               float small = 0.f;  // sum_{d >= 5} acc_d 2^(-7 (d - 4)), Horner from the smallest
 #pragma unroll
-              for (int d = kOzS - 1; d >= 5; --d) small = (small + __uint_as_float(a[d][e])) * 0x1p-7f;
+              for (int d = kOzAcc - 1; d >= 5; --d) small = (small + __uint_as_float(a[d][e])) * 0x1p-7f;
               const double t = (double)I + (double)small;
               const int ex = ei + EX[cj] - 40;
               const double sc = ex >= -1022 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
@@ -770,25 +802,15 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint32_
           }
         }
       }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-  }
-  // a wait given up may leave copies or MMAs in flight: wait (bounded) for the last ones issued
-  if (tid == 0 && *abort_flag) {
-    if (last_mma >= 0) {
-      const uint32_t gq = g0 + last_mma;
-      mbar_wait(smem_u32(&gbar[gq % kOzStages]), (gq / kOzStages) & 1);
-    }
-    if (last_load > last_mma) {
-      const uint32_t gq = g0 + last_load;
-      mbar_wait(smem_u32(&fbar[gq % kOzStages]), (gq / kOzStages) & 1);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[set])) : "memory");
     }
   }
-  __syncthreads();
-  okall = !*abort_flag;
+  __syncthreads();  // every role has finished this update
   g = g0 + total;
-  return okall;
+  tcnt = t0 + ntile;
+  return !*abortv;
 }
 
 // The large fronts (P.sn_big), one task of the plan's split per item (subdomain, task, global task id, parent's
@@ -805,6 +827,7 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
   uint8_t* ring = oz_raw + ((1024u - (smem_u32(oz_raw) & 1023u)) & 1023u);
   Smem& sm = *reinterpret_cast<Smem*>(ring);  // the FP64 steps' buffers (never in use with the ring)
   __shared__ uint64_t gbar[kOzStages], fbar[kOzStages];  // per stage: MMAs done ("empty"), copies landed ("full")
+  __shared__ uint64_t afull[2], aempty[2];  // per accumulator set: tile multiplied / epilogue done
   __shared__ uint32_t tmem_s;
   __shared__ int abort_s, bad;
   __shared__ double red[kThreads / 32];
@@ -819,6 +842,10 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gbar[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar[k])));
     }
+    for (int k = 0; k < 2; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&afull[k])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&aempty[k])));  // the 4 epilogue warps
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
   }
@@ -826,7 +853,7 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_s;
-  uint32_t g = 0;
+  uint32_t g = 0, tcnt = 0;
   double* W = ws + (int64_t)blockIdx.x * ws_stride;
   double* stack = W + front_sz;
   uint16_t* SL = slices + (int64_t)blockIdx.x * slice_stride;
@@ -891,14 +918,16 @@ __global__ void __launch_bounds__(kThreads, 1) chol_tc_kernel(DevPlan P, const i
             if (ke < kE) {
               int* EX = oz_ex(SL, f - ke);
               oz_slice(Ls, f, ke, kb, ke, SL, EX);
-              okf = oz_update(ring, gbar, fbar, tmem, g, &abort_s, SL, EX, f - ke, ke - kb, Ls, f, w, W, r, ke, kE);
+              okf = oz_update(ring, gbar, fbar, afull, aempty, tmem, g, tcnt, &abort_s, SL, EX, f - ke, ke - kb, Ls, f,
+                              w, W, r, ke, kE);
             }
           }
           // the rank-128 update of the rest of the front
           if (okf && kE < f) {
             int* EX = oz_ex(SL, f - kE);
             oz_slice(Ls, f, kE, kB, kE, SL, EX);
-            okf = oz_update(ring, gbar, fbar, tmem, g, &abort_s, SL, EX, f - kE, kE - kB, Ls, f, w, W, r, kE, f);
+            okf = oz_update(ring, gbar, fbar, afull, aempty, tmem, g, tcnt, &abort_s, SL, EX, f - kE, kE - kB, Ls, f,
+                            w, W, r, kE, f);
           }
         }
       }
@@ -1731,7 +1760,7 @@ void launch_chol_tc(const DevPlan& P, const int4* items, int nitems, int* queue,
 
 int64_t chol_tc_scratch(int fmax) {
   const int64_t npad = (fmax + kOzM - 1) / kOzM * kOzM;
-  return (npad * (kOzS * kOzK + 2) + 127) / 128 * 128;
+  return (npad * (2 * kOzS * kOzK + 2) + 127) / 128 * 128;
 }
 
 int chol_ctas_per_sm() {
