@@ -532,9 +532,9 @@ __global__ void __launch_bounds__(kThreads, 4) chol_kernel(DevPlan P, const int4
 // e_i the largest exponent in the row, and its 63 leading fixed-point bits are cut into 9 signed 7-bit
 // integers s_p (p = 0 most significant), each exact in bf16, so A_ik = 2^(e_i - 6) sum_p s_p,ik 2^(-7p) up to
 // 2^(e_i - 62).  The products of slices p, q (p + q <= 8, 45 pairs) are summed over K = 128 on the tensor cores
-// with FP32 accumulation, one TMEM accumulator per d = p + q.  For d <= 7 every partial sum is an integer below
-// (d + 1) 128 127^2 < 2^24, so those FP32 sums are exact (d = 8 may round by one unit, at 2^-56 of the leading
-// scale).  The epilogue combines them,
+// with FP32 accumulation, one TMEM accumulator per d = p + q <= 7 (the d = 8 products into the d = 7 one, their
+// B slices scaled by 2^-7).  For d <= 6 every partial sum is an integer below (d + 1) 128 127^2 < 2^24, so those
+// FP32 sums are exact; the d = 7 one lies 2^-49 below the leading scale.  The epilogue combines them,
 // sum_k A_ik A_jk = 2^(e_i + e_j - 40) (sum_{d <= 4} acc_d 2^(7 (4 - d)) + sum_{d >= 5} acc_d 2^(7 (4 - d))),
 // the first sum exactly in 64-bit integers, the small rest in FP32 (its rounding below 2^-53 of K sigma_i sigma_j,
 // sigma = 2^(e + 1)), and applies C_ij -= that with one FP64 FMA.  The dropped pairs (p + q >= 9) and the cut
@@ -814,8 +814,8 @@ __device__ bool oz_update(uint8_t* ring, uint64_t* gbar, uint64_t* fbar, uint64_
 }
 
 // The large fronts (P.sn_big), one task of the plan's split per item (subdomain, task, global task id, parent's
-// global task id), children before parents; one CTA per SM (the stage ring takes 181 KB of shared memory and
-// the nine accumulators 288 of the 512 TMEM columns), all resident.  The fronts' children outside the set
+// global task id), children before parents; one CTA per SM (the stage ring takes 217 KB of shared memory and
+// the two accumulator sets all 512 TMEM columns), all resident.  The fronts' children outside the set
 // handed their update blocks over (chol_kernel ran first); a large child task's block comes from its hand-over
 // slot after a bounded wait on the task's counter of finished large children (tdone), others through the
 // CTA's stack as in chol_kernel.  The same flags as chol_kernel.

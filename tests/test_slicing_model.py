@@ -2,8 +2,9 @@
 the rank-k updates of its large fronts (`chol_tc_kernel`): every FP64 entry
 of a row scaled by 2^(e_i - 6) (e_i the row's largest exponent) and its 63
 leading fixed-point bits cut into 9 signed 7-bit integers; products of slices
-p, q with p + q <= 8 summed per d = p + q in FP32 (exact for d <= 7: every
-partial sum an integer below 2^24 for K = 128); recombined as
+p, q with p + q <= 8 summed per d = p + q in FP32, the d = 8 products into the
+d = 7 accumulator with a factor 2^-7 (exact for d <= 6: every partial sum an
+integer below 2^24 for K = 128); recombined as
 2^(e_i + e_j - 40) (sum_{d<=4} acc_d 2^(7(4-d)) + small), the first sum in
 64-bit integers, `small` the FP32 Horner sum of the d >= 5 accumulators.
 
@@ -11,7 +12,7 @@ The model repeats the kernel's arithmetic on the host (integer matrix products
 for the slice products, float32 for the small accumulators and their Horner
 sum, float64 for the last step) and checks it against the exact dot products
 (Python integers): the integer bounds behind the exactness claims (every
-accumulator with d <= 7 an integer below 2^24), and the error bound
+accumulator with d <= 6 an integer below 2^24), and the error bound
 K 2^-52 sigma_i sigma_j (sigma = 2^(e + 1) above every entry of the row: FP64's
 own normwise bound for a K-term dot product is larger), on rows whose entries
 spread over 2^-12 .. 1 of their largest."""
@@ -56,9 +57,11 @@ def _model(A):
             acc[p + q] += sl[p] @ sl[q].T
     bound = [int(np.abs(a).max()) for a in acc]
     I = sum(acc[d] << (7 * (4 - d)) for d in range(5))
+    # the kernel's eight accumulators: d = 8 folded into d = 7 (B slices scaled by 2^-7), summed in FP32
+    acc7 = (acc[7].astype(np.float64) + acc[8].astype(np.float64) / 128.0).astype(np.float32)
     small = np.zeros((n, n), dtype=np.float32)
-    for d in range(S - 1, 4, -1):
-        small = ((small + acc[d].astype(np.float32)) * np.float32(2.0 ** -7)).astype(np.float32)
+    for a in (acc7, acc[6].astype(np.float32), acc[5].astype(np.float32)):
+        small = ((small + a) * np.float32(2.0 ** -7)).astype(np.float32)
     t = I.astype(np.float64) + small.astype(np.float64)
     scale = np.ldexp(1.0, (ex[:, None] + ex[None, :] - 40).astype(np.int64))
     return t * scale, ex, bound
@@ -88,8 +91,8 @@ def test_slicing_exact_bound_and_error(seed):
     A = rng.choice([-1.0, 1.0], size=(n, K)) * 2.0 ** rng.uniform(-12, 0, size=(n, K)) * scale[:, None]
     A[rng.random((n, K)) < 0.05] = 0.0
     C, ex, bound = _model(A)
-    # exactness of the FP32 accumulators for d <= 7: (d + 1) K 127^2 < 2^24
-    for d in range(8):
+    # exactness of the FP32 accumulators for d <= 6: (d + 1) K 127^2 < 2^24
+    for d in range(7):
         assert bound[d] <= (d + 1) * K * 127 * 127 < 2 ** 24, (d, bound[d])
     worst = 0.0
     for i in range(n):
