@@ -128,9 +128,10 @@ typedef struct {
                                  SMs.  The factor is the same bit for bit either way */
   int32_t syrk_kernel;        /* split-bf16 SYRK kernel: 0 = autotuned at the first feti_assemble; 1, 2, 3 =
                                  feti_stats.syrk_variant 0, 1, 2 (the same F bit for bit) */
-  int32_t chol_tc;            /* 0 = the rank-128 updates of the fronts at least 384 wide run on the tensor
-                                 cores by exact slicing into bf16 integers (FP64 accuracy, see DESIGN); 1 = all
-                                 of the Cholesky on the FP64 pipe */
+  int32_t chol_tc;            /* 0 = the rank-32 and rank-128 updates of the fronts at least 384 wide run on
+                                 the tensor cores by exact slicing of FP64 into bf16 integers (integer partial
+                                 sums exact in FP32; error below FP64's own normwise bound); 1 = all of the
+                                 Cholesky on the FP64 pipe */
 } feti_options;
 
 typedef struct {
