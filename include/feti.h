@@ -132,6 +132,8 @@ typedef struct {
                                  the tensor cores by exact slicing of FP64 into bf16 integers (integer partial
                                  sums exact in FP32; error below FP64's own normwise bound); 1 = all of the
                                  Cholesky on the FP64 pipe */
+  int32_t chol_tc_front;      /* with chol_tc = 0: the narrowest front (w + r) taken by the tensor-core kernel,
+                                 with all its ancestors (0 = 384) */
 } feti_options;
 
 typedef struct {

@@ -255,7 +255,8 @@ void build(feti_ctx* c) {
     const double target = total / (4.0 * slots);
     // fronts at least 384 wide (and their ancestors) go to the tensor-core Cholesky unless switched off
     if (c->opt.chol_tc < 0 || c->opt.chol_tc > 1) throw ArgError("bad chol_tc (0 tensor cores for large fronts, 1 off)");
-    const int big_f = c->opt.chol_tc == 1 ? 0 : 384;
+    if (c->opt.chol_tc_front < 0) throw ArgError("bad chol_tc_front (0 default, else the narrowest front)");
+    const int big_f = c->opt.chol_tc == 1 ? 0 : (c->opt.chol_tc_front > 0 ? std::max(c->opt.chol_tc_front, 128) : 384);
     for (auto& P : c->pats) plan_tasks(P, target, big_f);
   }
   c->stats.t_symbolic_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();

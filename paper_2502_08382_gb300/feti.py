@@ -51,7 +51,7 @@ class FetiOptions(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p), ("leaf_dofs", C.c_int32),
                 ("use_coords", C.c_int32), ("refine_drop", C.c_double), ("refine_restart", C.c_int32),
                 ("precond", C.c_int32), ("adjoint_work_bytes", C.c_int64), ("assembly_route", C.c_int32),
-                ("chol_split", C.c_int32), ("syrk_kernel", C.c_int32), ("chol_tc", C.c_int32)]
+                ("chol_split", C.c_int32), ("syrk_kernel", C.c_int32), ("chol_tc", C.c_int32), ("chol_tc_front", C.c_int32)]
 
 
 class FetiSolveInfo(C.Structure):
@@ -246,7 +246,7 @@ class FetiOperator:
                  with_elements: bool = False, unit_scale: bool = False, per_element: bool = False,
                  recompute_X: bool = False, adjoint_work_bytes: int = 0, route: str = "syrk",
                  chol_split: str = "auto", syrk_kernel: int = -1, chol_tc: bool = True,
-                 torch_alloc: bool = True):
+                 chol_tc_front: int = 0, torch_alloc: bool = True):
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -275,6 +275,7 @@ class FetiOperator:
         opt.chol_split = {"auto": 0, "whole": 1, "tasks": 2}[chol_split]
         opt.syrk_kernel = 0 if syrk_kernel < 0 else syrk_kernel + 1
         opt.chol_tc = 0 if chol_tc else 1
+        opt.chol_tc_front = int(chol_tc_front)
         self._cb = None
         if torch_alloc:
             dev = self.device.index

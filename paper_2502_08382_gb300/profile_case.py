@@ -34,6 +34,7 @@ def main():
     ap.add_argument("--precond", default="none", choices=["none", "lumped", "dirichlet"])
     ap.add_argument("--route", default="syrk", choices=["syrk", "schur", "trsm", "auto"])
     ap.add_argument("--chol-split", default="auto", choices=["auto", "whole", "tasks"])
+    ap.add_argument("--chol-tc-front", type=int, default=0, help="narrowest front of the tensor-core Cholesky")
     args = ap.parse_args()
 
     import torch
@@ -45,7 +46,8 @@ def main():
     mixed = args.prec != "fp64"
     op = feti.FetiOperator(P, prec=args.prec, tol=1e-10, maxit=5000, refine_every=args.refine_every if mixed else 0,
                            refine_drop=args.refine_drop if mixed else 0.0, refine_restart=args.restart,
-                           precond=args.precond, route=args.route, chol_split=args.chol_split)
+                           precond=args.precond, route=args.route, chol_split=args.chol_split,
+                           chol_tc_front=args.chol_tc_front)
     op.assemble()
     p = torch.from_numpy(seeded_vector(P.n_lambda, 0)).cuda()
     q = torch.empty_like(p)
@@ -92,7 +94,7 @@ def main():
                       "refine_drop": args.refine_drop, "restart": args.restart, "precond": args.precond,
                       "route": args.route, "route_used": s["assembly_route"], "route_ms": s["route_ms"],
                       "phases_ms": {k: s[k] for k in ("t_chol_ms", "t_chol_tc_ms", "t_trsm_ms", "t_syrk_ms")},
-                      "trsm_cols": s["trsm_cols"], "trsm_grid": s["trsm_grid"], "syrk_variant": s["syrk_variant"], "chol_tasks": s["chol_tasks"], "chol_split": args.chol_split,
+                      "trsm_cols": s["trsm_cols"], "trsm_grid": s["trsm_grid"], "syrk_variant": s["syrk_variant"], "chol_tasks": s["chol_tasks"], "chol_split": args.chol_split, "chol_tc_front": args.chol_tc_front,
                       "solve": info, "launches": s["launches"], "profiled": prof}))
     op.close()
 
