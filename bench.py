@@ -57,6 +57,17 @@ REFINE_RESTART = True  # the search direction restarts after each FP64 residual 
 TOL = 1e-10
 
 
+def arm_config(workload, world):
+    """The workload and settings both arms name (the same dict on the reference line)."""
+    return {"workload": WORKLOADS[workload],
+            "prec": f"{PREC} SYRK and TRSM panel updates, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
+            "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual after each {1 / REFINE_DROP:.0e} "
+                    f"drop, CG direction restarted after it)",
+            "value": "explicit F.lambda apply GB/s (algorithmic bytes / F-streaming kernel time)",
+            "l2": "256 MB buffer written before each timed step; the F tiles of one apply exceed L2 (129 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -233,7 +244,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]},
+            "config": arm_config(args.workload, args.gpus),
             "assembly_ms_extrapolated": statistics.median(tf) * 1e3 * P.nsub,
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -409,14 +420,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload],
-                       "prec": f"{PREC} SYRK and TRSM panel updates, FP32 TRSM/F tiles, FP64 Cholesky/PCPG",
-                       "step": f"feti_assemble + feti_solve (tol {TOL}, FP64 residual after each {1 / REFINE_DROP:.0e} "
-                               f"drop, CG direction restarted after it)",
-                       "value": "explicit F.lambda apply GB/s (algorithmic bytes / F-streaming kernel time)",
-                       "l2": f"256 MB buffer written before each timed step; F tiles "
-                             f"{st_['F_elems'] * 4 / 1e6:.0f} MB > L2 (129 MB) per apply",
-                       "parallelism": f"replicas x{world}"},
+            "config": arm_config(args.workload, world),
+            "F_tile_mb": st_["F_elems"] * 4 / 1e6,
             "assembly_ms": {"mixed": t_asm, "fp64": statistics.median(asm64),
                             "speedup": statistics.median(asm64) / t_asm,
                             "mixed_phases": {k: st_last[k] for k in ("t_chol_ms", "t_trsm_ms", "t_syrk_ms")},
