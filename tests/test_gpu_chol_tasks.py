@@ -133,3 +133,27 @@ def test_tensor_core_cholesky(torch_cuda, name, route):
         worst = max(worst, np.linalg.norm(Fs[True][i] - Fo) / np.linalg.norm(Fo) / bar)
         assert d <= bar, (i, d)
     print(f"{name} {route}: tensor-core Cholesky F_i at most {worst:.3f} of the FP64 bar")
+
+
+@pytest.mark.parametrize("front", [128, 256])
+@pytest.mark.parametrize("name", ["elast3d_one_large", "cfg3_2x2x2"])
+def test_tensor_core_cholesky_front_threshold(torch_cuda, name, front):
+    """options.chol_tc_front hands narrower fronts (with all their ancestors) to the tensor-core kernel: its
+    time share grows, and F_i stays within the FP64 bar of the oracle."""
+    from paper_2502_08382_gb300 import feti
+    P = make_config(3, nsub_axis=2) if name == "cfg3_2x2x2" else CASES[name]()
+    op = feti.FetiOperator(P, prec="fp64", chol_tc_front=front)
+    op.assemble()
+    st = op.stats()
+    Fs = [op.get_F(i) for i in range(P.nsub)]
+    op.close()
+    assert st["t_chol_tc_ms"] > 0.0, st["t_chol_tc_ms"]
+    worst = 0.0
+    for i, s in enumerate(P.subs):
+        Fo = O.local_F(s)
+        err = np.linalg.norm(Fs[i] - Fo) / np.linalg.norm(Fo)
+        bar = F_bar("fp64", Fo, s.n)
+        worst = max(worst, err / bar)
+        assert err <= bar, (i, err)
+    print(f"{name} front {front}: F_i at most {worst:.3f} of the FP64 bar, Cholesky {st['t_chol_ms']:.2f} ms "
+          f"({st['t_chol_tc_ms']:.2f} ms tensor-core kernel)")
