@@ -166,7 +166,22 @@ __device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int 
       if (lane < nbk) sf[kb + lane] = yi;
     }
     __syncthreads();
-    for (int i = kb + nbk + tid; i < f_; i += kThreads) {
+    // rows in pairs (i, i + kThreads) per thread, so that each group of column loads has twice the bytes in
+    // flight; a last unpaired row alone.  Every row's sum runs over k in the same order either way.
+    int i = kb + nbk + tid;
+    for (; i + kThreads < f_; i += 2 * kThreads) {
+      double acc = 0.0, acc2 = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < nbk; ++k) {
+        const double* col = Ls + (int64_t)(kb + k) * f_;
+        const double zk = sf[kb + k];
+        acc = fma(col[i], zk, acc);
+        acc2 = fma(col[i + kThreads], zk, acc2);
+      }
+      sf[i] -= acc;
+      sf[i + kThreads] -= acc2;
+    }
+    if (i < f_) {
       double acc = 0.0;
 #pragma unroll 8
       for (int k = 0; k < nbk; ++k) acc = fma(Ls[(int64_t)(kb + k) * f_ + i], sf[kb + k], acc);
@@ -182,29 +197,86 @@ __device__ __forceinline__ void fwd_cta(const DevPlan& P, const SubInfo& S, int 
   __syncthreads();
 }
 
-// Whole CTA: backward step of a large supernode (x_rows already final).
-__device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int gs, double* y,
+// Whole CTA: backward step of a large supernode (x_rows already final).  The
+// entries x_rows are gathered into sf first; then each warp takes kBC own
+// columns at a time, so their column loads are in flight together (the dot
+// product of each column runs over the rows in the same order as with one
+// column per warp, and is reduced the same way).
+constexpr int kBC = 4;
+__device__ __forceinline__ void bwd_cta(const DevPlan& P, const SubInfo& S, int gs, double* y, double* sf,
                                         double (*sm_blk)[kW + 1], int tid) {
   const int warp = tid / 32, lane = tid % 32;
   const int c0 = P.sn_c0[gs], w = P.sn_w[gs], r = P.sn_r[gs], f_ = w + r;
   const double* Ls = P.L + S.L + P.Lofs[gs];
   const int* rows = P.rows + P.sn_rows[gs];
-  for (int l = warp; l < w; l += kThreads / 32) {
-    double acc = 0.0;
+  for (int k = tid; k < r; k += kThreads) sf[k] = y[rows[k]];
+  __syncthreads();
+  for (int l0 = warp * kBC; l0 < w; l0 += (kThreads / 32) * kBC) {
+    if (l0 + kBC <= w) {
+      double acc[kBC];
+      const double* col[kBC];
+#pragma unroll
+      for (int u = 0; u < kBC; ++u) {
+        acc[u] = 0.0;
+        col[u] = Ls + (int64_t)(l0 + u) * f_ + w;
+      }
+#pragma unroll 2
+      for (int k = lane; k < r; k += 32) {
+        const double xk = sf[k];
+#pragma unroll
+        for (int u = 0; u < kBC; ++u) acc[u] = fma(col[u][k], xk, acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kBC; ++u) {
+        double a = acc[u];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) y[c0 + l0 + u] -= a;
+      }
+    } else {
+      // the last w mod kBC columns one at a time (warp-uniform branch)
+      for (int l = l0; l < w; ++l) {
+        const double* col = Ls + (int64_t)l * f_ + w;
+        double a = 0.0;
 #pragma unroll 4
-    for (int k = lane; k < r; k += 32) acc = fma(Ls[(int64_t)l * f_ + w + k], y[rows[k]], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[c0 + l] -= acc;
+        for (int k = lane; k < r; k += 32) a = fma(col[k], sf[k], a);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) y[c0 + l] -= a;
+      }
+    }
   }
   __syncthreads();
   for (int kb = ((w - 1) / kW) * kW; kb >= 0; kb -= kW) {
     const int nbk = min(kW, w - kb);
-    for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
-      double acc = 0.0;
+    if (nbk == kW) {
+      // a full block: the warp's columns l = kb + warp + 8 u all at once
+      constexpr int kU = kW / (kThreads / 32);
+      double acc[kU];
+      const double* col[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        acc[u] = 0.0;
+        col[u] = Ls + (int64_t)(kb + warp + (kThreads / 32) * u) * f_;
+      }
+#pragma unroll 2
+      for (int i = kb + nbk + lane; i < w; i += 32) {
+        const double xi = y[c0 + i];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) acc[u] = fma(col[u][i], xi, acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        double a = acc[u];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) y[c0 + kb + warp + (kThreads / 32) * u] -= a;
+      }
+    } else {
+      for (int l = kb + warp; l < kb + nbk; l += kThreads / 32) {
+        double acc = 0.0;
 #pragma unroll 4
-      for (int i = kb + nbk + lane; i < w; i += 32) acc = fma(Ls[(int64_t)l * f_ + i], y[c0 + i], acc);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[c0 + l] -= acc;
+        for (int i = kb + nbk + lane; i < w; i += 32) acc = fma(Ls[(int64_t)l * f_ + i], y[c0 + i], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[c0 + l] -= acc;
+      }
     }
     for (int idx = tid; idx < nbk * kW; idx += kThreads) {
       const int k = idx / kW, i = idx % kW;
@@ -304,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 4) implicit_kernel(DevPlan P, const 
         const int gs = S.sn0 + lsn[it];
         const int w = P.sn_w[gs], f_ = w + P.sn_r[gs];
         if (w <= 32 && f_ <= kWF) continue;
-        bwd_cta(P, S, gs, y, sm_blk, tid);
+        bwd_cta(P, S, gs, y, sfront, sm_blk, tid);
       }
     }
     __syncthreads();
