@@ -418,7 +418,12 @@ def main():
     impl64_ms = st64i["implicit_ms"] / max(st64i["implicit_calls"], 1)
     cpu_leg = rank == 0 and world == 1 and not args.no_cpu_baseline
     ns_cpu = 4 if args.workload == 2 else 1
-    F64_sample = [op64.get_F(i) for i in range(ns_cpu)] if cpu_leg else None
+    F64_sample = None
+    if cpu_leg:
+        try:
+            F64_sample = [op64.get_F(i) for i in range(ns_cpu)]
+        except Exception:  # the comparison is reported, never allowed to stop the bench
+            F64_sample = None
     op64.close()
     t_asm = statistics.median(asm)
     st_last = op.stats()
@@ -458,11 +463,14 @@ def main():
     if cpu_leg:
         gbs, t_f, t_ap, Fo = oracle_sample(P, ns_cpu, 300 if args.workload == 2 else 20, keep_F=True)
         # the CPU leg's oracle F_i of the same subdomains: relative Frobenius errors of both GPU paths
-        line["errors"]["F_fp64_vs_oracle"] = max(float(np.linalg.norm(F64_sample[i] - Fo[i]) / np.linalg.norm(Fo[i]))
-                                                 for i in range(ns_cpu))
-        line["errors"]["F_mixed_vs_oracle"] = max(float(np.linalg.norm(op.get_F(i) - Fo[i]) / np.linalg.norm(Fo[i]))
-                                                  for i in range(ns_cpu))
-        line["errors"]["F_vs_oracle_sample"] = f"subdomains 0..{ns_cpu - 1} (the CPU baseline's oracle F_i)"
+        try:
+            rel = lambda A, i: float(np.linalg.norm(A - Fo[i]) / np.linalg.norm(Fo[i]))
+            if F64_sample is not None:
+                line["errors"]["F_fp64_vs_oracle"] = max(rel(F64_sample[i], i) for i in range(ns_cpu))
+            line["errors"]["F_mixed_vs_oracle"] = max(rel(op.get_F(i), i) for i in range(ns_cpu))
+            line["errors"]["F_vs_oracle_sample"] = f"subdomains 0..{ns_cpu - 1} (the CPU baseline's oracle F_i)"
+        except Exception as exc:
+            line["errors"]["F_vs_oracle_sample"] = f"not computed: {type(exc).__name__}"
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{ns_cpu} of {P.nsub} subdomains: scipy dense Cholesky F_i "
                                           f"({t_f * 1e3:.0f} ms each) and {300 if args.workload == 2 else 20} "
