@@ -3,10 +3,11 @@
 Default workload (3): 3D linear elasticity, Hex8, the unit cube cut into
 8 x 8 x 8 = 512 subdomains of 12^3 elements (6591 DOFs each, m_i 1407..2814,
 n_lambda = 664 800), E = 1, nu = 0.3, clamped at x = 0, body force (0, 0, -1):
-the largest of the forward configurations (6.7 GB of FP32 F tiles; the
-sensitivity configuration, 8.0 GB, runs with `--workload 5`).  `--workload 2|4|5` runs the other configurations (2: 2D lognormal
-heat, 1024 subdomains of 4225 DOFs; 4: uneven 3D heat; 5: the sensitivity
-configuration's mesh).  Seeded synthetic inputs; the paper's data are not used.
+the largest of the forward configurations (6.7 GB of FP32 F tiles).
+`--workload 2|4|5` runs the other configurations (2: 2D lognormal heat, 1024
+subdomains of 4225 DOFs; 4: uneven 3D heat; 5: the sensitivity
+configuration, 8.0 GB of F tiles, with its adjoint timed).  Seeded synthetic
+inputs; the paper's data are not used.
 
 A step is one pass of the whole path, on the mixed-precision configuration
 (FP64 Cholesky; FP32 pruned TRSM with split-bf16 tensor-core panel updates;
