@@ -128,6 +128,9 @@ class Clocks:
         return out
 
 
+# GB300's nominal HBM3e bandwidth, reported beside the measured copy peak
+HBM_NOMINAL_GBS = 7900.0
+
 # Peaks of the SIMT pipes, derived from GB300's unit counts at the 2070 MHz maximum SM clock:
 # FP64 1.25 TFLOP/s nominal (an FMA probe on this GPU measured 1.20), FP32 152 SMs x 128 FMA x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.25
@@ -454,7 +457,8 @@ def main():
             "break_even_iters": n_star,
             "roofline": {"bound": "hbm", "achieved": tiles_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": tiles_gbs / hbm, "traffic": traffic, "traffic_source": traffic_src,
-                         "kernel": kname, "peak_kind": pk_kind},
+                         "kernel": kname, "peak_kind": pk_kind,
+                         "frac_of_nominal": tiles_gbs / HBM_NOMINAL_GBS, "nominal_gbs": HBM_NOMINAL_GBS},
             "roofline_other": other_rooflines(st_last, impl64_ms, hbm),
             "e2e": {"value": e2e_gbs * world, "unit": "GB/s", "h2d_bytes_per_step": 8 * P.n_lambda,
                     "d2h_bytes_per_step": 8 * P.n_lambda},
