@@ -479,3 +479,53 @@ def test_scaled_lumped_preconditioner(tiny_el, cfg1):
     um = O.monolithic_solve(cfg1)
     err = max(np.abs(u - um[s.l2g]).max() for s, u in zip(cfg1.subs, res["u"]))
     assert err <= 1e-10 * np.abs(um).max()
+
+
+# ------------------------------------------------------------- e, d and Z
+
+
+def test_e_vector_closed_form(cfg1, tiny_el):
+    """e = R^T f (eq. 7) against the integrals of the load (consistent loads of bilinear / trilinear elements
+    reproduce constants and linear functions).  Heat with f = 1 and R = 1: each subdomain's area, 1/16 on
+    workload 1.  Elasticity with the body force (0, 0, -1): (0, 0, -volume) for the translations and zero for
+    the rotations, whose moments are taken about the subdomain's centroid."""
+    e = O.e_vector(cfg1)
+    assert e.shape == (16,)
+    assert np.abs(e - 1.0 / 16.0).max() <= 1e-15
+    e = O.e_vector(tiny_el).reshape(-1, 6)
+    for s, ei in zip(tiny_el.subs, e):
+        ext = s.coords.max(axis=0) - s.coords.min(axis=0)
+        vol = float(np.prod(ext))
+        want = np.array([0.0, 0.0, -vol, 0.0, 0.0, 0.0])
+        assert np.abs(ei - want).max() <= 1e-14 * max(1.0, vol), (ei, want)
+
+
+def test_d_vector_routes_and_sign(cfg1):
+    """d = B K^+ f - c (eq. 7): against a sparse LU solve of K_reg (an independent factorisation of the same
+    generalised inverse), and, with the load removed and c nonzero, exactly -c."""
+    import copy
+
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    d = O.d_vector(cfg1)
+    dd = -np.asarray(cfg1.c, dtype=np.float64).copy()
+    for s in cfg1.subs:
+        x = spla.splu(sp.csc_matrix(O.K_reg(s))).solve(s.f)
+        np.add.at(dd, np.asarray(s.B_lambda, dtype=np.int64), s.B_sign * x[s.B_dof])
+    assert np.linalg.norm(d - dd) <= 1e-12 * np.linalg.norm(d)
+    P0 = copy.deepcopy(cfg1)
+    for s in P0.subs:
+        s.f = np.zeros_like(s.f)
+    P0.c = np.random.default_rng(5).standard_normal(P0.n_lambda)
+    assert np.array_equal(O.d_vector(P0), -P0.c)
+
+
+def test_local_Z_against_schur_route(cfg1, tiny_el):
+    """Z_i = K_reg^{-1} B_i^T (the adjoint's Z): B_i Z_i equals F_i of the Schur-complement route (eq. 13, LU
+    solves on the interior block, no Cholesky)."""
+    for P in (cfg1, tiny_el):
+        for s in P.subs[:4]:
+            Z = O.local_Z(s)
+            assert Z.shape == (s.n, s.m)
+            Fs = O.local_F_schur(s)
+            assert np.linalg.norm(O.B_dense(s) @ Z - Fs) <= 1e-12 * np.linalg.norm(Fs)
