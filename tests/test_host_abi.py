@@ -132,6 +132,44 @@ def test_symbolic_vs_brute_force(lib, case, use_coords):
         assert info["m"] == sub.m
 
 
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_trsm_syrk_counts(lib, case):
+    """The algorithmic TRSM and SYRK flop counts that the rooflines divide by, recomputed from the plan:
+    column j of X = L^{-1} P B^T starts in the supernode holding its permuted DOF and reaches every supernode
+    on the path to the root, so J_s counts the columns starting in the subtree of s; TRSM = sum_s J_s (w_s^2 +
+    2 w_s r_s), SYRK = sum_s w_s J_s (J_s + 1), X = sum_s ceil8(w_s) J_s stored values (rows padded to 8).  The SYRK count is
+    bounded by the suffix model sum_{a <= b} 2 (n - max(s_a, s_b)) and the TRSM count by the model that
+    counts each supernode's triangle twice, sum_s J_s 2 w_s (w_s + r_s)."""
+    P = make_problem(**CASES[case])
+    for sub in P.subs[:3]:
+        info = feti.analyse(sub, leaf_dofs=16)
+        n = sub.n
+        perm = info["perm"]
+        iperm = np.empty(n, dtype=np.int64)
+        iperm[perm] = np.arange(n)
+        w, par, r = info["sn_w"].astype(np.int64), info["sn_parent"], info["sn_r"].astype(np.int64)
+        col2sn = np.repeat(np.arange(len(w)), w)
+        J = np.zeros(len(w), dtype=np.int64)
+        start = iperm[np.asarray(sub.B_dof, dtype=np.int64)]
+        for p0 in start:
+            t = int(col2sn[p0])
+            while t >= 0:
+                J[t] += 1
+                t = int(par[t])
+        trsm = float(np.sum(J * (w * w + 2 * w * r)))
+        syrk = float(np.sum(w * J * (J + 1)))
+        xs = float(np.sum(((w + 7) // 8 * 8) * J))
+        assert info["trsm_flops"] == pytest.approx(trsm, rel=1e-12)
+        assert info["syrk_flops"] == pytest.approx(syrk, rel=1e-12)
+        assert info["Xsize"] == xs
+        sa = np.sort(start)
+        m = len(sa)
+        # sum over a <= b of 2 (n - max(s_a, s_b)): with sorted starts, pair (a, b <= a) has max s_a
+        suffix = float(np.sum(2.0 * (n - sa) * (np.arange(m) + 1)))
+        assert syrk <= suffix
+        assert trsm <= float(np.sum(J * 2 * w * (w + r))) <= 2 * trsm
+
+
 def test_nested_dissection_reduces_fill(lib):
     """On a 64 x 64 Q1 grid (the 2D heat subdomain) the exact fill of the
     nested-dissection order is well below the banded fill of the natural
