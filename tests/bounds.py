@@ -33,7 +33,7 @@ U_TF32 = 2.0 ** -11
 U_ACC = 2.0 ** -23
 SPLIT_OPERAND = 3 * 2.0 ** -16
 SPLIT_BAR = 1e-4      # relative Frobenius error of split-bf16 F_i against the FP64 oracle
-FP64_BAR = 1e-12      # the plain FP64 path (spec bar)
+FP64_BAR = 1e-12      # the plain FP64 path: relative Frobenius error of F_i
 
 
 def gamma(k: int, u: float = U_ACC) -> float:
